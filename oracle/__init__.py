@@ -1,0 +1,186 @@
+"""CPU FP64 oracle for the second-order nested-grid thin-disk force.
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers.  The product path (the
+CUDA library under ``paper_1603_03142_gb300``) never imports this package, and
+this package imports nothing from it.
+
+The arithmetic lives in ``oracle.c`` (plain C, FP64, OpenMP over targets):
+a direct O(N^4) sum, over every source cell of every level, of the exact cell
+integrals of the linear density of Eq. (eqnSigma) against the force kernel
+(Sec. 2.1).  This module only builds and loads that library and marshals numpy
+arrays.  Nest descriptors are duck-typed: any object with ``n``, ``levels``,
+``x0``, ``y0``, ``h0`` and ``off`` (a sequence of ``(ox, oy)`` per level,
+entry 0 unused) works.
+
+Parity status of each function is stated in the design notes; every function
+here is pinned by a ``-m "not gpu"`` test against quadrature, closed forms or
+invariants (tests/test_oracle_*.py).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "oracle.c"
+_LIB = _HERE / "liboracle.so"
+MAX_LEVELS = 8
+
+
+class _Nest(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int),
+        ("levels", ctypes.c_int),
+        ("x0", ctypes.c_double),
+        ("y0", ctypes.c_double),
+        ("h0", ctypes.c_double),
+        ("off", (ctypes.c_int * 2) * MAX_LEVELS),
+    ]
+
+
+def build_oracle(force: bool = False) -> Path:
+    """Compile oracle.c into liboracle.so next to it (gcc, -O2, OpenMP)."""
+    if _LIB.exists() and not force and _LIB.stat().st_mtime >= _SRC.stat().st_mtime:
+        return _LIB
+    tmp = _LIB.with_suffix(f".so.tmp{os.getpid()}")
+    cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11", "-o", str(tmp), str(_SRC), "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build_oracle()
+        lib = ctypes.CDLL(str(_LIB))
+        dp = ctypes.POINTER(ctypes.c_double)
+        dpp = ctypes.POINTER(dp)
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.oracle_cell_integrals.argtypes = [ctypes.c_double] * 4 + [dp]
+        lib.oracle_cell_integrals.restype = None
+        lib.oracle_validate.argtypes = [ctypes.POINTER(_Nest)]
+        lib.oracle_validate.restype = ctypes.c_int
+        lib.oracle_prepare.argtypes = [ctypes.POINTER(_Nest), dpp, dpp, dpp, dpp]
+        lib.oracle_prepare.restype = ctypes.c_int
+        lib.oracle_force_targets.argtypes = [ctypes.POINTER(_Nest), dpp, dpp, dpp, ctypes.c_long,
+                                             ip, ip, ip, dp, dp, ctypes.c_int]
+        lib.oracle_force_targets.restype = ctypes.c_int
+        lib.oracle_max_threads.argtypes = []
+        lib.oracle_max_threads.restype = ctypes.c_int
+        for name in ("oracle_genconv_case2", "oracle_genconv_case3"):
+            fn = getattr(lib, name)
+            fn.argtypes = [dp, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int]
+            fn.restype = None
+        _lib = lib
+    return _lib
+
+
+def _nest(desc) -> _Nest:
+    g = _Nest()
+    g.n, g.levels = int(desc.n), int(desc.levels)
+    g.x0, g.y0, g.h0 = float(desc.x0), float(desc.y0), float(desc.h0)
+    for l in range(1, int(desc.levels)):
+        g.off[l][0], g.off[l][1] = int(desc.off[l][0]), int(desc.off[l][1])
+    return g
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ptr_array(arrs):
+    return (ctypes.POINTER(ctypes.c_double) * len(arrs))(*[_dp(a) for a in arrs])
+
+
+def max_threads() -> int:
+    return int(_load().oracle_max_threads())
+
+
+def cell_integrals(a: float, b: float, c: float, d: float) -> np.ndarray:
+    """Exact integrals over [a,b]x[c,d] of u/r^3, v/r^3, u^2/r^3, v^2/r^3, uv/r^3."""
+    out = np.zeros(5)
+    _load().oracle_cell_integrals(a, b, c, d, _dp(out))
+    return out
+
+
+def validate(desc) -> bool:
+    return _load().oracle_validate(ctypes.byref(_nest(desc))) == 0
+
+
+def prepare(desc, sigma):
+    """Source fields of Eq. (eqnSigma) per level: (sig, dsig/dx, dsig/dy), covered cells 0."""
+    n, L = int(desc.n), int(desc.levels)
+    sin = [np.ascontiguousarray(s, dtype=np.float64).reshape(n, n) for s in sigma]
+    if len(sin) != L:
+        raise ValueError("need one sigma array per level")
+    sig = [np.zeros((n, n)) for _ in range(L)]
+    dsx = [np.zeros((n, n)) for _ in range(L)]
+    dsy = [np.zeros((n, n)) for _ in range(L)]
+    rc = _load().oracle_prepare(ctypes.byref(_nest(desc)), _ptr_array(sin), _ptr_array(sig),
+                                _ptr_array(dsx), _ptr_array(dsy))
+    if rc:
+        raise ValueError(f"invalid nest descriptor (oracle_prepare rc={rc})")
+    return sig, dsx, dsy
+
+
+def force_at(desc, sigma, levels, ii, jj, nthreads: int = 0, prepared=None):
+    """(Fx, Fy) at target cells (levels[k], ii[k], jj[k]); covered targets give 0."""
+    lib = _load()
+    sig, dsx, dsy = prepared if prepared is not None else prepare(desc, sigma)
+    lv = np.ascontiguousarray(levels, dtype=np.int32)
+    iv = np.ascontiguousarray(ii, dtype=np.int32)
+    jv = np.ascontiguousarray(jj, dtype=np.int32)
+    nt = lv.size
+    fx = np.zeros(nt)
+    fy = np.zeros(nt)
+    ip = ctypes.POINTER(ctypes.c_int)
+    rc = lib.oracle_force_targets(ctypes.byref(_nest(desc)), _ptr_array(sig), _ptr_array(dsx),
+                                  _ptr_array(dsy), nt, lv.ctypes.data_as(ip), iv.ctypes.data_as(ip),
+                                  jv.ctypes.data_as(ip), _dp(fx), _dp(fy), int(nthreads))
+    if rc:
+        raise ValueError(f"oracle_force_targets failed rc={rc}")
+    return fx, fy
+
+
+def force(desc, sigma, nthreads: int = 0):
+    """Full direct sum: lists of (n, n) arrays Fx[l], Fy[l]; covered cells are 0."""
+    n, L = int(desc.n), int(desc.levels)
+    jj, ii = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    lv = np.repeat(np.arange(L), n * n)
+    iv = np.tile(ii.ravel(), L)
+    jv = np.tile(jj.ravel(), L)
+    fx, fy = force_at(desc, sigma, lv, iv, jv, nthreads=nthreads)
+    return [fx[l * n * n:(l + 1) * n * n].reshape(n, n) for l in range(L)], \
+           [fy[l * n * n:(l + 1) * n * n].reshape(n, n) for l in range(L)]
+
+
+def genconv_case2(b, c, m: int, nout: int) -> np.ndarray:
+    """a_k = sum_j b_{m k - j} c_j  (Eq. eqnbmnn), k = 0..nout-1."""
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    out = np.zeros(nout)
+    _load().oracle_genconv_case2(_dp(b), b.size, _dp(c), c.size, int(m), _dp(out), int(nout))
+    return out
+
+
+def genconv_case3(b, c, m: int, nout: int) -> np.ndarray:
+    """a_k = sum_j b_{k - m j} c_j  (Eq. eqnbnmn), k = 0..nout-1."""
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    out = np.zeros(nout)
+    _load().oracle_genconv_case3(_dp(b), b.size, _dp(c), c.size, int(m), _dp(out), int(nout))
+    return out
+
+
+if __name__ == "__main__":  # pragma: no cover - manual build helper
+    print(build_oracle(force="--force" in sys.argv))
