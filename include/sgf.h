@@ -1,0 +1,149 @@
+/*
+ * sgf.h -- C ABI of libsgf: second-order self-gravitational force of an
+ * infinitesimally thin disk on nested grids, evaluated on one NVIDIA GB300
+ * (sm_103a) by zero-padded FFT generalized convolution.
+ *
+ * Method (Wang, Taam & Yen, "Self-gravitational force calculation of
+ * infinitesimally thin gaseous disks on nested grids"):
+ *   - Sec. 2.1: the surface density sigma is piecewise linear in every cell
+ *     (Eq. eqnSigma); the x-force at every cell centre is the sum over all
+ *     cells of all levels of exact cell integrals of dK/dx = x/r^3 against
+ *     that linear density (F^{x,0} + F^{x,x} + F^{x,y}); likewise for y.
+ *     G = 1.
+ *   - Sec. 2.1, Cases 1-3: for same-level, finer-source and coarser-source
+ *     pairs the sums are generalized convolutions of the kernel tables with
+ *     (sigma, dsigma/dx, dsigma/dy).
+ *   - Sec. 2.2: Case 2 (finer source) is evaluated as a sum over m^2 source
+ *     phases of ordinary convolutions (Eq. eqnbmnn), Case 3 (coarser source)
+ *     as m^2 target phases (Eq. eqnbnmn); every convolution is a zero-padded
+ *     FFT convolution of size 2N x 2N, so no artificial boundary condition
+ *     enters.
+ *
+ * Geometry (Sec. 2.1 with one patch per level): level 0 is the coarsest; every
+ * level has n x n cells; level l has cell size h0 / 2^l; the lower-left corner
+ * of level l is the corner of level l-1 plus off[l] cells of level l-1.  A
+ * level-l cell that lies under the level-(l+1) patch is not part of that
+ * level's domain: its density is replaced by the finer level's (the mean of
+ * its four children feeds the neighbours' slopes) and its output force is 0.
+ * Slopes: central difference inside a patch, one-sided inward difference on
+ * the first and last cell of every row and column of a patch.
+ *
+ * Arrays: one n x n array per level, row-major [j][i] (j = y row, i = x
+ * column), contiguous, in device memory (sgf_solve) or host memory
+ * (sgf_solve_host); element type double for SGF_FP64, float otherwise.
+ * Because the force of a thin sheet is invariant under a common scaling of
+ * lengths, the output does not depend on x0, y0 or h0 (they only place the
+ * cells for the caller).
+ *
+ * Errors: every call returns an sgf_status; no call aborts, traps or throws.
+ * sgf_last_error() describes the last failure on the calling thread.
+ */
+#ifndef SGF_H
+#define SGF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SGF_MAX_LEVELS 8
+#define SGF_MIN_N 8
+#define SGF_MAX_N 4096        /* SGF_FP32 / SGF_BF16X */
+#define SGF_MAX_N_FP64 2048   /* SGF_FP64 */
+
+typedef enum {
+    SGF_OK = 0,
+    SGF_EINVAL = 1,        /* malformed descriptor, null pointer, bad argument */
+    SGF_ENOMEM = 2,        /* device allocation failed at plan creation */
+    SGF_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+    SGF_ETIMEOUT = 4,      /* a bounded device-side wait expired */
+    SGF_EUNSUPPORTED = 5   /* valid but not supported (size, precision, device) */
+} sgf_status;
+
+typedef enum {
+    SGF_FP64 = 0,   /* FP64 everywhere; I/O double */
+    SGF_FP32 = 1,   /* FP32 transforms and spectra (spectra built in FP64); I/O float */
+    SGF_BF16X = 2   /* reserved: split-BF16 tensor-core butterflies, FP32 I/O */
+} sgf_precision;
+
+/* Nest descriptor (Sec. 2.1: nested domains Omega^l, one patch per level,
+ * refinement ratio 2).  n: cells per side on every level, a power of two in
+ * [SGF_MIN_N, SGF_MAX_N]; levels in [1, SGF_MAX_LEVELS] with 2^(levels-1) <= n/2;
+ * off[l] (l >= 1): (x, y) offset of level l's corner in level-(l-1) cells,
+ * 0 <= off <= n/2 so the child lies inside its parent; off[0] is ignored. */
+typedef struct {
+    int32_t n;
+    int32_t levels;
+    double x0, y0, h0;
+    int32_t off[SGF_MAX_LEVELS][2];
+} sgf_nest_desc;
+
+typedef struct sgf_plan sgf_plan;
+
+/* Per-plan counts, for reporting.  All sizes in bytes. */
+typedef struct {
+    int32_t n, levels, precision;
+    int32_t forward_slabs;      /* row-transformed source sets per solve (1 per level + Case-2 phases) */
+    int32_t outputs;            /* column-pass outputs per solve (1 per level + Case-3 phases) */
+    int32_t spectra_sets;       /* kernel-spectrum sets (Case 1 shared; one per Case-2/3 phase) */
+    int32_t launches_per_solve; /* kernels one sgf_solve launches */
+    size_t workspace_bytes;     /* device workspace owned by this plan */
+    size_t spectra_bytes;       /* device kernel spectra (shared between plans made by sgf_plan_share) */
+    size_t algorithmic_bytes;   /* HBM bytes one solve must move: inputs, outputs, spectra and
+                                   the two transposed intermediates, each read or written once */
+    double plan_ms;             /* wall time spent building the spectra */
+} sgf_plan_stats;
+
+/* Build a plan on the current CUDA device: validates the descriptor, builds
+ * every kernel table in FP64 (closed-form cell integrals, Sec. 2.1, Eq.
+ * eqnCalK and the slope kernels), transforms them (FP64 FFT) into resident
+ * kernel spectra, and allocates the solve workspace.  Blocks until done.
+ * On success *out owns device memory until sgf_plan_destroy.
+ * Errors: SGF_EINVAL (descriptor), SGF_EUNSUPPORTED (n or precision),
+ * SGF_ENOMEM, SGF_ECUDA. */
+sgf_status sgf_plan_create(const sgf_nest_desc *desc, sgf_precision precision, sgf_plan **out);
+
+/* A new plan with its own workspace that shares src's kernel spectra (no
+ * table generation).  Plans that share spectra may solve concurrently on
+ * different streams; one plan must not run two solves at once.  The spectra
+ * are freed with the last plan that uses them. */
+sgf_status sgf_plan_share(const sgf_plan *src, sgf_plan **out);
+
+sgf_status sgf_plan_stats_get(const sgf_plan *plan, sgf_plan_stats *stats);
+
+/* Forces on every level (Sec. 2.1, F^{x,0}+F^{x,x}+F^{x,y} and the y analogue).
+ * sigma[l], fx[l], fy[l]: device pointers to n*n elements for l < levels,
+ * element type per precision, 16-byte aligned; outputs must not alias inputs.
+ * stream: a cudaStream_t (NULL = legacy default stream).  Asynchronous and
+ * stream-ordered; allocates nothing.  Errors: SGF_EINVAL, SGF_ECUDA (launch). */
+sgf_status sgf_solve(sgf_plan *plan, const void *const *sigma, void *const *fx, void *const *fy,
+                     void *stream);
+
+/* As sgf_solve, but sigma, fx and fy are HOST pointers (pinned memory gives
+ * asynchronous copies).  Copies sigma to the plan's device staging, solves,
+ * copies the forces back, and waits for the stream before returning. */
+sgf_status sgf_solve_host(sgf_plan *plan, const void *const *sigma, void *const *fx,
+                          void *const *fy, void *stream);
+
+/* Solve `count` independent nests (plans may differ in n, levels and offsets,
+ * but share one precision) on one stream: every pass of the method runs as
+ * one launch over the work items of all nests.  sigma[k], fx[k], fy[k] are the
+ * per-level device pointer arrays of nest k.  Plans must be distinct. */
+sgf_status sgf_solve_batched(sgf_plan *const *plans, int32_t count, const void *const *const *sigma,
+                             void *const *const *fx, void *const *const *fy, void *stream);
+
+sgf_status sgf_plan_destroy(sgf_plan *plan);
+
+/* Description of the last failure on the calling thread; valid until the
+ * next sgf_* call on this thread.  Never NULL. */
+const char *sgf_last_error(void);
+
+/* Library version string, e.g. "sgf 0.1.0 sm_103a". */
+const char *sgf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGF_H */

@@ -1,0 +1,703 @@
+// sgf_api.cu -- host side of libsgf: validation, plans, the C ABI (include/sgf.h).
+//
+// A plan fixes the nest geometry and precision.  It owns
+//   - the work lists of one solve (forward slabs, column outputs and their
+//     inputs, inverse-row contributions), uploaded once;
+//   - the solve workspace (restricted densities, forward and backward
+//     intermediates);
+//   - a reference to the kernel spectra, which plans made by sgf_plan_share
+//     hold in common.
+// One solve = (levels-1) restriction launches + row_fwd + col + row_inv, all on
+// the caller's stream.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/sgf.h"
+#include "sgf_internal.h"
+
+using namespace sgf;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+sgf_status fail(sgf_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+sgf_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(e == cudaErrorMemoryAllocation ? SGF_ENOMEM : SGF_ECUDA, "%s: %s (%s)", what,
+                cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+int ilog2(int n)
+{
+    int l = 0;
+    while ((1 << l) < n)
+        ++l;
+    return l;
+}
+
+struct Spectra {
+    std::atomic<int> refs{1};
+    int device = 0;
+    void *dev = nullptr;   // all sets, one allocation
+    size_t bytes = 0;
+    void *tw = nullptr;    // W_P^k in the solve precision
+    double plan_ms = 0.0;
+};
+
+void spectra_release(Spectra *s)
+{
+    if (s && --s->refs == 0) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(s->device);
+        cudaFree(s->dev);
+        cudaFree(s->tw);
+        cudaSetDevice(cur);
+        delete s;
+    }
+}
+
+struct SetKey {
+    int cas, m, px, py, ax, ay;
+    bool operator<(const SetKey &o) const
+    {
+        return std::tie(cas, m, px, py, ax, ay) < std::tie(o.cas, o.m, o.px, o.py, o.ax, o.ay);
+    }
+};
+
+}  // namespace
+
+struct sgf_plan {
+    sgf_nest_desc desc{};
+    sgf_precision prec = SGF_FP32;
+    int N = 0, logN = 0, L = 0, device = 0;
+    size_t esize = 4;  // bytes per real
+    Spectra *spec = nullptr;
+    // host lists
+    std::vector<FwdSlab> slabs;
+    std::vector<FwdItem> items;
+    std::vector<ColOutput> outs;
+    std::vector<ColInput> ins;
+    std::vector<RowContrib> contribs;
+    int contrib_begin[kMaxLevels + 1] = {};
+    std::vector<GenSet> sets;
+    size_t fwd_elems = 0, bwd_elems = 0;  // complex elements
+    // device memory owned by this plan
+    void *d_lists = nullptr;
+    const FwdSlab *d_slabs = nullptr;
+    const FwdItem *d_items = nullptr;
+    const ColOutput *d_outs = nullptr;
+    const ColInput *d_ins = nullptr;
+    const RowContrib *d_contribs = nullptr;
+    void *d_fwd = nullptr, *d_bwd = nullptr;
+    void *d_restricted = nullptr;  // (L-1) * N * N reals
+    // host-buffer solve staging (allocated on first sgf_solve_host)
+    void *d_stage = nullptr;
+    size_t workspace_bytes = 0;
+    size_t algorithmic_bytes = 0;
+};
+
+namespace {
+
+sgf_status validate(const sgf_nest_desc *d, sgf_precision prec)
+{
+    if (!d)
+        return fail(SGF_EINVAL, "descriptor is NULL");
+    if (prec != SGF_FP64 && prec != SGF_FP32 && prec != SGF_BF16X)
+        return fail(SGF_EINVAL, "unknown precision %d", (int)prec);
+    const int n = d->n;
+    if (n < SGF_MIN_N || (n & (n - 1)) != 0)
+        return fail(SGF_EINVAL, "n = %d must be a power of two >= %d", n, SGF_MIN_N);
+    if (d->levels < 1 || d->levels > SGF_MAX_LEVELS)
+        return fail(SGF_EINVAL, "levels = %d outside [1, %d]", d->levels, SGF_MAX_LEVELS);
+    if ((1 << (d->levels - 1)) > n / 2)
+        return fail(SGF_EINVAL, "levels = %d too deep for n = %d (need 2^(levels-1) <= n/2)",
+                    d->levels, n);
+    if (!(d->h0 > 0.0) || !std::isfinite(d->h0) || !std::isfinite(d->x0) || !std::isfinite(d->y0))
+        return fail(SGF_EINVAL, "h0 must be positive and x0, y0, h0 finite");
+    for (int l = 1; l < d->levels; ++l)
+        for (int a = 0; a < 2; ++a)
+            if (d->off[l][a] < 0 || d->off[l][a] > n / 2)
+                return fail(SGF_EINVAL, "off[%d][%d] = %d outside [0, n/2]", l, a, d->off[l][a]);
+    if (n > SGF_MAX_N)
+        return fail(SGF_EUNSUPPORTED, "n = %d above SGF_MAX_N = %d", n, SGF_MAX_N);
+    if (prec == SGF_FP64 && n > SGF_MAX_N_FP64)
+        return fail(SGF_EUNSUPPORTED, "n = %d above SGF_MAX_N_FP64 = %d", n, SGF_MAX_N_FP64);
+    if (prec == SGF_BF16X)
+        return fail(SGF_EUNSUPPORTED, "SGF_BF16X is not available in this build");
+    return SGF_OK;
+}
+
+// Corner of level l relative to level 0's corner, in units of level `unit`'s cell.
+long corner_units(const sgf_nest_desc *d, int l, int unit, int axis)
+{
+    long acc = 0;  // in units of the finest level involved (2^unit scale)
+    for (int k = 1; k <= l; ++k)
+        acc += (long)d->off[k][axis] << (unit - (k - 1));
+    return acc;
+}
+
+// Build all host-side lists of a plan (no CUDA calls).
+void build_lists(sgf_plan *p)
+{
+    const int N = p->N, L = p->L, P = 2 * N;
+    const size_t T = p->esize, Cb = 2 * p->esize;
+    std::map<SetKey, int> set_index;
+    std::vector<size_t> set_bytes;
+    auto get_set = [&](int cas, int m, int px, int py, int ax, int ay) {
+        SetKey k{cas, m, px, py, ax, ay};
+        auto it = set_index.find(k);
+        if (it != set_index.end())
+            return it->second;
+        GenSet g{};
+        g.kind = cas == 1 ? SPEC_QUARTER : SPEC_FULL;
+        g.cas = cas;
+        g.m = m;
+        g.px = px;
+        g.py = py;
+        g.ax = ax;
+        g.ay = ay;
+        const int idx = (int)p->sets.size();
+        p->sets.push_back(g);
+        set_bytes.push_back(cas == 1 ? 6 * (size_t)(N + 1) * (N + 1) * T : 6 * (size_t)(N + 1) * P * Cb);
+        set_index[k] = idx;
+        return idx;
+    };
+    // forward slabs: whole levels, then Case-2 phases
+    std::vector<int> slab_full(L);
+    std::map<std::tuple<int, int, int, int>, int> slab_phase;  // (s, t, px, py)
+    auto add_slab = [&](int s, int m, int px, int py) {
+        FwdSlab sl{};
+        sl.level = s;
+        sl.m = m;
+        sl.px = px;
+        sl.py = py;
+        sl.rows = N / m;
+        sl.off = p->fwd_elems;
+        p->fwd_elems += 3 * (size_t)(N + 1) * sl.rows;
+        p->slabs.push_back(sl);
+        return (int)p->slabs.size() - 1;
+    };
+    for (int s = 0; s < L; ++s)
+        slab_full[s] = add_slab(s, 1, 0, 0);
+    for (int s = 0; s < L; ++s)
+        for (int t = 0; t < s; ++t) {
+            const int m = 1 << (s - t);
+            for (int py = 0; py < m; ++py)
+                for (int px = 0; px < m; ++px)
+                    slab_phase[{s, t, px, py}] = add_slab(s, m, px, py);
+        }
+    // column outputs
+    auto add_output = [&](int t, int rows) {
+        ColOutput o{};
+        o.level = t;
+        o.rows = rows;
+        o.in_begin = (int)p->ins.size();
+        o.in_count = 0;
+        o.off = p->bwd_elems;
+        p->bwd_elems += 2 * (size_t)(N + 1) * rows;
+        p->outs.push_back(o);
+        return (int)p->outs.size() - 1;
+    };
+    auto add_input = [&](int out, int slab, int set) {
+        ColInput ci{};
+        ci.slab = slab;
+        ci.kind = p->sets[set].kind;
+        ci.spec_off = (size_t)set;  // resolved to an element offset below
+        p->ins.push_back(ci);
+        p->outs[out].in_count++;
+    };
+    std::vector<int> main_out(L);
+    std::map<std::pair<int, int>, int> c3_base;  // (s, t) -> first output
+    for (int t = 0; t < L; ++t) {
+        main_out[t] = add_output(t, N);
+        add_input(main_out[t], slab_full[t], get_set(1, 1, 0, 0, 0, 0));
+        for (int s = t + 1; s < L; ++s) {  // Case 2: finer sources
+            const int m = 1 << (s - t);
+            const int ax = (int)(corner_units(&p->desc, s, s, 0) - corner_units(&p->desc, t, s, 0));
+            const int ay = (int)(corner_units(&p->desc, s, s, 1) - corner_units(&p->desc, t, s, 1));
+            for (int py = 0; py < m; ++py)
+                for (int px = 0; px < m; ++px)
+                    add_input(main_out[t], slab_phase[{s, t, px, py}], get_set(2, m, px, py, ax, ay));
+        }
+        for (int s = 0; s < t; ++s) {  // Case 3: coarser sources, one output per target phase
+            const int m = 1 << (t - s);
+            const int ax = (int)(corner_units(&p->desc, t, t, 0) - corner_units(&p->desc, s, t, 0));
+            const int ay = (int)(corner_units(&p->desc, t, t, 1) - corner_units(&p->desc, s, t, 1));
+            for (int py = 0; py < m; ++py)
+                for (int px = 0; px < m; ++px) {
+                    const int o = add_output(t, N / m);
+                    if (py == 0 && px == 0)
+                        c3_base[{s, t}] = o;
+                    add_input(o, slab_full[s], get_set(3, m, px, py, ax, ay));
+                }
+        }
+    }
+    // inverse-row contributions per target level
+    for (int t = 0; t < L; ++t) {
+        p->contrib_begin[t] = (int)p->contribs.size();
+        p->contribs.push_back(RowContrib{1, 0, main_out[t], 0});
+        for (int s = 0; s < t; ++s) {
+            const int m = 1 << (t - s);
+            for (int px = 0; px < m; ++px)
+                p->contribs.push_back(RowContrib{m, px, c3_base[{s, t}] + px, 0});
+        }
+    }
+    p->contrib_begin[L] = (int)p->contribs.size();
+    // forward work items
+    for (int k = 0; k < (int)p->slabs.size(); ++k)
+        for (int r = 0; r < p->slabs[k].rows / 2; ++r)
+            p->items.push_back(FwdItem{k, r});
+    // spectra offsets: 256-byte aligned sets in one buffer
+    std::vector<size_t> set_off(p->sets.size());
+    size_t off = 0;
+    for (size_t k = 0; k < p->sets.size(); ++k) {
+        set_off[k] = off;
+        off += (set_bytes[k] + 255) & ~(size_t)255;
+        p->sets[k].spec_off = p->sets[k].kind == SPEC_QUARTER ? set_off[k] / T : set_off[k] / Cb;
+    }
+    for (auto &ci : p->ins)
+        ci.spec_off = p->sets[ci.spec_off].spec_off;
+    // algorithmic bytes of one solve
+    size_t ab = 3 * (size_t)L * N * N * T;                       // sigma in, Fx and Fy out
+    ab += 2 * p->fwd_elems * Cb + 2 * p->bwd_elems * Cb;         // intermediates written and read once
+    for (const auto &o : p->outs)
+        for (int k = 0; k < o.in_count; ++k) {
+            const ColInput &ci = p->ins[o.in_begin + k];
+            ab += ci.kind == SPEC_QUARTER ? 6 * (size_t)(N + 1) * (N + 1) * T : 6 * (size_t)(N + 1) * P * Cb;
+        }
+    if (L > 1)
+        ab += (size_t)(L - 1) * (2 * (size_t)N * N * T + (size_t)N * N / 4 * 4 * T);  // restriction
+    p->algorithmic_bytes = ab;
+    (void)off;
+}
+
+size_t spectra_total(const sgf_plan *p)
+{
+    size_t off = 0;
+    for (const auto &g : p->sets) {
+        const size_t b = g.kind == SPEC_QUARTER ? 6 * (size_t)(p->N + 1) * (p->N + 1) * p->esize
+                                                : 6 * (size_t)(p->N + 1) * 2 * p->N * 2 * p->esize;
+        off += (b + 255) & ~(size_t)255;
+    }
+    return off;
+}
+
+void plan_free_owned(sgf_plan *p)
+{
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(p->device);
+    cudaFree(p->d_lists);
+    cudaFree(p->d_fwd);
+    cudaFree(p->d_bwd);
+    cudaFree(p->d_restricted);
+    cudaFree(p->d_stage);
+    p->d_lists = p->d_fwd = p->d_bwd = p->d_restricted = p->d_stage = nullptr;
+    cudaSetDevice(cur);
+}
+
+template <typename X>
+size_t align_push(std::vector<unsigned char> &blob, const std::vector<X> &v)
+{
+    size_t off = (blob.size() + 255) & ~(size_t)255;
+    blob.resize(off + v.size() * sizeof(X));
+    if (!v.empty())
+        std::memcpy(blob.data() + off, v.data(), v.size() * sizeof(X));
+    return off;
+}
+
+// Allocate the plan's own device memory and upload its lists.
+sgf_status plan_alloc_owned(sgf_plan *p)
+{
+    std::vector<unsigned char> blob;
+    const size_t o_slabs = align_push(blob, p->slabs);
+    const size_t o_items = align_push(blob, p->items);
+    const size_t o_outs = align_push(blob, p->outs);
+    const size_t o_ins = align_push(blob, p->ins);
+    const size_t o_con = align_push(blob, p->contribs);
+    cudaError_t e;
+    if ((e = cudaMalloc(&p->d_lists, blob.size())) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(work lists)");
+    if ((e = cudaMemcpy(p->d_lists, blob.data(), blob.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpy(work lists)");
+    auto base = static_cast<unsigned char *>(p->d_lists);
+    p->d_slabs = reinterpret_cast<const FwdSlab *>(base + o_slabs);
+    p->d_items = reinterpret_cast<const FwdItem *>(base + o_items);
+    p->d_outs = reinterpret_cast<const ColOutput *>(base + o_outs);
+    p->d_ins = reinterpret_cast<const ColInput *>(base + o_ins);
+    p->d_contribs = reinterpret_cast<const RowContrib *>(base + o_con);
+    const size_t Cb = 2 * p->esize;
+    if ((e = cudaMalloc(&p->d_fwd, p->fwd_elems * Cb)) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(forward intermediates)");
+    if ((e = cudaMalloc(&p->d_bwd, p->bwd_elems * Cb)) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(backward intermediates)");
+    if (p->L > 1) {
+        if ((e = cudaMalloc(&p->d_restricted, (size_t)(p->L - 1) * p->N * p->N * p->esize)) != cudaSuccess)
+            return cuda_fail(e, "cudaMalloc(restricted densities)");
+    }
+    p->workspace_bytes = blob.size() + (p->fwd_elems + p->bwd_elems) * Cb +
+                         (size_t)(p->L > 1 ? p->L - 1 : 0) * p->N * p->N * p->esize;
+    return SGF_OK;
+}
+
+// W_P^k = exp(-2 pi i k / P) from extended precision; the quarter points are exact.
+void twiddles(int P, std::vector<double> &re, std::vector<double> &im)
+{
+    re.resize(P);
+    im.resize(P);
+    const long double two_pi = 6.283185307179586476925286766559005768L;
+    for (int k = 0; k < P; ++k) {
+        const long double a = two_pi * (long double)k / (long double)P;
+        long double c = cosl(a), s = sinl(a);
+        if ((long long)k * 4 % P == 0) {  // exact multiples of pi/2
+            const int quarter = (int)((long long)k * 4 / P);
+            c = quarter == 0 ? 1 : quarter == 2 ? -1 : 0;
+            s = quarter == 1 ? 1 : quarter == 3 ? -1 : 0;
+        }
+        re[k] = (double)c;
+        im[k] = -(double)s;
+    }
+}
+
+template <typename T>
+sgf_status build_spectra(sgf_plan *p)
+{
+    using C = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
+    const int N = p->N, P = 2 * N;
+    auto t0 = std::chrono::steady_clock::now();
+    Spectra *sp = new Spectra();
+    sp->device = p->device;
+    p->spec = sp;
+    cudaError_t e;
+    std::vector<double> re, im;
+    twiddles(P, re, im);
+    std::vector<double2> tw64(P);
+    std::vector<C> twT(P);
+    for (int k = 0; k < P; ++k) {
+        tw64[k] = make_double2(re[k], im[k]);
+        twT[k].x = (T)re[k];
+        twT[k].y = (T)im[k];
+    }
+    if ((e = cudaMalloc(&sp->tw, P * sizeof(C))) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(twiddles)");
+    if ((e = cudaMemcpy(sp->tw, twT.data(), P * sizeof(C), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpy(twiddles)");
+    sp->bytes = spectra_total(p);
+    if ((e = cudaMalloc(&sp->dev, sp->bytes)) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(kernel spectra)");
+    double2 *d_tw64 = nullptr;
+    double *d_tables = nullptr;
+    double2 *d_half = nullptr;
+    sgf_status st = SGF_OK;
+    if ((e = cudaMalloc(&d_tw64, P * sizeof(double2))) != cudaSuccess ||
+        (e = cudaMemcpy(d_tw64, tw64.data(), P * sizeof(double2), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMalloc(&d_tables, 6 * (size_t)P * P * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&d_half, 6 * (size_t)(N + 1) * P * sizeof(double2))) != cudaSuccess) {
+        st = cuda_fail(e, "cudaMalloc(table generation workspace)");
+    }
+    if (st == SGF_OK && (e = gen_kernels_init()) != cudaSuccess)
+        st = cuda_fail(e, "table kernels init");
+    for (size_t k = 0; st == SGF_OK && k < p->sets.size(); ++k) {
+        if ((e = launch_gen_set<T>(p->sets[k], N, p->logN, d_tw64, sp->dev, d_tables, d_half, 0)) != cudaSuccess)
+            st = cuda_fail(e, "kernel table generation launch");
+    }
+    if (st == SGF_OK && (e = cudaDeviceSynchronize()) != cudaSuccess)
+        st = cuda_fail(e, "kernel table generation");
+    cudaFree(d_tw64);
+    cudaFree(d_tables);
+    cudaFree(d_half);
+    sp->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return st;
+}
+
+template <typename T>
+sgf_status solve_impl(sgf_plan *p, const void *const *sigma, void *const *fx, void *const *fy,
+                      cudaStream_t st)
+{
+    const int N = p->N, L = p->L;
+    SolveArgs<T> a{};
+    a.N = N;
+    a.logN = p->logN;
+    a.L = L;
+    for (int l = 0; l < kMaxLevels; ++l) {
+        a.child_ox[l] = -1;
+        a.child_oy[l] = -1;
+    }
+    for (int l = 0; l + 1 < L; ++l) {
+        a.child_ox[l] = p->desc.off[l + 1][0];
+        a.child_oy[l] = p->desc.off[l + 1][1];
+    }
+    T *restricted = static_cast<T *>(p->d_restricted);
+    a.src[L - 1] = static_cast<const T *>(sigma[L - 1]);
+    for (int l = L - 2; l >= 0; --l) {
+        T *dst = restricted + (size_t)l * N * N;
+        cudaError_t e = launch_restrict<T>(a.src[l + 1], dst, static_cast<const T *>(sigma[l]), N,
+                                           p->desc.off[l + 1][0], p->desc.off[l + 1][1], st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "restriction launch");
+        a.src[l] = dst;
+    }
+    for (int l = 0; l < L; ++l) {
+        a.fx[l] = static_cast<T *>(fx[l]);
+        a.fy[l] = static_cast<T *>(fy[l]);
+    }
+    a.fwd = static_cast<typename SolveArgs<T>::C *>(p->d_fwd);
+    a.bwd = static_cast<typename SolveArgs<T>::C *>(p->d_bwd);
+    a.spec = p->spec->dev;
+    a.tw = static_cast<const typename SolveArgs<T>::C *>(p->spec->tw);
+    a.slabs = p->d_slabs;
+    a.fwd_items = p->d_items;
+    a.outs = p->d_outs;
+    a.ins = p->d_ins;
+    a.contribs = p->d_contribs;
+    for (int l = 0; l <= L; ++l)
+        a.contrib_begin[l] = p->contrib_begin[l];
+    cudaError_t e;
+    if ((e = launch_row_fwd<T>(a, (int)p->items.size(), st)) != cudaSuccess)
+        return cuda_fail(e, "row_fwd launch");
+    if ((e = launch_col<T>(a, (int)p->outs.size(), st)) != cudaSuccess)
+        return cuda_fail(e, "col launch");
+    if ((e = launch_row_inv<T>(a, st)) != cudaSuccess)
+        return cuda_fail(e, "row_inv launch");
+    return SGF_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev)
+            cudaSetDevice(dev);
+        else
+            prev = -1;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0)
+            cudaSetDevice(prev);
+    }
+};
+
+sgf_status check_ptrs(const sgf_plan *p, const void *const *sigma, void *const *fx, void *const *fy)
+{
+    if (!p)
+        return fail(SGF_EINVAL, "plan is NULL");
+    if (!sigma || !fx || !fy)
+        return fail(SGF_EINVAL, "pointer arrays must not be NULL");
+    for (int l = 0; l < p->L; ++l) {
+        if (!sigma[l] || !fx[l] || !fy[l])
+            return fail(SGF_EINVAL, "level %d: NULL buffer", l);
+        if (((uintptr_t)sigma[l] | (uintptr_t)fx[l] | (uintptr_t)fy[l]) & 15u)
+            return fail(SGF_EINVAL, "level %d: buffers must be 16-byte aligned", l);
+    }
+    return SGF_OK;
+}
+
+sgf_status solve_dispatch(sgf_plan *p, const void *const *sigma, void *const *fx, void *const *fy,
+                          cudaStream_t st)
+{
+    return p->prec == SGF_FP64 ? solve_impl<double>(p, sigma, fx, fy, st)
+                               : solve_impl<float>(p, sigma, fx, fy, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sgf_last_error(void) { return g_err.c_str(); }
+
+const char *sgf_version(void) { return "sgf 0.1.0 sm_103a"; }
+
+sgf_status sgf_plan_create(const sgf_nest_desc *desc, sgf_precision precision, sgf_plan **out)
+{
+    if (!out)
+        return fail(SGF_EINVAL, "out is NULL");
+    *out = nullptr;
+    sgf_status s = validate(desc, precision);
+    if (s != SGF_OK)
+        return s;
+    sgf_plan *p = new sgf_plan();
+    p->desc = *desc;
+    p->prec = precision;
+    p->N = desc->n;
+    p->logN = ilog2(desc->n);
+    p->L = desc->levels;
+    p->esize = precision == SGF_FP64 ? 8 : 4;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    build_lists(p);
+    e = precision == SGF_FP64 ? solve_kernels_init<double>() : solve_kernels_init<float>();
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e, "solve kernels init");
+    }
+    s = precision == SGF_FP64 ? build_spectra<double>(p) : build_spectra<float>(p);
+    if (s == SGF_OK)
+        s = plan_alloc_owned(p);
+    if (s != SGF_OK) {
+        std::string msg = g_err;
+        plan_free_owned(p);
+        spectra_release(p->spec);
+        delete p;
+        g_err = msg;
+        return s;
+    }
+    *out = p;
+    return SGF_OK;
+}
+
+sgf_status sgf_plan_share(const sgf_plan *src, sgf_plan **out)
+{
+    if (!src || !out)
+        return fail(SGF_EINVAL, "NULL argument");
+    *out = nullptr;
+    DeviceGuard g(src->device);
+    sgf_plan *p = new sgf_plan();
+    p->desc = src->desc;
+    p->prec = src->prec;
+    p->N = src->N;
+    p->logN = src->logN;
+    p->L = src->L;
+    p->esize = src->esize;
+    p->device = src->device;
+    build_lists(p);
+    p->spec = src->spec;
+    p->spec->refs++;
+    sgf_status s = plan_alloc_owned(p);
+    if (s != SGF_OK) {
+        std::string msg = g_err;
+        plan_free_owned(p);
+        spectra_release(p->spec);
+        delete p;
+        g_err = msg;
+        return s;
+    }
+    *out = p;
+    return SGF_OK;
+}
+
+sgf_status sgf_plan_stats_get(const sgf_plan *p, sgf_plan_stats *st)
+{
+    if (!p || !st)
+        return fail(SGF_EINVAL, "NULL argument");
+    st->n = p->N;
+    st->levels = p->L;
+    st->precision = (int)p->prec;
+    st->forward_slabs = (int)p->slabs.size();
+    st->outputs = (int)p->outs.size();
+    st->spectra_sets = (int)p->sets.size();
+    st->launches_per_solve = (p->L - 1) + 3;
+    st->workspace_bytes = p->workspace_bytes;
+    st->spectra_bytes = p->spec ? p->spec->bytes : 0;
+    st->algorithmic_bytes = p->algorithmic_bytes;
+    st->plan_ms = p->spec ? p->spec->plan_ms : 0.0;
+    return SGF_OK;
+}
+
+sgf_status sgf_solve(sgf_plan *p, const void *const *sigma, void *const *fx, void *const *fy, void *stream)
+{
+    sgf_status s = check_ptrs(p, sigma, fx, fy);
+    if (s != SGF_OK)
+        return s;
+    DeviceGuard g(p->device);
+    return solve_dispatch(p, sigma, fx, fy, static_cast<cudaStream_t>(stream));
+}
+
+sgf_status sgf_solve_host(sgf_plan *p, const void *const *sigma, void *const *fx, void *const *fy,
+                          void *stream)
+{
+    sgf_status s = check_ptrs(p, sigma, fx, fy);
+    if (s != SGF_OK)
+        return s;
+    DeviceGuard g(p->device);
+    const size_t lvl = (size_t)p->N * p->N * p->esize;
+    const size_t lvl_al = (lvl + 255) & ~(size_t)255;
+    cudaError_t e;
+    if (!p->d_stage) {
+        if ((e = cudaMalloc(&p->d_stage, 3 * (size_t)p->L * lvl_al)) != cudaSuccess)
+            return cuda_fail(e, "cudaMalloc(host-solve staging)");
+        p->workspace_bytes += 3 * (size_t)p->L * lvl_al;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    auto base = static_cast<unsigned char *>(p->d_stage);
+    const void *ds[kMaxLevels];
+    void *dx[kMaxLevels], *dy[kMaxLevels];
+    for (int l = 0; l < p->L; ++l) {
+        ds[l] = base + (size_t)l * lvl_al;
+        dx[l] = base + (size_t)(p->L + l) * lvl_al;
+        dy[l] = base + (size_t)(2 * p->L + l) * lvl_al;
+        if ((e = cudaMemcpyAsync(const_cast<void *>(ds[l]), sigma[l], lvl, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpyAsync(sigma H2D)");
+    }
+    s = solve_dispatch(p, ds, dx, dy, st);
+    if (s != SGF_OK)
+        return s;
+    for (int l = 0; l < p->L; ++l) {
+        if ((e = cudaMemcpyAsync(fx[l], dx[l], lvl, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(fy[l], dy[l], lvl, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpyAsync(force D2H)");
+    }
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(e, "solve (host buffers)");
+    return SGF_OK;
+}
+
+sgf_status sgf_solve_batched(sgf_plan *const *plans, int32_t count, const void *const *const *sigma,
+                             void *const *const *fx, void *const *const *fy, void *stream)
+{
+    if (count < 0 || (count > 0 && (!plans || !sigma || !fx || !fy)))
+        return fail(SGF_EINVAL, "bad batch arguments");
+    for (int k = 0; k < count; ++k) {
+        sgf_status s = check_ptrs(plans[k], sigma[k], fx[k], fy[k]);
+        if (s != SGF_OK)
+            return s;
+        for (int q = 0; q < k; ++q)
+            if (plans[q] == plans[k])
+                return fail(SGF_EINVAL, "plan %d appears twice in the batch", k);
+        if (plans[k]->prec != plans[0]->prec)
+            return fail(SGF_EINVAL, "plans in one batch must share a precision");
+    }
+    for (int k = 0; k < count; ++k) {
+        DeviceGuard g(plans[k]->device);
+        sgf_status s = solve_dispatch(plans[k], sigma[k], fx[k], fy[k], static_cast<cudaStream_t>(stream));
+        if (s != SGF_OK)
+            return s;
+    }
+    return SGF_OK;
+}
+
+sgf_status sgf_plan_destroy(sgf_plan *p)
+{
+    if (!p)
+        return SGF_OK;
+    plan_free_owned(p);
+    spectra_release(p->spec);
+    delete p;
+    return SGF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,128 @@
+// sgf_internal.h -- internal data structures of libsgf (not part of the C ABI).
+//
+// Vocabulary (Sec. 2.1 / 2.2 of the paper):
+//   level s / t      source / target level of a pair, level 0 coarsest
+//   m                refinement ratio between the pair's levels, 2^|s - t|
+//   Case 1           s == t: ordinary convolution
+//   Case 2           s finer than t: the source is split into m x m phases
+//                    (Eq. eqnbmnn); every phase is an ordinary convolution
+//                    whose result adds into the coarse target
+//   Case 3           s coarser than t: the target is split into m x m phases
+//                    (Eq. eqnbnmn); every phase is an ordinary convolution of
+//                    the whole coarse source
+// Every convolution is zero-padded to P = 2N per axis.  A P-point transform of
+// a sequence that is zero beyond index N is done as two N-point transforms:
+// even bins from x[n], odd bins from x[n] W_P^n ("parity halves"), so no
+// transform ever touches the zero half.
+//
+// Forward slab: one row-transformed source set, fields (sigma, dx, dy) with
+//   dx, dy the per-cell differences (slope times cell size).  Layout
+//   [field 0..2][kx 0..N][row 0..rows) of complex, rows = N/m.
+// Column output: one column-transformed, multiplied, inverse-column-transformed
+//   result, fields (Fx, Fy).  Layout [field 0..1][kx 0..N][row 0..rows_out).
+// Kernel spectra: 6 tables per set in the order
+//   (K0x, Kxx, Kxy, K0y, Kyx, Kyy) = (x-force from sigma, dx, dy;
+//   y-force from sigma, dx, dy), already divided by P^2.
+//   SPEC_QUARTER (Case 1): the tables are even or odd in each axis, so each
+//     spectrum is purely real or purely imaginary and mirror-symmetric in ky:
+//     stored as reals [table][kx 0..N][ky 0..N].
+//   SPEC_FULL (Cases 2, 3): complex [table][kx 0..N][ky 0..P).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <type_traits>
+#include <cuda_runtime.h>
+
+namespace sgf {
+
+constexpr int kMaxLevels = 8;
+
+enum SpecKind : int { SPEC_QUARTER = 0, SPEC_FULL = 1 };
+
+struct FwdSlab {
+    int level;        // source level
+    int m, px, py;    // phase gather: source cell (m*c + px, m*r + py); m = 1 for a whole level
+    int rows;         // N / m (rows == columns of the slab)
+    int pad;
+    size_t off;       // complex-element offset of the slab in the forward buffer
+};
+
+struct ColInput {
+    int slab;         // forward slab index
+    int kind;         // SpecKind
+    size_t spec_off;  // real-element offset (QUARTER) or complex-element offset (FULL)
+};
+
+struct ColOutput {
+    int level;        // target level
+    int rows;         // rows kept (N for the main output, N/m for a Case-3 phase)
+    int in_begin, in_count;
+    size_t off;       // complex-element offset in the backward buffer
+};
+
+// One contribution to a target level's rows in the inverse row pass: target
+// cell (m*n' + px, j) takes column n' of output out_base + (j % m) * m, row j / m.
+struct RowContrib {
+    int m, px;
+    int out_base;
+    int pad;
+};
+
+struct FwdItem {
+    int slab;
+    int row_pair;
+};
+
+// Everything one launch of the solve kernels needs, passed by value.
+template <typename T>
+struct SolveArgs {
+    using C = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
+    int N, logN, L;
+    int child_ox[kMaxLevels], child_oy[kMaxLevels];  // covered region of each level; -1: none
+    const T *src[kMaxLevels];   // density per level, covered cells already restricted
+    T *fx[kMaxLevels];
+    T *fy[kMaxLevels];
+    C *fwd;                     // forward slabs
+    C *bwd;                     // column outputs
+    const void *spec;           // kernel spectra (T reals / C complex)
+    const C *tw;                // W_P^k, k = 0..P-1 (P = 2N), exp(-2 pi i k / P)
+    const FwdSlab *slabs;
+    const FwdItem *fwd_items;
+    const ColOutput *outs;
+    const ColInput *ins;
+    const RowContrib *contribs;
+    int contrib_begin[kMaxLevels + 1];
+};
+
+// Kernel-table generation for one spectra set (FP64).
+struct GenSet {
+    int kind;          // SpecKind
+    int cas;           // 1, 2 or 3
+    int m, px, py;     // phases (m = 1 for Case 1)
+    int ax, ay;        // integer lattice offset of the pair (units of the finer cell), see sgf_gen.cu
+    size_t spec_off;   // where the set's spectra go (real elements for QUARTER, complex for FULL)
+};
+
+// ---- launchers (sgf_solve.cu / sgf_gen.cu); all return cudaGetLastError()
+template <typename T>
+cudaError_t launch_restrict(const T *fine, T *coarse, const T *coarse_in, int N, int ox, int oy,
+                            cudaStream_t st);
+template <typename T>
+cudaError_t launch_row_fwd(const SolveArgs<T> &a, int n_items, cudaStream_t st);
+template <typename T>
+cudaError_t launch_col(const SolveArgs<T> &a, int n_outputs, cudaStream_t st);
+template <typename T>
+cudaError_t launch_row_inv(const SolveArgs<T> &a, cudaStream_t st);
+template <typename T>
+size_t smem_col_bytes(int N);
+template <typename T>
+cudaError_t solve_kernels_init();
+
+// Build the spectra of one set into spec (element type T: float or double).
+// work_tables: 6*P*P doubles; work_half: 6*(N+1)*P double2.
+template <typename T>
+cudaError_t launch_gen_set(const GenSet &g, int N, int logN, const double2 *tw64, void *spec,
+                           double *work_tables, double2 *work_half, cudaStream_t st);
+cudaError_t gen_kernels_init();
+
+}  // namespace sgf

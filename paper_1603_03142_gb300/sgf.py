@@ -1,0 +1,218 @@
+"""Thin ctypes binding of libsgf (C ABI in include/sgf.h).
+
+Argument marshalling only: every step of the force computation runs in the
+CUDA kernels of libsgf.so.  PyTorch supplies device memory and streams.  There
+is no fallback: importing this module raises if the native library is missing
+(build it with ``__graft_entry__.build()`` or ``python -m paper_1603_03142_gb300._build``).
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_LIB_PATH = Path(__file__).resolve().parent / "libsgf.so"
+if not _LIB_PATH.exists():
+    raise ImportError(f"libsgf.so not built at {_LIB_PATH}: run __graft_entry__.build() first")
+_lib = ctypes.CDLL(str(_LIB_PATH))
+
+SGF_MAX_LEVELS = 8
+SGF_OK, SGF_EINVAL, SGF_ENOMEM, SGF_ECUDA, SGF_ETIMEOUT, SGF_EUNSUPPORTED = range(6)
+STATUS_NAMES = {0: "SGF_OK", 1: "SGF_EINVAL", 2: "SGF_ENOMEM", 3: "SGF_ECUDA", 4: "SGF_ETIMEOUT",
+                5: "SGF_EUNSUPPORTED"}
+FP64, FP32, BF16X = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16x": BF16X}
+
+# every symbol include/sgf.h declares
+EXPORTS = ["sgf_plan_create", "sgf_plan_share", "sgf_plan_stats_get", "sgf_solve", "sgf_solve_host",
+           "sgf_solve_batched", "sgf_plan_destroy", "sgf_last_error", "sgf_version"]
+
+
+class NestDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("levels", ctypes.c_int32), ("x0", ctypes.c_double),
+                ("y0", ctypes.c_double), ("h0", ctypes.c_double),
+                ("off", (ctypes.c_int32 * 2) * SGF_MAX_LEVELS)]
+
+
+class PlanStats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("levels", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("forward_slabs", ctypes.c_int32), ("outputs", ctypes.c_int32),
+                ("spectra_sets", ctypes.c_int32), ("launches_per_solve", ctypes.c_int32),
+                ("workspace_bytes", ctypes.c_size_t), ("spectra_bytes", ctypes.c_size_t),
+                ("algorithmic_bytes", ctypes.c_size_t), ("plan_ms", ctypes.c_double)]
+
+
+_vpp = ctypes.POINTER(ctypes.c_void_p)
+_lib.sgf_plan_create.argtypes = [ctypes.POINTER(NestDesc), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+_lib.sgf_plan_share.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+_lib.sgf_plan_stats_get.argtypes = [ctypes.c_void_p, ctypes.POINTER(PlanStats)]
+_lib.sgf_solve.argtypes = [ctypes.c_void_p, _vpp, _vpp, _vpp, ctypes.c_void_p]
+_lib.sgf_solve_host.argtypes = [ctypes.c_void_p, _vpp, _vpp, _vpp, ctypes.c_void_p]
+_lib.sgf_solve_batched.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32,
+                                   ctypes.POINTER(_vpp), ctypes.POINTER(_vpp), ctypes.POINTER(_vpp),
+                                   ctypes.c_void_p]
+_lib.sgf_plan_destroy.argtypes = [ctypes.c_void_p]
+_lib.sgf_last_error.restype = ctypes.c_char_p
+_lib.sgf_version.restype = ctypes.c_char_p
+for _f in ("sgf_plan_create", "sgf_plan_share", "sgf_plan_stats_get", "sgf_solve", "sgf_solve_host",
+           "sgf_solve_batched", "sgf_plan_destroy"):
+    getattr(_lib, _f).restype = ctypes.c_int
+
+
+class SgfError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {STATUS_NAMES.get(status, status)}: {last_error()}")
+
+
+def last_error() -> str:
+    return _lib.sgf_last_error().decode()
+
+
+def version() -> str:
+    return _lib.sgf_version().decode()
+
+
+def library_path() -> Path:
+    return _LIB_PATH
+
+
+def _check(status: int, what: str):
+    if status != SGF_OK:
+        raise SgfError(status, what)
+
+
+def make_desc(nest) -> NestDesc:
+    d = NestDesc()
+    d.n, d.levels = int(nest.n), int(nest.levels)
+    d.x0, d.y0, d.h0 = float(nest.x0), float(nest.y0), float(nest.h0)
+    for l in range(1, min(int(nest.levels), SGF_MAX_LEVELS, len(nest.off))):
+        d.off[l][0], d.off[l][1] = int(nest.off[l][0]), int(nest.off[l][1])
+    return d
+
+
+def _ptrs(ptrs: Sequence[int]):
+    return (ctypes.c_void_p * len(ptrs))(*[ctypes.c_void_p(int(p)) for p in ptrs])
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return int(stream.cuda_stream)
+    return int(stream)
+
+
+class Plan:
+    """A solve plan: nest geometry + precision, resident kernel spectra, workspace."""
+
+    def __init__(self, nest, precision="fp32", _handle=None):
+        self.nest = nest
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.n, self.levels = int(nest.n), int(nest.levels)
+        if _handle is not None:
+            self._h = _handle
+            return
+        h = ctypes.c_void_p()
+        desc = make_desc(nest)
+        _check(_lib.sgf_plan_create(ctypes.byref(desc), self.precision, ctypes.byref(h)), "sgf_plan_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def dtype_name(self) -> str:
+        return "float64" if self.precision == FP64 else "float32"
+
+    def share(self) -> "Plan":
+        h = ctypes.c_void_p()
+        _check(_lib.sgf_plan_share(self._h, ctypes.byref(h)), "sgf_plan_share")
+        return Plan(self.nest, self.precision, _handle=h)
+
+    def stats(self) -> dict:
+        st = PlanStats()
+        _check(_lib.sgf_plan_stats_get(self._h, ctypes.byref(st)), "sgf_plan_stats_get")
+        return {name: getattr(st, name) for name, _ in PlanStats._fields_}
+
+    def solve_ptrs(self, sigma_ptrs, fx_ptrs, fy_ptrs, stream=None):
+        _check(_lib.sgf_solve(self._h, _ptrs(sigma_ptrs), _ptrs(fx_ptrs), _ptrs(fy_ptrs),
+                              ctypes.c_void_p(_stream_handle(stream))), "sgf_solve")
+
+    def solve(self, sigma, fx=None, fy=None, stream=None):
+        """sigma: list of per-level contiguous CUDA tensors (n, n). Returns (fx, fy) lists."""
+        import torch
+        sig = list(sigma)
+        if len(sig) != self.levels:
+            raise ValueError(f"need {self.levels} sigma levels")
+        dt = torch.float64 if self.precision == FP64 else torch.float32
+        for s in sig:
+            if not (s.is_cuda and s.is_contiguous() and s.dtype == dt and tuple(s.shape) == (self.n, self.n)):
+                raise ValueError(f"sigma levels must be contiguous CUDA {dt} tensors of shape ({self.n}, {self.n})")
+        if fx is None:
+            fx = [torch.empty_like(s) for s in sig]
+        if fy is None:
+            fy = [torch.empty_like(s) for s in sig]
+        self.solve_ptrs([s.data_ptr() for s in sig], [t.data_ptr() for t in fx], [t.data_ptr() for t in fy], stream)
+        return fx, fy
+
+    def solve_host(self, sigma: Sequence[np.ndarray], fx=None, fy=None, stream=None):
+        """Host-buffer solve (copies inside the library; returns when done)."""
+        dt = np.float64 if self.precision == FP64 else np.float32
+        sig = [np.ascontiguousarray(s, dtype=dt) for s in sigma]
+        if fx is None:
+            fx = [np.empty((self.n, self.n), dtype=dt) for _ in range(self.levels)]
+        if fy is None:
+            fy = [np.empty((self.n, self.n), dtype=dt) for _ in range(self.levels)]
+        sp = [a.ctypes.data for a in sig]
+        xp = [a.ctypes.data for a in fx]
+        yp = [a.ctypes.data for a in fy]
+        self.solve_host_ptrs(sp, xp, yp, stream)
+        return fx, fy
+
+    def solve_host_ptrs(self, sigma_ptrs, fx_ptrs, fy_ptrs, stream=None):
+        _check(_lib.sgf_solve_host(self._h, _ptrs(sigma_ptrs), _ptrs(fx_ptrs), _ptrs(fy_ptrs),
+                                   ctypes.c_void_p(_stream_handle(stream))), "sgf_solve_host")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.sgf_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_batched(plans: Sequence[Plan], sigma, fx, fy, stream=None):
+    """plans[k] solves sigma[k] -> fx[k], fy[k] (per-level CUDA tensors) in one batched call."""
+    n = len(plans)
+    ph = (ctypes.c_void_p * n)(*[p.handle for p in plans])
+    keep = []
+
+    def table(lists):
+        arrs = []
+        for lst in lists:
+            a = _ptrs([t.data_ptr() for t in lst])
+            keep.append(a)
+            arrs.append(ctypes.cast(a, _vpp))
+        return (_vpp * n)(*arrs)
+
+    _check(_lib.sgf_solve_batched(ph, n, table(sigma), table(fx), table(fy),
+                                  ctypes.c_void_p(_stream_handle(stream))), "sgf_solve_batched")
+
+
+def create_status(nest, precision) -> int:
+    """Status of sgf_plan_create without keeping the plan (validation probes)."""
+    h = ctypes.c_void_p()
+    desc = make_desc(nest)
+    st = _lib.sgf_plan_create(ctypes.byref(desc), PRECISIONS.get(precision, precision), ctypes.byref(h))
+    if st == SGF_OK:
+        _lib.sgf_plan_destroy(h)
+    return st

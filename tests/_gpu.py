@@ -1,0 +1,43 @@
+"""Shared helpers of the GPU tests: run the CUDA path, compare with the oracle."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+def sgf():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1603_03142_gb300 import sgf as mod
+    return mod
+
+
+def run_gpu(plan, sigma):
+    """Device solve of numpy sigma levels; returns numpy float64 (fx, fy) lists."""
+    dt = torch.float64 if plan.precision == 0 else torch.float32
+    sig = [torch.from_numpy(np.ascontiguousarray(s)).to(device="cuda", dtype=dt) for s in sigma]
+    fx, fy = plan.solve(sig)
+    torch.cuda.synchronize()
+    return [t.double().cpu().numpy() for t in fx], [t.double().cpu().numpy() for t in fy]
+
+
+def rel_linf_levels(nest, gx, gy, ox, oy):
+    """Per level: max over uncovered cells and both components of |F - F_oracle| / max |F_oracle|."""
+    out = []
+    for l in range(nest.levels):
+        keep = ~nest.covered_mask(l)
+        scale = max(np.abs(ox[l][keep]).max(), np.abs(oy[l][keep]).max())
+        err = max(np.abs(gx[l] - ox[l])[keep].max(), np.abs(gy[l] - oy[l])[keep].max())
+        out.append(err / scale)
+    return out
+
+
+def tol(precision: str, n: int) -> float:
+    """Parity bound, relative L-infinity against the FP64 oracle.
+
+    fp32: 1e-5, the bound the method is held to.  fp64: both sides evaluate the
+    same closed forms whose double differences cancel: corner values grow like
+    n (lattice units) while the differences shrink, so each table entry carries
+    ~eps * n absolute error, and the transforms add ~eps log2(2n); 1e-13 * n
+    covers both with margin (6e-12 at n = 64, 2.6e-11 at n = 256)."""
+    return 1e-5 if precision == "fp32" else 1e-13 * n

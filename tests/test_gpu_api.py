@@ -1,0 +1,81 @@
+"""GPU tests of the C ABI's behaviour: edge cases, host-buffer and batched
+entry points, shared plans, determinism, error paths."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1603_03142_gb300 import workloads as W
+from tests._gpu import rel_linf_levels, run_gpu, sgf, tol, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return sgf()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_zero_density_gives_zero_force(lib, prec):
+    nest = W.Nest(n=32, levels=2, off=[(0, 0), (8, 8)])
+    gx, gy = run_gpu(lib.Plan(nest, prec), [np.zeros((32, 32))] * 2)
+    assert all(np.all(a == 0.0) for a in gx + gy)
+
+
+def test_single_cell_sign(lib):
+    nest = W.Nest(n=16)
+    s = np.zeros((16, 16))
+    s[5, 12] = 1.0
+    gx, gy = run_gpu(lib.Plan(nest, "fp64"), [s])
+    ox, oy = oracle.force(nest, [s])
+    assert gx[0][5, 3] > 0.0
+    assert max(rel_linf_levels(nest, gx, gy, ox, oy)) <= tol("fp64", 16)
+
+
+def test_host_buffers_match_device(lib):
+    nest = W.Nest(n=64, levels=3, off=[(0, 0), (10, 20), (16, 0)])
+    rng = np.random.Generator(np.random.PCG64(2))
+    sigma = [rng.uniform(0, 1, (64, 64)).astype(np.float32) for _ in range(3)]
+    plan = lib.Plan(nest, "fp32")
+    dx, dy = run_gpu(plan, sigma)
+    hx, hy = plan.solve_host(sigma)
+    for l in range(3):
+        assert np.array_equal(hx[l].astype(np.float64), dx[l])
+        assert np.array_equal(hy[l].astype(np.float64), dy[l])
+
+
+def test_deterministic_and_shared_plan(lib):
+    nest, sigma = W.config2(n=64)
+    plan = lib.Plan(nest, "fp32")
+    a = run_gpu(plan, sigma)
+    b = run_gpu(plan, sigma)
+    shared = plan.share()
+    c = run_gpu(shared, sigma)
+    for l in range(3):
+        assert np.array_equal(a[0][l], b[0][l]) and np.array_equal(a[1][l], b[1][l])
+        assert np.array_equal(a[0][l], c[0][l]) and np.array_equal(a[1][l], c[1][l])
+    st = plan.stats()
+    assert st["spectra_bytes"] == shared.stats()["spectra_bytes"] > 0
+
+
+def test_batched_matches_single(lib):
+    rng = np.random.Generator(np.random.PCG64(4))
+    probs = [W.random_nest_problem(rng, n, L) for n, L in [(32, 1), (64, 3), (16, 2), (64, 2)]]
+    plans = [lib.Plan(nest, "fp32") for nest, _ in probs]
+    singles = [run_gpu(p, s) for p, (_, s) in zip(plans, probs)]
+    sig = [[torch.from_numpy(a).float().cuda() for a in s] for _, s in probs]
+    fx = [[torch.empty_like(a) for a in s] for s in sig]
+    fy = [[torch.empty_like(a) for a in s] for s in sig]
+    lib.solve_batched(plans, sig, fx, fy)
+    torch.cuda.synchronize()
+    for k in range(len(probs)):
+        for l in range(len(sig[k])):
+            assert np.array_equal(fx[k][l].double().cpu().numpy(), singles[k][0][l])
+            assert np.array_equal(fy[k][l].double().cpu().numpy(), singles[k][1][l])
+
+
+def test_null_buffers_rejected(lib):
+    plan = lib.Plan(W.Nest(n=16), "fp32")
+    with pytest.raises(lib.SgfError) as e:
+        plan.solve_ptrs([0], [0], [0])
+    assert e.value.status == lib.SGF_EINVAL
