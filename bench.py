@@ -1,0 +1,323 @@
+"""Benchmark: second-order thin-disk force on the 4096^2 uniform grid, FP32.
+
+One step = one full solve through the C ABI (restriction is empty on one
+level; forward row pass with the slopes, column pass with the spectral
+multiply-accumulate, inverse row pass), kernel spectra resident in HBM (built
+once per shape at plan creation, timed separately as plan_ms).
+
+Prints ONE JSON line (rank 0).  --impl reference times the CPU FP64 oracle on
+a bounded sample of the same workload instead.
+
+Multi-GPU (torchrun): every rank solves its own replica of the workload; there
+is no data-path collective (replicas only); the timed region is bracketed by a
+barrier and the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+N_DEFAULT = 4096
+METRIC = "force cells/s"
+UNIT = "cells/s"
+L2_BYTES = 129 * 2 ** 20
+
+
+def peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in getattr(self, "lines", []):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def csrc_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for p in sorted((ROOT / "paper_1603_03142_gb300" / "csrc").glob("*")):
+        h.update(p.name.encode())
+        h.update(p.read_bytes())
+    return h.hexdigest()
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+    when the CUDA sources changed since those counters were taken."""
+    f = ROOT / "profiles" / "traffic.json"
+    if not f.exists():
+        return None
+    try:
+        d = json.loads(f.read_text())
+    except ValueError:
+        return None
+    if d.get("csrc_sha256") != csrc_digest():
+        return None
+    return d.get("dram_bytes_per_launch", {}).get(kernel)
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("SGF_BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+    return world, rank, local
+
+
+def oracle_sample_rate(n: int, seconds: float = 12.0, seed: int = 0):
+    """Oracle cells/s on a bounded sample of target cells of the 4096^2 workload."""
+    import numpy as np
+    import oracle
+    from paper_1603_03142_gb300 import workloads as W
+    nest, sigma = W.config3(n, seed=0)
+    prepared = oracle.prepare(nest, sigma)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    cores = oracle.max_threads()
+    # calibrate with one target per core, then size the sample to ~`seconds`
+    k0 = max(1, cores)
+    ii = rng.integers(0, n, k0)
+    jj = rng.integers(0, n, k0)
+    t0 = time.perf_counter()
+    oracle.force_at(nest, sigma, np.zeros(k0, dtype=int), ii, jj, prepared=prepared)
+    dt0 = time.perf_counter() - t0
+    k = max(k0, int(k0 * seconds / max(dt0, 1e-3)) // k0 * k0)
+    ii = rng.integers(0, n, k)
+    jj = rng.integers(0, n, k)
+    t0 = time.perf_counter()
+    oracle.force_at(nest, sigma, np.zeros(k, dtype=int), ii, jj, prepared=prepared)
+    dt = time.perf_counter() - t0
+    return {"value": k / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{k} seeded target cells of the {n}^2 grid, full direct sum over all {n * n} "
+                      f"source cells each ({dt:.1f} s)", "seconds": dt, "targets": k}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    steps = []
+    for s in range(args.warmup + args.steps):
+        warm = s < args.warmup
+        info = oracle_sample_rate(args.n, seconds=1.0 if warm else args.ref_seconds, seed=s)
+        if not warm:
+            steps.append(info)
+    tot_t = sum(x["seconds"] for x in steps)
+    tot_c = sum(x["targets"] for x in steps)
+    value = tot_c / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / len(steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"uniform-{args.n}x{args.n}-lognormal-taper", "n": args.n, "levels": 1,
+                       "precision": "fp32", "parallelism": "replicas", "engine": "cpu-fp64-oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": steps[-1]["cores"], "kind": "oracle",
+                             "sample": steps[-1]["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_1603_03142_gb300 import sgf, workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n
+    nest, sigma = W.config3(n, seed=rank)
+    plan = sgf.Plan(nest, "fp32")
+    st = plan.stats()
+    # rotating input/output sets so nothing carries over in L2 between steps
+    sets = max(2, -(-4 * L2_BYTES // (3 * n * n * 4)))
+    base = torch.from_numpy(sigma[0].astype(np.float32)).to(dev)
+    sig = [base.roll(shifts=k, dims=0).contiguous() for k in range(sets)]
+    fx = [torch.empty_like(base) for _ in range(sets)]
+    fy = [torch.empty_like(base) for _ in range(sets)]
+    stream = torch.cuda.current_stream(dev)
+
+    def step(k):
+        plan.solve_ptrs([sig[k % sets].data_ptr()], [fx[k % sets].data_ptr()], [fy[k % sets].data_ptr()], stream)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    plan.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ev0.record(stream)
+        for k in range(args.steps):
+            step(k)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    plan.profile(False)
+    ms = ev0.elapsed_time(ev1)
+    prof = plan.profile_read()
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    cells = float(n * n)
+    value = world * cells * args.steps / (ms / 1e3)
+
+    # e2e: host buffers through the C ABI, copies inside the timed region
+    pin_s = torch.from_numpy(sigma[0].astype(np.float32)).pin_memory()
+    pin_x = torch.empty((n, n), dtype=torch.float32).pin_memory()
+    pin_y = torch.empty((n, n), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        plan.solve_host_ptrs([pin_s.data_ptr()], [pin_x.data_ptr()], [pin_y.data_ptr()], stream)
+    e2e_steps = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.solve_host_ptrs([pin_s.data_ptr()], [pin_x.data_ptr()], [pin_y.data_ptr()], stream)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * cells * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": n * n * 4, "d2h_bytes_per_step": 2 * n * n * 4}
+
+    if rank != 0:
+        return
+    # roofline of the dominant kernel
+    peak, peak_kind = peaks()
+    kern = prof["kernels"]
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    C = 8  # complex64 bytes
+    N1 = n + 1
+    algo = {"row_fwd": n * n * 4 + 3 * N1 * n * C,
+            "col": 3 * N1 * n * C + 6 * N1 * N1 * 4 + 2 * N1 * n * C,
+            "row_inv": 2 * N1 * n * C + 2 * n * n * 4,
+            "restrict": 0}
+    avg_ms = kern[dom]["ms"] / max(1, kern[dom]["launches"])
+    achieved = algo[dom] / (avg_ms / 1e3) / 1e9
+    total_ms = sum(v["ms"] for v in kern.values())
+    traffic = recorded_traffic(dom)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample_rate(n, seconds=args.ref_seconds)
+        cpu.pop("seconds", None)
+        cpu.pop("targets", None)
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"uniform-{n}x{n}-lognormal-taper", "n": n, "levels": 1,
+                   "precision": "fp32", "parallelism": f"replicas{world}",
+                   "l2": f"{sets} rotating input/output sets ({sets * 3 * n * n * 4 / 2**20:.0f} MiB) > 129 MiB L2",
+                   "plan_ms": st["plan_ms"], "spectra_mib": st["spectra_bytes"] / 2**20,
+                   "algorithmic_bytes_per_solve": st["algorithmic_bytes"],
+                   "solve_gbs": st["algorithmic_bytes"] / (ms_step / 1e3) / 1e9},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": algo[dom],
+                     "kernel_ms": {k: v["ms"] / max(1, v["launches"]) for k, v in kern.items() if v["launches"]},
+                     "kernel_share": {k: v["ms"] / total_ms for k, v in kern.items() if v["launches"]}},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": args.steps * st["launches_per_solve"],
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--ref-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        args.warmup = 3
+    if args.impl == "reference":
+        # the oracle runs on rank 0's host cores only; other ranks exit without work
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        args.ref_seconds = min(args.ref_seconds, max(1.0, 90.0 / (args.steps + args.warmup)))
+        run_reference(args, world, rank)
+        return
+    world, rank, local = dist_setup()
+    run_gpu(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -136,6 +136,23 @@ sgf_status sgf_solve_batched(sgf_plan *const *plans, int32_t count, const void *
 
 sgf_status sgf_plan_destroy(sgf_plan *plan);
 
+/* Per-kernel device times of this plan's solves, for measurement (no paper
+ * counterpart).  Kernel k: 0 restriction, 1 forward row pass, 2 column pass
+ * (with the spectral multiply-accumulate), 3 inverse row pass. */
+typedef struct {
+    int32_t solves;       /* solves recorded since the last read */
+    int32_t launches[4];  /* launches per kernel */
+    double ms[4];         /* summed device time per kernel (CUDA events on the solve stream) */
+} sgf_kernel_times;
+
+/* enable != 0: every later sgf_solve on this plan records CUDA events around
+ * its kernel launches on the solve's stream (events are created on first
+ * use); enable == 0 stops recording. */
+sgf_status sgf_plan_profile(sgf_plan *plan, int32_t enable);
+
+/* Waits for the recorded solves, returns their summed times and clears them. */
+sgf_status sgf_plan_profile_read(sgf_plan *plan, sgf_kernel_times *out);
+
 /* Description of the last failure on the calling thread; valid until the
  * next sgf_* call on this thread.  Never NULL. */
 const char *sgf_last_error(void);

@@ -115,6 +115,11 @@ struct sgf_plan {
     void *d_stage = nullptr;
     size_t workspace_bytes = 0;
     size_t algorithmic_bytes = 0;
+    // optional per-kernel timing: 5 events per solve (before restriction, after
+    // restriction, after row_fwd, after col, after row_inv)
+    bool profile = false;
+    std::vector<cudaEvent_t> events;
+    size_t events_used = 0;
 };
 
 namespace {
@@ -431,6 +436,22 @@ sgf_status build_spectra(sgf_plan *p)
     return st;
 }
 
+sgf_status mark(sgf_plan *p, cudaStream_t st)
+{
+    if (!p->profile)
+        return SGF_OK;
+    cudaError_t e;
+    if (p->events_used == p->events.size()) {
+        cudaEvent_t ev;
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess)
+            return cuda_fail(e, "cudaEventCreate(profile)");
+        p->events.push_back(ev);
+    }
+    if ((e = cudaEventRecord(p->events[p->events_used++], st)) != cudaSuccess)
+        return cuda_fail(e, "cudaEventRecord(profile)");
+    return SGF_OK;
+}
+
 template <typename T>
 sgf_status solve_impl(sgf_plan *p, const void *const *sigma, void *const *fx, void *const *fy,
                       cudaStream_t st)
@@ -448,6 +469,9 @@ sgf_status solve_impl(sgf_plan *p, const void *const *sigma, void *const *fx, vo
         a.child_ox[l] = p->desc.off[l + 1][0];
         a.child_oy[l] = p->desc.off[l + 1][1];
     }
+    sgf_status ms;
+    if ((ms = mark(p, st)) != SGF_OK)
+        return ms;
     T *restricted = static_cast<T *>(p->d_restricted);
     a.src[L - 1] = static_cast<const T *>(sigma[L - 1]);
     for (int l = L - 2; l >= 0; --l) {
@@ -474,13 +498,19 @@ sgf_status solve_impl(sgf_plan *p, const void *const *sigma, void *const *fx, vo
     for (int l = 0; l <= L; ++l)
         a.contrib_begin[l] = p->contrib_begin[l];
     cudaError_t e;
+    if ((ms = mark(p, st)) != SGF_OK)
+        return ms;
     if ((e = launch_row_fwd<T>(a, (int)p->items.size(), st)) != cudaSuccess)
         return cuda_fail(e, "row_fwd launch");
+    if ((ms = mark(p, st)) != SGF_OK)
+        return ms;
     if ((e = launch_col<T>(a, (int)p->outs.size(), st)) != cudaSuccess)
         return cuda_fail(e, "col launch");
+    if ((ms = mark(p, st)) != SGF_OK)
+        return ms;
     if ((e = launch_row_inv<T>(a, st)) != cudaSuccess)
         return cuda_fail(e, "row_inv launch");
-    return SGF_OK;
+    return mark(p, st);
 }
 
 struct DeviceGuard {
@@ -690,10 +720,47 @@ sgf_status sgf_solve_batched(sgf_plan *const *plans, int32_t count, const void *
     return SGF_OK;
 }
 
+sgf_status sgf_plan_profile(sgf_plan *p, int32_t enable)
+{
+    if (!p)
+        return fail(SGF_EINVAL, "plan is NULL");
+    p->profile = enable != 0;
+    return SGF_OK;
+}
+
+sgf_status sgf_plan_profile_read(sgf_plan *p, sgf_kernel_times *out)
+{
+    if (!p || !out)
+        return fail(SGF_EINVAL, "NULL argument");
+    DeviceGuard g(p->device);
+    std::memset(out, 0, sizeof *out);
+    const size_t per = 5;
+    cudaError_t e;
+    if (p->events_used >= per && (e = cudaEventSynchronize(p->events[p->events_used - 1])) != cudaSuccess)
+        return cuda_fail(e, "cudaEventSynchronize(profile)");
+    for (size_t b = 0; b + per <= p->events_used; b += per) {
+        out->solves++;
+        for (int k = 0; k < 4; ++k) {
+            float ms = 0.f;
+            if ((e = cudaEventElapsedTime(&ms, p->events[b + k], p->events[b + k + 1])) != cudaSuccess)
+                return cuda_fail(e, "cudaEventElapsedTime(profile)");
+            out->ms[k] += ms;
+            out->launches[k] += k == 0 ? p->L - 1 : 1;
+        }
+    }
+    p->events_used = 0;
+    return SGF_OK;
+}
+
 sgf_status sgf_plan_destroy(sgf_plan *p)
 {
     if (!p)
         return SGF_OK;
+    {
+        DeviceGuard g(p->device);
+        for (cudaEvent_t ev : p->events)
+            cudaEventDestroy(ev);
+    }
     plan_free_owned(p);
     spectra_release(p->spec);
     delete p;

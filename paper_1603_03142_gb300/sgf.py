@@ -27,7 +27,9 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16x": BF16X}
 
 # every symbol include/sgf.h declares
 EXPORTS = ["sgf_plan_create", "sgf_plan_share", "sgf_plan_stats_get", "sgf_solve", "sgf_solve_host",
-           "sgf_solve_batched", "sgf_plan_destroy", "sgf_last_error", "sgf_version"]
+           "sgf_solve_batched", "sgf_plan_destroy", "sgf_last_error", "sgf_version", "sgf_plan_profile",
+           "sgf_plan_profile_read"]
+KERNELS = ["restrict", "row_fwd", "col", "row_inv"]
 
 
 class NestDesc(ctypes.Structure):
@@ -44,6 +46,10 @@ class PlanStats(ctypes.Structure):
                 ("algorithmic_bytes", ctypes.c_size_t), ("plan_ms", ctypes.c_double)]
 
 
+class KernelTimes(ctypes.Structure):
+    _fields_ = [("solves", ctypes.c_int32), ("launches", ctypes.c_int32 * 4), ("ms", ctypes.c_double * 4)]
+
+
 _vpp = ctypes.POINTER(ctypes.c_void_p)
 _lib.sgf_plan_create.argtypes = [ctypes.POINTER(NestDesc), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
 _lib.sgf_plan_share.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
@@ -54,10 +60,12 @@ _lib.sgf_solve_batched.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int
                                    ctypes.POINTER(_vpp), ctypes.POINTER(_vpp), ctypes.POINTER(_vpp),
                                    ctypes.c_void_p]
 _lib.sgf_plan_destroy.argtypes = [ctypes.c_void_p]
+_lib.sgf_plan_profile.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+_lib.sgf_plan_profile_read.argtypes = [ctypes.c_void_p, ctypes.POINTER(KernelTimes)]
 _lib.sgf_last_error.restype = ctypes.c_char_p
 _lib.sgf_version.restype = ctypes.c_char_p
 for _f in ("sgf_plan_create", "sgf_plan_share", "sgf_plan_stats_get", "sgf_solve", "sgf_solve_host",
-           "sgf_solve_batched", "sgf_plan_destroy"):
+           "sgf_solve_batched", "sgf_plan_destroy", "sgf_plan_profile", "sgf_plan_profile_read"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -138,6 +146,15 @@ class Plan:
         st = PlanStats()
         _check(_lib.sgf_plan_stats_get(self._h, ctypes.byref(st)), "sgf_plan_stats_get")
         return {name: getattr(st, name) for name, _ in PlanStats._fields_}
+
+    def profile(self, enable: bool = True):
+        _check(_lib.sgf_plan_profile(self._h, 1 if enable else 0), "sgf_plan_profile")
+
+    def profile_read(self) -> dict:
+        kt = KernelTimes()
+        _check(_lib.sgf_plan_profile_read(self._h, ctypes.byref(kt)), "sgf_plan_profile_read")
+        return {"solves": kt.solves,
+                "kernels": {KERNELS[k]: {"launches": kt.launches[k], "ms": kt.ms[k]} for k in range(4)}}
 
     def solve_ptrs(self, sigma_ptrs, fx_ptrs, fy_ptrs, stream=None):
         _check(_lib.sgf_solve(self._h, _ptrs(sigma_ptrs), _ptrs(fx_ptrs), _ptrs(fy_ptrs),
