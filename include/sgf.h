@@ -49,7 +49,7 @@ extern "C" {
 #endif
 
 #define SGF_MAX_LEVELS 8
-#define SGF_MIN_N 8
+#define SGF_MIN_N 16
 #define SGF_MAX_N 4096        /* SGF_FP32 / SGF_BF16X */
 #define SGF_MAX_N_FP64 2048   /* SGF_FP64 */
 

@@ -500,15 +500,15 @@ sgf_status solve_impl(sgf_plan *p, const void *const *sigma, void *const *fx, vo
     cudaError_t e;
     if ((ms = mark(p, st)) != SGF_OK)
         return ms;
-    if ((e = launch_row_fwd<T>(a, (int)p->items.size(), st)) != cudaSuccess)
+    if ((e = launch_row_fwd16<T>(a, (int)p->items.size(), st)) != cudaSuccess)
         return cuda_fail(e, "row_fwd launch");
     if ((ms = mark(p, st)) != SGF_OK)
         return ms;
-    if ((e = launch_col<T>(a, (int)p->outs.size(), st)) != cudaSuccess)
+    if ((e = launch_col16<T>(a, (int)p->outs.size(), st)) != cudaSuccess)
         return cuda_fail(e, "col launch");
     if ((ms = mark(p, st)) != SGF_OK)
         return ms;
-    if ((e = launch_row_inv<T>(a, st)) != cudaSuccess)
+    if ((e = launch_row_inv16<T>(a, st)) != cudaSuccess)
         return cuda_fail(e, "row_inv launch");
     return mark(p, st);
 }
@@ -580,7 +580,7 @@ sgf_status sgf_plan_create(const sgf_nest_desc *desc, sgf_precision precision, s
         return cuda_fail(e, "cudaGetDevice");
     }
     build_lists(p);
-    e = precision == SGF_FP64 ? solve_kernels_init<double>() : solve_kernels_init<float>();
+    e = precision == SGF_FP64 ? solve16_init<double>() : solve16_init<float>();
     if (e != cudaSuccess) {
         delete p;
         return cuda_fail(e, "solve kernels init");

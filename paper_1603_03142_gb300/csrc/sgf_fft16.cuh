@@ -1,0 +1,255 @@
+// sgf_fft16.cuh -- register-resident block FFT (radix 16) for N in [16, 4096].
+//
+// Layout.  A CTA transforms B sequences of length N.  The data are cut into
+// "slots" of 16 complex values: slot (s, j), j in [0, N/16), holds elements
+// j + u*N/16 (u = 0..15) of sequence s, in one thread's registers.  Every
+// stage of the Stockham autosort recursion reads its butterfly inputs in
+// exactly this pattern; radix-16 stages run while 16 divides the remaining
+// length and one radix-2/4/8 stage closes (a slot then holds 16/R
+// butterflies).  Between stages the data go through shared memory once
+// (padded by one element every 16 so strided writes do not collide in banks).
+// The last stage's outputs land in the same slot pattern, in natural order:
+// after a forward transform, slot (s, j) holds bins j + u*N/16.  So data can be
+// loaded from global memory straight into registers, transformed, multiplied
+// bin by bin, inverse-transformed and stored, with the shared-memory traffic
+// limited to the exchanges between stages.
+//
+// Twiddles: W_{R Ns}^{r k} from the table W_P^k = exp(-2 pi i k / P), P = 2N.
+// The in-register 16- and 8-point DFTs use the exact constants cos(pi/8),
+// sin(pi/8) and sqrt(1/2).
+#pragma once
+#include "sgf_fft.cuh"
+
+namespace sgf {
+
+#define SGF_HD __host__ __device__ __forceinline__
+
+template <typename C> struct K16;
+template <> struct K16<float2> {
+    static SGF_HD float c1() { return 0.92387953251128674f; }   // cos(pi/8)
+    static SGF_HD float s1() { return 0.38268343236508978f; }   // sin(pi/8)
+    static SGF_HD float h() { return 0.70710678118654752f; }    // sqrt(1/2)
+};
+template <> struct K16<double2> {
+    static SGF_HD double c1() { return 0.92387953251128674; }
+    static SGF_HD double s1() { return 0.38268343236508978; }
+    static SGF_HD double h() { return 0.70710678118654752; }
+};
+
+template <typename C> SGF_HD C hmk(typename Real<C>::T x, typename Real<C>::T y) { C c; c.x = x; c.y = y; return c; }
+template <typename C> SGF_HD C hadd(C a, C b) { return hmk<C>(a.x + b.x, a.y + b.y); }
+template <typename C> SGF_HD C hsub(C a, C b) { return hmk<C>(a.x - b.x, a.y - b.y); }
+template <typename C> SGF_HD C hmul(C a, C b) { return hmk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+template <typename C> SGF_HD C hmulc(C a, C b) { return hmk<C>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y); }
+// times exp(-i pi/2) (forward) / exp(+i pi/2) (inverse)
+template <typename C, bool INV> SGF_HD C hrot(C a) { return INV ? hmk<C>(-a.y, a.x) : hmk<C>(a.y, -a.x); }
+
+template <typename C, bool INV>
+SGF_HD void hdft4(C &v0, C &v1, C &v2, C &v3)
+{
+    C a0 = hadd(v0, v2), a1 = hsub(v0, v2), a2 = hadd(v1, v3), a3 = hrot<C, INV>(hsub(v1, v3));
+    v0 = hadd(a0, a2);
+    v1 = hadd(a1, a3);
+    v2 = hsub(a0, a2);
+    v3 = hsub(a1, a3);
+}
+
+// multiply by W16^e (forward: exp(-2 pi i e/16)), e in 0..9
+template <typename C, bool INV>
+SGF_HD C w16(C a, int e)
+{
+    using T = typename Real<C>::T;
+    const T c1 = K16<C>::c1(), s1 = K16<C>::s1(), h = K16<C>::h();
+    T wr, wi;
+    switch (e) {
+    case 0: return a;
+    case 1: wr = c1; wi = -s1; break;
+    case 2: wr = h; wi = -h; break;
+    case 3: wr = s1; wi = -c1; break;
+    case 4: return hrot<C, INV>(a);
+    case 6: wr = -h; wi = -h; break;
+    case 9: wr = -c1; wi = s1; break;
+    default: wr = 1; wi = 0; break;  // not used
+    }
+    if (INV)
+        wi = -wi;
+    return hmk<C>(a.x * wr - a.y * wi, a.x * wi + a.y * wr);
+}
+
+// In-place 16-point DFT in natural order: v[k] <- sum_n v[n] W16^{nk}.
+template <typename C, bool INV>
+SGF_HD void hdft16(C *v)
+{
+    C a[16];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        C x0 = v[n2], x1 = v[n2 + 4], x2 = v[n2 + 8], x3 = v[n2 + 12];
+        hdft4<C, INV>(x0, x1, x2, x3);
+        a[4 * n2 + 0] = x0;
+        a[4 * n2 + 1] = w16<C, INV>(x1, n2);
+        a[4 * n2 + 2] = w16<C, INV>(x2, 2 * n2);
+        a[4 * n2 + 3] = w16<C, INV>(x3, 3 * n2);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        C b0 = a[k1], b1 = a[4 + k1], b2 = a[8 + k1], b3 = a[12 + k1];
+        hdft4<C, INV>(b0, b1, b2, b3);
+        v[k1] = b0;
+        v[k1 + 4] = b1;
+        v[k1 + 8] = b2;
+        v[k1 + 12] = b3;
+    }
+}
+
+// In-place R-point DFT (R = 2, 4, 8) of the values v[Q + r*(16/R)], r = 0..R-1;
+// R and Q are compile-time so the register array is never indexed at run time.
+template <typename C, bool INV, int R, int Q>
+SGF_HD void hdft_small(C *v)
+{
+    constexpr int S = 16 / R;
+    if (R == 2) {
+        C a = v[Q], b = v[Q + S];
+        v[Q] = hadd(a, b);
+        v[Q + S] = hsub(a, b);
+    } else if (R == 4) {
+        hdft4<C, INV>(v[Q], v[Q + S], v[Q + 2 * S], v[Q + 3 * S]);
+    } else {  // R == 8: n = 2 n1 + n2, k = k1 + 4 k2
+        C e0 = v[Q], e1 = v[Q + 2 * S], e2 = v[Q + 4 * S], e3 = v[Q + 6 * S];
+        C o0 = v[Q + S], o1 = v[Q + 3 * S], o2 = v[Q + 5 * S], o3 = v[Q + 7 * S];
+        hdft4<C, INV>(e0, e1, e2, e3);
+        hdft4<C, INV>(o0, o1, o2, o3);
+        o1 = w16<C, INV>(o1, 2);  // W8^1 = W16^2
+        o2 = w16<C, INV>(o2, 4);  // W8^2
+        o3 = w16<C, INV>(o3, 6);  // W8^3
+        v[Q] = hadd(e0, o0);
+        v[Q + S] = hadd(e1, o1);
+        v[Q + 2 * S] = hadd(e2, o2);
+        v[Q + 3 * S] = hadd(e3, o3);
+        v[Q + 4 * S] = hsub(e0, o0);
+        v[Q + 5 * S] = hsub(e1, o1);
+        v[Q + 6 * S] = hsub(e2, o2);
+        v[Q + 7 * S] = hsub(e3, o3);
+    }
+}
+
+// The closing radix-R stage on one slot: 16/R butterflies, butterfly Q holding
+// v[Q + r*(16/R)]; its twiddles are W_{R Ns}^{r k}.
+template <typename C, bool INV, int R, int Q>
+SGF_HD void stage_small_one(C *v, int N, int Ns, int j, const C *tw)
+{
+    constexpr int S = 16 / R;
+    const int jq = j + Q * (N / 16);
+    const int k = jq & (Ns - 1);
+    if (Ns > 1) {
+        const int step = k * ((2 * N) / (R * Ns));
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            const C w = tw[r * step];
+            v[Q + r * S] = INV ? hmulc(v[Q + r * S], w) : hmul(v[Q + r * S], w);
+        }
+    }
+    hdft_small<C, INV, R, Q>(v);
+}
+
+template <typename C, bool INV, int R>
+SGF_HD void stage_small(C *v, int N, int Ns, int j, const C *tw)
+{
+    stage_small_one<C, INV, R, 0>(v, N, Ns, j, tw);
+    if (16 / R > 1) stage_small_one<C, INV, R, (16 / R > 1 ? 1 : 0)>(v, N, Ns, j, tw);
+    if (16 / R > 2) {
+        stage_small_one<C, INV, R, (16 / R > 2 ? 2 : 0)>(v, N, Ns, j, tw);
+        stage_small_one<C, INV, R, (16 / R > 3 ? 3 : 0)>(v, N, Ns, j, tw);
+    }
+    if (16 / R > 4) {
+        stage_small_one<C, INV, R, (16 / R > 4 ? 4 : 0)>(v, N, Ns, j, tw);
+        stage_small_one<C, INV, R, (16 / R > 5 ? 5 : 0)>(v, N, Ns, j, tw);
+        stage_small_one<C, INV, R, (16 / R > 6 ? 6 : 0)>(v, N, Ns, j, tw);
+        stage_small_one<C, INV, R, (16 / R > 7 ? 7 : 0)>(v, N, Ns, j, tw);
+    }
+}
+
+SGF_HD int pad16(int i) { return i + (i >> 4); }
+
+// Stage bookkeeping shared by the device engine and the host test emulator.
+struct Fft16Plan {
+    int N, logN, nst, S16, rlast;
+    SGF_HD void init(int n, int logn)
+    {
+        N = n;
+        logN = logn;
+        S16 = logn >> 2;
+        rlast = 1 << (logn & 3);
+        nst = S16 + (rlast > 1 ? 1 : 0);
+    }
+    SGF_HD int radix(int st) const { return st < S16 ? 16 : rlast; }
+};
+
+// One stage's arithmetic on a slot: twiddles + DFT.  Ns = product of earlier radices.
+template <typename C, bool INV>
+SGF_HD void fft16_stage_compute(C *v, const Fft16Plan &pl, int st, int Ns, int j, const C *tw)
+{
+    const int R = pl.radix(st), N = pl.N;
+    if (R == 16) {
+        const int k = j & (Ns - 1);
+        if (Ns > 1) {
+            const int step = k * (N / (8 * Ns));  // W_{16 Ns}^{r k} = W_P^{r k 2N/(16 Ns)}
+#pragma unroll
+            for (int r = 1; r < 16; ++r) {
+                const C w = tw[r * step];
+                v[r] = INV ? hmulc(v[r], w) : hmul(v[r], w);
+            }
+        }
+        hdft16<C, INV>(v);
+    } else if (R == 8) {
+        stage_small<C, INV, 8>(v, N, Ns, j, tw);
+    } else if (R == 4) {
+        stage_small<C, INV, 4>(v, N, Ns, j, tw);
+    } else {
+        stage_small<C, INV, 2>(v, N, Ns, j, tw);
+    }
+}
+
+// Where a non-final (radix-16) stage writes output r of slot j.
+SGF_HD int fft16_out_index(int j, int Ns, int r)
+{
+    const int k = j & (Ns - 1);
+    return (j - k) * 16 + k + r * Ns;
+}
+
+#ifdef __CUDACC__
+// Block-wide transform of the slot held in v.  sbuf: B * pad16(N) complex in
+// shared memory (sequence s at s * (N + N/16)).  Every thread of the block must
+// call this (active == false: a thread without a slot still takes part in the
+// barriers).  Starts with a barrier, so sbuf may still be in use on entry.
+template <typename C, bool INV>
+__device__ __forceinline__ void fft16_block(C *v, C *sbuf, int s, int j, bool active, const Fft16Plan &pl,
+                                            const C *__restrict__ tw)
+{
+    const int N = pl.N, SP = N + (N >> 4), Q = N >> 4;
+    C *seq = sbuf + (size_t)s * SP;
+    int Ns = 1;
+    for (int st = 0; st < pl.nst; ++st) {
+        if (st > 0) {
+            __syncthreads();  // previous stage's stores are visible
+            if (active) {
+#pragma unroll
+                for (int u = 0; u < 16; ++u)
+                    v[u] = seq[pad16(j + u * Q)];
+            }
+        }
+        if (active)
+            fft16_stage_compute<C, INV>(v, pl, st, Ns, j, tw);
+        if (st + 1 < pl.nst) {
+            __syncthreads();  // every thread has read this stage's inputs
+            if (active) {
+#pragma unroll
+                for (int r = 0; r < 16; ++r)
+                    seq[pad16(fft16_out_index(j, Ns, r))] = v[r];
+            }
+        }
+        Ns *= pl.radix(st);
+    }
+}
+#endif
+
+}  // namespace sgf

@@ -108,15 +108,13 @@ template <typename T>
 cudaError_t launch_restrict(const T *fine, T *coarse, const T *coarse_in, int N, int ox, int oy,
                             cudaStream_t st);
 template <typename T>
-cudaError_t launch_row_fwd(const SolveArgs<T> &a, int n_items, cudaStream_t st);
+cudaError_t launch_row_fwd16(const SolveArgs<T> &a, int n_items, cudaStream_t st);
 template <typename T>
-cudaError_t launch_col(const SolveArgs<T> &a, int n_outputs, cudaStream_t st);
+cudaError_t launch_col16(const SolveArgs<T> &a, int n_outputs, cudaStream_t st);
 template <typename T>
-cudaError_t launch_row_inv(const SolveArgs<T> &a, cudaStream_t st);
+cudaError_t launch_row_inv16(const SolveArgs<T> &a, cudaStream_t st);
 template <typename T>
-size_t smem_col_bytes(int N);
-template <typename T>
-cudaError_t solve_kernels_init();
+cudaError_t solve16_init();
 
 // Build the spectra of one set into spec (element type T: float or double).
 // work_tables: 6*P*P doubles; work_half: 6*(N+1)*P double2.

@@ -1,0 +1,372 @@
+// sgf_solve16.cu -- solve kernels on the register-resident radix-16 FFT
+// (sgf_fft16.cuh), N in [16, 4096].
+//
+// Every P = 2N point transform of the method splits into two N-point "parity
+// halves" (even bins: x[n]; odd bins: x[n] W_P^n).  One slot of 16 values per
+// thread and per half; a CTA holds both halves of one row pair (row passes),
+// or one half of one column (column pass, two CTAs per column in a cluster).
+//
+//  k_row_fwd16 : sigma rows -> (sigma, dx, dy) with the slope rule and the
+//                covered-cell mask, Case-2 phase gather, two rows per complex
+//                transform, Hermitian unpack, transposed store.
+//  k_col16     : per (column, parity half): forward column transforms of all
+//                inputs and fields, spectral multiply-accumulate in registers
+//                (the sums of products of Sec. 2.2), inverse transforms; the
+//                odd half is folded into the even half through distributed
+//                shared memory and the even CTA stores the column.
+//  k_row_inv16 : per row pair of a target level: Hermitian extension, inverse
+//                row transforms of every contributing output, Case-3 phase
+//                interleave, covered cells zeroed, Fx/Fy stored.
+#include <cooperative_groups.h>
+
+#include "sgf_fft16.cuh"
+#include "sgf_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace sgf {
+
+template <typename T> struct Cx;
+template <> struct Cx<float> { using C = float2; using C2 = float4; };
+template <> struct Cx<double> { using C = double2; using C2 = double4; };
+
+template <typename T>
+__device__ __forceinline__ bool covered16(const SolveArgs<T> &a, int s, int j, int i)
+{
+    const int ox = a.child_ox[s];
+    if (ox < 0)
+        return false;
+    const int oy = a.child_oy[s], half = a.N >> 1;
+    return i >= ox && i < ox + half && j >= oy && j < oy + half;
+}
+
+// (sigma, x difference, y difference)[f] of level s at cell (j, i); 0 on covered cells.
+template <typename T>
+__device__ __forceinline__ T field16(const SolveArgs<T> &a, int s, int j, int i, int f)
+{
+    if (covered16(a, s, j, i))
+        return T(0);
+    const int N = a.N;
+    const T *__restrict__ src = a.src[s];
+    const T *row = src + (size_t)j * N;
+    if (f == 0)
+        return __ldg(row + i);
+    if (f == 1) {
+        const int il = i == 0 ? 0 : i - 1, ir = i == N - 1 ? N - 1 : i + 1;
+        const T d = __ldg(row + ir) - __ldg(row + il);
+        return (ir - il == 2) ? T(0.5) * d : d;
+    }
+    const int jl = j == 0 ? 0 : j - 1, jr = j == N - 1 ? N - 1 : j + 1;
+    const T d = __ldg(src + (size_t)jr * N + i) - __ldg(src + (size_t)jl * N + i);
+    return (jr - jl == 2) ? T(0.5) * d : d;
+}
+
+// ------------------------------------------------------------------ row_fwd
+template <typename T>
+__global__ void __launch_bounds__(512) k_row_fwd16(SolveArgs<T> a)
+{
+    using C = typename Cx<T>::C;
+    using C2 = typename Cx<T>::C2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *sbuf = reinterpret_cast<C *>(smem_raw);
+    const int N = a.N, Q = N >> 4, SP = N + Q;
+    const FwdItem item = a.fwd_items[blockIdx.x];
+    const FwdSlab sl = a.slabs[item.slab];
+    const int rows = sl.rows, r0 = 2 * item.row_pair;
+    const int ja = sl.m * r0 + sl.py, jb = sl.m * (r0 + 1) + sl.py;
+    const int t = threadIdx.x;
+    const bool active = t < 2 * Q;
+    const int b = active ? t / Q : 0, j = active ? t - b * Q : 0;
+    Fft16Plan pl;
+    pl.init(N, a.logN);
+    C2 *out = reinterpret_cast<C2 *>(a.fwd + sl.off);  // pairs of rows (r0, r0+1)
+    for (int f = 0; f < 3; ++f) {
+        C v[16];
+        if (active) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int c = j + u * Q;
+                C z = hmk<C>(T(0), T(0));
+                if (c < rows) {
+                    const int i = sl.m * c + sl.px;
+                    z = hmk<C>(field16(a, sl.level, ja, i, f), field16(a, sl.level, jb, i, f));
+                    if (b)
+                        z = hmul(z, a.tw[c]);
+                }
+                v[u] = z;
+            }
+        }
+        fft16_block<C, false>(v, sbuf, b, j, active, pl, a.tw);
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+                sbuf[b * SP + pad16(j + u * Q)] = v[u];
+        }
+        __syncthreads();
+        // X_a = (Z + conj Z~)/2, X_b = (Z - conj Z~)/(2i); Z~ = bin -kx, same parity half
+        for (int kx = t; kx <= N; kx += blockDim.x) {
+            const int bb = kx & 1, k = kx >> 1;
+            const int km = (N - bb - k) & (N - 1);
+            const C Z = sbuf[bb * SP + pad16(k)];
+            const C Zm = sbuf[bb * SP + pad16(km)];
+            const T sx = Z.x + Zm.x, sy = Z.y - Zm.y;  // Z + conj(Zm)
+            const T dx = Z.x - Zm.x, dy = Z.y + Zm.y;  // Z - conj(Zm)
+            C2 o;
+            o.x = T(0.5) * sx;
+            o.y = T(0.5) * sy;
+            o.z = T(0.5) * dy;
+            o.w = T(-0.5) * dx;
+            out[(((size_t)f * (N + 1) + kx) * rows + r0) >> 1] = o;
+        }
+    }
+}
+
+// --------------------------------------------------------------------- col
+template <typename T>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256) k_col16(SolveArgs<T> a)
+{
+    using C = typename Cx<T>::C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = a.N, Q = N >> 4, P = 2 * N;
+    C *sbuf = reinterpret_cast<C *>(smem_raw);   // N + N/16: exchanges of this half
+    C *fold = sbuf + N + Q;                      // 2N: the odd half's results (x, y), in the even CTA
+    cg::cluster_group cluster = cg::this_cluster();
+    const int b = (int)cluster.block_rank();     // parity half
+    const int kx = blockIdx.x >> 1;
+    const ColOutput o = a.outs[blockIdx.y];
+    const int t = threadIdx.x;
+    const bool active = t < Q;
+    const int j = active ? t : 0;
+    Fft16Plan pl;
+    pl.init(N, a.logN);
+    C ax[16], ay[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        ax[u] = hmk<C>(T(0), T(0));
+        ay[u] = hmk<C>(T(0), T(0));
+    }
+    for (int in = 0; in < o.in_count; ++in) {
+        const ColInput ci = a.ins[o.in_begin + in];
+        const FwdSlab sl = a.slabs[ci.slab];
+        const int rows = sl.rows;
+        for (int f = 0; f < 3; ++f) {
+            const C *__restrict__ col = a.fwd + sl.off + ((size_t)f * (N + 1) + kx) * rows;
+            C v[16];
+            if (active) {
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int n = j + u * Q;
+                    C x = hmk<C>(T(0), T(0));
+                    if (n < rows) {
+                        x = col[n];
+                        if (b)
+                            x = hmul(x, a.tw[n]);
+                    }
+                    v[u] = x;
+                }
+            }
+            fft16_block<C, false>(v, sbuf, 0, j, active, pl, a.tw);
+            if (active) {
+                if (ci.kind == SPEC_QUARTER) {
+                    // K0x, K0y imaginary (stored Im), the rest real; mirror sign in ky
+                    // (bins above N read the quarter at P - ky): + K0x Kxx Kyy, - Kxy K0y Kyx
+                    const T *sx = reinterpret_cast<const T *>(a.spec) + ci.spec_off +
+                                  ((size_t)f * (N + 1) + kx) * (N + 1);
+                    const T *sy = reinterpret_cast<const T *>(a.spec) + ci.spec_off +
+                                  ((size_t)(3 + f) * (N + 1) + kx) * (N + 1);
+                    const T mx = (f == 2) ? T(-1) : T(1);
+                    const T my = (f == 2) ? T(1) : T(-1);
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const int ky = 2 * (j + u * Q) + b;
+                        const bool hi = ky > N;
+                        const int q = hi ? P - ky : ky;
+                        const T rx = __ldg(sx + q) * (hi ? mx : T(1));
+                        const T ry = __ldg(sy + q) * (hi ? my : T(1));
+                        C tx = hmk<C>(rx * v[u].x, rx * v[u].y), ty = hmk<C>(ry * v[u].x, ry * v[u].y);
+                        if (f == 0) {
+                            tx = hmk<C>(-tx.y, tx.x);
+                            ty = hmk<C>(-ty.y, ty.x);
+                        }
+                        ax[u] = hadd(ax[u], tx);
+                        ay[u] = hadd(ay[u], ty);
+                    }
+                } else {
+                    const C *sx = reinterpret_cast<const C *>(a.spec) + ci.spec_off + ((size_t)f * (N + 1) + kx) * P;
+                    const C *sy = reinterpret_cast<const C *>(a.spec) + ci.spec_off + ((size_t)(3 + f) * (N + 1) + kx) * P;
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const int ky = 2 * (j + u * Q) + b;
+                        ax[u] = hadd(ax[u], hmul(sx[ky], v[u]));
+                        ay[u] = hadd(ay[u], hmul(sy[ky], v[u]));
+                    }
+                }
+            }
+        }
+    }
+    // inverse column transforms; y[n] = even[n] + W_P^{-n} odd[n]
+    fft16_block<C, true>(ax, sbuf, 0, j, active, pl, a.tw);
+    fft16_block<C, true>(ay, sbuf, 0, j, active, pl, a.tw);
+    if (b == 1 && active) {
+        C *dst = cluster.map_shared_rank(fold, 0);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int n = j + u * Q;
+            const C w = a.tw[n];
+            dst[n] = hmulc(ax[u], w);
+            dst[N + n] = hmulc(ay[u], w);
+        }
+    }
+    cluster.sync();
+    if (b == 0 && active) {
+        C *dst = a.bwd + o.off;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int n = j + u * Q;
+            if (n < o.rows) {
+                dst[(size_t)kx * o.rows + n] = hadd(ax[u], fold[n]);
+                dst[((size_t)(N + 1) + kx) * o.rows + n] = hadd(ay[u], fold[N + n]);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ row_inv
+template <typename T>
+__global__ void __launch_bounds__(512) k_row_inv16(SolveArgs<T> a)
+{
+    using C = typename Cx<T>::C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = a.N, Q = N >> 4, SP = N + Q, P = 2 * N;
+    C *sbuf = reinterpret_cast<C *>(smem_raw);             // 2 * SP
+    T *O = reinterpret_cast<T *>(sbuf + 2 * SP);            // [comp][row 0..1][N]
+    const int tl = blockIdx.y;
+    const int j0 = 2 * blockIdx.x, j1 = j0 + 1;
+    const int t = threadIdx.x;
+    const bool active = t < 2 * Q;
+    const int b = active ? t / Q : 0, j = active ? t - b * Q : 0;
+    Fft16Plan pl;
+    pl.init(N, a.logN);
+    for (int i = t; i < 4 * N; i += blockDim.x)
+        O[i] = T(0);
+    for (int c = a.contrib_begin[tl]; c < a.contrib_begin[tl + 1]; ++c) {
+        const RowContrib rc = a.contribs[c];
+        const ColOutput oa = a.outs[rc.out_base + (j0 % rc.m) * rc.m];
+        const ColOutput ob = a.outs[rc.out_base + (j1 % rc.m) * rc.m];
+        const int ra = j0 / rc.m, rb = j1 / rc.m;
+        const int nout = N / rc.m;
+        for (int comp = 0; comp < 2; ++comp) {
+            const C *ya = a.bwd + oa.off + (size_t)comp * (N + 1) * oa.rows + ra;
+            const C *yb = a.bwd + ob.off + (size_t)comp * (N + 1) * ob.rows + rb;
+            C v[16];
+            if (active) {
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int kx = 2 * (j + u * Q) + b;
+                    C z;
+                    if (kx <= N) {
+                        const C A = ya[(size_t)kx * oa.rows], B = yb[(size_t)kx * ob.rows];
+                        z = hmk<C>(A.x - B.y, A.y + B.x);  // A + iB
+                    } else {
+                        const int k2 = P - kx;
+                        const C A = ya[(size_t)k2 * oa.rows], B = yb[(size_t)k2 * ob.rows];
+                        z = hmk<C>(A.x + B.y, B.x - A.y);  // conj(A) + i conj(B)
+                    }
+                    v[u] = z;
+                }
+            }
+            fft16_block<C, true>(v, sbuf, b, j, active, pl, a.tw);
+            __syncthreads();
+            if (active && b == 1) {
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int n = j + u * Q;
+                    sbuf[pad16(n)] = hmulc(v[u], a.tw[n]);
+                }
+            }
+            __syncthreads();
+            if (active && b == 0) {
+                T *Oc = O + comp * 2 * N;
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int n = j + u * Q;
+                    if (n < nout) {
+                        const C y = hadd(v[u], sbuf[pad16(n)]);
+                        const int i = rc.m * n + rc.px;
+                        Oc[i] += y.x;
+                        Oc[N + i] += y.y;
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    T *fx = a.fx[tl], *fy = a.fy[tl];
+    for (int i = t; i < N; i += blockDim.x) {
+        const bool ca = covered16(a, tl, j0, i), cb = covered16(a, tl, j1, i);
+        fx[(size_t)j0 * N + i] = ca ? T(0) : O[i];
+        fx[(size_t)j1 * N + i] = cb ? T(0) : O[N + i];
+        fy[(size_t)j0 * N + i] = ca ? T(0) : O[2 * N + i];
+        fy[(size_t)j1 * N + i] = cb ? T(0) : O[3 * N + i];
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+static inline int warps_up(int n) { return ((n < 32 ? 32 : n) + 31) / 32 * 32; }
+
+template <typename T>
+static size_t smem_fwd16(int N) { return 2 * (size_t)(N + N / 16) * sizeof(typename Cx<T>::C); }
+template <typename T>
+static size_t smem_col16(int N) { return (size_t)(N + N / 16 + 2 * N) * sizeof(typename Cx<T>::C); }
+template <typename T>
+static size_t smem_inv16(int N) { return 2 * (size_t)(N + N / 16) * sizeof(typename Cx<T>::C) + 4 * (size_t)N * sizeof(T); }
+
+template <typename T>
+cudaError_t solve16_init()
+{
+    const int maxN = sizeof(T) == 8 ? 2048 : 4096;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_row_fwd16<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_fwd16<T>(maxN))) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_col16<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_col16<T>(maxN))) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(k_row_inv16<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_inv16<T>(maxN));
+}
+
+template <typename T>
+cudaError_t launch_row_fwd16(const SolveArgs<T> &a, int n_items, cudaStream_t st)
+{
+    k_row_fwd16<T><<<n_items, warps_up(2 * (a.N / 16)), smem_fwd16<T>(a.N), st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_col16(const SolveArgs<T> &a, int n_outputs, cudaStream_t st)
+{
+    dim3 grid(2 * (a.N + 1), n_outputs);
+    k_col16<T><<<grid, warps_up(a.N / 16), smem_col16<T>(a.N), st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_row_inv16(const SolveArgs<T> &a, cudaStream_t st)
+{
+    dim3 grid(a.N / 2, a.L);
+    k_row_inv16<T><<<grid, warps_up(2 * (a.N / 16)), smem_inv16<T>(a.N), st>>>(a);
+    return cudaGetLastError();
+}
+
+template cudaError_t solve16_init<float>();
+template cudaError_t solve16_init<double>();
+template cudaError_t launch_row_fwd16<float>(const SolveArgs<float> &, int, cudaStream_t);
+template cudaError_t launch_row_fwd16<double>(const SolveArgs<double> &, int, cudaStream_t);
+template cudaError_t launch_col16<float>(const SolveArgs<float> &, int, cudaStream_t);
+template cudaError_t launch_col16<double>(const SolveArgs<double> &, int, cudaStream_t);
+template cudaError_t launch_row_inv16<float>(const SolveArgs<float> &, cudaStream_t);
+template cudaError_t launch_row_inv16<double>(const SolveArgs<double> &, cudaStream_t);
+
+}  // namespace sgf

@@ -26,10 +26,10 @@ def _random_sigma(nest, seed, lo=0.2, hi=1.5):
 
 
 NESTS = [
-    (8, 1, [(0, 0)]),
     (16, 1, [(0, 0)]),
-    (8, 2, [(0, 0), (4, 0)]),            # child on the parent's edges
-    (8, 3, [(0, 0), (2, 2), (0, 4)]),    # m = 4 with two-row phase slabs
+    (32, 1, [(0, 0)]),
+    (16, 2, [(0, 0), (8, 0)]),           # child on the parent's edges
+    (16, 4, [(0, 0), (4, 4), (0, 8), (8, 2)]),  # m = 8 with two-row phase slabs
     (16, 2, [(0, 0), (3, 5)]),
     (16, 3, [(0, 0), (8, 0), (1, 7)]),
     (32, 3, [(0, 0), (5, 9), (4, 12)]),
