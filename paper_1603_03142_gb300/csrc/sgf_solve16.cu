@@ -28,7 +28,7 @@ namespace sgf {
 
 template <typename T> struct Cx;
 template <> struct Cx<float> { using C = float2; using C2 = float4; };
-template <> struct Cx<double> { using C = double2; using C2 = double4; };
+template <> struct Cx<double> { using C = double2; using C2 = double4_32a; };
 
 template <typename T>
 __device__ __forceinline__ bool covered16(const SolveArgs<T> &a, int s, int j, int i)
