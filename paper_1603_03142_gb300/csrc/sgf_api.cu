@@ -60,7 +60,8 @@ struct Spectra {
     int device = 0;
     void *dev = nullptr;   // all sets, one allocation
     size_t bytes = 0;
-    void *tw = nullptr;    // W_P^k in the solve precision
+    void *tw = nullptr;    // W_N^k (k < N) in the solve precision
+    double wp1[2] = {1.0, 0.0};  // W_P^1
     double plan_ms = 0.0;
 };
 
@@ -184,7 +185,7 @@ void build_lists(sgf_plan *p)
         g.ay = ay;
         const int idx = (int)p->sets.size();
         p->sets.push_back(g);
-        set_bytes.push_back(cas == 1 ? 6 * (size_t)(N + 1) * (N + 1) * T : 6 * (size_t)(N + 1) * P * Cb);
+        set_bytes.push_back(cas == 1 ? 6 * (size_t)(N + 1) * quarter_stride(N) * T : 6 * (size_t)(N + 1) * P * Cb);
         set_index[k] = idx;
         return idx;
     };
@@ -289,7 +290,7 @@ void build_lists(sgf_plan *p)
     for (const auto &o : p->outs)
         for (int k = 0; k < o.in_count; ++k) {
             const ColInput &ci = p->ins[o.in_begin + k];
-            ab += ci.kind == SPEC_QUARTER ? 6 * (size_t)(N + 1) * (N + 1) * T : 6 * (size_t)(N + 1) * P * Cb;
+            ab += ci.kind == SPEC_QUARTER ? 6 * (size_t)(N + 1) * (N + 1) * T : 6 * (size_t)(N + 1) * P * Cb;  // padding not counted
         }
     if (L > 1)
         ab += (size_t)(L - 1) * (2 * (size_t)N * N * T + (size_t)N * N / 4 * 4 * T);  // restriction
@@ -301,7 +302,7 @@ size_t spectra_total(const sgf_plan *p)
 {
     size_t off = 0;
     for (const auto &g : p->sets) {
-        const size_t b = g.kind == SPEC_QUARTER ? 6 * (size_t)(p->N + 1) * (p->N + 1) * p->esize
+        const size_t b = g.kind == SPEC_QUARTER ? 6 * (size_t)(p->N + 1) * quarter_stride(p->N) * p->esize
                                                 : 6 * (size_t)(p->N + 1) * 2 * p->N * 2 * p->esize;
         off += (b + 255) & ~(size_t)255;
     }
@@ -398,15 +399,18 @@ sgf_status build_spectra(sgf_plan *p)
     std::vector<double> re, im;
     twiddles(P, re, im);
     std::vector<double2> tw64(P);
-    std::vector<C> twT(P);
-    for (int k = 0; k < P; ++k) {
+    std::vector<C> twT(N);  // W_N^k = W_P^{2k}
+    for (int k = 0; k < P; ++k)
         tw64[k] = make_double2(re[k], im[k]);
-        twT[k].x = (T)re[k];
-        twT[k].y = (T)im[k];
+    for (int k = 0; k < N; ++k) {
+        twT[k].x = (T)re[2 * k];
+        twT[k].y = (T)im[2 * k];
     }
-    if ((e = cudaMalloc(&sp->tw, P * sizeof(C))) != cudaSuccess)
+    sp->wp1[0] = re[1];
+    sp->wp1[1] = im[1];
+    if ((e = cudaMalloc(&sp->tw, N * sizeof(C))) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc(twiddles)");
-    if ((e = cudaMemcpy(sp->tw, twT.data(), P * sizeof(C), cudaMemcpyHostToDevice)) != cudaSuccess)
+    if ((e = cudaMemcpy(sp->tw, twT.data(), N * sizeof(C), cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpy(twiddles)");
     sp->bytes = spectra_total(p);
     if ((e = cudaMalloc(&sp->dev, sp->bytes)) != cudaSuccess)
@@ -489,7 +493,9 @@ sgf_status solve_impl(sgf_plan *p, const void *const *sigma, void *const *fx, vo
     a.fwd = static_cast<typename SolveArgs<T>::C *>(p->d_fwd);
     a.bwd = static_cast<typename SolveArgs<T>::C *>(p->d_bwd);
     a.spec = p->spec->dev;
-    a.tw = static_cast<const typename SolveArgs<T>::C *>(p->spec->tw);
+    a.twN = static_cast<const typename SolveArgs<T>::C *>(p->spec->tw);
+    a.wp1.x = (T)p->spec->wp1[0];
+    a.wp1.y = (T)p->spec->wp1[1];
     a.slabs = p->d_slabs;
     a.fwd_items = p->d_items;
     a.outs = p->d_outs;

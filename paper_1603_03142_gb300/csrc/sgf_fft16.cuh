@@ -14,7 +14,8 @@
 // bin by bin, inverse-transformed and stored, with the shared-memory traffic
 // limited to the exchanges between stages.
 //
-// Twiddles: W_{R Ns}^{r k} from the table W_P^k = exp(-2 pi i k / P), P = 2N.
+// Twiddles: W_{R Ns}^{r k} from a table of W_N^i = exp(-2 pi i i / N), i < N,
+// which the kernels keep in shared memory.
 // The in-register 16- and 8-point DFTs use the exact constants cos(pi/8),
 // sin(pi/8) and sqrt(1/2).
 #pragma once
@@ -141,7 +142,7 @@ SGF_HD void stage_small_one(C *v, int N, int Ns, int j, const C *tw)
     const int jq = j + Q * (N / 16);
     const int k = jq & (Ns - 1);
     if (Ns > 1) {
-        const int step = k * ((2 * N) / (R * Ns));
+        const int step = k * (N / (R * Ns));  // W_{R Ns}^{r k} = W_N^{r k N/(R Ns)}
 #pragma unroll
         for (int r = 1; r < R; ++r) {
             const C w = tw[r * step];
@@ -192,7 +193,7 @@ SGF_HD void fft16_stage_compute(C *v, const Fft16Plan &pl, int st, int Ns, int j
     if (R == 16) {
         const int k = j & (Ns - 1);
         if (Ns > 1) {
-            const int step = k * (N / (8 * Ns));  // W_{16 Ns}^{r k} = W_P^{r k 2N/(16 Ns)}
+            const int step = k * (N / (16 * Ns));  // W_{16 Ns}^{r k} = W_N^{r k N/(16 Ns)}
 #pragma unroll
             for (int r = 1; r < 16; ++r) {
                 const C w = tw[r * step];
@@ -218,12 +219,14 @@ SGF_HD int fft16_out_index(int j, int Ns, int r)
 
 #ifdef __CUDACC__
 // Block-wide transform of the slot held in v.  sbuf: B * pad16(N) complex in
-// shared memory (sequence s at s * (N + N/16)).  Every thread of the block must
-// call this (active == false: a thread without a slot still takes part in the
-// barriers).  Starts with a barrier, so sbuf may still be in use on entry.
+// shared memory (sequence s at s * (N + N/16)); twN: W_N^i table (shared
+// memory).  Every thread of the block must call this (active == false: a
+// thread without a slot still takes part in the barriers).  sbuf is first
+// written after a barrier, so it may still be in use on entry; the last stage
+// reads sbuf without a closing barrier, so callers synchronise before reusing it.
 template <typename C, bool INV>
 __device__ __forceinline__ void fft16_block(C *v, C *sbuf, int s, int j, bool active, const Fft16Plan &pl,
-                                            const C *__restrict__ tw)
+                                            const C *tw)
 {
     const int N = pl.N, SP = N + (N >> 4), Q = N >> 4;
     C *seq = sbuf + (size_t)s * SP;

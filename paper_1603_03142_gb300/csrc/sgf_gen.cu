@@ -170,10 +170,11 @@ __global__ void k_gen_cols(int N, int logN, const double2 *__restrict__ half, co
     const double scale = 1.0 / ((double)P * (double)P);
     if (kind == SPEC_QUARTER) {
         // K0x and K0y (tables 0, 3) are odd in one axis: purely imaginary
-        T *dst = reinterpret_cast<T *>(spec) + spec_off + ((size_t)t * (N + 1) + kx) * (N + 1);
+        const int QS = quarter_stride(N);
+        T *dst = reinterpret_cast<T *>(spec) + spec_off + ((size_t)t * (N + 1) + kx) * QS;
         const bool imag = (t == 0 || t == 3);
-        for (int q = tid; q <= N; q += nt) {
-            const double2 X = W[(q & 1) * N + (q >> 1)];
+        for (int q = tid; q < QS; q += nt) {
+            const double2 X = q <= N ? W[(q & 1) * N + (q >> 1)] : make_double2(0.0, 0.0);
             dst[q] = (T)((imag ? X.y : X.x) * scale);
         }
     } else {

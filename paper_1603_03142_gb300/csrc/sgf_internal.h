@@ -25,7 +25,8 @@
 //   y-force from sigma, dx, dy), already divided by P^2.
 //   SPEC_QUARTER (Case 1): the tables are even or odd in each axis, so each
 //     spectrum is purely real or purely imaginary and mirror-symmetric in ky:
-//     stored as reals [table][kx 0..N][ky 0..N].
+//     stored as reals [table][kx 0..N][ky 0..N], rows padded to N + 4 reals
+//     (16-byte multiples, for asynchronous copies).
 //   SPEC_FULL (Cases 2, 3): complex [table][kx 0..N][ky 0..P).
 #pragma once
 #include <cstddef>
@@ -38,6 +39,9 @@ namespace sgf {
 constexpr int kMaxLevels = 8;
 
 enum SpecKind : int { SPEC_QUARTER = 0, SPEC_FULL = 1 };
+
+// Row stride (reals) of a quarter-stored spectrum.
+inline __host__ __device__ int quarter_stride(int N) { return N + 4; }
 
 struct FwdSlab {
     int level;        // source level
@@ -85,7 +89,8 @@ struct SolveArgs {
     C *fwd;                     // forward slabs
     C *bwd;                     // column outputs
     const void *spec;           // kernel spectra (T reals / C complex)
-    const C *tw;                // W_P^k, k = 0..P-1 (P = 2N), exp(-2 pi i k / P)
+    const C *twN;               // W_N^k, k = 0..N-1, exp(-2 pi i k / N)
+    C wp1;                      // W_P^1 = exp(-2 pi i / P), P = 2N
     const FwdSlab *slabs;
     const FwdItem *fwd_items;
     const ColOutput *outs;

@@ -5,6 +5,9 @@
 // halves" (even bins: x[n]; odd bins: x[n] W_P^n).  One slot of 16 values per
 // thread and per half; a CTA holds both halves of one row pair (row passes),
 // or one half of one column (column pass, two CTAs per column in a cluster).
+// Operands are staged in shared memory with asynchronous copies (cp.async,
+// 16-byte chunks) so that the loads of the next operand overlap the transform
+// of the current one; the twiddle table W_N lives in shared memory.
 //
 //  k_row_fwd16 : sigma rows -> (sigma, dx, dy) with the slope rule and the
 //                covered-cell mask, Case-2 phase gather, two rows per complex
@@ -30,6 +33,31 @@ template <typename T> struct Cx;
 template <> struct Cx<float> { using C = float2; using C2 = float4; };
 template <> struct Cx<double> { using C = double2; using C2 = double4_32a; };
 
+// ------------------------------------------------------------ async copies
+__device__ __forceinline__ void cp16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory"); }
+
+// Whole block: copy `bytes` (a multiple of 16, both ends 16-byte aligned).
+__device__ __forceinline__ void cp_block(void *smem, const void *gmem, size_t bytes)
+{
+    for (size_t o = (size_t)threadIdx.x * 16; o < bytes; o += (size_t)blockDim.x * 16)
+        cp16(static_cast<char *>(smem) + o, static_cast<const char *>(gmem) + o);
+}
+
+// W_P^n for n < N from the shared W_N table (W_P^{2q} = W_N^q) and W_P^1.
+template <typename C>
+__device__ __forceinline__ C twist(const C *twN, C wp1, int n)
+{
+    const C w = twN[n >> 1];
+    return (n & 1) ? hmul(w, wp1) : w;
+}
+
 template <typename T>
 __device__ __forceinline__ bool covered16(const SolveArgs<T> &a, int s, int j, int i)
 {
@@ -40,45 +68,38 @@ __device__ __forceinline__ bool covered16(const SolveArgs<T> &a, int s, int j, i
     return i >= ox && i < ox + half && j >= oy && j < oy + half;
 }
 
-// (sigma, x difference, y difference)[f] of level s at cell (j, i); 0 on covered cells.
-template <typename T>
-__device__ __forceinline__ T field16(const SolveArgs<T> &a, int s, int j, int i, int f)
-{
-    if (covered16(a, s, j, i))
-        return T(0);
-    const int N = a.N;
-    const T *__restrict__ src = a.src[s];
-    const T *row = src + (size_t)j * N;
-    if (f == 0)
-        return __ldg(row + i);
-    if (f == 1) {
-        const int il = i == 0 ? 0 : i - 1, ir = i == N - 1 ? N - 1 : i + 1;
-        const T d = __ldg(row + ir) - __ldg(row + il);
-        return (ir - il == 2) ? T(0.5) * d : d;
-    }
-    const int jl = j == 0 ? 0 : j - 1, jr = j == N - 1 ? N - 1 : j + 1;
-    const T d = __ldg(src + (size_t)jr * N + i) - __ldg(src + (size_t)jl * N + i);
-    return (jr - jl == 2) ? T(0.5) * d : d;
-}
-
 // ------------------------------------------------------------------ row_fwd
+// Shared memory: twN[N] | sigma rows[6][N] | sbuf[2 (N + N/16)].
 template <typename T>
 __global__ void __launch_bounds__(512) k_row_fwd16(SolveArgs<T> a)
 {
     using C = typename Cx<T>::C;
     using C2 = typename Cx<T>::C2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *sbuf = reinterpret_cast<C *>(smem_raw);
     const int N = a.N, Q = N >> 4, SP = N + Q;
+    C *twN = reinterpret_cast<C *>(smem_raw);
+    T *srow = reinterpret_cast<T *>(twN + N);  // logical rows ja-1, ja, ja+1, jb-1, jb, jb+1 (clamped)
+    C *sbuf = reinterpret_cast<C *>(srow + 6 * N);
     const FwdItem item = a.fwd_items[blockIdx.x];
     const FwdSlab sl = a.slabs[item.slab];
     const int rows = sl.rows, r0 = 2 * item.row_pair;
     const int ja = sl.m * r0 + sl.py, jb = sl.m * (r0 + 1) + sl.py;
+    const T *src = a.src[sl.level];
+    cp_block(twN, a.twN, (size_t)N * sizeof(C));
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const int jr = min(max((q < 3 ? ja : jb) + (q % 3) - 1, 0), N - 1);
+        cp_block(srow + q * N, src + (size_t)jr * N, (size_t)N * sizeof(T));
+    }
+    cp_commit();
     const int t = threadIdx.x;
     const bool active = t < 2 * Q;
     const int b = active ? t / Q : 0, j = active ? t - b * Q : 0;
     Fft16Plan pl;
     pl.init(N, a.logN);
+    const C wp1 = a.wp1;
+    cp_wait<0>();
+    __syncthreads();
     C2 *out = reinterpret_cast<C2 *>(a.fwd + sl.off);  // pairs of rows (r0, r0+1)
     for (int f = 0; f < 3; ++f) {
         C v[16];
@@ -86,17 +107,36 @@ __global__ void __launch_bounds__(512) k_row_fwd16(SolveArgs<T> a)
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
                 const int c = j + u * Q;
-                C z = hmk<C>(T(0), T(0));
+                T fv[2] = {T(0), T(0)};
                 if (c < rows) {
                     const int i = sl.m * c + sl.px;
-                    z = hmk<C>(field16(a, sl.level, ja, i, f), field16(a, sl.level, jb, i, f));
-                    if (b)
-                        z = hmul(z, a.tw[c]);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int jj = h ? jb : ja;
+                        const T *r = srow + (3 * h + 1) * N;  // row jj; rows jj -+ 1 sit beside it
+                        if (covered16(a, sl.level, jj, i))
+                            continue;
+                        if (f == 0) {
+                            fv[h] = r[i];
+                        } else if (f == 1) {
+                            const int il = i == 0 ? 0 : i - 1, ir = i == N - 1 ? N - 1 : i + 1;
+                            const T d = r[ir] - r[il];
+                            fv[h] = (ir - il == 2) ? T(0.5) * d : d;
+                        } else {
+                            const T *rl = jj == 0 ? r : r - N;
+                            const T *rr = jj == N - 1 ? r : r + N;
+                            const T d = rr[i] - rl[i];
+                            fv[h] = (jj == 0 || jj == N - 1) ? d : T(0.5) * d;
+                        }
+                    }
                 }
+                C z = hmk<C>(fv[0], fv[1]);
+                if (b)
+                    z = hmul(z, twist(twN, wp1, c));
                 v[u] = z;
             }
         }
-        fft16_block<C, false>(v, sbuf, b, j, active, pl, a.tw);
+        fft16_block<C, false>(v, sbuf, b, j, active, pl, twN);
         __syncthreads();
         if (active) {
 #pragma unroll
@@ -110,110 +150,140 @@ __global__ void __launch_bounds__(512) k_row_fwd16(SolveArgs<T> a)
             const int km = (N - bb - k) & (N - 1);
             const C Z = sbuf[bb * SP + pad16(k)];
             const C Zm = sbuf[bb * SP + pad16(km)];
-            const T sx = Z.x + Zm.x, sy = Z.y - Zm.y;  // Z + conj(Zm)
-            const T dx = Z.x - Zm.x, dy = Z.y + Zm.y;  // Z - conj(Zm)
             C2 o;
-            o.x = T(0.5) * sx;
-            o.y = T(0.5) * sy;
-            o.z = T(0.5) * dy;
-            o.w = T(-0.5) * dx;
+            o.x = T(0.5) * (Z.x + Zm.x);
+            o.y = T(0.5) * (Z.y - Zm.y);
+            o.z = T(0.5) * (Z.y + Zm.y);
+            o.w = T(-0.5) * (Z.x - Zm.x);
             out[(((size_t)f * (N + 1) + kx) * rows + r0) >> 1] = o;
         }
     }
 }
 
 // --------------------------------------------------------------------- col
+// Shared memory: twN[N] | sbuf[N + N/16] | stage[2] { column[N] (complex), spectra rows 2 x QS (real) }.
+// The odd half's results are folded into the even CTA's stage area at the end.
 template <typename T>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256) k_col16(SolveArgs<T> a)
 {
     using C = typename Cx<T>::C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = a.N, Q = N >> 4, P = 2 * N;
-    C *sbuf = reinterpret_cast<C *>(smem_raw);   // N + N/16: exchanges of this half
-    C *fold = sbuf + N + Q;                      // 2N: the odd half's results (x, y), in the even CTA
+    const int N = a.N, Q = N >> 4, P = 2 * N, QS = N + 4;
+    C *twN = reinterpret_cast<C *>(smem_raw);
+    C *sbuf = twN + N;
+    unsigned char *stage_base = reinterpret_cast<unsigned char *>(sbuf + N + Q);
+    const size_t stage_bytes = (size_t)N * sizeof(C) + 2 * (size_t)QS * sizeof(T);
     cg::cluster_group cluster = cg::this_cluster();
-    const int b = (int)cluster.block_rank();     // parity half
+    const int b = (int)cluster.block_rank();  // parity half
     const int kx = blockIdx.x >> 1;
     const ColOutput o = a.outs[blockIdx.y];
     const int t = threadIdx.x;
     const bool active = t < Q;
     const int j = active ? t : 0;
+    const int nitems = 3 * o.in_count;
     Fft16Plan pl;
     pl.init(N, a.logN);
+    const C wp1 = a.wp1;
+
+    auto issue = [&](int k) {
+        unsigned char *st = stage_base + (size_t)(k & 1) * stage_bytes;
+        const ColInput ci = a.ins[o.in_begin + k / 3];
+        const FwdSlab sl = a.slabs[ci.slab];
+        const int f = k % 3;
+        cp_block(st, a.fwd + sl.off + ((size_t)f * (N + 1) + kx) * sl.rows, (size_t)sl.rows * sizeof(C));
+        if (ci.kind == SPEC_QUARTER) {
+            const T *sp = reinterpret_cast<const T *>(a.spec) + ci.spec_off;
+            T *dst = reinterpret_cast<T *>(st + (size_t)N * sizeof(C));
+            cp_block(dst, sp + ((size_t)f * (N + 1) + kx) * QS, (size_t)QS * sizeof(T));
+            cp_block(dst + QS, sp + ((size_t)(3 + f) * (N + 1) + kx) * QS, (size_t)QS * sizeof(T));
+        }
+    };
+    cp_block(twN, a.twN, (size_t)N * sizeof(C));
+    issue(0);
+    cp_commit();
+    if (nitems > 1)
+        issue(1);
+    cp_commit();
+
     C ax[16], ay[16];
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
         ax[u] = hmk<C>(T(0), T(0));
         ay[u] = hmk<C>(T(0), T(0));
     }
-    for (int in = 0; in < o.in_count; ++in) {
-        const ColInput ci = a.ins[o.in_begin + in];
-        const FwdSlab sl = a.slabs[ci.slab];
-        const int rows = sl.rows;
-        for (int f = 0; f < 3; ++f) {
-            const C *__restrict__ col = a.fwd + sl.off + ((size_t)f * (N + 1) + kx) * rows;
-            C v[16];
-            if (active) {
+    for (int k = 0; k < nitems; ++k) {
+        cp_wait<1>();
+        __syncthreads();
+        const unsigned char *st = stage_base + (size_t)(k & 1) * stage_bytes;
+        const C *col = reinterpret_cast<const C *>(st);
+        const T *spx = reinterpret_cast<const T *>(st + (size_t)N * sizeof(C));
+        const ColInput ci = a.ins[o.in_begin + k / 3];
+        const int rows = a.slabs[ci.slab].rows;
+        const int f = k % 3;
+        C v[16];
+        if (active) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int n = j + u * Q;
+                C x = hmk<C>(T(0), T(0));
+                if (n < rows) {
+                    x = col[n];
+                    if (b)
+                        x = hmul(x, twist(twN, wp1, n));
+                }
+                v[u] = x;
+            }
+        }
+        fft16_block<C, false>(v, sbuf, 0, j, active, pl, twN);
+        if (active) {
+            if (ci.kind == SPEC_QUARTER) {
+                // K0x, K0y imaginary (stored Im), the rest real; bins above N read the
+                // quarter at P - ky with the table's ky parity: + K0x Kxx Kyy, - Kxy K0y Kyx
+                const T mx = (f == 2) ? T(-1) : T(1);
+                const T my = (f == 2) ? T(1) : T(-1);
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {
-                    const int n = j + u * Q;
-                    C x = hmk<C>(T(0), T(0));
-                    if (n < rows) {
-                        x = col[n];
-                        if (b)
-                            x = hmul(x, a.tw[n]);
+                    const int ky = 2 * (j + u * Q) + b;
+                    const bool hi = ky > N;
+                    const int q = hi ? P - ky : ky;
+                    const T rx = spx[q] * (hi ? mx : T(1));
+                    const T ry = spx[QS + q] * (hi ? my : T(1));
+                    C tx = hmk<C>(rx * v[u].x, rx * v[u].y), ty = hmk<C>(ry * v[u].x, ry * v[u].y);
+                    if (f == 0) {
+                        tx = hmk<C>(-tx.y, tx.x);
+                        ty = hmk<C>(-ty.y, ty.x);
                     }
-                    v[u] = x;
+                    ax[u] = hadd(ax[u], tx);
+                    ay[u] = hadd(ay[u], ty);
                 }
-            }
-            fft16_block<C, false>(v, sbuf, 0, j, active, pl, a.tw);
-            if (active) {
-                if (ci.kind == SPEC_QUARTER) {
-                    // K0x, K0y imaginary (stored Im), the rest real; mirror sign in ky
-                    // (bins above N read the quarter at P - ky): + K0x Kxx Kyy, - Kxy K0y Kyx
-                    const T *sx = reinterpret_cast<const T *>(a.spec) + ci.spec_off +
-                                  ((size_t)f * (N + 1) + kx) * (N + 1);
-                    const T *sy = reinterpret_cast<const T *>(a.spec) + ci.spec_off +
-                                  ((size_t)(3 + f) * (N + 1) + kx) * (N + 1);
-                    const T mx = (f == 2) ? T(-1) : T(1);
-                    const T my = (f == 2) ? T(1) : T(-1);
+            } else {
+                const C *sx = reinterpret_cast<const C *>(a.spec) + ci.spec_off + ((size_t)f * (N + 1) + kx) * P;
+                const C *sy = reinterpret_cast<const C *>(a.spec) + ci.spec_off + ((size_t)(3 + f) * (N + 1) + kx) * P;
 #pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        const int ky = 2 * (j + u * Q) + b;
-                        const bool hi = ky > N;
-                        const int q = hi ? P - ky : ky;
-                        const T rx = __ldg(sx + q) * (hi ? mx : T(1));
-                        const T ry = __ldg(sy + q) * (hi ? my : T(1));
-                        C tx = hmk<C>(rx * v[u].x, rx * v[u].y), ty = hmk<C>(ry * v[u].x, ry * v[u].y);
-                        if (f == 0) {
-                            tx = hmk<C>(-tx.y, tx.x);
-                            ty = hmk<C>(-ty.y, ty.x);
-                        }
-                        ax[u] = hadd(ax[u], tx);
-                        ay[u] = hadd(ay[u], ty);
-                    }
-                } else {
-                    const C *sx = reinterpret_cast<const C *>(a.spec) + ci.spec_off + ((size_t)f * (N + 1) + kx) * P;
-                    const C *sy = reinterpret_cast<const C *>(a.spec) + ci.spec_off + ((size_t)(3 + f) * (N + 1) + kx) * P;
-#pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        const int ky = 2 * (j + u * Q) + b;
-                        ax[u] = hadd(ax[u], hmul(sx[ky], v[u]));
-                        ay[u] = hadd(ay[u], hmul(sy[ky], v[u]));
-                    }
+                for (int u = 0; u < 16; ++u) {
+                    const int ky = 2 * (j + u * Q) + b;
+                    ax[u] = hadd(ax[u], hmul(__ldg(sx + ky), v[u]));
+                    ay[u] = hadd(ay[u], hmul(__ldg(sy + ky), v[u]));
                 }
             }
         }
+        __syncthreads();  // stage (k & 1) consumed by every thread
+        if (k + 2 < nitems)
+            issue(k + 2);
+        cp_commit();
     }
+    cp_wait<0>();
     // inverse column transforms; y[n] = even[n] + W_P^{-n} odd[n]
-    fft16_block<C, true>(ax, sbuf, 0, j, active, pl, a.tw);
-    fft16_block<C, true>(ay, sbuf, 0, j, active, pl, a.tw);
+    fft16_block<C, true>(ax, sbuf, 0, j, active, pl, twN);
+    fft16_block<C, true>(ay, sbuf, 0, j, active, pl, twN);
+    C *fold = reinterpret_cast<C *>(stage_base);  // 2N complex in the even CTA
+    cluster.sync();  // the even CTA's stage area is free
     if (b == 1 && active) {
         C *dst = cluster.map_shared_rank(fold, 0);
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
             const int n = j + u * Q;
-            const C w = a.tw[n];
+            const C w = twist(twN, wp1, n);
             dst[n] = hmulc(ax[u], w);
             dst[N + n] = hmulc(ay[u], w);
         }
@@ -233,14 +303,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256) k_col16(SolveAr
 }
 
 // ------------------------------------------------------------------ row_inv
+// Shared memory: twN[N] | sbuf[2 (N + N/16)] | O[2 comps][2 rows][N] (real).
 template <typename T>
 __global__ void __launch_bounds__(512) k_row_inv16(SolveArgs<T> a)
 {
     using C = typename Cx<T>::C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = a.N, Q = N >> 4, SP = N + Q, P = 2 * N;
-    C *sbuf = reinterpret_cast<C *>(smem_raw);             // 2 * SP
-    T *O = reinterpret_cast<T *>(sbuf + 2 * SP);            // [comp][row 0..1][N]
+    C *twN = reinterpret_cast<C *>(smem_raw);
+    C *sbuf = twN + N;
+    T *O = reinterpret_cast<T *>(sbuf + 2 * SP);
     const int tl = blockIdx.y;
     const int j0 = 2 * blockIdx.x, j1 = j0 + 1;
     const int t = threadIdx.x;
@@ -248,41 +320,41 @@ __global__ void __launch_bounds__(512) k_row_inv16(SolveArgs<T> a)
     const int b = active ? t / Q : 0, j = active ? t - b * Q : 0;
     Fft16Plan pl;
     pl.init(N, a.logN);
+    const C wp1 = a.wp1;
+    cp_block(twN, a.twN, (size_t)N * sizeof(C));
+    cp_commit();
     for (int i = t; i < 4 * N; i += blockDim.x)
         O[i] = T(0);
+    cp_wait<0>();
+    __syncthreads();
     for (int c = a.contrib_begin[tl]; c < a.contrib_begin[tl + 1]; ++c) {
         const RowContrib rc = a.contribs[c];
         const ColOutput oa = a.outs[rc.out_base + (j0 % rc.m) * rc.m];
         const ColOutput ob = a.outs[rc.out_base + (j1 % rc.m) * rc.m];
         const int ra = j0 / rc.m, rb = j1 / rc.m;
         const int nout = N / rc.m;
+        const C *ya0 = a.bwd + oa.off + ra, *yb0 = a.bwd + ob.off + rb;
         for (int comp = 0; comp < 2; ++comp) {
-            const C *ya = a.bwd + oa.off + (size_t)comp * (N + 1) * oa.rows + ra;
-            const C *yb = a.bwd + ob.off + (size_t)comp * (N + 1) * ob.rows + rb;
+            const C *ya = ya0 + (size_t)comp * (N + 1) * oa.rows;
+            const C *yb = yb0 + (size_t)comp * (N + 1) * ob.rows;
             C v[16];
             if (active) {
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {
                     const int kx = 2 * (j + u * Q) + b;
-                    C z;
-                    if (kx <= N) {
-                        const C A = ya[(size_t)kx * oa.rows], B = yb[(size_t)kx * ob.rows];
-                        z = hmk<C>(A.x - B.y, A.y + B.x);  // A + iB
-                    } else {
-                        const int k2 = P - kx;
-                        const C A = ya[(size_t)k2 * oa.rows], B = yb[(size_t)k2 * ob.rows];
-                        z = hmk<C>(A.x + B.y, B.x - A.y);  // conj(A) + i conj(B)
-                    }
-                    v[u] = z;
+                    const int k2 = kx <= N ? kx : P - kx;
+                    const C A = ya[(size_t)k2 * oa.rows], B = yb[(size_t)k2 * ob.rows];
+                    // Z = A + iB, from the stored half (kx <= N) or its conjugate mirror
+                    v[u] = kx <= N ? hmk<C>(A.x - B.y, A.y + B.x) : hmk<C>(A.x + B.y, B.x - A.y);
                 }
             }
-            fft16_block<C, true>(v, sbuf, b, j, active, pl, a.tw);
+            fft16_block<C, true>(v, sbuf, b, j, active, pl, twN);
             __syncthreads();
             if (active && b == 1) {
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {
                     const int n = j + u * Q;
-                    sbuf[pad16(n)] = hmulc(v[u], a.tw[n]);
+                    sbuf[pad16(n)] = hmulc(v[u], twist(twN, wp1, n));
                 }
             }
             __syncthreads();
@@ -316,11 +388,24 @@ __global__ void __launch_bounds__(512) k_row_inv16(SolveArgs<T> a)
 static inline int warps_up(int n) { return ((n < 32 ? 32 : n) + 31) / 32 * 32; }
 
 template <typename T>
-static size_t smem_fwd16(int N) { return 2 * (size_t)(N + N / 16) * sizeof(typename Cx<T>::C); }
+static size_t smem_fwd16(int N)
+{
+    using C = typename Cx<T>::C;
+    return (size_t)N * sizeof(C) + 6 * (size_t)N * sizeof(T) + 2 * (size_t)(N + N / 16) * sizeof(C);
+}
 template <typename T>
-static size_t smem_col16(int N) { return (size_t)(N + N / 16 + 2 * N) * sizeof(typename Cx<T>::C); }
+static size_t smem_col16(int N)
+{
+    using C = typename Cx<T>::C;
+    const size_t stage = (size_t)N * sizeof(C) + 2 * (size_t)(N + 4) * sizeof(T);
+    return (size_t)N * sizeof(C) + (size_t)(N + N / 16) * sizeof(C) + 2 * stage;  // 2 stages >= 2N complex (fold)
+}
 template <typename T>
-static size_t smem_inv16(int N) { return 2 * (size_t)(N + N / 16) * sizeof(typename Cx<T>::C) + 4 * (size_t)N * sizeof(T); }
+static size_t smem_inv16(int N)
+{
+    using C = typename Cx<T>::C;
+    return (size_t)N * sizeof(C) + 2 * (size_t)(N + N / 16) * sizeof(C) + 4 * (size_t)N * sizeof(T);
+}
 
 template <typename T>
 cudaError_t solve16_init()
