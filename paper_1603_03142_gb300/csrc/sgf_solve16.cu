@@ -161,6 +161,13 @@ __global__ void __launch_bounds__(512) k_row_fwd16(SolveArgs<T> a)
 }
 
 // --------------------------------------------------------------------- col
+// Exchange buffer of the column pass, rounded up to a 16-byte multiple.
+template <typename C>
+__host__ __device__ __forceinline__ size_t col_sbuf_bytes(int N)
+{
+    return (((size_t)(N + N / 16) * sizeof(C)) + 15) & ~(size_t)15;
+}
+
 // Shared memory: twN[N] | sbuf[N + N/16] | stage[2] { column[N] (complex), spectra rows 2 x QS (real) }.
 // The odd half's results are folded into the even CTA's stage area at the end.
 template <typename T>
@@ -171,7 +178,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256) k_col16(SolveAr
     const int N = a.N, Q = N >> 4, P = 2 * N, QS = N + 4;
     C *twN = reinterpret_cast<C *>(smem_raw);
     C *sbuf = twN + N;
-    unsigned char *stage_base = reinterpret_cast<unsigned char *>(sbuf + N + Q);
+    // the stages take 16-byte asynchronous copies: start them on a 16-byte boundary
+    unsigned char *stage_base = reinterpret_cast<unsigned char *>(sbuf) + col_sbuf_bytes<C>(N);
     const size_t stage_bytes = (size_t)N * sizeof(C) + 2 * (size_t)QS * sizeof(T);
     cg::cluster_group cluster = cg::this_cluster();
     const int b = (int)cluster.block_rank();  // parity half
@@ -398,7 +406,7 @@ static size_t smem_col16(int N)
 {
     using C = typename Cx<T>::C;
     const size_t stage = (size_t)N * sizeof(C) + 2 * (size_t)(N + 4) * sizeof(T);
-    return (size_t)N * sizeof(C) + (size_t)(N + N / 16) * sizeof(C) + 2 * stage;  // 2 stages >= 2N complex (fold)
+    return (size_t)N * sizeof(C) + col_sbuf_bytes<C>(N) + 2 * stage;  // 2 stages >= 2N complex (fold)
 }
 template <typename T>
 static size_t smem_inv16(int N)
