@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "../../include/sgf.h"
+#include "sgf_fft16.cuh"
 #include "sgf_internal.h"
 
 using namespace sgf;
@@ -60,8 +61,8 @@ struct Spectra {
     int device = 0;
     void *dev = nullptr;   // all sets, one allocation
     size_t bytes = 0;
-    void *tw = nullptr;    // W_N^k (k < N) in the solve precision
-    double wp1[2] = {1.0, 0.0};  // W_P^1
+    void *tw = nullptr;    // twiddle area (TwLayout) in the solve precision
+    int tw_entries = 0;
     double plan_ms = 0.0;
 };
 
@@ -399,18 +400,34 @@ sgf_status build_spectra(sgf_plan *p)
     std::vector<double> re, im;
     twiddles(P, re, im);
     std::vector<double2> tw64(P);
-    std::vector<C> twT(N);  // W_N^k = W_P^{2k}
     for (int k = 0; k < P; ++k)
         tw64[k] = make_double2(re[k], im[k]);
-    for (int k = 0; k < N; ++k) {
-        twT[k].x = (T)re[2 * k];
-        twT[k].y = (T)im[2 * k];
+    // solve twiddle area: stage tables W_{R Ns}^{r k} = W_P^{2N r k / (R Ns)}, then W_P^j, then W_32^u
+    Fft16Plan pl;
+    pl.init(N, p->logN);
+    const TwLayout tl = tw_layout(pl.twlen, N);
+    std::vector<C> twT(tl.entries);
+    for (auto &c : twT)
+        c.x = c.y = (T)0;
+    auto put = [&](int at, long idx) {
+        idx %= P;
+        twT[at].x = (T)re[idx];
+        twT[at].y = (T)im[idx];
+    };
+    for (int st = 1, Ns = pl.radix(0); st < pl.nst; Ns *= pl.radix(st), ++st) {
+        const int R = pl.radix(st);
+        for (int r = 1; r < R; ++r)
+            for (int k = 0; k < Ns; ++k)
+                put(pl.twoff[st] + (r - 1) * Ns + k, (long)2 * N / (R * Ns) * r * k);
     }
-    sp->wp1[0] = re[1];
-    sp->wp1[1] = im[1];
-    if ((e = cudaMalloc(&sp->tw, N * sizeof(C))) != cudaSuccess)
+    for (int jj = 0; jj < N / 16; ++jj)
+        put(tl.base + jj, jj);
+    for (int u = 0; u < 16; ++u)
+        put(tl.w32 + u, (long)u * (P / 32));
+    sp->tw_entries = tl.entries;
+    if ((e = cudaMalloc(&sp->tw, tl.entries * sizeof(C))) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc(twiddles)");
-    if ((e = cudaMemcpy(sp->tw, twT.data(), N * sizeof(C), cudaMemcpyHostToDevice)) != cudaSuccess)
+    if ((e = cudaMemcpy(sp->tw, twT.data(), tl.entries * sizeof(C), cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpy(twiddles)");
     sp->bytes = spectra_total(p);
     if ((e = cudaMalloc(&sp->dev, sp->bytes)) != cudaSuccess)
@@ -493,9 +510,8 @@ sgf_status solve_impl(sgf_plan *p, const void *const *sigma, void *const *fx, vo
     a.fwd = static_cast<typename SolveArgs<T>::C *>(p->d_fwd);
     a.bwd = static_cast<typename SolveArgs<T>::C *>(p->d_bwd);
     a.spec = p->spec->dev;
-    a.twN = static_cast<const typename SolveArgs<T>::C *>(p->spec->tw);
-    a.wp1.x = (T)p->spec->wp1[0];
-    a.wp1.y = (T)p->spec->wp1[1];
+    a.tw = static_cast<const typename SolveArgs<T>::C *>(p->spec->tw);
+    a.tw_entries = p->spec->tw_entries;
     a.slabs = p->d_slabs;
     a.fwd_items = p->d_items;
     a.outs = p->d_outs;

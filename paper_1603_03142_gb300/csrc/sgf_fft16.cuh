@@ -14,8 +14,11 @@
 // bin by bin, inverse-transformed and stored, with the shared-memory traffic
 // limited to the exchanges between stages.
 //
-// Twiddles: W_{R Ns}^{r k} from a table of W_N^i = exp(-2 pi i i / N), i < N,
-// which the kernels keep in shared memory.
+// Twiddles: every stage after the first multiplies by W_{R Ns}^{r k}
+// (k = the butterfly's index modulo Ns).  They come from per-stage tables laid
+// out [r-1][k] (r = 1..R-1, k < Ns), so the threads of a warp, whose k are
+// consecutive, read consecutive words (no bank conflicts); the tables are
+// built on the host in extended precision and kept in shared memory.
 // The in-register 16- and 8-point DFTs use the exact constants cos(pi/8),
 // sin(pi/8) and sqrt(1/2).
 #pragma once
@@ -142,10 +145,9 @@ SGF_HD void stage_small_one(C *v, int N, int Ns, int j, const C *tw)
     const int jq = j + Q * (N / 16);
     const int k = jq & (Ns - 1);
     if (Ns > 1) {
-        const int step = k * (N / (R * Ns));  // W_{R Ns}^{r k} = W_N^{r k N/(R Ns)}
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-            const C w = tw[r * step];
+            const C w = tw[(r - 1) * Ns + k];  // this stage's table
             v[Q + r * S] = INV ? hmulc(v[Q + r * S], w) : hmul(v[Q + r * S], w);
         }
     }
@@ -171,9 +173,12 @@ SGF_HD void stage_small(C *v, int N, int Ns, int j, const C *tw)
 
 SGF_HD int pad16(int i) { return i + (i >> 4); }
 
-// Stage bookkeeping shared by the device engine and the host test emulator.
+// Stage bookkeeping shared by the device engine, the host table builder and
+// the host test emulator.  twoff[st]: offset of stage st's twiddle table.
 struct Fft16Plan {
     int N, logN, nst, S16, rlast;
+    int twoff[5];
+    int twlen;  // entries of all stage tables together
     SGF_HD void init(int n, int logn)
     {
         N = n;
@@ -181,6 +186,16 @@ struct Fft16Plan {
         S16 = logn >> 2;
         rlast = 1 << (logn & 3);
         nst = S16 + (rlast > 1 ? 1 : 0);
+        int off = 0, Ns = 1;
+        for (int st = 0; st < 5; ++st) {
+            twoff[st] = off;
+            if (st < nst) {
+                if (st > 0)
+                    off += (radix(st) - 1) * Ns;
+                Ns *= radix(st);
+            }
+        }
+        twlen = off;
     }
     SGF_HD int radix(int st) const { return st < S16 ? 16 : rlast; }
 };
@@ -190,23 +205,23 @@ template <typename C, bool INV>
 SGF_HD void fft16_stage_compute(C *v, const Fft16Plan &pl, int st, int Ns, int j, const C *tw)
 {
     const int R = pl.radix(st), N = pl.N;
+    const C *tws = tw + pl.twoff[st];  // [r-1][k], k < Ns
     if (R == 16) {
         const int k = j & (Ns - 1);
         if (Ns > 1) {
-            const int step = k * (N / (16 * Ns));  // W_{16 Ns}^{r k} = W_N^{r k N/(16 Ns)}
 #pragma unroll
             for (int r = 1; r < 16; ++r) {
-                const C w = tw[r * step];
+                const C w = tws[(r - 1) * Ns + k];
                 v[r] = INV ? hmulc(v[r], w) : hmul(v[r], w);
             }
         }
         hdft16<C, INV>(v);
     } else if (R == 8) {
-        stage_small<C, INV, 8>(v, N, Ns, j, tw);
+        stage_small<C, INV, 8>(v, N, Ns, j, tws);
     } else if (R == 4) {
-        stage_small<C, INV, 4>(v, N, Ns, j, tw);
+        stage_small<C, INV, 4>(v, N, Ns, j, tws);
     } else {
-        stage_small<C, INV, 2>(v, N, Ns, j, tw);
+        stage_small<C, INV, 2>(v, N, Ns, j, tws);
     }
 }
 
@@ -218,17 +233,17 @@ SGF_HD int fft16_out_index(int j, int Ns, int r)
 }
 
 #ifdef __CUDACC__
-// Block-wide transform of the slot held in v.  sbuf: B * pad16(N) complex in
-// shared memory (sequence s at s * (N + N/16)); twN: W_N^i table (shared
-// memory).  Every thread of the block must call this (active == false: a
-// thread without a slot still takes part in the barriers).  sbuf is first
+// Block-wide transform of the slot held in v.  sbuf: shared memory, sequence s
+// at s * SP (SP >= N + N/16); tw: the stage twiddle tables (shared memory).
+// Every thread of the block must call this (active == false: a thread without
+// a slot still takes part in the barriers).  sbuf is first
 // written after a barrier, so it may still be in use on entry; the last stage
 // reads sbuf without a closing barrier, so callers synchronise before reusing it.
 template <typename C, bool INV>
-__device__ __forceinline__ void fft16_block(C *v, C *sbuf, int s, int j, bool active, const Fft16Plan &pl,
-                                            const C *tw)
+__device__ __forceinline__ void fft16_block(C *v, C *sbuf, int s, int SP, int j, bool active,
+                                            const Fft16Plan &pl, const C *tw)
 {
-    const int N = pl.N, SP = N + (N >> 4), Q = N >> 4;
+    const int N = pl.N, Q = N >> 4;
     C *seq = sbuf + (size_t)s * SP;
     int Ns = 1;
     for (int st = 0; st < pl.nst; ++st) {

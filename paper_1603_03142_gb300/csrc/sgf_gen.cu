@@ -170,12 +170,13 @@ __global__ void k_gen_cols(int N, int logN, const double2 *__restrict__ half, co
     const double scale = 1.0 / ((double)P * (double)P);
     if (kind == SPEC_QUARTER) {
         // K0x and K0y (tables 0, 3) are odd in one axis: purely imaginary
-        const int QS = quarter_stride(N);
+        const int QS = quarter_stride(N), HQ = quarter_half(N);
         T *dst = reinterpret_cast<T *>(spec) + spec_off + ((size_t)t * (N + 1) + kx) * QS;
         const bool imag = (t == 0 || t == 3);
-        for (int q = tid; q < QS; q += nt) {
+        for (int idx = tid; idx < QS; idx += nt) {
+            const int q = idx < HQ ? 2 * idx : 2 * (idx - HQ) + 1;  // even half, then odd half
             const double2 X = q <= N ? W[(q & 1) * N + (q >> 1)] : make_double2(0.0, 0.0);
-            dst[q] = (T)((imag ? X.y : X.x) * scale);
+            dst[idx] = (T)((imag ? X.y : X.x) * scale);
         }
     } else {
         C *dst = reinterpret_cast<C *>(spec) + spec_off + ((size_t)t * (N + 1) + kx) * P;

@@ -25,8 +25,8 @@
 //   y-force from sigma, dx, dy), already divided by P^2.
 //   SPEC_QUARTER (Case 1): the tables are even or odd in each axis, so each
 //     spectrum is purely real or purely imaginary and mirror-symmetric in ky:
-//     stored as reals [table][kx 0..N][ky 0..N], rows padded to N + 4 reals
-//     (16-byte multiples, for asynchronous copies).
+//     stored as reals [table][kx 0..N][row of ky 0..N split by parity, see
+//     quarter_half], so each parity half of a column reads one contiguous half.
 //   SPEC_FULL (Cases 2, 3): complex [table][kx 0..N][ky 0..P).
 #pragma once
 #include <cstddef>
@@ -40,8 +40,11 @@ constexpr int kMaxLevels = 8;
 
 enum SpecKind : int { SPEC_QUARTER = 0, SPEC_FULL = 1 };
 
-// Row stride (reals) of a quarter-stored spectrum.
-inline __host__ __device__ int quarter_stride(int N) { return N + 4; }
+// A quarter-stored spectrum row holds ky = 0..N split by parity: even ky
+// (0, 2, .., N) at [0, N/2 + 1), odd ky (1, 3, .., N-1) at [N/2 + 4, N + 4);
+// each half is padded to N/2 + 4 reals so it starts on a 16-byte boundary.
+inline __host__ __device__ int quarter_half(int N) { return N / 2 + 4; }
+inline __host__ __device__ int quarter_stride(int N) { return 2 * quarter_half(N); }
 
 struct FwdSlab {
     int level;        // source level
@@ -89,8 +92,8 @@ struct SolveArgs {
     C *fwd;                     // forward slabs
     C *bwd;                     // column outputs
     const void *spec;           // kernel spectra (T reals / C complex)
-    const C *twN;               // W_N^k, k = 0..N-1, exp(-2 pi i k / N)
-    C wp1;                      // W_P^1 = exp(-2 pi i / P), P = 2N
+    const C *tw;                // twiddle area (tw_layout), copied to shared memory by every CTA
+    int tw_entries;             // its length in complex entries (even)
     const FwdSlab *slabs;
     const FwdItem *fwd_items;
     const ColOutput *outs;
@@ -98,6 +101,24 @@ struct SolveArgs {
     const RowContrib *contribs;
     int contrib_begin[kMaxLevels + 1];
 };
+
+// Twiddle area of a solve (complex entries, precision of the solve):
+//   [0, twlen)            radix-16 engine stage tables (Fft16Plan::twoff), W_{R Ns}^{r k}
+//   [twlen, twlen + N/16) W_P^j, j < N/16 (P = 2N)
+//   [.. + 16)             W_32^u, u < 16
+// so that the twist W_P^n of element n = j + u N/16 is W_P^j W_32^u.
+struct TwLayout {
+    int twlen, base, w32, entries;
+};
+inline __host__ __device__ TwLayout tw_layout(int twlen, int N)
+{
+    TwLayout t;
+    t.twlen = twlen;
+    t.base = twlen;
+    t.w32 = twlen + N / 16;
+    t.entries = (t.w32 + 16 + 1) & ~1;
+    return t;
+}
 
 // Kernel-table generation for one spectra set (FP64).
 struct GenSet {

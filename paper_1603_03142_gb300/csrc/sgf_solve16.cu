@@ -50,12 +50,18 @@ __device__ __forceinline__ void cp_block(void *smem, const void *gmem, size_t by
         cp16(static_cast<char *>(smem) + o, static_cast<const char *>(gmem) + o);
 }
 
-// W_P^n for n < N from the shared W_N table (W_P^{2q} = W_N^q) and W_P^1.
+// W_P^n for n = j + u N/16: W_P^j W_32^u from the shared twiddle area.
 template <typename C>
-__device__ __forceinline__ C twist(const C *twN, C wp1, int n)
+__device__ __forceinline__ C twist(const C *tw, const TwLayout &tl, int j, int u)
 {
-    const C w = twN[n >> 1];
-    return (n & 1) ? hmul(w, wp1) : w;
+    return hmul(tw[tl.base + j], tw[tl.w32 + u]);
+}
+
+// Twiddle area bytes in shared memory (a 16-byte multiple).
+template <typename C>
+__host__ __device__ __forceinline__ size_t tw_bytes(int entries)
+{
+    return (((size_t)entries * sizeof(C)) + 15) & ~(size_t)15;
 }
 
 template <typename T>
@@ -69,23 +75,24 @@ __device__ __forceinline__ bool covered16(const SolveArgs<T> &a, int s, int j, i
 }
 
 // ------------------------------------------------------------------ row_fwd
-// Shared memory: twN[N] | sigma rows[6][N] | sbuf[2 (N + N/16)].
+// Shared memory: twiddle area | sigma rows[6][N] | sbuf[2 SP], SP = N + N/16 + 2
+// (the pad keeps the two parity halves on different banks in the unpack).
 template <typename T>
 __global__ void __launch_bounds__(512) k_row_fwd16(SolveArgs<T> a)
 {
     using C = typename Cx<T>::C;
     using C2 = typename Cx<T>::C2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = a.N, Q = N >> 4, SP = N + Q;
-    C *twN = reinterpret_cast<C *>(smem_raw);
-    T *srow = reinterpret_cast<T *>(twN + N);  // logical rows ja-1, ja, ja+1, jb-1, jb, jb+1 (clamped)
+    const int N = a.N, Q = N >> 4, SP = N + Q + 2;
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    T *srow = reinterpret_cast<T *>(smem_raw + tw_bytes<C>(a.tw_entries));  // rows ja-1, ja, ja+1, jb-1, jb, jb+1
     C *sbuf = reinterpret_cast<C *>(srow + 6 * N);
     const FwdItem item = a.fwd_items[blockIdx.x];
     const FwdSlab sl = a.slabs[item.slab];
     const int rows = sl.rows, r0 = 2 * item.row_pair;
     const int ja = sl.m * r0 + sl.py, jb = sl.m * (r0 + 1) + sl.py;
     const T *src = a.src[sl.level];
-    cp_block(twN, a.twN, (size_t)N * sizeof(C));
+    cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
         const int jr = min(max((q < 3 ? ja : jb) + (q % 3) - 1, 0), N - 1);
@@ -97,7 +104,7 @@ __global__ void __launch_bounds__(512) k_row_fwd16(SolveArgs<T> a)
     const int b = active ? t / Q : 0, j = active ? t - b * Q : 0;
     Fft16Plan pl;
     pl.init(N, a.logN);
-    const C wp1 = a.wp1;
+    const TwLayout tl = tw_layout(pl.twlen, N);
     cp_wait<0>();
     __syncthreads();
     C2 *out = reinterpret_cast<C2 *>(a.fwd + sl.off);  // pairs of rows (r0, r0+1)
@@ -132,11 +139,11 @@ __global__ void __launch_bounds__(512) k_row_fwd16(SolveArgs<T> a)
                 }
                 C z = hmk<C>(fv[0], fv[1]);
                 if (b)
-                    z = hmul(z, twist(twN, wp1, c));
+                    z = hmul(z, twist(tw, tl, j, u));
                 v[u] = z;
             }
         }
-        fft16_block<C, false>(v, sbuf, b, j, active, pl, twN);
+        fft16_block<C, false>(v, sbuf, b, SP, j, active, pl, tw);
         __syncthreads();
         if (active) {
 #pragma unroll
@@ -168,19 +175,20 @@ __host__ __device__ __forceinline__ size_t col_sbuf_bytes(int N)
     return (((size_t)(N + N / 16) * sizeof(C)) + 15) & ~(size_t)15;
 }
 
-// Shared memory: twN[N] | sbuf[N + N/16] | stage[2] { column[N] (complex), spectra rows 2 x QS (real) }.
+// Shared memory: twiddle area | sbuf[N + N/16] | stage[2] { column[N] (complex),
+// this parity's half of the two spectrum rows, 2 x (N/2 + 4) reals }.
 // The odd half's results are folded into the even CTA's stage area at the end.
 template <typename T>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256) k_col16(SolveArgs<T> a)
 {
     using C = typename Cx<T>::C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = a.N, Q = N >> 4, P = 2 * N, QS = N + 4;
-    C *twN = reinterpret_cast<C *>(smem_raw);
-    C *sbuf = twN + N;
+    const int N = a.N, Q = N >> 4, QS = quarter_stride(N), HQ = quarter_half(N);
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *sbuf = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
     // the stages take 16-byte asynchronous copies: start them on a 16-byte boundary
     unsigned char *stage_base = reinterpret_cast<unsigned char *>(sbuf) + col_sbuf_bytes<C>(N);
-    const size_t stage_bytes = (size_t)N * sizeof(C) + 2 * (size_t)QS * sizeof(T);
+    const size_t stage_bytes = (size_t)N * sizeof(C) + 2 * (size_t)HQ * sizeof(T);
     cg::cluster_group cluster = cg::this_cluster();
     const int b = (int)cluster.block_rank();  // parity half
     const int kx = blockIdx.x >> 1;
@@ -191,7 +199,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256) k_col16(SolveAr
     const int nitems = 3 * o.in_count;
     Fft16Plan pl;
     pl.init(N, a.logN);
-    const C wp1 = a.wp1;
+    const TwLayout tl = tw_layout(pl.twlen, N);
+    const int P = 2 * N;
 
     auto issue = [&](int k) {
         unsigned char *st = stage_base + (size_t)(k & 1) * stage_bytes;
@@ -202,11 +211,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256) k_col16(SolveAr
         if (ci.kind == SPEC_QUARTER) {
             const T *sp = reinterpret_cast<const T *>(a.spec) + ci.spec_off;
             T *dst = reinterpret_cast<T *>(st + (size_t)N * sizeof(C));
-            cp_block(dst, sp + ((size_t)f * (N + 1) + kx) * QS, (size_t)QS * sizeof(T));
-            cp_block(dst + QS, sp + ((size_t)(3 + f) * (N + 1) + kx) * QS, (size_t)QS * sizeof(T));
+            cp_block(dst, sp + ((size_t)f * (N + 1) + kx) * QS + b * HQ, (size_t)HQ * sizeof(T));
+            cp_block(dst + HQ, sp + ((size_t)(3 + f) * (N + 1) + kx) * QS + b * HQ, (size_t)HQ * sizeof(T));
         }
     };
-    cp_block(twN, a.twN, (size_t)N * sizeof(C));
+    cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
     issue(0);
     cp_commit();
     if (nitems > 1)
@@ -237,25 +246,27 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256) k_col16(SolveAr
                 if (n < rows) {
                     x = col[n];
                     if (b)
-                        x = hmul(x, twist(twN, wp1, n));
+                        x = hmul(x, twist(tw, tl, j, u));
                 }
                 v[u] = x;
             }
         }
-        fft16_block<C, false>(v, sbuf, 0, j, active, pl, twN);
+        fft16_block<C, false>(v, sbuf, 0, N + Q, j, active, pl, tw);
         if (active) {
             if (ci.kind == SPEC_QUARTER) {
                 // K0x, K0y imaginary (stored Im), the rest real; bins above N read the
-                // quarter at P - ky with the table's ky parity: + K0x Kxx Kyy, - Kxy K0y Kyx
+                // quarter at P - ky with the table's ky parity: + K0x Kxx Kyy, - Kxy K0y Kyx.
+                // Bin ky = 2k' + b sits at k' of this parity's half row; its mirror
+                // P - ky sits at N - k' - b.
                 const T mx = (f == 2) ? T(-1) : T(1);
                 const T my = (f == 2) ? T(1) : T(-1);
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {
-                    const int ky = 2 * (j + u * Q) + b;
-                    const bool hi = ky > N;
-                    const int q = hi ? P - ky : ky;
+                    const int kp = j + u * Q;
+                    const bool hi = 2 * kp + b > N;
+                    const int q = hi ? N - kp - b : kp;
                     const T rx = spx[q] * (hi ? mx : T(1));
-                    const T ry = spx[QS + q] * (hi ? my : T(1));
+                    const T ry = spx[HQ + q] * (hi ? my : T(1));
                     C tx = hmk<C>(rx * v[u].x, rx * v[u].y), ty = hmk<C>(ry * v[u].x, ry * v[u].y);
                     if (f == 0) {
                         tx = hmk<C>(-tx.y, tx.x);
@@ -282,8 +293,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256) k_col16(SolveAr
     }
     cp_wait<0>();
     // inverse column transforms; y[n] = even[n] + W_P^{-n} odd[n]
-    fft16_block<C, true>(ax, sbuf, 0, j, active, pl, twN);
-    fft16_block<C, true>(ay, sbuf, 0, j, active, pl, twN);
+    fft16_block<C, true>(ax, sbuf, 0, N + Q, j, active, pl, tw);
+    fft16_block<C, true>(ay, sbuf, 0, N + Q, j, active, pl, tw);
     C *fold = reinterpret_cast<C *>(stage_base);  // 2N complex in the even CTA
     cluster.sync();  // the even CTA's stage area is free
     if (b == 1 && active) {
@@ -291,7 +302,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256) k_col16(SolveAr
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
             const int n = j + u * Q;
-            const C w = twist(twN, wp1, n);
+            const C w = twist(tw, tl, j, u);
             dst[n] = hmulc(ax[u], w);
             dst[N + n] = hmulc(ay[u], w);
         }
@@ -311,15 +322,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256) k_col16(SolveAr
 }
 
 // ------------------------------------------------------------------ row_inv
-// Shared memory: twN[N] | sbuf[2 (N + N/16)] | O[2 comps][2 rows][N] (real).
+// Shared memory: twiddle area | sbuf[2 SP], SP = N + N/16 + 2 | O[2 comps][2 rows][N] (real).
 template <typename T>
 __global__ void __launch_bounds__(512) k_row_inv16(SolveArgs<T> a)
 {
     using C = typename Cx<T>::C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = a.N, Q = N >> 4, SP = N + Q, P = 2 * N;
-    C *twN = reinterpret_cast<C *>(smem_raw);
-    C *sbuf = twN + N;
+    const int N = a.N, Q = N >> 4, SP = N + Q + 2, P = 2 * N;
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *sbuf = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
     T *O = reinterpret_cast<T *>(sbuf + 2 * SP);
     const int tl = blockIdx.y;
     const int j0 = 2 * blockIdx.x, j1 = j0 + 1;
@@ -328,8 +339,8 @@ __global__ void __launch_bounds__(512) k_row_inv16(SolveArgs<T> a)
     const int b = active ? t / Q : 0, j = active ? t - b * Q : 0;
     Fft16Plan pl;
     pl.init(N, a.logN);
-    const C wp1 = a.wp1;
-    cp_block(twN, a.twN, (size_t)N * sizeof(C));
+    const TwLayout twl = tw_layout(pl.twlen, N);
+    cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
     cp_commit();
     for (int i = t; i < 4 * N; i += blockDim.x)
         O[i] = T(0);
@@ -356,13 +367,13 @@ __global__ void __launch_bounds__(512) k_row_inv16(SolveArgs<T> a)
                     v[u] = kx <= N ? hmk<C>(A.x - B.y, A.y + B.x) : hmk<C>(A.x + B.y, B.x - A.y);
                 }
             }
-            fft16_block<C, true>(v, sbuf, b, j, active, pl, twN);
+            fft16_block<C, true>(v, sbuf, b, SP, j, active, pl, tw);
             __syncthreads();
             if (active && b == 1) {
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {
                     const int n = j + u * Q;
-                    sbuf[pad16(n)] = hmulc(v[u], twist(twN, wp1, n));
+                    sbuf[pad16(n)] = hmulc(v[u], twist(tw, twl, j, u));
                 }
             }
             __syncthreads();
@@ -396,23 +407,33 @@ __global__ void __launch_bounds__(512) k_row_inv16(SolveArgs<T> a)
 static inline int warps_up(int n) { return ((n < 32 ? 32 : n) + 31) / 32 * 32; }
 
 template <typename T>
+static int tw_entries_for(int N)
+{
+    int logN = 0;
+    while ((1 << logN) < N)
+        ++logN;
+    Fft16Plan pl;
+    pl.init(N, logN);
+    return tw_layout(pl.twlen, N).entries;
+}
+template <typename T>
 static size_t smem_fwd16(int N)
 {
     using C = typename Cx<T>::C;
-    return (size_t)N * sizeof(C) + 6 * (size_t)N * sizeof(T) + 2 * (size_t)(N + N / 16) * sizeof(C);
+    return tw_bytes<C>(tw_entries_for<T>(N)) + 6 * (size_t)N * sizeof(T) + 2 * (size_t)(N + N / 16 + 2) * sizeof(C);
 }
 template <typename T>
 static size_t smem_col16(int N)
 {
     using C = typename Cx<T>::C;
-    const size_t stage = (size_t)N * sizeof(C) + 2 * (size_t)(N + 4) * sizeof(T);
-    return (size_t)N * sizeof(C) + col_sbuf_bytes<C>(N) + 2 * stage;  // 2 stages >= 2N complex (fold)
+    const size_t stage = (size_t)N * sizeof(C) + 2 * (size_t)quarter_half(N) * sizeof(T);
+    return tw_bytes<C>(tw_entries_for<T>(N)) + col_sbuf_bytes<C>(N) + 2 * stage;  // 2 stages >= 2N complex (fold)
 }
 template <typename T>
 static size_t smem_inv16(int N)
 {
     using C = typename Cx<T>::C;
-    return (size_t)N * sizeof(C) + 2 * (size_t)(N + N / 16) * sizeof(C) + 4 * (size_t)N * sizeof(T);
+    return tw_bytes<C>(tw_entries_for<T>(N)) + 2 * (size_t)(N + N / 16 + 2) * sizeof(C) + 4 * (size_t)N * sizeof(T);
 }
 
 template <typename T>
