@@ -105,6 +105,27 @@ typedef struct {
  * SGF_ENOMEM, SGF_ECUDA. */
 sgf_status sgf_plan_create(const sgf_nest_desc *desc, sgf_precision precision, sgf_plan **out);
 
+/* Plan options (bit flags) for sgf_plan_create_ex. */
+#define SGF_PLAN_ZERO_RIM 0x1u
+/* SGF_PLAN_ZERO_RIM (one level only): the caller guarantees that sigma is 0 on
+ * the two outermost rings of cells.  The slope rule of Eq. (eqnSigma) then
+ * reduces to central differences everywhere, (sigma, dsigma/dx, dsigma/dy) are
+ * all linear in sigma, and the solve convolves sigma alone with two merged
+ * kernel tables (the same discrete sum, 1 forward field instead of 3).  Every
+ * solve verifies the guarantee on the device; a violation is reported by
+ * sgf_plan_check as SGF_EINVAL and that solve's output is not the method's. */
+
+/* As sgf_plan_create, with option flags (0 = sgf_plan_create).  Errors as
+ * sgf_plan_create; SGF_EINVAL for unknown flags or SGF_PLAN_ZERO_RIM with
+ * levels > 1. */
+sgf_status sgf_plan_create_ex(const sgf_nest_desc *desc, sgf_precision precision, uint32_t flags,
+                              sgf_plan **out);
+
+/* Waits for this plan's last solve and reports what the device recorded for
+ * the solves since the previous check: SGF_EINVAL when a SGF_PLAN_ZERO_RIM
+ * guarantee was violated, SGF_OK otherwise.  Clears the record. */
+sgf_status sgf_plan_check(sgf_plan *plan);
+
 /* A new plan with its own workspace that shares src's kernel spectra (no
  * table generation).  Plans that share spectra may solve concurrently on
  * different streams; one plan must not run two solves at once.  The spectra

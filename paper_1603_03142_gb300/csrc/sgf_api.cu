@@ -92,6 +92,10 @@ struct SetKey {
 struct sgf_plan {
     sgf_nest_desc desc{};
     sgf_precision prec = SGF_FP32;
+    uint32_t flags = 0;
+    bool merged = false;       // SGF_PLAN_ZERO_RIM: one forward field, merged spectra
+    int *d_status = nullptr;   // device status word (STATUS_* bits)
+    cudaEvent_t done = nullptr;  // recorded after every solve (sgf_plan_check)
     int N = 0, logN = 0, L = 0, device = 0;
     size_t esize = 4;  // bytes per real
     Spectra *spec = nullptr;
@@ -164,9 +168,54 @@ long corner_units(const sgf_nest_desc *d, int l, int unit, int axis)
     return acc;
 }
 
+// Lists of a zero-rim single-level plan: one slab of sigma alone, one output,
+// one merged spectra set.
+void build_lists_merged(sgf_plan *p)
+{
+    const int N = p->N;
+    const size_t T = p->esize, Cb = 2 * p->esize;
+    GenSet g{};
+    g.kind = SPEC_MERGED;
+    g.cas = 4;
+    g.m = 1;
+    p->sets.push_back(g);
+    FwdSlab sl{};
+    sl.level = 0;
+    sl.m = 1;
+    sl.rows = N;
+    sl.off = 0;
+    p->slabs.push_back(sl);
+    p->fwd_elems = (size_t)(N + 1) * N;
+    ColOutput o{};
+    o.level = 0;
+    o.rows = N;
+    o.in_begin = 0;
+    o.in_count = 1;
+    o.off = 0;
+    p->outs.push_back(o);
+    p->bwd_elems = 2 * (size_t)(N + 1) * N;
+    ColInput ci{};
+    ci.slab = 0;
+    ci.kind = SPEC_MERGED;
+    ci.spec_off = 0;
+    p->ins.push_back(ci);
+    p->contrib_begin[0] = 0;
+    p->contribs.push_back(RowContrib{1, 0, 0, 0});
+    p->contrib_begin[1] = 1;
+    for (int r = 0; r < N / 2; ++r)
+        p->items.push_back(FwdItem{0, r});
+    // sigma in, Fx Fy out; 1-field forward and 2-field backward intermediates; 2 quarter spectra
+    p->algorithmic_bytes = 3 * (size_t)N * N * T + 2 * p->fwd_elems * Cb + 2 * p->bwd_elems * Cb +
+                           2 * (size_t)(N + 1) * (N + 1) * T;
+}
+
 // Build all host-side lists of a plan (no CUDA calls).
 void build_lists(sgf_plan *p)
 {
+    if (p->merged) {
+        build_lists_merged(p);
+        return;
+    }
     const int N = p->N, L = p->L, P = 2 * N;
     const size_t T = p->esize, Cb = 2 * p->esize;
     std::map<SetKey, int> set_index;
@@ -303,8 +352,9 @@ size_t spectra_total(const sgf_plan *p)
 {
     size_t off = 0;
     for (const auto &g : p->sets) {
-        const size_t b = g.kind == SPEC_QUARTER ? 6 * (size_t)(p->N + 1) * quarter_stride(p->N) * p->esize
-                                                : 6 * (size_t)(p->N + 1) * 2 * p->N * 2 * p->esize;
+        const size_t b = g.kind == SPEC_MERGED  ? 2 * (size_t)(p->N + 1) * quarter_stride(p->N) * p->esize
+                         : g.kind == SPEC_QUARTER ? 6 * (size_t)(p->N + 1) * quarter_stride(p->N) * p->esize
+                                                  : 6 * (size_t)(p->N + 1) * 2 * p->N * 2 * p->esize;
         off += (b + 255) & ~(size_t)255;
     }
     return off;
@@ -320,6 +370,11 @@ void plan_free_owned(sgf_plan *p)
     cudaFree(p->d_bwd);
     cudaFree(p->d_restricted);
     cudaFree(p->d_stage);
+    cudaFree(p->d_status);
+    if (p->done)
+        cudaEventDestroy(p->done);
+    p->done = nullptr;
+    p->d_status = nullptr;
     p->d_lists = p->d_fwd = p->d_bwd = p->d_restricted = p->d_stage = nullptr;
     cudaSetDevice(cur);
 }
@@ -363,6 +418,12 @@ sgf_status plan_alloc_owned(sgf_plan *p)
         if ((e = cudaMalloc(&p->d_restricted, (size_t)(p->L - 1) * p->N * p->N * p->esize)) != cudaSuccess)
             return cuda_fail(e, "cudaMalloc(restricted densities)");
     }
+    if ((e = cudaMalloc(&p->d_status, 16)) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(status word)");
+    if ((e = cudaMemset(p->d_status, 0, 16)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemset(status word)");
+    if ((e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "cudaEventCreate(solve completion)");
     p->workspace_bytes = blob.size() + (p->fwd_elems + p->bwd_elems) * Cb +
                          (size_t)(p->L > 1 ? p->L - 1 : 0) * p->N * p->N * p->esize;
     return SGF_OK;
@@ -414,11 +475,22 @@ sgf_status build_spectra(sgf_plan *p)
         twT[at].x = (T)re[idx];
         twT[at].y = (T)im[idx];
     };
+    // W_{R Ns}^{e} = W_P^{e 2N / (R Ns)}; layout per Fft16Plan (direct or factored over k = 16 kh + kl)
     for (int st = 1, Ns = pl.radix(0); st < pl.nst; Ns *= pl.radix(st), ++st) {
         const int R = pl.radix(st);
-        for (int r = 1; r < R; ++r)
-            for (int k = 0; k < Ns; ++k)
-                put(pl.twoff[st] + (r - 1) * Ns + k, (long)2 * N / (R * Ns) * r * k);
+        const long scale = (long)2 * N / ((long)R * Ns);
+        const int t0 = pl.twoff[st];
+        for (int r = 1; r < R; ++r) {
+            if (Ns < 256) {
+                for (int k = 0; k < Ns; ++k)
+                    put(t0 + (r - 1) * Ns + k, scale * r * k);
+            } else {
+                for (int kl = 0; kl < 16; ++kl)
+                    put(t0 + (r - 1) * 16 + kl, scale * r * kl);
+                for (int kh = 0; kh < Ns / 16; ++kh)
+                    put(t0 + (R - 1) * 16 + (r - 1) * (Ns / 16) + kh, scale * 16 * r * kh);
+            }
+        }
     }
     for (int jj = 0; jj < N / 16; ++jj)
         put(tl.base + jj, jj);
@@ -512,6 +584,7 @@ sgf_status solve_impl(sgf_plan *p, const void *const *sigma, void *const *fx, vo
     a.spec = p->spec->dev;
     a.tw = static_cast<const typename SolveArgs<T>::C *>(p->spec->tw);
     a.tw_entries = p->spec->tw_entries;
+    a.status = p->d_status;
     a.slabs = p->d_slabs;
     a.fwd_items = p->d_items;
     a.outs = p->d_outs;
@@ -522,17 +595,23 @@ sgf_status solve_impl(sgf_plan *p, const void *const *sigma, void *const *fx, vo
     cudaError_t e;
     if ((ms = mark(p, st)) != SGF_OK)
         return ms;
-    if ((e = launch_row_fwd16<T>(a, (int)p->items.size(), st)) != cudaSuccess)
+    e = p->merged ? launch_row_fwd_merged<T>(a, st) : launch_row_fwd16<T>(a, (int)p->items.size(), st);
+    if (e != cudaSuccess)
         return cuda_fail(e, "row_fwd launch");
     if ((ms = mark(p, st)) != SGF_OK)
         return ms;
-    if ((e = launch_col16<T>(a, (int)p->outs.size(), st)) != cudaSuccess)
+    e = p->merged ? launch_col_merged<T>(a, st) : launch_col16<T>(a, (int)p->outs.size(), st);
+    if (e != cudaSuccess)
         return cuda_fail(e, "col launch");
     if ((ms = mark(p, st)) != SGF_OK)
         return ms;
     if ((e = launch_row_inv16<T>(a, st)) != cudaSuccess)
         return cuda_fail(e, "row_inv launch");
-    return mark(p, st);
+    if ((ms = mark(p, st)) != SGF_OK)
+        return ms;
+    if ((e = cudaEventRecord(p->done, st)) != cudaSuccess)
+        return cuda_fail(e, "cudaEventRecord(solve completion)");
+    return SGF_OK;
 }
 
 struct DeviceGuard {
@@ -583,15 +662,27 @@ const char *sgf_version(void) { return "sgf 0.1.0 sm_103a"; }
 
 sgf_status sgf_plan_create(const sgf_nest_desc *desc, sgf_precision precision, sgf_plan **out)
 {
+    return sgf_plan_create_ex(desc, precision, 0u, out);
+}
+
+sgf_status sgf_plan_create_ex(const sgf_nest_desc *desc, sgf_precision precision, uint32_t flags,
+                              sgf_plan **out)
+{
     if (!out)
         return fail(SGF_EINVAL, "out is NULL");
     *out = nullptr;
     sgf_status s = validate(desc, precision);
     if (s != SGF_OK)
         return s;
+    if (flags & ~SGF_PLAN_ZERO_RIM)
+        return fail(SGF_EINVAL, "unknown plan flags 0x%x", flags);
+    if ((flags & SGF_PLAN_ZERO_RIM) && desc->levels != 1)
+        return fail(SGF_EINVAL, "SGF_PLAN_ZERO_RIM needs a single level (levels = %d)", desc->levels);
     sgf_plan *p = new sgf_plan();
     p->desc = *desc;
     p->prec = precision;
+    p->flags = flags;
+    p->merged = (flags & SGF_PLAN_ZERO_RIM) != 0;
     p->N = desc->n;
     p->logN = ilog2(desc->n);
     p->L = desc->levels;
@@ -631,6 +722,8 @@ sgf_status sgf_plan_share(const sgf_plan *src, sgf_plan **out)
     sgf_plan *p = new sgf_plan();
     p->desc = src->desc;
     p->prec = src->prec;
+    p->flags = src->flags;
+    p->merged = src->merged;
     p->N = src->N;
     p->logN = src->logN;
     p->L = src->L;
@@ -742,6 +835,24 @@ sgf_status sgf_solve_batched(sgf_plan *const *plans, int32_t count, const void *
     return SGF_OK;
 }
 
+sgf_status sgf_plan_check(sgf_plan *p)
+{
+    if (!p)
+        return fail(SGF_EINVAL, "plan is NULL");
+    DeviceGuard g(p->device);
+    cudaError_t e;
+    if ((e = cudaEventSynchronize(p->done)) != cudaSuccess)
+        return cuda_fail(e, "waiting for the plan's last solve");
+    int word = 0;
+    if ((e = cudaMemcpy(&word, p->d_status, sizeof word, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "reading the plan status word");
+    if (word != 0 && (e = cudaMemset(p->d_status, 0, sizeof word)) != cudaSuccess)
+        return cuda_fail(e, "clearing the plan status word");
+    if (word & STATUS_RIM_NONZERO)
+        return fail(SGF_EINVAL, "SGF_PLAN_ZERO_RIM: sigma was nonzero on the two outer rings of cells");
+    return SGF_OK;
+}
+
 sgf_status sgf_plan_profile(sgf_plan *p, int32_t enable)
 {
     if (!p)
@@ -756,7 +867,7 @@ sgf_status sgf_plan_profile_read(sgf_plan *p, sgf_kernel_times *out)
         return fail(SGF_EINVAL, "NULL argument");
     DeviceGuard g(p->device);
     std::memset(out, 0, sizeof *out);
-    const size_t per = 5;
+    const size_t per = 5;  // events per solve (mark() calls)
     cudaError_t e;
     if (p->events_used >= per && (e = cudaEventSynchronize(p->events[p->events_used - 1])) != cudaSuccess)
         return cuda_fail(e, "cudaEventSynchronize(profile)");

@@ -105,6 +105,17 @@ SGF_HD void hdft16(C *v)
     }
 }
 
+// W_{R Ns}^{r k} of stage table `tws` (see Fft16Plan).
+template <typename C>
+SGF_HD C stage_twiddle(const C *tws, int R, int Ns, int r, int k)
+{
+    if (Ns < 256)
+        return tws[(r - 1) * Ns + k];
+    const C a = tws[(r - 1) * 16 + (k & 15)];
+    const C b = tws[(R - 1) * 16 + (r - 1) * (Ns >> 4) + (k >> 4)];
+    return hmul(a, b);
+}
+
 // In-place R-point DFT (R = 2, 4, 8) of the values v[Q + r*(16/R)], r = 0..R-1;
 // R and Q are compile-time so the register array is never indexed at run time.
 template <typename C, bool INV, int R, int Q>
@@ -147,7 +158,7 @@ SGF_HD void stage_small_one(C *v, int N, int Ns, int j, const C *tw)
     if (Ns > 1) {
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-            const C w = tw[(r - 1) * Ns + k];  // this stage's table
+            const C w = stage_twiddle(tw, R, Ns, r, k);  // this stage's table
             v[Q + r * S] = INV ? hmulc(v[Q + r * S], w) : hmul(v[Q + r * S], w);
         }
     }
@@ -174,7 +185,13 @@ SGF_HD void stage_small(C *v, int N, int Ns, int j, const C *tw)
 SGF_HD int pad16(int i) { return i + (i >> 4); }
 
 // Stage bookkeeping shared by the device engine, the host table builder and
-// the host test emulator.  twoff[st]: offset of stage st's twiddle table.
+// the host test emulator.  Stage st (> 0) multiplies by W_{R Ns}^{r k},
+// r = 1..R-1, k < Ns.  For Ns < 256 its table is D[r-1][k] (at twoff[st]);
+// for Ns >= 256 the twiddle is factored over k = 16 kh + kl into
+// A[r-1][kl] = W_{R Ns}^{r kl} (16 per r) times B[r-1][kh] = W_{R Ns}^{16 r kh}
+// (Ns/16 per r), which keeps the tables a few KB.  Within a warp kl runs
+// over 16 consecutive values and kh over at most two, so the reads are
+// conflict-free or broadcasts.
 struct Fft16Plan {
     int N, logN, nst, S16, rlast;
     int twoff[5];
@@ -190,9 +207,10 @@ struct Fft16Plan {
         for (int st = 0; st < 5; ++st) {
             twoff[st] = off;
             if (st < nst) {
+                const int R = radix(st);
                 if (st > 0)
-                    off += (radix(st) - 1) * Ns;
-                Ns *= radix(st);
+                    off += Ns >= 256 ? (R - 1) * (16 + Ns / 16) : (R - 1) * Ns;
+                Ns *= R;
             }
         }
         twlen = off;
@@ -211,7 +229,7 @@ SGF_HD void fft16_stage_compute(C *v, const Fft16Plan &pl, int st, int Ns, int j
         if (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < 16; ++r) {
-                const C w = tws[(r - 1) * Ns + k];
+                const C w = stage_twiddle(tws, 16, Ns, r, k);
                 v[r] = INV ? hmulc(v[r], w) : hmul(v[r], w);
             }
         }

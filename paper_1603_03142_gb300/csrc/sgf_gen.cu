@@ -82,6 +82,49 @@ struct AxisMap {
     }
 };
 
+// The six tables of one source cell at convolution index (dx, dy).
+__device__ __forceinline__ void cell_tables(const AxisMap &mx, const AxisMap &my, int dx, int dy, int cas, int m,
+                                            double out[6])
+{
+    double a, wx, c, wy;
+    mx.edges(dx, a, wx);
+    my.edges(dy, c, wy);
+    const double b = a + wx, d = c + wy;
+    const Corner k1 = corner_eval(b, d), k2 = corner_eval(a, d), k3 = corner_eval(b, c), k4 = corner_eval(a, c);
+    const double i0x = (k1.g0x - k2.g0x) - (k3.g0x - k4.g0x);
+    const double i0y = (k1.g0y - k3.g0y) - (k2.g0y - k4.g0y);
+    const double ixx = (k1.hxx - k2.hxx) - (k3.hxx - k4.hxx);
+    const double iyy = (k1.hyy - k3.hyy) - (k2.hyy - k4.hyy);
+    const double ixy = (k1.hxy - k2.hxy) - (k3.hxy - k4.hxy);
+    const double uc = a + 0.5 * wx, vc = c + 0.5 * wy;
+    const double sf = cas == 3 ? 1.0 / m : 1.0;
+    out[0] = i0x;
+    out[1] = (ixx - uc * i0x) * sf;
+    out[2] = (ixy - vc * i0x) * sf;
+    out[3] = i0y;
+    out[4] = (ixy - uc * i0y) * sf;
+    out[5] = (iyy - vc * i0y) * sf;
+}
+
+// Case 1 with the central-difference slope stencils folded in (zero-rim
+// single level): dx = (s[i+1] - s[i-1])/2 gives
+//   sum_s Kxx[t-s] dx[s] = sum_s s[s] (Kxx[d + x] - Kxx[d - x])/2,  d = t - s,
+// so Gx = K0x + (Kxx[d+x] - Kxx[d-x])/2 + (Kxy[d+y] - Kxy[d-y])/2 and
+//    Gy = K0y + (Kyx[d+x] - Kyx[d-x])/2 + (Kyy[d+y] - Kyy[d-y])/2,
+// with the neighbouring entries evaluated exactly (they may lie one cell
+// beyond the table's range).
+__device__ __forceinline__ void merged_tables(const AxisMap &mx, const AxisMap &my, int dx, int dy, double out[2])
+{
+    double c0[6], xp[6], xm[6], yp[6], ym[6];
+    cell_tables(mx, my, dx, dy, 1, 1, c0);
+    cell_tables(mx, my, dx + 1, dy, 1, 1, xp);
+    cell_tables(mx, my, dx - 1, dy, 1, 1, xm);
+    cell_tables(mx, my, dx, dy + 1, 1, 1, yp);
+    cell_tables(mx, my, dx, dy - 1, 1, 1, ym);
+    out[0] = c0[0] + 0.5 * (xp[1] - xm[1]) + 0.5 * (yp[2] - ym[2]);
+    out[1] = c0[3] + 0.5 * (xp[4] - xm[4]) + 0.5 * (yp[5] - ym[5]);
+}
+
 __global__ void k_gen_tables(GenSet g, int N, double *__restrict__ tables)
 {
     const int P = 2 * N;
@@ -89,33 +132,19 @@ __global__ void k_gen_tables(GenSet g, int N, double *__restrict__ tables)
     const int py = blockIdx.y;
     if (px >= P)
         return;
-    const AxisMap mx{g.cas, g.m, g.px, g.ax, N}, my{g.cas, g.m, g.py, g.ay, N};
+    const int cas = g.cas == 4 ? 1 : g.cas;
+    const AxisMap mx{cas, g.m, g.px, g.ax, N}, my{cas, g.m, g.py, g.ay, N};
     double out[6] = {0, 0, 0, 0, 0, 0};
     int dx, dy;
+    const int ntab = g.cas == 4 ? 2 : 6;
     if (mx.index(px, P, dx) && my.index(py, P, dy)) {
-        double a, wx, c, wy;
-        mx.edges(dx, a, wx);
-        my.edges(dy, c, wy);
-        const double b = a + wx, d = c + wy;
-        const Corner k1 = corner_eval(b, d), k2 = corner_eval(a, d), k3 = corner_eval(b, c),
-                     k4 = corner_eval(a, c);
-        const double i0x = (k1.g0x - k2.g0x) - (k3.g0x - k4.g0x);
-        const double i0y = (k1.g0y - k3.g0y) - (k2.g0y - k4.g0y);
-        const double ixx = (k1.hxx - k2.hxx) - (k3.hxx - k4.hxx);
-        const double iyy = (k1.hyy - k3.hyy) - (k2.hyy - k4.hyy);
-        const double ixy = (k1.hxy - k2.hxy) - (k3.hxy - k4.hxy);
-        const double uc = a + 0.5 * wx, vc = c + 0.5 * wy;
-        const double sf = g.cas == 3 ? 1.0 / g.m : 1.0;
-        out[0] = i0x;
-        out[1] = (ixx - uc * i0x) * sf;
-        out[2] = (ixy - vc * i0x) * sf;
-        out[3] = i0y;
-        out[4] = (ixy - uc * i0y) * sf;
-        out[5] = (iyy - vc * i0y) * sf;
+        if (g.cas == 4)
+            merged_tables(mx, my, dx, dy, out);
+        else
+            cell_tables(mx, my, dx, dy, g.cas, g.m, out);
     }
     const size_t plane = (size_t)P * P, at = (size_t)py * P + px;
-#pragma unroll
-    for (int t = 0; t < 6; ++t)
+    for (int t = 0; t < ntab; ++t)
         tables[t * plane + at] = out[t];
 }
 
@@ -168,11 +197,11 @@ __global__ void k_gen_cols(int N, int logN, const double2 *__restrict__ half, co
     __syncthreads();
     block_fft<double2, false>(W, N, logN, 2, tw);
     const double scale = 1.0 / ((double)P * (double)P);
-    if (kind == SPEC_QUARTER) {
-        // K0x and K0y (tables 0, 3) are odd in one axis: purely imaginary
+    if (kind == SPEC_QUARTER || kind == SPEC_MERGED) {
+        // K0x and K0y (tables 0, 3) are odd in one axis: purely imaginary; merged Gx, Gy too
         const int QS = quarter_stride(N), HQ = quarter_half(N);
         T *dst = reinterpret_cast<T *>(spec) + spec_off + ((size_t)t * (N + 1) + kx) * QS;
-        const bool imag = (t == 0 || t == 3);
+        const bool imag = kind == SPEC_MERGED || t == 0 || t == 3;
         for (int idx = tid; idx < QS; idx += nt) {
             const int q = idx < HQ ? 2 * idx : 2 * (idx - HQ) + 1;  // even half, then odd half
             const double2 X = q <= N ? W[(q & 1) * N + (q >> 1)] : make_double2(0.0, 0.0);
@@ -226,11 +255,12 @@ cudaError_t launch_gen_set(const GenSet &g, int N, int logN, const double2 *tw64
     if (e != cudaSuccess)
         return e;
     const size_t smem = 2 * (size_t)N * sizeof(double2);
-    k_gen_rows<<<dim3(P / 2, 6), gen_threads(N), smem, st>>>(N, logN, work_tables, work_half, tw64);
+    const int ntab = g.kind == SPEC_MERGED ? 2 : 6;
+    k_gen_rows<<<dim3(P / 2, ntab), gen_threads(N), smem, st>>>(N, logN, work_tables, work_half, tw64);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
-    k_gen_cols<T><<<dim3(N + 1, 6), gen_threads(N), smem, st>>>(N, logN, work_half, tw64, g.kind, spec,
-                                                                  g.spec_off);
+    k_gen_cols<T><<<dim3(N + 1, ntab), gen_threads(N), smem, st>>>(N, logN, work_half, tw64, g.kind, spec,
+                                                                     g.spec_off);
     return cudaGetLastError();
 }
 

@@ -28,6 +28,9 @@
 //     stored as reals [table][kx 0..N][row of ky 0..N split by parity, see
 //     quarter_half], so each parity half of a column reads one contiguous half.
 //   SPEC_FULL (Cases 2, 3): complex [table][kx 0..N][ky 0..P).
+//   SPEC_MERGED (Case 1 of a zero-rim single level): 2 tables (Gx, Gy), the
+//     kernels with the central-difference slope stencils folded in; both
+//     imaginary, quarter-stored like SPEC_QUARTER; mirror sign + for Gx, - for Gy.
 #pragma once
 #include <cstddef>
 #include <cstdint>
@@ -38,7 +41,10 @@ namespace sgf {
 
 constexpr int kMaxLevels = 8;
 
-enum SpecKind : int { SPEC_QUARTER = 0, SPEC_FULL = 1 };
+enum SpecKind : int { SPEC_QUARTER = 0, SPEC_FULL = 1, SPEC_MERGED = 2 };
+
+// Device status bits of a plan (sgf_plan_check).
+enum : int { STATUS_RIM_NONZERO = 1 };
 
 // A quarter-stored spectrum row holds ky = 0..N split by parity: even ky
 // (0, 2, .., N) at [0, N/2 + 1), odd ky (1, 3, .., N-1) at [N/2 + 4, N + 4);
@@ -94,6 +100,7 @@ struct SolveArgs {
     const void *spec;           // kernel spectra (T reals / C complex)
     const C *tw;                // twiddle area (tw_layout), copied to shared memory by every CTA
     int tw_entries;             // its length in complex entries (even)
+    int *status;                // device status word of the plan (STATUS_* bits)
     const FwdSlab *slabs;
     const FwdItem *fwd_items;
     const ColOutput *outs;
@@ -123,7 +130,7 @@ inline __host__ __device__ TwLayout tw_layout(int twlen, int N)
 // Kernel-table generation for one spectra set (FP64).
 struct GenSet {
     int kind;          // SpecKind
-    int cas;           // 1, 2 or 3
+    int cas;           // 1, 2 or 3; 4 = merged Case 1 (SPEC_MERGED)
     int m, px, py;     // phases (m = 1 for Case 1)
     int ax, ay;        // integer lattice offset of the pair (units of the finer cell), see sgf_gen.cu
     size_t spec_off;   // where the set's spectra go (real elements for QUARTER, complex for FULL)
@@ -141,6 +148,10 @@ template <typename T>
 cudaError_t launch_row_inv16(const SolveArgs<T> &a, cudaStream_t st);
 template <typename T>
 cudaError_t solve16_init();
+template <typename T>
+cudaError_t launch_row_fwd_merged(const SolveArgs<T> &a, cudaStream_t st);
+template <typename T>
+cudaError_t launch_col_merged(const SolveArgs<T> &a, cudaStream_t st);
 
 // Build the spectra of one set into spec (element type T: float or double).
 // work_tables: 6*P*P doubles; work_half: 6*(N+1)*P double2.

@@ -321,6 +321,171 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256) k_col16(SolveAr
     }
 }
 
+// ------------------------------------------------------------ zero-rim path
+// Forward row pass of a SGF_PLAN_ZERO_RIM plan: the rows of sigma alone (the
+// slopes are folded into the merged spectra).  Also verifies the guarantee:
+// the CTAs of rows 0-1 and N-2..N-1 scan their rows, every CTA its cells in
+// columns 0, 1, N-2, N-1; a nonzero value sets STATUS_RIM_NONZERO.
+// Shared memory: twiddle area | sigma rows[2][N] | sbuf[2 SP], SP = N + N/16 + 2.
+template <typename T>
+__global__ void __launch_bounds__(512) k_row_fwd_m(SolveArgs<T> a)
+{
+    using C = typename Cx<T>::C;
+    using C2 = typename Cx<T>::C2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = a.N, Q = N >> 4, SP = N + Q + 2;
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    T *srow = reinterpret_cast<T *>(smem_raw + tw_bytes<C>(a.tw_entries));
+    C *sbuf = reinterpret_cast<C *>(srow + 2 * N);
+    __shared__ int rim_bad;
+    const int r0 = 2 * blockIdx.x;
+    const T *src = a.src[0] + (size_t)r0 * N;
+    cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
+    cp_block(srow, src, 2 * (size_t)N * sizeof(T));
+    cp_commit();
+    const int t = threadIdx.x;
+    if (t == 0)
+        rim_bad = 0;
+    const bool active = t < 2 * Q;
+    const int b = active ? t / Q : 0, j = active ? t - b * Q : 0;
+    Fft16Plan pl;
+    pl.init(N, a.logN);
+    const TwLayout tl = tw_layout(pl.twlen, N);
+    cp_wait<0>();
+    __syncthreads();
+    {
+        bool bad = false;
+        if (r0 == 0 || r0 == N - 2) {
+            for (int i = t; i < 2 * N; i += blockDim.x)
+                bad |= srow[i] != T(0);
+        } else if (t < 8) {
+            const int col = (t & 3) < 2 ? (t & 3) : N - 4 + (t & 3);  // 0, 1, N-2, N-1
+            bad = srow[(t >> 2) * N + col] != T(0);
+        }
+        if (bad)
+            rim_bad = 1;
+    }
+    C v[16];
+    if (active) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int c = j + u * Q;
+            C z = hmk<C>(srow[c], srow[N + c]);
+            if (b)
+                z = hmul(z, twist(tw, tl, j, u));
+            v[u] = z;
+        }
+    }
+    fft16_block<C, false>(v, sbuf, b, SP, j, active, pl, tw);
+    __syncthreads();
+    if (t == 0 && rim_bad)
+        atomicOr(a.status, STATUS_RIM_NONZERO);
+    if (active) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+            sbuf[b * SP + pad16(j + u * Q)] = v[u];
+    }
+    __syncthreads();
+    C2 *out = reinterpret_cast<C2 *>(a.fwd);
+    for (int kx = t; kx <= N; kx += blockDim.x) {
+        const int bb = kx & 1, k = kx >> 1;
+        const int km = (N - bb - k) & (N - 1);
+        const C Z = sbuf[bb * SP + pad16(k)];
+        const C Zm = sbuf[bb * SP + pad16(km)];
+        C2 o;
+        o.x = T(0.5) * (Z.x + Zm.x);
+        o.y = T(0.5) * (Z.y - Zm.y);
+        o.z = T(0.5) * (Z.y + Zm.y);
+        o.w = T(-0.5) * (Z.x - Zm.x);
+        out[((size_t)kx * N + r0) >> 1] = o;
+    }
+}
+
+// Column pass of a SGF_PLAN_ZERO_RIM plan: one forward transform, the two
+// merged spectra (Fx^ = Gx^ sigma^, Fy^ = Gy^ sigma^, both imaginary), two
+// inverse transforms; parity halves folded through distributed shared memory.
+// Two CTAs per SM.  Shared memory: twiddle area | sbuf[N + N/16] | stage
+// {column[N], this parity's half rows of Gx and Gy}; the fold reuses sbuf+stage.
+template <typename T>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_col_m(SolveArgs<T> a)
+{
+    using C = typename Cx<T>::C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = a.N, Q = N >> 4, QS = quarter_stride(N), HQ = quarter_half(N);
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *sbuf = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
+    unsigned char *stage = reinterpret_cast<unsigned char *>(sbuf) + col_sbuf_bytes<C>(N);
+    C *col = reinterpret_cast<C *>(stage);
+    T *gsp = reinterpret_cast<T *>(stage + (size_t)N * sizeof(C));
+    cg::cluster_group cluster = cg::this_cluster();
+    const int b = (int)cluster.block_rank();
+    const int kx = blockIdx.x >> 1;
+    const int t = threadIdx.x;
+    const bool active = t < Q;
+    const int j = active ? t : 0;
+    Fft16Plan pl;
+    pl.init(N, a.logN);
+    const TwLayout tl = tw_layout(pl.twlen, N);
+    const T *spec = reinterpret_cast<const T *>(a.spec);
+    cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
+    cp_block(col, a.fwd + (size_t)kx * N, (size_t)N * sizeof(C));
+    cp_block(gsp, spec + (size_t)kx * QS + b * HQ, (size_t)HQ * sizeof(T));
+    cp_block(gsp + HQ, spec + ((size_t)(N + 1) + kx) * QS + b * HQ, (size_t)HQ * sizeof(T));
+    cp_commit();
+    cp_wait<0>();
+    __syncthreads();
+    C ax[16], ay[16];
+    {
+        C v[16];
+        if (active) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                C x = col[j + u * Q];
+                if (b)
+                    x = hmul(x, twist(tw, tl, j, u));
+                v[u] = x;
+            }
+        }
+        fft16_block<C, false>(v, sbuf, 0, N + Q, j, active, pl, tw);
+        if (active) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int kp = j + u * Q;
+                const bool hi = 2 * kp + b > N;
+                const int q = hi ? N - kp - b : kp;
+                const T gx = gsp[q];                           // Gx even in ky
+                const T gy = hi ? -gsp[HQ + q] : gsp[HQ + q];  // Gy odd in ky
+                ax[u] = hmk<C>(-gx * v[u].y, gx * v[u].x);     // i gx v
+                ay[u] = hmk<C>(-gy * v[u].y, gy * v[u].x);
+            }
+        }
+    }
+    fft16_block<C, true>(ax, sbuf, 0, N + Q, j, active, pl, tw);
+    fft16_block<C, true>(ay, sbuf, 0, N + Q, j, active, pl, tw);
+    C *fold = sbuf;  // 2N complex over sbuf and the stage (both free after the transforms)
+    cluster.sync();
+    if (b == 1 && active) {
+        C *dst = cluster.map_shared_rank(fold, 0);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int n = j + u * Q;
+            const C w = twist(tw, tl, j, u);
+            dst[n] = hmulc(ax[u], w);
+            dst[N + n] = hmulc(ay[u], w);
+        }
+    }
+    cluster.sync();
+    if (b == 0 && active) {
+        C *dst = a.bwd;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int n = j + u * Q;
+            dst[(size_t)kx * N + n] = hadd(ax[u], fold[n]);
+            dst[((size_t)(N + 1) + kx) * N + n] = hadd(ay[u], fold[N + n]);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ row_inv
 // Shared memory: twiddle area | sbuf[2 SP], SP = N + N/16 + 2 | O[2 comps][2 rows][N] (real).
 template <typename T>
@@ -437,6 +602,9 @@ static size_t smem_inv16(int N)
 }
 
 template <typename T>
+cudaError_t merged_init();
+
+template <typename T>
 cudaError_t solve16_init()
 {
     const int maxN = sizeof(T) == 8 ? 2048 : 4096;
@@ -447,8 +615,10 @@ cudaError_t solve16_init()
     if ((e = cudaFuncSetAttribute(k_col16<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem_col16<T>(maxN))) != cudaSuccess)
         return e;
-    return cudaFuncSetAttribute(k_row_inv16<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_inv16<T>(maxN));
+    if ((e = cudaFuncSetAttribute(k_row_inv16<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_inv16<T>(maxN))) != cudaSuccess)
+        return e;
+    return merged_init<T>();
 }
 
 template <typename T>
@@ -473,6 +643,53 @@ cudaError_t launch_row_inv16(const SolveArgs<T> &a, cudaStream_t st)
     k_row_inv16<T><<<grid, warps_up(2 * (a.N / 16)), smem_inv16<T>(a.N), st>>>(a);
     return cudaGetLastError();
 }
+
+template <typename T>
+static size_t smem_fwd_m(int N)
+{
+    using C = typename Cx<T>::C;
+    return tw_bytes<C>(tw_entries_for<T>(N)) + 2 * (size_t)N * sizeof(T) + 2 * (size_t)(N + N / 16 + 2) * sizeof(C);
+}
+template <typename T>
+static size_t smem_col_m(int N)
+{
+    using C = typename Cx<T>::C;
+    size_t stage = (size_t)N * sizeof(C) + 2 * (size_t)quarter_half(N) * sizeof(T);
+    const size_t sb = col_sbuf_bytes<C>(N);
+    if (sb + stage < 2 * (size_t)N * sizeof(C))  // the fold spans sbuf and the stage
+        stage = 2 * (size_t)N * sizeof(C) - sb;
+    return tw_bytes<C>(tw_entries_for<T>(N)) + sb + stage;
+}
+
+template <typename T>
+cudaError_t merged_init()
+{
+    const int maxN = sizeof(T) == 8 ? 2048 : 4096;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_row_fwd_m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_fwd_m<T>(maxN))) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(k_col_m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col_m<T>(maxN));
+}
+
+template <typename T>
+cudaError_t launch_row_fwd_merged(const SolveArgs<T> &a, cudaStream_t st)
+{
+    k_row_fwd_m<T><<<a.N / 2, warps_up(2 * (a.N / 16)), smem_fwd_m<T>(a.N), st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_col_merged(const SolveArgs<T> &a, cudaStream_t st)
+{
+    k_col_m<T><<<2 * (a.N + 1), warps_up(a.N / 16), smem_col_m<T>(a.N), st>>>(a);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_row_fwd_merged<float>(const SolveArgs<float> &, cudaStream_t);
+template cudaError_t launch_row_fwd_merged<double>(const SolveArgs<double> &, cudaStream_t);
+template cudaError_t launch_col_merged<float>(const SolveArgs<float> &, cudaStream_t);
+template cudaError_t launch_col_merged<double>(const SolveArgs<double> &, cudaStream_t);
 
 template cudaError_t solve16_init<float>();
 template cudaError_t solve16_init<double>();

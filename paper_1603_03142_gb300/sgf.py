@@ -26,9 +26,10 @@ FP64, FP32, BF16X = 0, 1, 2
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16x": BF16X}
 
 # every symbol include/sgf.h declares
-EXPORTS = ["sgf_plan_create", "sgf_plan_share", "sgf_plan_stats_get", "sgf_solve", "sgf_solve_host",
-           "sgf_solve_batched", "sgf_plan_destroy", "sgf_last_error", "sgf_version", "sgf_plan_profile",
-           "sgf_plan_profile_read"]
+EXPORTS = ["sgf_plan_create", "sgf_plan_create_ex", "sgf_plan_check", "sgf_plan_share", "sgf_plan_stats_get",
+           "sgf_solve", "sgf_solve_host", "sgf_solve_batched", "sgf_plan_destroy", "sgf_last_error", "sgf_version",
+           "sgf_plan_profile", "sgf_plan_profile_read"]
+PLAN_ZERO_RIM = 0x1
 KERNELS = ["restrict", "row_fwd", "col", "row_inv"]
 
 
@@ -52,6 +53,9 @@ class KernelTimes(ctypes.Structure):
 
 _vpp = ctypes.POINTER(ctypes.c_void_p)
 _lib.sgf_plan_create.argtypes = [ctypes.POINTER(NestDesc), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+_lib.sgf_plan_create_ex.argtypes = [ctypes.POINTER(NestDesc), ctypes.c_int, ctypes.c_uint32,
+                                    ctypes.POINTER(ctypes.c_void_p)]
+_lib.sgf_plan_check.argtypes = [ctypes.c_void_p]
 _lib.sgf_plan_share.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
 _lib.sgf_plan_stats_get.argtypes = [ctypes.c_void_p, ctypes.POINTER(PlanStats)]
 _lib.sgf_solve.argtypes = [ctypes.c_void_p, _vpp, _vpp, _vpp, ctypes.c_void_p]
@@ -64,7 +68,7 @@ _lib.sgf_plan_profile.argtypes = [ctypes.c_void_p, ctypes.c_int32]
 _lib.sgf_plan_profile_read.argtypes = [ctypes.c_void_p, ctypes.POINTER(KernelTimes)]
 _lib.sgf_last_error.restype = ctypes.c_char_p
 _lib.sgf_version.restype = ctypes.c_char_p
-for _f in ("sgf_plan_create", "sgf_plan_share", "sgf_plan_stats_get", "sgf_solve", "sgf_solve_host",
+for _f in ("sgf_plan_create", "sgf_plan_create_ex", "sgf_plan_check", "sgf_plan_share", "sgf_plan_stats_get", "sgf_solve", "sgf_solve_host",
            "sgf_solve_batched", "sgf_plan_destroy", "sgf_plan_profile", "sgf_plan_profile_read"):
     getattr(_lib, _f).restype = ctypes.c_int
 
@@ -117,17 +121,27 @@ def _stream_handle(stream) -> int:
 class Plan:
     """A solve plan: nest geometry + precision, resident kernel spectra, workspace."""
 
-    def __init__(self, nest, precision="fp32", _handle=None):
+    def __init__(self, nest, precision="fp32", zero_rim: bool = False, _handle=None):
         self.nest = nest
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.n, self.levels = int(nest.n), int(nest.levels)
+        self.zero_rim = bool(zero_rim)
         if _handle is not None:
             self._h = _handle
             return
         h = ctypes.c_void_p()
         desc = make_desc(nest)
-        _check(_lib.sgf_plan_create(ctypes.byref(desc), self.precision, ctypes.byref(h)), "sgf_plan_create")
+        flags = PLAN_ZERO_RIM if zero_rim else 0
+        _check(_lib.sgf_plan_create_ex(ctypes.byref(desc), self.precision, flags, ctypes.byref(h)),
+               "sgf_plan_create_ex")
         self._h = h
+
+    def check(self):
+        """Wait for the last solve and raise SgfError if the device recorded a violation."""
+        _check(_lib.sgf_plan_check(self._h), "sgf_plan_check")
+
+    def check_status(self) -> int:
+        return int(_lib.sgf_plan_check(self._h))
 
     @property
     def handle(self):
@@ -140,7 +154,7 @@ class Plan:
     def share(self) -> "Plan":
         h = ctypes.c_void_p()
         _check(_lib.sgf_plan_share(self._h, ctypes.byref(h)), "sgf_plan_share")
-        return Plan(self.nest, self.precision, _handle=h)
+        return Plan(self.nest, self.precision, zero_rim=self.zero_rim, _handle=h)
 
     def stats(self) -> dict:
         st = PlanStats()
@@ -225,11 +239,11 @@ def solve_batched(plans: Sequence[Plan], sigma, fx, fy, stream=None):
                                   ctypes.c_void_p(_stream_handle(stream))), "sgf_solve_batched")
 
 
-def create_status(nest, precision) -> int:
-    """Status of sgf_plan_create without keeping the plan (validation probes)."""
+def create_status(nest, precision, flags: int = 0) -> int:
+    """Status of sgf_plan_create_ex without keeping the plan (validation probes)."""
     h = ctypes.c_void_p()
     desc = make_desc(nest)
-    st = _lib.sgf_plan_create(ctypes.byref(desc), PRECISIONS.get(precision, precision), ctypes.byref(h))
+    st = _lib.sgf_plan_create_ex(ctypes.byref(desc), PRECISIONS.get(precision, precision), flags, ctypes.byref(h))
     if st == SGF_OK:
         _lib.sgf_plan_destroy(h)
     return st

@@ -60,3 +60,9 @@ def test_unsupported_sizes_rejected_on_host(lib):
 
 def test_unknown_precision(lib):
     assert lib.create_status(W.Nest(n=16), 7) == lib.SGF_EINVAL
+
+
+def test_zero_rim_flag_rules(lib):
+    # SGF_PLAN_ZERO_RIM is a single-level option; unknown flags are rejected
+    assert lib.create_status(W.Nest(n=16, levels=2, off=[(0, 0), (4, 4)]), "fp32", lib.PLAN_ZERO_RIM) == lib.SGF_EINVAL
+    assert lib.create_status(W.Nest(n=16), "fp32", 0x80) == lib.SGF_EINVAL
