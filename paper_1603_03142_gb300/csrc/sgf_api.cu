@@ -193,7 +193,7 @@ void build_lists_merged(sgf_plan *p)
     o.in_count = 1;
     o.off = 0;
     p->outs.push_back(o);
-    p->bwd_elems = 2 * (size_t)(N + 1) * N;
+    p->bwd_elems = 2 * (size_t)(N + 4) * N;
     ColInput ci{};
     ci.slab = 0;
     ci.kind = SPEC_MERGED;
@@ -271,7 +271,7 @@ void build_lists(sgf_plan *p)
         o.in_begin = (int)p->ins.size();
         o.in_count = 0;
         o.off = p->bwd_elems;
-        p->bwd_elems += 2 * (size_t)(N + 1) * rows;
+        p->bwd_elems += 2 * (size_t)(N + 4) * rows;
         p->outs.push_back(o);
         return (int)p->outs.size() - 1;
     };

@@ -19,7 +19,9 @@
 //   dx, dy the per-cell differences (slope times cell size).  Layout
 //   [field 0..2][kx 0..N][row 0..rows) of complex, rows = N/m.
 // Column output: one column-transformed, multiplied, inverse-column-transformed
-//   result, fields (Fx, Fy).  Layout [field 0..1][kx 0..N][row 0..rows_out).
+//   result, fields (Fx, Fy).  Layout [field 0..1][kx/4][row 0..rows_out)[kx%4]
+//   (kx padded to N + 4): the inverse row pass then reads 4 bins of a row as
+//   one 32-byte piece (bwd_index).
 // Kernel spectra: 6 tables per set in the order
 //   (K0x, Kxx, Kxy, K0y, Kyx, Kyy) = (x-force from sigma, dx, dy;
 //   y-force from sigma, dx, dy), already divided by P^2.
@@ -42,6 +44,12 @@ namespace sgf {
 constexpr int kMaxLevels = 8;
 
 enum SpecKind : int { SPEC_QUARTER = 0, SPEC_FULL = 1, SPEC_MERGED = 2 };
+
+// Element (comp, kx, row) of a column output with `rows` rows (complex units).
+inline __host__ __device__ size_t bwd_index(int N, int rows, int comp, int kx, int row)
+{
+    return (size_t)comp * (N + 4) * rows + ((size_t)(kx >> 2) * rows + row) * 4 + (kx & 3);
+}
 
 // Device status bits of a plan (sgf_plan_check).
 enum : int { STATUS_RIM_NONZERO = 1 };

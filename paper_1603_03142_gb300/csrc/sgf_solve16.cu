@@ -314,8 +314,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256) k_col16(SolveAr
         for (int u = 0; u < 16; ++u) {
             const int n = j + u * Q;
             if (n < o.rows) {
-                dst[(size_t)kx * o.rows + n] = hadd(ax[u], fold[n]);
-                dst[((size_t)(N + 1) + kx) * o.rows + n] = hadd(ay[u], fold[N + n]);
+                dst[bwd_index(N, o.rows, 0, kx, n)] = hadd(ax[u], fold[n]);
+                dst[bwd_index(N, o.rows, 1, kx, n)] = hadd(ay[u], fold[N + n]);
             }
         }
     }
@@ -480,22 +480,27 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, sizeof(T) == 4 
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
             const int n = j + u * Q;
-            dst[(size_t)kx * N + n] = hadd(ax[u], fold[n]);
-            dst[((size_t)(N + 1) + kx) * N + n] = hadd(ay[u], fold[N + n]);
+            dst[bwd_index(N, N, 0, kx, n)] = hadd(ax[u], fold[n]);
+            dst[bwd_index(N, N, 1, kx, n)] = hadd(ay[u], fold[N + n]);
         }
     }
 }
 
 // ------------------------------------------------------------------ row_inv
-// Shared memory: twiddle area | sbuf[2 SP], SP = N + N/16 + 2 | O[2 comps][2 rows][N] (real).
+// The two rows of every (contribution, component) are gathered as 32-byte
+// pieces (4 bins of one row, tiled output layout) with asynchronous copies
+// into a staging buffer; the next gather is issued as soon as the current one
+// has been read into registers, so it overlaps the inverse transform.
+// Shared memory: twiddle area | stage[2 rows][N/4 + 1][4] | sbuf[2 SP] | O[2 comps][2 rows][N].
 template <typename T>
 __global__ void __launch_bounds__(512) k_row_inv16(SolveArgs<T> a)
 {
     using C = typename Cx<T>::C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = a.N, Q = N >> 4, SP = N + Q + 2, P = 2 * N;
+    const int N = a.N, Q = N >> 4, SP = N + Q + 2, P = 2 * N, G = N / 4 + 1;
     C *tw = reinterpret_cast<C *>(smem_raw);
-    C *sbuf = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
+    C *stg = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));  // [row][G][4]
+    C *sbuf = stg + 2 * 4 * G;
     T *O = reinterpret_cast<T *>(sbuf + 2 * SP);
     const int tl = blockIdx.y;
     const int j0 = 2 * blockIdx.x, j1 = j0 + 1;
@@ -505,54 +510,72 @@ __global__ void __launch_bounds__(512) k_row_inv16(SolveArgs<T> a)
     Fft16Plan pl;
     pl.init(N, a.logN);
     const TwLayout twl = tw_layout(pl.twlen, N);
-    cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
-    cp_commit();
-    for (int i = t; i < 4 * N; i += blockDim.x)
-        O[i] = T(0);
-    cp_wait<0>();
-    __syncthreads();
-    for (int c = a.contrib_begin[tl]; c < a.contrib_begin[tl + 1]; ++c) {
-        const RowContrib rc = a.contribs[c];
+    const int c0 = a.contrib_begin[tl], c1 = a.contrib_begin[tl + 1];
+    const int nitems = 2 * (c1 - c0);  // (contribution, component)
+
+    // gather item k: rows j0 and j1 of component k % 2 of contribution c0 + k / 2
+    auto issue = [&](int k) {
+        const RowContrib rc = a.contribs[c0 + k / 2];
+        const int comp = k & 1;
         const ColOutput oa = a.outs[rc.out_base + (j0 % rc.m) * rc.m];
         const ColOutput ob = a.outs[rc.out_base + (j1 % rc.m) * rc.m];
         const int ra = j0 / rc.m, rb = j1 / rc.m;
+        constexpr int PG = 4 * (int)sizeof(C) / 16;  // 16-byte pieces per group of 4 bins
+        constexpr int EP = 16 / (int)sizeof(C);      // bins per piece
+        for (int q = t; q < 2 * G * PG; q += blockDim.x) {
+            const int row = q / (G * PG), rem = q - row * G * PG, g = rem / PG, piece = rem - g * PG;
+            const ColOutput &o = row ? ob : oa;
+            const C *src = a.bwd + o.off + bwd_index(N, o.rows, comp, 4 * g, row ? rb : ra) + piece * EP;
+            cp16(stg + ((size_t)row * G + g) * 4 + piece * EP, src);
+        }
+    };
+    cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
+    if (nitems > 0)
+        issue(0);
+    cp_commit();
+    for (int i = t; i < 4 * N; i += blockDim.x)
+        O[i] = T(0);
+    for (int k = 0; k < nitems; ++k) {
+        const RowContrib rc = a.contribs[c0 + k / 2];
+        const int comp = k & 1;
         const int nout = N / rc.m;
-        const C *ya0 = a.bwd + oa.off + ra, *yb0 = a.bwd + ob.off + rb;
-        for (int comp = 0; comp < 2; ++comp) {
-            const C *ya = ya0 + (size_t)comp * (N + 1) * oa.rows;
-            const C *yb = yb0 + (size_t)comp * (N + 1) * ob.rows;
-            C v[16];
-            if (active) {
+        cp_wait<0>();
+        __syncthreads();
+        C v[16];
+        if (active) {
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int kx = 2 * (j + u * Q) + b;
-                    const int k2 = kx <= N ? kx : P - kx;
-                    const C A = ya[(size_t)k2 * oa.rows], B = yb[(size_t)k2 * ob.rows];
-                    // Z = A + iB, from the stored half (kx <= N) or its conjugate mirror
-                    v[u] = kx <= N ? hmk<C>(A.x - B.y, A.y + B.x) : hmk<C>(A.x + B.y, B.x - A.y);
-                }
+            for (int u = 0; u < 16; ++u) {
+                const int kx = 2 * (j + u * Q) + b;
+                const int k2 = kx <= N ? kx : P - kx;
+                const C A = stg[k2], B = stg[4 * G + k2];
+                // Z = A + iB, from the stored half (kx <= N) or its conjugate mirror
+                v[u] = kx <= N ? hmk<C>(A.x - B.y, A.y + B.x) : hmk<C>(A.x + B.y, B.x - A.y);
             }
-            fft16_block<C, true>(v, sbuf, b, SP, j, active, pl, tw);
-            __syncthreads();
-            if (active && b == 1) {
+        }
+        __syncthreads();  // the stage has been read
+        if (k + 1 < nitems)
+            issue(k + 1);
+        cp_commit();
+        fft16_block<C, true>(v, sbuf, b, SP, j, active, pl, tw);
+        __syncthreads();
+        if (active && b == 1) {
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int n = j + u * Q;
-                    sbuf[pad16(n)] = hmulc(v[u], twist(tw, twl, j, u));
-                }
+            for (int u = 0; u < 16; ++u) {
+                const int n = j + u * Q;
+                sbuf[pad16(n)] = hmulc(v[u], twist(tw, twl, j, u));
             }
-            __syncthreads();
-            if (active && b == 0) {
-                T *Oc = O + comp * 2 * N;
+        }
+        __syncthreads();
+        if (active && b == 0) {
+            T *Oc = O + comp * 2 * N;
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int n = j + u * Q;
-                    if (n < nout) {
-                        const C y = hadd(v[u], sbuf[pad16(n)]);
-                        const int i = rc.m * n + rc.px;
-                        Oc[i] += y.x;
-                        Oc[N + i] += y.y;
-                    }
+            for (int u = 0; u < 16; ++u) {
+                const int n = j + u * Q;
+                if (n < nout) {
+                    const C y = hadd(v[u], sbuf[pad16(n)]);
+                    const int i = rc.m * n + rc.px;
+                    Oc[i] += y.x;
+                    Oc[N + i] += y.y;
                 }
             }
         }
@@ -598,7 +621,8 @@ template <typename T>
 static size_t smem_inv16(int N)
 {
     using C = typename Cx<T>::C;
-    return tw_bytes<C>(tw_entries_for<T>(N)) + 2 * (size_t)(N + N / 16 + 2) * sizeof(C) + 4 * (size_t)N * sizeof(T);
+    return tw_bytes<C>(tw_entries_for<T>(N)) + 2 * 4 * (size_t)(N / 4 + 1) * sizeof(C) +
+           2 * (size_t)(N + N / 16 + 2) * sizeof(C) + 4 * (size_t)N * sizeof(T);
 }
 
 template <typename T>
