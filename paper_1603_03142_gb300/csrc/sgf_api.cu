@@ -193,7 +193,7 @@ void build_lists_merged(sgf_plan *p)
     o.in_count = 1;
     o.off = 0;
     p->outs.push_back(o);
-    p->bwd_elems = 2 * (size_t)(N + 4) * N;
+    p->bwd_elems = 2 * (size_t)(N + 1) * N;
     ColInput ci{};
     ci.slab = 0;
     ci.kind = SPEC_MERGED;
@@ -271,7 +271,7 @@ void build_lists(sgf_plan *p)
         o.in_begin = (int)p->ins.size();
         o.in_count = 0;
         o.off = p->bwd_elems;
-        p->bwd_elems += 2 * (size_t)(N + 4) * rows;
+        p->bwd_elems += 2 * (size_t)(N + 1) * rows;
         p->outs.push_back(o);
         return (int)p->outs.size() - 1;
     };
@@ -595,17 +595,19 @@ sgf_status solve_impl(sgf_plan *p, const void *const *sigma, void *const *fx, vo
     cudaError_t e;
     if ((ms = mark(p, st)) != SGF_OK)
         return ms;
-    e = p->merged ? launch_row_fwd_merged<T>(a, st) : launch_row_fwd16<T>(a, (int)p->items.size(), st);
+    e = p->merged ? launch_pass_n<T>(PASS_ROW_FWD_M, p->logN, a, 0, st)
+                  : launch_pass_n<T>(PASS_ROW_FWD, p->logN, a, (int)p->items.size(), st);
     if (e != cudaSuccess)
         return cuda_fail(e, "row_fwd launch");
     if ((ms = mark(p, st)) != SGF_OK)
         return ms;
-    e = p->merged ? launch_col_merged<T>(a, st) : launch_col16<T>(a, (int)p->outs.size(), st);
+    e = p->merged ? launch_pass_n<T>(PASS_COL_M, p->logN, a, 1, st)
+                  : launch_pass_n<T>(PASS_COL, p->logN, a, (int)p->outs.size(), st);
     if (e != cudaSuccess)
         return cuda_fail(e, "col launch");
     if ((ms = mark(p, st)) != SGF_OK)
         return ms;
-    if ((e = launch_row_inv16<T>(a, st)) != cudaSuccess)
+    if ((e = launch_pass_n<T>(PASS_ROW_INV, p->logN, a, L, st)) != cudaSuccess)
         return cuda_fail(e, "row_inv launch");
     if ((ms = mark(p, st)) != SGF_OK)
         return ms;
@@ -693,11 +695,6 @@ sgf_status sgf_plan_create_ex(const sgf_nest_desc *desc, sgf_precision precision
         return cuda_fail(e, "cudaGetDevice");
     }
     build_lists(p);
-    e = precision == SGF_FP64 ? solve16_init<double>() : solve16_init<float>();
-    if (e != cudaSuccess) {
-        delete p;
-        return cuda_fail(e, "solve kernels init");
-    }
     s = precision == SGF_FP64 ? build_spectra<double>(p) : build_spectra<float>(p);
     if (s == SGF_OK)
         s = plan_alloc_owned(p);

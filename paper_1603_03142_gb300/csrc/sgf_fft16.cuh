@@ -288,4 +288,138 @@ __device__ __forceinline__ void fft16_block(C *v, C *sbuf, int s, int SP, int j,
 }
 #endif
 
+
+// ---------------------------------------------------------------------------
+// Compile-time engine: the same transform with N a template constant, so every
+// stride, radix, twiddle-table offset and padded index folds at compile time.
+template <int LOGN>
+struct F16 {
+    static constexpr int N = 1 << LOGN;
+    static constexpr int Q = N >> 4;
+    static constexpr int S16 = LOGN >> 2;
+    static constexpr int RL = 1 << (LOGN & 3);
+    static constexpr int NST = S16 + (RL > 1 ? 1 : 0);
+    static constexpr int radix(int st) { return st < S16 ? 16 : RL; }
+    static constexpr int ns(int st)
+    {
+        int n = 1;
+        for (int s = 0; s < st; ++s)
+            n *= radix(s);
+        return n;
+    }
+    static constexpr int tsize(int st)
+    {
+        return st == 0 ? 0 : (ns(st) >= 256 ? (radix(st) - 1) * (16 + ns(st) / 16) : (radix(st) - 1) * ns(st));
+    }
+    static constexpr int twoff(int st)
+    {
+        int o = 0;
+        for (int s = 1; s < st; ++s)
+            o += tsize(s);
+        return o;
+    }
+    static constexpr int twlen = twoff(NST);
+};
+
+template <typename C, int R, int NS>
+SGF_HD C stage_tw(const C *tws, int r, int k)
+{
+    if constexpr (NS < 256) {
+        return tws[(r - 1) * NS + k];
+    } else {
+        const C a = tws[(r - 1) * 16 + (k & 15)];
+        const C b = tws[(R - 1) * 16 + (r - 1) * (NS >> 4) + (k >> 4)];
+        return hmul(a, b);
+    }
+}
+
+template <typename C, bool INV, int N, int R, int NS, int QB>
+SGF_HD void stage_small_ct(C *v, int j, const C *tws)
+{
+    if constexpr (QB < 16 / R) {
+        constexpr int S = 16 / R;
+        if constexpr (NS > 1) {
+            const int k = (j + QB * (N / 16)) & (NS - 1);
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const C w = stage_tw<C, R, NS>(tws, r, k);
+                v[QB + r * S] = INV ? hmulc(v[QB + r * S], w) : hmul(v[QB + r * S], w);
+            }
+        }
+        hdft_small<C, INV, R, QB>(v);
+        stage_small_ct<C, INV, N, R, NS, QB + 1>(v, j, tws);
+    }
+}
+
+// Arithmetic of stage ST on one slot.
+template <typename C, bool INV, int LOGN, int ST>
+SGF_HD void stage_ct(C *v, int j, const C *tw)
+{
+    using P = F16<LOGN>;
+    constexpr int R = P::radix(ST), NS = P::ns(ST);
+    const C *tws = tw + P::twoff(ST);
+    if constexpr (R == 16) {
+        if constexpr (NS > 1) {
+            const int k = j & (NS - 1);
+#pragma unroll
+            for (int r = 1; r < 16; ++r) {
+                const C w = stage_tw<C, 16, NS>(tws, r, k);
+                v[r] = INV ? hmulc(v[r], w) : hmul(v[r], w);
+            }
+        }
+        hdft16<C, INV>(v);
+    } else {
+        stage_small_ct<C, INV, P::N, R, NS, 0>(v, j, tws);
+    }
+}
+
+#ifdef __CUDACC__
+// Stages ST.. of the block transform (see fft16_block); B sequences per slot
+// (B = 1 or 2: a thread may carry the same slot of two sequences, which then
+// share the barriers), sequence b at sbuf + b * SP.
+template <typename C, bool INV, int LOGN, int B, int ST>
+__device__ __forceinline__ void fft_stages(C (*v)[16], C *sbuf, int SP, int j, bool active, const C *tw)
+{
+    using P = F16<LOGN>;
+    if constexpr (ST < P::NST) {
+        constexpr int Q = P::Q, NS = P::ns(ST);
+        if constexpr (ST > 0) {
+            __syncthreads();  // previous stage's stores are visible
+            if (active) {
+#pragma unroll
+                for (int bb = 0; bb < B; ++bb)
+#pragma unroll
+                    for (int u = 0; u < 16; ++u)
+                        v[bb][u] = sbuf[bb * SP + pad16(j + u * Q)];
+            }
+        }
+        if (active) {
+#pragma unroll
+            for (int bb = 0; bb < B; ++bb)
+                stage_ct<C, INV, LOGN, ST>(v[bb], j, tw);
+        }
+        if constexpr (ST + 1 < P::NST) {
+            __syncthreads();  // every thread has read this stage's inputs
+            if (active) {
+                const int k = j & (NS - 1);
+                const int base = (j - k) * 16 + k;
+#pragma unroll
+                for (int bb = 0; bb < B; ++bb)
+#pragma unroll
+                    for (int r = 0; r < 16; ++r)
+                        sbuf[bb * SP + pad16(base + r * NS)] = v[bb][r];
+            }
+        }
+        fft_stages<C, INV, LOGN, B, ST + 1>(v, sbuf, SP, j, active, tw);
+    }
+}
+
+// Block-wide transform, compile-time N: as fft16_block, for B slots per thread.
+template <typename C, bool INV, int LOGN, int B = 1>
+__device__ __forceinline__ void fft_ct(C (*v)[16], C *sbuf, int SP, int j, bool active, const C *tw)
+{
+    fft_stages<C, INV, LOGN, B, 0>(v, sbuf, SP, j, active, tw);
+}
+#endif
+
 }  // namespace sgf

@@ -1,0 +1,7 @@
+// sgf_inst_11.cu -- transform-pass instances for N = 2048.
+#include "sgf_kernels.cuh"
+
+namespace sgf {
+template cudaError_t launch_pass<float, 11>(int, const SolveArgs<float> &, int, cudaStream_t);
+template cudaError_t launch_pass<double, 11>(int, const SolveArgs<double> &, int, cudaStream_t);
+}  // namespace sgf

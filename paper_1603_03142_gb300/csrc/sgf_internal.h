@@ -19,9 +19,9 @@
 //   dx, dy the per-cell differences (slope times cell size).  Layout
 //   [field 0..2][kx 0..N][row 0..rows) of complex, rows = N/m.
 // Column output: one column-transformed, multiplied, inverse-column-transformed
-//   result, fields (Fx, Fy).  Layout [field 0..1][kx/4][row 0..rows_out)[kx%4]
-//   (kx padded to N + 4): the inverse row pass then reads 4 bins of a row as
-//   one 32-byte piece (bwd_index).
+//   result, fields (Fx, Fy).  Layout [field 0..1][kx 0..N][row 0..rows_out)
+//   (bwd_index); the column pass writes whole columns, the inverse row pass
+//   gathers two adjacent rows of a bin as one 16-byte piece.
 // Kernel spectra: 6 tables per set in the order
 //   (K0x, Kxx, Kxy, K0y, Kyx, Kyy) = (x-force from sigma, dx, dy;
 //   y-force from sigma, dx, dy), already divided by P^2.
@@ -48,7 +48,7 @@ enum SpecKind : int { SPEC_QUARTER = 0, SPEC_FULL = 1, SPEC_MERGED = 2 };
 // Element (comp, kx, row) of a column output with `rows` rows (complex units).
 inline __host__ __device__ size_t bwd_index(int N, int rows, int comp, int kx, int row)
 {
-    return (size_t)comp * (N + 4) * rows + ((size_t)(kx >> 2) * rows + row) * 4 + (kx & 3);
+    return ((size_t)comp * (N + 1) + kx) * rows + row;
 }
 
 // Device status bits of a plan (sgf_plan_check).
@@ -57,8 +57,8 @@ enum : int { STATUS_RIM_NONZERO = 1 };
 // A quarter-stored spectrum row holds ky = 0..N split by parity: even ky
 // (0, 2, .., N) at [0, N/2 + 1), odd ky (1, 3, .., N-1) at [N/2 + 4, N + 4);
 // each half is padded to N/2 + 4 reals so it starts on a 16-byte boundary.
-inline __host__ __device__ int quarter_half(int N) { return N / 2 + 4; }
-inline __host__ __device__ int quarter_stride(int N) { return 2 * quarter_half(N); }
+constexpr __host__ __device__ int quarter_half(int N) { return N / 2 + 4; }
+constexpr __host__ __device__ int quarter_stride(int N) { return 2 * quarter_half(N); }
 
 struct FwdSlab {
     int level;        // source level
@@ -148,18 +148,11 @@ struct GenSet {
 template <typename T>
 cudaError_t launch_restrict(const T *fine, T *coarse, const T *coarse_in, int N, int ox, int oy,
                             cudaStream_t st);
+// Transform passes of a solve (sgf_kernels.cuh); count = work items (row_fwd),
+// outputs (col) or levels (row_inv).
+enum : int { PASS_ROW_FWD = 0, PASS_COL = 1, PASS_ROW_INV = 2, PASS_ROW_FWD_M = 3, PASS_COL_M = 4 };
 template <typename T>
-cudaError_t launch_row_fwd16(const SolveArgs<T> &a, int n_items, cudaStream_t st);
-template <typename T>
-cudaError_t launch_col16(const SolveArgs<T> &a, int n_outputs, cudaStream_t st);
-template <typename T>
-cudaError_t launch_row_inv16(const SolveArgs<T> &a, cudaStream_t st);
-template <typename T>
-cudaError_t solve16_init();
-template <typename T>
-cudaError_t launch_row_fwd_merged(const SolveArgs<T> &a, cudaStream_t st);
-template <typename T>
-cudaError_t launch_col_merged(const SolveArgs<T> &a, cudaStream_t st);
+cudaError_t launch_pass_n(int pass, int logN, const SolveArgs<T> &a, int count, cudaStream_t st);
 
 // Build the spectra of one set into spec (element type T: float or double).
 // work_tables: 6*P*P doubles; work_half: 6*(N+1)*P double2.

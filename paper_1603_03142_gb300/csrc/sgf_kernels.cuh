@@ -1,0 +1,702 @@
+// sgf_kernels.cuh -- solve kernels on the register-resident radix-16 FFT,
+// templated on log2(N) so that every stride and index folds at compile time.
+// Instantiated once per N by sgf_inst_<logN>.cu; dispatched by sgf_dispatch.cu.
+//
+// Every P = 2N point transform of the method splits into two N-point "parity
+// halves" (even bins: x[n]; odd bins: x[n] W_P^n).  One slot of 16 values per
+// thread and per half; a CTA holds both halves of one row pair (row passes),
+// or one half of one column (column passes: two CTAs per column in a cluster,
+// the odd half folded into the even one through distributed shared memory).
+// Operands are staged in shared memory with asynchronous copies (cp.async,
+// 16-byte chunks) so that loads overlap transforms; twiddles live in shared
+// memory (sgf_fft16.cuh, TwLayout).
+//
+//  k_row_fwd   : sigma rows -> (sigma, dx, dy) with the slope rule and the
+//                covered-cell mask, Case-2 phase gather, two rows per complex
+//                transform, Hermitian unpack, transposed store.
+//  k_col       : per (column, parity half): forward column transforms of all
+//                inputs and fields, spectral multiply-accumulate in registers
+//                (the sums of products of Sec. 2.2), inverse transforms.
+//  k_row_inv   : per row pair of a target level: Hermitian extension, inverse
+//                row transforms of every contributing output, Case-3 phase
+//                interleave, covered cells zeroed, Fx/Fy stored.
+//  k_row_fwd_m,
+//  k_col_m     : the SGF_PLAN_ZERO_RIM variants (sigma alone, merged spectra).
+#pragma once
+#include <atomic>
+#include <cooperative_groups.h>
+
+#include "sgf_fft16.cuh"
+#include "sgf_internal.h"
+
+namespace sgf {
+
+namespace cg = cooperative_groups;
+
+template <typename T> struct Cx;
+template <> struct Cx<float> { using C = float2; using C2 = float4; };
+template <> struct Cx<double> { using C = double2; using C2 = double4_32a; };
+
+// ------------------------------------------------------------ async copies
+__device__ __forceinline__ void cp16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp8(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory"); }
+
+// Whole block: copy `bytes` (a multiple of 16, both ends 16-byte aligned).
+__device__ __forceinline__ void cp_block(void *smem, const void *gmem, size_t bytes)
+{
+    for (size_t o = (size_t)threadIdx.x * 16; o < bytes; o += (size_t)blockDim.x * 16)
+        cp16(static_cast<char *>(smem) + o, static_cast<const char *>(gmem) + o);
+}
+
+// Twiddle area bytes in shared memory (a 16-byte multiple).
+template <typename C>
+__host__ __device__ __forceinline__ size_t tw_bytes(int entries)
+{
+    return (((size_t)entries * sizeof(C)) + 15) & ~(size_t)15;
+}
+
+// W_P^n for n = j + u N/16: W_P^j W_32^u from the shared twiddle area.
+template <typename C>
+__device__ __forceinline__ C twist(const C *tw, const TwLayout &tl, int j, int u)
+{
+    return hmul(tw[tl.base + j], tw[tl.w32 + u]);
+}
+
+// Sequence stride (complex) of a column-pass exchange buffer: N + N/16 rounded
+// up so the next buffer starts on a 16-byte boundary.
+template <typename C>
+__host__ __device__ constexpr int col_sp(int N)
+{
+    return (int)(((((size_t)(N + N / 16) * sizeof(C)) + 15) & ~(size_t)15) / sizeof(C));
+}
+
+template <typename T>
+__device__ __forceinline__ bool covered(const SolveArgs<T> &a, int s, int j, int i)
+{
+    const int ox = a.child_ox[s];
+    if (ox < 0)
+        return false;
+    const int oy = a.child_oy[s], half = a.N >> 1;
+    return i >= ox && i < ox + half && j >= oy && j < oy + half;
+}
+
+template <int LOGN>
+struct KShape {
+    static constexpr int N = 1 << LOGN, Q = N >> 4;
+    static constexpr int ROW_THREADS = 2 * Q < 32 ? 32 : 2 * Q;  // both parity halves
+    static constexpr int COL_THREADS = Q < 32 ? 32 : Q;          // one parity half
+    static constexpr int SP_ROW = N + Q + 2;  // pad keeps the halves on different banks in the unpack
+};
+
+// ------------------------------------------------------------------ row_fwd
+// Shared memory: twiddle area | sigma rows[6][N] | sbuf[2 SP_ROW].
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd(SolveArgs<T> a)
+{
+    using C = typename Cx<T>::C;
+    using C2 = typename Cx<T>::C2;
+    using K = KShape<LOGN>;
+    constexpr int N = K::N, Q = K::Q, SP = K::SP_ROW;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    T *srow = reinterpret_cast<T *>(smem_raw + tw_bytes<C>(a.tw_entries));  // rows ja-1, ja, ja+1, jb-1, jb, jb+1
+    C *sbuf = reinterpret_cast<C *>(srow + 6 * N);
+    const FwdItem item = a.fwd_items[blockIdx.x];
+    const FwdSlab sl = a.slabs[item.slab];
+    const int rows = sl.rows, r0 = 2 * item.row_pair;
+    const int ja = sl.m * r0 + sl.py, jb = sl.m * (r0 + 1) + sl.py;
+    const T *src = a.src[sl.level];
+    cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const int jr = min(max((q < 3 ? ja : jb) + (q % 3) - 1, 0), N - 1);
+        cp_block(srow + q * N, src + (size_t)jr * N, (size_t)N * sizeof(T));
+    }
+    cp_commit();
+    const int t = threadIdx.x;
+    const bool active = t < 2 * Q;
+    const int b = active ? t / Q : 0, j = active ? t - b * Q : 0;
+    const TwLayout tl = tw_layout(F16<LOGN>::twlen, N);
+    cp_wait<0>();
+    __syncthreads();
+    C2 *out = reinterpret_cast<C2 *>(a.fwd + sl.off);  // pairs of rows (r0, r0+1)
+    for (int f = 0; f < 3; ++f) {
+        C v[1][16];
+        if (active) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int c = j + u * Q;
+                T fv[2] = {T(0), T(0)};
+                if (c < rows) {
+                    const int i = sl.m * c + sl.px;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int jj = h ? jb : ja;
+                        const T *r = srow + (3 * h + 1) * N;  // row jj; rows jj -+ 1 sit beside it
+                        if (covered(a, sl.level, jj, i))
+                            continue;
+                        if (f == 0) {
+                            fv[h] = r[i];
+                        } else if (f == 1) {
+                            const int il = i == 0 ? 0 : i - 1, ir = i == N - 1 ? N - 1 : i + 1;
+                            const T d = r[ir] - r[il];
+                            fv[h] = (ir - il == 2) ? T(0.5) * d : d;
+                        } else {
+                            const T *rl = jj == 0 ? r : r - N;
+                            const T *rr = jj == N - 1 ? r : r + N;
+                            const T d = rr[i] - rl[i];
+                            fv[h] = (jj == 0 || jj == N - 1) ? d : T(0.5) * d;
+                        }
+                    }
+                }
+                C z = hmk<C>(fv[0], fv[1]);
+                if (b)
+                    z = hmul(z, twist(tw, tl, j, u));
+                v[0][u] = z;
+            }
+        }
+        fft_ct<C, false, LOGN>(v, sbuf + b * SP, SP, j, active, tw);
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+                sbuf[b * SP + pad16(j + u * Q)] = v[0][u];
+        }
+        __syncthreads();
+        // X_a = (Z + conj Z~)/2, X_b = (Z - conj Z~)/(2i); Z~ = bin -kx, same parity half
+        for (int kx = t; kx <= N; kx += K::ROW_THREADS) {
+            const int bb = kx & 1, k = kx >> 1;
+            const int km = (N - bb - k) & (N - 1);
+            const C Z = sbuf[bb * SP + pad16(k)];
+            const C Zm = sbuf[bb * SP + pad16(km)];
+            C2 o;
+            o.x = T(0.5) * (Z.x + Zm.x);
+            o.y = T(0.5) * (Z.y - Zm.y);
+            o.z = T(0.5) * (Z.y + Zm.y);
+            o.w = T(-0.5) * (Z.x - Zm.x);
+            out[(((size_t)f * (N + 1) + kx) * rows + r0) >> 1] = o;
+        }
+    }
+}
+
+// --------------------------------------------------------------------- col
+// Shared memory: twiddle area | sbuf[SPC] | stage[2] { column[N] (complex),
+// this parity's half of the two spectrum rows, 2 x (N/2 + 4) reals }.  The
+// dual inverse transform uses sbuf and the stages as two sequence buffers, and
+// the fold of the odd half reuses them afterwards.
+template <typename T, int LOGN>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_THREADS) k_col(SolveArgs<T> a)
+{
+    using C = typename Cx<T>::C;
+    using K = KShape<LOGN>;
+    constexpr int N = K::N, Q = K::Q, P = 2 * N, QS = quarter_stride(N), HQ = quarter_half(N);
+    constexpr int SPC = col_sp<C>(N);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *sbuf = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
+    unsigned char *stage_base = reinterpret_cast<unsigned char *>(sbuf + SPC);
+    constexpr size_t stage_bytes = (size_t)N * sizeof(C) + 2 * (size_t)HQ * sizeof(T);
+    cg::cluster_group cluster = cg::this_cluster();
+    const int b = (int)cluster.block_rank();  // parity half
+    const int kx = blockIdx.x >> 1;
+    const ColOutput o = a.outs[blockIdx.y];
+    const int t = threadIdx.x;
+    const bool active = t < Q;
+    const int j = active ? t : 0;
+    const int nitems = 3 * o.in_count;
+    const TwLayout tl = tw_layout(F16<LOGN>::twlen, N);
+
+    auto issue = [&](int k) {
+        unsigned char *st = stage_base + (size_t)(k & 1) * stage_bytes;
+        const ColInput ci = a.ins[o.in_begin + k / 3];
+        const FwdSlab sl = a.slabs[ci.slab];
+        const int f = k % 3;
+        cp_block(st, a.fwd + sl.off + ((size_t)f * (N + 1) + kx) * sl.rows, (size_t)sl.rows * sizeof(C));
+        if (ci.kind == SPEC_QUARTER) {
+            const T *sp = reinterpret_cast<const T *>(a.spec) + ci.spec_off;
+            T *dst = reinterpret_cast<T *>(st + (size_t)N * sizeof(C));
+            cp_block(dst, sp + ((size_t)f * (N + 1) + kx) * QS + b * HQ, (size_t)HQ * sizeof(T));
+            cp_block(dst + HQ, sp + ((size_t)(3 + f) * (N + 1) + kx) * QS + b * HQ, (size_t)HQ * sizeof(T));
+        }
+    };
+    cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
+    issue(0);
+    cp_commit();
+    if (nitems > 1)
+        issue(1);
+    cp_commit();
+
+    C acc[2][16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        acc[0][u] = hmk<C>(T(0), T(0));
+        acc[1][u] = hmk<C>(T(0), T(0));
+    }
+    for (int k = 0; k < nitems; ++k) {
+        cp_wait<1>();
+        __syncthreads();
+        const unsigned char *st = stage_base + (size_t)(k & 1) * stage_bytes;
+        const C *col = reinterpret_cast<const C *>(st);
+        const T *spx = reinterpret_cast<const T *>(st + (size_t)N * sizeof(C));
+        const ColInput ci = a.ins[o.in_begin + k / 3];
+        const int rows = a.slabs[ci.slab].rows;
+        const int f = k % 3;
+        C v[1][16];
+        if (active) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int n = j + u * Q;
+                C x = hmk<C>(T(0), T(0));
+                if (n < rows) {
+                    x = col[n];
+                    if (b)
+                        x = hmul(x, twist(tw, tl, j, u));
+                }
+                v[0][u] = x;
+            }
+        }
+        fft_ct<C, false, LOGN>(v, sbuf, SPC, j, active, tw);
+        if (active) {
+            if (ci.kind == SPEC_QUARTER) {
+                // K0x, K0y imaginary (stored Im), the rest real; bins above N read the
+                // quarter at P - ky with the table's ky parity: + K0x Kxx Kyy, - Kxy K0y Kyx.
+                // Bin ky = 2k' + b sits at k' of this parity's half row; its mirror
+                // P - ky sits at N - k' - b.
+                const T mx = (f == 2) ? T(-1) : T(1);
+                const T my = (f == 2) ? T(1) : T(-1);
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int kp = j + u * Q;
+                    const bool hi = 2 * kp + b > N;
+                    const int q = hi ? N - kp - b : kp;
+                    const T rx = spx[q] * (hi ? mx : T(1));
+                    const T ry = spx[HQ + q] * (hi ? my : T(1));
+                    C tx = hmk<C>(rx * v[0][u].x, rx * v[0][u].y), ty = hmk<C>(ry * v[0][u].x, ry * v[0][u].y);
+                    if (f == 0) {
+                        tx = hmk<C>(-tx.y, tx.x);
+                        ty = hmk<C>(-ty.y, ty.x);
+                    }
+                    acc[0][u] = hadd(acc[0][u], tx);
+                    acc[1][u] = hadd(acc[1][u], ty);
+                }
+            } else {
+                const C *sx = reinterpret_cast<const C *>(a.spec) + ci.spec_off + ((size_t)f * (N + 1) + kx) * P;
+                const C *sy = reinterpret_cast<const C *>(a.spec) + ci.spec_off + ((size_t)(3 + f) * (N + 1) + kx) * P;
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int ky = 2 * (j + u * Q) + b;
+                    acc[0][u] = hadd(acc[0][u], hmul(__ldg(sx + ky), v[0][u]));
+                    acc[1][u] = hadd(acc[1][u], hmul(__ldg(sy + ky), v[0][u]));
+                }
+            }
+        }
+        __syncthreads();  // stage (k & 1) consumed by every thread
+        if (k + 2 < nitems)
+            issue(k + 2);
+        cp_commit();
+    }
+    cp_wait<0>();
+    // inverse column transforms of Fx^ and Fy^ together; y[n] = even[n] + W_P^{-n} odd[n]
+    fft_ct<C, true, LOGN, 2>(acc, sbuf, SPC, j, active, tw);
+    C *fold = sbuf;  // 2N complex over sbuf and the stages
+    cluster.sync();
+    if (b == 1 && active) {
+        C *dst = cluster.map_shared_rank(fold, 0);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int n = j + u * Q;
+            const C w = twist(tw, tl, j, u);
+            dst[n] = hmulc(acc[0][u], w);
+            dst[N + n] = hmulc(acc[1][u], w);
+        }
+    }
+    cluster.sync();
+    if (b == 0 && active) {
+        C *dst = a.bwd + o.off;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int n = j + u * Q;
+            if (n < o.rows) {
+                dst[bwd_index(N, o.rows, 0, kx, n)] = hadd(acc[0][u], fold[n]);
+                dst[bwd_index(N, o.rows, 1, kx, n)] = hadd(acc[1][u], fold[N + n]);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ row_inv
+// Shared memory: twiddle area | stage[N + 1][2 rows] | sbuf[2 SP_ROW] | O[2 comps][2 rows][N].
+// The two rows of every (contribution, component) are gathered with
+// asynchronous copies -- 16 bytes per bin when both rows are adjacent rows of
+// one output, 8 bytes otherwise -- and the next gather is issued as soon as
+// the current one has been read into registers, so it overlaps the transform.
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_inv(SolveArgs<T> a)
+{
+    using C = typename Cx<T>::C;
+    using K = KShape<LOGN>;
+    constexpr int N = K::N, Q = K::Q, SP = K::SP_ROW, P = 2 * N;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *stg = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));  // [kx][2]
+    C *sbuf = stg + 2 * (N + 1) + ((2 * (N + 1) * sizeof(C)) % 16 ? 1 : 0);
+    T *O = reinterpret_cast<T *>(sbuf + 2 * SP);
+    const int tl = blockIdx.y;
+    const int j0 = 2 * blockIdx.x, j1 = j0 + 1;
+    const int t = threadIdx.x;
+    const bool active = t < 2 * Q;
+    const int b = active ? t / Q : 0, j = active ? t - b * Q : 0;
+    const TwLayout twl = tw_layout(F16<LOGN>::twlen, N);
+    const int c0 = a.contrib_begin[tl], c1 = a.contrib_begin[tl + 1];
+    const int nitems = 2 * (c1 - c0);  // (contribution, component)
+
+    auto issue = [&](int k) {
+        const RowContrib rc = a.contribs[c0 + k / 2];
+        const int comp = k & 1;
+        const ColOutput oa = a.outs[rc.out_base + (j0 % rc.m) * rc.m];
+        const ColOutput ob = a.outs[rc.out_base + (j1 % rc.m) * rc.m];
+        const int ra = j0 / rc.m, rb = j1 / rc.m;
+        const C *ba = a.bwd + oa.off + bwd_index(N, oa.rows, comp, 0, ra);
+        const C *bb = a.bwd + ob.off + bwd_index(N, ob.rows, comp, 0, rb);
+        if (rc.m == 1) {  // rows j0, j0 + 1 of one output: one piece per bin
+            constexpr int PG = 2 * (int)sizeof(C) / 16;
+            for (int q = t; q < (N + 1) * PG; q += K::ROW_THREADS) {
+                const int kx = q / PG, piece = q - kx * PG;
+                cp16(stg + 2 * kx + piece * (16 / (int)sizeof(C)), ba + (size_t)kx * oa.rows + piece * (16 / (int)sizeof(C)));
+            }
+        } else {
+            for (int q = t; q < 2 * (N + 1); q += K::ROW_THREADS) {
+                const int kx = q >> 1, row = q & 1;
+                const C *s = row ? bb + (size_t)kx * ob.rows : ba + (size_t)kx * oa.rows;
+                if (sizeof(C) == 8)
+                    cp8(stg + 2 * kx + row, s);
+                else
+                    cp16(stg + 2 * kx + row, s);
+            }
+        }
+    };
+    cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
+    if (nitems > 0)
+        issue(0);
+    cp_commit();
+    for (int i = t; i < 4 * N; i += K::ROW_THREADS)
+        O[i] = T(0);
+    for (int k = 0; k < nitems; ++k) {
+        const RowContrib rc = a.contribs[c0 + k / 2];
+        const int comp = k & 1;
+        const int nout = N / rc.m;
+        cp_wait<0>();
+        __syncthreads();
+        C v[1][16];
+        if (active) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int kx = 2 * (j + u * Q) + b;
+                const int k2 = kx <= N ? kx : P - kx;
+                const C A = stg[2 * k2], B = stg[2 * k2 + 1];
+                // Z = A + iB, from the stored half (kx <= N) or its conjugate mirror
+                v[0][u] = kx <= N ? hmk<C>(A.x - B.y, A.y + B.x) : hmk<C>(A.x + B.y, B.x - A.y);
+            }
+        }
+        __syncthreads();  // the stage has been read
+        if (k + 1 < nitems)
+            issue(k + 1);
+        cp_commit();
+        fft_ct<C, true, LOGN>(v, sbuf + b * SP, SP, j, active, tw);
+        __syncthreads();
+        if (active && b == 1) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int n = j + u * Q;
+                sbuf[pad16(n)] = hmulc(v[0][u], twist(tw, twl, j, u));
+            }
+        }
+        __syncthreads();
+        if (active && b == 0) {
+            T *Oc = O + comp * 2 * N;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int n = j + u * Q;
+                if (n < nout) {
+                    const C y = hadd(v[0][u], sbuf[pad16(n)]);
+                    const int i = rc.m * n + rc.px;
+                    Oc[i] += y.x;
+                    Oc[N + i] += y.y;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    T *fx = a.fx[tl], *fy = a.fy[tl];
+    for (int i = t; i < N; i += K::ROW_THREADS) {
+        const bool ca = covered(a, tl, j0, i), cb = covered(a, tl, j1, i);
+        fx[(size_t)j0 * N + i] = ca ? T(0) : O[i];
+        fx[(size_t)j1 * N + i] = cb ? T(0) : O[N + i];
+        fy[(size_t)j0 * N + i] = ca ? T(0) : O[2 * N + i];
+        fy[(size_t)j1 * N + i] = cb ? T(0) : O[3 * N + i];
+    }
+}
+
+// ------------------------------------------------------------ zero-rim path
+// Forward row pass of a SGF_PLAN_ZERO_RIM plan: the rows of sigma alone (the
+// slopes are folded into the merged spectra).  Also verifies the guarantee:
+// the CTAs of rows 0-1 and N-2..N-1 scan their rows, every CTA its cells in
+// columns 0, 1, N-2, N-1; a nonzero value sets STATUS_RIM_NONZERO.
+// Shared memory: twiddle area | sigma rows[2][N] | sbuf[2 SP_ROW].
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd_m(SolveArgs<T> a)
+{
+    using C = typename Cx<T>::C;
+    using C2 = typename Cx<T>::C2;
+    using K = KShape<LOGN>;
+    constexpr int N = K::N, Q = K::Q, SP = K::SP_ROW;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    T *srow = reinterpret_cast<T *>(smem_raw + tw_bytes<C>(a.tw_entries));
+    C *sbuf = reinterpret_cast<C *>(srow + 2 * N);
+    __shared__ int rim_bad;
+    const int r0 = 2 * blockIdx.x;
+    const T *src = a.src[0] + (size_t)r0 * N;
+    cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
+    cp_block(srow, src, 2 * (size_t)N * sizeof(T));
+    cp_commit();
+    const int t = threadIdx.x;
+    if (t == 0)
+        rim_bad = 0;
+    const bool active = t < 2 * Q;
+    const int b = active ? t / Q : 0, j = active ? t - b * Q : 0;
+    const TwLayout tl = tw_layout(F16<LOGN>::twlen, N);
+    cp_wait<0>();
+    __syncthreads();
+    {
+        bool bad = false;
+        if (r0 == 0 || r0 == N - 2) {
+            for (int i = t; i < 2 * N; i += K::ROW_THREADS)
+                bad |= srow[i] != T(0);
+        } else if (t < 8) {
+            const int col = (t & 3) < 2 ? (t & 3) : N - 4 + (t & 3);  // 0, 1, N-2, N-1
+            bad = srow[(t >> 2) * N + col] != T(0);
+        }
+        if (bad)
+            rim_bad = 1;
+    }
+    C v[1][16];
+    if (active) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int c = j + u * Q;
+            C z = hmk<C>(srow[c], srow[N + c]);
+            if (b)
+                z = hmul(z, twist(tw, tl, j, u));
+            v[0][u] = z;
+        }
+    }
+    fft_ct<C, false, LOGN>(v, sbuf + b * SP, SP, j, active, tw);
+    __syncthreads();
+    if (t == 0 && rim_bad)
+        atomicOr(a.status, STATUS_RIM_NONZERO);
+    if (active) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+            sbuf[b * SP + pad16(j + u * Q)] = v[0][u];
+    }
+    __syncthreads();
+    C2 *out = reinterpret_cast<C2 *>(a.fwd);
+    for (int kx = t; kx <= N; kx += K::ROW_THREADS) {
+        const int bb = kx & 1, k = kx >> 1;
+        const int km = (N - bb - k) & (N - 1);
+        const C Z = sbuf[bb * SP + pad16(k)];
+        const C Zm = sbuf[bb * SP + pad16(km)];
+        C2 o;
+        o.x = T(0.5) * (Z.x + Zm.x);
+        o.y = T(0.5) * (Z.y - Zm.y);
+        o.z = T(0.5) * (Z.y + Zm.y);
+        o.w = T(-0.5) * (Z.x - Zm.x);
+        out[((size_t)kx * N + r0) >> 1] = o;
+    }
+}
+
+// Column pass of a SGF_PLAN_ZERO_RIM plan: one forward transform, the two
+// merged spectra (Fx^ = Gx^ sigma^, Fy^ = Gy^ sigma^, both imaginary), one
+// dual inverse transform; parity halves folded through distributed shared
+// memory.  Shared memory: twiddle area | sbuf[SPC] | stage {column[N], this
+// parity's half rows of Gx and Gy}; the dual transform and the fold reuse
+// sbuf + stage.
+template <typename T, int LOGN>
+__global__ void __cluster_dims__(2, 1, 1)
+    __launch_bounds__(KShape<LOGN>::COL_THREADS, sizeof(T) == 4 ? 2 : 1) k_col_m(SolveArgs<T> a)
+{
+    using C = typename Cx<T>::C;
+    using K = KShape<LOGN>;
+    constexpr int N = K::N, Q = K::Q, QS = quarter_stride(N), HQ = quarter_half(N);
+    constexpr int SPC = col_sp<C>(N);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *sbuf = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
+    C *col = sbuf + SPC;
+    T *gsp = reinterpret_cast<T *>(col + N);
+    cg::cluster_group cluster = cg::this_cluster();
+    const int b = (int)cluster.block_rank();
+    const int kx = blockIdx.x >> 1;
+    const int t = threadIdx.x;
+    const bool active = t < Q;
+    const int j = active ? t : 0;
+    const TwLayout tl = tw_layout(F16<LOGN>::twlen, N);
+    const T *spec = reinterpret_cast<const T *>(a.spec);
+    cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
+    cp_block(col, a.fwd + (size_t)kx * N, (size_t)N * sizeof(C));
+    cp_block(gsp, spec + (size_t)kx * QS + b * HQ, (size_t)HQ * sizeof(T));
+    cp_block(gsp + HQ, spec + ((size_t)(N + 1) + kx) * QS + b * HQ, (size_t)HQ * sizeof(T));
+    cp_commit();
+    cp_wait<0>();
+    __syncthreads();
+    C acc[2][16];
+    {
+        C v[1][16];
+        if (active) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                C x = col[j + u * Q];
+                if (b)
+                    x = hmul(x, twist(tw, tl, j, u));
+                v[0][u] = x;
+            }
+        }
+        fft_ct<C, false, LOGN>(v, sbuf, SPC, j, active, tw);
+        if (active) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int kp = j + u * Q;
+                const bool hi = 2 * kp + b > N;
+                const int q = hi ? N - kp - b : kp;
+                const T gx = gsp[q];                           // Gx even in ky
+                const T gy = hi ? -gsp[HQ + q] : gsp[HQ + q];  // Gy odd in ky
+                acc[0][u] = hmk<C>(-gx * v[0][u].y, gx * v[0][u].x);  // i gx v
+                acc[1][u] = hmk<C>(-gy * v[0][u].y, gy * v[0][u].x);
+            }
+        }
+    }
+    fft_ct<C, true, LOGN, 2>(acc, sbuf, SPC, j, active, tw);  // second sequence over the stage
+    C *fold = sbuf;
+    cluster.sync();
+    if (b == 1 && active) {
+        C *dst = cluster.map_shared_rank(fold, 0);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int n = j + u * Q;
+            const C w = twist(tw, tl, j, u);
+            dst[n] = hmulc(acc[0][u], w);
+            dst[N + n] = hmulc(acc[1][u], w);
+        }
+    }
+    cluster.sync();
+    if (b == 0 && active) {
+        C *dst = a.bwd;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int n = j + u * Q;
+            dst[bwd_index(N, N, 0, kx, n)] = hadd(acc[0][u], fold[n]);
+            dst[bwd_index(N, N, 1, kx, n)] = hadd(acc[1][u], fold[N + n]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- launching
+template <typename T, int LOGN>
+struct KSmem {
+    using C = typename Cx<T>::C;
+    static constexpr int N = 1 << LOGN;
+    static size_t tw() { return tw_bytes<C>(tw_layout(F16<LOGN>::twlen, N).entries); }
+    static size_t row_fwd() { return tw() + 6 * (size_t)N * sizeof(T) + 2 * (size_t)KShape<LOGN>::SP_ROW * sizeof(C); }
+    static size_t col()
+    {
+        const size_t stage = (size_t)N * sizeof(C) + 2 * (size_t)quarter_half(N) * sizeof(T);
+        return tw() + (size_t)col_sp<C>(N) * sizeof(C) + 2 * stage;
+    }
+    static size_t row_inv()
+    {
+        return tw() + ((2 * (size_t)(N + 1) * sizeof(C) + 15) & ~(size_t)15) + 2 * (size_t)KShape<LOGN>::SP_ROW * sizeof(C) +
+               4 * (size_t)N * sizeof(T);
+    }
+    static size_t row_fwd_m() { return tw() + 2 * (size_t)N * sizeof(T) + 2 * (size_t)KShape<LOGN>::SP_ROW * sizeof(C); }
+    static size_t col_m()
+    {
+        // sbuf + column + spectrum half rows; at least two exchange buffers (dual inverse) and the 2N fold
+        size_t body = (size_t)col_sp<C>(N) * sizeof(C) + (size_t)N * sizeof(C) + 2 * (size_t)quarter_half(N) * sizeof(T);
+        const size_t need = 2 * (size_t)col_sp<C>(N) * sizeof(C);
+        if (body < need)
+            body = need;
+        if (body < 2 * (size_t)N * sizeof(C))
+            body = 2 * (size_t)N * sizeof(C);
+        return tw() + body;
+    }
+};
+
+// Sets the dynamic shared-memory limit of a kernel once per device.
+template <typename F>
+inline cudaError_t ensure_smem(F *kernel, size_t bytes, std::atomic<unsigned long long> &done)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit)
+        return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+        done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
+
+template <typename T, int LOGN>
+cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t st)
+{
+    using K = KShape<LOGN>;
+    using S = KSmem<T, LOGN>;
+    static std::atomic<unsigned long long> d0{0}, d1{0}, d2{0}, d3{0}, d4{0};
+    cudaError_t e = cudaSuccess;
+    switch (pass) {
+    case PASS_ROW_FWD:
+        if ((e = ensure_smem(k_row_fwd<T, LOGN>, S::row_fwd(), d0)) != cudaSuccess)
+            return e;
+        k_row_fwd<T, LOGN><<<count, K::ROW_THREADS, S::row_fwd(), st>>>(a);
+        break;
+    case PASS_COL:
+        if ((e = ensure_smem(k_col<T, LOGN>, S::col(), d1)) != cudaSuccess)
+            return e;
+        k_col<T, LOGN><<<dim3(2 * (K::N + 1), count), K::COL_THREADS, S::col(), st>>>(a);
+        break;
+    case PASS_ROW_INV:
+        if ((e = ensure_smem(k_row_inv<T, LOGN>, S::row_inv(), d2)) != cudaSuccess)
+            return e;
+        k_row_inv<T, LOGN><<<dim3(K::N / 2, count), K::ROW_THREADS, S::row_inv(), st>>>(a);
+        break;
+    case PASS_ROW_FWD_M:
+        if ((e = ensure_smem(k_row_fwd_m<T, LOGN>, S::row_fwd_m(), d3)) != cudaSuccess)
+            return e;
+        k_row_fwd_m<T, LOGN><<<K::N / 2, K::ROW_THREADS, S::row_fwd_m(), st>>>(a);
+        break;
+    case PASS_COL_M:
+        if ((e = ensure_smem(k_col_m<T, LOGN>, S::col_m(), d4)) != cudaSuccess)
+            return e;
+        k_col_m<T, LOGN><<<2 * (K::N + 1), K::COL_THREADS, S::col_m(), st>>>(a);
+        break;
+    default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace sgf
