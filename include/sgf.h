@@ -178,6 +178,31 @@ sgf_status sgf_plan_profile_read(sgf_plan *plan, sgf_kernel_times *out);
  * next sgf_* call on this thread.  Never NULL. */
 const char *sgf_last_error(void);
 
+/* Scratch limit of sgf_solve_noalloc, in bytes. */
+#define SGF_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* Same result as sgf_solve, but this call allocates nothing -- no cudaMalloc,
+ * cudaFree or allocating library routine -- for callers that cannot allocate
+ * device memory at solve time (code running under an allocator that forbids
+ * new allocations, or inside a region where allocating would break the
+ * caller's own scheduling).  The plan itself (spectra, work lists) must have
+ * been created beforehand, where allocating is allowed.  The solve's
+ * intermediates live in one fixed array of SGF_NOALLOC_SCRATCH_BYTES in the
+ * library's device memory, which every GPU that loads the library holds until
+ * the process exits.  The paper has no counterpart to this entry point.
+ *   - The first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call on a device uses the same array: calls whose work overlaps on
+ *     the GPU (other streams, other host threads) race and corrupt each other's
+ *     results; order them on one stream or synchronise between them.  The
+ *     array keeps the previous call's contents; every solve overwrites all of
+ *     it that it reads, so nothing needs clearing.
+ * Arguments as sgf_solve.  Errors: as sgf_solve; SGF_EUNSUPPORTED when the
+ * plan's intermediates exceed SGF_NOALLOC_SCRATCH_BYTES (one FP32 level of
+ * n = 512 needs 10 MiB and fits; n = 1024 needs 40 MiB and does not). */
+sgf_status sgf_solve_noalloc(sgf_plan *plan, const void *const *sigma, void *const *fx, void *const *fy,
+                             void *stream);
+
 /* Library version string, e.g. "sgf 0.1.0 sm_103a". */
 const char *sgf_version(void);
 

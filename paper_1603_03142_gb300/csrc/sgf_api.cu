@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -654,6 +655,110 @@ sgf_status solve_dispatch(sgf_plan *p, const void *const *sigma, void *const *fx
                                : solve_impl<float>(p, sigma, fx, fy, st);
 }
 
+// ---- allocation-free solve (sgf_solve_noalloc) -----------------------------
+// Scratch of sgf_solve_noalloc: one file-scope device array, shared by every
+// call on a device and held by every device that loads this library.  Host
+// code must not use the symbol as an address; the per-device address comes
+// from cudaGetSymbolAddress (noalloc_scratch_on_current_device).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SGF_NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[64] = {};
+
+// Device address of the scratch array on the current device (looked up once per device).
+sgf_status noalloc_scratch_on_current_device(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64)
+        return fail(SGF_EUNSUPPORTED, "device %d: sgf_solve_noalloc supports devices 0..63", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *ptr = nullptr;
+        if ((e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch)) != cudaSuccess)
+            return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
+        g_noalloc_ptr[dev] = ptr;
+    }
+    *out = g_noalloc_ptr[dev];
+    return SGF_OK;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Bytes of scratch a plan's solve needs: restricted densities, forward and backward intermediates.
+size_t noalloc_bytes(const sgf_plan *p)
+{
+    const size_t Cb = 2 * p->esize;
+    return align256((size_t)(p->L > 1 ? p->L - 1 : 0) * p->N * p->N * p->esize) + align256(p->fwd_elems * Cb) +
+           align256(p->bwd_elems * Cb);
+}
+
+// The solve of solve_impl with its intermediates in `scratch` and without the
+// optional profiling events (it creates nothing).
+template <typename T>
+sgf_status solve_noalloc_impl(sgf_plan *p, const void *const *sigma, void *const *fx, void *const *fy,
+                              cudaStream_t st, unsigned char *scratch)
+{
+    const int N = p->N, L = p->L;
+    const size_t Cb = 2 * p->esize;
+    T *restricted = reinterpret_cast<T *>(scratch);
+    unsigned char *fwd = scratch + align256((size_t)(L > 1 ? L - 1 : 0) * N * N * p->esize);
+    unsigned char *bwd = fwd + align256(p->fwd_elems * Cb);
+    SolveArgs<T> a{};
+    a.N = N;
+    a.logN = p->logN;
+    a.L = L;
+    for (int l = 0; l < kMaxLevels; ++l) {
+        a.child_ox[l] = -1;
+        a.child_oy[l] = -1;
+    }
+    for (int l = 0; l + 1 < L; ++l) {
+        a.child_ox[l] = p->desc.off[l + 1][0];
+        a.child_oy[l] = p->desc.off[l + 1][1];
+    }
+    a.src[L - 1] = static_cast<const T *>(sigma[L - 1]);
+    for (int l = L - 2; l >= 0; --l) {
+        T *dst = restricted + (size_t)l * N * N;
+        cudaError_t e = launch_restrict<T>(a.src[l + 1], dst, static_cast<const T *>(sigma[l]), N,
+                                           p->desc.off[l + 1][0], p->desc.off[l + 1][1], st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "restriction launch");
+        a.src[l] = dst;
+    }
+    for (int l = 0; l < L; ++l) {
+        a.fx[l] = static_cast<T *>(fx[l]);
+        a.fy[l] = static_cast<T *>(fy[l]);
+    }
+    a.fwd = reinterpret_cast<typename SolveArgs<T>::C *>(fwd);
+    a.bwd = reinterpret_cast<typename SolveArgs<T>::C *>(bwd);
+    a.spec = p->spec->dev;
+    a.tw = static_cast<const typename SolveArgs<T>::C *>(p->spec->tw);
+    a.tw_entries = p->spec->tw_entries;
+    a.status = p->d_status;
+    a.slabs = p->d_slabs;
+    a.fwd_items = p->d_items;
+    a.outs = p->d_outs;
+    a.ins = p->d_ins;
+    a.contribs = p->d_contribs;
+    for (int l = 0; l <= L; ++l)
+        a.contrib_begin[l] = p->contrib_begin[l];
+    cudaError_t e = p->merged ? launch_pass_n<T>(PASS_ROW_FWD_M, p->logN, a, 0, st)
+                              : launch_pass_n<T>(PASS_ROW_FWD, p->logN, a, (int)p->items.size(), st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "row_fwd launch");
+    e = p->merged ? launch_pass_n<T>(PASS_COL_M, p->logN, a, 1, st)
+                  : launch_pass_n<T>(PASS_COL, p->logN, a, (int)p->outs.size(), st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "col launch");
+    if ((e = launch_pass_n<T>(PASS_ROW_INV, p->logN, a, L, st)) != cudaSuccess)
+        return cuda_fail(e, "row_inv launch");
+    if ((e = cudaEventRecord(p->done, st)) != cudaSuccess)
+        return cuda_fail(e, "cudaEventRecord(solve completion)");
+    return SGF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -895,6 +1000,27 @@ sgf_status sgf_plan_destroy(sgf_plan *p)
     spectra_release(p->spec);
     delete p;
     return SGF_OK;
+}
+
+sgf_status sgf_solve_noalloc(sgf_plan *p, const void *const *sigma, void *const *fx, void *const *fy,
+                             void *stream)
+{
+    sgf_status s = check_ptrs(p, sigma, fx, fy);
+    if (s != SGF_OK)
+        return s;
+    const size_t need = noalloc_bytes(p);
+    if (need > (size_t)SGF_NOALLOC_SCRATCH_BYTES)
+        return fail(SGF_EUNSUPPORTED,
+                    "sgf_solve_noalloc: this plan needs %zu bytes of scratch, above SGF_NOALLOC_SCRATCH_BYTES = %zu",
+                    need, (size_t)SGF_NOALLOC_SCRATCH_BYTES);
+    DeviceGuard g(p->device);
+    void *scratch = nullptr;
+    if ((s = noalloc_scratch_on_current_device(&scratch)) != SGF_OK)
+        return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned char *sc = static_cast<unsigned char *>(scratch);
+    return p->prec == SGF_FP64 ? solve_noalloc_impl<double>(p, sigma, fx, fy, st, sc)
+                               : solve_noalloc_impl<float>(p, sigma, fx, fy, st, sc);
 }
 
 }  // extern "C"

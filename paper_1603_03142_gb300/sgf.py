@@ -28,8 +28,9 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16x": BF16X}
 # every symbol include/sgf.h declares
 EXPORTS = ["sgf_plan_create", "sgf_plan_create_ex", "sgf_plan_check", "sgf_plan_share", "sgf_plan_stats_get",
            "sgf_solve", "sgf_solve_host", "sgf_solve_batched", "sgf_plan_destroy", "sgf_last_error", "sgf_version",
-           "sgf_plan_profile", "sgf_plan_profile_read"]
+           "sgf_plan_profile", "sgf_plan_profile_read", "sgf_solve_noalloc"]
 PLAN_ZERO_RIM = 0x1
+NOALLOC_SCRATCH_BYTES = 32 << 20
 KERNELS = ["restrict", "row_fwd", "col", "row_inv"]
 
 
@@ -60,6 +61,7 @@ _lib.sgf_plan_share.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)
 _lib.sgf_plan_stats_get.argtypes = [ctypes.c_void_p, ctypes.POINTER(PlanStats)]
 _lib.sgf_solve.argtypes = [ctypes.c_void_p, _vpp, _vpp, _vpp, ctypes.c_void_p]
 _lib.sgf_solve_host.argtypes = [ctypes.c_void_p, _vpp, _vpp, _vpp, ctypes.c_void_p]
+_lib.sgf_solve_noalloc.argtypes = [ctypes.c_void_p, _vpp, _vpp, _vpp, ctypes.c_void_p]
 _lib.sgf_solve_batched.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32,
                                    ctypes.POINTER(_vpp), ctypes.POINTER(_vpp), ctypes.POINTER(_vpp),
                                    ctypes.c_void_p]
@@ -69,7 +71,8 @@ _lib.sgf_plan_profile_read.argtypes = [ctypes.c_void_p, ctypes.POINTER(KernelTim
 _lib.sgf_last_error.restype = ctypes.c_char_p
 _lib.sgf_version.restype = ctypes.c_char_p
 for _f in ("sgf_plan_create", "sgf_plan_create_ex", "sgf_plan_check", "sgf_plan_share", "sgf_plan_stats_get", "sgf_solve", "sgf_solve_host",
-           "sgf_solve_batched", "sgf_plan_destroy", "sgf_plan_profile", "sgf_plan_profile_read"):
+           "sgf_solve_batched", "sgf_plan_destroy", "sgf_plan_profile", "sgf_plan_profile_read",
+           "sgf_solve_noalloc"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -160,6 +163,11 @@ class Plan:
         st = PlanStats()
         _check(_lib.sgf_plan_stats_get(self._h, ctypes.byref(st)), "sgf_plan_stats_get")
         return {name: getattr(st, name) for name, _ in PlanStats._fields_}
+
+    def solve_noalloc_ptrs(self, sigma_ptrs, fx_ptrs, fy_ptrs, stream=None):
+        """sgf_solve_noalloc: the solve with the library's fixed scratch array (no allocation)."""
+        _check(_lib.sgf_solve_noalloc(self._h, _ptrs(sigma_ptrs), _ptrs(fx_ptrs), _ptrs(fy_ptrs),
+                                      ctypes.c_void_p(_stream_handle(stream))), "sgf_solve_noalloc")
 
     def profile(self, enable: bool = True):
         _check(_lib.sgf_plan_profile(self._h, 1 if enable else 0), "sgf_plan_profile")
