@@ -148,14 +148,32 @@ sgf_status sgf_solve(sgf_plan *plan, const void *const *sigma, void *const *fx, 
 sgf_status sgf_solve_host(sgf_plan *plan, const void *const *sigma, void *const *fx,
                           void *const *fy, void *stream);
 
-/* Solve `count` independent nests (plans may differ in n, levels and offsets,
- * but share one precision) on one stream: every pass of the method runs as
- * one launch over the work items of all nests.  sigma[k], fx[k], fy[k] are the
- * per-level device pointer arrays of nest k.  Plans must be distinct. */
+/* Solve `count` independent nests on one stream, one nest after the other
+ * (sgf_solve for each).  sigma[k], fx[k], fy[k] are the per-level device
+ * pointer arrays of nest k; plans must be distinct and share one precision.
+ * For fused launches over many nests use sgf_batch_*. */
 sgf_status sgf_solve_batched(sgf_plan *const *plans, int32_t count, const void *const *const *sigma,
                              void *const *const *fx, void *const *const *fy, void *stream);
 
 sgf_status sgf_plan_destroy(sgf_plan *plan);
+
+/* Fused batches of independent nests (no paper counterpart: throughput for many
+ * small solves).  A batch is built once from distinct plans of one precision
+ * and device (they may differ in n, levels, offsets and options).  Each solve
+ * runs every transform pass as one launch per group of nests that share n (the
+ * kernels are compiled per n) plus one restriction launch per nesting depth,
+ * and the whole sequence is captured once in a CUDA graph and replayed on the
+ * caller's stream (SGF_BATCH_NO_GRAPH: launch directly).  The plans'
+ * workspaces are used, so a plan must not solve elsewhere while its batch
+ * runs.  sgf_batch_solve copies the pointer tables through pinned memory and
+ * waits only for the previous solve's copy; arguments as sgf_solve_batched. */
+typedef struct sgf_batch sgf_batch;
+#define SGF_BATCH_NO_GRAPH 0x1u
+sgf_status sgf_batch_create(sgf_plan *const *plans, int32_t count, uint32_t flags, sgf_batch **out);
+sgf_status sgf_batch_solve(sgf_batch *batch, const void *const *const *sigma, void *const *const *fx,
+                           void *const *const *fy, void *stream);
+sgf_status sgf_batch_info(const sgf_batch *batch, int32_t *groups, int32_t *launches_per_solve);
+sgf_status sgf_batch_destroy(sgf_batch *batch);
 
 /* Per-kernel device times of this plan's solves, for measurement (no paper
  * counterpart).  Kernel k: 0 restriction, 1 forward row pass, 2 column pass

@@ -129,6 +129,34 @@ struct sgf_plan {
     size_t events_used = 0;
 };
 
+// A fixed set of plans solved together: per group of nests with the same N
+// (and path), one launch per transform pass; the whole solve is replayed as a
+// CUDA graph.
+struct sgf_batch {
+    int device = 0;
+    sgf_precision prec = SGF_FP32;
+    std::vector<sgf_plan *> plans;
+    struct Group {
+        int logN = 0;
+        bool merged = false;
+        int n_fwd = 0, n_col = 0, n_inv = 0;  // map entries per pass
+        size_t map_fwd = 0, map_col = 0, map_inv = 0;  // int2 offsets in the map buffer
+    };
+    std::vector<Group> groups;
+    std::vector<int> restrict_jobs;   // count per restriction depth
+    std::vector<size_t> restrict_off; // int2 offsets per depth
+    int max_n = 0;
+    size_t args_bytes = 0;            // sizeof(SolveArgs<T>) * count
+    void *d_args = nullptr;           // SolveArgs<T>[count]
+    void *h_args = nullptr;           // pinned staging of the same
+    int2 *d_maps = nullptr;
+    cudaEvent_t uploaded = nullptr;   // after the argument upload of the last solve
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    bool use_graph = true, solved_once = false;
+    int launches = 0;                 // kernel launches per solve
+};
+
 namespace {
 
 sgf_status validate(const sgf_nest_desc *d, sgf_precision prec)
@@ -759,6 +787,217 @@ sgf_status solve_noalloc_impl(sgf_plan *p, const void *const *sigma, void *const
     return SGF_OK;
 }
 
+
+// ---- fused batches (sgf_batch_*) -------------------------------------------
+// The solve arguments of one nest, as solve_impl builds them, without launching.
+template <typename T>
+void fill_args(const sgf_plan *p, const void *const *sigma, void *const *fx, void *const *fy, SolveArgs<T> &a)
+{
+    const int N = p->N, L = p->L;
+    a = SolveArgs<T>{};
+    a.N = N;
+    a.logN = p->logN;
+    a.L = L;
+    for (int l = 0; l < kMaxLevels; ++l) {
+        a.child_ox[l] = -1;
+        a.child_oy[l] = -1;
+    }
+    for (int l = 0; l + 1 < L; ++l) {
+        a.child_ox[l] = p->desc.off[l + 1][0];
+        a.child_oy[l] = p->desc.off[l + 1][1];
+    }
+    T *restricted = static_cast<T *>(p->d_restricted);
+    for (int l = 0; l < L; ++l) {
+        a.sigma_in[l] = static_cast<const T *>(sigma[l]);
+        a.src[l] = l + 1 < L ? restricted + (size_t)l * N * N : static_cast<const T *>(sigma[l]);
+        a.fx[l] = static_cast<T *>(fx[l]);
+        a.fy[l] = static_cast<T *>(fy[l]);
+    }
+    a.fwd = static_cast<typename SolveArgs<T>::C *>(p->d_fwd);
+    a.bwd = static_cast<typename SolveArgs<T>::C *>(p->d_bwd);
+    a.spec = p->spec->dev;
+    a.tw = static_cast<const typename SolveArgs<T>::C *>(p->spec->tw);
+    a.tw_entries = p->spec->tw_entries;
+    a.status = p->d_status;
+    a.slabs = p->d_slabs;
+    a.fwd_items = p->d_items;
+    a.outs = p->d_outs;
+    a.ins = p->d_ins;
+    a.contribs = p->d_contribs;
+    for (int l = 0; l <= L; ++l)
+        a.contrib_begin[l] = p->contrib_begin[l];
+}
+
+// The launches of one batch solve (the arguments are already on the device).
+template <typename T>
+sgf_status batch_launches(sgf_batch *bt, cudaStream_t st)
+{
+    const SolveArgs<T> *args = static_cast<const SolveArgs<T> *>(bt->d_args);
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(bt->d_args, bt->h_args, bt->args_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e, "batch argument upload");
+    if ((e = cudaEventRecord(bt->uploaded, st)) != cudaSuccess)
+        return cuda_fail(e, "cudaEventRecord(batch upload)");
+    for (size_t d = 0; d < bt->restrict_jobs.size(); ++d)
+        if ((e = launch_restrict_batch<T>(args, bt->d_maps + bt->restrict_off[d], bt->restrict_jobs[d], bt->max_n, st)) !=
+            cudaSuccess)
+            return cuda_fail(e, "batched restriction launch");
+    SolveArgs<T> dummy{};
+    for (const auto &g : bt->groups) {
+        BatchView<T> vf{args, bt->d_maps + g.map_fwd}, vc{args, bt->d_maps + g.map_col}, vi{args, bt->d_maps + g.map_inv};
+        dummy.N = 1 << g.logN;
+        if ((e = launch_pass_n<T>(g.merged ? PASS_ROW_FWD_M : PASS_ROW_FWD, g.logN, dummy, g.n_fwd, st, &vf)) != cudaSuccess)
+            return cuda_fail(e, "batched row_fwd launch");
+        if ((e = launch_pass_n<T>(g.merged ? PASS_COL_M : PASS_COL, g.logN, dummy, g.n_col, st, &vc)) != cudaSuccess)
+            return cuda_fail(e, "batched col launch");
+        if ((e = launch_pass_n<T>(PASS_ROW_INV, g.logN, dummy, g.n_inv, st, &vi)) != cudaSuccess)
+            return cuda_fail(e, "batched row_inv launch");
+    }
+    return SGF_OK;
+}
+
+void batch_free(sgf_batch *bt)
+{
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(bt->device);
+    if (bt->graph)
+        cudaGraphExecDestroy(bt->graph);
+    if (bt->capture_stream)
+        cudaStreamDestroy(bt->capture_stream);
+    if (bt->uploaded)
+        cudaEventDestroy(bt->uploaded);
+    cudaFree(bt->d_args);
+    cudaFree(bt->d_maps);
+    cudaFreeHost(bt->h_args);
+    cudaSetDevice(cur);
+    delete bt;
+}
+
+template <typename T>
+sgf_status batch_build(sgf_batch *bt)
+{
+    const int count = (int)bt->plans.size();
+    bt->args_bytes = sizeof(SolveArgs<T>) * (size_t)count;
+    // groups: one per (N, path), in order of first appearance
+    std::vector<int2> maps;
+    std::map<std::pair<int, bool>, int> gidx;
+    std::vector<std::vector<int>> members;
+    for (int k = 0; k < count; ++k) {
+        const sgf_plan *p = bt->plans[k];
+        bt->max_n = std::max(bt->max_n, p->N);
+        auto key = std::make_pair(p->logN, p->merged);
+        if (!gidx.count(key)) {
+            gidx[key] = (int)bt->groups.size();
+            sgf_batch::Group g;
+            g.logN = p->logN;
+            g.merged = p->merged;
+            bt->groups.push_back(g);
+            members.emplace_back();
+        }
+        members[gidx[key]].push_back(k);
+    }
+    for (size_t gi = 0; gi < bt->groups.size(); ++gi) {
+        auto &g = bt->groups[gi];
+        g.map_fwd = maps.size();
+        for (int k : members[gi]) {
+            const sgf_plan *p = bt->plans[k];
+            const int n = g.merged ? p->N / 2 : (int)p->items.size();
+            for (int i = 0; i < n; ++i)
+                maps.push_back(make_int2(k, i));
+        }
+        g.n_fwd = (int)(maps.size() - g.map_fwd);
+        if (g.merged) {  // row_fwd_m / col_m: one map row per nest (grid.y)
+            g.map_fwd = maps.size();
+            for (int k : members[gi])
+                maps.push_back(make_int2(k, 0));
+            g.n_fwd = (int)members[gi].size();
+        }
+        g.map_col = maps.size();
+        for (int k : members[gi])
+            for (int o = 0; o < (int)bt->plans[k]->outs.size(); ++o)
+                maps.push_back(make_int2(k, o));
+        g.n_col = (int)(maps.size() - g.map_col);
+        g.map_inv = maps.size();
+        for (int k : members[gi])
+            for (int l = 0; l < bt->plans[k]->L; ++l)
+                maps.push_back(make_int2(k, l));
+        g.n_inv = (int)(maps.size() - g.map_inv);
+        bt->launches += 3;
+    }
+    // restriction depths: depth d restricts level L-2-d of every nest that has it
+    int maxL = 1;
+    for (auto *p : bt->plans)
+        maxL = std::max(maxL, p->L);
+    for (int d = 0; d + 1 < maxL; ++d) {
+        bt->restrict_off.push_back(maps.size());
+        int n = 0;
+        for (int k = 0; k < count; ++k) {
+            const int l = bt->plans[k]->L - 2 - d;
+            if (l >= 0) {
+                maps.push_back(make_int2(k, l));
+                ++n;
+            }
+        }
+        bt->restrict_jobs.push_back(n);
+        bt->launches += n > 0 ? 1 : 0;
+    }
+    cudaError_t e;
+    if ((e = cudaMalloc(&bt->d_maps, maps.size() * sizeof(int2) + 16)) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(batch work maps)");
+    if (!maps.empty() &&
+        (e = cudaMemcpy(bt->d_maps, maps.data(), maps.size() * sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpy(batch work maps)");
+    if ((e = cudaMalloc(&bt->d_args, bt->args_bytes)) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(batch arguments)");
+    if ((e = cudaHostAlloc(&bt->h_args, bt->args_bytes, cudaHostAllocDefault)) != cudaSuccess)
+        return cuda_fail(e, "cudaHostAlloc(batch argument staging)");
+    if ((e = cudaEventCreateWithFlags(&bt->uploaded, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "cudaEventCreate(batch upload)");
+    if ((e = cudaStreamCreateWithFlags(&bt->capture_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e, "cudaStreamCreate(batch capture)");
+    SolveArgs<T> dummy{};
+    for (const auto &g : bt->groups)
+        if ((e = launch_pass_n<T>(PASS_PREPARE, g.logN, dummy, 0, nullptr)) != cudaSuccess)
+            return cuda_fail(e, "batch kernel attributes");
+    return SGF_OK;
+}
+
+template <typename T>
+sgf_status batch_solve(sgf_batch *bt, const void *const *const *sigma, void *const *const *fx,
+                       void *const *const *fy, cudaStream_t st)
+{
+    cudaError_t e;
+    if (bt->solved_once && (e = cudaEventSynchronize(bt->uploaded)) != cudaSuccess)
+        return cuda_fail(e, "waiting for the previous batch upload");
+    SolveArgs<T> *h = static_cast<SolveArgs<T> *>(bt->h_args);
+    for (size_t k = 0; k < bt->plans.size(); ++k)
+        fill_args<T>(bt->plans[k], sigma[k], fx[k], fy[k], h[k]);
+    bt->solved_once = true;
+    if (!bt->use_graph)
+        return batch_launches<T>(bt, st);
+    if (!bt->graph) {  // capture the launch sequence once; replays read the staged arguments
+        cudaGraph_t g = nullptr;
+        if ((e = cudaStreamBeginCapture(bt->capture_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamBeginCapture(batch)");
+        sgf_status s = batch_launches<T>(bt, bt->capture_stream);
+        e = cudaStreamEndCapture(bt->capture_stream, &g);
+        if (s != SGF_OK) {
+            if (g)
+                cudaGraphDestroy(g);
+            return s;
+        }
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cudaStreamEndCapture(batch)");
+        e = cudaGraphInstantiate(&bt->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cudaGraphInstantiate(batch)");
+    }
+    if ((e = cudaGraphLaunch(bt->graph, st)) != cudaSuccess)
+        return cuda_fail(e, "cudaGraphLaunch(batch)");
+    return SGF_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -1021,6 +1260,74 @@ sgf_status sgf_solve_noalloc(sgf_plan *p, const void *const *sigma, void *const 
     unsigned char *sc = static_cast<unsigned char *>(scratch);
     return p->prec == SGF_FP64 ? solve_noalloc_impl<double>(p, sigma, fx, fy, st, sc)
                                : solve_noalloc_impl<float>(p, sigma, fx, fy, st, sc);
+}
+
+sgf_status sgf_batch_create(sgf_plan *const *plans, int32_t count, uint32_t flags, sgf_batch **out)
+{
+    if (!out)
+        return fail(SGF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !plans)
+        return fail(SGF_EINVAL, "a batch needs at least one plan");
+    if (flags & ~SGF_BATCH_NO_GRAPH)
+        return fail(SGF_EINVAL, "unknown batch flags 0x%x", flags);
+    for (int k = 0; k < count; ++k) {
+        if (!plans[k])
+            return fail(SGF_EINVAL, "plan %d is NULL", k);
+        if (plans[k]->prec != plans[0]->prec || plans[k]->device != plans[0]->device)
+            return fail(SGF_EINVAL, "plans of one batch must share precision and device");
+        for (int q = 0; q < k; ++q)
+            if (plans[q] == plans[k])
+                return fail(SGF_EINVAL, "plan %d appears twice in the batch", k);
+    }
+    DeviceGuard g(plans[0]->device);
+    sgf_batch *bt = new sgf_batch();
+    bt->device = plans[0]->device;
+    bt->prec = plans[0]->prec;
+    bt->plans.assign(plans, plans + count);
+    bt->use_graph = !(flags & SGF_BATCH_NO_GRAPH);
+    sgf_status s = bt->prec == SGF_FP64 ? batch_build<double>(bt) : batch_build<float>(bt);
+    if (s != SGF_OK) {
+        std::string msg = g_err;
+        batch_free(bt);
+        g_err = msg;
+        return s;
+    }
+    *out = bt;
+    return SGF_OK;
+}
+
+sgf_status sgf_batch_solve(sgf_batch *bt, const void *const *const *sigma, void *const *const *fx,
+                           void *const *const *fy, void *stream)
+{
+    if (!bt || !sigma || !fx || !fy)
+        return fail(SGF_EINVAL, "NULL argument");
+    for (size_t k = 0; k < bt->plans.size(); ++k) {
+        sgf_status s = check_ptrs(bt->plans[k], sigma[k], fx[k], fy[k]);
+        if (s != SGF_OK)
+            return s;
+    }
+    DeviceGuard g(bt->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return bt->prec == SGF_FP64 ? batch_solve<double>(bt, sigma, fx, fy, st) : batch_solve<float>(bt, sigma, fx, fy, st);
+}
+
+sgf_status sgf_batch_info(const sgf_batch *bt, int32_t *groups, int32_t *launches_per_solve)
+{
+    if (!bt)
+        return fail(SGF_EINVAL, "batch is NULL");
+    if (groups)
+        *groups = (int32_t)bt->groups.size();
+    if (launches_per_solve)
+        *launches_per_solve = bt->launches;
+    return SGF_OK;
+}
+
+sgf_status sgf_batch_destroy(sgf_batch *bt)
+{
+    if (bt)
+        batch_free(bt);
+    return SGF_OK;
 }
 
 }  // extern "C"

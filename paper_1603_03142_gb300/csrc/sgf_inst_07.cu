@@ -2,6 +2,6 @@
 #include "sgf_kernels.cuh"
 
 namespace sgf {
-template cudaError_t launch_pass<float, 7>(int, const SolveArgs<float> &, int, cudaStream_t);
-template cudaError_t launch_pass<double, 7>(int, const SolveArgs<double> &, int, cudaStream_t);
+template cudaError_t launch_pass<float, 7>(int, const SolveArgs<float> &, int, cudaStream_t, const BatchView<float> *);
+template cudaError_t launch_pass<double, 7>(int, const SolveArgs<double> &, int, cudaStream_t, const BatchView<double> *);
 }  // namespace sgf

@@ -2,5 +2,5 @@
 #include "sgf_kernels.cuh"
 
 namespace sgf {
-template cudaError_t launch_pass<float, 12>(int, const SolveArgs<float> &, int, cudaStream_t);
+template cudaError_t launch_pass<float, 12>(int, const SolveArgs<float> &, int, cudaStream_t, const BatchView<float> *);
 }  // namespace sgf

@@ -101,6 +101,7 @@ struct SolveArgs {
     int N, logN, L;
     int child_ox[kMaxLevels], child_oy[kMaxLevels];  // covered region of each level; -1: none
     const T *src[kMaxLevels];   // density per level, covered cells already restricted
+    const T *sigma_in[kMaxLevels];  // the caller's density per level (batched restriction reads it)
     T *fx[kMaxLevels];
     T *fy[kMaxLevels];
     C *fwd;                     // forward slabs
@@ -145,14 +146,28 @@ struct GenSet {
 };
 
 // ---- launchers (sgf_solve.cu / sgf_gen.cu); all return cudaGetLastError()
+// Batched restriction: job k = (nest, level) restricts `level` of args[nest]
+// (fine = src[level+1], coarse = src[level], input = sigma_in[level]).
+template <typename T>
+cudaError_t launch_restrict_batch(const SolveArgs<T> *args, const int2 *jobs, int njobs, int max_n, cudaStream_t st);
 template <typename T>
 cudaError_t launch_restrict(const T *fine, T *coarse, const T *coarse_in, int N, int ox, int oy,
                             cudaStream_t st);
 // Transform passes of a solve (sgf_kernels.cuh); count = work items (row_fwd),
 // outputs (col) or levels (row_inv).
-enum : int { PASS_ROW_FWD = 0, PASS_COL = 1, PASS_ROW_INV = 2, PASS_ROW_FWD_M = 3, PASS_COL_M = 4 };
+enum : int { PASS_ROW_FWD = 0, PASS_COL = 1, PASS_ROW_INV = 2, PASS_ROW_FWD_M = 3, PASS_COL_M = 4, PASS_PREPARE = 5 };
+// Batch mode of the transform passes: a block's nest and its local work index
+// come from a per-launch map (one int2 per block row), and that nest's
+// arguments from a device array.
 template <typename T>
-cudaError_t launch_pass_n(int pass, int logN, const SolveArgs<T> &a, int count, cudaStream_t st);
+struct BatchView {
+    const SolveArgs<T> *args;
+    const int2 *map;  // (nest, local index)
+};
+// bv == nullptr: one nest (a); otherwise every block takes its nest's arguments from bv.
+template <typename T>
+cudaError_t launch_pass_n(int pass, int logN, const SolveArgs<T> &a, int count, cudaStream_t st,
+                          const BatchView<T> *bv = nullptr);
 
 // Build the spectra of one set into spec (element type T: float or double).
 // work_tables: 6*P*P doubles; work_half: 6*(N+1)*P double2.

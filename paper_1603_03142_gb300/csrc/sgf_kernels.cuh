@@ -101,9 +101,11 @@ struct KShape {
 
 // ------------------------------------------------------------------ row_fwd
 // Shared memory: twiddle area | sigma rows[6][N] | sbuf[2 SP_ROW].
-template <typename T, int LOGN>
-__global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd(SolveArgs<T> a)
+template <typename T, int LOGN, bool BATCH>
+__global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd(SolveArgs<T> a0, BatchView<T> bv)
 {
+    const int2 wm = BATCH ? bv.map[blockIdx.x] : make_int2(0, (int)blockIdx.x);
+    const SolveArgs<T> &a = BATCH ? bv.args[wm.x] : a0;
     using C = typename Cx<T>::C;
     using C2 = typename Cx<T>::C2;
     using K = KShape<LOGN>;
@@ -112,7 +114,7 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd(SolveArgs
     C *tw = reinterpret_cast<C *>(smem_raw);
     T *srow = reinterpret_cast<T *>(smem_raw + tw_bytes<C>(a.tw_entries));  // rows ja-1, ja, ja+1, jb-1, jb, jb+1
     C *sbuf = reinterpret_cast<C *>(srow + 6 * N);
-    const FwdItem item = a.fwd_items[blockIdx.x];
+    const FwdItem item = a.fwd_items[wm.y];
     const FwdSlab sl = a.slabs[item.slab];
     const int rows = sl.rows, r0 = 2 * item.row_pair;
     const int ja = sl.m * r0 + sl.py, jb = sl.m * (r0 + 1) + sl.py;
@@ -195,9 +197,11 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd(SolveArgs
 // this parity's half of the two spectrum rows, 2 x (N/2 + 4) reals }.  The
 // dual inverse transform uses sbuf and the stages as two sequence buffers, and
 // the fold of the odd half reuses them afterwards.
-template <typename T, int LOGN>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_THREADS) k_col(SolveArgs<T> a)
+template <typename T, int LOGN, bool BATCH>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_THREADS) k_col(SolveArgs<T> a0, BatchView<T> bv)
 {
+    const int2 wm = BATCH ? bv.map[blockIdx.y] : make_int2(0, (int)blockIdx.y);
+    const SolveArgs<T> &a = BATCH ? bv.args[wm.x] : a0;
     using C = typename Cx<T>::C;
     using K = KShape<LOGN>;
     constexpr int N = K::N, Q = K::Q, P = 2 * N, QS = quarter_stride(N), HQ = quarter_half(N);
@@ -210,7 +214,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
     cg::cluster_group cluster = cg::this_cluster();
     const int b = (int)cluster.block_rank();  // parity half
     const int kx = blockIdx.x >> 1;
-    const ColOutput o = a.outs[blockIdx.y];
+    const ColOutput o = a.outs[wm.y];
     const int t = threadIdx.x;
     const bool active = t < Q;
     const int j = active ? t : 0;
@@ -341,9 +345,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
 // asynchronous copies -- 16 bytes per bin when both rows are adjacent rows of
 // one output, 8 bytes otherwise -- and the next gather is issued as soon as
 // the current one has been read into registers, so it overlaps the transform.
-template <typename T, int LOGN>
-__global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_inv(SolveArgs<T> a)
+template <typename T, int LOGN, bool BATCH>
+__global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_inv(SolveArgs<T> a0, BatchView<T> bv)
 {
+    const int2 wm = BATCH ? bv.map[blockIdx.y] : make_int2(0, (int)blockIdx.y);
+    const SolveArgs<T> &a = BATCH ? bv.args[wm.x] : a0;
     using C = typename Cx<T>::C;
     using K = KShape<LOGN>;
     constexpr int N = K::N, Q = K::Q, SP = K::SP_ROW, P = 2 * N;
@@ -352,7 +358,7 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_inv(SolveArgs
     C *stg = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));  // [kx][2]
     C *sbuf = stg + 2 * (N + 1) + ((2 * (N + 1) * sizeof(C)) % 16 ? 1 : 0);
     T *O = reinterpret_cast<T *>(sbuf + 2 * SP);
-    const int tl = blockIdx.y;
+    const int tl = wm.y;
     const int j0 = 2 * blockIdx.x, j1 = j0 + 1;
     const int t = threadIdx.x;
     const bool active = t < 2 * Q;
@@ -454,9 +460,11 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_inv(SolveArgs
 // the CTAs of rows 0-1 and N-2..N-1 scan their rows, every CTA its cells in
 // columns 0, 1, N-2, N-1; a nonzero value sets STATUS_RIM_NONZERO.
 // Shared memory: twiddle area | sigma rows[2][N] | sbuf[2 SP_ROW].
-template <typename T, int LOGN>
-__global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd_m(SolveArgs<T> a)
+template <typename T, int LOGN, bool BATCH>
+__global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd_m(SolveArgs<T> a0, BatchView<T> bv)
 {
+    const int2 wm = BATCH ? bv.map[blockIdx.y] : make_int2(0, 0);
+    const SolveArgs<T> &a = BATCH ? bv.args[wm.x] : a0;
     using C = typename Cx<T>::C;
     using C2 = typename Cx<T>::C2;
     using K = KShape<LOGN>;
@@ -533,10 +541,12 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd_m(SolveAr
 // memory.  Shared memory: twiddle area | sbuf[SPC] | stage {column[N], this
 // parity's half rows of Gx and Gy}; the dual transform and the fold reuse
 // sbuf + stage.
-template <typename T, int LOGN>
+template <typename T, int LOGN, bool BATCH>
 __global__ void __cluster_dims__(2, 1, 1)
-    __launch_bounds__(KShape<LOGN>::COL_THREADS, sizeof(T) == 4 ? 2 : 1) k_col_m(SolveArgs<T> a)
+    __launch_bounds__(KShape<LOGN>::COL_THREADS, sizeof(T) == 4 ? 2 : 1) k_col_m(SolveArgs<T> a0, BatchView<T> bv)
 {
+    const int2 wm = BATCH ? bv.map[blockIdx.y] : make_int2(0, 0);
+    const SolveArgs<T> &a = BATCH ? bv.args[wm.x] : a0;
     using C = typename Cx<T>::C;
     using K = KShape<LOGN>;
     constexpr int N = K::N, Q = K::Q, QS = quarter_stride(N), HQ = quarter_half(N);
@@ -661,41 +671,69 @@ inline cudaError_t ensure_smem(F *kernel, size_t bytes, std::atomic<unsigned lon
 }
 
 template <typename T, int LOGN>
-cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t st)
+cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t st, const BatchView<T> *bv)
 {
     using K = KShape<LOGN>;
     using S = KSmem<T, LOGN>;
-    static std::atomic<unsigned long long> d0{0}, d1{0}, d2{0}, d3{0}, d4{0};
+    static std::atomic<unsigned long long> d[10];
+    const BatchView<T> none{nullptr, nullptr};
+    const bool batch = bv != nullptr;
+    const BatchView<T> v = batch ? *bv : none;
     cudaError_t e = cudaSuccess;
+#define SGF_LAUNCH(K0, K1, idx, smem, grid, threads)                                  \
+    if (batch) {                                                                      \
+        if ((e = ensure_smem(K1, smem, d[idx + 1])) != cudaSuccess)                   \
+            return e;                                                                 \
+        K1<<<grid, threads, smem, st>>>(a, v);                                        \
+    } else {                                                                          \
+        if ((e = ensure_smem(K0, smem, d[idx])) != cudaSuccess)                       \
+            return e;                                                                 \
+        K0<<<grid, threads, smem, st>>>(a, v);                                        \
+    }
+    if (pass == PASS_PREPARE) {  // set every shared-memory limit (before a graph capture)
+        if ((e = ensure_smem(k_row_fwd<T, LOGN, false>, S::row_fwd(), d[0])) != cudaSuccess ||
+            (e = ensure_smem(k_row_fwd<T, LOGN, true>, S::row_fwd(), d[1])) != cudaSuccess ||
+            (e = ensure_smem(k_col<T, LOGN, false>, S::col(), d[2])) != cudaSuccess ||
+            (e = ensure_smem(k_col<T, LOGN, true>, S::col(), d[3])) != cudaSuccess ||
+            (e = ensure_smem(k_row_inv<T, LOGN, false>, S::row_inv(), d[4])) != cudaSuccess ||
+            (e = ensure_smem(k_row_inv<T, LOGN, true>, S::row_inv(), d[5])) != cudaSuccess ||
+            (e = ensure_smem(k_row_fwd_m<T, LOGN, false>, S::row_fwd_m(), d[6])) != cudaSuccess ||
+            (e = ensure_smem(k_row_fwd_m<T, LOGN, true>, S::row_fwd_m(), d[7])) != cudaSuccess ||
+            (e = ensure_smem(k_col_m<T, LOGN, false>, S::col_m(), d[8])) != cudaSuccess ||
+            (e = ensure_smem(k_col_m<T, LOGN, true>, S::col_m(), d[9])) != cudaSuccess)
+            return e;
+        return cudaSuccess;
+    }
     switch (pass) {
-    case PASS_ROW_FWD:
-        if ((e = ensure_smem(k_row_fwd<T, LOGN>, S::row_fwd(), d0)) != cudaSuccess)
-            return e;
-        k_row_fwd<T, LOGN><<<count, K::ROW_THREADS, S::row_fwd(), st>>>(a);
+    case PASS_ROW_FWD: {
+        SGF_LAUNCH((k_row_fwd<T, LOGN, false>), (k_row_fwd<T, LOGN, true>), 0, S::row_fwd(), dim3(count),
+                   K::ROW_THREADS)
         break;
-    case PASS_COL:
-        if ((e = ensure_smem(k_col<T, LOGN>, S::col(), d1)) != cudaSuccess)
-            return e;
-        k_col<T, LOGN><<<dim3(2 * (K::N + 1), count), K::COL_THREADS, S::col(), st>>>(a);
+    }
+    case PASS_COL: {
+        SGF_LAUNCH((k_col<T, LOGN, false>), (k_col<T, LOGN, true>), 2, S::col(), dim3(2 * (K::N + 1), count),
+                   K::COL_THREADS)
         break;
-    case PASS_ROW_INV:
-        if ((e = ensure_smem(k_row_inv<T, LOGN>, S::row_inv(), d2)) != cudaSuccess)
-            return e;
-        k_row_inv<T, LOGN><<<dim3(K::N / 2, count), K::ROW_THREADS, S::row_inv(), st>>>(a);
+    }
+    case PASS_ROW_INV: {
+        SGF_LAUNCH((k_row_inv<T, LOGN, false>), (k_row_inv<T, LOGN, true>), 4, S::row_inv(), dim3(K::N / 2, count),
+                   K::ROW_THREADS)
         break;
-    case PASS_ROW_FWD_M:
-        if ((e = ensure_smem(k_row_fwd_m<T, LOGN>, S::row_fwd_m(), d3)) != cudaSuccess)
-            return e;
-        k_row_fwd_m<T, LOGN><<<K::N / 2, K::ROW_THREADS, S::row_fwd_m(), st>>>(a);
+    }
+    case PASS_ROW_FWD_M: {
+        SGF_LAUNCH((k_row_fwd_m<T, LOGN, false>), (k_row_fwd_m<T, LOGN, true>), 6, S::row_fwd_m(),
+                   dim3(K::N / 2, batch ? count : 1), K::ROW_THREADS)
         break;
-    case PASS_COL_M:
-        if ((e = ensure_smem(k_col_m<T, LOGN>, S::col_m(), d4)) != cudaSuccess)
-            return e;
-        k_col_m<T, LOGN><<<2 * (K::N + 1), K::COL_THREADS, S::col_m(), st>>>(a);
+    }
+    case PASS_COL_M: {
+        SGF_LAUNCH((k_col_m<T, LOGN, false>), (k_col_m<T, LOGN, true>), 8, S::col_m(),
+                   dim3(2 * (K::N + 1), batch ? count : 1), K::COL_THREADS)
         break;
+    }
     default:
         return cudaErrorInvalidValue;
     }
+#undef SGF_LAUNCH
     return cudaGetLastError();
 }
 

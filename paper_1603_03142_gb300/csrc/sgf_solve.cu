@@ -36,6 +36,39 @@ cudaError_t launch_restrict(const T *fine, T *coarse, const T *coarse_in, int N,
     return cudaGetLastError();
 }
 
+template <typename T>
+__global__ void k_restrict_batch(const SolveArgs<T> *__restrict__ args, const int2 *__restrict__ jobs)
+{
+    const int2 job = jobs[blockIdx.y];
+    const SolveArgs<T> &a = args[job.x];
+    const int l = job.y, N = a.N;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * N)
+        return;
+    const int j = idx / N, i = idx - j * N;
+    const int half = N >> 1, ox = a.child_ox[l], oy = a.child_oy[l];
+    T v = a.sigma_in[l][idx];
+    if (i >= ox && i < ox + half && j >= oy && j < oy + half) {
+        const T *f = a.src[l + 1] + (size_t)(2 * (j - oy)) * N + 2 * (i - ox);
+        v = T(0.25) * ((f[0] + f[1]) + (f[N] + f[N + 1]));
+    }
+    const_cast<T *>(a.src[l])[idx] = v;
+}
+
+template <typename T>
+cudaError_t launch_restrict_batch(const SolveArgs<T> *args, const int2 *jobs, int njobs, int max_n, cudaStream_t st)
+{
+    if (njobs <= 0)
+        return cudaSuccess;
+    const int bs = 256;
+    dim3 grid((max_n * max_n + bs - 1) / bs, njobs);
+    k_restrict_batch<T><<<grid, bs, 0, st>>>(args, jobs);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_restrict_batch<float>(const SolveArgs<float> *, const int2 *, int, int, cudaStream_t);
+template cudaError_t launch_restrict_batch<double>(const SolveArgs<double> *, const int2 *, int, int, cudaStream_t);
+
 template cudaError_t launch_restrict<float>(const float *, float *, const float *, int, int, int, cudaStream_t);
 template cudaError_t launch_restrict<double>(const double *, double *, const double *, int, int, int, cudaStream_t);
 

@@ -28,7 +28,9 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16x": BF16X}
 # every symbol include/sgf.h declares
 EXPORTS = ["sgf_plan_create", "sgf_plan_create_ex", "sgf_plan_check", "sgf_plan_share", "sgf_plan_stats_get",
            "sgf_solve", "sgf_solve_host", "sgf_solve_batched", "sgf_plan_destroy", "sgf_last_error", "sgf_version",
-           "sgf_plan_profile", "sgf_plan_profile_read", "sgf_solve_noalloc"]
+           "sgf_plan_profile", "sgf_plan_profile_read", "sgf_solve_noalloc", "sgf_batch_create",
+           "sgf_batch_solve", "sgf_batch_info", "sgf_batch_destroy"]
+BATCH_NO_GRAPH = 0x1
 PLAN_ZERO_RIM = 0x1
 NOALLOC_SCRATCH_BYTES = 32 << 20
 KERNELS = ["restrict", "row_fwd", "col", "row_inv"]
@@ -62,6 +64,12 @@ _lib.sgf_plan_stats_get.argtypes = [ctypes.c_void_p, ctypes.POINTER(PlanStats)]
 _lib.sgf_solve.argtypes = [ctypes.c_void_p, _vpp, _vpp, _vpp, ctypes.c_void_p]
 _lib.sgf_solve_host.argtypes = [ctypes.c_void_p, _vpp, _vpp, _vpp, ctypes.c_void_p]
 _lib.sgf_solve_noalloc.argtypes = [ctypes.c_void_p, _vpp, _vpp, _vpp, ctypes.c_void_p]
+_lib.sgf_batch_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.c_uint32,
+                                  ctypes.POINTER(ctypes.c_void_p)]
+_lib.sgf_batch_solve.argtypes = [ctypes.c_void_p, ctypes.POINTER(_vpp), ctypes.POINTER(_vpp), ctypes.POINTER(_vpp),
+                                 ctypes.c_void_p]
+_lib.sgf_batch_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+_lib.sgf_batch_destroy.argtypes = [ctypes.c_void_p]
 _lib.sgf_solve_batched.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32,
                                    ctypes.POINTER(_vpp), ctypes.POINTER(_vpp), ctypes.POINTER(_vpp),
                                    ctypes.c_void_p]
@@ -72,7 +80,7 @@ _lib.sgf_last_error.restype = ctypes.c_char_p
 _lib.sgf_version.restype = ctypes.c_char_p
 for _f in ("sgf_plan_create", "sgf_plan_create_ex", "sgf_plan_check", "sgf_plan_share", "sgf_plan_stats_get", "sgf_solve", "sgf_solve_host",
            "sgf_solve_batched", "sgf_plan_destroy", "sgf_plan_profile", "sgf_plan_profile_read",
-           "sgf_solve_noalloc"):
+           "sgf_solve_noalloc", "sgf_batch_create", "sgf_batch_solve", "sgf_batch_info", "sgf_batch_destroy"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -245,6 +253,50 @@ def solve_batched(plans: Sequence[Plan], sigma, fx, fy, stream=None):
 
     _check(_lib.sgf_solve_batched(ph, n, table(sigma), table(fx), table(fy),
                                   ctypes.c_void_p(_stream_handle(stream))), "sgf_solve_batched")
+
+
+def _ptr_table(lists, keep):
+    arrs = []
+    for lst in lists:
+        a = _ptrs([t.data_ptr() if hasattr(t, "data_ptr") else int(t) for t in lst])
+        keep.append(a)
+        arrs.append(ctypes.cast(a, _vpp))
+    return (_vpp * len(arrs))(*arrs)
+
+
+class Batch:
+    """Fused solve of many independent nests (sgf_batch_*): one launch per pass and
+    per group of equal N, replayed as a CUDA graph."""
+
+    def __init__(self, plans: Sequence[Plan], graph: bool = True):
+        self.plans = list(plans)
+        n = len(self.plans)
+        ph = (ctypes.c_void_p * n)(*[p.handle for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(_lib.sgf_batch_create(ph, n, 0 if graph else BATCH_NO_GRAPH, ctypes.byref(h)), "sgf_batch_create")
+        self._h = h
+
+    def info(self) -> dict:
+        g, l = ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.sgf_batch_info(self._h, ctypes.byref(g), ctypes.byref(l)), "sgf_batch_info")
+        return {"groups": g.value, "launches_per_solve": l.value}
+
+    def solve(self, sigma, fx, fy, stream=None):
+        """sigma[k], fx[k], fy[k]: per-level CUDA tensors (or device pointers) of nest k."""
+        keep = []
+        _check(_lib.sgf_batch_solve(self._h, _ptr_table(sigma, keep), _ptr_table(fx, keep), _ptr_table(fy, keep),
+                                    ctypes.c_void_p(_stream_handle(stream))), "sgf_batch_solve")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.sgf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def create_status(nest, precision, flags: int = 0) -> int:

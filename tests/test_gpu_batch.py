@@ -1,0 +1,59 @@
+"""Fused batches (sgf_batch_*): many independent nests of uneven N, level count
+and path solved with one launch per pass and per N group, replayed as a CUDA
+graph.  Every nest's result must equal its own single solve bitwise (the same
+kernels do the same arithmetic), call after call, with and without the graph."""
+import numpy as np
+import pytest
+
+from paper_1603_03142_gb300 import workloads as W
+from tests._gpu import run_gpu, sgf, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return sgf()
+
+
+def _problems(seed, count):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(count):
+        n = int(rng.choice([16, 32, 64, 128]))
+        L = int(rng.integers(1, min(4, n.bit_length() - 3) + 1))
+        out.append(W.random_nest_problem(rng, n, L))
+    return out
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_batch_equals_single_solves(lib, graph):
+    probs = _problems(21, 24)
+    plans = [lib.Plan(nest, "fp32") for nest, _ in probs]
+    # one zero-rim single-level nest in the mix (its own kernel group)
+    zr = W.Nest(n=64)
+    zs = np.zeros((64, 64))
+    zs[2:-2, 2:-2] = np.random.Generator(np.random.PCG64(3)).uniform(0.1, 1.0, (60, 60))
+    plans.append(lib.Plan(zr, "fp32", zero_rim=True))
+    probs.append((zr, [zs]))
+    batch = lib.Batch(plans, graph=graph)
+    info = batch.info()
+    assert info["groups"] >= 4 and info["launches_per_solve"] <= 3 * info["groups"] + 3
+    for call in range(3):
+        sig = [[torch.from_numpy(a * (1.0 + 0.1 * call)).float().cuda() for a in s] for _, s in probs]
+        fx = [[torch.empty_like(a) for a in s] for s in sig]
+        fy = [[torch.empty_like(a) for a in s] for s in sig]
+        batch.solve(sig, fx, fy)
+        torch.cuda.synchronize()
+        for k, (nest, s) in enumerate(probs):
+            gx, gy = run_gpu(plans[k], [a * (1.0 + 0.1 * call) for a in s])
+            for l in range(nest.levels):
+                assert np.array_equal(fx[k][l].double().cpu().numpy(), gx[l]), (call, k, l)
+                assert np.array_equal(fy[k][l].double().cpu().numpy(), gy[l]), (call, k, l)
+    plans[-1].check()
+
+
+def test_batch_rejects_duplicates(lib):
+    p = lib.Plan(W.Nest(n=16), "fp32")
+    with pytest.raises(lib.SgfError):
+        lib.Batch([p, p])
