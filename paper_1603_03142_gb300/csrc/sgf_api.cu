@@ -836,8 +836,13 @@ sgf_status batch_launches(sgf_batch *bt, cudaStream_t st)
     cudaError_t e;
     if ((e = cudaMemcpyAsync(bt->d_args, bt->h_args, bt->args_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return cuda_fail(e, "batch argument upload");
-    // External: inside a stream capture this becomes an event-record node the host can wait on
-    if ((e = cudaEventRecordWithFlags(bt->uploaded, st, cudaEventRecordExternal)) != cudaSuccess)
+    // inside a stream capture the record must be external to become a node the host can wait on
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(st, &cs)) != cudaSuccess)
+        return cuda_fail(e, "cudaStreamIsCapturing");
+    e = cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(bt->uploaded, st, cudaEventRecordExternal)
+                                            : cudaEventRecord(bt->uploaded, st);
+    if (e != cudaSuccess)
         return cuda_fail(e, "cudaEventRecord(batch upload)");
     for (size_t d = 0; d < bt->restrict_jobs.size(); ++d)
         if ((e = launch_restrict_batch<T>(args, bt->d_maps + bt->restrict_off[d], bt->restrict_jobs[d], bt->max_n, st)) !=
