@@ -311,6 +311,71 @@ def run_gpu(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args, world, rank, local):
+    """Batched workload: independent concentric nests of uneven N and level
+    count solved as one fused batch (sgf_batch_*).  value = all cells of all
+    levels of all nests / device time per batch solve.  Nests shard across ranks
+    by cost (replicas: no data-path collective)."""
+    import numpy as np
+    import torch
+    from paper_1603_03142_gb300 import replicas, sgf, workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    probs = W.config4(count=args.nests, seed=0)
+    costs = [replicas.nest_cost(nest.n, nest.levels) for nest, _ in probs]
+    mine = replicas.shard_by_cost(costs, rank, world)
+    t0 = time.perf_counter()
+    base, plans = {}, []
+    for k in mine:
+        nest = probs[k][0]
+        key = nest.key()
+        if key not in base:
+            base[key] = sgf.Plan(nest, "fp32")
+            plans.append(base[key])
+        else:
+            plans.append(base[key].share())
+    plan_s = time.perf_counter() - t0
+    sig = [[torch.from_numpy(a.astype(np.float32)).to(dev) for a in probs[k][1]] for k in mine]
+    fx = [[torch.empty_like(a) for a in s] for s in sig]
+    fy = [[torch.empty_like(a) for a in s] for s in sig]
+    batch = sgf.Batch(plans)
+    info = batch.info()
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        batch.solve(sig, fx, fy, stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            batch.solve(sig, fx, fy, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    cells = sum(probs[k][0].levels * probs[k][0].n ** 2 for k in range(len(probs)))
+    if rank != 0:
+        return
+    shapes = sorted({(p.n, p.levels) for p in base.values()})
+    line = {"metric": METRIC, "value": cells * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batched-{args.nests}-nests-N128-1024-L1-4", "nests": args.nests,
+                       "cells_per_batch": cells, "parallelism": f"replicas{world}", "shapes": len(shapes),
+                       "kernel_groups": info["groups"], "launches_per_batch": info["launches_per_solve"],
+                       "graph": True, "plan_s": plan_s,
+                       "spectra_gib": sum(p.stats()["spectra_bytes"] for p in base.values()) / 2**30},
+            "gpu_launches": args.steps * info["launches_per_solve"], "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -321,6 +386,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--general", action="store_true", help="time only the general three-field path")
+    ap.add_argument("--workload", default="uniform", choices=["uniform", "batched"])
+    ap.add_argument("--nests", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3
@@ -332,7 +399,10 @@ def main():
         run_reference(args, world, rank)
         return
     world, rank, local = dist_setup()
-    run_gpu(args, world, rank, local)
+    if args.workload == "batched":
+        run_batched(args, world, rank, local)
+    else:
+        run_gpu(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
