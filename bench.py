@@ -242,6 +242,24 @@ def run_gpu(args, world, rank, local):
                                  if v["launches"]},
                    "algorithmic_bytes_per_solve": plan_general.stats()["algorithmic_bytes"]}
 
+    bf16x = None
+    if not args.no_bf16x:
+        # the split-BF16 tensor-core path side by side: same workload, same launch shape
+        plan_bf = sgf.Plan(nest, "bf16x", zero_rim=not args.general)
+        bms, bprof = timed(plan_bf, args.steps)
+        ref_x, ref_y = torch.empty_like(base), torch.empty_like(base)
+        plan.solve_ptrs([sig[0].data_ptr()], [ref_x.data_ptr()], [ref_y.data_ptr()], stream)
+        plan_bf.solve_ptrs([sig[0].data_ptr()], [fx[0].data_ptr()], [fy[0].data_ptr()], stream)
+        torch.cuda.synchronize()
+        plan_bf.check()
+        scale = max(ref_x.abs().max().item(), ref_y.abs().max().item())
+        rel = max((fx[0] - ref_x).abs().max().item(), (fy[0] - ref_y).abs().max().item()) / scale
+        bf16x = {"cells_per_s": world * cells * args.steps / (bms / 1e3), "ms_per_step": bms / args.steps,
+                 "kernel_ms": {k: v["ms"] / max(1, v["launches"]) for k, v in bprof["kernels"].items()
+                               if v["launches"]},
+                 "rel_linf_vs_fp32": rel}
+        plan_bf.close()
+
     # e2e: host buffers through the C ABI, copies inside the timed region
     pin_s = torch.from_numpy(sigma[0].astype(np.float32)).pin_memory()
     pin_x = torch.empty((n, n), dtype=torch.float32).pin_memory()
@@ -294,6 +312,7 @@ def run_gpu(args, world, rank, local):
                    "precision": "fp32", "parallelism": f"replicas{world}",
                    "path": "general-3-field" if args.general else "zero-rim-merged (verified per solve)",
                    "general_path": general,
+                   "bf16x_path": bf16x,
                    "l2": f"{sets} rotating input/output sets ({sets * 3 * n * n * 4 / 2**20:.0f} MiB) > 129 MiB L2",
                    "plan_ms": st["plan_ms"], "spectra_mib": st["spectra_bytes"] / 2**20,
                    "algorithmic_bytes_per_solve": st["algorithmic_bytes"],
@@ -376,6 +395,82 @@ def run_batched(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args, world, rank, local):
+    """Serving workload: an open-loop Poisson stream of force requests with host
+    buffers, served by the request loop (sgf_server_*): continuous admission by
+    HBM footprint onto concurrent streams, spectra resident per shape.  Every
+    shape is warmed once (spectra built) before the timed stream.  value = cells
+    of the completed requests / span from the first arrival to the last
+    completion; latency percentiles over the timed stream.  Each rank serves its
+    own stream (replicas: seed + rank)."""
+    import numpy as np
+    import torch
+    from paper_1603_03142_gb300 import serving, sgf
+
+    torch.cuda.set_device(local)
+    sizes = tuple(int(x) for x in args.sizes.split(","))
+    lv = tuple(int(x) for x in args.levels.split(","))
+    precs = tuple(args.precisions.split(","))
+    arr = serving.poisson_arrivals(args.rate, args.seconds, args.seed + rank, sizes, (lv[0], lv[-1]), precs)
+    shapes = sorted({(a.n, a.levels, a.precision) for a in arr})
+    t0 = time.perf_counter()
+    pools = serving.make_pools(shapes, seed=args.seed)
+    pool_s = time.perf_counter() - t0
+    budget = int(args.budget_gb * 2 ** 30)
+    srv = sgf.Server(hbm_budget=budget, max_inflight=args.inflight)
+    # warm-up: one request per shape (builds and keeps its spectra), then a short stream
+    t0 = time.perf_counter()
+    warm = [serving.Arrival(0.0, n, L, p, 0) for (n, L, p) in shapes]
+    wrec, _ = serving.run_stream(srv, warm, pools, id_base=10 ** 8)
+    for k in range(max(0, args.warmup - 1)):
+        serving.run_stream(srv, arr[: max(1, len(arr) // 20)], pools, id_base=10 ** 8 + (k + 1) * 10 ** 6)
+    warm_s = time.perf_counter() - t0
+    accepted = {(r.n, r.levels) for r in wrec if r.status == sgf.SGF_OK}
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        recs, _ = serving.run_stream(srv, arr, pools)
+    summ = serving.summarize(recs, args.seconds)
+    st = srv.stats()
+    launches, h2d, d2h = 0, 0, 0
+    for r in recs:
+        if r.status == sgf.SGF_OK:
+            launches += (r.levels - 1) + 3 + (1 if r.levels > 1 else 0)
+            h2d += r.levels * r.n * r.n * 4
+            d2h += 2 * r.levels * r.n * r.n * 4
+    srv.close()
+    value = summ.get("cells_per_s", 0.0)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([value, summ.get("span_s", 0.0)], device=torch.device("cuda", local), dtype=torch.float64)
+        vals = [torch.zeros_like(t) for _ in range(world)]
+        dist.all_gather(vals, t)
+        value = float(sum(v[0].item() for v in vals))
+    if rank != 0:
+        return
+    done = max(1, summ.get("completed", 0))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": summ.get("completed", 0),
+            "warmup": args.warmup, "ms_per_step": summ.get("mean_ms"), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"serving-poisson-{args.rate:g}rps-{args.seconds:g}s-N{sizes[0]}-{sizes[-1]}"
+                                   f"-L{lv[0]}-{lv[-1]}-{'+'.join(precs)}",
+                       "requests": len(recs), "shapes": len(shapes), "shapes_served": sorted(accepted),
+                       "hbm_budget_gib": args.budget_gb, "max_inflight": args.inflight,
+                       "parallelism": f"replicas{world}", "pool_s": pool_s, "warm_s": warm_s,
+                       "inputs": "pinned host buffers, copies inside the latency"},
+            "latency_ms": {k: summ.get(k) for k in ("p50_ms", "p90_ms", "p99_ms", "max_ms", "mean_ms")},
+            "load": {"offered_rps": summ.get("offered_rps"), "achieved_rps": summ.get("achieved_rps"),
+                     "offered_cells_per_s": summ.get("offered_cells_per_s"), "completed": summ.get("completed"),
+                     "rejected": summ.get("rejected"), "failed": summ.get("failed")},
+            "server": {k: st[k] for k in ("inflight_peak", "slots", "shapes_resident", "shapes_built",
+                                          "slots_evicted", "bytes_peak")},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d / done, "d2h_bytes_per_step": d2h / done},
+            "gpu_launches": launches, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -386,8 +481,17 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--general", action="store_true", help="time only the general three-field path")
-    ap.add_argument("--workload", default="uniform", choices=["uniform", "batched"])
+    ap.add_argument("--no-bf16x", action="store_true", help="skip the split-BF16 tensor-core path")
+    ap.add_argument("--workload", default="uniform", choices=["uniform", "batched", "serving"])
     ap.add_argument("--nests", type=int, default=256)
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate (requests/s)")
+    ap.add_argument("--seconds", type=float, default=30.0, help="serving: length of the arrival stream")
+    ap.add_argument("--sizes", default="256,512,1024,2048", help="serving: n of the requests")
+    ap.add_argument("--levels", default="2,5", help="serving: min,max levels of the requests")
+    ap.add_argument("--budget-gb", type=float, default=120.0, help="serving: server HBM budget (GiB)")
+    ap.add_argument("--inflight", type=int, default=4, help="serving: requests on the device at once")
+    ap.add_argument("--precisions", default="fp32,bf16x", help="serving: precisions drawn uniformly per request")
+    ap.add_argument("--seed", type=int, default=0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3
@@ -401,6 +505,8 @@ def main():
     world, rank, local = dist_setup()
     if args.workload == "batched":
         run_batched(args, world, rank, local)
+    elif args.workload == "serving":
+        run_serving(args, world, rank, local)
     else:
         run_gpu(args, world, rank, local)
     if world > 1:

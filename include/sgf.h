@@ -65,7 +65,12 @@ typedef enum {
 typedef enum {
     SGF_FP64 = 0,   /* FP64 everywhere; I/O double */
     SGF_FP32 = 1,   /* FP32 transforms and spectra (spectra built in FP64); I/O float */
-    SGF_BF16X = 2   /* reserved: split-BF16 tensor-core butterflies, FP32 I/O */
+    SGF_BF16X = 2   /* FP32 data, I/O and spectra; the 16-point DFTs of every radix-16 FFT
+                       stage run on the tensor cores (tcgen05) as split-BF16 products
+                       (hi*hi + hi*lo + lo*hi) accumulated in FP32.  Relative force error
+                       about 1e-5 (bound 1e-4).  sgf_plan_check reports SGF_ETIMEOUT if a
+                       bounded wait for tensor-core completion expired.  Nests of
+                       n = SGF_MAX_N with levels > 1 are SGF_EUNSUPPORTED. */
 } sgf_precision;
 
 /* Nest descriptor (Sec. 2.1: nested domains Omega^l, one patch per level,
@@ -122,8 +127,10 @@ sgf_status sgf_plan_create_ex(const sgf_nest_desc *desc, sgf_precision precision
                               sgf_plan **out);
 
 /* Waits for this plan's last solve and reports what the device recorded for
- * the solves since the previous check: SGF_EINVAL when a SGF_PLAN_ZERO_RIM
- * guarantee was violated, SGF_OK otherwise.  Clears the record. */
+ * the solves since the previous check: SGF_ETIMEOUT when a bounded wait for
+ * tensor-core completion expired (SGF_BF16X), SGF_EINVAL when a
+ * SGF_PLAN_ZERO_RIM guarantee was violated, SGF_OK otherwise.  Clears the
+ * record. */
 sgf_status sgf_plan_check(sgf_plan *plan);
 
 /* A new plan with its own workspace that shares src's kernel spectra (no
@@ -220,6 +227,144 @@ const char *sgf_last_error(void);
  * n = 512 needs 10 MiB and fits; n = 1024 needs 40 MiB and does not). */
 sgf_status sgf_solve_noalloc(sgf_plan *plan, const void *const *sigma, void *const *fx, void *const *fy,
                              void *stream);
+
+/* ---- Tile schedule and autotuner (no paper counterpart) -----------------
+ * Two passes have more than one kernel schedule.  The schedules perform the
+ * same arithmetic in the same order, so the forces do not depend on the choice
+ * (bit for bit); only the time does.
+ *   col_pass (SGF_PLAN_ZERO_RIM plans): 0 = the two inverse column transforms
+ *     one after the other (one sequence per thread; three CTAs per SM at
+ *     n = 4096), 1 = both in flight (two sequences per thread sharing the
+ *     barriers; two CTAs per SM).
+ *   row_inv0: 0 = level 0's inverse row pass with one CTA per (row pair,
+ *     component), the finer levels through the nest kernel; 1 = every level
+ *     through the nest kernel (one CTA per row pair, both components, the
+ *     gather of the second overlapping the first's transform).
+ * A new plan starts from {0, 0}, or from the schedule the autotuner recorded for
+ * its key (device, n, precision, zero-rim, levels > 1); sgf_plan_share copies it. */
+typedef struct {
+    int32_t col_pass;
+    int32_t row_inv0;
+} sgf_schedule;
+
+sgf_status sgf_plan_schedule_get(const sgf_plan *plan, sgf_schedule *schedule);
+/* Errors: SGF_EINVAL for a NULL argument or a choice other than 0 or 1. */
+sgf_status sgf_plan_schedule_set(sgf_plan *plan, const sgf_schedule *schedule);
+
+/* The autotuner: runs one solve on zero density (temporary device buffers),
+ * then times every candidate of each pass on this plan's own intermediates --
+ * one warm-up launch and `reps` (1..1000) timed launches, CUDA events on
+ * `stream` -- keeps the fastest in the plan and records it for later plans of
+ * the same key: in the process, and in the text file named by the environment
+ * variable SGF_AUTOTUNE_CACHE if it is set (one line "<key> <col_pass>
+ * <row_inv0>" per key, read once, rewritten after each tuning).  chosen (may be
+ * NULL) receives the schedule; ms (may be NULL, else 4 doubles) the mean
+ * milliseconds per launch of col_pass 0, col_pass 1, row_inv0 0, row_inv0 1
+ * (-1 where a pass has a single candidate).  Blocks until done.
+ * Errors: SGF_EINVAL, SGF_ENOMEM, SGF_ECUDA. */
+sgf_status sgf_plan_autotune(sgf_plan *plan, int32_t reps, void *stream, sgf_schedule *chosen, double *ms);
+
+/* Device memory a plan for this nest would hold, computed on the host without
+ * creating it (no CUDA call; the paper has no counterpart).  workspace_bytes:
+ * what sgf_plan_create / sgf_plan_share allocate for the plan itself;
+ * spectra_bytes: its kernel spectra (once per set of sharing plans);
+ * build_bytes: transient memory of the table generator while sgf_plan_create
+ * builds the spectra (freed before it returns).  Errors as sgf_plan_create_ex
+ * for the descriptor, precision and flags; SGF_EINVAL for a NULL output. */
+sgf_status sgf_plan_estimate(const sgf_nest_desc *desc, sgf_precision precision, uint32_t flags,
+                             size_t *workspace_bytes, size_t *spectra_bytes, size_t *build_bytes);
+
+/* ---- Request loop (no paper counterpart: serving many force solves) ------
+ * A server takes force requests with host input and output buffers and runs
+ * them on the current CUDA device, continuously: whenever a request finishes,
+ * the requests waiting in the queue are admitted, in arrival order, as long as
+ * a slot is free (at most max_inflight requests on the device at once) and the
+ * device memory it needs fits the budget.  Each slot owns a CUDA stream, a plan
+ * and device copies of one request's sigma and forces, so the copies and
+ * kernels of admitted requests overlap on the device.  Kernel spectra stay
+ * resident per nest shape (n, levels, offsets, precision, plan flags) as long
+ * as a slot of that shape exists; new slots of a resident shape share them
+ * (sgf_plan_share).  When memory is short the least recently used idle slots
+ * are destroyed first, and a shape's spectra go with its last slot.  A server
+ * is driven by one host thread and calls no CUDA function outside its calls.
+ *
+ * Memory counted against hbm_budget: resident spectra, every slot's plan
+ * workspace and buffers (3 x levels x n^2 elements), and, while a new shape's
+ * spectra are built, the generator's transient memory (sgf_plan_estimate).
+ * Building a shape blocks the calling thread for the generation time; the
+ * device keeps running the admitted requests meanwhile. */
+typedef struct sgf_server sgf_server;
+
+/* SGF_SERVER_SIMULATE: no device work and no CUDA call; a request "runs" for
+ * (its slot's plan workspace + buffers + spectra bytes) / simulate_gbs after
+ * admission.  For testing the admission logic without a GPU; results are not
+ * written. */
+#define SGF_SERVER_SIMULATE 0x1u
+
+typedef struct {
+    size_t hbm_budget;     /* device bytes the server may hold; 0 = 90% of the free memory at creation */
+    int32_t max_inflight;  /* requests on the device at once, >= 1 */
+    uint32_t flags;        /* SGF_SERVER_* */
+    double simulate_gbs;   /* SGF_SERVER_SIMULATE: modelled rate in GB/s (> 0) */
+} sgf_server_config;
+
+/* One force request.  sigma[l], fx[l], fy[l] (l < desc.levels) are HOST arrays
+ * of n*n elements (double for SGF_FP64, float otherwise), row-major as for
+ * sgf_solve.  The caller keeps them valid and untouched from sgf_server_submit
+ * until the request's completion is returned; pinned host memory lets the
+ * copies overlap other requests' kernels.  id is the caller's tag. */
+typedef struct {
+    uint64_t id;
+    sgf_nest_desc desc;
+    sgf_precision precision;
+    uint32_t plan_flags;   /* as sgf_plan_create_ex */
+    const void *sigma[SGF_MAX_LEVELS];
+    void *fx[SGF_MAX_LEVELS];
+    void *fy[SGF_MAX_LEVELS];
+} sgf_request;
+
+typedef struct {
+    uint64_t id;
+    int32_t status;        /* sgf_status of the request's solve (SGF_OK: fx, fy hold the forces) */
+    int32_t slot;          /* slot index that ran it */
+    int32_t built_shape;   /* 1 if its admission built the shape's spectra */
+    int32_t pad;
+    double t_submit;       /* server clock (sgf_server_clock) at sgf_server_submit */
+    double t_admit;        /* ... when its copies and kernels were issued */
+    double t_done;         /* ... when a sgf_server_progress call saw it finished */
+} sgf_completion;
+
+typedef struct {
+    int64_t submitted, admitted, completed, rejected;
+    int32_t queued, inflight, inflight_peak, slots;
+    int32_t shapes_resident, pad;
+    int64_t shapes_built, slots_evicted;
+    size_t bytes_used, bytes_peak, hbm_budget;
+} sgf_server_stats;
+
+/* Errors: SGF_EINVAL (bad config), SGF_ECUDA. */
+sgf_status sgf_server_create(const sgf_server_config *config, sgf_server **out);
+
+/* Seconds since the server was created (steady clock). */
+double sgf_server_clock(const sgf_server *server);
+
+/* Queue a request (copied; the buffers are not touched yet).  Errors:
+ * SGF_EINVAL / SGF_EUNSUPPORTED for the descriptor, precision or buffers;
+ * SGF_ENOMEM if the request could never fit hbm_budget (rejected, not queued). */
+sgf_status sgf_server_submit(sgf_server *server, const sgf_request *request);
+
+/* One turn of the loop: collects the requests that have finished, then admits
+ * queued requests while a slot and memory allow.  Writes up to `capacity`
+ * completions (oldest first) to out and their number to *count; any others are
+ * returned by later calls.  Does not wait for the device.  Errors: SGF_EINVAL,
+ * SGF_ECUDA / SGF_ENOMEM when creating a slot failed (the request stays queued). */
+sgf_status sgf_server_progress(sgf_server *server, sgf_completion *out, int32_t capacity, int32_t *count);
+
+sgf_status sgf_server_stats_get(const sgf_server *server, sgf_server_stats *stats);
+
+/* Waits for the requests on the device, then frees every slot and spectrum.
+ * Completions not yet returned are dropped. */
+sgf_status sgf_server_destroy(sgf_server *server);
 
 /* Library version string, e.g. "sgf 0.1.0 sm_103a". */
 const char *sgf_version(void);

@@ -24,11 +24,12 @@
 
 #include "../../include/sgf.h"
 #include "sgf_fft16.cuh"
+#include "sgf_host.h"
 #include "sgf_internal.h"
 
 using namespace sgf;
 
-namespace {
+namespace sgf {
 
 thread_local std::string g_err = "no error";
 
@@ -48,6 +49,10 @@ sgf_status cuda_fail(cudaError_t e, const char *what)
     return fail(e == cudaErrorMemoryAllocation ? SGF_ENOMEM : SGF_ECUDA, "%s: %s (%s)", what,
                 cudaGetErrorName(e), cudaGetErrorString(e));
 }
+
+}  // namespace sgf
+
+namespace {
 
 int ilog2(int n)
 {
@@ -95,6 +100,8 @@ struct sgf_plan {
     sgf_precision prec = SGF_FP32;
     uint32_t flags = 0;
     bool merged = false;       // SGF_PLAN_ZERO_RIM: one forward field, merged spectra
+    bool tc = false;           // SGF_BF16X: split-BF16 tensor-core radix-16 tiles (FP32 data)
+    sgf_schedule sched{};      // tile schedule of the transform passes (autotuner)
     int *d_status = nullptr;   // device status word (STATUS_* bits)
     cudaEvent_t done = nullptr;  // recorded after every solve (sgf_plan_check)
     int N = 0, logN = 0, L = 0, device = 0;
@@ -139,8 +146,10 @@ struct sgf_batch {
     struct Group {
         int logN = 0;
         bool merged = false;
-        int n_fwd = 0, n_col = 0, n_inv = 0;  // map entries per pass
-        size_t map_fwd = 0, map_col = 0, map_inv = 0;  // int2 offsets in the map buffer
+        bool tc = false;
+        sgf_schedule sched{};  // of the group's first plan
+        int n_fwd = 0, n_col = 0, n_inv1 = 0, n_inv = 0;  // map entries per pass (inv1: level 0)
+        size_t map_fwd = 0, map_col = 0, map_inv1 = 0, map_inv = 0;  // int2 offsets in the map buffer
     };
     std::vector<Group> groups;
     std::vector<int> restrict_jobs;   // count per restriction depth
@@ -183,8 +192,8 @@ sgf_status validate(const sgf_nest_desc *d, sgf_precision prec)
         return fail(SGF_EUNSUPPORTED, "n = %d above SGF_MAX_N = %d", n, SGF_MAX_N);
     if (prec == SGF_FP64 && n > SGF_MAX_N_FP64)
         return fail(SGF_EUNSUPPORTED, "n = %d above SGF_MAX_N_FP64 = %d", n, SGF_MAX_N_FP64);
-    if (prec == SGF_BF16X)
-        return fail(SGF_EUNSUPPORTED, "SGF_BF16X is not available in this build");
+    if (prec == SGF_BF16X && n == SGF_MAX_N && d->levels > 1)
+        return fail(SGF_EUNSUPPORTED, "SGF_BF16X nests (levels > 1) need n < %d", SGF_MAX_N);
     return SGF_OK;
 }
 
@@ -418,6 +427,19 @@ size_t align_push(std::vector<unsigned char> &blob, const std::vector<X> &v)
     return off;
 }
 
+// Device bytes plan_alloc_owned allocates for p (lists, intermediates, restricted densities).
+size_t workspace_of(const sgf_plan *p)
+{
+    std::vector<unsigned char> blob;
+    align_push(blob, p->slabs);
+    align_push(blob, p->items);
+    align_push(blob, p->outs);
+    align_push(blob, p->ins);
+    align_push(blob, p->contribs);
+    return blob.size() + (p->fwd_elems + p->bwd_elems) * 2 * p->esize +
+           (size_t)(p->L > 1 ? p->L - 1 : 0) * p->N * p->N * p->esize;
+}
+
 // Allocate the plan's own device memory and upload its lists.
 sgf_status plan_alloc_owned(sgf_plan *p)
 {
@@ -453,8 +475,7 @@ sgf_status plan_alloc_owned(sgf_plan *p)
         return cuda_fail(e, "cudaMemset(status word)");
     if ((e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming)) != cudaSuccess)
         return cuda_fail(e, "cudaEventCreate(solve completion)");
-    p->workspace_bytes = blob.size() + (p->fwd_elems + p->bwd_elems) * Cb +
-                         (size_t)(p->L > 1 ? p->L - 1 : 0) * p->N * p->N * p->esize;
+    p->workspace_bytes = workspace_of(p);
     return SGF_OK;
 }
 
@@ -475,6 +496,13 @@ void twiddles(int P, std::vector<double> &re, std::vector<double> &im)
         re[k] = (double)c;
         im[k] = -(double)s;
     }
+}
+
+// Transient device memory of the table generator (FP64 tables, half spectra, twiddles).
+size_t gen_workspace_bytes(int N)
+{
+    const size_t P = 2 * (size_t)N;
+    return 6 * P * P * sizeof(double) + 6 * (size_t)(N + 1) * P * sizeof(double2) + P * sizeof(double2);
 }
 
 template <typename T>
@@ -545,12 +573,19 @@ sgf_status build_spectra(sgf_plan *p)
     }
     if (st == SGF_OK && (e = gen_kernels_init()) != cudaSuccess)
         st = cuda_fail(e, "table kernels init");
+    // a private stream: generation neither waits for nor holds up other streams' solves
+    cudaStream_t gs = nullptr;
+    if (st == SGF_OK && (e = cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking)) != cudaSuccess)
+        st = cuda_fail(e, "cudaStreamCreate(table generation)");
     for (size_t k = 0; st == SGF_OK && k < p->sets.size(); ++k) {
-        if ((e = launch_gen_set<T>(p->sets[k], N, p->logN, d_tw64, sp->dev, d_tables, d_half, 0)) != cudaSuccess)
+        if ((e = launch_gen_set<T>(p->sets[k], N, p->logN, d_tw64, sp->dev, d_tables, d_half, gs)) != cudaSuccess)
             st = cuda_fail(e, "kernel table generation launch");
     }
-    if (st == SGF_OK && (e = cudaDeviceSynchronize()) != cudaSuccess)
-        st = cuda_fail(e, "kernel table generation");
+    if (gs) {
+        if ((e = cudaStreamSynchronize(gs)) != cudaSuccess && st == SGF_OK)
+            st = cuda_fail(e, "kernel table generation");
+        cudaStreamDestroy(gs);
+    }
     cudaFree(d_tw64);
     cudaFree(d_tables);
     cudaFree(d_half);
@@ -573,6 +608,25 @@ sgf_status mark(sgf_plan *p, cudaStream_t st)
         return cuda_fail(e, "cudaEventRecord(profile)");
     return SGF_OK;
 }
+
+// Inverse row passes of a solve.  Schedule row_inv0 = 0: level 0 (its own main
+// output alone) through k_row_inv1, the finer levels (main output plus Case-3
+// phases) through k_row_inv; row_inv0 = 1: every level through k_row_inv.
+template <typename T>
+cudaError_t launch_row_inv(int logN, int L, SolveArgs<T> a, cudaStream_t st, bool tc, int row_inv0)
+{
+    a.level_base = 0;
+    if (row_inv0 == 1)
+        return launch_pass_n<T>(PASS_ROW_INV, logN, a, L, st, nullptr, tc);
+    cudaError_t e = launch_pass_n<T>(PASS_ROW_INV1, logN, a, 1, st, nullptr, tc);
+    if (e != cudaSuccess || L == 1)
+        return e;
+    a.level_base = 1;
+    return launch_pass_n<T>(PASS_ROW_INV, logN, a, L - 1, st, nullptr, tc);
+}
+
+// Zero-rim column pass of the plan's schedule.
+inline int col_m_pass(const sgf_plan *p) { return p->sched.col_pass == 1 ? PASS_COL_MD : PASS_COL_M; }
 
 template <typename T>
 sgf_status solve_impl(sgf_plan *p, const void *const *sigma, void *const *fx, void *const *fy,
@@ -624,19 +678,19 @@ sgf_status solve_impl(sgf_plan *p, const void *const *sigma, void *const *fx, vo
     cudaError_t e;
     if ((ms = mark(p, st)) != SGF_OK)
         return ms;
-    e = p->merged ? launch_pass_n<T>(PASS_ROW_FWD_M, p->logN, a, 0, st)
-                  : launch_pass_n<T>(PASS_ROW_FWD, p->logN, a, (int)p->items.size(), st);
+    e = p->merged ? launch_pass_n<T>(PASS_ROW_FWD_M, p->logN, a, 0, st, nullptr, p->tc)
+                  : launch_pass_n<T>(PASS_ROW_FWD, p->logN, a, (int)p->items.size(), st, nullptr, p->tc);
     if (e != cudaSuccess)
         return cuda_fail(e, "row_fwd launch");
     if ((ms = mark(p, st)) != SGF_OK)
         return ms;
-    e = p->merged ? launch_pass_n<T>(PASS_COL_M, p->logN, a, 1, st)
-                  : launch_pass_n<T>(PASS_COL, p->logN, a, (int)p->outs.size(), st);
+    e = p->merged ? launch_pass_n<T>(col_m_pass(p), p->logN, a, 1, st, nullptr, p->tc)
+                  : launch_pass_n<T>(PASS_COL, p->logN, a, (int)p->outs.size(), st, nullptr, p->tc);
     if (e != cudaSuccess)
         return cuda_fail(e, "col launch");
     if ((ms = mark(p, st)) != SGF_OK)
         return ms;
-    if ((e = launch_pass_n<T>(PASS_ROW_INV, p->logN, a, L, st)) != cudaSuccess)
+    if ((e = launch_row_inv<T>(p->logN, L, a, st, p->tc, p->sched.row_inv0)) != cudaSuccess)
         return cuda_fail(e, "row_inv launch");
     if ((ms = mark(p, st)) != SGF_OK)
         return ms;
@@ -772,15 +826,15 @@ sgf_status solve_noalloc_impl(sgf_plan *p, const void *const *sigma, void *const
     a.contribs = p->d_contribs;
     for (int l = 0; l <= L; ++l)
         a.contrib_begin[l] = p->contrib_begin[l];
-    cudaError_t e = p->merged ? launch_pass_n<T>(PASS_ROW_FWD_M, p->logN, a, 0, st)
-                              : launch_pass_n<T>(PASS_ROW_FWD, p->logN, a, (int)p->items.size(), st);
+    cudaError_t e = p->merged ? launch_pass_n<T>(PASS_ROW_FWD_M, p->logN, a, 0, st, nullptr, p->tc)
+                              : launch_pass_n<T>(PASS_ROW_FWD, p->logN, a, (int)p->items.size(), st, nullptr, p->tc);
     if (e != cudaSuccess)
         return cuda_fail(e, "row_fwd launch");
-    e = p->merged ? launch_pass_n<T>(PASS_COL_M, p->logN, a, 1, st)
-                  : launch_pass_n<T>(PASS_COL, p->logN, a, (int)p->outs.size(), st);
+    e = p->merged ? launch_pass_n<T>(col_m_pass(p), p->logN, a, 1, st, nullptr, p->tc)
+                  : launch_pass_n<T>(PASS_COL, p->logN, a, (int)p->outs.size(), st, nullptr, p->tc);
     if (e != cudaSuccess)
         return cuda_fail(e, "col launch");
-    if ((e = launch_pass_n<T>(PASS_ROW_INV, p->logN, a, L, st)) != cudaSuccess)
+    if ((e = launch_row_inv<T>(p->logN, L, a, st, p->tc, p->sched.row_inv0)) != cudaSuccess)
         return cuda_fail(e, "row_inv launch");
     if ((e = cudaEventRecord(p->done, st)) != cudaSuccess)
         return cuda_fail(e, "cudaEventRecord(solve completion)");
@@ -850,13 +904,22 @@ sgf_status batch_launches(sgf_batch *bt, cudaStream_t st)
             return cuda_fail(e, "batched restriction launch");
     SolveArgs<T> dummy{};
     for (const auto &g : bt->groups) {
-        BatchView<T> vf{args, bt->d_maps + g.map_fwd}, vc{args, bt->d_maps + g.map_col}, vi{args, bt->d_maps + g.map_inv};
+        BatchView<T> vf{args, bt->d_maps + g.map_fwd}, vc{args, bt->d_maps + g.map_col};
+        BatchView<T> vi1{args, bt->d_maps + g.map_inv1}, vi{args, bt->d_maps + g.map_inv};
         dummy.N = 1 << g.logN;
-        if ((e = launch_pass_n<T>(g.merged ? PASS_ROW_FWD_M : PASS_ROW_FWD, g.logN, dummy, g.n_fwd, st, &vf)) != cudaSuccess)
+        if ((e = launch_pass_n<T>(g.merged ? PASS_ROW_FWD_M : PASS_ROW_FWD, g.logN, dummy, g.n_fwd, st, &vf, g.tc)) != cudaSuccess)
             return cuda_fail(e, "batched row_fwd launch");
-        if ((e = launch_pass_n<T>(g.merged ? PASS_COL_M : PASS_COL, g.logN, dummy, g.n_col, st, &vc)) != cudaSuccess)
+        const int colp = !g.merged ? PASS_COL : g.sched.col_pass == 1 ? PASS_COL_MD : PASS_COL_M;
+        if ((e = launch_pass_n<T>(colp, g.logN, dummy, g.n_col, st, &vc, g.tc)) != cudaSuccess)
             return cuda_fail(e, "batched col launch");
-        if ((e = launch_pass_n<T>(PASS_ROW_INV, g.logN, dummy, g.n_inv, st, &vi)) != cudaSuccess)
+        if (g.sched.row_inv0 == 1) {  // every level through k_row_inv (level-0 entries precede the others)
+            if ((e = launch_pass_n<T>(PASS_ROW_INV, g.logN, dummy, g.n_inv1 + g.n_inv, st, &vi1, g.tc)) != cudaSuccess)
+                return cuda_fail(e, "batched row_inv launch");
+            continue;
+        }
+        if ((e = launch_pass_n<T>(PASS_ROW_INV1, g.logN, dummy, g.n_inv1, st, &vi1, g.tc)) != cudaSuccess)
+            return cuda_fail(e, "batched row_inv1 launch");
+        if (g.n_inv > 0 && (e = launch_pass_n<T>(PASS_ROW_INV, g.logN, dummy, g.n_inv, st, &vi, g.tc)) != cudaSuccess)
             return cuda_fail(e, "batched row_inv launch");
     }
     return SGF_OK;
@@ -898,6 +961,8 @@ sgf_status batch_build(sgf_batch *bt)
             sgf_batch::Group g;
             g.logN = p->logN;
             g.merged = p->merged;
+            g.tc = p->tc;
+            g.sched = p->sched;
             bt->groups.push_back(g);
             members.emplace_back();
         }
@@ -924,12 +989,16 @@ sgf_status batch_build(sgf_batch *bt)
             for (int o = 0; o < (int)bt->plans[k]->outs.size(); ++o)
                 maps.push_back(make_int2(k, o));
         g.n_col = (int)(maps.size() - g.map_col);
+        g.map_inv1 = maps.size();
+        for (int k : members[gi])
+            maps.push_back(make_int2(k, 0));
+        g.n_inv1 = (int)(maps.size() - g.map_inv1);
         g.map_inv = maps.size();
         for (int k : members[gi])
-            for (int l = 0; l < bt->plans[k]->L; ++l)
+            for (int l = 1; l < bt->plans[k]->L; ++l)
                 maps.push_back(make_int2(k, l));
         g.n_inv = (int)(maps.size() - g.map_inv);
-        bt->launches += 3;
+        bt->launches += g.n_inv > 0 && g.sched.row_inv0 != 1 ? 4 : 3;
     }
     // restriction depths: depth d restricts level L-2-d of every nest that has it
     int maxL = 1;
@@ -964,7 +1033,7 @@ sgf_status batch_build(sgf_batch *bt)
         return cuda_fail(e, "cudaStreamCreate(batch capture)");
     SolveArgs<T> dummy{};
     for (const auto &g : bt->groups)
-        if ((e = launch_pass_n<T>(PASS_PREPARE, g.logN, dummy, 0, nullptr)) != cudaSuccess)
+        if ((e = launch_pass_n<T>(PASS_PREPARE, g.logN, dummy, 0, nullptr, nullptr, g.tc)) != cudaSuccess)
             return cuda_fail(e, "batch kernel attributes");
     return SGF_OK;
 }
@@ -1006,6 +1075,151 @@ sgf_status batch_solve(sgf_batch *bt, const void *const *const *sigma, void *con
 }
 }  // namespace
 
+// ---- autotuner record (sgf_plan_autotune) ----------------------------------
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::string, sgf_schedule> g_tune;
+bool g_tune_loaded = false;
+
+std::string tune_key(const sgf_plan *p)
+{
+    cudaDeviceProp prop{};
+    char dev[64] = "device";
+    if (cudaGetDeviceProperties(&prop, p->device) == cudaSuccess)
+        snprintf(dev, sizeof dev, "%s", prop.name);
+    for (char *c = dev; *c; ++c)
+        if (*c == ' ')
+            *c = '_';
+    char buf[160];
+    snprintf(buf, sizeof buf, "%s/n%d/p%d/zr%d/ml%d", dev, p->N, (int)p->prec, p->merged ? 1 : 0, p->L > 1 ? 1 : 0);
+    return buf;
+}
+
+// Load the table file named by SGF_AUTOTUNE_CACHE once (lines "<key> <col_pass> <row_inv0>").
+void tune_load_locked()
+{
+    if (g_tune_loaded)
+        return;
+    g_tune_loaded = true;
+    const char *path = getenv("SGF_AUTOTUNE_CACHE");
+    if (!path || !*path)
+        return;
+    FILE *f = fopen(path, "r");
+    if (!f)
+        return;
+    char key[160];
+    int a = 0, b = 0;
+    while (fscanf(f, "%159s %d %d", key, &a, &b) == 3)
+        if ((a == 0 || a == 1) && (b == 0 || b == 1))
+            g_tune[key] = sgf_schedule{a, b};
+    fclose(f);
+}
+
+void tune_store(const std::string &key, const sgf_schedule &s)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    g_tune[key] = s;
+    const char *path = getenv("SGF_AUTOTUNE_CACHE");
+    if (!path || !*path)
+        return;
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "w");
+    if (!f)
+        return;
+    for (const auto &kv : g_tune)
+        fprintf(f, "%s %d %d\n", kv.first.c_str(), kv.second.col_pass, kv.second.row_inv0);
+    fclose(f);
+    rename(tmp.c_str(), path);
+}
+
+void tune_apply(sgf_plan *p)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    auto it = g_tune.find(tune_key(p));
+    if (it != g_tune.end())
+        p->sched = it->second;
+}
+
+template <typename T>
+sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[4])
+{
+    const size_t lvl = (size_t)p->N * p->N * p->esize;
+    const size_t lal = (lvl + 255) & ~(size_t)255;
+    void *buf = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&buf, 3 * (size_t)p->L * lal)) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(autotune buffers)");
+    struct Free {
+        void *b;
+        ~Free() { cudaFree(b); }
+    } fr{buf};
+    if ((e = cudaMemsetAsync(buf, 0, 3 * (size_t)p->L * lal, st)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemset(autotune buffers)");
+    auto base = static_cast<unsigned char *>(buf);
+    const void *ds[kMaxLevels];
+    void *dx[kMaxLevels], *dy[kMaxLevels];
+    for (int l = 0; l < p->L; ++l) {
+        ds[l] = base + (size_t)l * lal;
+        dx[l] = base + (size_t)(p->L + l) * lal;
+        dy[l] = base + (size_t)(2 * p->L + l) * lal;
+    }
+    sgf_status s = solve_impl<T>(p, ds, dx, dy, st);  // fills the intermediates
+    if (s != SGF_OK)
+        return s;
+    SolveArgs<T> a;
+    fill_args<T>(p, ds, dx, dy, a);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+        if (e0)
+            cudaEventDestroy(e0);
+        return cuda_fail(e, "cudaEventCreate(autotune)");
+    }
+    auto timeit = [&](auto launch, double &out) -> sgf_status {
+        cudaError_t ee;
+        if ((ee = launch()) != cudaSuccess)  // warm-up
+            return cuda_fail(ee, "autotune launch");
+        if ((ee = cudaEventRecord(e0, st)) != cudaSuccess)
+            return cuda_fail(ee, "cudaEventRecord(autotune)");
+        for (int r = 0; r < reps; ++r)
+            if ((ee = launch()) != cudaSuccess)
+                return cuda_fail(ee, "autotune launch");
+        float t = 0.f;
+        if ((ee = cudaEventRecord(e1, st)) != cudaSuccess || (ee = cudaEventSynchronize(e1)) != cudaSuccess ||
+            (ee = cudaEventElapsedTime(&t, e0, e1)) != cudaSuccess)
+            return cuda_fail(ee, "autotune timing");
+        out = t / reps;
+        return SGF_OK;
+    };
+    for (int k = 0; k < 4; ++k)
+        ms[k] = -1.0;
+    sgf_schedule best = p->sched;
+    if (p->merged) {
+        for (int c = 0; c < 2 && s == SGF_OK; ++c)
+            s = timeit([&] { return launch_pass_n<T>(c ? PASS_COL_MD : PASS_COL_M, p->logN, a, 1, st, nullptr, p->tc); },
+                       ms[c]);
+        if (s == SGF_OK)
+            best.col_pass = ms[1] < ms[0] ? 1 : 0;
+    }
+    for (int c = 0; c < 2 && s == SGF_OK; ++c)
+        s = timeit([&] { return launch_row_inv<T>(p->logN, p->L, a, st, p->tc, c); }, ms[2 + c]);
+    if (s == SGF_OK)
+        best.row_inv0 = ms[3] < ms[2] ? 1 : 0;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s == SGF_OK && (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        s = cuda_fail(e, "autotune");
+    if (s == SGF_OK) {
+        p->sched = best;
+        tune_store(tune_key(p), best);
+    }
+    return s;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *sgf_last_error(void) { return g_err.c_str(); }
@@ -1035,6 +1249,7 @@ sgf_status sgf_plan_create_ex(const sgf_nest_desc *desc, sgf_precision precision
     p->prec = precision;
     p->flags = flags;
     p->merged = (flags & SGF_PLAN_ZERO_RIM) != 0;
+    p->tc = precision == SGF_BF16X;
     p->N = desc->n;
     p->logN = ilog2(desc->n);
     p->L = desc->levels;
@@ -1045,6 +1260,7 @@ sgf_status sgf_plan_create_ex(const sgf_nest_desc *desc, sgf_precision precision
         return cuda_fail(e, "cudaGetDevice");
     }
     build_lists(p);
+    tune_apply(p);
     s = precision == SGF_FP64 ? build_spectra<double>(p) : build_spectra<float>(p);
     if (s == SGF_OK)
         s = plan_alloc_owned(p);
@@ -1060,6 +1276,34 @@ sgf_status sgf_plan_create_ex(const sgf_nest_desc *desc, sgf_precision precision
     return SGF_OK;
 }
 
+sgf_status sgf_plan_estimate(const sgf_nest_desc *desc, sgf_precision precision, uint32_t flags,
+                             size_t *workspace_bytes, size_t *spectra_bytes, size_t *build_bytes)
+{
+    if (!workspace_bytes || !spectra_bytes || !build_bytes)
+        return fail(SGF_EINVAL, "NULL argument");
+    sgf_status s = validate(desc, precision);
+    if (s != SGF_OK)
+        return s;
+    if (flags & ~SGF_PLAN_ZERO_RIM)
+        return fail(SGF_EINVAL, "unknown plan flags 0x%x", flags);
+    if ((flags & SGF_PLAN_ZERO_RIM) && desc->levels != 1)
+        return fail(SGF_EINVAL, "SGF_PLAN_ZERO_RIM needs a single level (levels = %d)", desc->levels);
+    sgf_plan p;
+    p.desc = *desc;
+    p.prec = precision;
+    p.flags = flags;
+    p.merged = (flags & SGF_PLAN_ZERO_RIM) != 0;
+    p.N = desc->n;
+    p.logN = ilog2(desc->n);
+    p.L = desc->levels;
+    p.esize = precision == SGF_FP64 ? 8 : 4;
+    build_lists(&p);
+    *workspace_bytes = workspace_of(&p);
+    *spectra_bytes = spectra_total(&p);
+    *build_bytes = gen_workspace_bytes(p.N);
+    return SGF_OK;
+}
+
 sgf_status sgf_plan_share(const sgf_plan *src, sgf_plan **out)
 {
     if (!src || !out)
@@ -1071,6 +1315,8 @@ sgf_status sgf_plan_share(const sgf_plan *src, sgf_plan **out)
     p->prec = src->prec;
     p->flags = src->flags;
     p->merged = src->merged;
+    p->tc = src->tc;
+    p->sched = src->sched;
     p->N = src->N;
     p->logN = src->logN;
     p->L = src->L;
@@ -1102,7 +1348,8 @@ sgf_status sgf_plan_stats_get(const sgf_plan *p, sgf_plan_stats *st)
     st->forward_slabs = (int)p->slabs.size();
     st->outputs = (int)p->outs.size();
     st->spectra_sets = (int)p->sets.size();
-    st->launches_per_solve = (p->L - 1) + 3;
+    // restrictions, row_fwd, col, row_inv1 (+ row_inv for the finer levels) or one row_inv for all
+    st->launches_per_solve = (p->L - 1) + 3 + (p->L > 1 && p->sched.row_inv0 != 1 ? 1 : 0);
     st->workspace_bytes = p->workspace_bytes;
     st->spectra_bytes = p->spec ? p->spec->bytes : 0;
     st->algorithmic_bytes = p->algorithmic_bytes;
@@ -1195,6 +1442,8 @@ sgf_status sgf_plan_check(sgf_plan *p)
         return cuda_fail(e, "reading the plan status word");
     if (word != 0 && (e = cudaMemset(p->d_status, 0, sizeof word)) != cudaSuccess)
         return cuda_fail(e, "clearing the plan status word");
+    if (word & STATUS_TC_TIMEOUT)
+        return fail(SGF_ETIMEOUT, "SGF_BF16X: a wait for tensor-core completion timed out; the output is invalid");
     if (word & STATUS_RIM_NONZERO)
         return fail(SGF_EINVAL, "SGF_PLAN_ZERO_RIM: sigma was nonzero on the two outer rings of cells");
     return SGF_OK;
@@ -1229,6 +1478,44 @@ sgf_status sgf_plan_profile_read(sgf_plan *p, sgf_kernel_times *out)
         }
     }
     p->events_used = 0;
+    return SGF_OK;
+}
+
+sgf_status sgf_plan_schedule_get(const sgf_plan *p, sgf_schedule *out)
+{
+    if (!p || !out)
+        return fail(SGF_EINVAL, "NULL argument");
+    *out = p->sched;
+    return SGF_OK;
+}
+
+sgf_status sgf_plan_schedule_set(sgf_plan *p, const sgf_schedule *in)
+{
+    if (!p || !in)
+        return fail(SGF_EINVAL, "NULL argument");
+    if ((in->col_pass != 0 && in->col_pass != 1) || (in->row_inv0 != 0 && in->row_inv0 != 1))
+        return fail(SGF_EINVAL, "schedule choices are 0 or 1 (col_pass %d, row_inv0 %d)", in->col_pass, in->row_inv0);
+    p->sched = *in;
+    return SGF_OK;
+}
+
+sgf_status sgf_plan_autotune(sgf_plan *p, int32_t reps, void *stream, sgf_schedule *chosen, double *ms)
+{
+    if (!p)
+        return fail(SGF_EINVAL, "plan is NULL");
+    if (reps < 1 || reps > 1000)
+        return fail(SGF_EINVAL, "reps = %d outside [1, 1000]", reps);
+    DeviceGuard g(p->device);
+    double t[4];
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    sgf_status s = p->prec == SGF_FP64 ? autotune_impl<double>(p, reps, st, t) : autotune_impl<float>(p, reps, st, t);
+    if (s != SGF_OK)
+        return s;
+    if (chosen)
+        *chosen = p->sched;
+    if (ms)
+        for (int k = 0; k < 4; ++k)
+            ms[k] = t[k];
     return SGF_OK;
 }
 

@@ -23,6 +23,9 @@
 // sin(pi/8) and sqrt(1/2).
 #pragma once
 #include "sgf_fft.cuh"
+#ifdef __CUDACC__
+#include "sgf_tc.cuh"
+#endif
 
 namespace sgf {
 
@@ -351,34 +354,47 @@ SGF_HD void stage_small_ct(C *v, int j, const C *tws)
     }
 }
 
+// Twiddles of a radix-16 stage ST on one slot.
+template <typename C, bool INV, int LOGN, int ST>
+SGF_HD void stage_tw16(C *v, int j, const C *tw)
+{
+    using P = F16<LOGN>;
+    constexpr int NS = P::ns(ST);
+    if constexpr (NS > 1) {
+        const C *tws = tw + P::twoff(ST);
+        const int k = j & (NS - 1);
+#pragma unroll
+        for (int r = 1; r < 16; ++r) {
+            const C w = stage_tw<C, 16, NS>(tws, r, k);
+            v[r] = INV ? hmulc(v[r], w) : hmul(v[r], w);
+        }
+    }
+}
+
 // Arithmetic of stage ST on one slot.
 template <typename C, bool INV, int LOGN, int ST>
 SGF_HD void stage_ct(C *v, int j, const C *tw)
 {
     using P = F16<LOGN>;
     constexpr int R = P::radix(ST), NS = P::ns(ST);
-    const C *tws = tw + P::twoff(ST);
     if constexpr (R == 16) {
-        if constexpr (NS > 1) {
-            const int k = j & (NS - 1);
-#pragma unroll
-            for (int r = 1; r < 16; ++r) {
-                const C w = stage_tw<C, 16, NS>(tws, r, k);
-                v[r] = INV ? hmulc(v[r], w) : hmul(v[r], w);
-            }
-        }
+        stage_tw16<C, INV, LOGN, ST>(v, j, tw);
         hdft16<C, INV>(v);
     } else {
-        stage_small_ct<C, INV, P::N, R, NS, 0>(v, j, tws);
+        stage_small_ct<C, INV, P::N, R, NS, 0>(v, j, tw + P::twoff(ST));
     }
 }
 
 #ifdef __CUDACC__
 // Stages ST.. of the block transform (see fft16_block); B sequences per slot
 // (B = 1 or 2: a thread may carry the same slot of two sequences, which then
-// share the barriers), sequence b at sbuf + b * SP.
-template <typename C, bool INV, int LOGN, int B, int ST>
-__device__ __forceinline__ void fft_stages(C (*v)[16], C *sbuf, int SP, int j, bool active, const C *tw)
+// share the barriers), sequence b at sbuf + b * SP.  TC (float only): the
+// 16-point DFTs of the radix-16 stages run as split-BF16 tensor-core tiles
+// (sgf_tc.cuh, context tc); twiddles, exchanges and the closing radix-2/4/8
+// stage stay in FP32.
+template <typename C, bool INV, int LOGN, int B, int ST, bool TC = false>
+__device__ __forceinline__ void fft_stages(C (*v)[16], C *sbuf, int SP, int j, bool active, const C *tw,
+                                           TcCtx *tc = nullptr)
 {
     using P = F16<LOGN>;
     if constexpr (ST < P::NST) {
@@ -393,7 +409,14 @@ __device__ __forceinline__ void fft_stages(C (*v)[16], C *sbuf, int SP, int j, b
                         v[bb][u] = sbuf[bb * SP + pad16(j + u * Q)];
             }
         }
-        if (active) {
+        if constexpr (TC && P::radix(ST) == 16) {
+            if (active) {
+#pragma unroll
+                for (int bb = 0; bb < B; ++bb)
+                    stage_tw16<C, INV, LOGN, ST>(v[bb], j, tw);
+            }
+            tc_dft16<INV, B>(v, *tc, active);
+        } else if (active) {
 #pragma unroll
             for (int bb = 0; bb < B; ++bb)
                 stage_ct<C, INV, LOGN, ST>(v[bb], j, tw);
@@ -410,15 +433,16 @@ __device__ __forceinline__ void fft_stages(C (*v)[16], C *sbuf, int SP, int j, b
                         sbuf[bb * SP + pad16(base + r * NS)] = v[bb][r];
             }
         }
-        fft_stages<C, INV, LOGN, B, ST + 1>(v, sbuf, SP, j, active, tw);
+        fft_stages<C, INV, LOGN, B, ST + 1, TC>(v, sbuf, SP, j, active, tw, tc);
     }
 }
 
 // Block-wide transform, compile-time N: as fft16_block, for B slots per thread.
-template <typename C, bool INV, int LOGN, int B = 1>
-__device__ __forceinline__ void fft_ct(C (*v)[16], C *sbuf, int SP, int j, bool active, const C *tw)
+template <typename C, bool INV, int LOGN, int B = 1, bool TC = false>
+__device__ __forceinline__ void fft_ct(C (*v)[16], C *sbuf, int SP, int j, bool active, const C *tw,
+                                       TcCtx *tc = nullptr)
 {
-    fft_stages<C, INV, LOGN, B, 0>(v, sbuf, SP, j, active, tw);
+    fft_stages<C, INV, LOGN, B, 0, TC>(v, sbuf, SP, j, active, tw, tc);
 }
 #endif
 

@@ -1,6 +1,6 @@
-// sgf_inst_12.cu -- transform-pass instances for N = 4096.
+// sgf_inst_12.cu -- transform-pass instances for N = 4096 (FP32 and FP64 paths).
 #include "sgf_kernels.cuh"
 
 namespace sgf {
-template cudaError_t launch_pass<float, 12>(int, const SolveArgs<float> &, int, cudaStream_t, const BatchView<float> *);
+template cudaError_t launch_pass<float, 12, false>(int, const SolveArgs<float> &, int, cudaStream_t, const BatchView<float> *);
 }  // namespace sgf

@@ -1,0 +1,6 @@
+// sgf_inst_tc_04.cu -- transform-pass instances for N = 16, SGF_BF16X (tensor-core tiles).
+#include "sgf_kernels.cuh"
+
+namespace sgf {
+template cudaError_t launch_pass<float, 4, true>(int, const SolveArgs<float> &, int, cudaStream_t, const BatchView<float> *);
+}  // namespace sgf

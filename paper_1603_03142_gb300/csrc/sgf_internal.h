@@ -51,8 +51,9 @@ inline __host__ __device__ size_t bwd_index(int N, int rows, int comp, int kx, i
     return ((size_t)comp * (N + 1) + kx) * rows + row;
 }
 
-// Device status bits of a plan (sgf_plan_check).
-enum : int { STATUS_RIM_NONZERO = 1 };
+// Device status bits of a plan (sgf_plan_check).  STATUS_TC_TIMEOUT: a bounded
+// wait for tensor-core completion (SGF_BF16X) gave up.
+enum : int { STATUS_RIM_NONZERO = 1, STATUS_TC_TIMEOUT = 2 };
 
 // A quarter-stored spectrum row holds ky = 0..N split by parity: even ky
 // (0, 2, .., N) at [0, N/2 + 1), odd ky (1, 3, .., N-1) at [N/2 + 4, N + 4);
@@ -116,6 +117,7 @@ struct SolveArgs {
     const ColInput *ins;
     const RowContrib *contribs;
     int contrib_begin[kMaxLevels + 1];
+    int level_base;             // first target level of a k_row_inv launch without a batch view
 };
 
 // Twiddle area of a solve (complex entries, precision of the solve):
@@ -155,7 +157,18 @@ cudaError_t launch_restrict(const T *fine, T *coarse, const T *coarse_in, int N,
                             cudaStream_t st);
 // Transform passes of a solve (sgf_kernels.cuh); count = work items (row_fwd),
 // outputs (col) or levels (row_inv).
-enum : int { PASS_ROW_FWD = 0, PASS_COL = 1, PASS_ROW_INV = 2, PASS_ROW_FWD_M = 3, PASS_COL_M = 4, PASS_PREPARE = 5 };
+// PASS_ROW_INV1: the inverse row pass of a level whose only contribution is
+// its own main output (m = 1; level 0 of every nest).
+enum : int {
+    PASS_ROW_FWD = 0,
+    PASS_COL = 1,
+    PASS_ROW_INV = 2,
+    PASS_ROW_FWD_M = 3,
+    PASS_COL_M = 4,
+    PASS_PREPARE = 5,
+    PASS_ROW_INV1 = 6,
+    PASS_COL_MD = 7
+};
 // Batch mode of the transform passes: a block's nest and its local work index
 // come from a per-launch map (one int2 per block row), and that nest's
 // arguments from a device array.
@@ -165,9 +178,10 @@ struct BatchView {
     const int2 *map;  // (nest, local index)
 };
 // bv == nullptr: one nest (a); otherwise every block takes its nest's arguments from bv.
+// tc (float only): the SGF_BF16X kernels (split-BF16 tensor-core radix-16 tiles).
 template <typename T>
 cudaError_t launch_pass_n(int pass, int logN, const SolveArgs<T> &a, int count, cudaStream_t st,
-                          const BatchView<T> *bv = nullptr);
+                          const BatchView<T> *bv = nullptr, bool tc = false);
 
 // Build the spectra of one set into spec (element type T: float or double).
 // work_tables: 6*P*P doubles; work_half: 6*(N+1)*P double2.

@@ -20,8 +20,12 @@
 //  k_row_inv   : per row pair of a target level: Hermitian extension, inverse
 //                row transforms of every contributing output, Case-3 phase
 //                interleave, covered cells zeroed, Fx/Fy stored.
+//  k_row_inv1  : k_row_inv for a level whose only contribution is its own
+//                main output (level 0), one CTA per (row pair, component).
 //  k_row_fwd_m,
-//  k_col_m     : the SGF_PLAN_ZERO_RIM variants (sigma alone, merged spectra).
+//  k_col_m     : the SGF_PLAN_ZERO_RIM variants (sigma alone, merged spectra);
+//  k_col_md    : k_col_m with both inverse transforms in flight (another
+//                schedule of the same arithmetic, chosen by the autotuner).
 #pragma once
 #include <atomic>
 #include <cooperative_groups.h>
@@ -96,12 +100,22 @@ struct KShape {
     static constexpr int N = 1 << LOGN, Q = N >> 4;
     static constexpr int ROW_THREADS = 2 * Q < 32 ? 32 : 2 * Q;  // both parity halves
     static constexpr int COL_THREADS = Q < 32 ? 32 : Q;          // one parity half
-    static constexpr int SP_ROW = N + Q + 2;  // pad keeps the halves on different banks in the unpack
+    static constexpr int SP_ROW = N + Q + 8;  // pad puts the two halves 16 banks apart for the unpack
 };
+
+// Tensor-core tiles (SGF_BF16X) issued per round, i.e. A-tile buffers in shared
+// memory: all of them, except where the kernel's own staging leaves no room at
+// N = 4096 (k_row_fwd keeps two; k_row_inv keeps one and is never launched
+// there: the host refuses SGF_BF16X nests of N = 4096 with more than one level).
+enum : int { KK_ROW_FWD, KK_COL, KK_ROW_INV, KK_ROW_INV1, KK_ROW_FWD_M, KK_COL_M, KK_COL_MD };
+__host__ __device__ constexpr int tc_round(int logn, int tiles, int kind)
+{
+    return logn < 12 ? tiles : kind == KK_ROW_FWD ? (tiles < 2 ? tiles : 2) : kind == KK_ROW_INV ? 1 : tiles;
+}
 
 // ------------------------------------------------------------------ row_fwd
 // Shared memory: twiddle area | sigma rows[6][N] | sbuf[2 SP_ROW].
-template <typename T, int LOGN, bool BATCH>
+template <typename T, int LOGN, bool BATCH, bool TC>
 __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd(SolveArgs<T> a0, BatchView<T> bv)
 {
     const int2 wm = BATCH ? bv.map[blockIdx.x] : make_int2(0, (int)blockIdx.x);
@@ -110,7 +124,14 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd(SolveArgs
     using C2 = typename Cx<T>::C2;
     using K = KShape<LOGN>;
     constexpr int N = K::N, Q = K::Q, SP = K::SP_ROW;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_tc[];
+    constexpr int TCT = tc_tiles(KShape<LOGN>::ROW_THREADS, 1);
+    constexpr int TCR = tc_round(LOGN, TCT, KK_ROW_FWD);
+    static_assert(!TC || sizeof(T) == 4, "tensor-core tiles take FP32 data");
+    unsigned char *smem_raw = smem_tc + (TC ? tc_smem_bytes(TCR) : 0);
+    TcCtx tcx;
+    if constexpr (TC)
+        tc_begin(tcx, smem_tc, TCT, TCR, a.status);
     C *tw = reinterpret_cast<C *>(smem_raw);
     T *srow = reinterpret_cast<T *>(smem_raw + tw_bytes<C>(a.tw_entries));  // rows ja-1, ja, ja+1, jb-1, jb, jb+1
     C *sbuf = reinterpret_cast<C *>(srow + 6 * N);
@@ -168,7 +189,7 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd(SolveArgs
                 v[0][u] = z;
             }
         }
-        fft_ct<C, false, LOGN>(v, sbuf + b * SP, SP, j, active, tw);
+        fft_ct<C, false, LOGN, 1, TC>(v, sbuf + b * SP, SP, j, active, tw, &tcx);
         __syncthreads();
         if (active) {
 #pragma unroll
@@ -190,6 +211,8 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd(SolveArgs
             out[(((size_t)f * (N + 1) + kx) * rows + r0) >> 1] = o;
         }
     }
+    if constexpr (TC)
+        tc_end(tcx, TCT);
 }
 
 // --------------------------------------------------------------------- col
@@ -197,7 +220,7 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd(SolveArgs
 // this parity's half of the two spectrum rows, 2 x (N/2 + 4) reals }.  The
 // dual inverse transform uses sbuf and the stages as two sequence buffers, and
 // the fold of the odd half reuses them afterwards.
-template <typename T, int LOGN, bool BATCH>
+template <typename T, int LOGN, bool BATCH, bool TC>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_THREADS) k_col(SolveArgs<T> a0, BatchView<T> bv)
 {
     const int2 wm = BATCH ? bv.map[blockIdx.y] : make_int2(0, (int)blockIdx.y);
@@ -206,7 +229,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
     using K = KShape<LOGN>;
     constexpr int N = K::N, Q = K::Q, P = 2 * N, QS = quarter_stride(N), HQ = quarter_half(N);
     constexpr int SPC = col_sp<C>(N);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_tc[];
+    constexpr int TCT = tc_tiles(KShape<LOGN>::COL_THREADS, 2);
+    constexpr int TCR = tc_round(LOGN, TCT, KK_COL);
+    static_assert(!TC || sizeof(T) == 4, "tensor-core tiles take FP32 data");
+    unsigned char *smem_raw = smem_tc + (TC ? tc_smem_bytes(TCR) : 0);
+    TcCtx tcx;
+    if constexpr (TC)
+        tc_begin(tcx, smem_tc, TCT, TCR, a.status);
     C *tw = reinterpret_cast<C *>(smem_raw);
     C *sbuf = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
     unsigned char *stage_base = reinterpret_cast<unsigned char *>(sbuf + SPC);
@@ -270,7 +300,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
                 v[0][u] = x;
             }
         }
-        fft_ct<C, false, LOGN>(v, sbuf, SPC, j, active, tw);
+        fft_ct<C, false, LOGN, 1, TC>(v, sbuf, SPC, j, active, tw, &tcx);
         if (active) {
             if (ci.kind == SPEC_QUARTER) {
                 // K0x, K0y imaginary (stored Im), the rest real; bins above N read the
@@ -312,7 +342,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
     }
     cp_wait<0>();
     // inverse column transforms of Fx^ and Fy^ together; y[n] = even[n] + W_P^{-n} odd[n]
-    fft_ct<C, true, LOGN, 2>(acc, sbuf, SPC, j, active, tw);
+    fft_ct<C, true, LOGN, 2, TC>(acc, sbuf, SPC, j, active, tw, &tcx);
     C *fold = sbuf;  // 2N complex over sbuf and the stages
     cluster.sync();
     if (b == 1 && active) {
@@ -337,6 +367,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
             }
         }
     }
+    if constexpr (TC)
+        tc_end(tcx, TCT);
 }
 
 // ------------------------------------------------------------------ row_inv
@@ -345,7 +377,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
 // asynchronous copies -- 16 bytes per bin when both rows are adjacent rows of
 // one output, 8 bytes otherwise -- and the next gather is issued as soon as
 // the current one has been read into registers, so it overlaps the transform.
-template <typename T, int LOGN, bool BATCH>
+template <typename T, int LOGN, bool BATCH, bool TC>
 __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_inv(SolveArgs<T> a0, BatchView<T> bv)
 {
     const int2 wm = BATCH ? bv.map[blockIdx.y] : make_int2(0, (int)blockIdx.y);
@@ -353,12 +385,19 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_inv(SolveArgs
     using C = typename Cx<T>::C;
     using K = KShape<LOGN>;
     constexpr int N = K::N, Q = K::Q, SP = K::SP_ROW, P = 2 * N;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_tc[];
+    constexpr int TCT = tc_tiles(KShape<LOGN>::ROW_THREADS, 1);
+    constexpr int TCR = tc_round(LOGN, TCT, KK_ROW_INV);
+    static_assert(!TC || sizeof(T) == 4, "tensor-core tiles take FP32 data");
+    unsigned char *smem_raw = smem_tc + (TC ? tc_smem_bytes(TCR) : 0);
+    TcCtx tcx;
+    if constexpr (TC)
+        tc_begin(tcx, smem_tc, TCT, TCR, a.status);
     C *tw = reinterpret_cast<C *>(smem_raw);
     C *stg = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));  // [kx][2]
     C *sbuf = stg + 2 * (N + 1) + ((2 * (N + 1) * sizeof(C)) % 16 ? 1 : 0);
     T *O = reinterpret_cast<T *>(sbuf + 2 * SP);
-    const int tl = wm.y;
+    const int tl = BATCH ? wm.y : a.level_base + wm.y;
     const int j0 = 2 * blockIdx.x, j1 = j0 + 1;
     const int t = threadIdx.x;
     const bool active = t < 2 * Q;
@@ -419,7 +458,7 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_inv(SolveArgs
         if (k + 1 < nitems)
             issue(k + 1);
         cp_commit();
-        fft_ct<C, true, LOGN>(v, sbuf + b * SP, SP, j, active, tw);
+        fft_ct<C, true, LOGN, 1, TC>(v, sbuf + b * SP, SP, j, active, tw, &tcx);
         __syncthreads();
         if (active && b == 1) {
 #pragma unroll
@@ -452,6 +491,94 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_inv(SolveArgs
         fy[(size_t)j0 * N + i] = ca ? T(0) : O[2 * N + i];
         fy[(size_t)j1 * N + i] = cb ? T(0) : O[3 * N + i];
     }
+    if constexpr (TC)
+        tc_end(tcx, TCT);
+}
+
+// ----------------------------------------------------------------- row_inv1
+// Inverse row pass of a level with a single contribution, its own main output
+// (m = 1: level 0 of every nest, every uniform solve).  One CTA per (row pair,
+// component): the two rows are gathered (16 bytes per bin in FP32), turned
+// into one complex sequence Z = A + iB by the Hermitian extension, inverse
+// transformed as two parity halves, folded, and stored straight from
+// registers.  The exchange buffer of the transform aliases the gather stage,
+// so a CTA needs (N + N/16) complex pairs of shared memory and two of them fit
+// on an SM; the gather of one CTA overlaps the transform of the other.
+// Grid: x = component * N/2 + row pair, y = work item (batch) or 0.
+template <typename T, int LOGN, bool BATCH, bool TC>
+__global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, sizeof(T) == 4 && !TC ? 2 : 1)
+    k_row_inv1(SolveArgs<T> a0, BatchView<T> bv)
+{
+    const int2 wm = BATCH ? bv.map[blockIdx.y] : make_int2(0, 0);
+    const SolveArgs<T> &a = BATCH ? bv.args[wm.x] : a0;
+    using C = typename Cx<T>::C;
+    using K = KShape<LOGN>;
+    constexpr int N = K::N, Q = K::Q, SP = K::SP_ROW, P = 2 * N;
+    extern __shared__ __align__(16) unsigned char smem_tc[];
+    constexpr int TCT = tc_tiles(KShape<LOGN>::ROW_THREADS, 1);
+    constexpr int TCR = tc_round(LOGN, TCT, KK_ROW_INV1);
+    static_assert(!TC || sizeof(T) == 4, "tensor-core tiles take FP32 data");
+    unsigned char *smem_raw = smem_tc + (TC ? tc_smem_bytes(TCR) : 0);
+    TcCtx tcx;
+    if constexpr (TC)
+        tc_begin(tcx, smem_tc, TCT, TCR, a.status);
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *stg = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));  // [kx][2], then the exchange buffer
+    C *sbuf = stg;
+    const int tl = BATCH ? wm.y : a.level_base;
+    const int comp = (int)blockIdx.x >= N / 2 ? 1 : 0;
+    const int j0 = 2 * ((int)blockIdx.x - comp * (N / 2)), j1 = j0 + 1;
+    const int t = threadIdx.x;
+    const bool active = t < 2 * Q;
+    const int b = active ? t / Q : 0, j = active ? t - b * Q : 0;
+    const TwLayout twl = tw_layout(F16<LOGN>::twlen, N);
+    const RowContrib rc = a.contribs[a.contrib_begin[tl]];
+    const ColOutput o = a.outs[rc.out_base];
+    const C *base = a.bwd + o.off + bwd_index(N, o.rows, comp, 0, j0);
+    cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
+    {
+        constexpr int PG = 2 * (int)sizeof(C) / 16;  // 16-byte pieces per bin (rows j0, j1 adjacent)
+        for (int q = t; q < (N + 1) * PG; q += K::ROW_THREADS) {
+            const int kx = q / PG, piece = q - kx * PG;
+            cp16(stg + 2 * kx + piece * (16 / (int)sizeof(C)), base + (size_t)kx * o.rows + piece * (16 / (int)sizeof(C)));
+        }
+    }
+    cp_commit();
+    cp_wait<0>();
+    __syncthreads();
+    C v[1][16];
+    if (active) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int kx = 2 * (j + u * Q) + b;
+            const int k2 = kx <= N ? kx : P - kx;
+            const C A = stg[2 * k2], B = stg[2 * k2 + 1];
+            v[0][u] = kx <= N ? hmk<C>(A.x - B.y, A.y + B.x) : hmk<C>(A.x + B.y, B.x - A.y);
+        }
+    }
+    // the transform's first exchange write follows a barrier, after every read of the stage
+    fft_ct<C, true, LOGN, 1, TC>(v, sbuf + b * SP, SP, j, active, tw, &tcx);
+    __syncthreads();
+    if (active && b == 1) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int n = j + u * Q;
+            sbuf[pad16(n)] = hmulc(v[0][u], twist(tw, twl, j, u));
+        }
+    }
+    __syncthreads();
+    if (active && b == 0) {
+        T *out = comp ? a.fy[tl] : a.fx[tl];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int n = j + u * Q;
+            const C y = hadd(v[0][u], sbuf[pad16(n)]);
+            out[(size_t)j0 * N + n] = covered(a, tl, j0, n) ? T(0) : y.x;
+            out[(size_t)j1 * N + n] = covered(a, tl, j1, n) ? T(0) : y.y;
+        }
+    }
+    if constexpr (TC)
+        tc_end(tcx, TCT);
 }
 
 // ------------------------------------------------------------ zero-rim path
@@ -460,7 +587,7 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_inv(SolveArgs
 // the CTAs of rows 0-1 and N-2..N-1 scan their rows, every CTA its cells in
 // columns 0, 1, N-2, N-1; a nonzero value sets STATUS_RIM_NONZERO.
 // Shared memory: twiddle area | sigma rows[2][N] | sbuf[2 SP_ROW].
-template <typename T, int LOGN, bool BATCH>
+template <typename T, int LOGN, bool BATCH, bool TC>
 __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd_m(SolveArgs<T> a0, BatchView<T> bv)
 {
     const int2 wm = BATCH ? bv.map[blockIdx.y] : make_int2(0, 0);
@@ -469,7 +596,14 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd_m(SolveAr
     using C2 = typename Cx<T>::C2;
     using K = KShape<LOGN>;
     constexpr int N = K::N, Q = K::Q, SP = K::SP_ROW;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_tc[];
+    constexpr int TCT = tc_tiles(KShape<LOGN>::ROW_THREADS, 1);
+    constexpr int TCR = tc_round(LOGN, TCT, KK_ROW_FWD_M);
+    static_assert(!TC || sizeof(T) == 4, "tensor-core tiles take FP32 data");
+    unsigned char *smem_raw = smem_tc + (TC ? tc_smem_bytes(TCR) : 0);
+    TcCtx tcx;
+    if constexpr (TC)
+        tc_begin(tcx, smem_tc, TCT, TCR, a.status);
     C *tw = reinterpret_cast<C *>(smem_raw);
     T *srow = reinterpret_cast<T *>(smem_raw + tw_bytes<C>(a.tw_entries));
     C *sbuf = reinterpret_cast<C *>(srow + 2 * N);
@@ -510,7 +644,7 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd_m(SolveAr
             v[0][u] = z;
         }
     }
-    fft_ct<C, false, LOGN>(v, sbuf + b * SP, SP, j, active, tw);
+    fft_ct<C, false, LOGN, 1, TC>(v, sbuf + b * SP, SP, j, active, tw, &tcx);
     __syncthreads();
     if (t == 0 && rim_bad)
         atomicOr(a.status, STATUS_RIM_NONZERO);
@@ -533,17 +667,21 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd_m(SolveAr
         o.w = T(-0.5) * (Z.x - Zm.x);
         out[((size_t)kx * N + r0) >> 1] = o;
     }
+    if constexpr (TC)
+        tc_end(tcx, TCT);
 }
 
 // Column pass of a SGF_PLAN_ZERO_RIM plan: one forward transform, the two
-// merged spectra (Fx^ = Gx^ sigma^, Fy^ = Gy^ sigma^, both imaginary), one
-// dual inverse transform; parity halves folded through distributed shared
-// memory.  Shared memory: twiddle area | sbuf[SPC] | stage {column[N], this
-// parity's half rows of Gx and Gy}; the dual transform and the fold reuse
-// sbuf + stage.
-template <typename T, int LOGN, bool BATCH>
+// merged spectra (Fx^ = Gx^ sigma^, Fy^ = Gy^ sigma^, both imaginary), and the
+// two inverse transforms one after the other; parity halves folded through
+// distributed shared memory.  The column and the spectrum half rows are read
+// straight into registers (coalesced), Fy^ waits in shared memory while Fx^ is
+// transformed, so a thread holds one sequence at a time and three CTAs fit on
+// an SM.  Shared memory: twiddle area | sbuf[SPC] (exchanges, then the fold) |
+// park[N] (Fy^ in slot order).
+template <typename T, int LOGN, bool BATCH, bool TC>
 __global__ void __cluster_dims__(2, 1, 1)
-    __launch_bounds__(KShape<LOGN>::COL_THREADS, sizeof(T) == 4 ? 2 : 1) k_col_m(SolveArgs<T> a0, BatchView<T> bv)
+    __launch_bounds__(KShape<LOGN>::COL_THREADS, sizeof(T) == 4 && !TC ? 3 : 1) k_col_m(SolveArgs<T> a0, BatchView<T> bv)
 {
     const int2 wm = BATCH ? bv.map[blockIdx.y] : make_int2(0, 0);
     const SolveArgs<T> &a = BATCH ? bv.args[wm.x] : a0;
@@ -551,7 +689,109 @@ __global__ void __cluster_dims__(2, 1, 1)
     using K = KShape<LOGN>;
     constexpr int N = K::N, Q = K::Q, QS = quarter_stride(N), HQ = quarter_half(N);
     constexpr int SPC = col_sp<C>(N);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_tc[];
+    constexpr int TCT = tc_tiles(KShape<LOGN>::COL_THREADS, 1);
+    constexpr int TCR = tc_round(LOGN, TCT, KK_COL_M);
+    static_assert(!TC || sizeof(T) == 4, "tensor-core tiles take FP32 data");
+    unsigned char *smem_raw = smem_tc + (TC ? tc_smem_bytes(TCR) : 0);
+    TcCtx tcx;
+    if constexpr (TC)
+        tc_begin(tcx, smem_tc, TCT, TCR, a.status);
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *sbuf = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
+    C *park = sbuf + SPC;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int b = (int)cluster.block_rank();
+    const int kx = blockIdx.x >> 1;
+    const int t = threadIdx.x;
+    const bool active = t < Q;
+    const int j = active ? t : 0;
+    const TwLayout tl = tw_layout(F16<LOGN>::twlen, N);
+    const T *gxr = reinterpret_cast<const T *>(a.spec) + (size_t)kx * QS + b * HQ;
+    const T *gyr = reinterpret_cast<const T *>(a.spec) + ((size_t)(N + 1) + kx) * QS + b * HQ;
+    cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
+    cp_commit();
+    C v[1][16];
+    if (active) {
+        const C *col = a.fwd + (size_t)kx * N;
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+            v[0][u] = col[j + u * Q];
+    }
+    cp_wait<0>();
+    __syncthreads();
+    if (active && b) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+            v[0][u] = hmul(v[0][u], twist(tw, tl, j, u));
+    }
+    fft_ct<C, false, LOGN, 1, TC>(v, sbuf, SPC, j, active, tw, &tcx);
+    if (active) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int kp = j + u * Q;
+            const bool hi = 2 * kp + b > N;
+            const int q = hi ? N - kp - b : kp;
+            const T gx = __ldg(gxr + q);                               // Gx even in ky
+            const T gy = hi ? -__ldg(gyr + q) : __ldg(gyr + q);        // Gy odd in ky
+            park[u * Q + j] = hmk<C>(-gy * v[0][u].y, gy * v[0][u].x);  // i gy v
+            v[0][u] = hmk<C>(-gx * v[0][u].y, gx * v[0][u].x);          // i gx v
+        }
+    }
+    C *const out = a.bwd;
+#pragma unroll 1
+    for (int comp = 0; comp < 2; ++comp) {
+        if (comp == 1 && active) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+                v[0][u] = park[u * Q + j];
+        }
+        // y[n] = even[n] + W_P^{-n} odd[n]
+        fft_ct<C, true, LOGN, 1, TC>(v, sbuf, SPC, j, active, tw, &tcx);
+        cluster.sync();  // both CTAs are done with their exchange buffers
+        if (b == 1 && active) {
+            C *dst = cluster.map_shared_rank(sbuf, 0);
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+                dst[j + u * Q] = hmulc(v[0][u], twist(tw, tl, j, u));
+        }
+        cluster.sync();
+        if (b == 0 && active) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int n = j + u * Q;
+                out[bwd_index(N, N, comp, kx, n)] = hadd(v[0][u], sbuf[n]);
+            }
+        }
+    }
+    if constexpr (TC)
+        tc_end(tcx, TCT);
+}
+
+// The same column pass with both inverse transforms in flight at once (B = 2
+// sequences per thread share the barriers): fewer barriers, twice the
+// registers, two CTAs per SM.  The column and the spectrum half rows are
+// staged with asynchronous copies.  Shared memory: twiddle area | sbuf[SPC] |
+// column[N] | Gx, Gy half rows; the second sequence and the 2N fold reuse
+// sbuf + column.
+template <typename T, int LOGN, bool BATCH, bool TC>
+__global__ void __cluster_dims__(2, 1, 1)
+    __launch_bounds__(KShape<LOGN>::COL_THREADS, sizeof(T) == 4 && !TC ? 2 : 1) k_col_md(SolveArgs<T> a0, BatchView<T> bv)
+{
+    const int2 wm = BATCH ? bv.map[blockIdx.y] : make_int2(0, 0);
+    const SolveArgs<T> &a = BATCH ? bv.args[wm.x] : a0;
+    using C = typename Cx<T>::C;
+    using K = KShape<LOGN>;
+    constexpr int N = K::N, Q = K::Q, QS = quarter_stride(N), HQ = quarter_half(N);
+    constexpr int SPC = col_sp<C>(N);
+    extern __shared__ __align__(16) unsigned char smem_tc[];
+    constexpr int TCT = tc_tiles(KShape<LOGN>::COL_THREADS, 2);
+    constexpr int TCR = tc_round(LOGN, TCT, KK_COL_MD);
+    static_assert(!TC || sizeof(T) == 4, "tensor-core tiles take FP32 data");
+    unsigned char *smem_raw = smem_tc + (TC ? tc_smem_bytes(TCR) : 0);
+    TcCtx tcx;
+    if constexpr (TC)
+        tc_begin(tcx, smem_tc, TCT, TCR, a.status);
     C *tw = reinterpret_cast<C *>(smem_raw);
     C *sbuf = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
     C *col = sbuf + SPC;
@@ -583,7 +823,7 @@ __global__ void __cluster_dims__(2, 1, 1)
                 v[0][u] = x;
             }
         }
-        fft_ct<C, false, LOGN>(v, sbuf, SPC, j, active, tw);
+        fft_ct<C, false, LOGN, 1, TC>(v, sbuf, SPC, j, active, tw, &tcx);
         if (active) {
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
@@ -597,7 +837,7 @@ __global__ void __cluster_dims__(2, 1, 1)
             }
         }
     }
-    fft_ct<C, true, LOGN, 2>(acc, sbuf, SPC, j, active, tw);  // second sequence over the stage
+    fft_ct<C, true, LOGN, 2, TC>(acc, sbuf, SPC, j, active, tw, &tcx);  // second sequence over the column
     C *fold = sbuf;
     cluster.sync();
     if (b == 1 && active) {
@@ -620,27 +860,53 @@ __global__ void __cluster_dims__(2, 1, 1)
             dst[bwd_index(N, N, 1, kx, n)] = hadd(acc[1][u], fold[N + n]);
         }
     }
+    if constexpr (TC)
+        tc_end(tcx, TCT);
 }
 
 // ---------------------------------------------------------------- launching
-template <typename T, int LOGN>
+// Dynamic shared memory per kernel; TC adds the tensor-core area in front.
+template <typename T, int LOGN, bool TC = false>
 struct KSmem {
     using C = typename Cx<T>::C;
     static constexpr int N = 1 << LOGN;
+    static size_t tc(int threads, int B, int kind)
+    {
+        return TC ? tc_smem_bytes(tc_round(LOGN, tc_tiles(threads, B), kind)) : 0;
+    }
+    static size_t rtc(int kind) { return tc(KShape<LOGN>::ROW_THREADS, 1, kind); }
+    static size_t ctc(int kind) { return tc(KShape<LOGN>::COL_THREADS, 2, kind); }
     static size_t tw() { return tw_bytes<C>(tw_layout(F16<LOGN>::twlen, N).entries); }
-    static size_t row_fwd() { return tw() + 6 * (size_t)N * sizeof(T) + 2 * (size_t)KShape<LOGN>::SP_ROW * sizeof(C); }
+    static size_t row_fwd()
+    {
+        return rtc(KK_ROW_FWD) + tw() + 6 * (size_t)N * sizeof(T) + 2 * (size_t)KShape<LOGN>::SP_ROW * sizeof(C);
+    }
     static size_t col()
     {
         const size_t stage = (size_t)N * sizeof(C) + 2 * (size_t)quarter_half(N) * sizeof(T);
-        return tw() + (size_t)col_sp<C>(N) * sizeof(C) + 2 * stage;
+        return ctc(KK_COL) + tw() + (size_t)col_sp<C>(N) * sizeof(C) + 2 * stage;
     }
     static size_t row_inv()
     {
-        return tw() + ((2 * (size_t)(N + 1) * sizeof(C) + 15) & ~(size_t)15) + 2 * (size_t)KShape<LOGN>::SP_ROW * sizeof(C) +
-               4 * (size_t)N * sizeof(T);
+        return rtc(KK_ROW_INV) + tw() + ((2 * (size_t)(N + 1) * sizeof(C) + 15) & ~(size_t)15) +
+               2 * (size_t)KShape<LOGN>::SP_ROW * sizeof(C) + 4 * (size_t)N * sizeof(T);
     }
-    static size_t row_fwd_m() { return tw() + 2 * (size_t)N * sizeof(T) + 2 * (size_t)KShape<LOGN>::SP_ROW * sizeof(C); }
+    static size_t row_inv1()
+    {
+        const size_t stage = (2 * (size_t)(N + 1) * sizeof(C) + 15) & ~(size_t)15;
+        const size_t xbuf = 2 * (size_t)KShape<LOGN>::SP_ROW * sizeof(C);
+        return rtc(KK_ROW_INV1) + tw() + (stage > xbuf ? stage : xbuf);
+    }
+    static size_t row_fwd_m()
+    {
+        return rtc(KK_ROW_FWD_M) + tw() + 2 * (size_t)N * sizeof(T) + 2 * (size_t)KShape<LOGN>::SP_ROW * sizeof(C);
+    }
     static size_t col_m()
+    {
+        return tc(KShape<LOGN>::COL_THREADS, 1, KK_COL_M) + tw() + (size_t)col_sp<C>(N) * sizeof(C) +
+               (size_t)N * sizeof(C);
+    }
+    static size_t col_md()
     {
         // sbuf + column + spectrum half rows; at least two exchange buffers (dual inverse) and the 2N fold
         size_t body = (size_t)col_sp<C>(N) * sizeof(C) + (size_t)N * sizeof(C) + 2 * (size_t)quarter_half(N) * sizeof(T);
@@ -649,7 +915,7 @@ struct KSmem {
             body = need;
         if (body < 2 * (size_t)N * sizeof(C))
             body = 2 * (size_t)N * sizeof(C);
-        return tw() + body;
+        return ctc(KK_COL_MD) + tw() + body;
     }
 };
 
@@ -670,12 +936,12 @@ inline cudaError_t ensure_smem(F *kernel, size_t bytes, std::atomic<unsigned lon
     return e;
 }
 
-template <typename T, int LOGN>
+template <typename T, int LOGN, bool TC>
 cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t st, const BatchView<T> *bv)
 {
     using K = KShape<LOGN>;
-    using S = KSmem<T, LOGN>;
-    static std::atomic<unsigned long long> d[10];
+    using S = KSmem<T, LOGN, TC>;
+    static std::atomic<unsigned long long> d[14];
     const BatchView<T> none{nullptr, nullptr};
     const bool batch = bv != nullptr;
     const BatchView<T> v = batch ? *bv : none;
@@ -691,42 +957,56 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
         K0<<<grid, threads, smem, st>>>(a, v);                                        \
     }
     if (pass == PASS_PREPARE) {  // set every shared-memory limit (before a graph capture)
-        if ((e = ensure_smem(k_row_fwd<T, LOGN, false>, S::row_fwd(), d[0])) != cudaSuccess ||
-            (e = ensure_smem(k_row_fwd<T, LOGN, true>, S::row_fwd(), d[1])) != cudaSuccess ||
-            (e = ensure_smem(k_col<T, LOGN, false>, S::col(), d[2])) != cudaSuccess ||
-            (e = ensure_smem(k_col<T, LOGN, true>, S::col(), d[3])) != cudaSuccess ||
-            (e = ensure_smem(k_row_inv<T, LOGN, false>, S::row_inv(), d[4])) != cudaSuccess ||
-            (e = ensure_smem(k_row_inv<T, LOGN, true>, S::row_inv(), d[5])) != cudaSuccess ||
-            (e = ensure_smem(k_row_fwd_m<T, LOGN, false>, S::row_fwd_m(), d[6])) != cudaSuccess ||
-            (e = ensure_smem(k_row_fwd_m<T, LOGN, true>, S::row_fwd_m(), d[7])) != cudaSuccess ||
-            (e = ensure_smem(k_col_m<T, LOGN, false>, S::col_m(), d[8])) != cudaSuccess ||
-            (e = ensure_smem(k_col_m<T, LOGN, true>, S::col_m(), d[9])) != cudaSuccess)
+        if ((e = ensure_smem(k_row_fwd<T, LOGN, false, TC>, S::row_fwd(), d[0])) != cudaSuccess ||
+            (e = ensure_smem(k_row_fwd<T, LOGN, true, TC>, S::row_fwd(), d[1])) != cudaSuccess ||
+            (e = ensure_smem(k_col<T, LOGN, false, TC>, S::col(), d[2])) != cudaSuccess ||
+            (e = ensure_smem(k_col<T, LOGN, true, TC>, S::col(), d[3])) != cudaSuccess ||
+            (e = ensure_smem(k_row_inv<T, LOGN, false, TC>, S::row_inv(), d[4])) != cudaSuccess ||
+            (e = ensure_smem(k_row_inv<T, LOGN, true, TC>, S::row_inv(), d[5])) != cudaSuccess ||
+            (e = ensure_smem(k_row_fwd_m<T, LOGN, false, TC>, S::row_fwd_m(), d[6])) != cudaSuccess ||
+            (e = ensure_smem(k_row_fwd_m<T, LOGN, true, TC>, S::row_fwd_m(), d[7])) != cudaSuccess ||
+            (e = ensure_smem(k_col_m<T, LOGN, false, TC>, S::col_m(), d[8])) != cudaSuccess ||
+            (e = ensure_smem(k_col_m<T, LOGN, true, TC>, S::col_m(), d[9])) != cudaSuccess ||
+            (e = ensure_smem(k_row_inv1<T, LOGN, false, TC>, S::row_inv1(), d[10])) != cudaSuccess ||
+            (e = ensure_smem(k_row_inv1<T, LOGN, true, TC>, S::row_inv1(), d[11])) != cudaSuccess ||
+            (e = ensure_smem(k_col_md<T, LOGN, false, TC>, S::col_md(), d[12])) != cudaSuccess ||
+            (e = ensure_smem(k_col_md<T, LOGN, true, TC>, S::col_md(), d[13])) != cudaSuccess)
             return e;
         return cudaSuccess;
     }
     switch (pass) {
     case PASS_ROW_FWD: {
-        SGF_LAUNCH((k_row_fwd<T, LOGN, false>), (k_row_fwd<T, LOGN, true>), 0, S::row_fwd(), dim3(count),
+        SGF_LAUNCH((k_row_fwd<T, LOGN, false, TC>), (k_row_fwd<T, LOGN, true, TC>), 0, S::row_fwd(), dim3(count),
                    K::ROW_THREADS)
         break;
     }
     case PASS_COL: {
-        SGF_LAUNCH((k_col<T, LOGN, false>), (k_col<T, LOGN, true>), 2, S::col(), dim3(2 * (K::N + 1), count),
+        SGF_LAUNCH((k_col<T, LOGN, false, TC>), (k_col<T, LOGN, true, TC>), 2, S::col(), dim3(2 * (K::N + 1), count),
                    K::COL_THREADS)
         break;
     }
     case PASS_ROW_INV: {
-        SGF_LAUNCH((k_row_inv<T, LOGN, false>), (k_row_inv<T, LOGN, true>), 4, S::row_inv(), dim3(K::N / 2, count),
+        SGF_LAUNCH((k_row_inv<T, LOGN, false, TC>), (k_row_inv<T, LOGN, true, TC>), 4, S::row_inv(), dim3(K::N / 2, count),
                    K::ROW_THREADS)
         break;
     }
+    case PASS_ROW_INV1: {
+        SGF_LAUNCH((k_row_inv1<T, LOGN, false, TC>), (k_row_inv1<T, LOGN, true, TC>), 10, S::row_inv1(),
+                   dim3(K::N, batch ? count : 1), K::ROW_THREADS)
+        break;
+    }
     case PASS_ROW_FWD_M: {
-        SGF_LAUNCH((k_row_fwd_m<T, LOGN, false>), (k_row_fwd_m<T, LOGN, true>), 6, S::row_fwd_m(),
+        SGF_LAUNCH((k_row_fwd_m<T, LOGN, false, TC>), (k_row_fwd_m<T, LOGN, true, TC>), 6, S::row_fwd_m(),
                    dim3(K::N / 2, batch ? count : 1), K::ROW_THREADS)
         break;
     }
     case PASS_COL_M: {
-        SGF_LAUNCH((k_col_m<T, LOGN, false>), (k_col_m<T, LOGN, true>), 8, S::col_m(),
+        SGF_LAUNCH((k_col_m<T, LOGN, false, TC>), (k_col_m<T, LOGN, true, TC>), 8, S::col_m(),
+                   dim3(2 * (K::N + 1), batch ? count : 1), K::COL_THREADS)
+        break;
+    }
+    case PASS_COL_MD: {
+        SGF_LAUNCH((k_col_md<T, LOGN, false, TC>), (k_col_md<T, LOGN, true, TC>), 12, S::col_md(),
                    dim3(2 * (K::N + 1), batch ? count : 1), K::COL_THREADS)
         break;
     }

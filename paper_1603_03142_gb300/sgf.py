@@ -29,7 +29,9 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16x": BF16X}
 EXPORTS = ["sgf_plan_create", "sgf_plan_create_ex", "sgf_plan_check", "sgf_plan_share", "sgf_plan_stats_get",
            "sgf_solve", "sgf_solve_host", "sgf_solve_batched", "sgf_plan_destroy", "sgf_last_error", "sgf_version",
            "sgf_plan_profile", "sgf_plan_profile_read", "sgf_solve_noalloc", "sgf_batch_create",
-           "sgf_batch_solve", "sgf_batch_info", "sgf_batch_destroy"]
+           "sgf_batch_solve", "sgf_batch_info", "sgf_batch_destroy", "sgf_plan_estimate", "sgf_server_create",
+           "sgf_server_clock", "sgf_server_submit", "sgf_server_progress", "sgf_server_stats_get",
+           "sgf_server_destroy", "sgf_plan_schedule_get", "sgf_plan_schedule_set", "sgf_plan_autotune"]
 BATCH_NO_GRAPH = 0x1
 PLAN_ZERO_RIM = 0x1
 NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -54,7 +56,38 @@ class KernelTimes(ctypes.Structure):
     _fields_ = [("solves", ctypes.c_int32), ("launches", ctypes.c_int32 * 4), ("ms", ctypes.c_double * 4)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_inflight", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("simulate_gbs", ctypes.c_double)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("desc", NestDesc), ("precision", ctypes.c_int), ("plan_flags", ctypes.c_uint32),
+                ("sigma", ctypes.c_void_p * SGF_MAX_LEVELS), ("fx", ctypes.c_void_p * SGF_MAX_LEVELS),
+                ("fy", ctypes.c_void_p * SGF_MAX_LEVELS)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("slot", ctypes.c_int32),
+                ("built_shape", ctypes.c_int32), ("pad", ctypes.c_int32), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("rejected", ctypes.c_int64), ("queued", ctypes.c_int32), ("inflight", ctypes.c_int32),
+                ("inflight_peak", ctypes.c_int32), ("slots", ctypes.c_int32), ("shapes_resident", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("shapes_built", ctypes.c_int64), ("slots_evicted", ctypes.c_int64),
+                ("bytes_used", ctypes.c_size_t), ("bytes_peak", ctypes.c_size_t), ("hbm_budget", ctypes.c_size_t)]
+
+
+class Schedule(ctypes.Structure):
+    _fields_ = [("col_pass", ctypes.c_int32), ("row_inv0", ctypes.c_int32)]
+
+
+SERVER_SIMULATE = 0x1
 _vpp = ctypes.POINTER(ctypes.c_void_p)
+_szp = ctypes.POINTER(ctypes.c_size_t)
 _lib.sgf_plan_create.argtypes = [ctypes.POINTER(NestDesc), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
 _lib.sgf_plan_create_ex.argtypes = [ctypes.POINTER(NestDesc), ctypes.c_int, ctypes.c_uint32,
                                     ctypes.POINTER(ctypes.c_void_p)]
@@ -76,11 +109,27 @@ _lib.sgf_solve_batched.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int
 _lib.sgf_plan_destroy.argtypes = [ctypes.c_void_p]
 _lib.sgf_plan_profile.argtypes = [ctypes.c_void_p, ctypes.c_int32]
 _lib.sgf_plan_profile_read.argtypes = [ctypes.c_void_p, ctypes.POINTER(KernelTimes)]
+_lib.sgf_plan_estimate.argtypes = [ctypes.POINTER(NestDesc), ctypes.c_int, ctypes.c_uint32, _szp, _szp, _szp]
+_lib.sgf_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(ctypes.c_void_p)]
+_lib.sgf_server_clock.argtypes = [ctypes.c_void_p]
+_lib.sgf_server_clock.restype = ctypes.c_double
+_lib.sgf_server_submit.argtypes = [ctypes.c_void_p, ctypes.POINTER(Request)]
+_lib.sgf_server_progress.argtypes = [ctypes.c_void_p, ctypes.POINTER(Completion), ctypes.c_int32,
+                                     ctypes.POINTER(ctypes.c_int32)]
+_lib.sgf_server_stats_get.argtypes = [ctypes.c_void_p, ctypes.POINTER(ServerStats)]
+_lib.sgf_server_destroy.argtypes = [ctypes.c_void_p]
+_lib.sgf_plan_schedule_get.argtypes = [ctypes.c_void_p, ctypes.POINTER(Schedule)]
+_lib.sgf_plan_schedule_set.argtypes = [ctypes.c_void_p, ctypes.POINTER(Schedule)]
+_lib.sgf_plan_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(Schedule),
+                                   ctypes.POINTER(ctypes.c_double)]
 _lib.sgf_last_error.restype = ctypes.c_char_p
 _lib.sgf_version.restype = ctypes.c_char_p
 for _f in ("sgf_plan_create", "sgf_plan_create_ex", "sgf_plan_check", "sgf_plan_share", "sgf_plan_stats_get", "sgf_solve", "sgf_solve_host",
            "sgf_solve_batched", "sgf_plan_destroy", "sgf_plan_profile", "sgf_plan_profile_read",
-           "sgf_solve_noalloc", "sgf_batch_create", "sgf_batch_solve", "sgf_batch_info", "sgf_batch_destroy"):
+           "sgf_solve_noalloc", "sgf_batch_create", "sgf_batch_solve", "sgf_batch_info", "sgf_batch_destroy",
+           "sgf_plan_estimate", "sgf_server_create", "sgf_server_submit", "sgf_server_progress",
+           "sgf_server_stats_get", "sgf_server_destroy", "sgf_plan_schedule_get", "sgf_plan_schedule_set",
+           "sgf_plan_autotune"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -176,6 +225,24 @@ class Plan:
         """sgf_solve_noalloc: the solve with the library's fixed scratch array (no allocation)."""
         _check(_lib.sgf_solve_noalloc(self._h, _ptrs(sigma_ptrs), _ptrs(fx_ptrs), _ptrs(fy_ptrs),
                                       ctypes.c_void_p(_stream_handle(stream))), "sgf_solve_noalloc")
+
+    def schedule(self) -> dict:
+        sc = Schedule()
+        _check(_lib.sgf_plan_schedule_get(self._h, ctypes.byref(sc)), "sgf_plan_schedule_get")
+        return {"col_pass": sc.col_pass, "row_inv0": sc.row_inv0}
+
+    def set_schedule(self, col_pass: int = 0, row_inv0: int = 0):
+        sc = Schedule(int(col_pass), int(row_inv0))
+        _check(_lib.sgf_plan_schedule_set(self._h, ctypes.byref(sc)), "sgf_plan_schedule_set")
+
+    def autotune(self, reps: int = 5, stream=None) -> dict:
+        """sgf_plan_autotune: time every schedule candidate, keep the fastest."""
+        sc = Schedule()
+        ms = (ctypes.c_double * 4)()
+        _check(_lib.sgf_plan_autotune(self._h, int(reps), ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(sc),
+                                      ms), "sgf_plan_autotune")
+        return {"chosen": {"col_pass": sc.col_pass, "row_inv0": sc.row_inv0},
+                "ms": {"col_pass0": ms[0], "col_pass1": ms[1], "row_inv0_0": ms[2], "row_inv0_1": ms[3]}}
 
     def profile(self, enable: bool = True):
         _check(_lib.sgf_plan_profile(self._h, 1 if enable else 0), "sgf_plan_profile")
@@ -307,3 +374,98 @@ def create_status(nest, precision, flags: int = 0) -> int:
     if st == SGF_OK:
         _lib.sgf_plan_destroy(h)
     return st
+
+
+def estimate(nest, precision="fp32", flags: int = 0) -> dict:
+    """sgf_plan_estimate: device bytes of a plan for this nest, without creating it (host only)."""
+    ws, sp, bb = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    desc = make_desc(nest)
+    _check(_lib.sgf_plan_estimate(ctypes.byref(desc), PRECISIONS.get(precision, precision), flags,
+                                  ctypes.byref(ws), ctypes.byref(sp), ctypes.byref(bb)), "sgf_plan_estimate")
+    return {"workspace_bytes": ws.value, "spectra_bytes": sp.value, "build_bytes": bb.value}
+
+
+class Server:
+    """The request loop (sgf_server_*): continuous admission of force requests with
+    host buffers onto concurrent streams under an HBM budget.
+
+    submit() queues a request; progress() collects finished ones and admits
+    waiting ones; both return at once.  The numpy arrays of a request are kept
+    referenced here until its completion has been returned.
+    """
+
+    def __init__(self, hbm_budget: int = 0, max_inflight: int = 4, simulate_gbs: Optional[float] = None):
+        cfg = ServerConfig()
+        cfg.hbm_budget = int(hbm_budget)
+        cfg.max_inflight = int(max_inflight)
+        cfg.flags = SERVER_SIMULATE if simulate_gbs is not None else 0
+        cfg.simulate_gbs = float(simulate_gbs or 0.0)
+        h = ctypes.c_void_p()
+        _check(_lib.sgf_server_create(ctypes.byref(cfg), ctypes.byref(h)), "sgf_server_create")
+        self._h = h
+        self._held = {}
+        self._buf = (Completion * 256)()
+
+    def clock(self) -> float:
+        return float(_lib.sgf_server_clock(self._h))
+
+    def submit(self, rid: int, nest, precision, sigma, fx, fy, plan_flags: int = 0) -> int:
+        """Queue request rid (sigma, fx, fy: per-level contiguous host arrays of the
+        precision's dtype).  Returns the sgf status (SGF_ENOMEM: rejected)."""
+        prec = PRECISIONS.get(precision, precision)
+        dt = np.float64 if prec == FP64 else np.float32
+        L = int(nest.levels)
+        arrays = (list(sigma), list(fx), list(fy))
+        for lst in arrays:
+            if len(lst) != L:
+                raise ValueError(f"need {L} arrays per field")
+            for a in lst:
+                if a.dtype != dt or not a.flags["C_CONTIGUOUS"] or a.shape != (nest.n, nest.n):
+                    raise ValueError(f"request arrays must be C-contiguous {np.dtype(dt).name} ({nest.n}, {nest.n})")
+        r = Request()
+        r.id = int(rid)
+        r.desc = make_desc(nest)
+        r.precision = prec
+        r.plan_flags = int(plan_flags)
+        for l in range(L):
+            r.sigma[l] = arrays[0][l].ctypes.data
+            r.fx[l] = arrays[1][l].ctypes.data
+            r.fy[l] = arrays[2][l].ctypes.data
+        st = int(_lib.sgf_server_submit(self._h, ctypes.byref(r)))
+        if st == SGF_OK:
+            self._held[int(rid)] = arrays
+        elif st != SGF_ENOMEM:
+            raise SgfError(st, "sgf_server_submit")
+        return st
+
+    def progress(self) -> List[dict]:
+        done = []
+        while True:
+            n = ctypes.c_int32()
+            st = int(_lib.sgf_server_progress(self._h, self._buf, len(self._buf), ctypes.byref(n)))
+            for k in range(n.value):
+                c = self._buf[k]
+                self._held.pop(int(c.id), None)
+                done.append({"id": int(c.id), "status": int(c.status), "slot": int(c.slot),
+                             "built_shape": bool(c.built_shape), "t_submit": c.t_submit, "t_admit": c.t_admit,
+                             "t_done": c.t_done})
+            _check(st, "sgf_server_progress")
+            if n.value < len(self._buf):
+                return done
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(_lib.sgf_server_stats_get(self._h, ctypes.byref(st)), "sgf_server_stats_get")
+        return {name: getattr(st, name) for name, _ in ServerStats._fields_ if name != "pad"}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.sgf_server_destroy(self._h)
+            self._h = None
+            self._held.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
