@@ -188,6 +188,10 @@ def run_gpu(args, world, rank, local):
     # three-field path is timed beside it and reported in config
     plan = sgf.Plan(nest, "fp32", zero_rim=not args.general)
     plan_general = sgf.Plan(nest, "fp32") if not args.general else None
+    # the autotuner picks each pass's kernel schedule (same arithmetic, bit-identical results)
+    tune = plan.autotune(reps=5)
+    if plan_general is not None:
+        plan_general.autotune(reps=3)
     st = plan.stats()
     # rotating input/output sets so nothing carries over in L2 between steps
     sets = max(2, -(-4 * L2_BYTES // (3 * n * n * 4)))
@@ -246,6 +250,7 @@ def run_gpu(args, world, rank, local):
     if not args.no_bf16x:
         # the split-BF16 tensor-core path side by side: same workload, same launch shape
         plan_bf = sgf.Plan(nest, "bf16x", zero_rim=not args.general)
+        plan_bf.autotune(reps=3)
         bms, bprof = timed(plan_bf, args.steps)
         ref_x, ref_y = torch.empty_like(base), torch.empty_like(base)
         plan.solve_ptrs([sig[0].data_ptr()], [ref_x.data_ptr()], [ref_y.data_ptr()], stream)
@@ -311,6 +316,7 @@ def run_gpu(args, world, rank, local):
         "config": {"workload": f"uniform-{n}x{n}-lognormal-taper", "n": n, "levels": 1,
                    "precision": "fp32", "parallelism": f"replicas{world}",
                    "path": "general-3-field" if args.general else "zero-rim-merged (verified per solve)",
+                   "schedule": tune["chosen"], "autotune_ms": tune["ms"],
                    "general_path": general,
                    "bf16x_path": bf16x,
                    "l2": f"{sets} rotating input/output sets ({sets * 3 * n * n * 4 / 2**20:.0f} MiB) > 129 MiB L2",
@@ -417,7 +423,7 @@ def run_serving(args, world, rank, local):
     pools = serving.make_pools(shapes, seed=args.seed)
     pool_s = time.perf_counter() - t0
     budget = int(args.budget_gb * 2 ** 30)
-    srv = sgf.Server(hbm_budget=budget, max_inflight=args.inflight)
+    srv = sgf.Server(hbm_budget=budget, max_inflight=args.inflight, max_shape_bytes=int(args.max_shape_gb * 2 ** 30))
     # warm-up: one request per shape (builds and keeps its spectra), then a short stream
     t0 = time.perf_counter()
     warm = [serving.Arrival(0.0, n, L, p, 0) for (n, L, p) in shapes]
@@ -457,7 +463,8 @@ def run_serving(args, world, rank, local):
             "config": {"workload": f"serving-poisson-{args.rate:g}rps-{args.seconds:g}s-N{sizes[0]}-{sizes[-1]}"
                                    f"-L{lv[0]}-{lv[-1]}-{'+'.join(precs)}",
                        "requests": len(recs), "shapes": len(shapes), "shapes_served": sorted(accepted),
-                       "hbm_budget_gib": args.budget_gb, "max_inflight": args.inflight,
+                       "hbm_budget_gib": args.budget_gb, "max_shape_gib": args.max_shape_gb,
+                       "max_inflight": args.inflight,
                        "parallelism": f"replicas{world}", "pool_s": pool_s, "warm_s": warm_s,
                        "inputs": "pinned host buffers, copies inside the latency"},
             "latency_ms": {k: summ.get(k) for k in ("p50_ms", "p90_ms", "p99_ms", "max_ms", "mean_ms")},
@@ -490,6 +497,8 @@ def main():
     ap.add_argument("--levels", default="2,5", help="serving: min,max levels of the requests")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serving: server HBM budget (GiB)")
     ap.add_argument("--inflight", type=int, default=4, help="serving: requests on the device at once")
+    ap.add_argument("--max-shape-gb", type=float, default=24.0,
+                    help="serving: largest spectra + generator memory of one shape (GiB); larger shapes are rejected")
     ap.add_argument("--precisions", default="fp32,bf16x", help="serving: precisions drawn uniformly per request")
     ap.add_argument("--seed", type=int, default=0)
     args = ap.parse_args()

@@ -139,6 +139,12 @@ sgf_status sgf_plan_check(sgf_plan *plan);
  * are freed with the last plan that uses them. */
 sgf_status sgf_plan_share(const sgf_plan *src, sgf_plan **out);
 
+/* As sgf_plan_share, with the new plan's precision: src's own, or SGF_FP32 and
+ * SGF_BF16X for each other (both keep FP32 spectra).  Errors: SGF_EINVAL for
+ * another precision, SGF_EUNSUPPORTED where SGF_BF16X does not apply (n = 4096
+ * with levels > 1), SGF_ENOMEM, SGF_ECUDA. */
+sgf_status sgf_plan_share_ex(const sgf_plan *src, sgf_precision precision, sgf_plan **out);
+
 sgf_status sgf_plan_stats_get(const sgf_plan *plan, sgf_plan_stats *stats);
 
 /* Forces on every level (Sec. 2.1, F^{x,0}+F^{x,x}+F^{x,y} and the y analogue).
@@ -284,7 +290,7 @@ sgf_status sgf_plan_estimate(const sgf_nest_desc *desc, sgf_precision precision,
  * kernels of admitted requests overlap on the device.  Kernel spectra stay
  * resident per nest shape (n, levels, offsets, precision, plan flags) as long
  * as a slot of that shape exists; new slots of a resident shape share them
- * (sgf_plan_share).  When memory is short the least recently used idle slots
+ * (sgf_plan_share_ex; FP32 and BF16X requests of one shape share FP32 spectra).  When memory is short the least recently used idle slots
  * are destroyed first, and a shape's spectra go with its last slot.  A server
  * is driven by one host thread and calls no CUDA function outside its calls.
  *
@@ -306,6 +312,9 @@ typedef struct {
     int32_t max_inflight;  /* requests on the device at once, >= 1 */
     uint32_t flags;        /* SGF_SERVER_* */
     double simulate_gbs;   /* SGF_SERVER_SIMULATE: modelled rate in GB/s (> 0) */
+    size_t max_shape_bytes; /* 0, or the largest spectra + generator memory of one shape: requests of
+                               larger shapes are rejected at submit (SGF_ENOMEM) instead of evicting
+                               every other resident shape */
 } sgf_server_config;
 
 /* One force request.  sigma[l], fx[l], fy[l] (l < desc.levels) are HOST arrays

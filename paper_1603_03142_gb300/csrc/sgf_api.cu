@@ -1308,14 +1308,29 @@ sgf_status sgf_plan_share(const sgf_plan *src, sgf_plan **out)
 {
     if (!src || !out)
         return fail(SGF_EINVAL, "NULL argument");
+    return sgf_plan_share_ex(src, src->prec, out);
+}
+
+sgf_status sgf_plan_share_ex(const sgf_plan *src, sgf_precision precision, sgf_plan **out)
+{
+    if (!src || !out)
+        return fail(SGF_EINVAL, "NULL argument");
     *out = nullptr;
+    const bool f32family = (src->prec == SGF_FP32 || src->prec == SGF_BF16X) &&
+                           (precision == SGF_FP32 || precision == SGF_BF16X);
+    if (precision != src->prec && !f32family)
+        return fail(SGF_EINVAL, "a plan of precision %d cannot share spectra of precision %d", (int)precision,
+                    (int)src->prec);
+    sgf_status vs = validate(&src->desc, precision);
+    if (vs != SGF_OK)
+        return vs;
     DeviceGuard g(src->device);
     sgf_plan *p = new sgf_plan();
     p->desc = src->desc;
-    p->prec = src->prec;
+    p->prec = precision;
     p->flags = src->flags;
     p->merged = src->merged;
-    p->tc = src->tc;
+    p->tc = precision == SGF_BF16X;
     p->sched = src->sched;
     p->N = src->N;
     p->logN = src->logN;

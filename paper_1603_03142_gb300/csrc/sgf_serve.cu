@@ -8,7 +8,8 @@
 //   H2D sigma -> sgf_solve -> D2H Fx, Fy -> event
 // on the slot's stream, so admitted requests overlap on the device.  Slots are
 // kept after their request finishes and reused by the next request of the same
-// shape; a new slot of a resident shape shares its spectra (sgf_plan_share).
+// shape; a new slot of a resident shape shares its spectra (sgf_plan_share_ex:
+// FP32 and BF16X slots of one shape hold the same FP32 spectra).
 // Memory pressure destroys the least recently used idle slots first.
 //
 // This file is a client of the plan API; it adds no kernels.
@@ -31,13 +32,14 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 struct Pending {
     sgf_request r;
-    std::string key;
+    std::string key;   // slot key: spectra key + precision
+    std::string skey;  // spectra key
     size_t ws = 0, spectra = 0, build = 0, io = 0;  // bytes (sgf_plan_estimate; io = 3 L n^2 elements)
     double t_submit = 0;
 };
 
 struct Slot {
-    std::string key;
+    std::string key, skey;
     sgf_plan *plan = nullptr;
     void *d_io = nullptr;
     size_t ws = 0, io = 0;
@@ -55,11 +57,13 @@ struct Shape {
     int slots = 0;
 };
 
-std::string shape_key(const sgf_request &r)
+// Spectra key of a request: FP32 and BF16X plans hold the same FP32 spectra.
+std::string spectra_key(const sgf_request &r)
 {
     std::string k;
     char buf[64];
-    snprintf(buf, sizeof buf, "%d/%d/%d/%u", r.desc.n, r.desc.levels, (int)r.precision, r.plan_flags);
+    snprintf(buf, sizeof buf, "%d/%d/%s/%u", r.desc.n, r.desc.levels, r.precision == SGF_FP64 ? "f64" : "f32",
+             r.plan_flags);
     k = buf;
     for (int l = 1; l < r.desc.levels; ++l) {
         snprintf(buf, sizeof buf, ":%d,%d", r.desc.off[l][0], r.desc.off[l][1]);
@@ -132,7 +136,7 @@ void slot_free(sgf_server *sv, Slot *s)
             cudaStreamDestroy(s->stream);
     }
     sv->account(-(long long)(s->ws + s->io));
-    auto it = sv->shapes.find(s->key);
+    auto it = sv->shapes.find(s->skey);
     if (it != sv->shapes.end() && --it->second.slots == 0) {
         sv->account(-(long long)it->second.spectra);
         sv->shapes.erase(it);
@@ -179,20 +183,22 @@ sgf_status slot_create(sgf_server *sv, const Pending &p, Slot **out)
 {
     Slot *s = new Slot();
     s->key = p.key;
+    s->skey = p.skey;
     s->ws = p.ws;
     s->io = p.io;
-    auto it = sv->shapes.find(p.key);
+    auto it = sv->shapes.find(p.skey);
     const bool resident = it != sv->shapes.end();
     sgf_status rc = SGF_OK;
     if (!sv->sim) {
         if (resident) {
             const sgf_plan *tmpl = nullptr;
             for (auto *o : sv->slots)
-                if (o && o->key == p.key) {
+                if (o && o->skey == p.skey) {
                     tmpl = o->plan;
                     break;
                 }
-            rc = tmpl ? sgf_plan_share(tmpl, &s->plan) : fail(SGF_EINVAL, "resident shape without a slot");
+            rc = tmpl ? sgf_plan_share_ex(tmpl, p.r.precision, &s->plan)
+                      : fail(SGF_EINVAL, "resident shape without a slot");
         } else {
             rc = sgf_plan_create_ex(&p.r.desc, p.r.precision, p.r.plan_flags, &s->plan);
         }
@@ -221,7 +227,7 @@ sgf_status slot_create(sgf_server *sv, const Pending &p, Slot **out)
         Shape sh;
         sh.spectra = p.spectra;
         sh.slots = 1;
-        sv->shapes[p.key] = sh;
+        sv->shapes[p.skey] = sh;
         sv->account((long long)p.spectra);
         sv->st.shapes_built++;
         s->built = true;
@@ -327,8 +333,14 @@ sgf_status sgf_server_submit(sgf_server *sv, const sgf_request *r)
             return fail(SGF_EINVAL, "request %llu: level %d has a NULL buffer", (unsigned long long)r->id, l);
     const size_t lvl = (size_t)r->desc.n * r->desc.n * (r->precision == SGF_FP64 ? 8 : 4);
     p.io = 3 * (size_t)L * align256(lvl);
-    p.key = shape_key(*r);
+    p.skey = spectra_key(*r);
+    p.key = p.skey + "/p" + std::to_string((int)r->precision);
     const size_t worst = p.ws + p.io + p.spectra + p.build;
+    if (sv->cfg.max_shape_bytes && p.spectra + p.build > sv->cfg.max_shape_bytes) {
+        sv->st.rejected++;
+        return fail(SGF_ENOMEM, "request %llu: its shape needs %zu bytes of spectra and generator memory, above "
+                    "max_shape_bytes %zu", (unsigned long long)r->id, p.spectra + p.build, sv->cfg.max_shape_bytes);
+    }
     if (worst > sv->cfg.hbm_budget) {
         sv->st.rejected++;
         return fail(SGF_ENOMEM, "request %llu needs %zu bytes (spectra %zu, generator %zu), above the budget %zu",
@@ -373,7 +385,7 @@ sgf_status sgf_server_progress(sgf_server *sv, sgf_completion *out, int32_t capa
                 idx = i;
         }
         if (idx < 0) {
-            const bool resident = sv->shapes.count(p.key) != 0;
+            const bool resident = sv->shapes.count(p.skey) != 0;
             const size_t need = p.ws + p.io + (resident ? 0 : p.spectra + p.build);
             while (sv->used + need > sv->cfg.hbm_budget && evict_one(sv)) {
             }

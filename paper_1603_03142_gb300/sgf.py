@@ -31,7 +31,8 @@ EXPORTS = ["sgf_plan_create", "sgf_plan_create_ex", "sgf_plan_check", "sgf_plan_
            "sgf_plan_profile", "sgf_plan_profile_read", "sgf_solve_noalloc", "sgf_batch_create",
            "sgf_batch_solve", "sgf_batch_info", "sgf_batch_destroy", "sgf_plan_estimate", "sgf_server_create",
            "sgf_server_clock", "sgf_server_submit", "sgf_server_progress", "sgf_server_stats_get",
-           "sgf_server_destroy", "sgf_plan_schedule_get", "sgf_plan_schedule_set", "sgf_plan_autotune"]
+           "sgf_server_destroy", "sgf_plan_schedule_get", "sgf_plan_schedule_set", "sgf_plan_autotune",
+           "sgf_plan_share_ex"]
 BATCH_NO_GRAPH = 0x1
 PLAN_ZERO_RIM = 0x1
 NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -58,7 +59,7 @@ class KernelTimes(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_inflight", ctypes.c_int32), ("flags", ctypes.c_uint32),
-                ("simulate_gbs", ctypes.c_double)]
+                ("simulate_gbs", ctypes.c_double), ("max_shape_bytes", ctypes.c_size_t)]
 
 
 class Request(ctypes.Structure):
@@ -93,6 +94,7 @@ _lib.sgf_plan_create_ex.argtypes = [ctypes.POINTER(NestDesc), ctypes.c_int, ctyp
                                     ctypes.POINTER(ctypes.c_void_p)]
 _lib.sgf_plan_check.argtypes = [ctypes.c_void_p]
 _lib.sgf_plan_share.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+_lib.sgf_plan_share_ex.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
 _lib.sgf_plan_stats_get.argtypes = [ctypes.c_void_p, ctypes.POINTER(PlanStats)]
 _lib.sgf_solve.argtypes = [ctypes.c_void_p, _vpp, _vpp, _vpp, ctypes.c_void_p]
 _lib.sgf_solve_host.argtypes = [ctypes.c_void_p, _vpp, _vpp, _vpp, ctypes.c_void_p]
@@ -129,7 +131,7 @@ for _f in ("sgf_plan_create", "sgf_plan_create_ex", "sgf_plan_check", "sgf_plan_
            "sgf_solve_noalloc", "sgf_batch_create", "sgf_batch_solve", "sgf_batch_info", "sgf_batch_destroy",
            "sgf_plan_estimate", "sgf_server_create", "sgf_server_submit", "sgf_server_progress",
            "sgf_server_stats_get", "sgf_server_destroy", "sgf_plan_schedule_get", "sgf_plan_schedule_set",
-           "sgf_plan_autotune"):
+           "sgf_plan_autotune", "sgf_plan_share_ex"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -211,10 +213,17 @@ class Plan:
     def dtype_name(self) -> str:
         return "float64" if self.precision == FP64 else "float32"
 
-    def share(self) -> "Plan":
+    def share(self, precision=None) -> "Plan":
+        """A plan with its own workspace on these spectra (precision: this plan's, or
+        fp32 / bf16x for each other)."""
         h = ctypes.c_void_p()
-        _check(_lib.sgf_plan_share(self._h, ctypes.byref(h)), "sgf_plan_share")
-        return Plan(self.nest, self.precision, zero_rim=self.zero_rim, _handle=h)
+        if precision is None:
+            _check(_lib.sgf_plan_share(self._h, ctypes.byref(h)), "sgf_plan_share")
+            prec = self.precision
+        else:
+            prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+            _check(_lib.sgf_plan_share_ex(self._h, prec, ctypes.byref(h)), "sgf_plan_share_ex")
+        return Plan(self.nest, prec, zero_rim=self.zero_rim, _handle=h)
 
     def stats(self) -> dict:
         st = PlanStats()
@@ -394,9 +403,11 @@ class Server:
     referenced here until its completion has been returned.
     """
 
-    def __init__(self, hbm_budget: int = 0, max_inflight: int = 4, simulate_gbs: Optional[float] = None):
+    def __init__(self, hbm_budget: int = 0, max_inflight: int = 4, simulate_gbs: Optional[float] = None,
+                 max_shape_bytes: int = 0):
         cfg = ServerConfig()
         cfg.hbm_budget = int(hbm_budget)
+        cfg.max_shape_bytes = int(max_shape_bytes)
         cfg.max_inflight = int(max_inflight)
         cfg.flags = SERVER_SIMULATE if simulate_gbs is not None else 0
         cfg.simulate_gbs = float(simulate_gbs or 0.0)

@@ -178,3 +178,28 @@ def test_bf16x_limits():
     with pytest.raises(sgf.SgfError) as ei:
         sgf.estimate(W.centred_nest(4096, 2), "bf16x")
     assert ei.value.status == sgf.SGF_EUNSUPPORTED
+
+
+def test_fp32_and_bf16x_share_spectra():
+    """FP32 and BF16X requests of one shape hold one set of FP32 spectra."""
+    srv = sgf.Server(hbm_budget=4 << 30, max_inflight=2, simulate_gbs=100.0)
+    nest = W.centred_nest(256, 2)
+    for i, prec in enumerate(["fp32", "bf16x", "fp32", "bf16x"]):
+        assert srv.submit(i, nest, prec, _arrays(256, 2), _arrays(256, 2), _arrays(256, 2)) == 0
+    _drain(srv, 4)
+    st = srv.stats()
+    assert st["shapes_built"] == 1 and st["shapes_resident"] == 1 and st["slots"] == 2
+    srv.close()
+
+
+def test_max_shape_bytes_rejects_large_shapes():
+    big, small = W.centred_nest(1024, 3), W.centred_nest(128, 2)
+    eb = sgf.estimate(big, "fp32")
+    cap = eb["spectra_bytes"] + eb["build_bytes"] - 1
+    srv = sgf.Server(hbm_budget=64 << 30, max_inflight=2, simulate_gbs=100.0, max_shape_bytes=cap)
+    assert srv.submit(0, big, "fp32", _arrays(1024, 3), _arrays(1024, 3), _arrays(1024, 3)) == sgf.SGF_ENOMEM
+    assert "max_shape_bytes" in sgf.last_error()
+    assert srv.submit(1, small, "fp32", _arrays(128, 2), _arrays(128, 2), _arrays(128, 2)) == 0
+    assert [d["id"] for d in _drain(srv, 1)] == [1]
+    assert srv.stats()["rejected"] == 1
+    srv.close()
