@@ -188,10 +188,18 @@ def run_gpu(args, world, rank, local):
     # three-field path is timed beside it and reported in config
     plan = sgf.Plan(nest, "fp32", zero_rim=not args.general)
     plan_general = sgf.Plan(nest, "fp32") if not args.general else None
-    # the autotuner picks each pass's kernel schedule (same arithmetic, bit-identical results)
-    tune = plan.autotune(reps=5)
-    if plan_general is not None:
-        plan_general.autotune(reps=3)
+    # the autotuner picks each pass's kernel schedule (same arithmetic; results agree to rounding),
+    # unless --schedule fixes it
+    if args.schedule == "auto":
+        tune = plan.autotune(reps=5)
+        if plan_general is not None:
+            plan_general.autotune(reps=3)
+    else:
+        col, inv = (int(x) for x in args.schedule.split(","))
+        plan.set_schedule(col, inv)
+        if plan_general is not None:
+            plan_general.set_schedule(0, inv)
+        tune = {"chosen": plan.schedule(), "ms": None}
     st = plan.stats()
     # rotating input/output sets so nothing carries over in L2 between steps
     sets = max(2, -(-4 * L2_BYTES // (3 * n * n * 4)))
@@ -489,6 +497,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--general", action="store_true", help="time only the general three-field path")
     ap.add_argument("--no-bf16x", action="store_true", help="skip the split-BF16 tensor-core path")
+    ap.add_argument("--schedule", default="auto",
+                    help="uniform: 'auto' (autotuner) or 'col_pass,row_inv0' to fix the kernel schedule")
     ap.add_argument("--workload", default="uniform", choices=["uniform", "batched", "serving"])
     ap.add_argument("--nests", type=int, default=256)
     ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate (requests/s)")

@@ -235,9 +235,11 @@ sgf_status sgf_solve_noalloc(sgf_plan *plan, const void *const *sigma, void *con
                              void *stream);
 
 /* ---- Tile schedule and autotuner (no paper counterpart) -----------------
- * Two passes have more than one kernel schedule.  The schedules perform the
- * same arithmetic in the same order, so the forces do not depend on the choice
- * (bit for bit); only the time does.
+ * Two passes have more than one kernel schedule.  The schedules evaluate the
+ * same expressions in the same order, so the forces agree to rounding (the
+ * compiler may fuse a multiply and an add differently in two kernels: a few
+ * units in the last place); only the time differs.  One plan with one schedule
+ * is bitwise reproducible.
  *   col_pass (SGF_PLAN_ZERO_RIM plans): 0 = the two inverse column transforms
  *     one after the other (one sequence per thread; three CTAs per SM at
  *     n = 4096), 1 = both in flight (two sequences per thread sharing the
@@ -246,15 +248,23 @@ sgf_status sgf_solve_noalloc(sgf_plan *plan, const void *const *sigma, void *con
  *     component), the finer levels through the nest kernel; 1 = every level
  *     through the nest kernel (one CTA per row pair, both components, the
  *     gather of the second overlapping the first's transform).
- * A new plan starts from {0, 0}, or from the schedule the autotuner recorded for
+ *   col_case3 (nests): 0 = the m^2 Case-3 phase outputs of a (coarser source,
+ *     target) pair in one cluster per column, the source's forward column
+ *     transforms done once for all of them; 1 = one cluster per phase output,
+ *     each transforming the source again.
+ * A new plan starts from {0, 0, 0}, or from the schedule the autotuner recorded for
  * its key (device, n, precision, zero-rim, levels > 1); sgf_plan_share copies it. */
 typedef struct {
     int32_t col_pass;
     int32_t row_inv0;
+    int32_t col_case3;
 } sgf_schedule;
 
 sgf_status sgf_plan_schedule_get(const sgf_plan *plan, sgf_schedule *schedule);
-/* Errors: SGF_EINVAL for a NULL argument or a choice other than 0 or 1. */
+/* Errors: SGF_EINVAL for a NULL argument or a choice other than 0 or 1;
+ * SGF_EUNSUPPORTED for row_inv0 = 1 on a SGF_BF16X plan of n = SGF_MAX_N (that
+ * kernel has no shared memory left for the tensor-core tiles there; the
+ * autotuner skips it). */
 sgf_status sgf_plan_schedule_set(sgf_plan *plan, const sgf_schedule *schedule);
 
 /* The autotuner: runs one solve on zero density (temporary device buffers),
@@ -263,10 +273,11 @@ sgf_status sgf_plan_schedule_set(sgf_plan *plan, const sgf_schedule *schedule);
  * `stream` -- keeps the fastest in the plan and records it for later plans of
  * the same key: in the process, and in the text file named by the environment
  * variable SGF_AUTOTUNE_CACHE if it is set (one line "<key> <col_pass>
- * <row_inv0>" per key, read once, rewritten after each tuning).  chosen (may be
- * NULL) receives the schedule; ms (may be NULL, else 4 doubles) the mean
- * milliseconds per launch of col_pass 0, col_pass 1, row_inv0 0, row_inv0 1
- * (-1 where a pass has a single candidate).  Blocks until done.
+ * <row_inv0> <col_case3>" per key, read once, rewritten after each tuning).  chosen (may be
+ * NULL) receives the schedule; ms (may be NULL, else 6 doubles) the mean
+ * milliseconds per launch of col_pass 0, col_pass 1, row_inv0 0, row_inv0 1,
+ * col_case3 0, col_case3 1 (-1 where a candidate does not apply).  Blocks until
+ * done.
  * Errors: SGF_EINVAL, SGF_ENOMEM, SGF_ECUDA. */
 sgf_status sgf_plan_autotune(sgf_plan *plan, int32_t reps, void *stream, sgf_schedule *chosen, double *ms);
 

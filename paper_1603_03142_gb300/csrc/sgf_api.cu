@@ -113,6 +113,10 @@ struct sgf_plan {
     std::vector<ColOutput> outs;
     std::vector<ColInput> ins;
     std::vector<RowContrib> contribs;
+    std::vector<ColWork> work_all, work_main;  // k_col work lists: every output / the main outputs
+    std::vector<ColGroup> groups;              // Case-3 output groups (k_col_g)
+    std::vector<ColSum> sums;                  // chunked outputs (k_col_sum)
+    size_t partial_elems = 0;                  // complex elements of the chunk accumulators
     int contrib_begin[kMaxLevels + 1] = {};
     std::vector<GenSet> sets;
     size_t fwd_elems = 0, bwd_elems = 0;  // complex elements
@@ -123,6 +127,10 @@ struct sgf_plan {
     const ColOutput *d_outs = nullptr;
     const ColInput *d_ins = nullptr;
     const RowContrib *d_contribs = nullptr;
+    const ColWork *d_work_all = nullptr, *d_work_main = nullptr;
+    const ColGroup *d_groups = nullptr;
+    const ColSum *d_sums = nullptr;
+    void *d_partial = nullptr;
     void *d_fwd = nullptr, *d_bwd = nullptr;
     void *d_restricted = nullptr;  // (L-1) * N * N reals
     // host-buffer solve staging (allocated on first sgf_solve_host)
@@ -150,8 +158,11 @@ struct sgf_batch {
         sgf_schedule sched{};  // of the group's first plan
         int n_fwd = 0, n_col = 0, n_inv1 = 0, n_inv = 0;  // map entries per pass (inv1: level 0)
         size_t map_fwd = 0, map_col = 0, map_inv1 = 0, map_inv = 0;  // int2 offsets in the map buffer
+        int n_grp = 0, n_sum = 0;
+        size_t map_grp = 0, map_sum = 0;  // Case-3 groups (k_col_g), chunked outputs (k_col_sum)
     };
     std::vector<Group> groups;
+    std::vector<int> plan_group;      // group index of every plan
     std::vector<int> restrict_jobs;   // count per restriction depth
     std::vector<size_t> restrict_off; // int2 offsets per depth
     int max_n = 0;
@@ -240,12 +251,21 @@ void build_lists_merged(sgf_plan *p)
     p->contrib_begin[0] = 0;
     p->contribs.push_back(RowContrib{1, 0, 0, 0});
     p->contrib_begin[1] = 1;
+    p->work_all.push_back(ColWork{0, 0, 1, -1});
+    p->work_main.push_back(ColWork{0, 0, 1, -1});
     for (int r = 0; r < N / 2; ++r)
         p->items.push_back(FwdItem{0, r});
     // sigma in, Fx Fy out; 1-field forward and 2-field backward intermediates; 2 quarter spectra
     p->algorithmic_bytes = 3 * (size_t)N * N * T + 2 * p->fwd_elems * Cb + 2 * p->bwd_elems * Cb +
                            2 * (size_t)(N + 1) * (N + 1) * T;
 }
+
+// Case-3 phase outputs that share one forward transform of their source (k_col_g):
+// more per group saves transforms, fewer keeps more clusters running at once.
+constexpr int kCase3Group = 8;
+// Inputs of one k_col work item: a main output with more (the Case-2 phases of
+// deep nests) is split into chunks that run in parallel.
+constexpr int kChunkInputs = 16;
 
 // Build all host-side lists of a plan (no CUDA calls).
 void build_lists(sgf_plan *p)
@@ -358,6 +378,32 @@ void build_lists(sgf_plan *p)
         }
     }
     p->contrib_begin[L] = (int)p->contribs.size();
+    // k_col work lists (main outputs with long input lists split into chunks of
+    // kChunkInputs, summed by k_col_sum) and the Case-3 groups of k_col_g
+    int slots = 0;
+    for (int t = 0; t < L; ++t) {
+        const ColOutput &o = p->outs[main_out[t]];
+        if (o.in_count <= kChunkInputs) {
+            p->work_main.push_back(ColWork{main_out[t], o.in_begin, o.in_count, -1});
+            continue;
+        }
+        const int first = slots;
+        for (int k = 0; k < o.in_count; k += kChunkInputs)
+            p->work_main.push_back(ColWork{main_out[t], o.in_begin + k, std::min(kChunkInputs, o.in_count - k), slots++});
+        p->sums.push_back(ColSum{main_out[t], first, slots - first, 0});
+    }
+    p->partial_elems = (size_t)slots * 4 * N * (N + 1);
+    p->work_all = p->work_main;
+    for (int o = 0; o < (int)p->outs.size(); ++o)
+        if (std::find(main_out.begin(), main_out.end(), o) == main_out.end())
+            p->work_all.push_back(ColWork{o, p->outs[o].in_begin, p->outs[o].in_count, -1});
+    for (int t = 0; t < L; ++t) {
+        for (int s = 0; s < t; ++s) {  // sub-groups of at most kCase3Group outputs keep the columns parallel
+            const int m = 1 << (t - s);
+            for (int q = 0; q < m * m; q += kCase3Group)
+                p->groups.push_back(ColGroup{c3_base[{s, t}] + q, std::min(kCase3Group, m * m - q)});
+        }
+    }
     // forward work items
     for (int k = 0; k < (int)p->slabs.size(); ++k)
         for (int r = 0; r < p->slabs[k].rows / 2; ++r)
@@ -408,6 +454,8 @@ void plan_free_owned(sgf_plan *p)
     cudaFree(p->d_bwd);
     cudaFree(p->d_restricted);
     cudaFree(p->d_stage);
+    cudaFree(p->d_partial);
+    p->d_partial = nullptr;
     cudaFree(p->d_status);
     if (p->done)
         cudaEventDestroy(p->done);
@@ -436,7 +484,11 @@ size_t workspace_of(const sgf_plan *p)
     align_push(blob, p->outs);
     align_push(blob, p->ins);
     align_push(blob, p->contribs);
-    return blob.size() + (p->fwd_elems + p->bwd_elems) * 2 * p->esize +
+    align_push(blob, p->work_all);
+    align_push(blob, p->work_main);
+    align_push(blob, p->groups);
+    align_push(blob, p->sums);
+    return blob.size() + p->partial_elems * 2 * p->esize + (p->fwd_elems + p->bwd_elems) * 2 * p->esize +
            (size_t)(p->L > 1 ? p->L - 1 : 0) * p->N * p->N * p->esize;
 }
 
@@ -449,6 +501,10 @@ sgf_status plan_alloc_owned(sgf_plan *p)
     const size_t o_outs = align_push(blob, p->outs);
     const size_t o_ins = align_push(blob, p->ins);
     const size_t o_con = align_push(blob, p->contribs);
+    const size_t o_call = align_push(blob, p->work_all);
+    const size_t o_cmain = align_push(blob, p->work_main);
+    const size_t o_grp = align_push(blob, p->groups);
+    const size_t o_sum = align_push(blob, p->sums);
     cudaError_t e;
     if ((e = cudaMalloc(&p->d_lists, blob.size())) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc(work lists)");
@@ -460,7 +516,13 @@ sgf_status plan_alloc_owned(sgf_plan *p)
     p->d_outs = reinterpret_cast<const ColOutput *>(base + o_outs);
     p->d_ins = reinterpret_cast<const ColInput *>(base + o_ins);
     p->d_contribs = reinterpret_cast<const RowContrib *>(base + o_con);
+    p->d_work_all = reinterpret_cast<const ColWork *>(base + o_call);
+    p->d_work_main = reinterpret_cast<const ColWork *>(base + o_cmain);
+    p->d_groups = reinterpret_cast<const ColGroup *>(base + o_grp);
+    p->d_sums = reinterpret_cast<const ColSum *>(base + o_sum);
     const size_t Cb = 2 * p->esize;
+    if (p->partial_elems && (e = cudaMalloc(&p->d_partial, p->partial_elems * Cb)) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(chunk accumulators)");
     if ((e = cudaMalloc(&p->d_fwd, p->fwd_elems * Cb)) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc(forward intermediates)");
     if ((e = cudaMalloc(&p->d_bwd, p->bwd_elems * Cb)) != cudaSuccess)
@@ -628,6 +690,38 @@ cudaError_t launch_row_inv(int logN, int L, SolveArgs<T> a, cudaStream_t st, boo
 // Zero-rim column pass of the plan's schedule.
 inline int col_m_pass(const sgf_plan *p) { return p->sched.col_pass == 1 ? PASS_COL_MD : PASS_COL_M; }
 
+// Column pass of a solve: zero-rim plans through k_col_m / k_col_md; general
+// plans through k_col over the main outputs and k_col_g over the Case-3 groups
+// (col_case3 = 0), or k_col over every output (col_case3 = 1).  a.col_list
+// matches the schedule.
+template <typename T>
+cudaError_t launch_col(const sgf_plan *p, const SolveArgs<T> &a, cudaStream_t st)
+{
+    if (p->merged)
+        return launch_pass_n<T>(col_m_pass(p), p->logN, a, 1, st, nullptr, p->tc);
+    cudaError_t e;
+    if (p->sched.col_case3 == 1) {
+        e = launch_pass_n<T>(PASS_COL, p->logN, a, (int)p->work_all.size(), st, nullptr, p->tc);
+    } else {
+        e = launch_pass_n<T>(PASS_COL, p->logN, a, (int)p->work_main.size(), st, nullptr, p->tc);
+        if (e == cudaSuccess && !p->groups.empty())
+            e = launch_pass_n<T>(PASS_COL_G, p->logN, a, (int)p->groups.size(), st, nullptr, p->tc);
+    }
+    if (e != cudaSuccess || p->sums.empty())
+        return e;
+    return launch_pass_n<T>(PASS_COL_SUM, p->logN, a, (int)p->sums.size(), st, nullptr, p->tc);
+}
+
+// Whether a schedule applies to a plan: the nest inverse kernel (row_inv0 = 1
+// for level 0) has no shared memory left for tensor-core tiles at n = 4096.
+inline bool schedule_ok(const sgf_plan *p, const sgf_schedule &s)
+{
+    if ((s.col_pass != 0 && s.col_pass != 1) || (s.row_inv0 != 0 && s.row_inv0 != 1) ||
+        (s.col_case3 != 0 && s.col_case3 != 1))
+        return false;
+    return !(s.row_inv0 == 1 && p->tc && p->N == SGF_MAX_N);
+}
+
 template <typename T>
 sgf_status solve_impl(sgf_plan *p, const void *const *sigma, void *const *fx, void *const *fy,
                       cudaStream_t st)
@@ -673,6 +767,10 @@ sgf_status solve_impl(sgf_plan *p, const void *const *sigma, void *const *fx, vo
     a.outs = p->d_outs;
     a.ins = p->d_ins;
     a.contribs = p->d_contribs;
+    a.col_list = p->sched.col_case3 == 0 ? p->d_work_main : p->d_work_all;
+    a.groups = p->d_groups;
+    a.sums = p->d_sums;
+    a.partial = static_cast<typename SolveArgs<T>::C *>(p->d_partial);
     for (int l = 0; l <= L; ++l)
         a.contrib_begin[l] = p->contrib_begin[l];
     cudaError_t e;
@@ -684,8 +782,7 @@ sgf_status solve_impl(sgf_plan *p, const void *const *sigma, void *const *fx, vo
         return cuda_fail(e, "row_fwd launch");
     if ((ms = mark(p, st)) != SGF_OK)
         return ms;
-    e = p->merged ? launch_pass_n<T>(col_m_pass(p), p->logN, a, 1, st, nullptr, p->tc)
-                  : launch_pass_n<T>(PASS_COL, p->logN, a, (int)p->outs.size(), st, nullptr, p->tc);
+    e = launch_col<T>(p, a, st);
     if (e != cudaSuccess)
         return cuda_fail(e, "col launch");
     if ((ms = mark(p, st)) != SGF_OK)
@@ -774,7 +871,7 @@ size_t noalloc_bytes(const sgf_plan *p)
 {
     const size_t Cb = 2 * p->esize;
     return align256((size_t)(p->L > 1 ? p->L - 1 : 0) * p->N * p->N * p->esize) + align256(p->fwd_elems * Cb) +
-           align256(p->bwd_elems * Cb);
+           align256(p->bwd_elems * Cb) + align256(p->partial_elems * Cb);
 }
 
 // The solve of solve_impl with its intermediates in `scratch` and without the
@@ -788,6 +885,7 @@ sgf_status solve_noalloc_impl(sgf_plan *p, const void *const *sigma, void *const
     T *restricted = reinterpret_cast<T *>(scratch);
     unsigned char *fwd = scratch + align256((size_t)(L > 1 ? L - 1 : 0) * N * N * p->esize);
     unsigned char *bwd = fwd + align256(p->fwd_elems * Cb);
+    unsigned char *partial = bwd + align256(p->bwd_elems * Cb);
     SolveArgs<T> a{};
     a.N = N;
     a.logN = p->logN;
@@ -824,14 +922,17 @@ sgf_status solve_noalloc_impl(sgf_plan *p, const void *const *sigma, void *const
     a.outs = p->d_outs;
     a.ins = p->d_ins;
     a.contribs = p->d_contribs;
+    a.col_list = p->sched.col_case3 == 0 ? p->d_work_main : p->d_work_all;
+    a.groups = p->d_groups;
+    a.sums = p->d_sums;
+    a.partial = reinterpret_cast<typename SolveArgs<T>::C *>(partial);
     for (int l = 0; l <= L; ++l)
         a.contrib_begin[l] = p->contrib_begin[l];
     cudaError_t e = p->merged ? launch_pass_n<T>(PASS_ROW_FWD_M, p->logN, a, 0, st, nullptr, p->tc)
                               : launch_pass_n<T>(PASS_ROW_FWD, p->logN, a, (int)p->items.size(), st, nullptr, p->tc);
     if (e != cudaSuccess)
         return cuda_fail(e, "row_fwd launch");
-    e = p->merged ? launch_pass_n<T>(col_m_pass(p), p->logN, a, 1, st, nullptr, p->tc)
-                  : launch_pass_n<T>(PASS_COL, p->logN, a, (int)p->outs.size(), st, nullptr, p->tc);
+    e = launch_col<T>(p, a, st);
     if (e != cudaSuccess)
         return cuda_fail(e, "col launch");
     if ((e = launch_row_inv<T>(p->logN, L, a, st, p->tc, p->sched.row_inv0)) != cudaSuccess)
@@ -845,7 +946,8 @@ sgf_status solve_noalloc_impl(sgf_plan *p, const void *const *sigma, void *const
 // ---- fused batches (sgf_batch_*) -------------------------------------------
 // The solve arguments of one nest, as solve_impl builds them, without launching.
 template <typename T>
-void fill_args(const sgf_plan *p, const void *const *sigma, void *const *fx, void *const *fy, SolveArgs<T> &a)
+void fill_args(const sgf_plan *p, const void *const *sigma, void *const *fx, void *const *fy, SolveArgs<T> &a,
+               const sgf_schedule &sc)
 {
     const int N = p->N, L = p->L;
     a = SolveArgs<T>{};
@@ -878,6 +980,10 @@ void fill_args(const sgf_plan *p, const void *const *sigma, void *const *fx, voi
     a.outs = p->d_outs;
     a.ins = p->d_ins;
     a.contribs = p->d_contribs;
+    a.col_list = sc.col_case3 == 0 ? p->d_work_main : p->d_work_all;
+    a.groups = p->d_groups;
+    a.sums = p->d_sums;
+    a.partial = static_cast<typename SolveArgs<T>::C *>(p->d_partial);
     for (int l = 0; l <= L; ++l)
         a.contrib_begin[l] = p->contrib_begin[l];
 }
@@ -912,6 +1018,16 @@ sgf_status batch_launches(sgf_batch *bt, cudaStream_t st)
         const int colp = !g.merged ? PASS_COL : g.sched.col_pass == 1 ? PASS_COL_MD : PASS_COL_M;
         if ((e = launch_pass_n<T>(colp, g.logN, dummy, g.n_col, st, &vc, g.tc)) != cudaSuccess)
             return cuda_fail(e, "batched col launch");
+        if (g.n_grp > 0) {
+            BatchView<T> vg{args, bt->d_maps + g.map_grp};
+            if ((e = launch_pass_n<T>(PASS_COL_G, g.logN, dummy, g.n_grp, st, &vg, g.tc)) != cudaSuccess)
+                return cuda_fail(e, "batched Case-3 group launch");
+        }
+        if (g.n_sum > 0) {
+            BatchView<T> vs{args, bt->d_maps + g.map_sum};
+            if ((e = launch_pass_n<T>(PASS_COL_SUM, g.logN, dummy, g.n_sum, st, &vs, g.tc)) != cudaSuccess)
+                return cuda_fail(e, "batched chunk-sum launch");
+        }
         if (g.sched.row_inv0 == 1) {  // every level through k_row_inv (level-0 entries precede the others)
             if ((e = launch_pass_n<T>(PASS_ROW_INV, g.logN, dummy, g.n_inv1 + g.n_inv, st, &vi1, g.tc)) != cudaSuccess)
                 return cuda_fail(e, "batched row_inv launch");
@@ -967,6 +1083,7 @@ sgf_status batch_build(sgf_batch *bt)
             members.emplace_back();
         }
         members[gidx[key]].push_back(k);
+        bt->plan_group.push_back(gidx[key]);
     }
     for (size_t gi = 0; gi < bt->groups.size(); ++gi) {
         auto &g = bt->groups[gi];
@@ -985,10 +1102,26 @@ sgf_status batch_build(sgf_batch *bt)
             g.n_fwd = (int)members[gi].size();
         }
         g.map_col = maps.size();
-        for (int k : members[gi])
-            for (int o = 0; o < (int)bt->plans[k]->outs.size(); ++o)
+        for (int k : members[gi]) {
+            const sgf_plan *p = bt->plans[k];
+            const int n = g.sched.col_case3 == 0 ? (int)p->work_main.size() : (int)p->work_all.size();
+            for (int o = 0; o < n; ++o)
                 maps.push_back(make_int2(k, o));
+        }
         g.n_col = (int)(maps.size() - g.map_col);
+        g.map_grp = maps.size();
+        if (g.sched.col_case3 == 0)
+            for (int k : members[gi])
+                for (int q = 0; q < (int)bt->plans[k]->groups.size(); ++q)
+                    maps.push_back(make_int2(k, q));
+        g.n_grp = (int)(maps.size() - g.map_grp);
+        bt->launches += g.n_grp > 0 ? 1 : 0;
+        g.map_sum = maps.size();
+        for (int k : members[gi])
+            for (int q = 0; q < (int)bt->plans[k]->sums.size(); ++q)
+                maps.push_back(make_int2(k, q));
+        g.n_sum = (int)(maps.size() - g.map_sum);
+        bt->launches += g.n_sum > 0 ? 1 : 0;
         g.map_inv1 = maps.size();
         for (int k : members[gi])
             maps.push_back(make_int2(k, 0));
@@ -1047,7 +1180,7 @@ sgf_status batch_solve(sgf_batch *bt, const void *const *const *sigma, void *con
         return cuda_fail(e, "waiting for the previous batch upload");
     SolveArgs<T> *h = static_cast<SolveArgs<T> *>(bt->h_args);
     for (size_t k = 0; k < bt->plans.size(); ++k)
-        fill_args<T>(bt->plans[k], sigma[k], fx[k], fy[k], h[k]);
+        fill_args<T>(bt->plans[k], sigma[k], fx[k], fy[k], h[k], bt->groups[bt->plan_group[k]].sched);
     bt->solved_once = true;
     if (!bt->use_graph)
         return batch_launches<T>(bt, st);
@@ -1109,10 +1242,10 @@ void tune_load_locked()
     if (!f)
         return;
     char key[160];
-    int a = 0, b = 0;
-    while (fscanf(f, "%159s %d %d", key, &a, &b) == 3)
-        if ((a == 0 || a == 1) && (b == 0 || b == 1))
-            g_tune[key] = sgf_schedule{a, b};
+    int a = 0, b = 0, c = 0;
+    while (fscanf(f, "%159s %d %d %d", key, &a, &b, &c) == 4)
+        if ((a == 0 || a == 1) && (b == 0 || b == 1) && (c == 0 || c == 1))
+            g_tune[key] = sgf_schedule{a, b, c};
     fclose(f);
 }
 
@@ -1129,7 +1262,7 @@ void tune_store(const std::string &key, const sgf_schedule &s)
     if (!f)
         return;
     for (const auto &kv : g_tune)
-        fprintf(f, "%s %d %d\n", kv.first.c_str(), kv.second.col_pass, kv.second.row_inv0);
+        fprintf(f, "%s %d %d %d\n", kv.first.c_str(), kv.second.col_pass, kv.second.row_inv0, kv.second.col_case3);
     fclose(f);
     rename(tmp.c_str(), path);
 }
@@ -1139,12 +1272,12 @@ void tune_apply(sgf_plan *p)
     std::lock_guard<std::mutex> lk(g_tune_mu);
     tune_load_locked();
     auto it = g_tune.find(tune_key(p));
-    if (it != g_tune.end())
+    if (it != g_tune.end() && schedule_ok(p, it->second))
         p->sched = it->second;
 }
 
 template <typename T>
-sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[4])
+sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[6])
 {
     const size_t lvl = (size_t)p->N * p->N * p->esize;
     const size_t lal = (lvl + 255) & ~(size_t)255;
@@ -1170,7 +1303,7 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[4])
     if (s != SGF_OK)
         return s;
     SolveArgs<T> a;
-    fill_args<T>(p, ds, dx, dy, a);
+    fill_args<T>(p, ds, dx, dy, a, p->sched);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
         if (e0)
@@ -1193,7 +1326,7 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[4])
         out = t / reps;
         return SGF_OK;
     };
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < 6; ++k)
         ms[k] = -1.0;
     sgf_schedule best = p->sched;
     if (p->merged) {
@@ -1203,10 +1336,26 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[4])
         if (s == SGF_OK)
             best.col_pass = ms[1] < ms[0] ? 1 : 0;
     }
-    for (int c = 0; c < 2 && s == SGF_OK; ++c)
-        s = timeit([&] { return launch_row_inv<T>(p->logN, p->L, a, st, p->tc, c); }, ms[2 + c]);
+    for (int c = 0; c < 2 && s == SGF_OK; ++c) {
+        sgf_schedule cand = best;
+        cand.row_inv0 = c;
+        if (schedule_ok(p, cand))
+            s = timeit([&] { return launch_row_inv<T>(p->logN, p->L, a, st, p->tc, c); }, ms[2 + c]);
+    }
     if (s == SGF_OK)
-        best.row_inv0 = ms[3] < ms[2] ? 1 : 0;
+        best.row_inv0 = ms[3] >= 0.0 && ms[3] < ms[2] ? 1 : 0;
+    if (!p->merged && !p->groups.empty()) {  // Case-3 outputs grouped or one cluster each
+        const sgf_schedule keep = p->sched;
+        for (int c = 0; c < 2 && s == SGF_OK; ++c) {
+            p->sched.col_case3 = c;
+            SolveArgs<T> ac;
+            fill_args<T>(p, ds, dx, dy, ac, p->sched);
+            s = timeit([&] { return launch_col<T>(p, ac, st); }, ms[4 + c]);
+        }
+        p->sched = keep;
+        if (s == SGF_OK)
+            best.col_case3 = ms[5] < ms[4] ? 1 : 0;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (s == SGF_OK && (e = cudaStreamSynchronize(st)) != cudaSuccess)
@@ -1337,6 +1486,8 @@ sgf_status sgf_plan_share_ex(const sgf_plan *src, sgf_precision precision, sgf_p
     p->L = src->L;
     p->esize = src->esize;
     p->device = src->device;
+    if (!schedule_ok(p, p->sched))
+        p->sched.row_inv0 = 0;
     build_lists(p);
     p->spec = src->spec;
     p->spec->refs++;
@@ -1364,7 +1515,9 @@ sgf_status sgf_plan_stats_get(const sgf_plan *p, sgf_plan_stats *st)
     st->outputs = (int)p->outs.size();
     st->spectra_sets = (int)p->sets.size();
     // restrictions, row_fwd, col, row_inv1 (+ row_inv for the finer levels) or one row_inv for all
-    st->launches_per_solve = (p->L - 1) + 3 + (p->L > 1 && p->sched.row_inv0 != 1 ? 1 : 0);
+    st->launches_per_solve = (p->L - 1) + 3 + (p->L > 1 && p->sched.row_inv0 != 1 ? 1 : 0) +
+                             (!p->groups.empty() && p->sched.col_case3 == 0 ? 1 : 0) +  // + k_col_g
+                             (p->sums.empty() ? 0 : 1);                                  // + k_col_sum
     st->workspace_bytes = p->workspace_bytes;
     st->spectra_bytes = p->spec ? p->spec->bytes : 0;
     st->algorithmic_bytes = p->algorithmic_bytes;
@@ -1508,8 +1661,12 @@ sgf_status sgf_plan_schedule_set(sgf_plan *p, const sgf_schedule *in)
 {
     if (!p || !in)
         return fail(SGF_EINVAL, "NULL argument");
-    if ((in->col_pass != 0 && in->col_pass != 1) || (in->row_inv0 != 0 && in->row_inv0 != 1))
-        return fail(SGF_EINVAL, "schedule choices are 0 or 1 (col_pass %d, row_inv0 %d)", in->col_pass, in->row_inv0);
+    if ((in->col_pass != 0 && in->col_pass != 1) || (in->row_inv0 != 0 && in->row_inv0 != 1) ||
+        (in->col_case3 != 0 && in->col_case3 != 1))
+        return fail(SGF_EINVAL, "schedule choices are 0 or 1 (col_pass %d, row_inv0 %d, col_case3 %d)", in->col_pass,
+                    in->row_inv0, in->col_case3);
+    if (!schedule_ok(p, *in))
+        return fail(SGF_EUNSUPPORTED, "row_inv0 = 1 is not available for SGF_BF16X plans of n = %d", SGF_MAX_N);
     p->sched = *in;
     return SGF_OK;
 }
@@ -1521,7 +1678,7 @@ sgf_status sgf_plan_autotune(sgf_plan *p, int32_t reps, void *stream, sgf_schedu
     if (reps < 1 || reps > 1000)
         return fail(SGF_EINVAL, "reps = %d outside [1, 1000]", reps);
     DeviceGuard g(p->device);
-    double t[4];
+    double t[6];
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     sgf_status s = p->prec == SGF_FP64 ? autotune_impl<double>(p, reps, st, t) : autotune_impl<float>(p, reps, st, t);
     if (s != SGF_OK)
@@ -1529,7 +1686,7 @@ sgf_status sgf_plan_autotune(sgf_plan *p, int32_t reps, void *stream, sgf_schedu
     if (chosen)
         *chosen = p->sched;
     if (ms)
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < 6; ++k)
             ms[k] = t[k];
     return SGF_OK;
 }

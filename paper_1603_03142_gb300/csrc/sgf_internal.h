@@ -90,6 +90,27 @@ struct RowContrib {
     int pad;
 };
 
+// A group of Case-3 phase outputs (Eq. eqnbnmn) of one (coarser source, target)
+// pair: outputs out_begin .. out_begin + out_count - 1, each with one input on the
+// same source slab (all three fields) and its own phase spectra.
+struct ColGroup {
+    int out_begin, out_count;
+};
+
+// One k_col work item: output `out` over inputs in_begin .. in_begin + in_count - 1
+// (indices into the input list).  slot >= 0: one chunk of a long input list; its
+// spectral accumulators go to partial slot `slot` (summed in order by k_col_sum)
+// instead of being transformed back.
+struct ColWork {
+    int out, in_begin, in_count, slot;
+};
+
+// An output whose inputs were split into chunks: partial slots slot_begin ..
+// slot_begin + slot_count - 1, summed in this order, then transformed back.
+struct ColSum {
+    int out, slot_begin, slot_count, pad;
+};
+
 struct FwdItem {
     int slab;
     int row_pair;
@@ -118,6 +139,10 @@ struct SolveArgs {
     const RowContrib *contribs;
     int contrib_begin[kMaxLevels + 1];
     int level_base;             // first target level of a k_row_inv launch without a batch view
+    const ColWork *col_list;    // work items of the k_col launch
+    const ColGroup *groups;     // Case-3 output groups of the k_col_g launch
+    const ColSum *sums;         // chunked outputs of the k_col_sum launch
+    C *partial;                 // partial accumulators [slot][parity][comp][kx 0..N][N]
 };
 
 // Twiddle area of a solve (complex entries, precision of the solve):
@@ -167,7 +192,9 @@ enum : int {
     PASS_COL_M = 4,
     PASS_PREPARE = 5,
     PASS_ROW_INV1 = 6,
-    PASS_COL_MD = 7
+    PASS_COL_MD = 7,
+    PASS_COL_G = 8,
+    PASS_COL_SUM = 9
 };
 // Batch mode of the transform passes: a block's nest and its local work index
 // come from a per-launch map (one int2 per block row), and that nest's

@@ -17,6 +17,10 @@
 //  k_col       : per (column, parity half): forward column transforms of all
 //                inputs and fields, spectral multiply-accumulate in registers
 //                (the sums of products of Sec. 2.2), inverse transforms.
+//  k_col_g     : the Case-3 phase outputs of one (coarser source, target)
+//                pair together: source fields transformed once per column.
+//  k_col_sum   : outputs with long input lists, split into chunks of k_col work
+//                items: chunk accumulators summed in order, transformed back.
 //  k_row_inv   : per row pair of a target level: Hermitian extension, inverse
 //                row transforms of every contributing output, Case-3 phase
 //                interleave, covered cells zeroed, Fx/Fy stored.
@@ -107,7 +111,7 @@ struct KShape {
 // memory: all of them, except where the kernel's own staging leaves no room at
 // N = 4096 (k_row_fwd keeps two; k_row_inv keeps one and is never launched
 // there: the host refuses SGF_BF16X nests of N = 4096 with more than one level).
-enum : int { KK_ROW_FWD, KK_COL, KK_ROW_INV, KK_ROW_INV1, KK_ROW_FWD_M, KK_COL_M, KK_COL_MD };
+enum : int { KK_ROW_FWD, KK_COL, KK_ROW_INV, KK_ROW_INV1, KK_ROW_FWD_M, KK_COL_M, KK_COL_MD, KK_COL_G, KK_COL_SUM };
 __host__ __device__ constexpr int tc_round(int logn, int tiles, int kind)
 {
     return logn < 12 ? tiles : kind == KK_ROW_FWD ? (tiles < 2 ? tiles : 2) : kind == KK_ROW_INV ? 1 : tiles;
@@ -244,16 +248,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
     cg::cluster_group cluster = cg::this_cluster();
     const int b = (int)cluster.block_rank();  // parity half
     const int kx = blockIdx.x >> 1;
-    const ColOutput o = a.outs[wm.y];
+    const ColWork w = a.col_list[wm.y];
+    const ColOutput o = a.outs[w.out];
     const int t = threadIdx.x;
     const bool active = t < Q;
     const int j = active ? t : 0;
-    const int nitems = 3 * o.in_count;
+    const int nitems = 3 * w.in_count;
     const TwLayout tl = tw_layout(F16<LOGN>::twlen, N);
 
     auto issue = [&](int k) {
         unsigned char *st = stage_base + (size_t)(k & 1) * stage_bytes;
-        const ColInput ci = a.ins[o.in_begin + k / 3];
+        const ColInput ci = a.ins[w.in_begin + k / 3];
         const FwdSlab sl = a.slabs[ci.slab];
         const int f = k % 3;
         cp_block(st, a.fwd + sl.off + ((size_t)f * (N + 1) + kx) * sl.rows, (size_t)sl.rows * sizeof(C));
@@ -283,7 +288,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
         const unsigned char *st = stage_base + (size_t)(k & 1) * stage_bytes;
         const C *col = reinterpret_cast<const C *>(st);
         const T *spx = reinterpret_cast<const T *>(st + (size_t)N * sizeof(C));
-        const ColInput ci = a.ins[o.in_begin + k / 3];
+        const ColInput ci = a.ins[w.in_begin + k / 3];
         const int rows = a.slabs[ci.slab].rows;
         const int f = k % 3;
         C v[1][16];
@@ -341,6 +346,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
         cp_commit();
     }
     cp_wait<0>();
+    if (w.slot >= 0) {  // one chunk of a long input list: hand the accumulators to k_col_sum
+        if (active) {
+#pragma unroll
+            for (int comp = 0; comp < 2; ++comp) {
+                C *dst = a.partial + ((((size_t)w.slot * 2 + b) * 2 + comp) * (N + 1) + kx) * N;
+#pragma unroll
+                for (int u = 0; u < 16; ++u)
+                    dst[j + u * Q] = acc[comp][u];
+            }
+        }
+        if constexpr (TC)
+            tc_end(tcx, TCT);
+        return;  // both CTAs of the cluster take this branch (w is per cluster)
+    }
     // inverse column transforms of Fx^ and Fy^ together; y[n] = even[n] + W_P^{-n} odd[n]
     fft_ct<C, true, LOGN, 2, TC>(acc, sbuf, SPC, j, active, tw, &tcx);
     C *fold = sbuf;  // 2N complex over sbuf and the stages
@@ -353,6 +372,208 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
             const C w = twist(tw, tl, j, u);
             dst[n] = hmulc(acc[0][u], w);
             dst[N + n] = hmulc(acc[1][u], w);
+        }
+    }
+    cluster.sync();
+    if (b == 0 && active) {
+        C *dst = a.bwd + o.off;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int n = j + u * Q;
+            if (n < o.rows) {
+                dst[bwd_index(N, o.rows, 0, kx, n)] = hadd(acc[0][u], fold[n]);
+                dst[bwd_index(N, o.rows, 1, kx, n)] = hadd(acc[1][u], fold[N + n]);
+            }
+        }
+    }
+    if constexpr (TC)
+        tc_end(tcx, TCT);
+}
+
+// ------------------------------------------------------------------- col_g
+// Column pass of a group of Case-3 phase outputs (Sec. 2.2, Eq. eqnbnmn): the
+// m^2 outputs of one (coarser source, target) pair convolve the same source
+// level with different phase kernels.  One 2-CTA cluster per (column, group):
+// the three fields of the source column are transformed once (this parity
+// half) and kept in shared memory; then, per output, the spectral
+// multiply-accumulate with that phase's spectra and the two inverse transforms,
+// one after the other, each folded through distributed shared memory.
+// Shared memory: twiddle area | sbuf[SPC] (exchanges, then the fold) | fld[3][N].
+template <typename T, int LOGN, bool BATCH, bool TC>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_THREADS) k_col_g(SolveArgs<T> a0, BatchView<T> bv)
+{
+    const int2 wm = BATCH ? bv.map[blockIdx.y] : make_int2(0, (int)blockIdx.y);
+    const SolveArgs<T> &a = BATCH ? bv.args[wm.x] : a0;
+    using C = typename Cx<T>::C;
+    using K = KShape<LOGN>;
+    constexpr int N = K::N, Q = K::Q, P = 2 * N;
+    constexpr int SPC = col_sp<C>(N);
+    extern __shared__ __align__(16) unsigned char smem_tc[];
+    constexpr int TCT = tc_tiles(KShape<LOGN>::COL_THREADS, 1);
+    constexpr int TCR = tc_round(LOGN, TCT, KK_COL_G);
+    static_assert(!TC || sizeof(T) == 4, "tensor-core tiles take FP32 data");
+    unsigned char *smem_raw = smem_tc + (TC ? tc_smem_bytes(TCR) : 0);
+    TcCtx tcx;
+    if constexpr (TC)
+        tc_begin(tcx, smem_tc, TCT, TCR, a.status);
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *sbuf = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
+    C *fld = sbuf + SPC;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int b = (int)cluster.block_rank();
+    const int kx = blockIdx.x >> 1;
+    const int t = threadIdx.x;
+    const bool active = t < Q;
+    const int j = active ? t : 0;
+    const TwLayout tl = tw_layout(F16<LOGN>::twlen, N);
+    const ColGroup g = a.groups[wm.y];
+    const FwdSlab sl = a.slabs[a.ins[a.outs[g.out_begin].in_begin].slab];
+    cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
+    cp_commit();
+    cp_wait<0>();
+    __syncthreads();
+    C v[1][16];
+    for (int f = 0; f < 3; ++f) {
+        if (active) {
+            const C *col = a.fwd + sl.off + ((size_t)f * (N + 1) + kx) * sl.rows;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int n = j + u * Q;
+                C x = hmk<C>(T(0), T(0));
+                if (n < sl.rows) {
+                    x = col[n];
+                    if (b)
+                        x = hmul(x, twist(tw, tl, j, u));
+                }
+                v[0][u] = x;
+            }
+        }
+        fft_ct<C, false, LOGN, 1, TC>(v, sbuf, SPC, j, active, tw, &tcx);
+        if (active) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+                fld[f * N + u * Q + j] = v[0][u];  // read back by this thread only
+        }
+    }
+    const C *spec = reinterpret_cast<const C *>(a.spec);
+#pragma unroll 1
+    for (int q = 0; q < g.out_count; ++q) {
+        const ColOutput o = a.outs[g.out_begin + q];
+        const ColInput ci = a.ins[o.in_begin];
+        C acc[2][16];
+        if (active) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                acc[0][u] = hmk<C>(T(0), T(0));
+                acc[1][u] = hmk<C>(T(0), T(0));
+            }
+#pragma unroll 1
+            for (int f = 0; f < 3; ++f) {
+                const C *sx = spec + ci.spec_off + ((size_t)f * (N + 1) + kx) * P;
+                const C *sy = spec + ci.spec_off + ((size_t)(3 + f) * (N + 1) + kx) * P;
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int ky = 2 * (j + u * Q) + b;
+                    const C x = fld[f * N + u * Q + j];
+                    acc[0][u] = hadd(acc[0][u], hmul(__ldg(sx + ky), x));
+                    acc[1][u] = hadd(acc[1][u], hmul(__ldg(sy + ky), x));
+                }
+            }
+        }
+#pragma unroll
+        for (int comp = 0; comp < 2; ++comp) {
+            // y[n] = even[n] + W_P^{-n} odd[n]
+            fft_ct<C, true, LOGN, 1, TC>(&acc[comp], sbuf, SPC, j, active, tw, &tcx);
+            cluster.sync();  // both CTAs are done with their exchange buffers
+            if (b == 1 && active) {
+                C *dst = cluster.map_shared_rank(sbuf, 0);
+#pragma unroll
+                for (int u = 0; u < 16; ++u)
+                    dst[j + u * Q] = hmulc(acc[comp][u], twist(tw, tl, j, u));
+            }
+            cluster.sync();
+            if (b == 0 && active) {
+                C *out = a.bwd + o.off;
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int n = j + u * Q;
+                    if (n < o.rows)
+                        out[bwd_index(N, o.rows, comp, kx, n)] = hadd(acc[comp][u], sbuf[n]);
+                }
+            }
+        }
+    }
+    if constexpr (TC)
+        tc_end(tcx, TCT);
+}
+
+// ----------------------------------------------------------------- col_sum
+// Second half of the column pass of an output whose input list was split into
+// chunks (k_col work items with a partial slot): the chunks' spectral
+// accumulators are summed in slot order, then transformed back and folded as
+// in k_col.  Shared memory: twiddle area | two exchange buffers (dual inverse),
+// reused for the fold.
+template <typename T, int LOGN, bool BATCH, bool TC>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_THREADS) k_col_sum(SolveArgs<T> a0, BatchView<T> bv)
+{
+    const int2 wm = BATCH ? bv.map[blockIdx.y] : make_int2(0, (int)blockIdx.y);
+    const SolveArgs<T> &a = BATCH ? bv.args[wm.x] : a0;
+    using C = typename Cx<T>::C;
+    using K = KShape<LOGN>;
+    constexpr int N = K::N, Q = K::Q;
+    constexpr int SPC = col_sp<C>(N);
+    extern __shared__ __align__(16) unsigned char smem_tc[];
+    constexpr int TCT = tc_tiles(KShape<LOGN>::COL_THREADS, 2);
+    constexpr int TCR = tc_round(LOGN, TCT, KK_COL_SUM);
+    static_assert(!TC || sizeof(T) == 4, "tensor-core tiles take FP32 data");
+    unsigned char *smem_raw = smem_tc + (TC ? tc_smem_bytes(TCR) : 0);
+    TcCtx tcx;
+    if constexpr (TC)
+        tc_begin(tcx, smem_tc, TCT, TCR, a.status);
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *sbuf = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
+    cg::cluster_group cluster = cg::this_cluster();
+    const int b = (int)cluster.block_rank();
+    const int kx = blockIdx.x >> 1;
+    const int t = threadIdx.x;
+    const bool active = t < Q;
+    const int j = active ? t : 0;
+    const TwLayout tl = tw_layout(F16<LOGN>::twlen, N);
+    const ColSum sm = a.sums[wm.y];
+    const ColOutput o = a.outs[sm.out];
+    cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
+    cp_commit();
+    C acc[2][16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        acc[0][u] = hmk<C>(T(0), T(0));
+        acc[1][u] = hmk<C>(T(0), T(0));
+    }
+    if (active) {
+#pragma unroll 1
+        for (int k = 0; k < sm.slot_count; ++k) {
+#pragma unroll
+            for (int comp = 0; comp < 2; ++comp) {
+                const C *src = a.partial + ((((size_t)(sm.slot_begin + k) * 2 + b) * 2 + comp) * (N + 1) + kx) * N;
+#pragma unroll
+                for (int u = 0; u < 16; ++u)
+                    acc[comp][u] = hadd(acc[comp][u], src[j + u * Q]);
+            }
+        }
+    }
+    cp_wait<0>();
+    __syncthreads();
+    fft_ct<C, true, LOGN, 2, TC>(acc, sbuf, SPC, j, active, tw, &tcx);
+    C *fold = sbuf;
+    cluster.sync();
+    if (b == 1 && active) {
+        C *dst = cluster.map_shared_rank(fold, 0);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int n = j + u * Q;
+            const C tw_n = twist(tw, tl, j, u);
+            dst[n] = hmulc(acc[0][u], tw_n);
+            dst[N + n] = hmulc(acc[1][u], tw_n);
         }
     }
     cluster.sync();
@@ -523,7 +744,10 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, sizeof(T) == 4 && !
     if constexpr (TC)
         tc_begin(tcx, smem_tc, TCT, TCR, a.status);
     C *tw = reinterpret_cast<C *>(smem_raw);
-    C *stg = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));  // [kx][2], then the exchange buffer
+    // stage: bin kx's two rows (a pair of C) at [kx & 1][kx >> 1], so the threads
+    // of a parity half read consecutive pairs; then the exchange buffer
+    C *stg = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
+    constexpr int HALF = N / 2 + 1;
     C *sbuf = stg;
     const int tl = BATCH ? wm.y : a.level_base;
     const int comp = (int)blockIdx.x >= N / 2 ? 1 : 0;
@@ -540,7 +764,8 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, sizeof(T) == 4 && !
         constexpr int PG = 2 * (int)sizeof(C) / 16;  // 16-byte pieces per bin (rows j0, j1 adjacent)
         for (int q = t; q < (N + 1) * PG; q += K::ROW_THREADS) {
             const int kx = q / PG, piece = q - kx * PG;
-            cp16(stg + 2 * kx + piece * (16 / (int)sizeof(C)), base + (size_t)kx * o.rows + piece * (16 / (int)sizeof(C)));
+            C *dst = stg + 2 * ((kx & 1) * HALF + (kx >> 1));
+            cp16(dst + piece * (16 / (int)sizeof(C)), base + (size_t)kx * o.rows + piece * (16 / (int)sizeof(C)));
         }
     }
     cp_commit();
@@ -551,8 +776,17 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, sizeof(T) == 4 && !
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
             const int kx = 2 * (j + u * Q) + b;
-            const int k2 = kx <= N ? kx : P - kx;
-            const C A = stg[2 * k2], B = stg[2 * k2 + 1];
+            const int k2 = kx <= N ? kx : P - kx;  // same parity as kx
+            const C *pr = stg + 2 * (b * HALF + (k2 >> 1));
+            C A, B;
+            if constexpr (sizeof(T) == 4) {  // one 16-byte load (pairs start on 16-byte boundaries)
+                const float4 ab = *reinterpret_cast<const float4 *>(pr);
+                A = hmk<C>(ab.x, ab.y);
+                B = hmk<C>(ab.z, ab.w);
+            } else {
+                A = pr[0];
+                B = pr[1];
+            }
             v[0][u] = kx <= N ? hmk<C>(A.x - B.y, A.y + B.x) : hmk<C>(A.x + B.y, B.x - A.y);
         }
     }
@@ -893,7 +1127,7 @@ struct KSmem {
     }
     static size_t row_inv1()
     {
-        const size_t stage = (2 * (size_t)(N + 1) * sizeof(C) + 15) & ~(size_t)15;
+        const size_t stage = 2 * (size_t)(N / 2 + 1) * 2 * sizeof(C);  // [parity][N/2 + 1] pairs
         const size_t xbuf = 2 * (size_t)KShape<LOGN>::SP_ROW * sizeof(C);
         return rtc(KK_ROW_INV1) + tw() + (stage > xbuf ? stage : xbuf);
     }
@@ -905,6 +1139,16 @@ struct KSmem {
     {
         return tc(KShape<LOGN>::COL_THREADS, 1, KK_COL_M) + tw() + (size_t)col_sp<C>(N) * sizeof(C) +
                (size_t)N * sizeof(C);
+    }
+    static size_t col_g()
+    {
+        return tc(KShape<LOGN>::COL_THREADS, 1, KK_COL_G) + tw() + (size_t)col_sp<C>(N) * sizeof(C) +
+               3 * (size_t)N * sizeof(C);
+    }
+    static size_t col_sum()
+    {
+        size_t body = 2 * (size_t)col_sp<C>(N) * sizeof(C);  // two exchange buffers; the 2N fold fits
+        return ctc(KK_COL_SUM) + tw() + body;
     }
     static size_t col_md()
     {
@@ -941,7 +1185,7 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
 {
     using K = KShape<LOGN>;
     using S = KSmem<T, LOGN, TC>;
-    static std::atomic<unsigned long long> d[14];
+    static std::atomic<unsigned long long> d[18];
     const BatchView<T> none{nullptr, nullptr};
     const bool batch = bv != nullptr;
     const BatchView<T> v = batch ? *bv : none;
@@ -970,7 +1214,11 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
             (e = ensure_smem(k_row_inv1<T, LOGN, false, TC>, S::row_inv1(), d[10])) != cudaSuccess ||
             (e = ensure_smem(k_row_inv1<T, LOGN, true, TC>, S::row_inv1(), d[11])) != cudaSuccess ||
             (e = ensure_smem(k_col_md<T, LOGN, false, TC>, S::col_md(), d[12])) != cudaSuccess ||
-            (e = ensure_smem(k_col_md<T, LOGN, true, TC>, S::col_md(), d[13])) != cudaSuccess)
+            (e = ensure_smem(k_col_md<T, LOGN, true, TC>, S::col_md(), d[13])) != cudaSuccess ||
+            (e = ensure_smem(k_col_g<T, LOGN, false, TC>, S::col_g(), d[14])) != cudaSuccess ||
+            (e = ensure_smem(k_col_g<T, LOGN, true, TC>, S::col_g(), d[15])) != cudaSuccess ||
+            (e = ensure_smem(k_col_sum<T, LOGN, false, TC>, S::col_sum(), d[16])) != cudaSuccess ||
+            (e = ensure_smem(k_col_sum<T, LOGN, true, TC>, S::col_sum(), d[17])) != cudaSuccess)
             return e;
         return cudaSuccess;
     }
@@ -1003,6 +1251,16 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
     case PASS_COL_M: {
         SGF_LAUNCH((k_col_m<T, LOGN, false, TC>), (k_col_m<T, LOGN, true, TC>), 8, S::col_m(),
                    dim3(2 * (K::N + 1), batch ? count : 1), K::COL_THREADS)
+        break;
+    }
+    case PASS_COL_SUM: {
+        SGF_LAUNCH((k_col_sum<T, LOGN, false, TC>), (k_col_sum<T, LOGN, true, TC>), 16, S::col_sum(),
+                   dim3(2 * (K::N + 1), count), K::COL_THREADS)
+        break;
+    }
+    case PASS_COL_G: {
+        SGF_LAUNCH((k_col_g<T, LOGN, false, TC>), (k_col_g<T, LOGN, true, TC>), 14, S::col_g(),
+                   dim3(2 * (K::N + 1), count), K::COL_THREADS)
         break;
     }
     case PASS_COL_MD: {

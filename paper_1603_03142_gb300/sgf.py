@@ -83,7 +83,7 @@ class ServerStats(ctypes.Structure):
 
 
 class Schedule(ctypes.Structure):
-    _fields_ = [("col_pass", ctypes.c_int32), ("row_inv0", ctypes.c_int32)]
+    _fields_ = [("col_pass", ctypes.c_int32), ("row_inv0", ctypes.c_int32), ("col_case3", ctypes.c_int32)]
 
 
 SERVER_SIMULATE = 0x1
@@ -238,20 +238,21 @@ class Plan:
     def schedule(self) -> dict:
         sc = Schedule()
         _check(_lib.sgf_plan_schedule_get(self._h, ctypes.byref(sc)), "sgf_plan_schedule_get")
-        return {"col_pass": sc.col_pass, "row_inv0": sc.row_inv0}
+        return {"col_pass": sc.col_pass, "row_inv0": sc.row_inv0, "col_case3": sc.col_case3}
 
-    def set_schedule(self, col_pass: int = 0, row_inv0: int = 0):
-        sc = Schedule(int(col_pass), int(row_inv0))
+    def set_schedule(self, col_pass: int = 0, row_inv0: int = 0, col_case3: int = 0):
+        sc = Schedule(int(col_pass), int(row_inv0), int(col_case3))
         _check(_lib.sgf_plan_schedule_set(self._h, ctypes.byref(sc)), "sgf_plan_schedule_set")
 
     def autotune(self, reps: int = 5, stream=None) -> dict:
         """sgf_plan_autotune: time every schedule candidate, keep the fastest."""
         sc = Schedule()
-        ms = (ctypes.c_double * 4)()
+        ms = (ctypes.c_double * 6)()
         _check(_lib.sgf_plan_autotune(self._h, int(reps), ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(sc),
                                       ms), "sgf_plan_autotune")
-        return {"chosen": {"col_pass": sc.col_pass, "row_inv0": sc.row_inv0},
-                "ms": {"col_pass0": ms[0], "col_pass1": ms[1], "row_inv0_0": ms[2], "row_inv0_1": ms[3]}}
+        return {"chosen": {"col_pass": sc.col_pass, "row_inv0": sc.row_inv0, "col_case3": sc.col_case3},
+                "ms": {"col_pass0": ms[0], "col_pass1": ms[1], "row_inv0_0": ms[2], "row_inv0_1": ms[3],
+                       "col_case3_0": ms[4], "col_case3_1": ms[5]}}
 
     def profile(self, enable: bool = True):
         _check(_lib.sgf_plan_profile(self._h, 1 if enable else 0), "sgf_plan_profile")

@@ -1,7 +1,10 @@
 """Tile schedules and the autotuner (sgf_plan_schedule_*, sgf_plan_autotune).
 
-Every schedule performs the same arithmetic in the same order, so the forces
-must agree bit for bit across schedules; the autotuner must pick one of the
+Every schedule evaluates the same expressions in the same order, so the forces
+agree across schedules to rounding: the compiler may contract a multiply and an
+add into one FMA in one kernel and not in another, which moves the last bits
+(bound here: 64 units of roundoff of the field's largest value, far below the
+method's parity bounds); the autotuner must pick one of the
 candidates, report a time for each, and record its choice for later plans of
 the same key (in the process and in the SGF_AUTOTUNE_CACHE table file).
 """
@@ -34,7 +37,7 @@ def _zero_rim_sigma(n, seed):
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16x", "fp64"])
 @pytest.mark.parametrize("n", [64, 512, 2048])
-def test_schedules_agree_bitwise_zero_rim(lib, prec, n):
+def test_schedules_agree_zero_rim(lib, prec, n):
     nest = W.Nest(n=n)
     sigma = _zero_rim_sigma(n, n)
     plan = lib.Plan(nest, prec, zero_rim=True)
@@ -42,25 +45,45 @@ def test_schedules_agree_bitwise_zero_rim(lib, prec, n):
     for col in (0, 1):
         for inv in (0, 1):
             plan.set_schedule(col, inv)
-            assert plan.schedule() == {"col_pass": col, "row_inv0": inv}
+            assert plan.schedule() == {"col_pass": col, "row_inv0": inv, "col_case3": 0}
             outs.append(run_gpu(plan, sigma))
             plan.check()
+    eps = np.finfo(np.float64 if prec == "fp64" else np.float32).eps
+    scale = max(np.abs(outs[0][0][0]).max(), np.abs(outs[0][1][0]).max())
     for gx, gy in outs[1:]:
-        assert np.array_equal(gx[0], outs[0][0][0]) and np.array_equal(gy[0], outs[0][1][0])
+        d = max(np.abs(gx[0] - outs[0][0][0]).max(), np.abs(gy[0] - outs[0][1][0]).max())
+        assert d <= 64 * eps * scale, d / scale
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_row_inv_schedules_agree_on_nests(lib, prec):
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "bf16x"])
+def test_nest_schedules_agree(lib, prec):
+    """row_inv0 and col_case3 (grouped Case-3 outputs) on a 3-level nest."""
     rng = np.random.Generator(np.random.PCG64(8))
     nest, sigma = W.random_nest_problem(rng, 128, 3)
     plan = lib.Plan(nest, prec)
-    plan.set_schedule(0, 0)
-    a = run_gpu(plan, sigma)
-    plan.set_schedule(0, 1)
-    b = run_gpu(plan, sigma)
-    assert plan.stats()["launches_per_solve"] == 2 + 3
-    for l in range(3):
-        assert np.array_equal(a[0][l], b[0][l]) and np.array_equal(a[1][l], b[1][l])
+    res = {}
+    for inv in (0, 1):
+        for c3 in (0, 1):
+            plan.set_schedule(0, inv, c3)
+            res[(inv, c3)] = run_gpu(plan, sigma)
+            # restrictions 2, row_fwd, col (+ k_col_g), row_inv1 + row_inv or one row_inv
+            assert plan.stats()["launches_per_solve"] == 2 + 3 + (1 - inv) + (1 - c3)
+    eps = np.finfo(np.float64 if prec == "fp64" else np.float32).eps
+    a = res[(0, 0)]
+    for key, b in res.items():
+        for l in range(3):
+            scale = max(np.abs(a[0][l]).max(), np.abs(a[1][l]).max())
+            d = max(np.abs(a[0][l] - b[0][l]).max(), np.abs(a[1][l] - b[1][l]).max())
+            assert d <= 64 * eps * scale, (key, l, d / scale)
+
+
+def test_bf16x_4096_refuses_nest_inverse_schedule(lib):
+    plan = lib.Plan(W.Nest(n=4096), "bf16x", zero_rim=True)
+    with pytest.raises(lib.SgfError) as ei:
+        plan.set_schedule(0, 1)
+    assert ei.value.status == lib.SGF_EUNSUPPORTED
+    r = plan.autotune(reps=1)
+    assert r["ms"]["row_inv0_1"] < 0 and r["chosen"]["row_inv0"] == 0
 
 
 def test_batch_follows_schedule(lib):
@@ -80,7 +103,8 @@ def test_batch_follows_schedule(lib):
         plans[k].set_schedule(0, 0)
         gx, gy = run_gpu(plans[k], s)
         for l in range(nest.levels):
-            assert np.array_equal(fx[k][l].double().cpu().numpy(), gx[l])
+            g = fx[k][l].double().cpu().numpy()
+            assert np.abs(g - gx[l]).max() <= 64 * np.finfo(np.float32).eps * np.abs(gx[l]).max()
 
 
 def test_autotune_picks_and_records(lib, tmp_path):
