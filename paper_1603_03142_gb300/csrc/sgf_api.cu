@@ -50,6 +50,35 @@ sgf_status cuda_fail(cudaError_t e, const char *what)
                 cudaGetErrorName(e), cudaGetErrorString(e));
 }
 
+// Host-to-device upload (pageable source) and memset that have reached the
+// device when the call returns.  A plain cudaMemcpy from pageable memory may
+// return before its DMA lands, and it is ordered only on the legacy default
+// stream: a kernel the caller then launches on a non-blocking stream (a server
+// slot, a private generation stream) could read the old contents.
+cudaError_t upload_landed(void *dst, const void *src, size_t bytes)
+{
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess)
+        return e;
+    e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    return e != cudaSuccess ? e : e2;
+}
+
+cudaError_t memset_landed(void *dst, int value, size_t bytes)
+{
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess)
+        return e;
+    e = cudaMemsetAsync(dst, value, bytes, s);
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    return e != cudaSuccess ? e : e2;
+}
+
 }  // namespace sgf
 
 namespace {
@@ -508,7 +537,7 @@ sgf_status plan_alloc_owned(sgf_plan *p)
     cudaError_t e;
     if ((e = cudaMalloc(&p->d_lists, blob.size())) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc(work lists)");
-    if ((e = cudaMemcpy(p->d_lists, blob.data(), blob.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+    if ((e = upload_landed(p->d_lists, blob.data(), blob.size())) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpy(work lists)");
     auto base = static_cast<unsigned char *>(p->d_lists);
     p->d_slabs = reinterpret_cast<const FwdSlab *>(base + o_slabs);
@@ -533,7 +562,7 @@ sgf_status plan_alloc_owned(sgf_plan *p)
     }
     if ((e = cudaMalloc(&p->d_status, 16)) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc(status word)");
-    if ((e = cudaMemset(p->d_status, 0, 16)) != cudaSuccess)
+    if ((e = memset_landed(p->d_status, 0, 16)) != cudaSuccess)
         return cuda_fail(e, "cudaMemset(status word)");
     if ((e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming)) != cudaSuccess)
         return cuda_fail(e, "cudaEventCreate(solve completion)");
@@ -618,7 +647,7 @@ sgf_status build_spectra(sgf_plan *p)
     sp->tw_entries = tl.entries;
     if ((e = cudaMalloc(&sp->tw, tl.entries * sizeof(C))) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc(twiddles)");
-    if ((e = cudaMemcpy(sp->tw, twT.data(), tl.entries * sizeof(C), cudaMemcpyHostToDevice)) != cudaSuccess)
+    if ((e = upload_landed(sp->tw, twT.data(), tl.entries * sizeof(C))) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpy(twiddles)");
     sp->bytes = spectra_total(p);
     if ((e = cudaMalloc(&sp->dev, sp->bytes)) != cudaSuccess)
@@ -628,7 +657,7 @@ sgf_status build_spectra(sgf_plan *p)
     double2 *d_half = nullptr;
     sgf_status st = SGF_OK;
     if ((e = cudaMalloc(&d_tw64, P * sizeof(double2))) != cudaSuccess ||
-        (e = cudaMemcpy(d_tw64, tw64.data(), P * sizeof(double2), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = upload_landed(d_tw64, tw64.data(), P * sizeof(double2))) != cudaSuccess ||
         (e = cudaMalloc(&d_tables, 6 * (size_t)P * P * sizeof(double))) != cudaSuccess ||
         (e = cudaMalloc(&d_half, 6 * (size_t)(N + 1) * P * sizeof(double2))) != cudaSuccess) {
         st = cuda_fail(e, "cudaMalloc(table generation workspace)");
@@ -1154,7 +1183,7 @@ sgf_status batch_build(sgf_batch *bt)
     if ((e = cudaMalloc(&bt->d_maps, maps.size() * sizeof(int2) + 16)) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc(batch work maps)");
     if (!maps.empty() &&
-        (e = cudaMemcpy(bt->d_maps, maps.data(), maps.size() * sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess)
+        (e = upload_landed(bt->d_maps, maps.data(), maps.size() * sizeof(int2))) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpy(batch work maps)");
     if ((e = cudaMalloc(&bt->d_args, bt->args_bytes)) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc(batch arguments)");
@@ -1608,7 +1637,7 @@ sgf_status sgf_plan_check(sgf_plan *p)
     int word = 0;
     if ((e = cudaMemcpy(&word, p->d_status, sizeof word, cudaMemcpyDeviceToHost)) != cudaSuccess)
         return cuda_fail(e, "reading the plan status word");
-    if (word != 0 && (e = cudaMemset(p->d_status, 0, sizeof word)) != cudaSuccess)
+    if (word != 0 && (e = memset_landed(p->d_status, 0, sizeof word)) != cudaSuccess)
         return cuda_fail(e, "clearing the plan status word");
     if (word & STATUS_TC_TIMEOUT)
         return fail(SGF_ETIMEOUT, "SGF_BF16X: a wait for tensor-core completion timed out; the output is invalid");

@@ -38,9 +38,9 @@ def test_batch_equals_single_solves(lib, graph):
     probs.append((zr, [zs]))
     batch = lib.Batch(plans, graph=graph)
     info = batch.info()
-    # per group: row_fwd, col (+ col_g for Case-3 groups), row_inv1 (+ row_inv for the finer
+    # per group: row_fwd, col (+ col_g for Case-3 groups, col_sum for chunked outputs), row_inv1 (+ row_inv for the finer
     # levels); one restriction per depth
-    assert info["groups"] >= 4 and info["launches_per_solve"] <= 5 * info["groups"] + 3
+    assert info["groups"] >= 4 and info["launches_per_solve"] <= 6 * info["groups"] + 3
     for call in range(3):
         sig = [[torch.from_numpy(a * (1.0 + 0.1 * call)).float().cuda() for a in s] for _, s in probs]
         fx = [[torch.empty_like(a) for a in s] for s in sig]
