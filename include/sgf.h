@@ -317,6 +317,11 @@ typedef struct sgf_server sgf_server;
  * admission.  For testing the admission logic without a GPU; results are not
  * written. */
 #define SGF_SERVER_SIMULATE 0x1u
+/* SGF_SERVER_NO_AUTOTUNE: keep every plan's default (or recorded) schedule.
+ * Otherwise the first slot of every slot key (shape and precision) runs
+ * sgf_plan_autotune on its own stream when it is created, and later slots of
+ * the key take the tuned schedule. */
+#define SGF_SERVER_NO_AUTOTUNE 0x2u
 
 typedef struct {
     size_t hbm_budget;     /* device bytes the server may hold; 0 = 90% of the free memory at creation */

@@ -114,7 +114,10 @@ struct KShape {
 enum : int { KK_ROW_FWD, KK_COL, KK_ROW_INV, KK_ROW_INV1, KK_ROW_FWD_M, KK_COL_M, KK_COL_MD, KK_COL_G, KK_COL_SUM };
 __host__ __device__ constexpr int tc_round(int logn, int tiles, int kind)
 {
-    return logn < 12 ? tiles : kind == KK_ROW_FWD ? (tiles < 2 ? tiles : 2) : kind == KK_ROW_INV ? 1 : tiles;
+    return logn < 12                                 ? tiles
+           : kind == KK_ROW_FWD                      ? (tiles < 2 ? tiles : 2)
+           : kind == KK_ROW_INV || kind == KK_COL_G ? 1
+                                                     : tiles;
 }
 
 // ------------------------------------------------------------------ row_fwd
@@ -397,8 +400,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
 // the three fields of the source column are transformed once (this parity
 // half) and kept in shared memory; then, per output, the spectral
 // multiply-accumulate with that phase's spectra and the two inverse transforms,
-// one after the other, each folded through distributed shared memory.
-// Shared memory: twiddle area | sbuf[SPC] (exchanges, then the fold) | fld[3][N].
+// together (two sequences per thread), folded through distributed shared
+// memory.  Shared memory: twiddle area | sbuf[2 SPC] (the two exchange buffers,
+// then the 2N fold) | fld[3][N].
 template <typename T, int LOGN, bool BATCH, bool TC>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_THREADS) k_col_g(SolveArgs<T> a0, BatchView<T> bv)
 {
@@ -409,7 +413,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
     constexpr int N = K::N, Q = K::Q, P = 2 * N;
     constexpr int SPC = col_sp<C>(N);
     extern __shared__ __align__(16) unsigned char smem_tc[];
-    constexpr int TCT = tc_tiles(KShape<LOGN>::COL_THREADS, 1);
+    constexpr int TCT = tc_tiles(KShape<LOGN>::COL_THREADS, 2);
     constexpr int TCR = tc_round(LOGN, TCT, KK_COL_G);
     static_assert(!TC || sizeof(T) == 4, "tensor-core tiles take FP32 data");
     unsigned char *smem_raw = smem_tc + (TC ? tc_smem_bytes(TCR) : 0);
@@ -418,7 +422,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
         tc_begin(tcx, smem_tc, TCT, TCR, a.status);
     C *tw = reinterpret_cast<C *>(smem_raw);
     C *sbuf = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
-    C *fld = sbuf + SPC;
+    C *fld = sbuf + 2 * SPC;  // after the two exchange buffers of the dual inverse
     cg::cluster_group cluster = cg::this_cluster();
     const int b = (int)cluster.block_rank();
     const int kx = blockIdx.x >> 1;
@@ -480,25 +484,27 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
                 }
             }
         }
+        // both inverse transforms together; y[n] = even[n] + W_P^{-n} odd[n]
+        fft_ct<C, true, LOGN, 2, TC>(acc, sbuf, SPC, j, active, tw, &tcx);
+        cluster.sync();  // both CTAs are done with their exchange buffers
+        if (b == 1 && active) {
+            C *dst = cluster.map_shared_rank(sbuf, 0);
 #pragma unroll
-        for (int comp = 0; comp < 2; ++comp) {
-            // y[n] = even[n] + W_P^{-n} odd[n]
-            fft_ct<C, true, LOGN, 1, TC>(&acc[comp], sbuf, SPC, j, active, tw, &tcx);
-            cluster.sync();  // both CTAs are done with their exchange buffers
-            if (b == 1 && active) {
-                C *dst = cluster.map_shared_rank(sbuf, 0);
-#pragma unroll
-                for (int u = 0; u < 16; ++u)
-                    dst[j + u * Q] = hmulc(acc[comp][u], twist(tw, tl, j, u));
+            for (int u = 0; u < 16; ++u) {
+                const C w = twist(tw, tl, j, u);
+                dst[j + u * Q] = hmulc(acc[0][u], w);
+                dst[N + j + u * Q] = hmulc(acc[1][u], w);
             }
-            cluster.sync();
-            if (b == 0 && active) {
-                C *out = a.bwd + o.off;
+        }
+        cluster.sync();
+        if (b == 0 && active) {
+            C *out = a.bwd + o.off;
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int n = j + u * Q;
-                    if (n < o.rows)
-                        out[bwd_index(N, o.rows, comp, kx, n)] = hadd(acc[comp][u], sbuf[n]);
+            for (int u = 0; u < 16; ++u) {
+                const int n = j + u * Q;
+                if (n < o.rows) {
+                    out[bwd_index(N, o.rows, 0, kx, n)] = hadd(acc[0][u], sbuf[n]);
+                    out[bwd_index(N, o.rows, 1, kx, n)] = hadd(acc[1][u], sbuf[N + n]);
                 }
             }
         }
@@ -1142,7 +1148,7 @@ struct KSmem {
     }
     static size_t col_g()
     {
-        return tc(KShape<LOGN>::COL_THREADS, 1, KK_COL_G) + tw() + (size_t)col_sp<C>(N) * sizeof(C) +
+        return tc(KShape<LOGN>::COL_THREADS, 2, KK_COL_G) + tw() + 2 * (size_t)col_sp<C>(N) * sizeof(C) +
                3 * (size_t)N * sizeof(C);
     }
     static size_t col_sum()
@@ -1163,10 +1169,16 @@ struct KSmem {
     }
 };
 
-// Sets the dynamic shared-memory limit of a kernel once per device.
+// Sets the dynamic shared-memory limit of a kernel once per device.  A kernel
+// that needs more than an SM offers (k_row_inv with tensor-core tiles at
+// n = 4096, a configuration the host refuses) is left alone here; launching it
+// would fail with a launch error.
+constexpr size_t kMaxDynSmem = 232448;
 template <typename F>
 inline cudaError_t ensure_smem(F *kernel, size_t bytes, std::atomic<unsigned long long> &done)
 {
+    if (bytes > kMaxDynSmem)
+        return cudaSuccess;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess)

@@ -82,6 +82,7 @@ struct sgf_server {
     std::deque<Pending> queue;
     std::vector<Slot *> slots;  // index = slot id; destroyed slots leave nullptr
     std::map<std::string, Shape> shapes;
+    std::map<std::string, sgf_schedule> tuned;  // autotuned schedule per slot key
     std::deque<sgf_completion> out;
     size_t used = 0;
     uint64_t tick = 0;
@@ -190,7 +191,10 @@ sgf_status slot_create(sgf_server *sv, const Pending &p, Slot **out)
     const bool resident = it != sv->shapes.end();
     sgf_status rc = SGF_OK;
     if (!sv->sim) {
-        if (resident) {
+        cudaError_t e;
+        if ((e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) != cudaSuccess)
+            rc = cuda_fail(e, "cudaStreamCreate(slot)");
+        if (rc == SGF_OK && resident) {
             const sgf_plan *tmpl = nullptr;
             for (auto *o : sv->slots)
                 if (o && o->skey == p.skey) {
@@ -199,14 +203,24 @@ sgf_status slot_create(sgf_server *sv, const Pending &p, Slot **out)
                 }
             rc = tmpl ? sgf_plan_share_ex(tmpl, p.r.precision, &s->plan)
                       : fail(SGF_EINVAL, "resident shape without a slot");
-        } else {
+        } else if (rc == SGF_OK) {
             rc = sgf_plan_create_ex(&p.r.desc, p.r.precision, p.r.plan_flags, &s->plan);
         }
-        cudaError_t e;
+        // the kernel schedule of this slot key: tuned once per server (on the slot's own
+        // stream, while the other slots keep running), then reused
+        if (rc == SGF_OK && !(sv->cfg.flags & SGF_SERVER_NO_AUTOTUNE)) {
+            auto tt = sv->tuned.find(p.key);
+            if (tt != sv->tuned.end()) {
+                rc = sgf_plan_schedule_set(s->plan, &tt->second);
+            } else {
+                sgf_schedule sc{};
+                rc = sgf_plan_autotune(s->plan, 2, s->stream, &sc, nullptr);
+                if (rc == SGF_OK)
+                    sv->tuned[p.key] = sc;
+            }
+        }
         if (rc == SGF_OK && (e = cudaMalloc(&s->d_io, p.io)) != cudaSuccess)
             rc = cuda_fail(e, "cudaMalloc(request buffers)");
-        if (rc == SGF_OK && (e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) != cudaSuccess)
-            rc = cuda_fail(e, "cudaStreamCreate(slot)");
         if (rc == SGF_OK && (e = cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming)) != cudaSuccess)
             rc = cuda_fail(e, "cudaEventCreate(slot)");
         if (rc != SGF_OK) {
@@ -290,7 +304,7 @@ sgf_status sgf_server_create(const sgf_server_config *config, sgf_server **out)
     *out = nullptr;
     if (config->max_inflight < 1)
         return fail(SGF_EINVAL, "max_inflight = %d must be >= 1", config->max_inflight);
-    if (config->flags & ~SGF_SERVER_SIMULATE)
+    if (config->flags & ~(SGF_SERVER_SIMULATE | SGF_SERVER_NO_AUTOTUNE))
         return fail(SGF_EINVAL, "unknown server flags 0x%x", config->flags);
     const bool sim = (config->flags & SGF_SERVER_SIMULATE) != 0;
     if (sim && !(config->simulate_gbs > 0.0))

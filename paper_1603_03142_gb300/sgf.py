@@ -87,6 +87,7 @@ class Schedule(ctypes.Structure):
 
 
 SERVER_SIMULATE = 0x1
+SERVER_NO_AUTOTUNE = 0x2
 _vpp = ctypes.POINTER(ctypes.c_void_p)
 _szp = ctypes.POINTER(ctypes.c_size_t)
 _lib.sgf_plan_create.argtypes = [ctypes.POINTER(NestDesc), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
@@ -405,12 +406,12 @@ class Server:
     """
 
     def __init__(self, hbm_budget: int = 0, max_inflight: int = 4, simulate_gbs: Optional[float] = None,
-                 max_shape_bytes: int = 0):
+                 max_shape_bytes: int = 0, autotune: bool = True):
         cfg = ServerConfig()
         cfg.hbm_budget = int(hbm_budget)
         cfg.max_shape_bytes = int(max_shape_bytes)
         cfg.max_inflight = int(max_inflight)
-        cfg.flags = SERVER_SIMULATE if simulate_gbs is not None else 0
+        cfg.flags = (SERVER_SIMULATE if simulate_gbs is not None else 0) | (0 if autotune else SERVER_NO_AUTOTUNE)
         cfg.simulate_gbs = float(simulate_gbs or 0.0)
         h = ctypes.c_void_p()
         _check(_lib.sgf_server_create(ctypes.byref(cfg), ctypes.byref(h)), "sgf_server_create")
