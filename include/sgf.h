@@ -245,9 +245,11 @@ sgf_status sgf_solve_noalloc(sgf_plan *plan, const void *const *sigma, void *con
  *     n = 4096), 1 = both in flight (two sequences per thread sharing the
  *     barriers; two CTAs per SM).
  *   row_inv0: 0 = level 0's inverse row pass with one CTA per (row pair,
- *     component), the finer levels through the nest kernel; 1 = every level
- *     through the nest kernel (one CTA per row pair, both components, the
- *     gather of the second overlapping the first's transform).
+ *     component), the finer levels through the nest kernel; 2 = the same with
+ *     one CTA per row pair holding both components (two sequences per thread
+ *     sharing the barriers); 1 = every level through the nest kernel (one CTA
+ *     per row pair, the components one after the other, the gather of the
+ *     second overlapping the first's transform).
  *   col_case3 (nests): 0 = the m^2 Case-3 phase outputs of a (coarser source,
  *     target) pair in one cluster per column, the source's forward column
  *     transforms done once for all of them; 1 = one cluster per phase output,
@@ -261,7 +263,7 @@ typedef struct {
 } sgf_schedule;
 
 sgf_status sgf_plan_schedule_get(const sgf_plan *plan, sgf_schedule *schedule);
-/* Errors: SGF_EINVAL for a NULL argument or a choice other than 0 or 1;
+/* Errors: SGF_EINVAL for a NULL argument or a choice out of range;
  * SGF_EUNSUPPORTED for row_inv0 = 1 on a SGF_BF16X plan of n = SGF_MAX_N (that
  * kernel has no shared memory left for the tensor-core tiles there; the
  * autotuner skips it). */
@@ -274,8 +276,8 @@ sgf_status sgf_plan_schedule_set(sgf_plan *plan, const sgf_schedule *schedule);
  * the same key: in the process, and in the text file named by the environment
  * variable SGF_AUTOTUNE_CACHE if it is set (one line "<key> <col_pass>
  * <row_inv0> <col_case3>" per key, read once, rewritten after each tuning).  chosen (may be
- * NULL) receives the schedule; ms (may be NULL, else 6 doubles) the mean
- * milliseconds per launch of col_pass 0, col_pass 1, row_inv0 0, row_inv0 1,
+ * NULL) receives the schedule; ms (may be NULL, else 7 doubles) the mean
+ * milliseconds per launch of col_pass 0, col_pass 1, row_inv0 0, 1, 2,
  * col_case3 0, col_case3 1 (-1 where a candidate does not apply).  Blocks until
  * done.
  * Errors: SGF_EINVAL, SGF_ENOMEM, SGF_ECUDA. */

@@ -700,16 +700,17 @@ sgf_status mark(sgf_plan *p, cudaStream_t st)
     return SGF_OK;
 }
 
-// Inverse row passes of a solve.  Schedule row_inv0 = 0: level 0 (its own main
-// output alone) through k_row_inv1, the finer levels (main output plus Case-3
-// phases) through k_row_inv; row_inv0 = 1: every level through k_row_inv.
+// Inverse row passes of a solve.  Schedule row_inv0 = 0 / 2: level 0 (its own
+// main output alone) through k_row_inv1 with one / both components per CTA, the
+// finer levels (main output plus Case-3 phases) through k_row_inv; row_inv0 = 1:
+// every level through k_row_inv.
 template <typename T>
 cudaError_t launch_row_inv(int logN, int L, SolveArgs<T> a, cudaStream_t st, bool tc, int row_inv0)
 {
     a.level_base = 0;
     if (row_inv0 == 1)
         return launch_pass_n<T>(PASS_ROW_INV, logN, a, L, st, nullptr, tc);
-    cudaError_t e = launch_pass_n<T>(PASS_ROW_INV1, logN, a, 1, st, nullptr, tc);
+    cudaError_t e = launch_pass_n<T>(row_inv0 == 2 ? PASS_ROW_INV2 : PASS_ROW_INV1, logN, a, 1, st, nullptr, tc);
     if (e != cudaSuccess || L == 1)
         return e;
     a.level_base = 1;
@@ -745,7 +746,7 @@ cudaError_t launch_col(const sgf_plan *p, const SolveArgs<T> &a, cudaStream_t st
 // for level 0) has no shared memory left for tensor-core tiles at n = 4096.
 inline bool schedule_ok(const sgf_plan *p, const sgf_schedule &s)
 {
-    if ((s.col_pass != 0 && s.col_pass != 1) || (s.row_inv0 != 0 && s.row_inv0 != 1) ||
+    if ((s.col_pass != 0 && s.col_pass != 1) || s.row_inv0 < 0 || s.row_inv0 > 2 ||
         (s.col_case3 != 0 && s.col_case3 != 1))
         return false;
     return !(s.row_inv0 == 1 && p->tc && p->N == SGF_MAX_N);
@@ -1062,7 +1063,8 @@ sgf_status batch_launches(sgf_batch *bt, cudaStream_t st)
                 return cuda_fail(e, "batched row_inv launch");
             continue;
         }
-        if ((e = launch_pass_n<T>(PASS_ROW_INV1, g.logN, dummy, g.n_inv1, st, &vi1, g.tc)) != cudaSuccess)
+        if ((e = launch_pass_n<T>(g.sched.row_inv0 == 2 ? PASS_ROW_INV2 : PASS_ROW_INV1, g.logN, dummy, g.n_inv1, st,
+                                  &vi1, g.tc)) != cudaSuccess)
             return cuda_fail(e, "batched row_inv1 launch");
         if (g.n_inv > 0 && (e = launch_pass_n<T>(PASS_ROW_INV, g.logN, dummy, g.n_inv, st, &vi, g.tc)) != cudaSuccess)
             return cuda_fail(e, "batched row_inv launch");
@@ -1273,7 +1275,7 @@ void tune_load_locked()
     char key[160];
     int a = 0, b = 0, c = 0;
     while (fscanf(f, "%159s %d %d %d", key, &a, &b, &c) == 4)
-        if ((a == 0 || a == 1) && (b == 0 || b == 1) && (c == 0 || c == 1))
+        if ((a == 0 || a == 1) && b >= 0 && b <= 2 && (c == 0 || c == 1))
             g_tune[key] = sgf_schedule{a, b, c};
     fclose(f);
 }
@@ -1306,7 +1308,7 @@ void tune_apply(sgf_plan *p)
 }
 
 template <typename T>
-sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[6])
+sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[7])
 {
     const size_t lvl = (size_t)p->N * p->N * p->esize;
     const size_t lal = (lvl + 255) & ~(size_t)255;
@@ -1355,7 +1357,7 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[6])
         out = t / reps;
         return SGF_OK;
     };
-    for (int k = 0; k < 6; ++k)
+    for (int k = 0; k < 7; ++k)
         ms[k] = -1.0;
     sgf_schedule best = p->sched;
     if (p->merged) {
@@ -1365,25 +1367,29 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[6])
         if (s == SGF_OK)
             best.col_pass = ms[1] < ms[0] ? 1 : 0;
     }
-    for (int c = 0; c < 2 && s == SGF_OK; ++c) {
+    for (int c = 0; c < 3 && s == SGF_OK; ++c) {
         sgf_schedule cand = best;
         cand.row_inv0 = c;
         if (schedule_ok(p, cand))
             s = timeit([&] { return launch_row_inv<T>(p->logN, p->L, a, st, p->tc, c); }, ms[2 + c]);
     }
-    if (s == SGF_OK)
-        best.row_inv0 = ms[3] >= 0.0 && ms[3] < ms[2] ? 1 : 0;
+    if (s == SGF_OK) {
+        best.row_inv0 = 0;
+        for (int c = 1; c < 3; ++c)
+            if (ms[2 + c] >= 0.0 && ms[2 + c] < ms[2 + best.row_inv0])
+                best.row_inv0 = c;
+    }
     if (!p->merged && !p->groups.empty()) {  // Case-3 outputs grouped or one cluster each
         const sgf_schedule keep = p->sched;
         for (int c = 0; c < 2 && s == SGF_OK; ++c) {
             p->sched.col_case3 = c;
             SolveArgs<T> ac;
             fill_args<T>(p, ds, dx, dy, ac, p->sched);
-            s = timeit([&] { return launch_col<T>(p, ac, st); }, ms[4 + c]);
+            s = timeit([&] { return launch_col<T>(p, ac, st); }, ms[5 + c]);
         }
         p->sched = keep;
         if (s == SGF_OK)
-            best.col_case3 = ms[5] < ms[4] ? 1 : 0;
+            best.col_case3 = ms[6] < ms[5] ? 1 : 0;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1690,9 +1696,9 @@ sgf_status sgf_plan_schedule_set(sgf_plan *p, const sgf_schedule *in)
 {
     if (!p || !in)
         return fail(SGF_EINVAL, "NULL argument");
-    if ((in->col_pass != 0 && in->col_pass != 1) || (in->row_inv0 != 0 && in->row_inv0 != 1) ||
+    if ((in->col_pass != 0 && in->col_pass != 1) || in->row_inv0 < 0 || in->row_inv0 > 2 ||
         (in->col_case3 != 0 && in->col_case3 != 1))
-        return fail(SGF_EINVAL, "schedule choices are 0 or 1 (col_pass %d, row_inv0 %d, col_case3 %d)", in->col_pass,
+        return fail(SGF_EINVAL, "schedule out of range (col_pass %d, row_inv0 %d, col_case3 %d)", in->col_pass,
                     in->row_inv0, in->col_case3);
     if (!schedule_ok(p, *in))
         return fail(SGF_EUNSUPPORTED, "row_inv0 = 1 is not available for SGF_BF16X plans of n = %d", SGF_MAX_N);
@@ -1707,7 +1713,7 @@ sgf_status sgf_plan_autotune(sgf_plan *p, int32_t reps, void *stream, sgf_schedu
     if (reps < 1 || reps > 1000)
         return fail(SGF_EINVAL, "reps = %d outside [1, 1000]", reps);
     DeviceGuard g(p->device);
-    double t[6];
+    double t[7];
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     sgf_status s = p->prec == SGF_FP64 ? autotune_impl<double>(p, reps, st, t) : autotune_impl<float>(p, reps, st, t);
     if (s != SGF_OK)
@@ -1715,7 +1721,7 @@ sgf_status sgf_plan_autotune(sgf_plan *p, int32_t reps, void *stream, sgf_schedu
     if (chosen)
         *chosen = p->sched;
     if (ms)
-        for (int k = 0; k < 6; ++k)
+        for (int k = 0; k < 7; ++k)
             ms[k] = t[k];
     return SGF_OK;
 }

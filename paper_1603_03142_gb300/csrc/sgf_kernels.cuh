@@ -74,11 +74,26 @@ __host__ __device__ __forceinline__ size_t tw_bytes(int entries)
     return (((size_t)entries * sizeof(C)) + 15) & ~(size_t)15;
 }
 
-// W_P^n for n = j + u N/16: W_P^j W_32^u from the shared twiddle area.
+// cos and sin of 2 pi u / 32, u = 0..15.
+__device__ constexpr double kW32c[16] = {
+    1.0, 0.98078528040323044913, 0.92387953251128675613, 0.83146961230254523708,
+    0.70710678118654752440, 0.55557023301960222474, 0.38268343236508977173, 0.19509032201612826785,
+    0.0, -0.19509032201612826785, -0.38268343236508977173, -0.55557023301960222474,
+    -0.70710678118654752440, -0.83146961230254523708, -0.92387953251128675613, -0.98078528040323044913};
+__device__ constexpr double kW32s[16] = {
+    0.0, 0.19509032201612826785, 0.38268343236508977173, 0.55557023301960222474,
+    0.70710678118654752440, 0.83146961230254523708, 0.92387953251128675613, 0.98078528040323044913,
+    1.0, 0.98078528040323044913, 0.92387953251128675613, 0.83146961230254523708,
+    0.70710678118654752440, 0.55557023301960222474, 0.38268343236508977173, 0.19509032201612826785};
+
+// W_P^n for n = j + u N/16 (P = 2N): W_P^j from the shared twiddle area times
+// W_32^u = cos(2 pi u/32) - i sin(2 pi u/32), a constant (u is unrolled at
+// every call).
 template <typename C>
 __device__ __forceinline__ C twist(const C *tw, const TwLayout &tl, int j, int u)
 {
-    return hmul(tw[tl.base + j], tw[tl.w32 + u]);
+    using T = typename Real<C>::T;
+    return hmul(tw[tl.base + j], hmk<C>((T)kW32c[u], (T)-kW32s[u]));
 }
 
 // Sequence stride (complex) of a column-pass exchange buffer: N + N/16 rounded
@@ -111,13 +126,13 @@ struct KShape {
 // memory: all of them, except where the kernel's own staging leaves no room at
 // N = 4096 (k_row_fwd keeps two; k_row_inv keeps one and is never launched
 // there: the host refuses SGF_BF16X nests of N = 4096 with more than one level).
-enum : int { KK_ROW_FWD, KK_COL, KK_ROW_INV, KK_ROW_INV1, KK_ROW_FWD_M, KK_COL_M, KK_COL_MD, KK_COL_G, KK_COL_SUM };
+enum : int { KK_ROW_FWD, KK_COL, KK_ROW_INV, KK_ROW_INV1, KK_ROW_FWD_M, KK_COL_M, KK_COL_MD, KK_COL_G, KK_COL_SUM, KK_ROW_INV2 };
 __host__ __device__ constexpr int tc_round(int logn, int tiles, int kind)
 {
     return logn < 12                                 ? tiles
            : kind == KK_ROW_FWD                      ? (tiles < 2 ? tiles : 2)
-           : kind == KK_ROW_INV || kind == KK_COL_G ? 1
-                                                     : tiles;
+           : kind == KK_ROW_INV || kind == KK_COL_G || kind == KK_ROW_INV2 ? 1
+                                                                          : tiles;
 }
 
 // ------------------------------------------------------------------ row_fwd
@@ -724,16 +739,17 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_inv(SolveArgs
 
 // ----------------------------------------------------------------- row_inv1
 // Inverse row pass of a level with a single contribution, its own main output
-// (m = 1: level 0 of every nest, every uniform solve).  One CTA per (row pair,
-// component): the two rows are gathered (16 bytes per bin in FP32), turned
-// into one complex sequence Z = A + iB by the Hermitian extension, inverse
-// transformed as two parity halves, folded, and stored straight from
-// registers.  The exchange buffer of the transform aliases the gather stage,
-// so a CTA needs (N + N/16) complex pairs of shared memory and two of them fit
-// on an SM; the gather of one CTA overlaps the transform of the other.
-// Grid: x = component * N/2 + row pair, y = work item (batch) or 0.
-template <typename T, int LOGN, bool BATCH, bool TC>
-__global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, sizeof(T) == 4 && !TC ? 2 : 1)
+// (m = 1: level 0 of every nest, every uniform solve).  NC = 1: one CTA per
+// (row pair, component); NC = 2: one CTA per row pair, a thread carrying the
+// same slot of both components (two sequences sharing the barriers).  The two
+// rows of a component are gathered (16 bytes per bin in FP32), turned into one
+// complex sequence Z = A + iB by the Hermitian extension, inverse transformed as
+// two parity halves, folded, and stored straight from registers.  The exchange
+// buffer of the transform aliases the gather stage.
+// Grid: x = component * N/2 + row pair (NC = 1) or row pair (NC = 2), y = work
+// item (batch) or 0.
+template <typename T, int LOGN, bool BATCH, bool TC, int NC>
+__global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, sizeof(T) == 4 && !TC && NC == 1 ? 2 : 1)
     k_row_inv1(SolveArgs<T> a0, BatchView<T> bv)
 {
     const int2 wm = BATCH ? bv.map[blockIdx.y] : make_int2(0, 0);
@@ -742,79 +758,89 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, sizeof(T) == 4 && !
     using K = KShape<LOGN>;
     constexpr int N = K::N, Q = K::Q, SP = K::SP_ROW, P = 2 * N;
     extern __shared__ __align__(16) unsigned char smem_tc[];
-    constexpr int TCT = tc_tiles(KShape<LOGN>::ROW_THREADS, 1);
-    constexpr int TCR = tc_round(LOGN, TCT, KK_ROW_INV1);
+    constexpr int TCT = tc_tiles(KShape<LOGN>::ROW_THREADS, NC);
+    constexpr int TCR = tc_round(LOGN, TCT, NC == 1 ? KK_ROW_INV1 : KK_ROW_INV2);
     static_assert(!TC || sizeof(T) == 4, "tensor-core tiles take FP32 data");
     unsigned char *smem_raw = smem_tc + (TC ? tc_smem_bytes(TCR) : 0);
     TcCtx tcx;
     if constexpr (TC)
         tc_begin(tcx, smem_tc, TCT, TCR, a.status);
     C *tw = reinterpret_cast<C *>(smem_raw);
-    // stage: bin kx's two rows (a pair of C) at [kx & 1][kx >> 1], so the threads
-    // of a parity half read consecutive pairs; then the exchange buffer
+    // stage: component c, bin kx's two rows (a pair of C) at [c][kx & 1][kx >> 1], so
+    // the threads of a parity half read consecutive pairs; then the exchange buffers
     C *stg = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
     constexpr int HALF = N / 2 + 1;
     C *sbuf = stg;
     const int tl = BATCH ? wm.y : a.level_base;
-    const int comp = (int)blockIdx.x >= N / 2 ? 1 : 0;
-    const int j0 = 2 * ((int)blockIdx.x - comp * (N / 2)), j1 = j0 + 1;
+    const int comp0 = NC == 1 && (int)blockIdx.x >= N / 2 ? 1 : 0;
+    const int j0 = 2 * ((int)blockIdx.x - comp0 * (N / 2)), j1 = j0 + 1;
     const int t = threadIdx.x;
     const bool active = t < 2 * Q;
     const int b = active ? t / Q : 0, j = active ? t - b * Q : 0;
     const TwLayout twl = tw_layout(F16<LOGN>::twlen, N);
     const RowContrib rc = a.contribs[a.contrib_begin[tl]];
     const ColOutput o = a.outs[rc.out_base];
-    const C *base = a.bwd + o.off + bwd_index(N, o.rows, comp, 0, j0);
     cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
-    {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const C *base = a.bwd + o.off + bwd_index(N, o.rows, comp0 + c, 0, j0);
         constexpr int PG = 2 * (int)sizeof(C) / 16;  // 16-byte pieces per bin (rows j0, j1 adjacent)
         for (int q = t; q < (N + 1) * PG; q += K::ROW_THREADS) {
             const int kx = q / PG, piece = q - kx * PG;
-            C *dst = stg + 2 * ((kx & 1) * HALF + (kx >> 1));
+            C *dst = stg + 2 * ((c * 2 + (kx & 1)) * HALF + (kx >> 1));
             cp16(dst + piece * (16 / (int)sizeof(C)), base + (size_t)kx * o.rows + piece * (16 / (int)sizeof(C)));
         }
     }
     cp_commit();
     cp_wait<0>();
     __syncthreads();
-    C v[1][16];
+    C v[NC][16];
     if (active) {
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const int kx = 2 * (j + u * Q) + b;
-            const int k2 = kx <= N ? kx : P - kx;  // same parity as kx
-            const C *pr = stg + 2 * (b * HALF + (k2 >> 1));
-            C A, B;
-            if constexpr (sizeof(T) == 4) {  // one 16-byte load (pairs start on 16-byte boundaries)
-                const float4 ab = *reinterpret_cast<const float4 *>(pr);
-                A = hmk<C>(ab.x, ab.y);
-                B = hmk<C>(ab.z, ab.w);
-            } else {
-                A = pr[0];
-                B = pr[1];
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int kx = 2 * (j + u * Q) + b;
+                const int k2 = kx <= N ? kx : P - kx;  // same parity as kx
+                const C *pr = stg + 2 * ((c * 2 + b) * HALF + (k2 >> 1));
+                C A, B;
+                if constexpr (sizeof(T) == 4) {  // one 16-byte load (pairs start on 16-byte boundaries)
+                    const float4 ab = *reinterpret_cast<const float4 *>(pr);
+                    A = hmk<C>(ab.x, ab.y);
+                    B = hmk<C>(ab.z, ab.w);
+                } else {
+                    A = pr[0];
+                    B = pr[1];
+                }
+                v[c][u] = kx <= N ? hmk<C>(A.x - B.y, A.y + B.x) : hmk<C>(A.x + B.y, B.x - A.y);
             }
-            v[0][u] = kx <= N ? hmk<C>(A.x - B.y, A.y + B.x) : hmk<C>(A.x + B.y, B.x - A.y);
-        }
     }
-    // the transform's first exchange write follows a barrier, after every read of the stage
-    fft_ct<C, true, LOGN, 1, TC>(v, sbuf + b * SP, SP, j, active, tw, &tcx);
+    // the transform's first exchange write follows a barrier, after every read of the stage;
+    // half b's NC sequences at sbuf + (b NC + c) SP
+    fft_ct<C, true, LOGN, NC, TC>(v, sbuf + b * NC * SP, SP, j, active, tw, &tcx);
     __syncthreads();
     if (active && b == 1) {
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
             const int n = j + u * Q;
-            sbuf[pad16(n)] = hmulc(v[0][u], twist(tw, twl, j, u));
+            const C w = twist(tw, twl, j, u);
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                sbuf[c * SP + pad16(n)] = hmulc(v[c][u], w);
         }
     }
     __syncthreads();
     if (active && b == 0) {
-        T *out = comp ? a.fy[tl] : a.fx[tl];
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const int n = j + u * Q;
-            const C y = hadd(v[0][u], sbuf[pad16(n)]);
-            out[(size_t)j0 * N + n] = covered(a, tl, j0, n) ? T(0) : y.x;
-            out[(size_t)j1 * N + n] = covered(a, tl, j1, n) ? T(0) : y.y;
+        for (int c = 0; c < NC; ++c) {
+            T *out = comp0 + c ? a.fy[tl] : a.fx[tl];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int n = j + u * Q;
+                const C y = hadd(v[c][u], sbuf[c * SP + pad16(n)]);
+                out[(size_t)j0 * N + n] = covered(a, tl, j0, n) ? T(0) : y.x;
+                out[(size_t)j1 * N + n] = covered(a, tl, j1, n) ? T(0) : y.y;
+            }
         }
     }
     if constexpr (TC)
@@ -1131,11 +1157,12 @@ struct KSmem {
         return rtc(KK_ROW_INV) + tw() + ((2 * (size_t)(N + 1) * sizeof(C) + 15) & ~(size_t)15) +
                2 * (size_t)KShape<LOGN>::SP_ROW * sizeof(C) + 4 * (size_t)N * sizeof(T);
     }
-    static size_t row_inv1()
+    static size_t row_inv1(int nc)
     {
-        const size_t stage = 2 * (size_t)(N / 2 + 1) * 2 * sizeof(C);  // [parity][N/2 + 1] pairs
-        const size_t xbuf = 2 * (size_t)KShape<LOGN>::SP_ROW * sizeof(C);
-        return rtc(KK_ROW_INV1) + tw() + (stage > xbuf ? stage : xbuf);
+        const size_t stage = (size_t)nc * 2 * (N / 2 + 1) * 2 * sizeof(C);  // [comp][parity][N/2 + 1] pairs
+        const size_t xbuf = (size_t)nc * 2 * KShape<LOGN>::SP_ROW * sizeof(C);
+        return tc(KShape<LOGN>::ROW_THREADS, nc, nc == 1 ? KK_ROW_INV1 : KK_ROW_INV2) + tw() +
+               (stage > xbuf ? stage : xbuf);
     }
     static size_t row_fwd_m()
     {
@@ -1197,7 +1224,7 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
 {
     using K = KShape<LOGN>;
     using S = KSmem<T, LOGN, TC>;
-    static std::atomic<unsigned long long> d[18];
+    static std::atomic<unsigned long long> d[20];
     const BatchView<T> none{nullptr, nullptr};
     const bool batch = bv != nullptr;
     const BatchView<T> v = batch ? *bv : none;
@@ -1223,8 +1250,10 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
             (e = ensure_smem(k_row_fwd_m<T, LOGN, true, TC>, S::row_fwd_m(), d[7])) != cudaSuccess ||
             (e = ensure_smem(k_col_m<T, LOGN, false, TC>, S::col_m(), d[8])) != cudaSuccess ||
             (e = ensure_smem(k_col_m<T, LOGN, true, TC>, S::col_m(), d[9])) != cudaSuccess ||
-            (e = ensure_smem(k_row_inv1<T, LOGN, false, TC>, S::row_inv1(), d[10])) != cudaSuccess ||
-            (e = ensure_smem(k_row_inv1<T, LOGN, true, TC>, S::row_inv1(), d[11])) != cudaSuccess ||
+            (e = ensure_smem(k_row_inv1<T, LOGN, false, TC, 1>, S::row_inv1(1), d[10])) != cudaSuccess ||
+            (e = ensure_smem(k_row_inv1<T, LOGN, true, TC, 1>, S::row_inv1(1), d[11])) != cudaSuccess ||
+            (e = ensure_smem(k_row_inv1<T, LOGN, false, TC, 2>, S::row_inv1(2), d[18])) != cudaSuccess ||
+            (e = ensure_smem(k_row_inv1<T, LOGN, true, TC, 2>, S::row_inv1(2), d[19])) != cudaSuccess ||
             (e = ensure_smem(k_col_md<T, LOGN, false, TC>, S::col_md(), d[12])) != cudaSuccess ||
             (e = ensure_smem(k_col_md<T, LOGN, true, TC>, S::col_md(), d[13])) != cudaSuccess ||
             (e = ensure_smem(k_col_g<T, LOGN, false, TC>, S::col_g(), d[14])) != cudaSuccess ||
@@ -1251,8 +1280,13 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
         break;
     }
     case PASS_ROW_INV1: {
-        SGF_LAUNCH((k_row_inv1<T, LOGN, false, TC>), (k_row_inv1<T, LOGN, true, TC>), 10, S::row_inv1(),
+        SGF_LAUNCH((k_row_inv1<T, LOGN, false, TC, 1>), (k_row_inv1<T, LOGN, true, TC, 1>), 10, S::row_inv1(1),
                    dim3(K::N, batch ? count : 1), K::ROW_THREADS)
+        break;
+    }
+    case PASS_ROW_INV2: {
+        SGF_LAUNCH((k_row_inv1<T, LOGN, false, TC, 2>), (k_row_inv1<T, LOGN, true, TC, 2>), 18, S::row_inv1(2),
+                   dim3(K::N / 2, batch ? count : 1), K::ROW_THREADS)
         break;
     }
     case PASS_ROW_FWD_M: {

@@ -43,7 +43,7 @@ def test_schedules_agree_zero_rim(lib, prec, n):
     plan = lib.Plan(nest, prec, zero_rim=True)
     outs = []
     for col in (0, 1):
-        for inv in (0, 1):
+        for inv in (0, 1, 2):
             plan.set_schedule(col, inv)
             assert plan.schedule() == {"col_pass": col, "row_inv0": inv, "col_case3": 0}
             outs.append(run_gpu(plan, sigma))
@@ -62,13 +62,13 @@ def test_nest_schedules_agree(lib, prec):
     nest, sigma = W.random_nest_problem(rng, 128, 3)
     plan = lib.Plan(nest, prec)
     res = {}
-    for inv in (0, 1):
+    for inv in (0, 1, 2):
         for c3 in (0, 1):
             plan.set_schedule(0, inv, c3)
             res[(inv, c3)] = run_gpu(plan, sigma)
             # restrictions 2, row_fwd, col (+ k_col_g), k_col_sum (level 0 has 21 inputs, more than
             # one chunk), row_inv1 + row_inv or one row_inv
-            assert plan.stats()["launches_per_solve"] == 2 + 3 + (1 - inv) + (1 - c3) + 1
+            assert plan.stats()["launches_per_solve"] == 2 + 3 + (0 if inv == 1 else 1) + (1 - c3) + 1
     eps = np.finfo(np.float64 if prec == "fp64" else np.float32).eps
     a = res[(0, 0)]
     for key, b in res.items():
@@ -128,10 +128,11 @@ print(json.dumps({"r": r, "q": q.schedule()}))
     import json
     d = json.loads(out.stdout.strip().splitlines()[-1])
     ms = d["r"]["ms"]
-    assert all(ms[k] > 0 for k in ("col_pass0", "col_pass1", "row_inv0_0", "row_inv0_1"))
+    assert all(ms[k] > 0 for k in ("col_pass0", "col_pass1", "row_inv0_0", "row_inv0_1", "row_inv0_2"))
     ch = d["r"]["chosen"]
     assert ch["col_pass"] == (1 if ms["col_pass1"] < ms["col_pass0"] else 0)
-    assert ch["row_inv0"] == (1 if ms["row_inv0_1"] < ms["row_inv0_0"] else 0)
+    inv = [ms["row_inv0_0"], ms["row_inv0_1"], ms["row_inv0_2"]]
+    assert ch["row_inv0"] == inv.index(min(inv))
     assert d["q"] == ch
     lines = table.read_text().split("\n")
     assert any("/n1024/p1/zr1/" in ln for ln in lines)
