@@ -22,6 +22,7 @@
 // The in-register 16- and 8-point DFTs use the exact constants cos(pi/8),
 // sin(pi/8) and sqrt(1/2).
 #pragma once
+#include <cstring>
 #include "sgf_fft.cuh"
 #ifdef __CUDACC__
 #include "sgf_tc.cuh"
@@ -51,14 +52,57 @@ template <typename C> SGF_HD C hmulc(C a, C b) { return hmk<C>(a.x * b.x + a.y *
 // times exp(-i pi/2) (forward) / exp(+i pi/2) (inverse)
 template <typename C, bool INV> SGF_HD C hrot(C a) { return INV ? hmk<C>(-a.y, a.x) : hmk<C>(a.y, -a.x); }
 
+// Complex add and subtract of the butterflies.  For float2 on the device each is
+// one packed two-lane FP32 instruction (add.rn.f32x2 / sub.rn.f32x2, sm_100 and
+// later), the same two IEEE operations as the scalar form.
+template <typename C> SGF_HD C badd(C a, C b) { return hadd(a, b); }
+template <typename C> SGF_HD C bsub(C a, C b) { return hsub(a, b); }
+template <>
+SGF_HD float2 badd<float2>(float2 a, float2 b)
+{
+#if defined(__CUDA_ARCH__)
+    unsigned long long ra, rb, rr;
+    memcpy(&ra, &a, 8);
+    memcpy(&rb, &b, 8);
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(rr) : "l"(ra), "l"(rb));
+    float2 r;
+    memcpy(&r, &rr, 8);
+    return r;
+#else
+    return hadd(a, b);
+#endif
+}
+template <>
+SGF_HD float2 bsub<float2>(float2 a, float2 b)
+{
+#if defined(__CUDA_ARCH__)
+    unsigned long long ra, rb, rr;
+    memcpy(&ra, &a, 8);
+    memcpy(&rb, &b, 8);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rr) : "l"(ra), "l"(rb));
+    float2 r;
+    memcpy(&r, &rr, 8);
+    return r;
+#else
+    return hsub(a, b);
+#endif
+}
+
+// 4-point DFT; the outputs 1 and 3 take the rotated difference (times -i
+// forward, +i inverse) with scalar adds.
 template <typename C, bool INV>
 SGF_HD void hdft4(C &v0, C &v1, C &v2, C &v3)
 {
-    C a0 = hadd(v0, v2), a1 = hsub(v0, v2), a2 = hadd(v1, v3), a3 = hrot<C, INV>(hsub(v1, v3));
-    v0 = hadd(a0, a2);
-    v1 = hadd(a1, a3);
-    v2 = hsub(a0, a2);
-    v3 = hsub(a1, a3);
+    const C a0 = badd(v0, v2), a1 = bsub(v0, v2), a2 = badd(v1, v3), d = bsub(v1, v3);
+    v0 = badd(a0, a2);
+    v2 = bsub(a0, a2);
+    if (INV) {
+        v1 = hmk<C>(a1.x - d.y, a1.y + d.x);
+        v3 = hmk<C>(a1.x + d.y, a1.y - d.x);
+    } else {
+        v1 = hmk<C>(a1.x + d.y, a1.y - d.x);
+        v3 = hmk<C>(a1.x - d.y, a1.y + d.x);
+    }
 }
 
 // multiply by W16^e (forward: exp(-2 pi i e/16)), e in 0..9
@@ -127,8 +171,8 @@ SGF_HD void hdft_small(C *v)
     constexpr int S = 16 / R;
     if (R == 2) {
         C a = v[Q], b = v[Q + S];
-        v[Q] = hadd(a, b);
-        v[Q + S] = hsub(a, b);
+        v[Q] = badd(a, b);
+        v[Q + S] = bsub(a, b);
     } else if (R == 4) {
         hdft4<C, INV>(v[Q], v[Q + S], v[Q + 2 * S], v[Q + 3 * S]);
     } else {  // R == 8: n = 2 n1 + n2, k = k1 + 4 k2
@@ -139,14 +183,14 @@ SGF_HD void hdft_small(C *v)
         o1 = w16<C, INV>(o1, 2);  // W8^1 = W16^2
         o2 = w16<C, INV>(o2, 4);  // W8^2
         o3 = w16<C, INV>(o3, 6);  // W8^3
-        v[Q] = hadd(e0, o0);
-        v[Q + S] = hadd(e1, o1);
-        v[Q + 2 * S] = hadd(e2, o2);
-        v[Q + 3 * S] = hadd(e3, o3);
-        v[Q + 4 * S] = hsub(e0, o0);
-        v[Q + 5 * S] = hsub(e1, o1);
-        v[Q + 6 * S] = hsub(e2, o2);
-        v[Q + 7 * S] = hsub(e3, o3);
+        v[Q] = badd(e0, o0);
+        v[Q + S] = badd(e1, o1);
+        v[Q + 2 * S] = badd(e2, o2);
+        v[Q + 3 * S] = badd(e3, o3);
+        v[Q + 4 * S] = bsub(e0, o0);
+        v[Q + 5 * S] = bsub(e1, o1);
+        v[Q + 6 * S] = bsub(e2, o2);
+        v[Q + 7 * S] = bsub(e3, o3);
     }
 }
 

@@ -84,7 +84,7 @@ def test_bf16x_4096_refuses_nest_inverse_schedule(lib):
         plan.set_schedule(0, 1)
     assert ei.value.status == lib.SGF_EUNSUPPORTED
     r = plan.autotune(reps=1)
-    assert r["ms"]["row_inv0_1"] < 0 and r["chosen"]["row_inv0"] == 0
+    assert r["ms"]["row_inv0_1"] < 0 and r["chosen"]["row_inv0"] != 1
 
 
 def test_batch_follows_schedule(lib):
