@@ -243,7 +243,9 @@ sgf_status sgf_solve_noalloc(sgf_plan *plan, const void *const *sigma, void *con
  *   col_pass (SGF_PLAN_ZERO_RIM plans): 0 = the two inverse column transforms
  *     one after the other (one sequence per thread; three CTAs per SM at
  *     n = 4096), 1 = both in flight (two sequences per thread sharing the
- *     barriers; two CTAs per SM).
+ *     barriers; two CTAs per SM, the parity halves of a column in a 2-CTA
+ *     cluster), 2 = as 1 with both parity halves in one CTA (no cluster; the
+ *     column staged once).
  *   row_inv0: 0 = level 0's inverse row pass with one CTA per (row pair,
  *     component), the finer levels through the nest kernel; 2 = the same with
  *     one CTA per row pair holding both components (two sequences per thread
@@ -264,9 +266,9 @@ typedef struct {
 
 sgf_status sgf_plan_schedule_get(const sgf_plan *plan, sgf_schedule *schedule);
 /* Errors: SGF_EINVAL for a NULL argument or a choice out of range;
- * SGF_EUNSUPPORTED for row_inv0 = 1 on a SGF_BF16X plan of n = SGF_MAX_N (that
- * kernel has no shared memory left for the tensor-core tiles there; the
- * autotuner skips it). */
+ * SGF_EUNSUPPORTED for col_pass = 2 or row_inv0 = 1 on a SGF_BF16X plan of
+ * n = SGF_MAX_N (those kernels have no shared memory left for the tensor-core
+ * tiles there; the autotuner skips them). */
 sgf_status sgf_plan_schedule_set(sgf_plan *plan, const sgf_schedule *schedule);
 
 /* The autotuner: runs one solve on zero density (temporary device buffers),
@@ -276,10 +278,9 @@ sgf_status sgf_plan_schedule_set(sgf_plan *plan, const sgf_schedule *schedule);
  * the same key: in the process, and in the text file named by the environment
  * variable SGF_AUTOTUNE_CACHE if it is set (one line "<key> <col_pass>
  * <row_inv0> <col_case3>" per key, read once, rewritten after each tuning).  chosen (may be
- * NULL) receives the schedule; ms (may be NULL, else 7 doubles) the mean
- * milliseconds per launch of col_pass 0, col_pass 1, row_inv0 0, 1, 2,
- * col_case3 0, col_case3 1 (-1 where a candidate does not apply).  Blocks until
- * done.
+ * NULL) receives the schedule; ms (may be NULL, else 8 doubles) the mean
+ * milliseconds per launch of col_pass 0, 1, 2, row_inv0 0, 1, 2, col_case3 0,
+ * 1 (-1 where a candidate does not apply).  Blocks until done.
  * Errors: SGF_EINVAL, SGF_ENOMEM, SGF_ECUDA. */
 sgf_status sgf_plan_autotune(sgf_plan *plan, int32_t reps, void *stream, sgf_schedule *chosen, double *ms);
 

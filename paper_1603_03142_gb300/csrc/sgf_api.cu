@@ -718,7 +718,10 @@ cudaError_t launch_row_inv(int logN, int L, SolveArgs<T> a, cudaStream_t st, boo
 }
 
 // Zero-rim column pass of the plan's schedule.
-inline int col_m_pass(const sgf_plan *p) { return p->sched.col_pass == 1 ? PASS_COL_MD : PASS_COL_M; }
+inline int col_m_pass(const sgf_plan *p)
+{
+    return p->sched.col_pass == 1 ? PASS_COL_MD : p->sched.col_pass == 2 ? PASS_COL_MW : PASS_COL_M;
+}
 
 // Column pass of a solve: zero-rim plans through k_col_m / k_col_md; general
 // plans through k_col over the main outputs and k_col_g over the Case-3 groups
@@ -746,10 +749,9 @@ cudaError_t launch_col(const sgf_plan *p, const SolveArgs<T> &a, cudaStream_t st
 // for level 0) has no shared memory left for tensor-core tiles at n = 4096.
 inline bool schedule_ok(const sgf_plan *p, const sgf_schedule &s)
 {
-    if ((s.col_pass != 0 && s.col_pass != 1) || s.row_inv0 < 0 || s.row_inv0 > 2 ||
-        (s.col_case3 != 0 && s.col_case3 != 1))
+    if (s.col_pass < 0 || s.col_pass > 2 || s.row_inv0 < 0 || s.row_inv0 > 2 || (s.col_case3 != 0 && s.col_case3 != 1))
         return false;
-    return !(s.row_inv0 == 1 && p->tc && p->N == SGF_MAX_N);
+    return !((s.row_inv0 == 1 || s.col_pass == 2) && p->tc && p->N == SGF_MAX_N);
 }
 
 template <typename T>
@@ -1045,7 +1047,10 @@ sgf_status batch_launches(sgf_batch *bt, cudaStream_t st)
         dummy.N = 1 << g.logN;
         if ((e = launch_pass_n<T>(g.merged ? PASS_ROW_FWD_M : PASS_ROW_FWD, g.logN, dummy, g.n_fwd, st, &vf, g.tc)) != cudaSuccess)
             return cuda_fail(e, "batched row_fwd launch");
-        const int colp = !g.merged ? PASS_COL : g.sched.col_pass == 1 ? PASS_COL_MD : PASS_COL_M;
+        const int colp = !g.merged              ? PASS_COL
+                         : g.sched.col_pass == 1 ? PASS_COL_MD
+                         : g.sched.col_pass == 2 ? PASS_COL_MW
+                                                 : PASS_COL_M;
         if ((e = launch_pass_n<T>(colp, g.logN, dummy, g.n_col, st, &vc, g.tc)) != cudaSuccess)
             return cuda_fail(e, "batched col launch");
         if (g.n_grp > 0) {
@@ -1275,7 +1280,7 @@ void tune_load_locked()
     char key[160];
     int a = 0, b = 0, c = 0;
     while (fscanf(f, "%159s %d %d %d", key, &a, &b, &c) == 4)
-        if ((a == 0 || a == 1) && b >= 0 && b <= 2 && (c == 0 || c == 1))
+        if (a >= 0 && a <= 2 && b >= 0 && b <= 2 && (c == 0 || c == 1))
             g_tune[key] = sgf_schedule{a, b, c};
     fclose(f);
 }
@@ -1308,7 +1313,7 @@ void tune_apply(sgf_plan *p)
 }
 
 template <typename T>
-sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[7])
+sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[8])
 {
     const size_t lvl = (size_t)p->N * p->N * p->esize;
     const size_t lal = (lvl + 255) & ~(size_t)255;
@@ -1357,26 +1362,34 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[7])
         out = t / reps;
         return SGF_OK;
     };
-    for (int k = 0; k < 7; ++k)
+    for (int k = 0; k < 8; ++k)
         ms[k] = -1.0;
     sgf_schedule best = p->sched;
     if (p->merged) {
-        for (int c = 0; c < 2 && s == SGF_OK; ++c)
-            s = timeit([&] { return launch_pass_n<T>(c ? PASS_COL_MD : PASS_COL_M, p->logN, a, 1, st, nullptr, p->tc); },
-                       ms[c]);
-        if (s == SGF_OK)
-            best.col_pass = ms[1] < ms[0] ? 1 : 0;
+        static const int col_kind[3] = {PASS_COL_M, PASS_COL_MD, PASS_COL_MW};
+        for (int c = 0; c < 3 && s == SGF_OK; ++c) {
+            sgf_schedule cand = best;
+            cand.col_pass = c;
+            if (schedule_ok(p, cand))
+                s = timeit([&] { return launch_pass_n<T>(col_kind[c], p->logN, a, 1, st, nullptr, p->tc); }, ms[c]);
+        }
+        if (s == SGF_OK) {
+            best.col_pass = 0;
+            for (int c = 1; c < 3; ++c)
+                if (ms[c] >= 0.0 && ms[c] < ms[best.col_pass])
+                    best.col_pass = c;
+        }
     }
     for (int c = 0; c < 3 && s == SGF_OK; ++c) {
         sgf_schedule cand = best;
         cand.row_inv0 = c;
         if (schedule_ok(p, cand))
-            s = timeit([&] { return launch_row_inv<T>(p->logN, p->L, a, st, p->tc, c); }, ms[2 + c]);
+            s = timeit([&] { return launch_row_inv<T>(p->logN, p->L, a, st, p->tc, c); }, ms[3 + c]);
     }
     if (s == SGF_OK) {
         best.row_inv0 = 0;
         for (int c = 1; c < 3; ++c)
-            if (ms[2 + c] >= 0.0 && ms[2 + c] < ms[2 + best.row_inv0])
+            if (ms[3 + c] >= 0.0 && ms[3 + c] < ms[3 + best.row_inv0])
                 best.row_inv0 = c;
     }
     if (!p->merged && !p->groups.empty()) {  // Case-3 outputs grouped or one cluster each
@@ -1385,11 +1398,11 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[7])
             p->sched.col_case3 = c;
             SolveArgs<T> ac;
             fill_args<T>(p, ds, dx, dy, ac, p->sched);
-            s = timeit([&] { return launch_col<T>(p, ac, st); }, ms[5 + c]);
+            s = timeit([&] { return launch_col<T>(p, ac, st); }, ms[6 + c]);
         }
         p->sched = keep;
         if (s == SGF_OK)
-            best.col_case3 = ms[6] < ms[5] ? 1 : 0;
+            best.col_case3 = ms[7] < ms[6] ? 1 : 0;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1696,12 +1709,13 @@ sgf_status sgf_plan_schedule_set(sgf_plan *p, const sgf_schedule *in)
 {
     if (!p || !in)
         return fail(SGF_EINVAL, "NULL argument");
-    if ((in->col_pass != 0 && in->col_pass != 1) || in->row_inv0 < 0 || in->row_inv0 > 2 ||
+    if (in->col_pass < 0 || in->col_pass > 2 || in->row_inv0 < 0 || in->row_inv0 > 2 ||
         (in->col_case3 != 0 && in->col_case3 != 1))
         return fail(SGF_EINVAL, "schedule out of range (col_pass %d, row_inv0 %d, col_case3 %d)", in->col_pass,
                     in->row_inv0, in->col_case3);
     if (!schedule_ok(p, *in))
-        return fail(SGF_EUNSUPPORTED, "row_inv0 = 1 is not available for SGF_BF16X plans of n = %d", SGF_MAX_N);
+        return fail(SGF_EUNSUPPORTED, "col_pass = 2 and row_inv0 = 1 are not available for SGF_BF16X plans of n = %d",
+                    SGF_MAX_N);
     p->sched = *in;
     return SGF_OK;
 }
@@ -1713,7 +1727,7 @@ sgf_status sgf_plan_autotune(sgf_plan *p, int32_t reps, void *stream, sgf_schedu
     if (reps < 1 || reps > 1000)
         return fail(SGF_EINVAL, "reps = %d outside [1, 1000]", reps);
     DeviceGuard g(p->device);
-    double t[7];
+    double t[8];
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     sgf_status s = p->prec == SGF_FP64 ? autotune_impl<double>(p, reps, st, t) : autotune_impl<float>(p, reps, st, t);
     if (s != SGF_OK)
@@ -1721,7 +1735,7 @@ sgf_status sgf_plan_autotune(sgf_plan *p, int32_t reps, void *stream, sgf_schedu
     if (chosen)
         *chosen = p->sched;
     if (ms)
-        for (int k = 0; k < 7; ++k)
+        for (int k = 0; k < 8; ++k)
             ms[k] = t[k];
     return SGF_OK;
 }

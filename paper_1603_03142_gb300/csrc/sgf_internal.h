@@ -195,7 +195,8 @@ enum : int {
     PASS_COL_MD = 7,
     PASS_COL_G = 8,
     PASS_COL_SUM = 9,
-    PASS_ROW_INV2 = 10
+    PASS_ROW_INV2 = 10,
+    PASS_COL_MW = 11
 };
 // Batch mode of the transform passes: a block's nest and its local work index
 // come from a per-launch map (one int2 per block row), and that nest's

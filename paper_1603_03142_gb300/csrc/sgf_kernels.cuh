@@ -126,12 +126,24 @@ struct KShape {
 // memory: all of them, except where the kernel's own staging leaves no room at
 // N = 4096 (k_row_fwd keeps two; k_row_inv keeps one and is never launched
 // there: the host refuses SGF_BF16X nests of N = 4096 with more than one level).
-enum : int { KK_ROW_FWD, KK_COL, KK_ROW_INV, KK_ROW_INV1, KK_ROW_FWD_M, KK_COL_M, KK_COL_MD, KK_COL_G, KK_COL_SUM, KK_ROW_INV2 };
+enum : int {
+    KK_ROW_FWD,
+    KK_COL,
+    KK_ROW_INV,
+    KK_ROW_INV1,
+    KK_ROW_FWD_M,
+    KK_COL_M,
+    KK_COL_MD,
+    KK_COL_G,
+    KK_COL_SUM,
+    KK_ROW_INV2,
+    KK_COL_MW
+};
 __host__ __device__ constexpr int tc_round(int logn, int tiles, int kind)
 {
     return logn < 12                                 ? tiles
            : kind == KK_ROW_FWD                      ? (tiles < 2 ? tiles : 2)
-           : kind == KK_ROW_INV || kind == KK_COL_G || kind == KK_ROW_INV2 ? 1
+           : kind == KK_ROW_INV || kind == KK_COL_G || kind == KK_ROW_INV2 || kind == KK_COL_MW ? 1
                                                                           : tiles;
 }
 
@@ -1130,6 +1142,102 @@ __global__ void __cluster_dims__(2, 1, 1)
         tc_end(tcx, TCT);
 }
 
+// The zero-rim column pass with one CTA per column holding both parity halves
+// (thread t: half t / (N/16), slot t mod (N/16)): the column is staged once and
+// the odd half is folded through shared memory under the CTA barrier, with no
+// cluster.  Both inverse transforms in flight (two sequences per thread).
+// Shared memory: twiddle area | column[N] | Gx, Gy half rows of both halves |
+// exchange buffers, half b's two sequences at sbuf + 2 b SPC (then the fold).
+template <typename T, int LOGN, bool BATCH, bool TC>
+__global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 1) k_col_mw(SolveArgs<T> a0, BatchView<T> bv)
+{
+    const int2 wm = BATCH ? bv.map[blockIdx.y] : make_int2(0, 0);
+    const SolveArgs<T> &a = BATCH ? bv.args[wm.x] : a0;
+    using C = typename Cx<T>::C;
+    using K = KShape<LOGN>;
+    constexpr int N = K::N, Q = K::Q, QS = quarter_stride(N), HQ = quarter_half(N);
+    constexpr int SPC = col_sp<C>(N);
+    extern __shared__ __align__(16) unsigned char smem_tc[];
+    constexpr int TCT = tc_tiles(KShape<LOGN>::ROW_THREADS, 2);
+    constexpr int TCR = tc_round(LOGN, TCT, KK_COL_MW);
+    static_assert(!TC || sizeof(T) == 4, "tensor-core tiles take FP32 data");
+    unsigned char *smem_raw = smem_tc + (TC ? tc_smem_bytes(TCR) : 0);
+    TcCtx tcx;
+    if constexpr (TC)
+        tc_begin(tcx, smem_tc, TCT, TCR, a.status);
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *col = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
+    T *gsp = reinterpret_cast<T *>(col + N);  // [half][Gx, Gy][HQ]
+    C *sbuf = reinterpret_cast<C *>(gsp + 4 * HQ);
+    const int kx = blockIdx.x;
+    const int t = threadIdx.x;
+    const bool active = t < 2 * Q;
+    const int b = active ? t / Q : 0, j = active ? t - b * Q : 0;
+    const TwLayout tl = tw_layout(F16<LOGN>::twlen, N);
+    const T *spec = reinterpret_cast<const T *>(a.spec);
+    cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
+    cp_block(col, a.fwd + (size_t)kx * N, (size_t)N * sizeof(C));
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        cp_block(gsp + (2 * h) * HQ, spec + (size_t)kx * QS + h * HQ, (size_t)HQ * sizeof(T));
+        cp_block(gsp + (2 * h + 1) * HQ, spec + ((size_t)(N + 1) + kx) * QS + h * HQ, (size_t)HQ * sizeof(T));
+    }
+    cp_commit();
+    cp_wait<0>();
+    __syncthreads();
+    C acc[2][16];
+    {
+        C v[1][16];
+        if (active) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                C x = col[j + u * Q];
+                if (b)
+                    x = hmul(x, twist(tw, tl, j, u));
+                v[0][u] = x;
+            }
+        }
+        fft_ct<C, false, LOGN, 1, TC>(v, sbuf + 2 * b * SPC, SPC, j, active, tw, &tcx);
+        if (active) {
+            const T *gx_r = gsp + (2 * b) * HQ, *gy_r = gsp + (2 * b + 1) * HQ;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int kp = j + u * Q;
+                const bool hi = 2 * kp + b > N;
+                const int q = hi ? N - kp - b : kp;
+                const T gx = gx_r[q];                        // Gx even in ky
+                const T gy = hi ? -gy_r[q] : gy_r[q];        // Gy odd in ky
+                acc[0][u] = hmk<C>(-gx * v[0][u].y, gx * v[0][u].x);  // i gx v
+                acc[1][u] = hmk<C>(-gy * v[0][u].y, gy * v[0][u].x);
+            }
+        }
+    }
+    fft_ct<C, true, LOGN, 2, TC>(acc, sbuf + 2 * b * SPC, SPC, j, active, tw, &tcx);
+    __syncthreads();  // every exchange buffer has been read
+    C *fold = sbuf;
+    if (active && b == 1) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int n = j + u * Q;
+            const C w = twist(tw, tl, j, u);
+            fold[n] = hmulc(acc[0][u], w);
+            fold[N + n] = hmulc(acc[1][u], w);
+        }
+    }
+    __syncthreads();
+    if (active && b == 0) {
+        C *dst = a.bwd;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int n = j + u * Q;
+            dst[bwd_index(N, N, 0, kx, n)] = hadd(acc[0][u], fold[n]);
+            dst[bwd_index(N, N, 1, kx, n)] = hadd(acc[1][u], fold[N + n]);
+        }
+    }
+    if constexpr (TC)
+        tc_end(tcx, TCT);
+}
+
 // ---------------------------------------------------------------- launching
 // Dynamic shared memory per kernel; TC adds the tensor-core area in front.
 template <typename T, int LOGN, bool TC = false>
@@ -1183,6 +1291,11 @@ struct KSmem {
         size_t body = 2 * (size_t)col_sp<C>(N) * sizeof(C);  // two exchange buffers; the 2N fold fits
         return ctc(KK_COL_SUM) + tw() + body;
     }
+    static size_t col_mw()
+    {
+        return tc(KShape<LOGN>::ROW_THREADS, 2, KK_COL_MW) + tw() + (size_t)N * sizeof(C) +
+               4 * (size_t)quarter_half(N) * sizeof(T) + 4 * (size_t)col_sp<C>(N) * sizeof(C);
+    }
     static size_t col_md()
     {
         // sbuf + column + spectrum half rows; at least two exchange buffers (dual inverse) and the 2N fold
@@ -1224,7 +1337,7 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
 {
     using K = KShape<LOGN>;
     using S = KSmem<T, LOGN, TC>;
-    static std::atomic<unsigned long long> d[20];
+    static std::atomic<unsigned long long> d[22];
     const BatchView<T> none{nullptr, nullptr};
     const bool batch = bv != nullptr;
     const BatchView<T> v = batch ? *bv : none;
@@ -1254,6 +1367,8 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
             (e = ensure_smem(k_row_inv1<T, LOGN, true, TC, 1>, S::row_inv1(1), d[11])) != cudaSuccess ||
             (e = ensure_smem(k_row_inv1<T, LOGN, false, TC, 2>, S::row_inv1(2), d[18])) != cudaSuccess ||
             (e = ensure_smem(k_row_inv1<T, LOGN, true, TC, 2>, S::row_inv1(2), d[19])) != cudaSuccess ||
+            (e = ensure_smem(k_col_mw<T, LOGN, false, TC>, S::col_mw(), d[20])) != cudaSuccess ||
+            (e = ensure_smem(k_col_mw<T, LOGN, true, TC>, S::col_mw(), d[21])) != cudaSuccess ||
             (e = ensure_smem(k_col_md<T, LOGN, false, TC>, S::col_md(), d[12])) != cudaSuccess ||
             (e = ensure_smem(k_col_md<T, LOGN, true, TC>, S::col_md(), d[13])) != cudaSuccess ||
             (e = ensure_smem(k_col_g<T, LOGN, false, TC>, S::col_g(), d[14])) != cudaSuccess ||
@@ -1307,6 +1422,11 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
     case PASS_COL_G: {
         SGF_LAUNCH((k_col_g<T, LOGN, false, TC>), (k_col_g<T, LOGN, true, TC>), 14, S::col_g(),
                    dim3(2 * (K::N + 1), count), K::COL_THREADS)
+        break;
+    }
+    case PASS_COL_MW: {
+        SGF_LAUNCH((k_col_mw<T, LOGN, false, TC>), (k_col_mw<T, LOGN, true, TC>), 20, S::col_mw(),
+                   dim3(K::N + 1, batch ? count : 1), K::ROW_THREADS)
         break;
     }
     case PASS_COL_MD: {

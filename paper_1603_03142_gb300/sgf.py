@@ -248,12 +248,12 @@ class Plan:
     def autotune(self, reps: int = 5, stream=None) -> dict:
         """sgf_plan_autotune: time every schedule candidate, keep the fastest."""
         sc = Schedule()
-        ms = (ctypes.c_double * 7)()
+        ms = (ctypes.c_double * 8)()
         _check(_lib.sgf_plan_autotune(self._h, int(reps), ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(sc),
                                       ms), "sgf_plan_autotune")
         return {"chosen": {"col_pass": sc.col_pass, "row_inv0": sc.row_inv0, "col_case3": sc.col_case3},
-                "ms": {"col_pass0": ms[0], "col_pass1": ms[1], "row_inv0_0": ms[2], "row_inv0_1": ms[3],
-                       "row_inv0_2": ms[4], "col_case3_0": ms[5], "col_case3_1": ms[6]}}
+                "ms": {"col_pass0": ms[0], "col_pass1": ms[1], "col_pass2": ms[2], "row_inv0_0": ms[3],
+                       "row_inv0_1": ms[4], "row_inv0_2": ms[5], "col_case3_0": ms[6], "col_case3_1": ms[7]}}
 
     def profile(self, enable: bool = True):
         _check(_lib.sgf_plan_profile(self._h, 1 if enable else 0), "sgf_plan_profile")

@@ -42,7 +42,7 @@ def test_schedules_agree_zero_rim(lib, prec, n):
     sigma = _zero_rim_sigma(n, n)
     plan = lib.Plan(nest, prec, zero_rim=True)
     outs = []
-    for col in (0, 1):
+    for col in (0, 1, 2):
         for inv in (0, 1, 2):
             plan.set_schedule(col, inv)
             assert plan.schedule() == {"col_pass": col, "row_inv0": inv, "col_case3": 0}
@@ -80,11 +80,13 @@ def test_nest_schedules_agree(lib, prec):
 
 def test_bf16x_4096_refuses_nest_inverse_schedule(lib):
     plan = lib.Plan(W.Nest(n=4096), "bf16x", zero_rim=True)
-    with pytest.raises(lib.SgfError) as ei:
-        plan.set_schedule(0, 1)
-    assert ei.value.status == lib.SGF_EUNSUPPORTED
+    for sched in ((0, 1), (2, 0)):
+        with pytest.raises(lib.SgfError) as ei:
+            plan.set_schedule(*sched)
+        assert ei.value.status == lib.SGF_EUNSUPPORTED
     r = plan.autotune(reps=1)
     assert r["ms"]["row_inv0_1"] < 0 and r["chosen"]["row_inv0"] != 1
+    assert r["ms"]["col_pass2"] < 0 and r["chosen"]["col_pass"] != 2
 
 
 def test_batch_follows_schedule(lib):
@@ -128,9 +130,10 @@ print(json.dumps({"r": r, "q": q.schedule()}))
     import json
     d = json.loads(out.stdout.strip().splitlines()[-1])
     ms = d["r"]["ms"]
-    assert all(ms[k] > 0 for k in ("col_pass0", "col_pass1", "row_inv0_0", "row_inv0_1", "row_inv0_2"))
+    assert all(ms[k] > 0 for k in ("col_pass0", "col_pass1", "col_pass2", "row_inv0_0", "row_inv0_1", "row_inv0_2"))
     ch = d["r"]["chosen"]
-    assert ch["col_pass"] == (1 if ms["col_pass1"] < ms["col_pass0"] else 0)
+    cp = [ms["col_pass0"], ms["col_pass1"], ms["col_pass2"]]
+    assert ch["col_pass"] == cp.index(min(cp))
     inv = [ms["row_inv0_0"], ms["row_inv0_1"], ms["row_inv0_2"]]
     assert ch["row_inv0"] == inv.index(min(inv))
     assert d["q"] == ch
