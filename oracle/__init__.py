@@ -75,6 +75,11 @@ def _load():
         lib.oracle_force_targets.argtypes = [ctypes.POINTER(_Nest), dpp, dpp, dpp, ctypes.c_long,
                                              ip, ip, ip, dp, dp, ctypes.c_int]
         lib.oracle_force_targets.restype = ctypes.c_int
+        lib.oracle_potential_targets.argtypes = [ctypes.POINTER(_Nest), dpp, dpp, dpp, ctypes.c_long,
+                                                 ip, ip, ip, dp, ctypes.c_int]
+        lib.oracle_potential_targets.restype = ctypes.c_int
+        lib.oracle_cell_integrals_potential.argtypes = [ctypes.c_double] * 4 + [dp]
+        lib.oracle_cell_integrals_potential.restype = None
         lib.oracle_max_threads.argtypes = []
         lib.oracle_max_threads.restype = ctypes.c_int
         for name in ("oracle_genconv_case2", "oracle_genconv_case3"):
@@ -110,6 +115,13 @@ def cell_integrals(a: float, b: float, c: float, d: float) -> np.ndarray:
     """Exact integrals over [a,b]x[c,d] of u/r^3, v/r^3, u^2/r^3, v^2/r^3, uv/r^3."""
     out = np.zeros(5)
     _load().oracle_cell_integrals(a, b, c, d, _dp(out))
+    return out
+
+
+def cell_integrals_potential(a: float, b: float, c: float, d: float) -> np.ndarray:
+    """Exact integrals over [a,b]x[c,d] of 1/r, u/r, v/r."""
+    out = np.zeros(3)
+    _load().oracle_cell_integrals_potential(a, b, c, d, _dp(out))
     return out
 
 
@@ -184,3 +196,29 @@ def genconv_case3(b, c, m: int, nout: int) -> np.ndarray:
 
 if __name__ == "__main__":  # pragma: no cover - manual build helper
     print(build_oracle(force="--force" in sys.argv))
+
+
+def potential_at(desc, sigma, levels, ii, jj, nthreads: int = 0, prepared=None):
+    """Potential (G = 1) at target cells (levels[k], ii[k], jj[k]); covered targets give 0."""
+    lib = _load()
+    sig, dsx, dsy = prepared if prepared is not None else prepare(desc, sigma)
+    lv = np.ascontiguousarray(levels, dtype=np.int32)
+    iv = np.ascontiguousarray(ii, dtype=np.int32)
+    jv = np.ascontiguousarray(jj, dtype=np.int32)
+    out = np.zeros(len(lv))
+    ip = ctypes.POINTER(ctypes.c_int)
+    rc = lib.oracle_potential_targets(ctypes.byref(_nest(desc)), _ptr_array(sig), _ptr_array(dsx),
+                                      _ptr_array(dsy), len(lv), lv.ctypes.data_as(ip), iv.ctypes.data_as(ip),
+                                      jv.ctypes.data_as(ip), _dp(out), int(nthreads))
+    if rc:
+        raise ValueError(f"oracle_potential_targets rc={rc}")
+    return out
+
+
+def potential(desc, sigma, nthreads: int = 0):
+    """Potential at every cell of every level, as a list of (n, n) arrays."""
+    n, L = int(desc.n), int(desc.levels)
+    jj, ii = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    lv = np.repeat(np.arange(L), n * n)
+    out = potential_at(desc, sigma, lv, np.tile(ii.ravel(), L), np.tile(jj.ravel(), L), nthreads)
+    return [out[l * n * n:(l + 1) * n * n].reshape(n, n) for l in range(L)]

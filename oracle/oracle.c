@@ -16,7 +16,8 @@
  *     F_y = same with (yb - y_t)/r^3,
  *   r = |(xb,yb) - (x_t,y_t)|, G = 1 (Sec. 2.1, Eq. for F^{x,0}+F^{x,x}+F^{x,y};
  *   the linear density within a cell is Eq. (eqnSigma), expanded about the
- *   source cell centre).
+ *   source cell centre), and the potential of the same density,
+ *     Phi = - sum over the same cells of Int_c [sig_c + ...] / r  (Sec. 2.1).
  * Each cell integral is evaluated exactly through antiderivatives evaluated at
  * the four cell corners (the double difference "g|^b_a|^d_c" of Sec. 2.1):
  *   Int u/r^3     = DD[ Kx0(u,v) ],  Kx0 = the kernel of Eq. (eqnCalK)
@@ -108,6 +109,43 @@ void oracle_cell_integrals(double a, double b, double c, double d, double *out)
     corner_values(b, c, kbc);
     corner_values(a, c, kac);
     for (int q = 0; q < 5; ++q)
+        out[q] = kbd[q] - kad[q] - kbc[q] + kac[q];
+}
+
+/* ------------------------------------------------------------ potential */
+/* The potential of the same linear density (G = 1):
+ *   Phi(t) = - sum_c Int_c [sig_c + dx_c (xb - x_c) + dy_c (yb - y_c)] / r,
+ * with the cell integrals (derived here by differentiation: each line's
+ * antiderivative G has d/du d/dv G equal to the integrand)
+ *   Int 1/r   = DD[ u ln(v + r) + v ln(u + r) ]
+ *   Int u/r   = DD[ (v r + u^2 ln(v + r)) / 2 ]
+ *   Int v/r   = DD[ (u r + v^2 ln(u + r)) / 2 ]
+ * and ln(y + sqrt(x^2 + y^2)) written as asinh(y/|x|) + ln|x| for x != 0; a
+ * term multiplied by the x that vanishes there is 0. */
+static double log_r(double y, double x)  /* ln(y + sqrt(x^2 + y^2)), x != 0 */
+{
+    return asinh(y / fabs(x)) + log(fabs(x));
+}
+
+static void corner_values_potential(double u, double v, double k[3])
+{
+    const double r = sqrt(u * u + v * v);
+    const double lu = u != 0.0 ? u * log_r(v, u) : 0.0;      /* u ln(v + r) */
+    const double lv = v != 0.0 ? v * log_r(u, v) : 0.0;      /* v ln(u + r) */
+    k[0] = lu + lv;                                          /* -> Int 1/r */
+    k[1] = 0.5 * (v * r + (u != 0.0 ? u * lu : 0.0));        /* -> Int u/r */
+    k[2] = 0.5 * (u * r + (v != 0.0 ? v * lv : 0.0));        /* -> Int v/r */
+}
+
+/* out = {Int 1/r, Int u/r, Int v/r} over u in [a,b], v in [c,d]. */
+void oracle_cell_integrals_potential(double a, double b, double c, double d, double *out)
+{
+    double kbd[3], kad[3], kbc[3], kac[3];
+    corner_values_potential(b, d, kbd);
+    corner_values_potential(a, d, kad);
+    corner_values_potential(b, c, kbc);
+    corner_values_potential(a, c, kac);
+    for (int q = 0; q < 3; ++q)
         out[q] = kbd[q] - kad[q] - kbc[q] + kac[q];
 }
 
@@ -293,6 +331,90 @@ int oracle_force_targets(const oracle_nest *g, const double *const *sig, const d
             }
             fx[k] = ax;
             fy[k] = ay;
+        }
+        free(buf);
+    }
+    return fail ? -3 : 0;
+}
+
+/* Potential at one target point from the prepared fields of one level (the
+ * same edge-lattice walk as sum_level). */
+static void sum_level_potential(const oracle_nest *g, int s, const double *sig, const double *dsx,
+                                const double *dsy, double xt, double yt, double *row_lo, double *row_hi,
+                                double *phi)
+{
+    const int n = g->n;
+    const double h = level_h(g, s);
+    double X, Y;
+    level_origin(g, s, &X, &Y);
+    double acc = 0.0;
+    for (int i = 0; i <= n; ++i)
+        corner_values_potential(X + i * h - xt, Y - yt, row_lo + 3 * i);
+    for (int j = 0; j < n; ++j) {
+        const double vlo = Y + j * h - yt;
+        const double vhi = Y + (j + 1) * h - yt;
+        for (int i = 0; i <= n; ++i)
+            corner_values_potential(X + i * h - xt, vhi, row_hi + 3 * i);
+        const double vc = vlo + 0.5 * h;
+        for (int i = 0; i < n; ++i) {
+            const size_t c = (size_t)j * n + i;
+            if (sig[c] == 0.0 && dsx[c] == 0.0 && dsy[c] == 0.0)
+                continue;
+            const double *kbd = row_hi + 3 * (i + 1), *kad = row_hi + 3 * i;
+            const double *kbc = row_lo + 3 * (i + 1), *kac = row_lo + 3 * i;
+            double J[3];
+            for (int q = 0; q < 3; ++q)
+                J[q] = kbd[q] - kad[q] - kbc[q] + kac[q];
+            const double uc = X + (i + 0.5) * h - xt;
+            acc -= sig[c] * J[0] + dsx[c] * (J[1] - uc * J[0]) + dsy[c] * (J[2] - vc * J[0]);
+        }
+        double *t = row_lo;
+        row_lo = row_hi;
+        row_hi = t;
+    }
+    *phi += acc;
+}
+
+/* Potential at nt targets (level tl[k], cell ti[k], tj[k]) from prepared
+ * fields.  Covered targets get 0.  nthreads <= 0 uses the OpenMP default. */
+int oracle_potential_targets(const oracle_nest *g, const double *const *sig, const double *const *dsx,
+                             const double *const *dsy, long nt, const int *tl, const int *ti,
+                             const int *tj, double *phi, int nthreads)
+{
+    if (oracle_validate(g))
+        return -1;
+    const int n = g->n, L = g->levels;
+    for (long k = 0; k < nt; ++k)
+        if (tl[k] < 0 || tl[k] >= L || ti[k] < 0 || ti[k] >= n || tj[k] < 0 || tj[k] >= n)
+            return -2;
+#ifdef _OPENMP
+    if (nthreads > 0)
+        omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    int fail = 0;
+#pragma omp parallel
+    {
+        double *buf = (double *)malloc(sizeof(double) * 6 * (size_t)(n + 1));
+        if (!buf) {
+#pragma omp atomic write
+            fail = 1;
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (long k = 0; k < nt; ++k) {
+            if (!buf)
+                continue;
+            double p = 0.0;
+            if (!covered(g, tl[k], ti[k], tj[k])) {
+                double X, Y;
+                level_origin(g, tl[k], &X, &Y);
+                const double h = level_h(g, tl[k]);
+                const double xt = X + (ti[k] + 0.5) * h, yt = Y + (tj[k] + 0.5) * h;
+                for (int s = 0; s < L; ++s)
+                    sum_level_potential(g, s, sig[s], dsx[s], dsy[s], xt, yt, buf, buf + 3 * (size_t)(n + 1), &p);
+            }
+            phi[k] = p;
         }
         free(buf);
     }
