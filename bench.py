@@ -218,7 +218,10 @@ def run_gpu(args, world, rank, local):
 
     def timed(p, steps, clocks=None):
         def step(k):
-            p.solve_ptrs([sig[k % sets].data_ptr()], [fx[k % sets].data_ptr()], [fy[k % sets].data_ptr()], stream)
+            if p.potential:
+                p.solve_potential_ptrs([sig[k % sets].data_ptr()], [fx[k % sets].data_ptr()], stream)
+            else:
+                p.solve_ptrs([sig[k % sets].data_ptr()], [fx[k % sets].data_ptr()], [fy[k % sets].data_ptr()], stream)
         for k in range(args.warmup):
             step(k)
         torch.cuda.synchronize()
@@ -280,6 +283,22 @@ def run_gpu(args, world, rank, local):
                  "rel_linf_vs_fp32": rel}
         plan_bf.close()
 
+    potential = None
+    if not args.no_potential:
+        # the potential (kernel -1/r, three tables per set, one output) on the same
+        # density: the general three-field path, since no zero-rim merge applies
+        plan_phi = sgf.Plan(nest, "fp32", potential=True)
+        plan_phi.autotune(reps=3)
+        pms, pprof = timed(plan_phi, args.steps)
+        pst = plan_phi.stats()
+        potential = {"cells_per_s": world * cells * args.steps / (pms / 1e3), "ms_per_step": pms / args.steps,
+                     "schedule": plan_phi.schedule(),
+                     "kernel_ms": {k: v["ms"] / max(1, v["launches"]) for k, v in pprof["kernels"].items()
+                                   if v["launches"]},
+                     "algorithmic_bytes_per_solve": pst["algorithmic_bytes"],
+                     "solve_gbs": pst["algorithmic_bytes"] / (pms / args.steps / 1e3) / 1e9}
+        plan_phi.close()
+
     # e2e: host buffers through the C ABI, copies inside the timed region
     pin_s = torch.from_numpy(sigma[0].astype(np.float32)).pin_memory()
     pin_x = torch.empty((n, n), dtype=torch.float32).pin_memory()
@@ -334,6 +353,7 @@ def run_gpu(args, world, rank, local):
                    "schedule": tune["chosen"], "autotune_ms": tune["ms"],
                    "general_path": general,
                    "bf16x_path": bf16x,
+                   "potential_path": potential,
                    "l2": f"{sets} rotating input/output sets ({sets * 3 * n * n * 4 / 2**20:.0f} MiB) > 129 MiB L2",
                    "plan_ms": st["plan_ms"], "spectra_mib": st["spectra_bytes"] / 2**20,
                    "algorithmic_bytes_per_solve": st["algorithmic_bytes"],
@@ -504,6 +524,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--general", action="store_true", help="time only the general three-field path")
     ap.add_argument("--no-bf16x", action="store_true", help="skip the split-BF16 tensor-core path")
+    ap.add_argument("--no-potential", action="store_true", help="skip the potential (SGF_PLAN_POTENTIAL) timing")
     ap.add_argument("--schedule", default="auto",
                     help="uniform: 'auto' (autotuner) or 'col_pass,row_inv0' to fix the kernel schedule")
     ap.add_argument("--workload", default="uniform", choices=["uniform", "batched", "serving"])

@@ -120,9 +120,22 @@ sgf_status sgf_plan_create(const sgf_nest_desc *desc, sgf_precision precision, s
  * solve verifies the guarantee on the device; a violation is reported by
  * sgf_plan_check as SGF_EINVAL and that solve's output is not the method's. */
 
+#define SGF_PLAN_POTENTIAL 0x2u
+/* SGF_PLAN_POTENTIAL: the plan computes the mid-plane potential instead of the
+ * forces (Sec. 2, Phi = -G Int sigma / r with G = 1, the same linear density
+ * per cell as the forces, Eq. eqnSigma): three kernel tables per pair of
+ * levels, -Int 1/r and the two slope moments -Int (u - u_c)/r, -Int (v - v_c)/r
+ * over each source cell, in closed form (DD of u ln(v + r) + v ln(u + r) and of
+ * (v r + u^2 ln(v + r))/2), convolved exactly like the force tables.  Such a
+ * plan solves only through sgf_solve_potential; every force entry point
+ * (sgf_solve, sgf_solve_host, sgf_solve_noalloc, sgf_solve_batched, batches,
+ * the request loop) refuses it with SGF_EINVAL / SGF_EUNSUPPORTED.  Not
+ * combinable with SGF_PLAN_ZERO_RIM.  The potential depends on the cell size
+ * (Phi scales with h0 at fixed sigma) where the forces do not. */
+
 /* As sgf_plan_create, with option flags (0 = sgf_plan_create).  Errors as
- * sgf_plan_create; SGF_EINVAL for unknown flags or SGF_PLAN_ZERO_RIM with
- * levels > 1. */
+ * sgf_plan_create; SGF_EINVAL for unknown flags, SGF_PLAN_ZERO_RIM with
+ * levels > 1, or SGF_PLAN_ZERO_RIM with SGF_PLAN_POTENTIAL. */
 sgf_status sgf_plan_create_ex(const sgf_nest_desc *desc, sgf_precision precision, uint32_t flags,
                               sgf_plan **out);
 
@@ -154,6 +167,15 @@ sgf_status sgf_plan_stats_get(const sgf_plan *plan, sgf_plan_stats *stats);
  * stream-ordered; allocates nothing.  Errors: SGF_EINVAL, SGF_ECUDA (launch). */
 sgf_status sgf_solve(sgf_plan *plan, const void *const *sigma, void *const *fx, void *const *fy,
                      void *stream);
+
+/* Mid-plane potential on every level of a SGF_PLAN_POTENTIAL plan (Sec. 2,
+ * kernel -1/r, G = 1).  sigma[l], phi[l]: device pointers to n*n elements for
+ * l < levels, element type per precision, 16-byte aligned; phi must not alias
+ * sigma.  Cells of a level covered by its finer child get 0 (the finer level
+ * holds the value there), as for the forces.  Asynchronous and stream-ordered;
+ * allocates nothing.  Errors: SGF_EINVAL (NULL or misaligned buffer, or a plan
+ * made without SGF_PLAN_POTENTIAL), SGF_ECUDA (launch). */
+sgf_status sgf_solve_potential(sgf_plan *plan, const void *const *sigma, void *const *phi, void *stream);
 
 /* As sgf_solve, but sigma, fx and fy are HOST pointers (pinned memory gives
  * asynchronous copies).  Copies sigma to the plan's device staging, solves,
@@ -345,7 +367,7 @@ typedef struct {
     uint64_t id;
     sgf_nest_desc desc;
     sgf_precision precision;
-    uint32_t plan_flags;   /* as sgf_plan_create_ex */
+    uint32_t plan_flags;   /* as sgf_plan_create_ex, without SGF_PLAN_POTENTIAL (SGF_EUNSUPPORTED) */
     const void *sigma[SGF_MAX_LEVELS];
     void *fx[SGF_MAX_LEVELS];
     void *fy[SGF_MAX_LEVELS];

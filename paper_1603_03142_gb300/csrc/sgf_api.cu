@@ -116,9 +116,10 @@ void spectra_release(Spectra *s)
 
 struct SetKey {
     int cas, m, px, py, ax, ay;
+    int fine;  // potential plans: the finer level of the pair (its cell size scales the tables); else 0
     bool operator<(const SetKey &o) const
     {
-        return std::tie(cas, m, px, py, ax, ay) < std::tie(o.cas, o.m, o.px, o.py, o.ax, o.ay);
+        return std::tie(cas, m, px, py, ax, ay, fine) < std::tie(o.cas, o.m, o.px, o.py, o.ax, o.ay, o.fine);
     }
 };
 
@@ -129,6 +130,7 @@ struct sgf_plan {
     sgf_precision prec = SGF_FP32;
     uint32_t flags = 0;
     bool merged = false;       // SGF_PLAN_ZERO_RIM: one forward field, merged spectra
+    bool pot = false;          // SGF_PLAN_POTENTIAL: the potential (one output component, 3 tables per set)
     bool tc = false;           // SGF_BF16X: split-BF16 tensor-core radix-16 tiles (FP32 data)
     sgf_schedule sched{};      // tile schedule of the transform passes (autotuner)
     int *d_status = nullptr;   // device status word (STATUS_* bits)
@@ -207,6 +209,17 @@ struct sgf_batch {
 };
 
 namespace {
+
+sgf_status check_flags(const sgf_nest_desc *d, uint32_t flags)
+{
+    if (flags & ~(SGF_PLAN_ZERO_RIM | SGF_PLAN_POTENTIAL))
+        return fail(SGF_EINVAL, "unknown plan flags 0x%x", flags);
+    if ((flags & SGF_PLAN_ZERO_RIM) && d->levels != 1)
+        return fail(SGF_EINVAL, "SGF_PLAN_ZERO_RIM needs a single level (levels = %d)", d->levels);
+    if ((flags & SGF_PLAN_ZERO_RIM) && (flags & SGF_PLAN_POTENTIAL))
+        return fail(SGF_EINVAL, "SGF_PLAN_ZERO_RIM and SGF_PLAN_POTENTIAL do not combine");
+    return SGF_OK;
+}
 
 sgf_status validate(const sgf_nest_desc *d, sgf_precision prec)
 {
@@ -307,22 +320,25 @@ void build_lists(sgf_plan *p)
     const size_t T = p->esize, Cb = 2 * p->esize;
     std::map<SetKey, int> set_index;
     std::vector<size_t> set_bytes;
-    auto get_set = [&](int cas, int m, int px, int py, int ax, int ay) {
-        SetKey k{cas, m, px, py, ax, ay};
+    // fine: the finer level of the pair (the potential tables carry its cell size)
+    auto get_set = [&](int cas, int m, int px, int py, int ax, int ay, int fine) {
+        SetKey k{cas, m, px, py, ax, ay, p->pot ? fine : 0};
         auto it = set_index.find(k);
         if (it != set_index.end())
             return it->second;
         GenSet g{};
-        g.kind = cas == 1 ? SPEC_QUARTER : SPEC_FULL;
+        g.kind = p->pot ? (cas == 1 ? SPEC_QUARTER_PHI : SPEC_FULL_PHI) : (cas == 1 ? SPEC_QUARTER : SPEC_FULL);
         g.cas = cas;
         g.m = m;
         g.px = px;
         g.py = py;
         g.ax = ax;
         g.ay = ay;
+        g.h = p->pot ? std::ldexp(p->desc.h0, -fine) : 0.0;
         const int idx = (int)p->sets.size();
         p->sets.push_back(g);
-        set_bytes.push_back(cas == 1 ? 6 * (size_t)(N + 1) * quarter_stride(N) * T : 6 * (size_t)(N + 1) * P * Cb);
+        const size_t nt = (size_t)spec_tables(g.kind);
+        set_bytes.push_back(cas == 1 ? nt * (N + 1) * quarter_stride(N) * T : nt * (N + 1) * P * Cb);
         set_index[k] = idx;
         return idx;
     };
@@ -374,14 +390,14 @@ void build_lists(sgf_plan *p)
     std::map<std::pair<int, int>, int> c3_base;  // (s, t) -> first output
     for (int t = 0; t < L; ++t) {
         main_out[t] = add_output(t, N);
-        add_input(main_out[t], slab_full[t], get_set(1, 1, 0, 0, 0, 0));
+        add_input(main_out[t], slab_full[t], get_set(1, 1, 0, 0, 0, 0, t));
         for (int s = t + 1; s < L; ++s) {  // Case 2: finer sources
             const int m = 1 << (s - t);
             const int ax = (int)(corner_units(&p->desc, s, s, 0) - corner_units(&p->desc, t, s, 0));
             const int ay = (int)(corner_units(&p->desc, s, s, 1) - corner_units(&p->desc, t, s, 1));
             for (int py = 0; py < m; ++py)
                 for (int px = 0; px < m; ++px)
-                    add_input(main_out[t], slab_phase[{s, t, px, py}], get_set(2, m, px, py, ax, ay));
+                    add_input(main_out[t], slab_phase[{s, t, px, py}], get_set(2, m, px, py, ax, ay, s));
         }
         for (int s = 0; s < t; ++s) {  // Case 3: coarser sources, one output per target phase
             const int m = 1 << (t - s);
@@ -392,7 +408,7 @@ void build_lists(sgf_plan *p)
                     const int o = add_output(t, N / m);
                     if (py == 0 && px == 0)
                         c3_base[{s, t}] = o;
-                    add_input(o, slab_full[s], get_set(3, m, px, py, ax, ay));
+                    add_input(o, slab_full[s], get_set(3, m, px, py, ax, ay, t));
                 }
         }
     }
@@ -443,17 +459,19 @@ void build_lists(sgf_plan *p)
     for (size_t k = 0; k < p->sets.size(); ++k) {
         set_off[k] = off;
         off += (set_bytes[k] + 255) & ~(size_t)255;
-        p->sets[k].spec_off = p->sets[k].kind == SPEC_QUARTER ? set_off[k] / T : set_off[k] / Cb;
+        p->sets[k].spec_off = spec_quarter(p->sets[k].kind) ? set_off[k] / T : set_off[k] / Cb;
     }
     for (auto &ci : p->ins)
         ci.spec_off = p->sets[ci.spec_off].spec_off;
     // algorithmic bytes of one solve
-    size_t ab = 3 * (size_t)L * N * N * T;                       // sigma in, Fx and Fy out
-    ab += 2 * p->fwd_elems * Cb + 2 * p->bwd_elems * Cb;         // intermediates written and read once
+    const size_t ncomp = p->pot ? 1 : 2;
+    size_t ab = (1 + ncomp) * (size_t)L * N * N * T;              // sigma in, Fx and Fy (or Phi) out
+    ab += 2 * p->fwd_elems * Cb + ncomp * p->bwd_elems * Cb;      // intermediates written and read once
     for (const auto &o : p->outs)
         for (int k = 0; k < o.in_count; ++k) {
             const ColInput &ci = p->ins[o.in_begin + k];
-            ab += ci.kind == SPEC_QUARTER ? 6 * (size_t)(N + 1) * (N + 1) * T : 6 * (size_t)(N + 1) * P * Cb;  // padding not counted
+            const size_t nt = (size_t)spec_tables(ci.kind);
+            ab += spec_quarter(ci.kind) ? nt * (N + 1) * (N + 1) * T : nt * (N + 1) * P * Cb;  // padding not counted
         }
     if (L > 1)
         ab += (size_t)(L - 1) * (2 * (size_t)N * N * T + (size_t)N * N / 4 * 4 * T);  // restriction
@@ -465,9 +483,10 @@ size_t spectra_total(const sgf_plan *p)
 {
     size_t off = 0;
     for (const auto &g : p->sets) {
-        const size_t b = g.kind == SPEC_MERGED  ? 2 * (size_t)(p->N + 1) * quarter_stride(p->N) * p->esize
-                         : g.kind == SPEC_QUARTER ? 6 * (size_t)(p->N + 1) * quarter_stride(p->N) * p->esize
-                                                  : 6 * (size_t)(p->N + 1) * 2 * p->N * 2 * p->esize;
+        const size_t nt = (size_t)spec_tables(g.kind);
+        const size_t b = g.kind == SPEC_MERGED || spec_quarter(g.kind)
+                             ? nt * (p->N + 1) * quarter_stride(p->N) * p->esize
+                             : nt * (p->N + 1) * 2 * p->N * 2 * p->esize;
         off += (b + 255) & ~(size_t)255;
     }
     return off;
@@ -751,6 +770,8 @@ inline bool schedule_ok(const sgf_plan *p, const sgf_schedule &s)
 {
     if (s.col_pass < 0 || s.col_pass > 2 || s.row_inv0 < 0 || s.row_inv0 > 2 || (s.col_case3 != 0 && s.col_case3 != 1))
         return false;
+    if (p->pot && s.row_inv0 == 2)  // both components per CTA: a potential plan has one
+        return false;
     return !((s.row_inv0 == 1 || s.col_pass == 2) && p->tc && p->N == SGF_MAX_N);
 }
 
@@ -763,6 +784,7 @@ sgf_status solve_impl(sgf_plan *p, const void *const *sigma, void *const *fx, vo
     a.N = N;
     a.logN = p->logN;
     a.L = L;
+    a.ncomp = p->pot ? 1 : 2;
     for (int l = 0; l < kMaxLevels; ++l) {
         a.child_ox[l] = -1;
         a.child_oy[l] = -1;
@@ -786,7 +808,7 @@ sgf_status solve_impl(sgf_plan *p, const void *const *sigma, void *const *fx, vo
     }
     for (int l = 0; l < L; ++l) {
         a.fx[l] = static_cast<T *>(fx[l]);
-        a.fy[l] = static_cast<T *>(fy[l]);
+        a.fy[l] = fy ? static_cast<T *>(fy[l]) : nullptr;  // NULL: potential plans
     }
     a.fwd = static_cast<typename SolveArgs<T>::C *>(p->d_fwd);
     a.bwd = static_cast<typename SolveArgs<T>::C *>(p->d_bwd);
@@ -844,16 +866,25 @@ struct DeviceGuard {
     }
 };
 
-sgf_status check_ptrs(const sgf_plan *p, const void *const *sigma, void *const *fx, void *const *fy)
+// Arguments of a solve.  Force solves (phi = false) pass fy and need a force
+// plan; sgf_solve_potential (phi = true) passes the potential as fx, no fy,
+// and needs a potential plan.
+sgf_status check_ptrs(const sgf_plan *p, const void *const *sigma, void *const *fx, void *const *fy,
+                      bool phi = false)
 {
     if (!p)
         return fail(SGF_EINVAL, "plan is NULL");
-    if (!sigma || !fx || !fy)
+    if (p->pot && !phi)
+        return fail(SGF_EINVAL, "a SGF_PLAN_POTENTIAL plan solves through sgf_solve_potential");
+    if (!p->pot && phi)
+        return fail(SGF_EINVAL, "sgf_solve_potential needs a plan created with SGF_PLAN_POTENTIAL");
+    if (!sigma || !fx || (!phi && !fy))
         return fail(SGF_EINVAL, "pointer arrays must not be NULL");
     for (int l = 0; l < p->L; ++l) {
-        if (!sigma[l] || !fx[l] || !fy[l])
+        const void *y = phi ? fx[l] : fy[l];
+        if (!sigma[l] || !fx[l] || !y)
             return fail(SGF_EINVAL, "level %d: NULL buffer", l);
-        if (((uintptr_t)sigma[l] | (uintptr_t)fx[l] | (uintptr_t)fy[l]) & 15u)
+        if (((uintptr_t)sigma[l] | (uintptr_t)fx[l] | (uintptr_t)y) & 15u)
             return fail(SGF_EINVAL, "level %d: buffers must be 16-byte aligned", l);
     }
     return SGF_OK;
@@ -922,6 +953,7 @@ sgf_status solve_noalloc_impl(sgf_plan *p, const void *const *sigma, void *const
     a.N = N;
     a.logN = p->logN;
     a.L = L;
+    a.ncomp = p->pot ? 1 : 2;
     for (int l = 0; l < kMaxLevels; ++l) {
         a.child_ox[l] = -1;
         a.child_oy[l] = -1;
@@ -941,7 +973,7 @@ sgf_status solve_noalloc_impl(sgf_plan *p, const void *const *sigma, void *const
     }
     for (int l = 0; l < L; ++l) {
         a.fx[l] = static_cast<T *>(fx[l]);
-        a.fy[l] = static_cast<T *>(fy[l]);
+        a.fy[l] = fy ? static_cast<T *>(fy[l]) : nullptr;  // NULL: potential plans
     }
     a.fwd = reinterpret_cast<typename SolveArgs<T>::C *>(fwd);
     a.bwd = reinterpret_cast<typename SolveArgs<T>::C *>(bwd);
@@ -986,6 +1018,7 @@ void fill_args(const sgf_plan *p, const void *const *sigma, void *const *fx, voi
     a.N = N;
     a.logN = p->logN;
     a.L = L;
+    a.ncomp = p->pot ? 1 : 2;
     for (int l = 0; l < kMaxLevels; ++l) {
         a.child_ox[l] = -1;
         a.child_oy[l] = -1;
@@ -999,7 +1032,7 @@ void fill_args(const sgf_plan *p, const void *const *sigma, void *const *fx, voi
         a.sigma_in[l] = static_cast<const T *>(sigma[l]);
         a.src[l] = l + 1 < L ? restricted + (size_t)l * N * N : static_cast<const T *>(sigma[l]);
         a.fx[l] = static_cast<T *>(fx[l]);
-        a.fy[l] = static_cast<T *>(fy[l]);
+        a.fy[l] = fy ? static_cast<T *>(fy[l]) : nullptr;
     }
     a.fwd = static_cast<typename SolveArgs<T>::C *>(p->d_fwd);
     a.bwd = static_cast<typename SolveArgs<T>::C *>(p->d_bwd);
@@ -1261,7 +1294,8 @@ std::string tune_key(const sgf_plan *p)
         if (*c == ' ')
             *c = '_';
     char buf[160];
-    snprintf(buf, sizeof buf, "%s/n%d/p%d/zr%d/ml%d", dev, p->N, (int)p->prec, p->merged ? 1 : 0, p->L > 1 ? 1 : 0);
+    snprintf(buf, sizeof buf, "%s/n%d/p%d/zr%d/ml%d%s", dev, p->N, (int)p->prec, p->merged ? 1 : 0, p->L > 1 ? 1 : 0,
+             p->pot ? "/phi" : "");
     return buf;
 }
 
@@ -1437,15 +1471,14 @@ sgf_status sgf_plan_create_ex(const sgf_nest_desc *desc, sgf_precision precision
     sgf_status s = validate(desc, precision);
     if (s != SGF_OK)
         return s;
-    if (flags & ~SGF_PLAN_ZERO_RIM)
-        return fail(SGF_EINVAL, "unknown plan flags 0x%x", flags);
-    if ((flags & SGF_PLAN_ZERO_RIM) && desc->levels != 1)
-        return fail(SGF_EINVAL, "SGF_PLAN_ZERO_RIM needs a single level (levels = %d)", desc->levels);
+    if ((s = check_flags(desc, flags)) != SGF_OK)
+        return s;
     sgf_plan *p = new sgf_plan();
     p->desc = *desc;
     p->prec = precision;
     p->flags = flags;
     p->merged = (flags & SGF_PLAN_ZERO_RIM) != 0;
+    p->pot = (flags & SGF_PLAN_POTENTIAL) != 0;
     p->tc = precision == SGF_BF16X;
     p->N = desc->n;
     p->logN = ilog2(desc->n);
@@ -1481,15 +1514,14 @@ sgf_status sgf_plan_estimate(const sgf_nest_desc *desc, sgf_precision precision,
     sgf_status s = validate(desc, precision);
     if (s != SGF_OK)
         return s;
-    if (flags & ~SGF_PLAN_ZERO_RIM)
-        return fail(SGF_EINVAL, "unknown plan flags 0x%x", flags);
-    if ((flags & SGF_PLAN_ZERO_RIM) && desc->levels != 1)
-        return fail(SGF_EINVAL, "SGF_PLAN_ZERO_RIM needs a single level (levels = %d)", desc->levels);
+    if ((s = check_flags(desc, flags)) != SGF_OK)
+        return s;
     sgf_plan p;
     p.desc = *desc;
     p.prec = precision;
     p.flags = flags;
     p.merged = (flags & SGF_PLAN_ZERO_RIM) != 0;
+    p.pot = (flags & SGF_PLAN_POTENTIAL) != 0;
     p.N = desc->n;
     p.logN = ilog2(desc->n);
     p.L = desc->levels;
@@ -1527,6 +1559,7 @@ sgf_status sgf_plan_share_ex(const sgf_plan *src, sgf_precision precision, sgf_p
     p->prec = precision;
     p->flags = src->flags;
     p->merged = src->merged;
+    p->pot = src->pot;
     p->tc = precision == SGF_BF16X;
     p->sched = src->sched;
     p->N = src->N;
@@ -1580,6 +1613,15 @@ sgf_status sgf_solve(sgf_plan *p, const void *const *sigma, void *const *fx, voi
         return s;
     DeviceGuard g(p->device);
     return solve_dispatch(p, sigma, fx, fy, static_cast<cudaStream_t>(stream));
+}
+
+sgf_status sgf_solve_potential(sgf_plan *p, const void *const *sigma, void *const *phi, void *stream)
+{
+    sgf_status s = check_ptrs(p, sigma, phi, nullptr, true);
+    if (s != SGF_OK)
+        return s;
+    DeviceGuard g(p->device);
+    return solve_dispatch(p, sigma, phi, nullptr, static_cast<cudaStream_t>(stream));
 }
 
 sgf_status sgf_solve_host(sgf_plan *p, const void *const *sigma, void *const *fx, void *const *fy,
@@ -1788,6 +1830,8 @@ sgf_status sgf_batch_create(sgf_plan *const *plans, int32_t count, uint32_t flag
     for (int k = 0; k < count; ++k) {
         if (!plans[k])
             return fail(SGF_EINVAL, "plan %d is NULL", k);
+        if (plans[k]->pot)
+            return fail(SGF_EUNSUPPORTED, "plan %d: batches solve forces, not SGF_PLAN_POTENTIAL plans", k);
         if (plans[k]->prec != plans[0]->prec || plans[k]->device != plans[0]->device)
             return fail(SGF_EINVAL, "plans of one batch must share precision and device");
         for (int q = 0; q < k; ++q)

@@ -33,6 +33,15 @@
 //   Case 3: lo = -m d - p - A - 1/2,    w = m,  d in [-(N-1), N/m-1]   (p: target phase,
 //                                                A: target corner minus source corner)
 // and each set is transformed in FP64 (P x P, P = 2N) and scaled by 1/P^2.
+//
+// Potential sets (kernel -1/r, Sec. 2): with the same DD and conventions
+//   Int 1/r = DD[u ln(v + r) + v ln(u + r)]
+//   Int u/r = DD[(v r + u^2 ln(v + r)) / 2]
+//   Int v/r = DD[(u r + v^2 ln(u + r)) / 2]
+// (one-variable terms dropped as above: u ln(v + r) -> u asinh(v/|u|)), and
+//   P0 = -h Int 1/r,  Px = -h (Int u/r - u_c Int 1/r),  Py = -h (Int v/r - v_c Int 1/r),
+// h the finer cell size of the pair (the force tables are scale-free, the
+// potential grows with the cell), the slope tables again scaled by 1/m in Case 3.
 #include "sgf_fft.cuh"
 #include "sgf_internal.h"
 
@@ -60,6 +69,18 @@ __device__ __forceinline__ Corner corner_eval(double u, double v)
     k.hyy = au > 0.0 ? u * A : 0.0;
     k.hxy = -hypot(u, v);
     return k;
+}
+
+// Corner values of the potential antiderivatives: (Int 1/r, Int u/r, Int v/r).
+__device__ __forceinline__ void corner_phi(double u, double v, double k[3])
+{
+    const double au = fabs(u), av = fabs(v);
+    const double r = hypot(u, v);
+    const double lu = au > 0.0 ? u * asinh(v / au) : 0.0;  // u ln(v + r), less u ln|u|
+    const double lv = av > 0.0 ? v * asinh(u / av) : 0.0;  // v ln(u + r), less v ln|v|
+    k[0] = lu + lv;
+    k[1] = 0.5 * (v * r + u * lu);
+    k[2] = 0.5 * (u * r + v * lv);
 }
 
 struct AxisMap {
@@ -106,6 +127,29 @@ __device__ __forceinline__ void cell_tables(const AxisMap &mx, const AxisMap &my
     out[5] = (iyy - vc * i0y) * sf;
 }
 
+// The three potential tables of one source cell at convolution index (dx, dy).
+__device__ __forceinline__ void cell_tables_phi(const AxisMap &mx, const AxisMap &my, int dx, int dy, int cas, int m,
+                                                double h, double out[3])
+{
+    double a, wx, c, wy;
+    mx.edges(dx, a, wx);
+    my.edges(dy, c, wy);
+    const double b = a + wx, d = c + wy;
+    double k1[3], k2[3], k3[3], k4[3];
+    corner_phi(b, d, k1);
+    corner_phi(a, d, k2);
+    corner_phi(b, c, k3);
+    corner_phi(a, c, k4);
+    double I[3];
+    for (int q = 0; q < 3; ++q)
+        I[q] = (k1[q] - k2[q]) - (k3[q] - k4[q]);
+    const double uc = a + 0.5 * wx, vc = c + 0.5 * wy;
+    const double sf = cas == 3 ? 1.0 / m : 1.0;
+    out[0] = -h * I[0];
+    out[1] = -h * sf * (I[1] - uc * I[0]);
+    out[2] = -h * sf * (I[2] - vc * I[0]);
+}
+
 // Case 1 with the central-difference slope stencils folded in (zero-rim
 // single level): dx = (s[i+1] - s[i-1])/2 gives
 //   sum_s Kxx[t-s] dx[s] = sum_s s[s] (Kxx[d + x] - Kxx[d - x])/2,  d = t - s,
@@ -136,10 +180,12 @@ __global__ void k_gen_tables(GenSet g, int N, double *__restrict__ tables)
     const AxisMap mx{cas, g.m, g.px, g.ax, N}, my{cas, g.m, g.py, g.ay, N};
     double out[6] = {0, 0, 0, 0, 0, 0};
     int dx, dy;
-    const int ntab = g.cas == 4 ? 2 : 6;
+    const int ntab = spec_tables(g.kind);
     if (mx.index(px, P, dx) && my.index(py, P, dy)) {
         if (g.cas == 4)
             merged_tables(mx, my, dx, dy, out);
+        else if (spec_phi(g.kind))
+            cell_tables_phi(mx, my, dx, dy, g.cas, g.m, g.h, out);
         else
             cell_tables(mx, my, dx, dy, g.cas, g.m, out);
     }
@@ -148,7 +194,7 @@ __global__ void k_gen_tables(GenSet g, int N, double *__restrict__ tables)
         tables[t * plane + at] = out[t];
 }
 
-// Rows of the six P x P tables -> half spectra along x: half[t][kx 0..N][y 0..P).
+// Rows of the P x P tables -> half spectra along x: half[t][kx 0..N][y 0..P).
 // Two real rows ride as one complex row; the P-point transform of a row is
 // folded into two N-point transforms: bin 2k+b = DFT_N[(x[n] + (-1)^b x[n+N]) W_P^{bn}].
 __global__ void k_gen_rows(int N, int logN, const double *__restrict__ tables,
@@ -197,11 +243,12 @@ __global__ void k_gen_cols(int N, int logN, const double2 *__restrict__ half, co
     __syncthreads();
     block_fft<double2, false>(W, N, logN, 2, tw);
     const double scale = 1.0 / ((double)P * (double)P);
-    if (kind == SPEC_QUARTER || kind == SPEC_MERGED) {
-        // K0x and K0y (tables 0, 3) are odd in one axis: purely imaginary; merged Gx, Gy too
+    if (spec_quarter(kind) || kind == SPEC_MERGED) {
+        // K0x and K0y (tables 0, 3) are odd in one axis: purely imaginary; merged Gx, Gy
+        // too; of the potential tables Px and Py (1, 2), while P0 is real
         const int QS = quarter_stride(N), HQ = quarter_half(N);
         T *dst = reinterpret_cast<T *>(spec) + spec_off + ((size_t)t * (N + 1) + kx) * QS;
-        const bool imag = kind == SPEC_MERGED || t == 0 || t == 3;
+        const bool imag = kind == SPEC_MERGED || (kind == SPEC_QUARTER_PHI ? t != 0 : t == 0 || t == 3);
         for (int idx = tid; idx < QS; idx += nt) {
             const int q = idx < HQ ? 2 * idx : 2 * (idx - HQ) + 1;  // even half, then odd half
             const double2 X = q <= N ? W[(q & 1) * N + (q >> 1)] : make_double2(0.0, 0.0);
@@ -255,7 +302,7 @@ cudaError_t launch_gen_set(const GenSet &g, int N, int logN, const double2 *tw64
     if (e != cudaSuccess)
         return e;
     const size_t smem = 2 * (size_t)N * sizeof(double2);
-    const int ntab = g.kind == SPEC_MERGED ? 2 : 6;
+    const int ntab = spec_tables(g.kind);
     k_gen_rows<<<dim3(P / 2, ntab), gen_threads(N), smem, st>>>(N, logN, work_tables, work_half, tw64);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;

@@ -33,6 +33,13 @@
 //   SPEC_MERGED (Case 1 of a zero-rim single level): 2 tables (Gx, Gy), the
 //     kernels with the central-difference slope stencils folded in; both
 //     imaginary, quarter-stored like SPEC_QUARTER; mirror sign + for Gx, - for Gy.
+// Potential plans (SGF_PLAN_POTENTIAL) carry 3 tables per set, (P0, Px, Py) =
+//   the potential from sigma, dx, dy (kernel -1/r of Sec. 2, times the finer
+//   cell size of the pair), and a single output component:
+//   SPEC_QUARTER_PHI (Case 1): P0 even in both axes (real), Px odd in x and Py
+//     odd in y (imaginary); quarter-stored like SPEC_QUARTER, mirror sign in ky
+//     + for P0 and Px, - for Py.
+//   SPEC_FULL_PHI (Cases 2, 3): complex [table][kx 0..N][ky 0..P).
 #pragma once
 #include <cstddef>
 #include <cstdint>
@@ -43,7 +50,11 @@ namespace sgf {
 
 constexpr int kMaxLevels = 8;
 
-enum SpecKind : int { SPEC_QUARTER = 0, SPEC_FULL = 1, SPEC_MERGED = 2 };
+enum SpecKind : int { SPEC_QUARTER = 0, SPEC_FULL = 1, SPEC_MERGED = 2, SPEC_QUARTER_PHI = 3, SPEC_FULL_PHI = 4 };
+
+inline __host__ __device__ bool spec_quarter(int kind) { return kind == SPEC_QUARTER || kind == SPEC_QUARTER_PHI; }
+inline __host__ __device__ bool spec_phi(int kind) { return kind == SPEC_QUARTER_PHI || kind == SPEC_FULL_PHI; }
+inline __host__ __device__ int spec_tables(int kind) { return kind == SPEC_MERGED ? 2 : spec_phi(kind) ? 3 : 6; }
 
 // Element (comp, kx, row) of a column output with `rows` rows (complex units).
 inline __host__ __device__ size_t bwd_index(int N, int rows, int comp, int kx, int row)
@@ -121,6 +132,7 @@ template <typename T>
 struct SolveArgs {
     using C = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
     int N, logN, L;
+    int ncomp;                  // output components: 2 (Fx, Fy) or 1 (the potential, in fx)
     int child_ox[kMaxLevels], child_oy[kMaxLevels];  // covered region of each level; -1: none
     const T *src[kMaxLevels];   // density per level, covered cells already restricted
     const T *sigma_in[kMaxLevels];  // the caller's density per level (batched restriction reads it)
@@ -170,6 +182,7 @@ struct GenSet {
     int m, px, py;     // phases (m = 1 for Case 1)
     int ax, ay;        // integer lattice offset of the pair (units of the finer cell), see sgf_gen.cu
     size_t spec_off;   // where the set's spectra go (real elements for QUARTER, complex for FULL)
+    double h;          // potential sets: the finer cell size of the pair (the tables scale with it)
 };
 
 // ---- launchers (sgf_solve.cu / sgf_gen.cu); all return cudaGetLastError()
@@ -213,7 +226,7 @@ cudaError_t launch_pass_n(int pass, int logN, const SolveArgs<T> &a, int count, 
                           const BatchView<T> *bv = nullptr, bool tc = false);
 
 // Build the spectra of one set into spec (element type T: float or double).
-// work_tables: 6*P*P doubles; work_half: 6*(N+1)*P double2.
+// work_tables: spec_tables(kind)*P*P doubles; work_half: spec_tables(kind)*(N+1)*P double2.
 template <typename T>
 cudaError_t launch_gen_set(const GenSet &g, int N, int logN, const double2 *tw64, void *spec,
                            double *work_tables, double2 *work_half, cudaStream_t st);

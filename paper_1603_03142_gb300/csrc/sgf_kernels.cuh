@@ -292,11 +292,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
         const FwdSlab sl = a.slabs[ci.slab];
         const int f = k % 3;
         cp_block(st, a.fwd + sl.off + ((size_t)f * (N + 1) + kx) * sl.rows, (size_t)sl.rows * sizeof(C));
-        if (ci.kind == SPEC_QUARTER) {
+        if (spec_quarter(ci.kind)) {
             const T *sp = reinterpret_cast<const T *>(a.spec) + ci.spec_off;
             T *dst = reinterpret_cast<T *>(st + (size_t)N * sizeof(C));
             cp_block(dst, sp + ((size_t)f * (N + 1) + kx) * QS + b * HQ, (size_t)HQ * sizeof(T));
-            cp_block(dst + HQ, sp + ((size_t)(3 + f) * (N + 1) + kx) * QS + b * HQ, (size_t)HQ * sizeof(T));
+            if (ci.kind == SPEC_QUARTER)
+                cp_block(dst + HQ, sp + ((size_t)(3 + f) * (N + 1) + kx) * QS + b * HQ, (size_t)HQ * sizeof(T));
         }
     };
     cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
@@ -358,6 +359,27 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
                     }
                     acc[0][u] = hadd(acc[0][u], tx);
                     acc[1][u] = hadd(acc[1][u], ty);
+                }
+            } else if (ci.kind == SPEC_QUARTER_PHI) {
+                // the potential alone: P0 real, Px Py imaginary; mirror signs + P0 Px, - Py
+                const T mx = (f == 2) ? T(-1) : T(1);
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int kp = j + u * Q;
+                    const bool hi = 2 * kp + b > N;
+                    const int q = hi ? N - kp - b : kp;
+                    const T rx = spx[q] * (hi ? mx : T(1));
+                    C tx = hmk<C>(rx * v[0][u].x, rx * v[0][u].y);
+                    if (f != 0)
+                        tx = hmk<C>(-tx.y, tx.x);
+                    acc[0][u] = hadd(acc[0][u], tx);
+                }
+            } else if (ci.kind == SPEC_FULL_PHI) {
+                const C *sx = reinterpret_cast<const C *>(a.spec) + ci.spec_off + ((size_t)f * (N + 1) + kx) * P;
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int ky = 2 * (j + u * Q) + b;
+                    acc[0][u] = hadd(acc[0][u], hmul(__ldg(sx + ky), v[0][u]));
                 }
             } else {
                 const C *sx = reinterpret_cast<const C *>(a.spec) + ci.spec_off + ((size_t)f * (N + 1) + kx) * P;
@@ -498,16 +520,28 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
                 acc[0][u] = hmk<C>(T(0), T(0));
                 acc[1][u] = hmk<C>(T(0), T(0));
             }
+            if (ci.kind == SPEC_FULL_PHI) {  // the potential alone
 #pragma unroll 1
-            for (int f = 0; f < 3; ++f) {
-                const C *sx = spec + ci.spec_off + ((size_t)f * (N + 1) + kx) * P;
-                const C *sy = spec + ci.spec_off + ((size_t)(3 + f) * (N + 1) + kx) * P;
+                for (int f = 0; f < 3; ++f) {
+                    const C *sx = spec + ci.spec_off + ((size_t)f * (N + 1) + kx) * P;
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int ky = 2 * (j + u * Q) + b;
-                    const C x = fld[f * N + u * Q + j];
-                    acc[0][u] = hadd(acc[0][u], hmul(__ldg(sx + ky), x));
-                    acc[1][u] = hadd(acc[1][u], hmul(__ldg(sy + ky), x));
+                    for (int u = 0; u < 16; ++u) {
+                        const int ky = 2 * (j + u * Q) + b;
+                        acc[0][u] = hadd(acc[0][u], hmul(__ldg(sx + ky), fld[f * N + u * Q + j]));
+                    }
+                }
+            } else {
+#pragma unroll 1
+                for (int f = 0; f < 3; ++f) {
+                    const C *sx = spec + ci.spec_off + ((size_t)f * (N + 1) + kx) * P;
+                    const C *sy = spec + ci.spec_off + ((size_t)(3 + f) * (N + 1) + kx) * P;
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const int ky = 2 * (j + u * Q) + b;
+                        const C x = fld[f * N + u * Q + j];
+                        acc[0][u] = hadd(acc[0][u], hmul(__ldg(sx + ky), x));
+                        acc[1][u] = hadd(acc[1][u], hmul(__ldg(sy + ky), x));
+                    }
                 }
             }
         }
@@ -658,11 +692,12 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_inv(SolveArgs
     const int b = active ? t / Q : 0, j = active ? t - b * Q : 0;
     const TwLayout twl = tw_layout(F16<LOGN>::twlen, N);
     const int c0 = a.contrib_begin[tl], c1 = a.contrib_begin[tl + 1];
-    const int nitems = 2 * (c1 - c0);  // (contribution, component)
+    const int nc = a.ncomp;  // 2 (Fx, Fy) or 1 (the potential)
+    const int nitems = nc * (c1 - c0);  // (contribution, component)
 
     auto issue = [&](int k) {
-        const RowContrib rc = a.contribs[c0 + k / 2];
-        const int comp = k & 1;
+        const RowContrib rc = a.contribs[c0 + (k >> (nc - 1))];
+        const int comp = k & (nc - 1);
         const ColOutput oa = a.outs[rc.out_base + (j0 % rc.m) * rc.m];
         const ColOutput ob = a.outs[rc.out_base + (j1 % rc.m) * rc.m];
         const int ra = j0 / rc.m, rb = j1 / rc.m;
@@ -692,8 +727,8 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_inv(SolveArgs
     for (int i = t; i < 4 * N; i += K::ROW_THREADS)
         O[i] = T(0);
     for (int k = 0; k < nitems; ++k) {
-        const RowContrib rc = a.contribs[c0 + k / 2];
-        const int comp = k & 1;
+        const RowContrib rc = a.contribs[c0 + (k >> (nc - 1))];
+        const int comp = k & (nc - 1);
         const int nout = N / rc.m;
         cp_wait<0>();
         __syncthreads();
@@ -742,8 +777,10 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_inv(SolveArgs
         const bool ca = covered(a, tl, j0, i), cb = covered(a, tl, j1, i);
         fx[(size_t)j0 * N + i] = ca ? T(0) : O[i];
         fx[(size_t)j1 * N + i] = cb ? T(0) : O[N + i];
-        fy[(size_t)j0 * N + i] = ca ? T(0) : O[2 * N + i];
-        fy[(size_t)j1 * N + i] = cb ? T(0) : O[3 * N + i];
+        if (nc == 2) {
+            fy[(size_t)j0 * N + i] = ca ? T(0) : O[2 * N + i];
+            fy[(size_t)j1 * N + i] = cb ? T(0) : O[3 * N + i];
+        }
     }
     if constexpr (TC)
         tc_end(tcx, TCT);
@@ -758,8 +795,8 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_inv(SolveArgs
 // complex sequence Z = A + iB by the Hermitian extension, inverse transformed as
 // two parity halves, folded, and stored straight from registers.  The exchange
 // buffer of the transform aliases the gather stage.
-// Grid: x = component * N/2 + row pair (NC = 1) or row pair (NC = 2), y = work
-// item (batch) or 0.
+// Grid: x = component * N/2 + row pair (NC = 1; component 0 only for the
+// potential) or row pair (NC = 2), y = work item (batch) or 0.
 template <typename T, int LOGN, bool BATCH, bool TC, int NC>
 __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, sizeof(T) == 4 && !TC && NC == 1 ? 2 : 1)
     k_row_inv1(SolveArgs<T> a0, BatchView<T> bv)
@@ -1396,7 +1433,7 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
     }
     case PASS_ROW_INV1: {
         SGF_LAUNCH((k_row_inv1<T, LOGN, false, TC, 1>), (k_row_inv1<T, LOGN, true, TC, 1>), 10, S::row_inv1(1),
-                   dim3(K::N, batch ? count : 1), K::ROW_THREADS)
+                   dim3(batch ? K::N : a.ncomp * (K::N / 2), batch ? count : 1), K::ROW_THREADS)
         break;
     }
     case PASS_ROW_INV2: {

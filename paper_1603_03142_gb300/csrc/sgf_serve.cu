@@ -341,6 +341,9 @@ sgf_status sgf_server_submit(sgf_server *sv, const sgf_request *r)
     sgf_status rc = sgf_plan_estimate(&r->desc, r->precision, r->plan_flags, &p.ws, &p.spectra, &p.build);
     if (rc != SGF_OK)
         return rc;
+    if (r->plan_flags & SGF_PLAN_POTENTIAL)
+        return fail(SGF_EUNSUPPORTED, "request %llu: the request loop solves forces, not SGF_PLAN_POTENTIAL",
+                    (unsigned long long)r->id);
     const int L = r->desc.levels;
     for (int l = 0; l < L; ++l)
         if (!r->sigma[l] || !r->fx[l] || !r->fy[l])

@@ -32,9 +32,10 @@ EXPORTS = ["sgf_plan_create", "sgf_plan_create_ex", "sgf_plan_check", "sgf_plan_
            "sgf_batch_solve", "sgf_batch_info", "sgf_batch_destroy", "sgf_plan_estimate", "sgf_server_create",
            "sgf_server_clock", "sgf_server_submit", "sgf_server_progress", "sgf_server_stats_get",
            "sgf_server_destroy", "sgf_plan_schedule_get", "sgf_plan_schedule_set", "sgf_plan_autotune",
-           "sgf_plan_share_ex"]
+           "sgf_plan_share_ex", "sgf_solve_potential"]
 BATCH_NO_GRAPH = 0x1
 PLAN_ZERO_RIM = 0x1
+PLAN_POTENTIAL = 0x2
 NOALLOC_SCRATCH_BYTES = 32 << 20
 KERNELS = ["restrict", "row_fwd", "col", "row_inv"]
 
@@ -100,6 +101,7 @@ _lib.sgf_plan_stats_get.argtypes = [ctypes.c_void_p, ctypes.POINTER(PlanStats)]
 _lib.sgf_solve.argtypes = [ctypes.c_void_p, _vpp, _vpp, _vpp, ctypes.c_void_p]
 _lib.sgf_solve_host.argtypes = [ctypes.c_void_p, _vpp, _vpp, _vpp, ctypes.c_void_p]
 _lib.sgf_solve_noalloc.argtypes = [ctypes.c_void_p, _vpp, _vpp, _vpp, ctypes.c_void_p]
+_lib.sgf_solve_potential.argtypes = [ctypes.c_void_p, _vpp, _vpp, ctypes.c_void_p]
 _lib.sgf_batch_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.c_uint32,
                                   ctypes.POINTER(ctypes.c_void_p)]
 _lib.sgf_batch_solve.argtypes = [ctypes.c_void_p, ctypes.POINTER(_vpp), ctypes.POINTER(_vpp), ctypes.POINTER(_vpp),
@@ -132,7 +134,7 @@ for _f in ("sgf_plan_create", "sgf_plan_create_ex", "sgf_plan_check", "sgf_plan_
            "sgf_solve_noalloc", "sgf_batch_create", "sgf_batch_solve", "sgf_batch_info", "sgf_batch_destroy",
            "sgf_plan_estimate", "sgf_server_create", "sgf_server_submit", "sgf_server_progress",
            "sgf_server_stats_get", "sgf_server_destroy", "sgf_plan_schedule_get", "sgf_plan_schedule_set",
-           "sgf_plan_autotune", "sgf_plan_share_ex"):
+           "sgf_plan_autotune", "sgf_plan_share_ex", "sgf_solve_potential"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -184,17 +186,18 @@ def _stream_handle(stream) -> int:
 class Plan:
     """A solve plan: nest geometry + precision, resident kernel spectra, workspace."""
 
-    def __init__(self, nest, precision="fp32", zero_rim: bool = False, _handle=None):
+    def __init__(self, nest, precision="fp32", zero_rim: bool = False, potential: bool = False, _handle=None):
         self.nest = nest
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.n, self.levels = int(nest.n), int(nest.levels)
         self.zero_rim = bool(zero_rim)
+        self.potential = bool(potential)
         if _handle is not None:
             self._h = _handle
             return
         h = ctypes.c_void_p()
         desc = make_desc(nest)
-        flags = PLAN_ZERO_RIM if zero_rim else 0
+        flags = (PLAN_ZERO_RIM if zero_rim else 0) | (PLAN_POTENTIAL if potential else 0)
         _check(_lib.sgf_plan_create_ex(ctypes.byref(desc), self.precision, flags, ctypes.byref(h)),
                "sgf_plan_create_ex")
         self._h = h
@@ -224,7 +227,7 @@ class Plan:
         else:
             prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
             _check(_lib.sgf_plan_share_ex(self._h, prec, ctypes.byref(h)), "sgf_plan_share_ex")
-        return Plan(self.nest, prec, zero_rim=self.zero_rim, _handle=h)
+        return Plan(self.nest, prec, zero_rim=self.zero_rim, potential=self.potential, _handle=h)
 
     def stats(self) -> dict:
         st = PlanStats()
@@ -268,8 +271,7 @@ class Plan:
         _check(_lib.sgf_solve(self._h, _ptrs(sigma_ptrs), _ptrs(fx_ptrs), _ptrs(fy_ptrs),
                               ctypes.c_void_p(_stream_handle(stream))), "sgf_solve")
 
-    def solve(self, sigma, fx=None, fy=None, stream=None):
-        """sigma: list of per-level contiguous CUDA tensors (n, n). Returns (fx, fy) lists."""
+    def _device_levels(self, sigma):
         import torch
         sig = list(sigma)
         if len(sig) != self.levels:
@@ -278,6 +280,25 @@ class Plan:
         for s in sig:
             if not (s.is_cuda and s.is_contiguous() and s.dtype == dt and tuple(s.shape) == (self.n, self.n)):
                 raise ValueError(f"sigma levels must be contiguous CUDA {dt} tensors of shape ({self.n}, {self.n})")
+        return sig
+
+    def solve_potential_ptrs(self, sigma_ptrs, phi_ptrs, stream=None):
+        _check(_lib.sgf_solve_potential(self._h, _ptrs(sigma_ptrs), _ptrs(phi_ptrs),
+                                        ctypes.c_void_p(_stream_handle(stream))), "sgf_solve_potential")
+
+    def solve_potential(self, sigma, phi=None, stream=None):
+        """Potential plans: sigma as for solve(); returns the per-level potential list."""
+        import torch
+        sig = self._device_levels(sigma)
+        if phi is None:
+            phi = [torch.empty_like(s) for s in sig]
+        self.solve_potential_ptrs([s.data_ptr() for s in sig], [t.data_ptr() for t in phi], stream)
+        return phi
+
+    def solve(self, sigma, fx=None, fy=None, stream=None):
+        """sigma: list of per-level contiguous CUDA tensors (n, n). Returns (fx, fy) lists."""
+        import torch
+        sig = self._device_levels(sigma)
         if fx is None:
             fx = [torch.empty_like(s) for s in sig]
         if fy is None:
