@@ -11,7 +11,10 @@ integrals of the linear density of Eq. (eqnSigma) against the force kernel
 (Sec. 2.1).  This module only builds and loads that library and marshals numpy
 arrays.  Nest descriptors are duck-typed: any object with ``n``, ``levels``,
 ``x0``, ``y0``, ``h0`` and ``off`` (a sequence of ``(ox, oy)`` per level,
-entry 0 unused) works.
+entry 0 unused) works.  Forests (several patches per level) are objects with
+``n``, ``x0``, ``y0``, ``h0``, ``level`` and ``org`` (per patch: its level and
+its corner in cells of that level from (x0, y0)) and ``levels`` = the number of
+patches: every per-level list below is then a per-patch list.
 
 Parity status of each function is stated in the design notes; every function
 here is pinned by a ``-m "not gpu"`` test against quadrature, closed forms or
@@ -31,6 +34,7 @@ _HERE = Path(__file__).resolve().parent
 _SRC = _HERE / "oracle.c"
 _LIB = _HERE / "liboracle.so"
 MAX_LEVELS = 8
+MAX_PATCHES = 16
 
 
 class _Nest(ctypes.Structure):
@@ -41,6 +45,18 @@ class _Nest(ctypes.Structure):
         ("y0", ctypes.c_double),
         ("h0", ctypes.c_double),
         ("off", (ctypes.c_int * 2) * MAX_LEVELS),
+    ]
+
+
+class _Forest(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int),
+        ("patches", ctypes.c_int),
+        ("x0", ctypes.c_double),
+        ("y0", ctypes.c_double),
+        ("h0", ctypes.c_double),
+        ("level", ctypes.c_int * MAX_PATCHES),
+        ("org", (ctypes.c_int * 2) * MAX_PATCHES),
     ]
 
 
@@ -80,6 +96,17 @@ def _load():
         lib.oracle_potential_targets.restype = ctypes.c_int
         lib.oracle_cell_integrals_potential.argtypes = [ctypes.c_double] * 4 + [dp]
         lib.oracle_cell_integrals_potential.restype = None
+        fp = ctypes.POINTER(_Forest)
+        lib.oracle_forest_validate.argtypes = [fp]
+        lib.oracle_forest_validate.restype = ctypes.c_int
+        lib.oracle_forest_prepare.argtypes = [fp, dpp, dpp, dpp, dpp]
+        lib.oracle_forest_prepare.restype = ctypes.c_int
+        lib.oracle_forest_force_targets.argtypes = [fp, dpp, dpp, dpp, ctypes.c_long, ip, ip, ip, dp, dp,
+                                                    ctypes.c_int]
+        lib.oracle_forest_force_targets.restype = ctypes.c_int
+        lib.oracle_forest_potential_targets.argtypes = [fp, dpp, dpp, dpp, ctypes.c_long, ip, ip, ip, dp,
+                                                        ctypes.c_int]
+        lib.oracle_forest_potential_targets.restype = ctypes.c_int
         lib.oracle_max_threads.argtypes = []
         lib.oracle_max_threads.restype = ctypes.c_int
         for name in ("oracle_genconv_case2", "oracle_genconv_case3"):
@@ -97,6 +124,23 @@ def _nest(desc) -> _Nest:
     for l in range(1, int(desc.levels)):
         g.off[l][0], g.off[l][1] = int(desc.off[l][0]), int(desc.off[l][1])
     return g
+
+
+def _is_forest(desc) -> bool:
+    return hasattr(desc, "org") and hasattr(desc, "level")
+
+
+def _forest(desc) -> _Forest:
+    f = _Forest()
+    K = len(desc.level)
+    if K > MAX_PATCHES:
+        raise ValueError(f"{K} patches, at most {MAX_PATCHES}")
+    f.n, f.patches = int(desc.n), K
+    f.x0, f.y0, f.h0 = float(desc.x0), float(desc.y0), float(desc.h0)
+    for p in range(K):
+        f.level[p] = int(desc.level[p])
+        f.org[p][0], f.org[p][1] = int(desc.org[p][0]), int(desc.org[p][1])
+    return f
 
 
 def _dp(a: np.ndarray):
@@ -126,6 +170,8 @@ def cell_integrals_potential(a: float, b: float, c: float, d: float) -> np.ndarr
 
 
 def validate(desc) -> bool:
+    if _is_forest(desc):
+        return _load().oracle_forest_validate(ctypes.byref(_forest(desc))) == 0
     return _load().oracle_validate(ctypes.byref(_nest(desc))) == 0
 
 
@@ -138,8 +184,12 @@ def prepare(desc, sigma):
     sig = [np.zeros((n, n)) for _ in range(L)]
     dsx = [np.zeros((n, n)) for _ in range(L)]
     dsy = [np.zeros((n, n)) for _ in range(L)]
-    rc = _load().oracle_prepare(ctypes.byref(_nest(desc)), _ptr_array(sin), _ptr_array(sig),
-                                _ptr_array(dsx), _ptr_array(dsy))
+    if _is_forest(desc):
+        rc = _load().oracle_forest_prepare(ctypes.byref(_forest(desc)), _ptr_array(sin), _ptr_array(sig),
+                                           _ptr_array(dsx), _ptr_array(dsy))
+    else:
+        rc = _load().oracle_prepare(ctypes.byref(_nest(desc)), _ptr_array(sin), _ptr_array(sig),
+                                    _ptr_array(dsx), _ptr_array(dsy))
     if rc:
         raise ValueError(f"invalid nest descriptor (oracle_prepare rc={rc})")
     return sig, dsx, dsy
@@ -156,7 +206,9 @@ def force_at(desc, sigma, levels, ii, jj, nthreads: int = 0, prepared=None):
     fx = np.zeros(nt)
     fy = np.zeros(nt)
     ip = ctypes.POINTER(ctypes.c_int)
-    rc = lib.oracle_force_targets(ctypes.byref(_nest(desc)), _ptr_array(sig), _ptr_array(dsx),
+    fn, g = ((lib.oracle_forest_force_targets, _forest(desc)) if _is_forest(desc)
+             else (lib.oracle_force_targets, _nest(desc)))
+    rc = fn(ctypes.byref(g), _ptr_array(sig), _ptr_array(dsx),
                                   _ptr_array(dsy), nt, lv.ctypes.data_as(ip), iv.ctypes.data_as(ip),
                                   jv.ctypes.data_as(ip), _dp(fx), _dp(fy), int(nthreads))
     if rc:
@@ -207,7 +259,9 @@ def potential_at(desc, sigma, levels, ii, jj, nthreads: int = 0, prepared=None):
     jv = np.ascontiguousarray(jj, dtype=np.int32)
     out = np.zeros(len(lv))
     ip = ctypes.POINTER(ctypes.c_int)
-    rc = lib.oracle_potential_targets(ctypes.byref(_nest(desc)), _ptr_array(sig), _ptr_array(dsx),
+    fn, g = ((lib.oracle_forest_potential_targets, _forest(desc)) if _is_forest(desc)
+             else (lib.oracle_potential_targets, _nest(desc)))
+    rc = fn(ctypes.byref(g), _ptr_array(sig), _ptr_array(dsx),
                                       _ptr_array(dsy), len(lv), lv.ctypes.data_as(ip), iv.ctypes.data_as(ip),
                                       jv.ctypes.data_as(ip), _dp(out), int(nthreads))
     if rc:

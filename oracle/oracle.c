@@ -247,17 +247,14 @@ int oracle_prepare(const oracle_nest *g, const double *const *sigma_in,
 
 /* ------------------------------------------------------------ direct sum */
 
-/* Force at one target point from the prepared source fields of one level.
- * The corner antiderivatives are evaluated on the level's (n+1)^2 edge
- * lattice one edge row at a time, and every cell takes its double difference. */
-static void sum_level(const oracle_nest *g, int s, const double *sig, const double *dsx,
+/* Force at one target point from the prepared source fields of one patch of
+ * n x n cells of size h with lower-left corner (X, Y).  The corner
+ * antiderivatives are evaluated on the patch's (n+1)^2 edge lattice one edge
+ * row at a time, and every cell takes its double difference. */
+static void sum_patch(int n, double X, double Y, double h, const double *sig, const double *dsx,
                       const double *dsy, double xt, double yt, double *row_lo, double *row_hi,
                       double *fx, double *fy)
 {
-    const int n = g->n;
-    const double h = level_h(g, s);
-    double X, Y;
-    level_origin(g, s, &X, &Y);
     double ax = 0.0, ay = 0.0;
     for (int i = 0; i <= n; ++i)
         corner_values(X + i * h - xt, Y - yt, row_lo + 5 * i);
@@ -287,6 +284,15 @@ static void sum_level(const oracle_nest *g, int s, const double *sig, const doub
     }
     *fx += ax;
     *fy += ay;
+}
+
+static void sum_level(const oracle_nest *g, int s, const double *sig, const double *dsx,
+                      const double *dsy, double xt, double yt, double *row_lo, double *row_hi,
+                      double *fx, double *fy)
+{
+    double X, Y;
+    level_origin(g, s, &X, &Y);
+    sum_patch(g->n, X, Y, level_h(g, s), sig, dsx, dsy, xt, yt, row_lo, row_hi, fx, fy);
 }
 
 /* Forces at nt targets (level tl[k], cell ti[k], tj[k]) from prepared fields.
@@ -337,16 +343,12 @@ int oracle_force_targets(const oracle_nest *g, const double *const *sig, const d
     return fail ? -3 : 0;
 }
 
-/* Potential at one target point from the prepared fields of one level (the
- * same edge-lattice walk as sum_level). */
-static void sum_level_potential(const oracle_nest *g, int s, const double *sig, const double *dsx,
+/* Potential at one target point from the prepared fields of one patch (the
+ * same edge-lattice walk as sum_patch). */
+static void sum_patch_potential(int n, double X, double Y, double h, const double *sig, const double *dsx,
                                 const double *dsy, double xt, double yt, double *row_lo, double *row_hi,
                                 double *phi)
 {
-    const int n = g->n;
-    const double h = level_h(g, s);
-    double X, Y;
-    level_origin(g, s, &X, &Y);
     double acc = 0.0;
     for (int i = 0; i <= n; ++i)
         corner_values_potential(X + i * h - xt, Y - yt, row_lo + 3 * i);
@@ -373,6 +375,15 @@ static void sum_level_potential(const oracle_nest *g, int s, const double *sig, 
         row_hi = t;
     }
     *phi += acc;
+}
+
+static void sum_level_potential(const oracle_nest *g, int s, const double *sig, const double *dsx,
+                                const double *dsy, double xt, double yt, double *row_lo, double *row_hi,
+                                double *phi)
+{
+    double X, Y;
+    level_origin(g, s, &X, &Y);
+    sum_patch_potential(g->n, X, Y, level_h(g, s), sig, dsx, dsy, xt, yt, row_lo, row_hi, phi);
 }
 
 /* Potential at nt targets (level tl[k], cell ti[k], tj[k]) from prepared
@@ -419,6 +430,217 @@ int oracle_potential_targets(const oracle_nest *g, const double *const *sig, con
         free(buf);
     }
     return fail ? -3 : 0;
+}
+
+/* ------------------------------------------------------------------ forests */
+/* Several patches per level (Sec. 2.1: Omega^l_k, k = 1..K^l).  Every patch has
+ * n x n cells of its level's size h0/2^l; patch p's lower-left corner is
+ * (x0, y0) + org[p] cells of its level.  Readings (the paper allows any patch
+ * extents; the patches here share n so that one transform size serves all):
+ *  - patches are listed coarsest level first, level 0 first of all;
+ *  - a patch of level l >= 1 starts on a cell edge of level l-1 (org even) and
+ *    lies inside the union of the level l-1 patches; it may straddle several;
+ *  - patches of one level do not overlap (they may share edges);
+ *  - a cell of level l under a level l+1 patch is covered: no mass, no force
+ *    (reported as 0), and for the slopes it takes the mean of its children;
+ *  - slopes as for nests: central inside each patch, one-sided inward on the
+ *    patch's first and last cell of every row and column (also where the
+ *    patch touches another patch of its level). */
+#define ORACLE_MAX_PATCHES 16
+
+typedef struct {
+    int n, patches;
+    double x0, y0, h0;
+    int level[ORACLE_MAX_PATCHES];
+    int org[ORACLE_MAX_PATCHES][2];
+} oracle_forest;
+
+static double patch_h(const oracle_forest *f, int p) { return ldexp(f->h0, -f->level[p]); }
+
+static void patch_origin(const oracle_forest *f, int p, double *X, double *Y)
+{
+    const double h = patch_h(f, p);
+    *X = f->x0 + f->org[p][0] * h;
+    *Y = f->y0 + f->org[p][1] * h;
+}
+
+/* The patch q of level(p)+1 that covers cell (i, j) of patch p, or -1; (fx, fy):
+ * q's corner in p's cells. */
+static int forest_child(const oracle_forest *f, int p, int i, int j, int *fx, int *fy)
+{
+    const int half = f->n / 2;
+    for (int q = 0; q < f->patches; ++q) {
+        if (f->level[q] != f->level[p] + 1)
+            continue;
+        const int cx = f->org[q][0] / 2 - f->org[p][0], cy = f->org[q][1] / 2 - f->org[p][1];
+        if (i >= cx && i < cx + half && j >= cy && j < cy + half) {
+            *fx = cx;
+            *fy = cy;
+            return q;
+        }
+    }
+    return -1;
+}
+
+int oracle_forest_validate(const oracle_forest *f)
+{
+    const int n = f->n, K = f->patches;
+    if (n < 4 || (n & 1) || K < 1 || K > ORACLE_MAX_PATCHES || !(f->h0 > 0.0) || f->level[0] != 0)
+        return -1;
+    for (int p = 1; p < K; ++p) {
+        if (f->level[p] < f->level[p - 1] || f->level[p] > f->level[p - 1] + 1 || f->level[p] > 20)
+            return -1;
+        if (f->level[p] > 0 && ((f->org[p][0] & 1) || (f->org[p][1] & 1)))
+            return -1;
+    }
+    for (int p = 0; p < K; ++p)
+        for (int q = p + 1; q < K; ++q)
+            if (f->level[p] == f->level[q] && abs(f->org[p][0] - f->org[q][0]) < n &&
+                abs(f->org[p][1] - f->org[q][1]) < n)
+                return -2; /* overlapping patches of one level */
+    for (int p = 0; p < K; ++p) {
+        if (f->level[p] == 0)
+            continue;
+        const int half = n / 2;
+        for (int y = f->org[p][1] / 2; y < f->org[p][1] / 2 + half; ++y)
+            for (int x = f->org[p][0] / 2; x < f->org[p][0] / 2 + half; ++x) {
+                int inside = 0;
+                for (int q = 0; q < K && !inside; ++q)
+                    inside = f->level[q] == f->level[p] - 1 && x >= f->org[q][0] && x < f->org[q][0] + n &&
+                             y >= f->org[q][1] && y < f->org[q][1] + n;
+                if (!inside)
+                    return -3; /* a patch outside the coarser level */
+            }
+    }
+    return 0;
+}
+
+/* As oracle_prepare, per patch. */
+int oracle_forest_prepare(const oracle_forest *f, const double *const *sigma_in, double **sig, double **dsx,
+                          double **dsy)
+{
+    if (oracle_forest_validate(f))
+        return -1;
+    const int n = f->n, K = f->patches;
+    for (int p = 0; p < K; ++p)
+        memcpy(sig[p], sigma_in[p], sizeof(double) * (size_t)n * n);
+    /* covered cells take the mean of their children, finest patches first */
+    for (int p = K - 1; p >= 0; --p)
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                int cx, cy;
+                const int q = forest_child(f, p, i, j, &cx, &cy);
+                if (q < 0)
+                    continue;
+                const int ci = 2 * (i - cx), cj = 2 * (j - cy);
+                const double *c = sig[q];
+                sig[p][(size_t)j * n + i] = 0.25 * (c[(size_t)cj * n + ci] + c[(size_t)cj * n + ci + 1] +
+                                                    c[(size_t)(cj + 1) * n + ci] + c[(size_t)(cj + 1) * n + ci + 1]);
+            }
+    for (int p = 0; p < K; ++p) {
+        const double h = patch_h(f, p);
+        const double *v = sig[p];
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                double sx, sy;
+                if (i == 0)
+                    sx = (v[(size_t)j * n + 1] - v[(size_t)j * n]) / h;
+                else if (i == n - 1)
+                    sx = (v[(size_t)j * n + n - 1] - v[(size_t)j * n + n - 2]) / h;
+                else
+                    sx = (v[(size_t)j * n + i + 1] - v[(size_t)j * n + i - 1]) / (2.0 * h);
+                if (j == 0)
+                    sy = (v[(size_t)n + i] - v[i]) / h;
+                else if (j == n - 1)
+                    sy = (v[(size_t)(n - 1) * n + i] - v[(size_t)(n - 2) * n + i]) / h;
+                else
+                    sy = (v[(size_t)(j + 1) * n + i] - v[(size_t)(j - 1) * n + i]) / (2.0 * h);
+                dsx[p][(size_t)j * n + i] = sx;
+                dsy[p][(size_t)j * n + i] = sy;
+            }
+    }
+    for (int p = 0; p < K; ++p)
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                int cx, cy;
+                if (forest_child(f, p, i, j, &cx, &cy) >= 0) {
+                    sig[p][(size_t)j * n + i] = 0.0;
+                    dsx[p][(size_t)j * n + i] = 0.0;
+                    dsy[p][(size_t)j * n + i] = 0.0;
+                }
+            }
+    return 0;
+}
+
+/* Forces (want_phi = 0) or the potential (want_phi = 1, into fx) at nt targets
+ * (patch tp[k], cell ti[k], tj[k]) from prepared fields; covered targets get 0. */
+static int forest_targets(const oracle_forest *f, const double *const *sig, const double *const *dsx,
+                          const double *const *dsy, long nt, const int *tp, const int *ti, const int *tj,
+                          double *fx, double *fy, int nthreads, int want_phi)
+{
+    if (oracle_forest_validate(f))
+        return -1;
+    const int n = f->n, K = f->patches;
+    for (long k = 0; k < nt; ++k)
+        if (tp[k] < 0 || tp[k] >= K || ti[k] < 0 || ti[k] >= n || tj[k] < 0 || tj[k] >= n)
+            return -2;
+#ifdef _OPENMP
+    if (nthreads > 0)
+        omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    int fail = 0;
+#pragma omp parallel
+    {
+        double *buf = (double *)malloc(sizeof(double) * 10 * (size_t)(n + 1));
+        if (!buf) {
+#pragma omp atomic write
+            fail = 1;
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (long k = 0; k < nt; ++k) {
+            if (!buf)
+                continue;
+            double ax = 0.0, ay = 0.0;
+            int cx, cy;
+            if (forest_child(f, tp[k], ti[k], tj[k], &cx, &cy) < 0) {
+                double X, Y;
+                patch_origin(f, tp[k], &X, &Y);
+                const double h = patch_h(f, tp[k]);
+                const double xt = X + (ti[k] + 0.5) * h, yt = Y + (tj[k] + 0.5) * h;
+                for (int s = 0; s < K; ++s) {
+                    double SX, SY;
+                    patch_origin(f, s, &SX, &SY);
+                    if (want_phi)
+                        sum_patch_potential(n, SX, SY, patch_h(f, s), sig[s], dsx[s], dsy[s], xt, yt, buf,
+                                            buf + 3 * (size_t)(n + 1), &ax);
+                    else
+                        sum_patch(n, SX, SY, patch_h(f, s), sig[s], dsx[s], dsy[s], xt, yt, buf,
+                                  buf + 5 * (size_t)(n + 1), &ax, &ay);
+                }
+            }
+            fx[k] = ax;
+            if (!want_phi)
+                fy[k] = ay;
+        }
+        free(buf);
+    }
+    return fail ? -3 : 0;
+}
+
+int oracle_forest_force_targets(const oracle_forest *f, const double *const *sig, const double *const *dsx,
+                                const double *const *dsy, long nt, const int *tp, const int *ti, const int *tj,
+                                double *fx, double *fy, int nthreads)
+{
+    return forest_targets(f, sig, dsx, dsy, nt, tp, ti, tj, fx, fy, nthreads, 0);
+}
+
+int oracle_forest_potential_targets(const oracle_forest *f, const double *const *sig, const double *const *dsx,
+                                    const double *const *dsy, long nt, const int *tp, const int *ti,
+                                    const int *tj, double *phi, int nthreads)
+{
+    return forest_targets(f, sig, dsx, dsy, nt, tp, ti, tj, phi, NULL, nthreads, 1);
 }
 
 /* Threads the OpenMP runtime would use (for reporting the CPU baseline). */

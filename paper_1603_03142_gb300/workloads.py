@@ -19,6 +19,13 @@ disks sigma_{D_n}) and the benchmark configurations:
            r = 0.95.
   config4: batches of concentric nests, N in {128..1024}, 1-4 levels.
   config5: Poisson request stream (serving).
+
+Forests (several patches per level, Sec. 2.1 Omega^l_k; Examples 3-4 of
+Sec. 3) are ``Forest`` objects: patch p has ``n`` x ``n`` cells of size
+h0/2^level[p] and its lower-left corner at (x0, y0) + org[p] cells of its
+level; patches are listed coarsest first.  A forest's ``levels`` attribute is
+its number of patches, so every per-level list (densities, forces) is a
+per-patch list.
 """
 from __future__ import annotations
 
@@ -77,6 +84,103 @@ class Nest:
 
     def key(self):
         return (self.n, self.levels, tuple(self.off))
+
+
+@dataclass
+class Forest:
+    """Several n x n patches per level (mirrors ``sgf_forest_desc``)."""
+    n: int
+    level: List[int]
+    org: List[Tuple[int, int]]
+    x0: float = -1.0
+    y0: float = -1.0
+    h0: float = 0.0  # 0 -> 2/n
+
+    def __post_init__(self):
+        if self.h0 == 0.0:
+            self.h0 = 2.0 / self.n
+        self.level = [int(v) for v in self.level]
+        self.org = [tuple(int(v) for v in o) for o in self.org]
+        if len(self.level) != len(self.org):
+            raise ValueError("one level and one corner per patch")
+
+    @property
+    def patches(self) -> int:
+        return len(self.level)
+
+    @property
+    def levels(self) -> int:  # per-patch lists stand where nests have per-level ones
+        return len(self.level)
+
+    def h(self, p: int) -> float:
+        return self.h0 / (1 << self.level[p])
+
+    def origin(self, p: int) -> Tuple[float, float]:
+        return self.x0 + self.org[p][0] * self.h(p), self.y0 + self.org[p][1] * self.h(p)
+
+    def centres(self, p: int):
+        X0, Y0 = self.origin(p)
+        c = (np.arange(self.n) + 0.5) * self.h(p)
+        Y, X = np.meshgrid(Y0 + c, X0 + c, indexing="ij")
+        return X, Y
+
+    def covered_mask(self, p: int) -> np.ndarray:
+        """True where patch p's cell lies under a patch of the next finer level."""
+        n, half = self.n, self.n // 2
+        m = np.zeros((n, n), dtype=bool)
+        for q in range(self.patches):
+            if self.level[q] != self.level[p] + 1:
+                continue
+            cx = self.org[q][0] // 2 - self.org[p][0]
+            cy = self.org[q][1] // 2 - self.org[p][1]
+            m[max(cy, 0):max(min(cy + half, n), 0), max(cx, 0):max(min(cx + half, n), 0)] = True
+        return m
+
+    def key(self):
+        return (self.n, tuple(self.level), tuple(self.org))
+
+    @staticmethod
+    def from_nest(nest: "Nest") -> "Forest":
+        """The one-patch-per-level nest as a forest (same cells, same order)."""
+        org, cx, cy = [], 0, 0
+        for l in range(nest.levels):
+            if l > 0:
+                cx, cy = 2 * (cx + nest.off[l][0]), 2 * (cy + nest.off[l][1])
+            org.append((cx, cy))
+        return Forest(n=nest.n, level=list(range(nest.levels)), org=org, x0=nest.x0, y0=nest.y0, h0=nest.h0)
+
+
+def example3_forest(n: int) -> Forest:
+    """Sec. 3, Example 3 exactly on Omega = [-1, 1]^2: level 0 of 2n cells across
+    [-1, 1] (cell 1/n) as six n x n tiles, columns x in [-1, 0] and [0, 1], rows
+    y in [-1.5, -0.5], [-0.5, 0.5], [0.5, 1.5]; level 1 the paper's two patches
+    [-0.75, -0.25] x [-0.25, 0.25] and [0.25, 0.75] x [-0.25, 0.25] (n cells of
+    1/(2n)).  The tile seams lie where the two disks have no mass, and cells
+    outside Omega carry none, so forces inside Omega are those of one level-0
+    patch over Omega; the paper's N is 2n."""
+    org0 = [(0, 0), (n, 0), (0, n), (n, n), (0, 2 * n), (n, 2 * n)]
+    org1 = [(n // 2, 5 * n // 2), (5 * n // 2, 5 * n // 2)]
+    return Forest(n=n, level=[0] * 6 + [1, 1], org=org0 + org1, x0=-1.0, y0=-1.5, h0=1.0 / n)
+
+
+def two_patch_forest(n: int) -> Forest:
+    """One level-0 patch [-1, 1]^2 (cell 2/n) and one level-1 patch over each disk of
+    Examples 3-4, [-1, 0] x [-0.5, 0.5] and [0, 1] x [-0.5, 0.5], sharing an edge."""
+    return Forest(n=n, level=[0, 1, 1], org=[(0, 0), (0, n // 2), (n, n // 2)])
+
+
+def example4_forest(n: int) -> Forest:
+    """Two disks, three levels (Sec. 3, Example 4): level 0 [-1, 1]^2 (cell 2/n);
+    level 1 as in two_patch_forest (the paper's 0.8-wide level-1 patches are not a
+    whole number of level-0 cells); level 2 exactly the paper's
+    [-0.75, -0.25] x [-0.25, 0.25] and [0.25, 0.75] x [-0.25, 0.25]."""
+    return Forest(n=n, level=[0, 1, 1, 2, 2],
+                  org=[(0, 0), (0, n // 2), (n, n // 2), (n // 2, 3 * n // 2), (5 * n // 2, 3 * n // 2)])
+
+
+def two_disk_density(forest, order: int = 5, alpha: float = math.sqrt(2.0) / 4.0) -> List[np.ndarray]:
+    """Examples 3-4: sigma_{D_order} disks of radius alpha centred at (-1/2, 0) and (1/2, 0)."""
+    return dn_density(forest, order, alpha, centres=((-0.5, 0.0), (0.5, 0.0)))
 
 
 def centred_nest(n: int, levels: int, centre=(0.0, 0.0), x0: float = -1.0, y0: float = -1.0,
