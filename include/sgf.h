@@ -85,11 +85,36 @@ typedef struct {
     int32_t off[SGF_MAX_LEVELS][2];
 } sgf_nest_desc;
 
+/* Forest descriptor (Sec. 2.1: domains Omega^l_k, K^l patches on level l, all
+ * patches of a level sharing its cell size h0/2^l; Examples 3-4 of Sec. 3).
+ * Every patch has n x n cells (n as for nests: one transform size serves the
+ * whole plan); patch p is of level level[p] and its lower-left corner lies at
+ * (x0, y0) + org[p] cells of that level.  Rules (checked; SGF_EINVAL otherwise):
+ *   - 1 <= patches <= SGF_MAX_PATCHES, listed coarsest first: level[0] = 0,
+ *     levels never decrease and never skip one, 2^level <= n/2;
+ *   - a patch of level >= 1 starts on a cell edge of the coarser level (both
+ *     org entries even) and lies inside the union of the coarser level's
+ *     patches (it may straddle several of them);
+ *   - patches of one level do not overlap (they may share edges).
+ * Cells under a patch of the next finer level are covered: no mass, output 0,
+ * and for the slopes they take the mean of their four children.  Slopes are
+ * one-sided on the first and last cell of every patch row and column (also
+ * where patches of one level touch).  A nest is the forest of its levels:
+ * level l's corner is twice the sum of (its parent's corner + off[l]). */
+#define SGF_MAX_PATCHES 16
+typedef struct {
+    int32_t n;
+    int32_t patches;
+    double x0, y0, h0;
+    int32_t level[SGF_MAX_PATCHES];
+    int32_t org[SGF_MAX_PATCHES][2];
+} sgf_forest_desc;
+
 typedef struct sgf_plan sgf_plan;
 
 /* Per-plan counts, for reporting.  All sizes in bytes. */
 typedef struct {
-    int32_t n, levels, precision;
+    int32_t n, levels, precision;  /* levels: patches of a forest plan */
     int32_t forward_slabs;      /* row-transformed source sets per solve (1 per level + Case-2 phases) */
     int32_t outputs;            /* column-pass outputs per solve (1 per level + Case-3 phases) */
     int32_t spectra_sets;       /* kernel-spectrum sets (Case 1 shared; one per Case-2/3 phase) */
@@ -138,6 +163,17 @@ sgf_status sgf_plan_create(const sgf_nest_desc *desc, sgf_precision precision, s
  * levels > 1, or SGF_PLAN_ZERO_RIM with SGF_PLAN_POTENTIAL. */
 sgf_status sgf_plan_create_ex(const sgf_nest_desc *desc, sgf_precision precision, uint32_t flags,
                               sgf_plan **out);
+
+/* As sgf_plan_create_ex for a forest.  Every ordered pair of patches (source,
+ * target) is one of Sec. 2.2's cases: the same patch (Case 1), another patch
+ * of the same level (Case 1 with a lattice offset), a finer source (Case 2) or
+ * a coarser one (Case 3).  Solves take per-patch arrays: sigma[p], fx[p],
+ * fy[p] (phi[p]) for p < patches, in descriptor order.  SGF_PLAN_ZERO_RIM
+ * needs patches == 1; SGF_BF16X needs n < SGF_MAX_N when patches > 1 (else
+ * SGF_EUNSUPPORTED); at most 64 covered rectangles in all (one per pair of
+ * overlapping patches of adjacent levels; SGF_EUNSUPPORTED beyond). */
+sgf_status sgf_plan_create_forest(const sgf_forest_desc *desc, sgf_precision precision, uint32_t flags,
+                                  sgf_plan **out);
 
 /* Waits for this plan's last solve and reports what the device recorded for
  * the solves since the previous check: SGF_ETIMEOUT when a bounded wait for
@@ -315,6 +351,10 @@ sgf_status sgf_plan_autotune(sgf_plan *plan, int32_t reps, void *stream, sgf_sch
  * for the descriptor, precision and flags; SGF_EINVAL for a NULL output. */
 sgf_status sgf_plan_estimate(const sgf_nest_desc *desc, sgf_precision precision, uint32_t flags,
                              size_t *workspace_bytes, size_t *spectra_bytes, size_t *build_bytes);
+
+/* sgf_plan_estimate for a forest (host only, no CUDA call). */
+sgf_status sgf_plan_estimate_forest(const sgf_forest_desc *desc, sgf_precision precision, uint32_t flags,
+                                    size_t *workspace_bytes, size_t *spectra_bytes, size_t *build_bytes);
 
 /* ---- Request loop (no paper counterpart: serving many force solves) ------
  * A server takes force requests with host input and output buffers and runs

@@ -1,14 +1,16 @@
 // sgf_api.cu -- host side of libsgf: validation, plans, the C ABI (include/sgf.h).
 //
-// A plan fixes the nest geometry and precision.  It owns
+// A plan fixes the geometry (a nest of one patch per level, or a forest of
+// several patches per level; a nest is kept as the forest of its levels) and
+// the precision.  It owns
 //   - the work lists of one solve (forward slabs, column outputs and their
 //     inputs, inverse-row contributions), uploaded once;
 //   - the solve workspace (restricted densities, forward and backward
 //     intermediates);
 //   - a reference to the kernel spectra, which plans made by sgf_plan_share
 //     hold in common.
-// One solve = (levels-1) restriction launches + row_fwd + col + row_inv, all on
-// the caller's stream.
+// One solve = one restriction launch per covered patch + row_fwd + col + row_inv,
+// all on the caller's stream.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -114,6 +116,15 @@ void spectra_release(Spectra *s)
     }
 }
 
+// The patches of a plan, coarsest level first (a nest: patch l = level l).
+struct Forest {
+    int n = 0, K = 0, R = 0;  // cells per side, patches, level-0 patches (the first R)
+    int depth = 1;            // levels
+    double x0 = 0.0, y0 = 0.0, h0 = 0.0;
+    int level[kMaxPatches] = {};
+    int org[kMaxPatches][2] = {};  // corner in cells of the patch's level, from (x0, y0)
+};
+
 struct SetKey {
     int cas, m, px, py, ax, ay;
     int fine;  // potential plans: the finer level of the pair (its cell size scales the tables); else 0
@@ -126,7 +137,7 @@ struct SetKey {
 }  // namespace
 
 struct sgf_plan {
-    sgf_nest_desc desc{};
+    Forest fo{};               // geometry
     sgf_precision prec = SGF_FP32;
     uint32_t flags = 0;
     bool merged = false;       // SGF_PLAN_ZERO_RIM: one forward field, merged spectra
@@ -135,7 +146,7 @@ struct sgf_plan {
     sgf_schedule sched{};      // tile schedule of the transform passes (autotuner)
     int *d_status = nullptr;   // device status word (STATUS_* bits)
     cudaEvent_t done = nullptr;  // recorded after every solve (sgf_plan_check)
-    int N = 0, logN = 0, L = 0, device = 0;
+    int N = 0, logN = 0, L = 0, device = 0;  // L: patches (the levels of a nest)
     size_t esize = 4;  // bytes per real
     Spectra *spec = nullptr;
     // host lists
@@ -148,7 +159,11 @@ struct sgf_plan {
     std::vector<ColGroup> groups;              // Case-3 output groups (k_col_g)
     std::vector<ColSum> sums;                  // chunked outputs (k_col_sum)
     size_t partial_elems = 0;                  // complex elements of the chunk accumulators
-    int contrib_begin[kMaxLevels + 1] = {};
+    int contrib_begin[kMaxPatches + 1] = {};
+    std::vector<CoverRect> cover;               // covered rectangles, by patch
+    int cover_begin[kMaxPatches + 1] = {};
+    int restrict_slot[kMaxPatches] = {};        // slot of a covered patch's restricted density, or -1
+    int restricted = 0;                         // covered patches (restriction launches per solve)
     std::vector<GenSet> sets;
     size_t fwd_elems = 0, bwd_elems = 0;  // complex elements
     // device memory owned by this plan
@@ -163,7 +178,7 @@ struct sgf_plan {
     const ColSum *d_sums = nullptr;
     void *d_partial = nullptr;
     void *d_fwd = nullptr, *d_bwd = nullptr;
-    void *d_restricted = nullptr;  // (L-1) * N * N reals
+    void *d_restricted = nullptr;  // restricted * N * N reals
     // host-buffer solve staging (allocated on first sgf_solve_host)
     void *d_stage = nullptr;
     size_t workspace_bytes = 0;
@@ -210,12 +225,12 @@ struct sgf_batch {
 
 namespace {
 
-sgf_status check_flags(const sgf_nest_desc *d, uint32_t flags)
+sgf_status check_flags(int patches, uint32_t flags)
 {
     if (flags & ~(SGF_PLAN_ZERO_RIM | SGF_PLAN_POTENTIAL))
         return fail(SGF_EINVAL, "unknown plan flags 0x%x", flags);
-    if ((flags & SGF_PLAN_ZERO_RIM) && d->levels != 1)
-        return fail(SGF_EINVAL, "SGF_PLAN_ZERO_RIM needs a single level (levels = %d)", d->levels);
+    if ((flags & SGF_PLAN_ZERO_RIM) && patches != 1)
+        return fail(SGF_EINVAL, "SGF_PLAN_ZERO_RIM needs a single level and patch (%d patches)", patches);
     if ((flags & SGF_PLAN_ZERO_RIM) && (flags & SGF_PLAN_POTENTIAL))
         return fail(SGF_EINVAL, "SGF_PLAN_ZERO_RIM and SGF_PLAN_POTENTIAL do not combine");
     return SGF_OK;
@@ -250,13 +265,146 @@ sgf_status validate(const sgf_nest_desc *d, sgf_precision prec)
     return SGF_OK;
 }
 
-// Corner of level l relative to level 0's corner, in units of level `unit`'s cell.
-long corner_units(const sgf_nest_desc *d, int l, int unit, int axis)
+// The nest as the forest of its levels: level l's corner, in its own cells,
+// is twice (the parent's corner plus off[l]).
+Forest forest_of_nest(const sgf_nest_desc *d)
 {
-    long acc = 0;  // in units of the finest level involved (2^unit scale)
-    for (int k = 1; k <= l; ++k)
-        acc += (long)d->off[k][axis] << (unit - (k - 1));
-    return acc;
+    Forest f;
+    f.n = d->n;
+    f.K = d->levels;
+    f.R = 1;
+    f.depth = d->levels;
+    f.x0 = d->x0;
+    f.y0 = d->y0;
+    f.h0 = d->h0;
+    long cx = 0, cy = 0;
+    for (int l = 0; l < d->levels; ++l) {
+        if (l > 0) {
+            cx = 2 * (cx + d->off[l][0]);
+            cy = 2 * (cy + d->off[l][1]);
+        }
+        f.level[l] = l;
+        f.org[l][0] = (int)cx;
+        f.org[l][1] = (int)cy;
+    }
+    return f;
+}
+
+// Area of the overlap of [ax, ax + an) x [ay, ay + an) and [bx, bx + bn) x [by, by + bn).
+long long overlap_area(long ax, long ay, long an, long bx, long by, long bn)
+{
+    const long w = std::min(ax + an, bx + bn) - std::max(ax, bx);
+    const long h = std::min(ay + an, by + bn) - std::max(ay, by);
+    return w > 0 && h > 0 ? (long long)w * h : 0;
+}
+
+// Forest rules (Sec. 2.1, Omega^l_k): patches coarsest first with level 0 first
+// of all and no level skipped; a patch of level >= 1 starts on a cell edge of the
+// coarser level (even corner) and lies inside the union of that level's patches
+// (it may straddle several); patches of one level do not overlap (edges may be
+// shared); 2^level <= n/2 as for nests.
+sgf_status validate_forest(const sgf_forest_desc *d, sgf_precision prec, Forest *out)
+{
+    if (!d)
+        return fail(SGF_EINVAL, "descriptor is NULL");
+    if (prec != SGF_FP64 && prec != SGF_FP32 && prec != SGF_BF16X)
+        return fail(SGF_EINVAL, "unknown precision %d", (int)prec);
+    const int n = d->n, K = d->patches;
+    if (n < SGF_MIN_N || (n & (n - 1)) != 0)
+        return fail(SGF_EINVAL, "n = %d must be a power of two >= %d", n, SGF_MIN_N);
+    if (K < 1 || K > SGF_MAX_PATCHES)
+        return fail(SGF_EINVAL, "patches = %d outside [1, %d]", K, SGF_MAX_PATCHES);
+    if (!(d->h0 > 0.0) || !std::isfinite(d->h0) || !std::isfinite(d->x0) || !std::isfinite(d->y0))
+        return fail(SGF_EINVAL, "h0 must be positive and x0, y0, h0 finite");
+    if (d->level[0] != 0)
+        return fail(SGF_EINVAL, "patch 0 must be of level 0 (patches are listed coarsest first)");
+    int depth = 1;
+    for (int p = 0; p < K; ++p) {
+        if (p > 0 && (d->level[p] < d->level[p - 1] || d->level[p] > d->level[p - 1] + 1))
+            return fail(SGF_EINVAL, "patch %d: levels must not decrease nor skip a level", p);
+        if (d->level[p] >= SGF_MAX_LEVELS || (1 << d->level[p]) > n / 2)
+            return fail(SGF_EINVAL, "patch %d: level %d too deep for n = %d (need 2^level <= n/2)", p, d->level[p], n);
+        for (int a = 0; a < 2; ++a)
+            if (d->org[p][a] < -(1 << 24) || d->org[p][a] > (1 << 24))
+                return fail(SGF_EINVAL, "patch %d: corner %d outside +-2^24 cells", p, d->org[p][a]);
+        if (d->level[p] > 0 && ((d->org[p][0] & 1) || (d->org[p][1] & 1)))
+            return fail(SGF_EINVAL, "patch %d: corner (%d, %d) not on a cell edge of level %d", p, d->org[p][0],
+                        d->org[p][1], d->level[p] - 1);
+        depth = std::max(depth, d->level[p] + 1);
+    }
+    for (int p = 0; p < K; ++p)
+        for (int q = p + 1; q < K; ++q)
+            if (d->level[p] == d->level[q] &&
+                overlap_area(d->org[p][0], d->org[p][1], n, d->org[q][0], d->org[q][1], n) > 0)
+                return fail(SGF_EINVAL, "patches %d and %d of level %d overlap", p, q, d->level[p]);
+    for (int p = 0; p < K; ++p) {
+        if (d->level[p] == 0)
+            continue;
+        const long fx = d->org[p][0] / 2, fy = d->org[p][1] / 2, half = n / 2;
+        long long in = 0;  // the coarser level's patches do not overlap: areas add up
+        for (int q = 0; q < K; ++q)
+            if (d->level[q] == d->level[p] - 1)
+                in += overlap_area(fx, fy, half, d->org[q][0], d->org[q][1], n);
+        if (in != (long long)half * half)
+            return fail(SGF_EINVAL, "patch %d lies partly outside the patches of level %d", p, d->level[p] - 1);
+    }
+    if (n > SGF_MAX_N)
+        return fail(SGF_EUNSUPPORTED, "n = %d above SGF_MAX_N = %d", n, SGF_MAX_N);
+    if (prec == SGF_FP64 && n > SGF_MAX_N_FP64)
+        return fail(SGF_EUNSUPPORTED, "n = %d above SGF_MAX_N_FP64 = %d", n, SGF_MAX_N_FP64);
+    if (prec == SGF_BF16X && n == SGF_MAX_N && K > 1)
+        return fail(SGF_EUNSUPPORTED, "SGF_BF16X plans of more than one patch need n < %d", SGF_MAX_N);
+    if (out) {
+        Forest f;
+        f.n = n;
+        f.K = K;
+        f.depth = depth;
+        f.x0 = d->x0;
+        f.y0 = d->y0;
+        f.h0 = d->h0;
+        for (int p = 0; p < K; ++p) {
+            f.level[p] = d->level[p];
+            f.org[p][0] = d->org[p][0];
+            f.org[p][1] = d->org[p][1];
+            f.R += d->level[p] == 0 ? 1 : 0;
+        }
+        *out = f;
+    }
+    return SGF_OK;
+}
+
+// Covered rectangles of every patch (one per overlapping finer patch) and the
+// restriction slots of the covered patches.
+sgf_status build_cover(sgf_plan *p)
+{
+    const Forest &f = p->fo;
+    const int N = f.n, half = N / 2;
+    p->cover.clear();
+    p->restricted = 0;
+    for (int s = 0; s < f.K; ++s) {
+        p->cover_begin[s] = (int)p->cover.size();
+        for (int q = 0; q < f.K; ++q) {
+            if (f.level[q] != f.level[s] + 1)
+                continue;
+            const int fx = f.org[q][0] / 2 - f.org[s][0], fy = f.org[q][1] / 2 - f.org[s][1];
+            CoverRect r{};
+            r.x0 = std::max(fx, 0);
+            r.y0 = std::max(fy, 0);
+            r.x1 = std::min(fx + half, N);
+            r.y1 = std::min(fy + half, N);
+            if (r.x0 >= r.x1 || r.y0 >= r.y1)
+                continue;
+            r.fine = q;
+            r.fx = fx;
+            r.fy = fy;
+            p->cover.push_back(r);
+        }
+        p->restrict_slot[s] = (int)p->cover.size() > p->cover_begin[s] ? p->restricted++ : -1;
+    }
+    p->cover_begin[f.K] = (int)p->cover.size();
+    if ((int)p->cover.size() > kMaxCover)
+        return fail(SGF_EUNSUPPORTED, "%d covered rectangles, at most %d", (int)p->cover.size(), kMaxCover);
+    return SGF_OK;
 }
 
 // Lists of a zero-rim single-level plan: one slab of sigma alone, one output,
@@ -271,14 +419,14 @@ void build_lists_merged(sgf_plan *p)
     g.m = 1;
     p->sets.push_back(g);
     FwdSlab sl{};
-    sl.level = 0;
+    sl.patch = 0;
     sl.m = 1;
     sl.rows = N;
     sl.off = 0;
     p->slabs.push_back(sl);
     p->fwd_elems = (size_t)(N + 1) * N;
     ColOutput o{};
-    o.level = 0;
+    o.patch = 0;
     o.rows = N;
     o.in_begin = 0;
     o.in_count = 1;
@@ -309,13 +457,20 @@ constexpr int kCase3Group = 8;
 // deep nests) is split into chunks that run in parallel.
 constexpr int kChunkInputs = 16;
 
-// Build all host-side lists of a plan (no CUDA calls).
+// Build all host-side lists of a plan (no CUDA calls).  Every ordered pair of
+// patches (source s, target t) contributes:
+//   same patch              Case 1, the shared quarter-stored set
+//   same level, other patch Case 1 with the lattice offset A = corner_s - corner_t,
+//                           run as Case 2 with m = 1 (a full complex set)
+//   s finer (Case 2)        m^2 source phases into t's main output
+//   s coarser (Case 3)      m^2 target-phase outputs of N/m rows each
 void build_lists(sgf_plan *p)
 {
     if (p->merged) {
         build_lists_merged(p);
         return;
     }
+    const Forest &fo = p->fo;
     const int N = p->N, L = p->L, P = 2 * N;
     const size_t T = p->esize, Cb = 2 * p->esize;
     std::map<SetKey, int> set_index;
@@ -334,7 +489,7 @@ void build_lists(sgf_plan *p)
         g.py = py;
         g.ax = ax;
         g.ay = ay;
-        g.h = p->pot ? std::ldexp(p->desc.h0, -fine) : 0.0;
+        g.h = p->pot ? std::ldexp(fo.h0, -fine) : 0.0;
         const int idx = (int)p->sets.size();
         p->sets.push_back(g);
         const size_t nt = (size_t)spec_tables(g.kind);
@@ -342,12 +497,12 @@ void build_lists(sgf_plan *p)
         set_index[k] = idx;
         return idx;
     };
-    // forward slabs: whole levels, then Case-2 phases
+    // forward slabs: whole patches, then the Case-2 phases of every finer source
     std::vector<int> slab_full(L);
-    std::map<std::tuple<int, int, int, int>, int> slab_phase;  // (s, t, px, py)
+    std::map<std::tuple<int, int, int, int>, int> slab_phase;  // (s, m, px, py)
     auto add_slab = [&](int s, int m, int px, int py) {
         FwdSlab sl{};
-        sl.level = s;
+        sl.patch = s;
         sl.m = m;
         sl.px = px;
         sl.py = py;
@@ -360,16 +515,19 @@ void build_lists(sgf_plan *p)
     for (int s = 0; s < L; ++s)
         slab_full[s] = add_slab(s, 1, 0, 0);
     for (int s = 0; s < L; ++s)
-        for (int t = 0; t < s; ++t) {
-            const int m = 1 << (s - t);
+        for (int t = 0; t < L; ++t) {
+            if (fo.level[s] <= fo.level[t])
+                continue;
+            const int m = 1 << (fo.level[s] - fo.level[t]);
             for (int py = 0; py < m; ++py)
                 for (int px = 0; px < m; ++px)
-                    slab_phase[{s, t, px, py}] = add_slab(s, m, px, py);
+                    if (!slab_phase.count({s, m, px, py}))
+                        slab_phase[{s, m, px, py}] = add_slab(s, m, px, py);
         }
     // column outputs
     auto add_output = [&](int t, int rows) {
         ColOutput o{};
-        o.level = t;
+        o.patch = t;
         o.rows = rows;
         o.in_begin = (int)p->ins.size();
         o.in_count = 0;
@@ -389,35 +547,48 @@ void build_lists(sgf_plan *p)
     std::vector<int> main_out(L);
     std::map<std::pair<int, int>, int> c3_base;  // (s, t) -> first output
     for (int t = 0; t < L; ++t) {
+        const int lt = fo.level[t];
         main_out[t] = add_output(t, N);
-        add_input(main_out[t], slab_full[t], get_set(1, 1, 0, 0, 0, 0, t));
-        for (int s = t + 1; s < L; ++s) {  // Case 2: finer sources
-            const int m = 1 << (s - t);
-            const int ax = (int)(corner_units(&p->desc, s, s, 0) - corner_units(&p->desc, t, s, 0));
-            const int ay = (int)(corner_units(&p->desc, s, s, 1) - corner_units(&p->desc, t, s, 1));
+        add_input(main_out[t], slab_full[t], get_set(1, 1, 0, 0, 0, 0, lt));
+        for (int s = 0; s < L; ++s) {  // other patches of the same level: Case 1 with an offset
+            if (s == t || fo.level[s] != lt)
+                continue;
+            add_input(main_out[t], slab_full[s],
+                      get_set(2, 1, 0, 0, fo.org[s][0] - fo.org[t][0], fo.org[s][1] - fo.org[t][1], lt));
+        }
+        for (int s = 0; s < L; ++s) {  // Case 2: finer sources, A = corner_s - corner_t in s cells
+            const int ls = fo.level[s];
+            if (ls <= lt)
+                continue;
+            const int m = 1 << (ls - lt);
+            const int ax = fo.org[s][0] - fo.org[t][0] * m, ay = fo.org[s][1] - fo.org[t][1] * m;
             for (int py = 0; py < m; ++py)
                 for (int px = 0; px < m; ++px)
-                    add_input(main_out[t], slab_phase[{s, t, px, py}], get_set(2, m, px, py, ax, ay, s));
+                    add_input(main_out[t], slab_phase[{s, m, px, py}], get_set(2, m, px, py, ax, ay, ls));
         }
-        for (int s = 0; s < t; ++s) {  // Case 3: coarser sources, one output per target phase
-            const int m = 1 << (t - s);
-            const int ax = (int)(corner_units(&p->desc, t, t, 0) - corner_units(&p->desc, s, t, 0));
-            const int ay = (int)(corner_units(&p->desc, t, t, 1) - corner_units(&p->desc, s, t, 1));
+        for (int s = 0; s < L; ++s) {  // Case 3: coarser sources, one output per target phase
+            const int ls = fo.level[s];
+            if (ls >= lt)
+                continue;
+            const int m = 1 << (lt - ls);
+            const int ax = fo.org[t][0] - fo.org[s][0] * m, ay = fo.org[t][1] - fo.org[s][1] * m;
             for (int py = 0; py < m; ++py)
                 for (int px = 0; px < m; ++px) {
                     const int o = add_output(t, N / m);
                     if (py == 0 && px == 0)
                         c3_base[{s, t}] = o;
-                    add_input(o, slab_full[s], get_set(3, m, px, py, ax, ay, t));
+                    add_input(o, slab_full[s], get_set(3, m, px, py, ax, ay, lt));
                 }
         }
     }
-    // inverse-row contributions per target level
+    // inverse-row contributions per target patch
     for (int t = 0; t < L; ++t) {
         p->contrib_begin[t] = (int)p->contribs.size();
         p->contribs.push_back(RowContrib{1, 0, main_out[t], 0});
-        for (int s = 0; s < t; ++s) {
-            const int m = 1 << (t - s);
+        for (int s = 0; s < L; ++s) {
+            if (fo.level[s] >= fo.level[t])
+                continue;
+            const int m = 1 << (fo.level[t] - fo.level[s]);
             for (int px = 0; px < m; ++px)
                 p->contribs.push_back(RowContrib{m, px, c3_base[{s, t}] + px, 0});
         }
@@ -443,8 +614,10 @@ void build_lists(sgf_plan *p)
         if (std::find(main_out.begin(), main_out.end(), o) == main_out.end())
             p->work_all.push_back(ColWork{o, p->outs[o].in_begin, p->outs[o].in_count, -1});
     for (int t = 0; t < L; ++t) {
-        for (int s = 0; s < t; ++s) {  // sub-groups of at most kCase3Group outputs keep the columns parallel
-            const int m = 1 << (t - s);
+        for (int s = 0; s < L; ++s) {  // sub-groups of at most kCase3Group outputs keep the columns parallel
+            if (fo.level[s] >= fo.level[t])
+                continue;
+            const int m = 1 << (fo.level[t] - fo.level[s]);
             for (int q = 0; q < m * m; q += kCase3Group)
                 p->groups.push_back(ColGroup{c3_base[{s, t}] + q, std::min(kCase3Group, m * m - q)});
         }
@@ -473,8 +646,14 @@ void build_lists(sgf_plan *p)
             const size_t nt = (size_t)spec_tables(ci.kind);
             ab += spec_quarter(ci.kind) ? nt * (N + 1) * (N + 1) * T : nt * (N + 1) * P * Cb;  // padding not counted
         }
-    if (L > 1)
-        ab += (size_t)(L - 1) * (2 * (size_t)N * N * T + (size_t)N * N / 4 * 4 * T);  // restriction
+    // restriction: each covered patch reads its input and writes its copy, plus the children of its covered cells
+    for (int s = 0; s < L; ++s)
+        if (p->restrict_slot[s] >= 0) {
+            size_t cov = 0;
+            for (int k = p->cover_begin[s]; k < p->cover_begin[s + 1]; ++k)
+                cov += (size_t)(p->cover[k].x1 - p->cover[k].x0) * (p->cover[k].y1 - p->cover[k].y0);
+            ab += 2 * (size_t)N * N * T + 4 * cov * T;
+        }
     p->algorithmic_bytes = ab;
     (void)off;
 }
@@ -537,7 +716,7 @@ size_t workspace_of(const sgf_plan *p)
     align_push(blob, p->groups);
     align_push(blob, p->sums);
     return blob.size() + p->partial_elems * 2 * p->esize + (p->fwd_elems + p->bwd_elems) * 2 * p->esize +
-           (size_t)(p->L > 1 ? p->L - 1 : 0) * p->N * p->N * p->esize;
+           (size_t)p->restricted * p->N * p->N * p->esize;
 }
 
 // Allocate the plan's own device memory and upload its lists.
@@ -575,8 +754,8 @@ sgf_status plan_alloc_owned(sgf_plan *p)
         return cuda_fail(e, "cudaMalloc(forward intermediates)");
     if ((e = cudaMalloc(&p->d_bwd, p->bwd_elems * Cb)) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc(backward intermediates)");
-    if (p->L > 1) {
-        if ((e = cudaMalloc(&p->d_restricted, (size_t)(p->L - 1) * p->N * p->N * p->esize)) != cudaSuccess)
+    if (p->restricted > 0) {
+        if ((e = cudaMalloc(&p->d_restricted, (size_t)p->restricted * p->N * p->N * p->esize)) != cudaSuccess)
             return cuda_fail(e, "cudaMalloc(restricted densities)");
     }
     if ((e = cudaMalloc(&p->d_status, 16)) != cudaSuccess)
@@ -719,21 +898,22 @@ sgf_status mark(sgf_plan *p, cudaStream_t st)
     return SGF_OK;
 }
 
-// Inverse row passes of a solve.  Schedule row_inv0 = 0 / 2: level 0 (its own
-// main output alone) through k_row_inv1 with one / both components per CTA, the
-// finer levels (main output plus Case-3 phases) through k_row_inv; row_inv0 = 1:
-// every level through k_row_inv.
+// Inverse row passes of a solve over L patches, the first R of level 0.
+// Schedule row_inv0 = 0 / 2: the level-0 patches (their own main output alone)
+// through k_row_inv1 with one / both components per CTA, the finer patches
+// (main output plus Case-3 phases) through k_row_inv; row_inv0 = 1: every
+// patch through k_row_inv.
 template <typename T>
-cudaError_t launch_row_inv(int logN, int L, SolveArgs<T> a, cudaStream_t st, bool tc, int row_inv0)
+cudaError_t launch_row_inv(int logN, int L, int R, SolveArgs<T> a, cudaStream_t st, bool tc, int row_inv0)
 {
     a.level_base = 0;
     if (row_inv0 == 1)
         return launch_pass_n<T>(PASS_ROW_INV, logN, a, L, st, nullptr, tc);
-    cudaError_t e = launch_pass_n<T>(row_inv0 == 2 ? PASS_ROW_INV2 : PASS_ROW_INV1, logN, a, 1, st, nullptr, tc);
-    if (e != cudaSuccess || L == 1)
+    cudaError_t e = launch_pass_n<T>(row_inv0 == 2 ? PASS_ROW_INV2 : PASS_ROW_INV1, logN, a, R, st, nullptr, tc);
+    if (e != cudaSuccess || L == R)
         return e;
-    a.level_base = 1;
-    return launch_pass_n<T>(PASS_ROW_INV, logN, a, L - 1, st, nullptr, tc);
+    a.level_base = R;
+    return launch_pass_n<T>(PASS_ROW_INV, logN, a, L - R, st, nullptr, tc);
 }
 
 // Zero-rim column pass of the plan's schedule.
@@ -775,37 +955,58 @@ inline bool schedule_ok(const sgf_plan *p, const sgf_schedule &s)
     return !((s.row_inv0 == 1 || s.col_pass == 2) && p->tc && p->N == SGF_MAX_N);
 }
 
+// Geometry of a solve's arguments: sizes, covered rectangles, row contributions.
+template <typename T>
+void fill_geometry(const sgf_plan *p, SolveArgs<T> &a)
+{
+    a.N = p->N;
+    a.logN = p->logN;
+    a.L = p->L;
+    a.ncomp = p->pot ? 1 : 2;
+    for (int s = 0; s <= p->L; ++s) {
+        a.cover_begin[s] = p->cover_begin[s];
+        a.contrib_begin[s] = p->contrib_begin[s];
+    }
+    for (size_t k = 0; k < p->cover.size(); ++k)
+        a.cover[k] = p->cover[k];
+}
+
+// Densities of a solve: covered patches read their restricted copy (slot of
+// `restricted`), the others the caller's array; then the restriction launches,
+// finest patches first (launch = false: arguments only, for batches).
+template <typename T>
+cudaError_t fill_sources(const sgf_plan *p, const void *const *sigma, T *restricted, SolveArgs<T> &a, bool launch,
+                         cudaStream_t st)
+{
+    const size_t NN = (size_t)p->N * p->N;
+    for (int s = 0; s < p->L; ++s) {
+        a.sigma_in[s] = static_cast<const T *>(sigma[s]);
+        a.src[s] = p->restrict_slot[s] >= 0 ? restricted + (size_t)p->restrict_slot[s] * NN : a.sigma_in[s];
+    }
+    if (!launch)
+        return cudaSuccess;
+    for (int s = p->L - 1; s >= 0; --s)
+        if (p->restrict_slot[s] >= 0) {
+            cudaError_t e = launch_restrict<T>(a, s, st);
+            if (e != cudaSuccess)
+                return e;
+        }
+    return cudaSuccess;
+}
+
 template <typename T>
 sgf_status solve_impl(sgf_plan *p, const void *const *sigma, void *const *fx, void *const *fy,
                       cudaStream_t st)
 {
-    const int N = p->N, L = p->L;
+    const int L = p->L;
     SolveArgs<T> a{};
-    a.N = N;
-    a.logN = p->logN;
-    a.L = L;
-    a.ncomp = p->pot ? 1 : 2;
-    for (int l = 0; l < kMaxLevels; ++l) {
-        a.child_ox[l] = -1;
-        a.child_oy[l] = -1;
-    }
-    for (int l = 0; l + 1 < L; ++l) {
-        a.child_ox[l] = p->desc.off[l + 1][0];
-        a.child_oy[l] = p->desc.off[l + 1][1];
-    }
+    fill_geometry(p, a);
     sgf_status ms;
     if ((ms = mark(p, st)) != SGF_OK)
         return ms;
-    T *restricted = static_cast<T *>(p->d_restricted);
-    a.src[L - 1] = static_cast<const T *>(sigma[L - 1]);
-    for (int l = L - 2; l >= 0; --l) {
-        T *dst = restricted + (size_t)l * N * N;
-        cudaError_t e = launch_restrict<T>(a.src[l + 1], dst, static_cast<const T *>(sigma[l]), N,
-                                           p->desc.off[l + 1][0], p->desc.off[l + 1][1], st);
-        if (e != cudaSuccess)
-            return cuda_fail(e, "restriction launch");
-        a.src[l] = dst;
-    }
+    cudaError_t er = fill_sources<T>(p, sigma, static_cast<T *>(p->d_restricted), a, true, st);
+    if (er != cudaSuccess)
+        return cuda_fail(er, "restriction launch");
     for (int l = 0; l < L; ++l) {
         a.fx[l] = static_cast<T *>(fx[l]);
         a.fy[l] = fy ? static_cast<T *>(fy[l]) : nullptr;  // NULL: potential plans
@@ -825,8 +1026,6 @@ sgf_status solve_impl(sgf_plan *p, const void *const *sigma, void *const *fx, vo
     a.groups = p->d_groups;
     a.sums = p->d_sums;
     a.partial = static_cast<typename SolveArgs<T>::C *>(p->d_partial);
-    for (int l = 0; l <= L; ++l)
-        a.contrib_begin[l] = p->contrib_begin[l];
     cudaError_t e;
     if ((ms = mark(p, st)) != SGF_OK)
         return ms;
@@ -841,7 +1040,7 @@ sgf_status solve_impl(sgf_plan *p, const void *const *sigma, void *const *fx, vo
         return cuda_fail(e, "col launch");
     if ((ms = mark(p, st)) != SGF_OK)
         return ms;
-    if ((e = launch_row_inv<T>(p->logN, L, a, st, p->tc, p->sched.row_inv0)) != cudaSuccess)
+    if ((e = launch_row_inv<T>(p->logN, L, p->fo.R, a, st, p->tc, p->sched.row_inv0)) != cudaSuccess)
         return cuda_fail(e, "row_inv launch");
     if ((ms = mark(p, st)) != SGF_OK)
         return ms;
@@ -933,7 +1132,7 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 size_t noalloc_bytes(const sgf_plan *p)
 {
     const size_t Cb = 2 * p->esize;
-    return align256((size_t)(p->L > 1 ? p->L - 1 : 0) * p->N * p->N * p->esize) + align256(p->fwd_elems * Cb) +
+    return align256((size_t)p->restricted * p->N * p->N * p->esize) + align256(p->fwd_elems * Cb) +
            align256(p->bwd_elems * Cb) + align256(p->partial_elems * Cb);
 }
 
@@ -946,31 +1145,14 @@ sgf_status solve_noalloc_impl(sgf_plan *p, const void *const *sigma, void *const
     const int N = p->N, L = p->L;
     const size_t Cb = 2 * p->esize;
     T *restricted = reinterpret_cast<T *>(scratch);
-    unsigned char *fwd = scratch + align256((size_t)(L > 1 ? L - 1 : 0) * N * N * p->esize);
+    unsigned char *fwd = scratch + align256((size_t)p->restricted * N * N * p->esize);
     unsigned char *bwd = fwd + align256(p->fwd_elems * Cb);
     unsigned char *partial = bwd + align256(p->bwd_elems * Cb);
     SolveArgs<T> a{};
-    a.N = N;
-    a.logN = p->logN;
-    a.L = L;
-    a.ncomp = p->pot ? 1 : 2;
-    for (int l = 0; l < kMaxLevels; ++l) {
-        a.child_ox[l] = -1;
-        a.child_oy[l] = -1;
-    }
-    for (int l = 0; l + 1 < L; ++l) {
-        a.child_ox[l] = p->desc.off[l + 1][0];
-        a.child_oy[l] = p->desc.off[l + 1][1];
-    }
-    a.src[L - 1] = static_cast<const T *>(sigma[L - 1]);
-    for (int l = L - 2; l >= 0; --l) {
-        T *dst = restricted + (size_t)l * N * N;
-        cudaError_t e = launch_restrict<T>(a.src[l + 1], dst, static_cast<const T *>(sigma[l]), N,
-                                           p->desc.off[l + 1][0], p->desc.off[l + 1][1], st);
-        if (e != cudaSuccess)
-            return cuda_fail(e, "restriction launch");
-        a.src[l] = dst;
-    }
+    fill_geometry(p, a);
+    cudaError_t er = fill_sources<T>(p, sigma, restricted, a, true, st);
+    if (er != cudaSuccess)
+        return cuda_fail(er, "restriction launch");
     for (int l = 0; l < L; ++l) {
         a.fx[l] = static_cast<T *>(fx[l]);
         a.fy[l] = fy ? static_cast<T *>(fy[l]) : nullptr;  // NULL: potential plans
@@ -990,8 +1172,6 @@ sgf_status solve_noalloc_impl(sgf_plan *p, const void *const *sigma, void *const
     a.groups = p->d_groups;
     a.sums = p->d_sums;
     a.partial = reinterpret_cast<typename SolveArgs<T>::C *>(partial);
-    for (int l = 0; l <= L; ++l)
-        a.contrib_begin[l] = p->contrib_begin[l];
     cudaError_t e = p->merged ? launch_pass_n<T>(PASS_ROW_FWD_M, p->logN, a, 0, st, nullptr, p->tc)
                               : launch_pass_n<T>(PASS_ROW_FWD, p->logN, a, (int)p->items.size(), st, nullptr, p->tc);
     if (e != cudaSuccess)
@@ -999,7 +1179,7 @@ sgf_status solve_noalloc_impl(sgf_plan *p, const void *const *sigma, void *const
     e = launch_col<T>(p, a, st);
     if (e != cudaSuccess)
         return cuda_fail(e, "col launch");
-    if ((e = launch_row_inv<T>(p->logN, L, a, st, p->tc, p->sched.row_inv0)) != cudaSuccess)
+    if ((e = launch_row_inv<T>(p->logN, L, p->fo.R, a, st, p->tc, p->sched.row_inv0)) != cudaSuccess)
         return cuda_fail(e, "row_inv launch");
     if ((e = cudaEventRecord(p->done, st)) != cudaSuccess)
         return cuda_fail(e, "cudaEventRecord(solve completion)");
@@ -1013,24 +1193,11 @@ template <typename T>
 void fill_args(const sgf_plan *p, const void *const *sigma, void *const *fx, void *const *fy, SolveArgs<T> &a,
                const sgf_schedule &sc)
 {
-    const int N = p->N, L = p->L;
+    const int L = p->L;
     a = SolveArgs<T>{};
-    a.N = N;
-    a.logN = p->logN;
-    a.L = L;
-    a.ncomp = p->pot ? 1 : 2;
-    for (int l = 0; l < kMaxLevels; ++l) {
-        a.child_ox[l] = -1;
-        a.child_oy[l] = -1;
-    }
-    for (int l = 0; l + 1 < L; ++l) {
-        a.child_ox[l] = p->desc.off[l + 1][0];
-        a.child_oy[l] = p->desc.off[l + 1][1];
-    }
-    T *restricted = static_cast<T *>(p->d_restricted);
+    fill_geometry(p, a);
+    fill_sources<T>(p, sigma, static_cast<T *>(p->d_restricted), a, false, nullptr);
     for (int l = 0; l < L; ++l) {
-        a.sigma_in[l] = static_cast<const T *>(sigma[l]);
-        a.src[l] = l + 1 < L ? restricted + (size_t)l * N * N : static_cast<const T *>(sigma[l]);
         a.fx[l] = static_cast<T *>(fx[l]);
         a.fy[l] = fy ? static_cast<T *>(fy[l]) : nullptr;
     }
@@ -1049,8 +1216,6 @@ void fill_args(const sgf_plan *p, const void *const *sigma, void *const *fx, voi
     a.groups = p->d_groups;
     a.sums = p->d_sums;
     a.partial = static_cast<typename SolveArgs<T>::C *>(p->d_partial);
-    for (int l = 0; l <= L; ++l)
-        a.contrib_begin[l] = p->contrib_begin[l];
 }
 
 // The launches of one batch solve (the arguments are already on the device).
@@ -1191,30 +1356,34 @@ sgf_status batch_build(sgf_batch *bt)
                 maps.push_back(make_int2(k, q));
         g.n_sum = (int)(maps.size() - g.map_sum);
         bt->launches += g.n_sum > 0 ? 1 : 0;
-        g.map_inv1 = maps.size();
+        g.map_inv1 = maps.size();  // the level-0 patches of every plan, then the others
         for (int k : members[gi])
-            maps.push_back(make_int2(k, 0));
+            for (int r = 0; r < bt->plans[k]->fo.R; ++r)
+                maps.push_back(make_int2(k, r));
         g.n_inv1 = (int)(maps.size() - g.map_inv1);
         g.map_inv = maps.size();
         for (int k : members[gi])
-            for (int l = 1; l < bt->plans[k]->L; ++l)
+            for (int l = bt->plans[k]->fo.R; l < bt->plans[k]->L; ++l)
                 maps.push_back(make_int2(k, l));
         g.n_inv = (int)(maps.size() - g.map_inv);
         bt->launches += g.n_inv > 0 && g.sched.row_inv0 != 1 ? 4 : 3;
     }
-    // restriction depths: depth d restricts level L-2-d of every nest that has it
-    int maxL = 1;
+    // restriction depths: depth d restricts the covered patches of level depth-2-d of
+    // every plan (finest first within each plan; patches of one level are independent)
+    int maxD = 1;
     for (auto *p : bt->plans)
-        maxL = std::max(maxL, p->L);
-    for (int d = 0; d + 1 < maxL; ++d) {
+        maxD = std::max(maxD, p->fo.depth);
+    for (int d = 0; d + 1 < maxD; ++d) {
         bt->restrict_off.push_back(maps.size());
         int n = 0;
         for (int k = 0; k < count; ++k) {
-            const int l = bt->plans[k]->L - 2 - d;
-            if (l >= 0) {
-                maps.push_back(make_int2(k, l));
-                ++n;
-            }
+            const sgf_plan *p = bt->plans[k];
+            const int l = p->fo.depth - 2 - d;
+            for (int s = 0; s < p->L && l >= 0; ++s)
+                if (p->fo.level[s] == l && p->restrict_slot[s] >= 0) {
+                    maps.push_back(make_int2(k, s));
+                    ++n;
+                }
         }
         bt->restrict_jobs.push_back(n);
         bt->launches += n > 0 ? 1 : 0;
@@ -1362,8 +1531,8 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[8])
     if ((e = cudaMemsetAsync(buf, 0, 3 * (size_t)p->L * lal, st)) != cudaSuccess)
         return cuda_fail(e, "cudaMemset(autotune buffers)");
     auto base = static_cast<unsigned char *>(buf);
-    const void *ds[kMaxLevels];
-    void *dx[kMaxLevels], *dy[kMaxLevels];
+    const void *ds[kMaxPatches];
+    void *dx[kMaxPatches], *dy[kMaxPatches];
     for (int l = 0; l < p->L; ++l) {
         ds[l] = base + (size_t)l * lal;
         dx[l] = base + (size_t)(p->L + l) * lal;
@@ -1418,7 +1587,7 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[8])
         sgf_schedule cand = best;
         cand.row_inv0 = c;
         if (schedule_ok(p, cand))
-            s = timeit([&] { return launch_row_inv<T>(p->logN, p->L, a, st, p->tc, c); }, ms[3 + c]);
+            s = timeit([&] { return launch_row_inv<T>(p->logN, p->L, p->fo.R, a, st, p->tc, c); }, ms[3 + c]);
     }
     if (s == SGF_OK) {
         best.row_inv0 = 0;
@@ -1451,6 +1620,70 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[8])
 
 }  // namespace
 
+namespace {
+
+// Plan fields that follow from the geometry, precision and flags.
+void plan_init(sgf_plan *p, const Forest &fo, sgf_precision precision, uint32_t flags)
+{
+    p->fo = fo;
+    p->prec = precision;
+    p->flags = flags;
+    p->merged = (flags & SGF_PLAN_ZERO_RIM) != 0;
+    p->pot = (flags & SGF_PLAN_POTENTIAL) != 0;
+    p->tc = precision == SGF_BF16X;
+    p->N = fo.n;
+    p->logN = ilog2(fo.n);
+    p->L = fo.K;
+    p->esize = precision == SGF_FP64 ? 8 : 4;
+}
+
+// A validated geometry's plan: lists, recorded schedule, spectra, workspace.
+sgf_status plan_create(const Forest &fo, sgf_precision precision, uint32_t flags, sgf_plan **out)
+{
+    sgf_plan *p = new sgf_plan();
+    plan_init(p, fo, precision, flags);
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    sgf_status s = build_cover(p);
+    if (s == SGF_OK) {
+        build_lists(p);
+        tune_apply(p);
+        s = precision == SGF_FP64 ? build_spectra<double>(p) : build_spectra<float>(p);
+    }
+    if (s == SGF_OK)
+        s = plan_alloc_owned(p);
+    if (s != SGF_OK) {
+        std::string msg = g_err;
+        plan_free_owned(p);
+        spectra_release(p->spec);
+        delete p;
+        g_err = msg;
+        return s;
+    }
+    *out = p;
+    return SGF_OK;
+}
+
+sgf_status plan_estimate(const Forest &fo, sgf_precision precision, uint32_t flags, size_t *workspace_bytes,
+                         size_t *spectra_bytes, size_t *build_bytes)
+{
+    sgf_plan p;
+    plan_init(&p, fo, precision, flags);
+    sgf_status s = build_cover(&p);
+    if (s != SGF_OK)
+        return s;
+    build_lists(&p);
+    *workspace_bytes = workspace_of(&p);
+    *spectra_bytes = spectra_total(&p);
+    *build_bytes = gen_workspace_bytes(p.N);
+    return SGF_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *sgf_last_error(void) { return g_err.c_str(); }
@@ -1471,39 +1704,24 @@ sgf_status sgf_plan_create_ex(const sgf_nest_desc *desc, sgf_precision precision
     sgf_status s = validate(desc, precision);
     if (s != SGF_OK)
         return s;
-    if ((s = check_flags(desc, flags)) != SGF_OK)
+    if ((s = check_flags(desc->levels, flags)) != SGF_OK)
         return s;
-    sgf_plan *p = new sgf_plan();
-    p->desc = *desc;
-    p->prec = precision;
-    p->flags = flags;
-    p->merged = (flags & SGF_PLAN_ZERO_RIM) != 0;
-    p->pot = (flags & SGF_PLAN_POTENTIAL) != 0;
-    p->tc = precision == SGF_BF16X;
-    p->N = desc->n;
-    p->logN = ilog2(desc->n);
-    p->L = desc->levels;
-    p->esize = precision == SGF_FP64 ? 8 : 4;
-    cudaError_t e = cudaGetDevice(&p->device);
-    if (e != cudaSuccess) {
-        delete p;
-        return cuda_fail(e, "cudaGetDevice");
-    }
-    build_lists(p);
-    tune_apply(p);
-    s = precision == SGF_FP64 ? build_spectra<double>(p) : build_spectra<float>(p);
-    if (s == SGF_OK)
-        s = plan_alloc_owned(p);
-    if (s != SGF_OK) {
-        std::string msg = g_err;
-        plan_free_owned(p);
-        spectra_release(p->spec);
-        delete p;
-        g_err = msg;
+    return plan_create(forest_of_nest(desc), precision, flags, out);
+}
+
+sgf_status sgf_plan_create_forest(const sgf_forest_desc *desc, sgf_precision precision, uint32_t flags,
+                                  sgf_plan **out)
+{
+    if (!out)
+        return fail(SGF_EINVAL, "out is NULL");
+    *out = nullptr;
+    Forest fo;
+    sgf_status s = validate_forest(desc, precision, &fo);
+    if (s != SGF_OK)
         return s;
-    }
-    *out = p;
-    return SGF_OK;
+    if ((s = check_flags(fo.K, flags)) != SGF_OK)
+        return s;
+    return plan_create(fo, precision, flags, out);
 }
 
 sgf_status sgf_plan_estimate(const sgf_nest_desc *desc, sgf_precision precision, uint32_t flags,
@@ -1514,23 +1732,23 @@ sgf_status sgf_plan_estimate(const sgf_nest_desc *desc, sgf_precision precision,
     sgf_status s = validate(desc, precision);
     if (s != SGF_OK)
         return s;
-    if ((s = check_flags(desc, flags)) != SGF_OK)
+    if ((s = check_flags(desc->levels, flags)) != SGF_OK)
         return s;
-    sgf_plan p;
-    p.desc = *desc;
-    p.prec = precision;
-    p.flags = flags;
-    p.merged = (flags & SGF_PLAN_ZERO_RIM) != 0;
-    p.pot = (flags & SGF_PLAN_POTENTIAL) != 0;
-    p.N = desc->n;
-    p.logN = ilog2(desc->n);
-    p.L = desc->levels;
-    p.esize = precision == SGF_FP64 ? 8 : 4;
-    build_lists(&p);
-    *workspace_bytes = workspace_of(&p);
-    *spectra_bytes = spectra_total(&p);
-    *build_bytes = gen_workspace_bytes(p.N);
-    return SGF_OK;
+    return plan_estimate(forest_of_nest(desc), precision, flags, workspace_bytes, spectra_bytes, build_bytes);
+}
+
+sgf_status sgf_plan_estimate_forest(const sgf_forest_desc *desc, sgf_precision precision, uint32_t flags,
+                                    size_t *workspace_bytes, size_t *spectra_bytes, size_t *build_bytes)
+{
+    if (!workspace_bytes || !spectra_bytes || !build_bytes)
+        return fail(SGF_EINVAL, "NULL argument");
+    Forest fo;
+    sgf_status s = validate_forest(desc, precision, &fo);
+    if (s != SGF_OK)
+        return s;
+    if ((s = check_flags(fo.K, flags)) != SGF_OK)
+        return s;
+    return plan_estimate(fo, precision, flags, workspace_bytes, spectra_bytes, build_bytes);
 }
 
 sgf_status sgf_plan_share(const sgf_plan *src, sgf_plan **out)
@@ -1550,29 +1768,22 @@ sgf_status sgf_plan_share_ex(const sgf_plan *src, sgf_precision precision, sgf_p
     if (precision != src->prec && !f32family)
         return fail(SGF_EINVAL, "a plan of precision %d cannot share spectra of precision %d", (int)precision,
                     (int)src->prec);
-    sgf_status vs = validate(&src->desc, precision);
-    if (vs != SGF_OK)
-        return vs;
+    if (precision == SGF_BF16X && src->N == SGF_MAX_N && src->L > 1)
+        return fail(SGF_EUNSUPPORTED, "SGF_BF16X plans of more than one patch need n < %d", SGF_MAX_N);
     DeviceGuard g(src->device);
     sgf_plan *p = new sgf_plan();
-    p->desc = src->desc;
-    p->prec = precision;
-    p->flags = src->flags;
-    p->merged = src->merged;
-    p->pot = src->pot;
-    p->tc = precision == SGF_BF16X;
+    plan_init(p, src->fo, precision, src->flags);
     p->sched = src->sched;
-    p->N = src->N;
-    p->logN = src->logN;
-    p->L = src->L;
-    p->esize = src->esize;
     p->device = src->device;
     if (!schedule_ok(p, p->sched))
         p->sched.row_inv0 = 0;
-    build_lists(p);
-    p->spec = src->spec;
-    p->spec->refs++;
-    sgf_status s = plan_alloc_owned(p);
+    sgf_status s = build_cover(p);
+    if (s == SGF_OK) {
+        build_lists(p);
+        p->spec = src->spec;
+        p->spec->refs++;
+        s = plan_alloc_owned(p);
+    }
     if (s != SGF_OK) {
         std::string msg = g_err;
         plan_free_owned(p);
@@ -1595,8 +1806,8 @@ sgf_status sgf_plan_stats_get(const sgf_plan *p, sgf_plan_stats *st)
     st->forward_slabs = (int)p->slabs.size();
     st->outputs = (int)p->outs.size();
     st->spectra_sets = (int)p->sets.size();
-    // restrictions, row_fwd, col, row_inv1 (+ row_inv for the finer levels) or one row_inv for all
-    st->launches_per_solve = (p->L - 1) + 3 + (p->L > 1 && p->sched.row_inv0 != 1 ? 1 : 0) +
+    // restrictions, row_fwd, col, row_inv1 (+ row_inv for the finer patches) or one row_inv for all
+    st->launches_per_solve = p->restricted + 3 + (p->L > p->fo.R && p->sched.row_inv0 != 1 ? 1 : 0) +
                              (!p->groups.empty() && p->sched.col_case3 == 0 ? 1 : 0) +  // + k_col_g
                              (p->sums.empty() ? 0 : 1);                                  // + k_col_sum
     st->workspace_bytes = p->workspace_bytes;
@@ -1641,8 +1852,8 @@ sgf_status sgf_solve_host(sgf_plan *p, const void *const *sigma, void *const *fx
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     auto base = static_cast<unsigned char *>(p->d_stage);
-    const void *ds[kMaxLevels];
-    void *dx[kMaxLevels], *dy[kMaxLevels];
+    const void *ds[kMaxPatches];
+    void *dx[kMaxPatches], *dy[kMaxPatches];
     for (int l = 0; l < p->L; ++l) {
         ds[l] = base + (size_t)l * lvl_al;
         dx[l] = base + (size_t)(p->L + l) * lvl_al;
@@ -1732,7 +1943,7 @@ sgf_status sgf_plan_profile_read(sgf_plan *p, sgf_kernel_times *out)
             if ((e = cudaEventElapsedTime(&ms, p->events[b + k], p->events[b + k + 1])) != cudaSuccess)
                 return cuda_fail(e, "cudaEventElapsedTime(profile)");
             out->ms[k] += ms;
-            out->launches[k] += k == 0 ? p->L - 1 : 1;
+            out->launches[k] += k == 0 ? p->restricted : 1;
         }
     }
     p->events_used = 0;

@@ -1,9 +1,13 @@
 // sgf_internal.h -- internal data structures of libsgf (not part of the C ABI).
 //
 // Vocabulary (Sec. 2.1 / 2.2 of the paper):
-//   level s / t      source / target level of a pair, level 0 coarsest
-//   m                refinement ratio between the pair's levels, 2^|s - t|
-//   Case 1           s == t: ordinary convolution
+//   patch            one N x N grid Omega^l_k; a plan holds one or more patches
+//                    per level (a nest: one per level), coarsest level first
+//   s / t            source / target patch of a pair, at levels l_s, l_t
+//                    (level 0 coarsest)
+//   m                refinement ratio between the pair's levels, 2^|l_s - l_t|
+//   Case 1           l_s == l_t: ordinary convolution (with a lattice offset
+//                    between two patches of one level: run as Case 2 with m = 1)
 //   Case 2           s finer than t: the source is split into m x m phases
 //                    (Eq. eqnbmnn); every phase is an ordinary convolution
 //                    whose result adds into the coarse target
@@ -48,7 +52,19 @@
 
 namespace sgf {
 
-constexpr int kMaxLevels = 8;
+constexpr int kMaxLevels = 8;    // levels of a nest descriptor
+constexpr int kMaxPatches = 16;  // patches of a plan (per-patch arrays of a solve)
+constexpr int kMaxCover = 64;    // covered rectangles of all patches of a plan
+
+// Cells [x0, x1) x [y0, y1) of a patch that lie under patch `fine` of the next
+// finer level, whose corner sits at (fx, fy) in this patch's cells (so the
+// children of cell (i, j) are cells 2 (i - fx) + {0, 1}, 2 (j - fy) + {0, 1} of
+// `fine`).  A finer patch straddling several coarser ones gives one rectangle
+// in each.
+struct CoverRect {
+    int x0, y0, x1, y1;
+    int fine, fx, fy, pad;
+};
 
 enum SpecKind : int { SPEC_QUARTER = 0, SPEC_FULL = 1, SPEC_MERGED = 2, SPEC_QUARTER_PHI = 3, SPEC_FULL_PHI = 4 };
 
@@ -73,7 +89,7 @@ constexpr __host__ __device__ int quarter_half(int N) { return N / 2 + 4; }
 constexpr __host__ __device__ int quarter_stride(int N) { return 2 * quarter_half(N); }
 
 struct FwdSlab {
-    int level;        // source level
+    int patch;        // source patch
     int m, px, py;    // phase gather: source cell (m*c + px, m*r + py); m = 1 for a whole level
     int rows;         // N / m (rows == columns of the slab)
     int pad;
@@ -87,13 +103,13 @@ struct ColInput {
 };
 
 struct ColOutput {
-    int level;        // target level
+    int patch;        // target patch
     int rows;         // rows kept (N for the main output, N/m for a Case-3 phase)
     int in_begin, in_count;
     size_t off;       // complex-element offset in the backward buffer
 };
 
-// One contribution to a target level's rows in the inverse row pass: target
+// One contribution to a target patch's rows in the inverse row pass: target
 // cell (m*n' + px, j) takes column n' of output out_base + (j % m) * m, row j / m.
 struct RowContrib {
     int m, px;
@@ -131,13 +147,14 @@ struct FwdItem {
 template <typename T>
 struct SolveArgs {
     using C = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
-    int N, logN, L;
+    int N, logN, L;             // L: patches (the levels of a nest)
     int ncomp;                  // output components: 2 (Fx, Fy) or 1 (the potential, in fx)
-    int child_ox[kMaxLevels], child_oy[kMaxLevels];  // covered region of each level; -1: none
-    const T *src[kMaxLevels];   // density per level, covered cells already restricted
-    const T *sigma_in[kMaxLevels];  // the caller's density per level (batched restriction reads it)
-    T *fx[kMaxLevels];
-    T *fy[kMaxLevels];
+    int cover_begin[kMaxPatches + 1];  // covered rectangles of patch p: cover[cover_begin[p] .. cover_begin[p+1])
+    CoverRect cover[kMaxCover];
+    const T *src[kMaxPatches];  // density per patch, covered cells already restricted
+    const T *sigma_in[kMaxPatches];  // the caller's density per patch (the restriction reads it)
+    T *fx[kMaxPatches];
+    T *fy[kMaxPatches];
     C *fwd;                     // forward slabs
     C *bwd;                     // column outputs
     const void *spec;           // kernel spectra (T reals / C complex)
@@ -149,13 +166,16 @@ struct SolveArgs {
     const ColOutput *outs;
     const ColInput *ins;
     const RowContrib *contribs;
-    int contrib_begin[kMaxLevels + 1];
-    int level_base;             // first target level of a k_row_inv launch without a batch view
+    int contrib_begin[kMaxPatches + 1];
+    int level_base;             // first target patch of an inverse row launch without a batch view
     const ColWork *col_list;    // work items of the k_col launch
     const ColGroup *groups;     // Case-3 output groups of the k_col_g launch
     const ColSum *sums;         // chunked outputs of the k_col_sum launch
     C *partial;                 // partial accumulators [slot][parity][comp][kx 0..N][N]
 };
+
+// Passed by value to every transform kernel: keep it within 4 KB of parameters.
+static_assert(sizeof(SolveArgs<double>) + 32 <= 4096, "SolveArgs exceeds the kernel parameter space");
 
 // Twiddle area of a solve (complex entries, precision of the solve):
 //   [0, twlen)            radix-16 engine stage tables (Fft16Plan::twoff), W_{R Ns}^{r k}
@@ -186,17 +206,17 @@ struct GenSet {
 };
 
 // ---- launchers (sgf_solve.cu / sgf_gen.cu); all return cudaGetLastError()
-// Batched restriction: job k = (nest, level) restricts `level` of args[nest]
-// (fine = src[level+1], coarse = src[level], input = sigma_in[level]).
+// Restriction of patch p: src[p] = sigma_in[p], with every covered cell the mean
+// of its four children in the finer patch's src (restricted first).
+// Batched: job k = (nest, patch) restricts that patch of args[nest].
 template <typename T>
 cudaError_t launch_restrict_batch(const SolveArgs<T> *args, const int2 *jobs, int njobs, int max_n, cudaStream_t st);
 template <typename T>
-cudaError_t launch_restrict(const T *fine, T *coarse, const T *coarse_in, int N, int ox, int oy,
-                            cudaStream_t st);
+cudaError_t launch_restrict(const SolveArgs<T> &a, int p, cudaStream_t st);
 // Transform passes of a solve (sgf_kernels.cuh); count = work items (row_fwd),
-// outputs (col) or levels (row_inv).
-// PASS_ROW_INV1: the inverse row pass of a level whose only contribution is
-// its own main output (m = 1; level 0 of every nest).
+// outputs (col) or patches (row_inv).
+// PASS_ROW_INV1: the inverse row pass of a patch whose only contribution is
+// its own main output (m = 1; the level-0 patches).
 enum : int {
     PASS_ROW_FWD = 0,
     PASS_COL = 1,

@@ -104,14 +104,16 @@ __host__ __device__ constexpr int col_sp(int N)
     return (int)(((((size_t)(N + N / 16) * sizeof(C)) + 15) & ~(size_t)15) / sizeof(C));
 }
 
+// Is cell (i, j) of patch s under a patch of the next finer level?
 template <typename T>
 __device__ __forceinline__ bool covered(const SolveArgs<T> &a, int s, int j, int i)
 {
-    const int ox = a.child_ox[s];
-    if (ox < 0)
-        return false;
-    const int oy = a.child_oy[s], half = a.N >> 1;
-    return i >= ox && i < ox + half && j >= oy && j < oy + half;
+    for (int k = a.cover_begin[s]; k < a.cover_begin[s + 1]; ++k) {
+        const CoverRect &r = a.cover[k];
+        if (i >= r.x0 && i < r.x1 && j >= r.y0 && j < r.y1)
+            return true;
+    }
+    return false;
 }
 
 template <int LOGN>
@@ -173,7 +175,7 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd(SolveArgs
     const FwdSlab sl = a.slabs[item.slab];
     const int rows = sl.rows, r0 = 2 * item.row_pair;
     const int ja = sl.m * r0 + sl.py, jb = sl.m * (r0 + 1) + sl.py;
-    const T *src = a.src[sl.level];
+    const T *src = a.src[sl.patch];
     cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
@@ -201,7 +203,7 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd(SolveArgs
                     for (int h = 0; h < 2; ++h) {
                         const int jj = h ? jb : ja;
                         const T *r = srow + (3 * h + 1) * N;  // row jj; rows jj -+ 1 sit beside it
-                        if (covered(a, sl.level, jj, i))
+                        if (covered(a, sl.patch, jj, i))
                             continue;
                         if (f == 0) {
                             fv[h] = r[i];
@@ -787,8 +789,8 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_inv(SolveArgs
 }
 
 // ----------------------------------------------------------------- row_inv1
-// Inverse row pass of a level with a single contribution, its own main output
-// (m = 1: level 0 of every nest, every uniform solve).  NC = 1: one CTA per
+// Inverse row pass of a patch with a single contribution, its own main output
+// (m = 1: the level-0 patches, every uniform solve).  NC = 1: one CTA per
 // (row pair, component); NC = 2: one CTA per row pair, a thread carrying the
 // same slot of both components (two sequences sharing the barriers).  The two
 // rows of a component are gathered (16 bytes per bin in FP32), turned into one
@@ -796,12 +798,12 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_inv(SolveArgs
 // two parity halves, folded, and stored straight from registers.  The exchange
 // buffer of the transform aliases the gather stage.
 // Grid: x = component * N/2 + row pair (NC = 1; component 0 only for the
-// potential) or row pair (NC = 2), y = work item (batch) or 0.
+// potential) or row pair (NC = 2), y = work item (batch) or patch from level_base.
 template <typename T, int LOGN, bool BATCH, bool TC, int NC>
 __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, sizeof(T) == 4 && !TC && NC == 1 ? 2 : 1)
     k_row_inv1(SolveArgs<T> a0, BatchView<T> bv)
 {
-    const int2 wm = BATCH ? bv.map[blockIdx.y] : make_int2(0, 0);
+    const int2 wm = BATCH ? bv.map[blockIdx.y] : make_int2(0, (int)blockIdx.y);
     const SolveArgs<T> &a = BATCH ? bv.args[wm.x] : a0;
     using C = typename Cx<T>::C;
     using K = KShape<LOGN>;
@@ -820,7 +822,7 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, sizeof(T) == 4 && !
     C *stg = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
     constexpr int HALF = N / 2 + 1;
     C *sbuf = stg;
-    const int tl = BATCH ? wm.y : a.level_base;
+    const int tl = BATCH ? wm.y : a.level_base + wm.y;
     const int comp0 = NC == 1 && (int)blockIdx.x >= N / 2 ? 1 : 0;
     const int j0 = 2 * ((int)blockIdx.x - comp0 * (N / 2)), j1 = j0 + 1;
     const int t = threadIdx.x;
@@ -1433,12 +1435,12 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
     }
     case PASS_ROW_INV1: {
         SGF_LAUNCH((k_row_inv1<T, LOGN, false, TC, 1>), (k_row_inv1<T, LOGN, true, TC, 1>), 10, S::row_inv1(1),
-                   dim3(batch ? K::N : a.ncomp * (K::N / 2), batch ? count : 1), K::ROW_THREADS)
+                   dim3(batch ? K::N : a.ncomp * (K::N / 2), count), K::ROW_THREADS)
         break;
     }
     case PASS_ROW_INV2: {
         SGF_LAUNCH((k_row_inv1<T, LOGN, false, TC, 2>), (k_row_inv1<T, LOGN, true, TC, 2>), 18, S::row_inv1(2),
-                   dim3(K::N / 2, batch ? count : 1), K::ROW_THREADS)
+                   dim3(K::N / 2, count), K::ROW_THREADS)
         break;
     }
     case PASS_ROW_FWD_M: {

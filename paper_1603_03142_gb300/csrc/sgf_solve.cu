@@ -1,38 +1,45 @@
 // sgf_solve.cu -- restriction kernel of libsgf.
 //
-// Every covered cell of level l takes the mean of its four children on level
-// l+1 (recursively from the finest level).  These values only feed the slopes
-// of the uncovered neighbours (Sec. 2.1 slope reading); covered cells carry no
-// mass.  The transform kernels are in sgf_solve16.cu.
+// Every covered cell of a patch takes the mean of its four children on the
+// finer patch over it (finest patches first, so the children are restricted
+// values themselves where they are covered in turn).  These values only feed
+// the slopes of the uncovered neighbours (Sec. 2.1 slope reading); covered
+// cells carry no mass.  The transform kernels are in sgf_kernels.cuh.
 #include "sgf_internal.h"
 
 namespace sgf {
 
 // ------------------------------------------------------------------ restrict
 template <typename T>
-__global__ void k_restrict(const T *__restrict__ fine, T *__restrict__ coarse,
-                           const T *__restrict__ coarse_in, int N, int ox, int oy)
+__device__ __forceinline__ void restrict_cell(const SolveArgs<T> &a, int p, int idx)
 {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= N * N)
-        return;
+    const int N = a.N;
     const int j = idx / N, i = idx - j * N;
-    const int half = N >> 1;
-    T v = coarse_in[idx];
-    if (i >= ox && i < ox + half && j >= oy && j < oy + half) {
-        const int ci = 2 * (i - ox), cj = 2 * (j - oy);
-        const T *f = fine + (size_t)cj * N + ci;
-        v = T(0.25) * ((f[0] + f[1]) + (f[N] + f[N + 1]));
+    T v = a.sigma_in[p][idx];
+    for (int k = a.cover_begin[p]; k < a.cover_begin[p + 1]; ++k) {
+        const CoverRect &r = a.cover[k];
+        if (i >= r.x0 && i < r.x1 && j >= r.y0 && j < r.y1) {
+            const T *f = a.src[r.fine] + (size_t)(2 * (j - r.fy)) * N + 2 * (i - r.fx);
+            v = T(0.25) * ((f[0] + f[1]) + (f[N] + f[N + 1]));
+            break;
+        }
     }
-    coarse[idx] = v;
+    const_cast<T *>(a.src[p])[idx] = v;
 }
 
 template <typename T>
-cudaError_t launch_restrict(const T *fine, T *coarse, const T *coarse_in, int N, int ox, int oy,
-                            cudaStream_t st)
+__global__ void k_restrict(SolveArgs<T> a, int p)
 {
-    const int n = N * N, bs = 256;
-    k_restrict<T><<<(n + bs - 1) / bs, bs, 0, st>>>(fine, coarse, coarse_in, N, ox, oy);
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < a.N * a.N)
+        restrict_cell(a, p, idx);
+}
+
+template <typename T>
+cudaError_t launch_restrict(const SolveArgs<T> &a, int p, cudaStream_t st)
+{
+    const int n = a.N * a.N, bs = 256;
+    k_restrict<T><<<(n + bs - 1) / bs, bs, 0, st>>>(a, p);
     return cudaGetLastError();
 }
 
@@ -41,18 +48,9 @@ __global__ void k_restrict_batch(const SolveArgs<T> *__restrict__ args, const in
 {
     const int2 job = jobs[blockIdx.y];
     const SolveArgs<T> &a = args[job.x];
-    const int l = job.y, N = a.N;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= N * N)
-        return;
-    const int j = idx / N, i = idx - j * N;
-    const int half = N >> 1, ox = a.child_ox[l], oy = a.child_oy[l];
-    T v = a.sigma_in[l][idx];
-    if (i >= ox && i < ox + half && j >= oy && j < oy + half) {
-        const T *f = a.src[l + 1] + (size_t)(2 * (j - oy)) * N + 2 * (i - ox);
-        v = T(0.25) * ((f[0] + f[1]) + (f[N] + f[N + 1]));
-    }
-    const_cast<T *>(a.src[l])[idx] = v;
+    if (idx < a.N * a.N)
+        restrict_cell(a, job.y, idx);
 }
 
 template <typename T>
@@ -69,7 +67,7 @@ cudaError_t launch_restrict_batch(const SolveArgs<T> *args, const int2 *jobs, in
 template cudaError_t launch_restrict_batch<float>(const SolveArgs<float> *, const int2 *, int, int, cudaStream_t);
 template cudaError_t launch_restrict_batch<double>(const SolveArgs<double> *, const int2 *, int, int, cudaStream_t);
 
-template cudaError_t launch_restrict<float>(const float *, float *, const float *, int, int, int, cudaStream_t);
-template cudaError_t launch_restrict<double>(const double *, double *, const double *, int, int, int, cudaStream_t);
+template cudaError_t launch_restrict<float>(const SolveArgs<float> &, int, cudaStream_t);
+template cudaError_t launch_restrict<double>(const SolveArgs<double> &, int, cudaStream_t);
 
 }  // namespace sgf

@@ -19,6 +19,7 @@ if not _LIB_PATH.exists():
 _lib = ctypes.CDLL(str(_LIB_PATH))
 
 SGF_MAX_LEVELS = 8
+SGF_MAX_PATCHES = 16
 SGF_OK, SGF_EINVAL, SGF_ENOMEM, SGF_ECUDA, SGF_ETIMEOUT, SGF_EUNSUPPORTED = range(6)
 STATUS_NAMES = {0: "SGF_OK", 1: "SGF_EINVAL", 2: "SGF_ENOMEM", 3: "SGF_ECUDA", 4: "SGF_ETIMEOUT",
                 5: "SGF_EUNSUPPORTED"}
@@ -32,7 +33,7 @@ EXPORTS = ["sgf_plan_create", "sgf_plan_create_ex", "sgf_plan_check", "sgf_plan_
            "sgf_batch_solve", "sgf_batch_info", "sgf_batch_destroy", "sgf_plan_estimate", "sgf_server_create",
            "sgf_server_clock", "sgf_server_submit", "sgf_server_progress", "sgf_server_stats_get",
            "sgf_server_destroy", "sgf_plan_schedule_get", "sgf_plan_schedule_set", "sgf_plan_autotune",
-           "sgf_plan_share_ex", "sgf_solve_potential"]
+           "sgf_plan_share_ex", "sgf_solve_potential", "sgf_plan_create_forest", "sgf_plan_estimate_forest"]
 BATCH_NO_GRAPH = 0x1
 PLAN_ZERO_RIM = 0x1
 PLAN_POTENTIAL = 0x2
@@ -44,6 +45,13 @@ class NestDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("levels", ctypes.c_int32), ("x0", ctypes.c_double),
                 ("y0", ctypes.c_double), ("h0", ctypes.c_double),
                 ("off", (ctypes.c_int32 * 2) * SGF_MAX_LEVELS)]
+
+
+class ForestDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("patches", ctypes.c_int32), ("x0", ctypes.c_double),
+                ("y0", ctypes.c_double), ("h0", ctypes.c_double),
+                ("level", ctypes.c_int32 * SGF_MAX_PATCHES),
+                ("org", (ctypes.c_int32 * 2) * SGF_MAX_PATCHES)]
 
 
 class PlanStats(ctypes.Structure):
@@ -115,6 +123,10 @@ _lib.sgf_plan_destroy.argtypes = [ctypes.c_void_p]
 _lib.sgf_plan_profile.argtypes = [ctypes.c_void_p, ctypes.c_int32]
 _lib.sgf_plan_profile_read.argtypes = [ctypes.c_void_p, ctypes.POINTER(KernelTimes)]
 _lib.sgf_plan_estimate.argtypes = [ctypes.POINTER(NestDesc), ctypes.c_int, ctypes.c_uint32, _szp, _szp, _szp]
+_lib.sgf_plan_create_forest.argtypes = [ctypes.POINTER(ForestDesc), ctypes.c_int, ctypes.c_uint32,
+                                        ctypes.POINTER(ctypes.c_void_p)]
+_lib.sgf_plan_estimate_forest.argtypes = [ctypes.POINTER(ForestDesc), ctypes.c_int, ctypes.c_uint32, _szp, _szp,
+                                          _szp]
 _lib.sgf_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(ctypes.c_void_p)]
 _lib.sgf_server_clock.argtypes = [ctypes.c_void_p]
 _lib.sgf_server_clock.restype = ctypes.c_double
@@ -134,7 +146,8 @@ for _f in ("sgf_plan_create", "sgf_plan_create_ex", "sgf_plan_check", "sgf_plan_
            "sgf_solve_noalloc", "sgf_batch_create", "sgf_batch_solve", "sgf_batch_info", "sgf_batch_destroy",
            "sgf_plan_estimate", "sgf_server_create", "sgf_server_submit", "sgf_server_progress",
            "sgf_server_stats_get", "sgf_server_destroy", "sgf_plan_schedule_get", "sgf_plan_schedule_set",
-           "sgf_plan_autotune", "sgf_plan_share_ex", "sgf_solve_potential"):
+           "sgf_plan_autotune", "sgf_plan_share_ex", "sgf_solve_potential", "sgf_plan_create_forest",
+           "sgf_plan_estimate_forest"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -159,6 +172,24 @@ def library_path() -> Path:
 def _check(status: int, what: str):
     if status != SGF_OK:
         raise SgfError(status, what)
+
+
+def is_forest(geom) -> bool:
+    """A forest (several patches per level) has per-patch ``level`` and ``org`` lists."""
+    return hasattr(geom, "org") and hasattr(geom, "level")
+
+
+def make_forest_desc(forest) -> ForestDesc:
+    d = ForestDesc()
+    K = len(forest.level)
+    if K > SGF_MAX_PATCHES:
+        raise ValueError(f"{K} patches, at most {SGF_MAX_PATCHES}")
+    d.n, d.patches = int(forest.n), K
+    d.x0, d.y0, d.h0 = float(forest.x0), float(forest.y0), float(forest.h0)
+    for p in range(K):
+        d.level[p] = int(forest.level[p])
+        d.org[p][0], d.org[p][1] = int(forest.org[p][0]), int(forest.org[p][1])
+    return d
 
 
 def make_desc(nest) -> NestDesc:
@@ -196,10 +227,13 @@ class Plan:
             self._h = _handle
             return
         h = ctypes.c_void_p()
-        desc = make_desc(nest)
         flags = (PLAN_ZERO_RIM if zero_rim else 0) | (PLAN_POTENTIAL if potential else 0)
-        _check(_lib.sgf_plan_create_ex(ctypes.byref(desc), self.precision, flags, ctypes.byref(h)),
-               "sgf_plan_create_ex")
+        if is_forest(nest):  # per-patch arrays stand where a nest has per-level ones
+            _check(_lib.sgf_plan_create_forest(ctypes.byref(make_forest_desc(nest)), self.precision, flags,
+                                               ctypes.byref(h)), "sgf_plan_create_forest")
+        else:
+            _check(_lib.sgf_plan_create_ex(ctypes.byref(make_desc(nest)), self.precision, flags, ctypes.byref(h)),
+                   "sgf_plan_create_ex")
         self._h = h
 
     def check(self):
@@ -411,9 +445,13 @@ def create_status(nest, precision, flags: int = 0) -> int:
 def estimate(nest, precision="fp32", flags: int = 0) -> dict:
     """sgf_plan_estimate: device bytes of a plan for this nest, without creating it (host only)."""
     ws, sp, bb = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
-    desc = make_desc(nest)
-    _check(_lib.sgf_plan_estimate(ctypes.byref(desc), PRECISIONS.get(precision, precision), flags,
-                                  ctypes.byref(ws), ctypes.byref(sp), ctypes.byref(bb)), "sgf_plan_estimate")
+    prec = PRECISIONS.get(precision, precision)
+    if is_forest(nest):
+        _check(_lib.sgf_plan_estimate_forest(ctypes.byref(make_forest_desc(nest)), prec, flags, ctypes.byref(ws),
+                                             ctypes.byref(sp), ctypes.byref(bb)), "sgf_plan_estimate_forest")
+    else:
+        _check(_lib.sgf_plan_estimate(ctypes.byref(make_desc(nest)), prec, flags,
+                                      ctypes.byref(ws), ctypes.byref(sp), ctypes.byref(bb)), "sgf_plan_estimate")
     return {"workspace_bytes": ws.value, "spectra_bytes": sp.value, "build_bytes": bb.value}
 
 
