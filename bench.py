@@ -181,6 +181,55 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def time_forest(args, world, dev, stream):
+    """Example 3's geometry (Sec. 3: two disks, six level-0 tiles and two level-1
+    patches of forest_n^2 cells each, the paper's N = 2 forest_n), FP32: ms per
+    solve over rotating input/output sets larger than L2, and the plan's
+    algorithmic bytes over that time."""
+    import numpy as np
+    import torch
+    from paper_1603_03142_gb300 import sgf, workloads as W
+    f = W.example3_forest(args.forest_n)
+    sig0 = [torch.from_numpy(a.astype(np.float32)).to(dev) for a in W.two_disk_density(f)]
+    plan = sgf.Plan(f, "fp32")
+    plan.autotune(reps=3)
+    per_set = 3 * sum(a.numel() for a in sig0) * 4
+    sets = max(2, -(-4 * L2_BYTES // per_set))
+    sig = [[a.roll(shifts=k, dims=1).contiguous() for a in sig0] for k in range(sets)]
+    fx = [[torch.empty_like(a) for a in sig0] for _ in range(sets)]
+    fy = [[torch.empty_like(a) for a in sig0] for _ in range(sets)]
+
+    def step(k):
+        plan.solve_ptrs([a.data_ptr() for a in sig[k % sets]], [a.data_ptr() for a in fx[k % sets]],
+                        [a.data_ptr() for a in fy[k % sets]], stream)
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    plan.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for k in range(args.steps):
+        step(k)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    plan.profile(False)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    prof = plan.profile_read()
+    st = plan.stats()
+    cells = sum(a.numel() for a in sig0)
+    out = {"workload": f"two-disk forest (Example 3): 6 level-0 + 2 level-1 patches of {args.forest_n}^2",
+           "cells": cells, "cells_per_s": world * cells / (ms / 1e3), "ms_per_step": ms,
+           "schedule": plan.schedule(), "launches_per_solve": st["launches_per_solve"],
+           "spectra_mib": st["spectra_bytes"] / 2**20,
+           "kernel_ms": {k: v["ms"] / max(1, v["launches"]) for k, v in prof["kernels"].items() if v["launches"]},
+           "algorithmic_bytes_per_solve": st["algorithmic_bytes"],
+           "solve_gbs": st["algorithmic_bytes"] / (ms / 1e3) / 1e9,
+           "solve_frac_of_peak": st["algorithmic_bytes"] / (ms / 1e3) / 1e9 / peaks()[0],
+           "l2": f"{sets} rotating input/output sets ({sets * per_set / 2**20:.0f} MiB)"}
+    plan.close()
+    return out
+
+
 def run_gpu(args, world, rank, local):
     import numpy as np
     import torch
@@ -291,13 +340,22 @@ def run_gpu(args, world, rank, local):
         plan_phi.autotune(reps=3)
         pms, pprof = timed(plan_phi, args.steps)
         pst = plan_phi.stats()
+        pk = {k: v["ms"] / max(1, v["launches"]) for k, v in pprof["kernels"].items() if v["launches"]}
+        # column pass: three forward fields in, three quarter-stored tables, one component out
+        N1 = n + 1
+        col_bytes = 3 * N1 * n * 8 + 3 * N1 * N1 * 4 + N1 * n * 8
         potential = {"cells_per_s": world * cells * args.steps / (pms / 1e3), "ms_per_step": pms / args.steps,
-                     "schedule": plan_phi.schedule(),
-                     "kernel_ms": {k: v["ms"] / max(1, v["launches"]) for k, v in pprof["kernels"].items()
-                                   if v["launches"]},
+                     "schedule": plan_phi.schedule(), "kernel_ms": pk,
                      "algorithmic_bytes_per_solve": pst["algorithmic_bytes"],
-                     "solve_gbs": pst["algorithmic_bytes"] / (pms / args.steps / 1e3) / 1e9}
+                     "solve_gbs": pst["algorithmic_bytes"] / (pms / args.steps / 1e3) / 1e9,
+                     "col_roofline": {"achieved_gbs": col_bytes / (pk["col"] / 1e3) / 1e9,
+                                      "frac": col_bytes / (pk["col"] / 1e3) / 1e9 / peaks()[0],
+                                      "algorithmic_bytes_per_launch": col_bytes}}
         plan_phi.close()
+
+    forest = None
+    if not args.no_forest:
+        forest = time_forest(args, world, dev, stream)
 
     # e2e: host buffers through the C ABI, copies inside the timed region
     pin_s = torch.from_numpy(sigma[0].astype(np.float32)).pin_memory()
@@ -354,6 +412,7 @@ def run_gpu(args, world, rank, local):
                    "general_path": general,
                    "bf16x_path": bf16x,
                    "potential_path": potential,
+                   "forest_path": forest,
                    "l2": f"{sets} rotating input/output sets ({sets * 3 * n * n * 4 / 2**20:.0f} MiB) > 129 MiB L2",
                    "plan_ms": st["plan_ms"], "spectra_mib": st["spectra_bytes"] / 2**20,
                    "algorithmic_bytes_per_solve": st["algorithmic_bytes"],
@@ -525,6 +584,8 @@ def main():
     ap.add_argument("--general", action="store_true", help="time only the general three-field path")
     ap.add_argument("--no-bf16x", action="store_true", help="skip the split-BF16 tensor-core path")
     ap.add_argument("--no-potential", action="store_true", help="skip the potential (SGF_PLAN_POTENTIAL) timing")
+    ap.add_argument("--no-forest", action="store_true", help="skip the two-disk forest (Example 3) timing")
+    ap.add_argument("--forest-n", type=int, default=512, help="cells per side of every patch of the forest")
     ap.add_argument("--schedule", default="auto",
                     help="uniform: 'auto' (autotuner) or 'col_pass,row_inv0' to fix the kernel schedule")
     ap.add_argument("--workload", default="uniform", choices=["uniform", "batched", "serving"])
