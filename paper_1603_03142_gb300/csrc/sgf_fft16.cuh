@@ -433,18 +433,35 @@ SGF_HD void stage_ct(C *v, int j, const C *tw)
 // Stages ST.. of the block transform (see fft16_block); B sequences per slot
 // (B = 1 or 2: a thread may carry the same slot of two sequences, which then
 // share the barriers), sequence b at sbuf + b * SP.  TC (float only): the
+// Barrier of a transform's exchanges: the whole block (HB = 0), or, where the
+// two parity halves of a block run independent transforms on disjoint exchange
+// buffers, the named barrier 1 + half over the HB threads of that half (HB a
+// multiple of 32, each half whole warps), so the halves need not wait for each
+// other between stages.
+template <int HB>
+__device__ __forceinline__ void xsync(int half)
+{
+    if constexpr (HB == 0)
+        __syncthreads();
+    else if (half)  // warp-uniform; immediate ids keep the block's barrier count at 3
+        asm volatile("bar.sync 2, %0;" ::"n"(HB) : "memory");
+    else
+        asm volatile("bar.sync 1, %0;" ::"n"(HB) : "memory");
+}
+
 // 16-point DFTs of the radix-16 stages run as split-BF16 tensor-core tiles
 // (sgf_tc.cuh, context tc); twiddles, exchanges and the closing radix-2/4/8
 // stage stay in FP32.
-template <typename C, bool INV, int LOGN, int B, int ST, bool TC = false>
+template <typename C, bool INV, int LOGN, int B, int ST, bool TC = false, int HB = 0>
 __device__ __forceinline__ void fft_stages(C (*v)[16], C *sbuf, int SP, int j, bool active, const C *tw,
-                                           TcCtx *tc = nullptr)
+                                           TcCtx *tc = nullptr, int half = 0)
 {
     using P = F16<LOGN>;
+    static_assert(HB == 0 || (!TC && HB % 32 == 0), "half barriers: FP32/FP64 engine, whole warps per half");
     if constexpr (ST < P::NST) {
         constexpr int Q = P::Q, NS = P::ns(ST);
         if constexpr (ST > 0) {
-            __syncthreads();  // previous stage's stores are visible
+            xsync<HB>(half);  // previous stage's stores are visible
             if (active) {
 #pragma unroll
                 for (int bb = 0; bb < B; ++bb)
@@ -466,7 +483,7 @@ __device__ __forceinline__ void fft_stages(C (*v)[16], C *sbuf, int SP, int j, b
                 stage_ct<C, INV, LOGN, ST>(v[bb], j, tw);
         }
         if constexpr (ST + 1 < P::NST) {
-            __syncthreads();  // every thread has read this stage's inputs
+            xsync<HB>(half);  // every thread has read this stage's inputs
             if (active) {
                 const int k = j & (NS - 1);
                 const int base = (j - k) * 16 + k;
@@ -477,16 +494,19 @@ __device__ __forceinline__ void fft_stages(C (*v)[16], C *sbuf, int SP, int j, b
                         sbuf[bb * SP + pad16(base + r * NS)] = v[bb][r];
             }
         }
-        fft_stages<C, INV, LOGN, B, ST + 1, TC>(v, sbuf, SP, j, active, tw, tc);
+        fft_stages<C, INV, LOGN, B, ST + 1, TC, HB>(v, sbuf, SP, j, active, tw, tc, half);
     }
 }
 
 // Block-wide transform, compile-time N: as fft16_block, for B slots per thread.
-template <typename C, bool INV, int LOGN, int B = 1, bool TC = false>
+// HB > 0: the transform of one parity half (`half`) with that half's named
+// barrier (xsync); the caller separates it from the other half's use of the
+// same shared memory by block barriers before and after.
+template <typename C, bool INV, int LOGN, int B = 1, bool TC = false, int HB = 0>
 __device__ __forceinline__ void fft_ct(C (*v)[16], C *sbuf, int SP, int j, bool active, const C *tw,
-                                       TcCtx *tc = nullptr)
+                                       TcCtx *tc = nullptr, int half = 0)
 {
-    fft_stages<C, INV, LOGN, B, 0, TC>(v, sbuf, SP, j, active, tw, tc);
+    fft_stages<C, INV, LOGN, B, 0, TC, HB>(v, sbuf, SP, j, active, tw, tc, half);
 }
 #endif
 

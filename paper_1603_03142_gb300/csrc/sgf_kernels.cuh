@@ -122,6 +122,8 @@ struct KShape {
     static constexpr int ROW_THREADS = 2 * Q < 32 ? 32 : 2 * Q;  // both parity halves
     static constexpr int COL_THREADS = Q < 32 ? 32 : Q;          // one parity half
     static constexpr int SP_ROW = N + Q + 8;  // pad puts the two halves 16 banks apart for the unpack
+    // threads per parity half for the half barriers of the row kernels (0: whole-block barriers)
+    static constexpr int HB_ROW = Q >= 32 ? Q : 0;
 };
 
 // Tensor-core tiles (SGF_BF16X) issued per round, i.e. A-tile buffers in shared
@@ -225,6 +227,7 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd(SolveArgs
                 v[0][u] = z;
             }
         }
+        // block barriers: a half barrier here would need one more block barrier per field
         fft_ct<C, false, LOGN, 1, TC>(v, sbuf + b * SP, SP, j, active, tw, &tcx);
         __syncthreads();
         if (active) {
@@ -749,7 +752,9 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_inv(SolveArgs
         if (k + 1 < nitems)
             issue(k + 1);
         cp_commit();
-        fft_ct<C, true, LOGN, 1, TC>(v, sbuf + b * SP, SP, j, active, tw, &tcx);
+        // the block barrier above also follows the previous item's fold
+        constexpr int HB = TC ? 0 : K::HB_ROW;
+        fft_ct<C, true, LOGN, 1, TC, HB>(v, sbuf + b * SP, SP, j, active, tw, &tcx, b);
         __syncthreads();
         if (active && b == 1) {
 #pragma unroll
@@ -868,7 +873,10 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, sizeof(T) == 4 && !
     }
     // the transform's first exchange write follows a barrier, after every read of the stage;
     // half b's NC sequences at sbuf + (b NC + c) SP
-    fft_ct<C, true, LOGN, NC, TC>(v, sbuf + b * NC * SP, SP, j, active, tw, &tcx);
+    constexpr int HB = TC ? 0 : K::HB_ROW;
+    if constexpr (HB > 0)
+        __syncthreads();  // half 0's exchange buffer overlaps half 1's part of the stage
+    fft_ct<C, true, LOGN, NC, TC, HB>(v, sbuf + b * NC * SP, SP, j, active, tw, &tcx, b);
     __syncthreads();
     if (active && b == 1) {
 #pragma unroll
@@ -961,7 +969,8 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd_m(SolveAr
             v[0][u] = z;
         }
     }
-    fft_ct<C, false, LOGN, 1, TC>(v, sbuf + b * SP, SP, j, active, tw, &tcx);
+    constexpr int HB = TC ? 0 : K::HB_ROW;
+    fft_ct<C, false, LOGN, 1, TC, HB>(v, sbuf + b * SP, SP, j, active, tw, &tcx, b);
     __syncthreads();
     if (t == 0 && rim_bad)
         atomicOr(a.status, STATUS_RIM_NONZERO);
