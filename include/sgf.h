@@ -309,7 +309,12 @@ sgf_status sgf_solve_noalloc(sgf_plan *plan, const void *const *sigma, void *con
  *     one CTA per row pair holding both components (two sequences per thread
  *     sharing the barriers); 1 = every level through the nest kernel (one CTA
  *     per row pair, the components one after the other, the gather of the
- *     second overlapping the first's transform).
+ *     second overlapping the first's transform); 3 = as 0 with the level-0
+ *     gather of a row pair's bins done by the tensor memory accelerator (a
+ *     tensor map over the plan's own column output, made at plan creation;
+ *     SGF_FP32 plans of n >= 512 with one level-0 patch; sgf_solve_noalloc,
+ *     whose intermediates are not the plan's, runs 0 instead).  Potential
+ *     plans take no 2.
  *   col_case3 (nests): 0 = the m^2 Case-3 phase outputs of a (coarser source,
  *     target) pair in one cluster per column, the source's forward column
  *     transforms done once for all of them; 1 = one cluster per phase output,
@@ -326,7 +331,8 @@ sgf_status sgf_plan_schedule_get(const sgf_plan *plan, sgf_schedule *schedule);
 /* Errors: SGF_EINVAL for a NULL argument or a choice out of range;
  * SGF_EUNSUPPORTED for col_pass = 2 or row_inv0 = 1 on a SGF_BF16X plan of
  * n = SGF_MAX_N (those kernels have no shared memory left for the tensor-core
- * tiles there; the autotuner skips them). */
+ * tiles there), row_inv0 = 2 on a potential plan, row_inv0 = 3 where it does
+ * not apply (the autotuner skips all of these). */
 sgf_status sgf_plan_schedule_set(sgf_plan *plan, const sgf_schedule *schedule);
 
 /* The autotuner: runs one solve on zero density (temporary device buffers),
@@ -336,10 +342,12 @@ sgf_status sgf_plan_schedule_set(sgf_plan *plan, const sgf_schedule *schedule);
  * the same key: in the process, and in the text file named by the environment
  * variable SGF_AUTOTUNE_CACHE if it is set (one line "<key> <col_pass>
  * <row_inv0> <col_case3>" per key, read once, rewritten after each tuning).  chosen (may be
- * NULL) receives the schedule; ms (may be NULL, else 8 doubles) the mean
- * milliseconds per launch of col_pass 0, 1, 2, row_inv0 0, 1, 2, col_case3 0,
- * 1 (-1 where a candidate does not apply).  Blocks until done.
+ * NULL) receives the schedule; ms (may be NULL, else SGF_AUTOTUNE_TIMES
+ * doubles) the mean milliseconds per launch of col_pass 0, 1, 2, row_inv0 0, 1,
+ * 2, col_case3 0, 1, row_inv0 3 (-1 where a candidate does not apply).  Blocks
+ * until done.
  * Errors: SGF_EINVAL, SGF_ENOMEM, SGF_ECUDA. */
+#define SGF_AUTOTUNE_TIMES 9
 sgf_status sgf_plan_autotune(sgf_plan *plan, int32_t reps, void *stream, sgf_schedule *chosen, double *ms);
 
 /* Device memory a plan for this nest would hold, computed on the host without

@@ -24,6 +24,9 @@
 #include <tuple>
 #include <vector>
 
+#include <cuda.h>          // CUtensorMap and its enums; the encoder is fetched from the driver at run time
+#include <cudaTypedefs.h>
+
 #include "../../include/sgf.h"
 #include "sgf_fft16.cuh"
 #include "sgf_host.h"
@@ -144,6 +147,8 @@ struct sgf_plan {
     bool pot = false;          // SGF_PLAN_POTENTIAL: the potential (one output component, 3 tables per set)
     bool tc = false;           // SGF_BF16X: split-BF16 tensor-core radix-16 tiles (FP32 data)
     sgf_schedule sched{};      // tile schedule of the transform passes (autotuner)
+    bool tma_inv = false;      // row_inv0 = 3 available: FP32, N >= 512, one level-0 patch
+    alignas(64) unsigned char tmap_inv[128] = {};  // its tensor map over the level-0 main column output
     int *d_status = nullptr;   // device status word (STATUS_* bits)
     cudaEvent_t done = nullptr;  // recorded after every solve (sgf_plan_check)
     int N = 0, logN = 0, L = 0, device = 0;  // L: patches (the levels of a nest)
@@ -719,6 +724,39 @@ size_t workspace_of(const sgf_plan *p)
            (size_t)p->restricted * p->N * p->N * p->esize;
 }
 
+// Tensor map of the level-0 patch's main column output (the first output, N
+// rows), as k_row_inv1t reads it: floats [comp * (N+1) + kx][2N] (row stride N
+// complex), boxes of 4 floats (one row pair) x kTmaBox bins, zero fill beyond
+// the end.
+sgf_status encode_tmap_inv(sgf_plan *p)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    if (!encode)
+        return fail(SGF_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const int N = p->N;
+    const ColOutput &o = p->outs[0];
+    void *base = static_cast<unsigned char *>(p->d_bwd) + o.off * 2 * p->esize;
+    const cuuint64_t dims[2] = {2 * (cuuint64_t)N, 2 * (cuuint64_t)(N + 1)};
+    const cuuint64_t strides[1] = {(cuuint64_t)N * 2 * sizeof(float)};
+    const cuuint32_t box[2] = {4, (cuuint32_t)kTmaBox};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(reinterpret_cast<CUtensorMap *>(p->tmap_inv), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base,
+                              dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(SGF_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return SGF_OK;
+}
+
 // Allocate the plan's own device memory and upload its lists.
 sgf_status plan_alloc_owned(sgf_plan *p)
 {
@@ -765,7 +803,7 @@ sgf_status plan_alloc_owned(sgf_plan *p)
     if ((e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming)) != cudaSuccess)
         return cuda_fail(e, "cudaEventCreate(solve completion)");
     p->workspace_bytes = workspace_of(p);
-    return SGF_OK;
+    return p->tma_inv ? encode_tmap_inv(p) : SGF_OK;
 }
 
 // W_P^k = exp(-2 pi i k / P) from extended precision; the quarter points are exact.
@@ -902,14 +940,16 @@ sgf_status mark(sgf_plan *p, cudaStream_t st)
 // Schedule row_inv0 = 0 / 2: the level-0 patches (their own main output alone)
 // through k_row_inv1 with one / both components per CTA, the finer patches
 // (main output plus Case-3 phases) through k_row_inv; row_inv0 = 1: every
-// patch through k_row_inv.
+// patch through k_row_inv; row_inv0 = 3: as 0 with the level-0 gather by the
+// tensor memory accelerator (k_row_inv1t; a.tmap_inv set).
 template <typename T>
 cudaError_t launch_row_inv(int logN, int L, int R, SolveArgs<T> a, cudaStream_t st, bool tc, int row_inv0)
 {
     a.level_base = 0;
     if (row_inv0 == 1)
         return launch_pass_n<T>(PASS_ROW_INV, logN, a, L, st, nullptr, tc);
-    cudaError_t e = launch_pass_n<T>(row_inv0 == 2 ? PASS_ROW_INV2 : PASS_ROW_INV1, logN, a, R, st, nullptr, tc);
+    const int first = row_inv0 == 2 ? PASS_ROW_INV2 : row_inv0 == 3 ? PASS_ROW_INV1T : PASS_ROW_INV1;
+    cudaError_t e = launch_pass_n<T>(first, logN, a, R, st, nullptr, tc);
     if (e != cudaSuccess || L == R)
         return e;
     a.level_base = R;
@@ -948,7 +988,9 @@ cudaError_t launch_col(const sgf_plan *p, const SolveArgs<T> &a, cudaStream_t st
 // for level 0) has no shared memory left for tensor-core tiles at n = 4096.
 inline bool schedule_ok(const sgf_plan *p, const sgf_schedule &s)
 {
-    if (s.col_pass < 0 || s.col_pass > 2 || s.row_inv0 < 0 || s.row_inv0 > 2 || (s.col_case3 != 0 && s.col_case3 != 1))
+    if (s.col_pass < 0 || s.col_pass > 2 || s.row_inv0 < 0 || s.row_inv0 > 3 || (s.col_case3 != 0 && s.col_case3 != 1))
+        return false;
+    if (s.row_inv0 == 3 && !p->tma_inv)
         return false;
     if (p->pot && s.row_inv0 == 2)  // both components per CTA: a potential plan has one
         return false;
@@ -1026,6 +1068,7 @@ sgf_status solve_impl(sgf_plan *p, const void *const *sigma, void *const *fx, vo
     a.groups = p->d_groups;
     a.sums = p->d_sums;
     a.partial = static_cast<typename SolveArgs<T>::C *>(p->d_partial);
+    std::memcpy(a.tmap_inv, p->tmap_inv, sizeof a.tmap_inv);
     cudaError_t e;
     if ((ms = mark(p, st)) != SGF_OK)
         return ms;
@@ -1179,7 +1222,9 @@ sgf_status solve_noalloc_impl(sgf_plan *p, const void *const *sigma, void *const
     e = launch_col<T>(p, a, st);
     if (e != cudaSuccess)
         return cuda_fail(e, "col launch");
-    if ((e = launch_row_inv<T>(p->logN, L, p->fo.R, a, st, p->tc, p->sched.row_inv0)) != cudaSuccess)
+    // the plan's tensor map points at its own intermediates, not at the scratch array
+    const int inv0 = p->sched.row_inv0 == 3 ? 0 : p->sched.row_inv0;
+    if ((e = launch_row_inv<T>(p->logN, L, p->fo.R, a, st, p->tc, inv0)) != cudaSuccess)
         return cuda_fail(e, "row_inv launch");
     if ((e = cudaEventRecord(p->done, st)) != cudaSuccess)
         return cuda_fail(e, "cudaEventRecord(solve completion)");
@@ -1216,6 +1261,7 @@ void fill_args(const sgf_plan *p, const void *const *sigma, void *const *fx, voi
     a.groups = p->d_groups;
     a.sums = p->d_sums;
     a.partial = static_cast<typename SolveArgs<T>::C *>(p->d_partial);
+    std::memcpy(a.tmap_inv, p->tmap_inv, sizeof a.tmap_inv);
 }
 
 // The launches of one batch solve (the arguments are already on the device).
@@ -1483,7 +1529,7 @@ void tune_load_locked()
     char key[160];
     int a = 0, b = 0, c = 0;
     while (fscanf(f, "%159s %d %d %d", key, &a, &b, &c) == 4)
-        if (a >= 0 && a <= 2 && b >= 0 && b <= 2 && (c == 0 || c == 1))
+        if (a >= 0 && a <= 2 && b >= 0 && b <= 3 && (c == 0 || c == 1))
             g_tune[key] = sgf_schedule{a, b, c};
     fclose(f);
 }
@@ -1516,7 +1562,7 @@ void tune_apply(sgf_plan *p)
 }
 
 template <typename T>
-sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[8])
+sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[SGF_AUTOTUNE_TIMES])
 {
     const size_t lvl = (size_t)p->N * p->N * p->esize;
     const size_t lal = (lvl + 255) & ~(size_t)255;
@@ -1565,7 +1611,7 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[8])
         out = t / reps;
         return SGF_OK;
     };
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < SGF_AUTOTUNE_TIMES; ++k)
         ms[k] = -1.0;
     sgf_schedule best = p->sched;
     if (p->merged) {
@@ -1583,16 +1629,17 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[8])
                     best.col_pass = c;
         }
     }
-    for (int c = 0; c < 3 && s == SGF_OK; ++c) {
+    auto inv_slot = [](int c) { return c < 3 ? 3 + c : 8; };  // row_inv0 = 3 appended after col_case3
+    for (int c = 0; c < 4 && s == SGF_OK; ++c) {
         sgf_schedule cand = best;
         cand.row_inv0 = c;
         if (schedule_ok(p, cand))
-            s = timeit([&] { return launch_row_inv<T>(p->logN, p->L, p->fo.R, a, st, p->tc, c); }, ms[3 + c]);
+            s = timeit([&] { return launch_row_inv<T>(p->logN, p->L, p->fo.R, a, st, p->tc, c); }, ms[inv_slot(c)]);
     }
     if (s == SGF_OK) {
         best.row_inv0 = 0;
-        for (int c = 1; c < 3; ++c)
-            if (ms[3 + c] >= 0.0 && ms[3 + c] < ms[3 + best.row_inv0])
+        for (int c = 1; c < 4; ++c)
+            if (ms[inv_slot(c)] >= 0.0 && ms[inv_slot(c)] < ms[inv_slot(best.row_inv0)])
                 best.row_inv0 = c;
     }
     if (!p->merged && !p->groups.empty()) {  // Case-3 outputs grouped or one cluster each
@@ -1635,6 +1682,7 @@ void plan_init(sgf_plan *p, const Forest &fo, sgf_precision precision, uint32_t 
     p->logN = ilog2(fo.n);
     p->L = fo.K;
     p->esize = precision == SGF_FP64 ? 8 : 4;
+    p->tma_inv = precision == SGF_FP32 && fo.n >= 512 && fo.R == 1;
 }
 
 // A validated geometry's plan: lists, recorded schedule, spectra, workspace.
@@ -1913,6 +1961,8 @@ sgf_status sgf_plan_check(sgf_plan *p)
         return cuda_fail(e, "clearing the plan status word");
     if (word & STATUS_TC_TIMEOUT)
         return fail(SGF_ETIMEOUT, "SGF_BF16X: a wait for tensor-core completion timed out; the output is invalid");
+    if (word & STATUS_TMA_TIMEOUT)
+        return fail(SGF_ETIMEOUT, "a wait for a tensor-memory-accelerator copy timed out; the output is invalid");
     if (word & STATUS_RIM_NONZERO)
         return fail(SGF_EINVAL, "SGF_PLAN_ZERO_RIM: sigma was nonzero on the two outer rings of cells");
     return SGF_OK;
@@ -1962,13 +2012,16 @@ sgf_status sgf_plan_schedule_set(sgf_plan *p, const sgf_schedule *in)
 {
     if (!p || !in)
         return fail(SGF_EINVAL, "NULL argument");
-    if (in->col_pass < 0 || in->col_pass > 2 || in->row_inv0 < 0 || in->row_inv0 > 2 ||
+    if (in->col_pass < 0 || in->col_pass > 2 || in->row_inv0 < 0 || in->row_inv0 > 3 ||
         (in->col_case3 != 0 && in->col_case3 != 1))
         return fail(SGF_EINVAL, "schedule out of range (col_pass %d, row_inv0 %d, col_case3 %d)", in->col_pass,
                     in->row_inv0, in->col_case3);
     if (!schedule_ok(p, *in))
-        return fail(SGF_EUNSUPPORTED, "col_pass = 2 and row_inv0 = 1 are not available for SGF_BF16X plans of n = %d",
-                    SGF_MAX_N);
+        return fail(SGF_EUNSUPPORTED,
+                    "schedule (col_pass %d, row_inv0 %d) not available for this plan: col_pass = 2 and row_inv0 = 1 "
+                    "need n < %d with SGF_BF16X, row_inv0 = 2 a force plan, row_inv0 = 3 SGF_FP32 with n >= 512 and "
+                    "one level-0 patch",
+                    in->col_pass, in->row_inv0, SGF_MAX_N);
     p->sched = *in;
     return SGF_OK;
 }
@@ -1980,7 +2033,7 @@ sgf_status sgf_plan_autotune(sgf_plan *p, int32_t reps, void *stream, sgf_schedu
     if (reps < 1 || reps > 1000)
         return fail(SGF_EINVAL, "reps = %d outside [1, 1000]", reps);
     DeviceGuard g(p->device);
-    double t[8];
+    double t[SGF_AUTOTUNE_TIMES];
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     sgf_status s = p->prec == SGF_FP64 ? autotune_impl<double>(p, reps, st, t) : autotune_impl<float>(p, reps, st, t);
     if (s != SGF_OK)
@@ -1988,7 +2041,7 @@ sgf_status sgf_plan_autotune(sgf_plan *p, int32_t reps, void *stream, sgf_schedu
     if (chosen)
         *chosen = p->sched;
     if (ms)
-        for (int k = 0; k < 8; ++k)
+        for (int k = 0; k < SGF_AUTOTUNE_TIMES; ++k)
             ms[k] = t[k];
     return SGF_OK;
 }

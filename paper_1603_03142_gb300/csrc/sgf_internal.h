@@ -80,7 +80,8 @@ inline __host__ __device__ size_t bwd_index(int N, int rows, int comp, int kx, i
 
 // Device status bits of a plan (sgf_plan_check).  STATUS_TC_TIMEOUT: a bounded
 // wait for tensor-core completion (SGF_BF16X) gave up.
-enum : int { STATUS_RIM_NONZERO = 1, STATUS_TC_TIMEOUT = 2 };
+// STATUS_TMA_TIMEOUT: a bounded wait for a tensor-memory-accelerator copy gave up.
+enum : int { STATUS_RIM_NONZERO = 1, STATUS_TC_TIMEOUT = 2, STATUS_TMA_TIMEOUT = 4 };
 
 // A quarter-stored spectrum row holds ky = 0..N split by parity: even ky
 // (0, 2, .., N) at [0, N/2 + 1), odd ky (1, 3, .., N-1) at [N/2 + 4, N + 4);
@@ -172,7 +173,14 @@ struct SolveArgs {
     const ColGroup *groups;     // Case-3 output groups of the k_col_g launch
     const ColSum *sums;         // chunked outputs of the k_col_sum launch
     C *partial;                 // partial accumulators [slot][parity][comp][kx 0..N][N]
+    // Tensor map (CUtensorMap) of the level-0 patch's main column output, for the
+    // tensor-memory-accelerator gather of k_row_inv1t (FP32 plans with one level-0
+    // patch; encoded at plan creation)
+    alignas(64) unsigned char tmap_inv[128];
 };
+
+// Bins per tensor-memory-accelerator box of the k_row_inv1t gather (the largest box extent).
+constexpr int kTmaBox = 256;
 
 // Passed by value to every transform kernel: keep it within 4 KB of parameters.
 static_assert(sizeof(SolveArgs<double>) + 32 <= 4096, "SolveArgs exceeds the kernel parameter space");
@@ -229,7 +237,8 @@ enum : int {
     PASS_COL_G = 8,
     PASS_COL_SUM = 9,
     PASS_ROW_INV2 = 10,
-    PASS_COL_MW = 11
+    PASS_COL_MW = 11,
+    PASS_ROW_INV1T = 12  // PASS_ROW_INV1 with the gather by the tensor memory accelerator (one patch, FP32)
 };
 // Batch mode of the transform passes: a block's nest and its local work index
 // come from a per-launch map (one int2 per block row), and that nest's

@@ -906,6 +906,123 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, sizeof(T) == 4 && !
         tc_end(tcx, TCT);
 }
 
+// ---------------------------------------------------------------- row_inv1t
+// k_row_inv1 (one CTA per row pair and component) with the gather done by the
+// tensor memory accelerator: the level-0 main column output, seen as a 2-D
+// tensor of floats [comp * (N+1) + kx][2N] (a.tmap_inv, encoded at plan
+// creation), is copied in boxes of kTmaBox bins x one row pair (16 bytes a bin)
+// into shared memory in bin order.  One thread issues the copies; every thread
+// waits on an mbarrier (bounded: a timeout sets STATUS_TMA_TIMEOUT).  The rest
+// is k_row_inv1's: Hermitian extension, two parity halves (half barriers), fold.
+// Shared memory: 128-byte aligned stage (aliased by the exchange buffers) |
+// twiddle area | mbarrier.  FP32, N >= 512, no batch view.
+constexpr long long kTmaWaitCycles = 2000000000LL;  // about one second at the SM clock
+
+template <typename T, int LOGN>
+__host__ __device__ constexpr size_t row_inv1t_body()
+{
+    using C = typename Cx<T>::C;
+    constexpr int N = 1 << LOGN;
+    constexpr size_t stage = (size_t)((N + 1 + kTmaBox - 1) / kTmaBox) * kTmaBox * 16;
+    constexpr size_t xbuf = 2 * (size_t)KShape<LOGN>::SP_ROW * sizeof(C);
+    return ((stage > xbuf ? stage : xbuf) + 127) & ~(size_t)127;
+}
+
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 2) k_row_inv1t(const __grid_constant__ SolveArgs<T> a)
+{
+    static_assert(sizeof(T) == 4 && KShape<LOGN>::HB_ROW > 0, "FP32, N >= 512");
+    using C = typename Cx<T>::C;
+    using K = KShape<LOGN>;
+    constexpr int N = K::N, Q = K::Q, SP = K::SP_ROW, P = 2 * N;
+    constexpr int NBOX = (N + 1 + kTmaBox - 1) / kTmaBox;
+    constexpr uint32_t STAGE_BYTES = (uint32_t)NBOX * kTmaBox * 16;
+    constexpr size_t BODY = row_inv1t_body<T, LOGN>();
+    extern __shared__ __align__(16) unsigned char smem_dyn[];
+    // the copies want a 128-byte aligned destination: the launch adds 128 bytes of slack
+    const uint32_t base_s = (uint32_t)__cvta_generic_to_shared(smem_dyn);
+    unsigned char *smem_raw = smem_dyn + (((base_s + 127u) & ~127u) - base_s);
+    unsigned char *stage = smem_raw;
+    C *sbuf = reinterpret_cast<C *>(smem_raw);
+    C *tw = reinterpret_cast<C *>(smem_raw + BODY);
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(smem_raw + BODY + tw_bytes<C>(a.tw_entries));
+    const int tl = a.level_base;
+    const int comp0 = (int)blockIdx.x >= N / 2 ? 1 : 0;
+    const int j0 = 2 * ((int)blockIdx.x - comp0 * (N / 2)), j1 = j0 + 1;
+    const int t = threadIdx.x;
+    const int b = t / Q, j = t - b * Q;  // every thread holds a slot (2Q threads)
+    const TwLayout twl = tw_layout(F16<LOGN>::twlen, N);
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(mb), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
+    cp_commit();
+    __syncthreads();  // the mbarrier is initialised
+    if (t == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mb), "r"(STAGE_BYTES) : "memory");
+        const unsigned long long map = reinterpret_cast<unsigned long long>(&a.tmap_inv[0]);
+        for (int k = 0; k < NBOX; ++k) {
+            const uint32_t dst = (uint32_t)__cvta_generic_to_shared(stage + (size_t)k * kTmaBox * 16);
+            const int x = 2 * j0, y = comp0 * (N + 1) + k * kTmaBox;  // x: 4 floats a row pair, 16-byte aligned
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                "[%4];\n" ::"r"(dst),
+                "l"(map), "r"(x), "r"(y), "r"(mb)
+                : "memory");
+        }
+    }
+    cp_wait<0>();
+    {
+        const long long t0 = clock64();
+        uint32_t ok = 0;
+        while (true) {
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(ok)
+                : "r"(mb), "r"(0u)
+                : "memory");
+            if (ok)
+                break;
+            if (clock64() - t0 > kTmaWaitCycles) {
+                atomicOr(a.status, STATUS_TMA_TIMEOUT);
+                break;
+            }
+        }
+    }
+    __syncthreads();  // the twiddles are in place
+    C v[1][16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        const int kx = 2 * (j + u * Q) + b;
+        const int k2 = kx <= N ? kx : P - kx;
+        const float4 ab = *reinterpret_cast<const float4 *>(stage + (size_t)k2 * 16);
+        const C A = hmk<C>(ab.x, ab.y), B = hmk<C>(ab.z, ab.w);
+        v[0][u] = kx <= N ? hmk<C>(A.x - B.y, A.y + B.x) : hmk<C>(A.x + B.y, B.x - A.y);
+    }
+    __syncthreads();  // the stage has been read: the exchange buffers alias it
+    fft_ct<C, true, LOGN, 1, false, K::HB_ROW>(v, sbuf + b * SP, SP, j, true, tw, nullptr, b);
+    __syncthreads();
+    if (b == 1) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int n = j + u * Q;
+            sbuf[pad16(n)] = hmulc(v[0][u], twist(tw, twl, j, u));
+        }
+    }
+    __syncthreads();
+    if (b == 0) {
+        T *out = comp0 ? a.fy[tl] : a.fx[tl];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int n = j + u * Q;
+            const C y = hadd(v[0][u], sbuf[pad16(n)]);
+            out[(size_t)j0 * N + n] = covered(a, tl, j0, n) ? T(0) : y.x;
+            out[(size_t)j1 * N + n] = covered(a, tl, j1, n) ? T(0) : y.y;
+        }
+    }
+}
+
 // ------------------------------------------------------------ zero-rim path
 // Forward row pass of a SGF_PLAN_ZERO_RIM plan: the rows of sigma alone (the
 // slopes are folded into the merged spectra).  Also verifies the guarantee:
@@ -1320,6 +1437,7 @@ struct KSmem {
         return tc(KShape<LOGN>::ROW_THREADS, nc, nc == 1 ? KK_ROW_INV1 : KK_ROW_INV2) + tw() +
                (stage > xbuf ? stage : xbuf);
     }
+    static size_t row_inv1t() { return row_inv1t_body<T, LOGN>() + tw() + 16 + 128; }  // + mbarrier, alignment slack
     static size_t row_fwd_m()
     {
         return rtc(KK_ROW_FWD_M) + tw() + 2 * (size_t)N * sizeof(T) + 2 * (size_t)KShape<LOGN>::SP_ROW * sizeof(C);
@@ -1385,7 +1503,7 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
 {
     using K = KShape<LOGN>;
     using S = KSmem<T, LOGN, TC>;
-    static std::atomic<unsigned long long> d[22];
+    static std::atomic<unsigned long long> d[23];
     const BatchView<T> none{nullptr, nullptr};
     const bool batch = bv != nullptr;
     const BatchView<T> v = batch ? *bv : none;
@@ -1475,6 +1593,18 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
     case PASS_COL_MW: {
         SGF_LAUNCH((k_col_mw<T, LOGN, false, TC>), (k_col_mw<T, LOGN, true, TC>), 20, S::col_mw(),
                    dim3(K::N + 1, batch ? count : 1), K::ROW_THREADS)
+        break;
+    }
+    case PASS_ROW_INV1T: {
+        if constexpr (sizeof(T) == 4 && !TC && K::HB_ROW > 0) {
+            if (batch)
+                return cudaErrorInvalidValue;
+            if ((e = ensure_smem(k_row_inv1t<T, LOGN>, S::row_inv1t(), d[22])) != cudaSuccess)
+                return e;
+            k_row_inv1t<T, LOGN><<<dim3(a.ncomp * (K::N / 2), count), K::ROW_THREADS, S::row_inv1t(), st>>>(a);
+        } else {
+            return cudaErrorInvalidValue;
+        }
         break;
     }
     case PASS_COL_MD: {

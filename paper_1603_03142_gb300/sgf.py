@@ -38,6 +38,7 @@ BATCH_NO_GRAPH = 0x1
 PLAN_ZERO_RIM = 0x1
 PLAN_POTENTIAL = 0x2
 NOALLOC_SCRATCH_BYTES = 32 << 20
+AUTOTUNE_TIMES = 9
 KERNELS = ["restrict", "row_fwd", "col", "row_inv"]
 
 
@@ -285,12 +286,13 @@ class Plan:
     def autotune(self, reps: int = 5, stream=None) -> dict:
         """sgf_plan_autotune: time every schedule candidate, keep the fastest."""
         sc = Schedule()
-        ms = (ctypes.c_double * 8)()
+        ms = (ctypes.c_double * AUTOTUNE_TIMES)()
         _check(_lib.sgf_plan_autotune(self._h, int(reps), ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(sc),
                                       ms), "sgf_plan_autotune")
         return {"chosen": {"col_pass": sc.col_pass, "row_inv0": sc.row_inv0, "col_case3": sc.col_case3},
                 "ms": {"col_pass0": ms[0], "col_pass1": ms[1], "col_pass2": ms[2], "row_inv0_0": ms[3],
-                       "row_inv0_1": ms[4], "row_inv0_2": ms[5], "col_case3_0": ms[6], "col_case3_1": ms[7]}}
+                       "row_inv0_1": ms[4], "row_inv0_2": ms[5], "col_case3_0": ms[6], "col_case3_1": ms[7],
+                       "row_inv0_3": ms[8]}}
 
     def profile(self, enable: bool = True):
         _check(_lib.sgf_plan_profile(self._h, 1 if enable else 0), "sgf_plan_profile")

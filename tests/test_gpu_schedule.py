@@ -42,8 +42,13 @@ def test_schedules_agree_zero_rim(lib, prec, n):
     sigma = _zero_rim_sigma(n, n)
     plan = lib.Plan(nest, prec, zero_rim=True)
     outs = []
+    tma = prec == "fp32" and n >= 512  # row_inv0 = 3: the level-0 gather by the tensor memory accelerator
+    if not tma:
+        with pytest.raises(lib.SgfError) as ei:
+            plan.set_schedule(0, 3)
+        assert ei.value.status == lib.SGF_EUNSUPPORTED
     for col in (0, 1, 2):
-        for inv in (0, 1, 2):
+        for inv in (0, 1, 2, 3) if tma else (0, 1, 2):
             plan.set_schedule(col, inv)
             assert plan.schedule() == {"col_pass": col, "row_inv0": inv, "col_case3": 0}
             outs.append(run_gpu(plan, sigma))
@@ -134,7 +139,8 @@ print(json.dumps({"r": r, "q": q.schedule()}))
     ch = d["r"]["chosen"]
     cp = [ms["col_pass0"], ms["col_pass1"], ms["col_pass2"]]
     assert ch["col_pass"] == cp.index(min(cp))
-    inv = [ms["row_inv0_0"], ms["row_inv0_1"], ms["row_inv0_2"]]
+    assert ms["row_inv0_3"] > 0  # FP32, n = 1024, one level-0 patch
+    inv = [ms["row_inv0_0"], ms["row_inv0_1"], ms["row_inv0_2"], ms["row_inv0_3"]]
     assert ch["row_inv0"] == inv.index(min(inv))
     assert d["q"] == ch
     lines = table.read_text().split("\n")
@@ -148,3 +154,69 @@ print(json.dumps(sgf.Plan(W.Nest(n=1024), "fp32", zero_rim=True).schedule()))
     out2 = subprocess.run([sys.executable, "-c", code2], env=env, capture_output=True, text=True, timeout=600)
     assert out2.returncode == 0, out2.stderr
     assert json.loads(out2.stdout.strip().splitlines()[-1]) == ch
+
+
+@pytest.mark.parametrize("case", ["zero_rim_4096", "general_1024", "nest_512", "potential_1024"])
+def test_tma_gather_matches_lane_gather(lib, case):
+    """row_inv0 = 3 (k_row_inv1t) against row_inv0 = 0 (k_row_inv1): the same
+    arithmetic on the same bins, only the gather differs."""
+    rng = np.random.Generator(np.random.PCG64(31))
+    kw = {}
+    if case == "zero_rim_4096":
+        nest, sigma, kw = W.Nest(n=4096), _zero_rim_sigma(4096, 3), {"zero_rim": True}
+    elif case == "general_1024":
+        nest = W.Nest(n=1024)
+        sigma = [rng.uniform(0.1, 1.0, (1024, 1024))]
+    elif case == "nest_512":
+        nest, sigma = W.random_nest_problem(rng, 512, 2)
+    else:
+        nest = W.Nest(n=1024)
+        sigma = [rng.uniform(0.1, 1.0, (1024, 1024))]
+        kw = {"potential": True}
+    plan = lib.Plan(nest, "fp32", **kw)
+
+    def run():
+        if kw.get("potential"):
+            import torch
+            phi = plan.solve_potential([torch.from_numpy(s).float().cuda() for s in sigma])
+            torch.cuda.synchronize()
+            return [t.double().cpu().numpy() for t in phi], []
+        return run_gpu(plan, sigma)
+    plan.set_schedule(0, 0)
+    a = run()
+    plan.set_schedule(0, 3)
+    b = run()
+    plan.check()  # no bounded wait gave up
+    eps = np.finfo(np.float32).eps
+    for ga, gb in zip(a[0] + a[1], b[0] + b[1]):
+        assert np.abs(ga - gb).max() <= 64 * eps * np.abs(ga).max()
+
+
+def test_tma_schedule_falls_back_where_it_cannot_apply(lib):
+    import torch
+    nest = W.Nest(n=512)
+    rng = np.random.Generator(np.random.PCG64(32))
+    sigma = [rng.uniform(0.1, 1.0, (512, 512))]
+    plan = lib.Plan(nest, "fp32")
+    plan.set_schedule(0, 0)
+    ref = run_gpu(plan, sigma)
+    plan.set_schedule(0, 3)
+    # the no-allocation solve's intermediates are not the plan's: it runs row_inv0 = 0
+    ts = [torch.from_numpy(sigma[0]).float().cuda()]
+    fx, fy = [torch.empty_like(ts[0])], [torch.empty_like(ts[0])]
+    plan.solve_noalloc_ptrs([ts[0].data_ptr()], [fx[0].data_ptr()], [fy[0].data_ptr()])
+    torch.cuda.synchronize()
+    assert np.array_equal(fx[0].double().cpu().numpy(), ref[0][0])
+    assert np.array_equal(fy[0].double().cpu().numpy(), ref[1][0])
+    # batches keep their own launch maps: a plan at row_inv0 = 3 runs k_row_inv1 there
+    batch = lib.Batch([plan])
+    bx, by = [[torch.empty_like(ts[0])]], [[torch.empty_like(ts[0])]]
+    batch.solve([ts], bx, by)
+    torch.cuda.synchronize()
+    assert np.array_equal(bx[0][0].double().cpu().numpy(), ref[0][0])
+    # not available: FP64, BF16X, two level-0 patches
+    for p in (lib.Plan(nest, "fp64"), lib.Plan(nest, "bf16x"),
+              lib.Plan(W.Forest(n=512, level=[0, 0], org=[(0, 0), (512, 0)]), "fp32")):
+        with pytest.raises(lib.SgfError) as ei:
+            p.set_schedule(0, 3)
+        assert ei.value.status == lib.SGF_EUNSUPPORTED
