@@ -220,3 +220,21 @@ def test_tma_schedule_falls_back_where_it_cannot_apply(lib):
         with pytest.raises(lib.SgfError) as ei:
             p.set_schedule(0, 3)
         assert ei.value.status == lib.SGF_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("n", [512, 1024])
+def test_zero_rim_noalloc_matches_solve(lib, n):
+    """The no-allocation solve of a zero-rim FP32 plan (scratch intermediates)
+    against its ordinary solve: same kernels, same arithmetic, bit-identical forces."""
+    import torch
+    plan = lib.Plan(W.Nest(n=n), "fp32", zero_rim=True)
+    plan.set_schedule(1, 0)
+    sig = _zero_rim_sigma(n, 5)
+    ref = run_gpu(plan, sig)
+    plan.check()
+    ts = torch.from_numpy(sig[0]).float().cuda()
+    fx, fy = torch.empty_like(ts), torch.empty_like(ts)
+    plan.solve_noalloc_ptrs([ts.data_ptr()], [fx.data_ptr()], [fy.data_ptr()])
+    torch.cuda.synchronize()
+    assert np.array_equal(fx.double().cpu().numpy(), ref[0][0])
+    assert np.array_equal(fy.double().cpu().numpy(), ref[1][0])
