@@ -1362,7 +1362,8 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 1) k_col_mw(SolveAr
                 v[0][u] = x;
             }
         }
-        fft_ct<C, false, LOGN, 1, TC>(v, sbuf + 2 * b * SPC, SPC, j, active, tw, &tcx);
+        // each half transforms in its own buffers until the fold: half barriers
+        fft_ct<C, false, LOGN, 1, TC, TC ? 0 : K::HB_ROW>(v, sbuf + 2 * b * SPC, SPC, j, active, tw, &tcx, b);
         if (active) {
             const T *gx_r = gsp + (2 * b) * HQ, *gy_r = gsp + (2 * b + 1) * HQ;
 #pragma unroll
@@ -1377,7 +1378,7 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 1) k_col_mw(SolveAr
             }
         }
     }
-    fft_ct<C, true, LOGN, 2, TC>(acc, sbuf + 2 * b * SPC, SPC, j, active, tw, &tcx);
+    fft_ct<C, true, LOGN, 2, TC, TC ? 0 : K::HB_ROW>(acc, sbuf + 2 * b * SPC, SPC, j, active, tw, &tcx, b);
     __syncthreads();  // every exchange buffer has been read
     C *fold = sbuf;
     if (active && b == 1) {
