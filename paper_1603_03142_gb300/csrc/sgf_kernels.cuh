@@ -1003,23 +1003,26 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 2) k_row_inv1t(cons
     __syncthreads();  // the stage has been read: the exchange buffers alias it
     fft_ct<C, true, LOGN, 1, false, K::HB_ROW>(v, sbuf + b * SP, SP, j, true, tw, nullptr, b);
     __syncthreads();
-    if (b == 1) {
+    // fold y = even + W_P^{-n} odd: the even half stores n < N/2 (slots u < 8), the
+    // odd half n >= N/2, each handing the other its values of the other range
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const int n = j + u * Q;
+    for (int u = 0; u < 16; ++u) {
+        const int n = j + u * Q;
+        if (b == 1 && u < 8)
             sbuf[pad16(n)] = hmulc(v[0][u], twist(tw, twl, j, u));
-        }
+        else if (b == 0 && u >= 8)
+            sbuf[pad16(n)] = v[0][u];
     }
     __syncthreads();
-    if (b == 0) {
-        T *out = comp0 ? a.fy[tl] : a.fx[tl];
+    T *out = comp0 ? a.fy[tl] : a.fx[tl];
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const int n = j + u * Q;
-            const C y = hadd(v[0][u], sbuf[pad16(n)]);
-            out[(size_t)j0 * N + n] = covered(a, tl, j0, n) ? T(0) : y.x;
-            out[(size_t)j1 * N + n] = covered(a, tl, j1, n) ? T(0) : y.y;
-        }
+    for (int u = 0; u < 16; ++u) {
+        const int n = j + u * Q;
+        if ((b == 0) != (u < 8))
+            continue;
+        const C y = b == 0 ? hadd(v[0][u], sbuf[pad16(n)]) : hadd(sbuf[pad16(n)], hmulc(v[0][u], twist(tw, twl, j, u)));
+        out[(size_t)j0 * N + n] = covered(a, tl, j0, n) ? T(0) : y.x;
+        out[(size_t)j1 * N + n] = covered(a, tl, j1, n) ? T(0) : y.y;
     }
 }
 
@@ -1380,24 +1383,29 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 1) k_col_mw(SolveAr
     }
     fft_ct<C, true, LOGN, 2, TC, TC ? 0 : K::HB_ROW>(acc, sbuf + 2 * b * SPC, SPC, j, active, tw, &tcx, b);
     __syncthreads();  // every exchange buffer has been read
+    // fold y = even + W_P^{-n} odd, one component per half: the odd half hands over
+    // Fx's twisted values, the even half Fy's own, and each stores one component
     C *fold = sbuf;
-    if (active && b == 1) {
+    if (active) {
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
             const int n = j + u * Q;
-            const C w = twist(tw, tl, j, u);
-            fold[n] = hmulc(acc[0][u], w);
-            fold[N + n] = hmulc(acc[1][u], w);
+            if (b == 1)
+                fold[n] = hmulc(acc[0][u], twist(tw, tl, j, u));
+            else
+                fold[N + n] = acc[1][u];
         }
     }
     __syncthreads();
-    if (active && b == 0) {
+    if (active) {
         C *dst = a.bwd;
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
             const int n = j + u * Q;
-            dst[bwd_index(N, N, 0, kx, n)] = hadd(acc[0][u], fold[n]);
-            dst[bwd_index(N, N, 1, kx, n)] = hadd(acc[1][u], fold[N + n]);
+            if (b == 0)
+                dst[bwd_index(N, N, 0, kx, n)] = hadd(acc[0][u], fold[n]);
+            else
+                dst[bwd_index(N, N, 1, kx, n)] = hadd(fold[N + n], hmulc(acc[1][u], twist(tw, tl, j, u)));
         }
     }
     if constexpr (TC)
