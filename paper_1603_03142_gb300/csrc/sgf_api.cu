@@ -962,20 +962,22 @@ inline int col_m_pass(const sgf_plan *p)
     return p->sched.col_pass == 1 ? PASS_COL_MD : p->sched.col_pass == 2 ? PASS_COL_MW : PASS_COL_M;
 }
 
-// Column pass of a solve: zero-rim plans through k_col_m / k_col_md; general
-// plans through k_col over the main outputs and k_col_g over the Case-3 groups
-// (col_case3 = 0), or k_col over every output (col_case3 = 1).  a.col_list
-// matches the schedule.
+// Column pass of a solve: zero-rim plans through k_col_m / k_col_md / k_col_mw;
+// general plans through k_col (col_pass 0, 1: a 2-CTA cluster per column) or
+// k_col_w (col_pass 2: both halves in one CTA) over the main outputs and
+// k_col_g over the Case-3 groups (col_case3 = 0), or over every output
+// (col_case3 = 1).  a.col_list matches the schedule.
 template <typename T>
 cudaError_t launch_col(const sgf_plan *p, const SolveArgs<T> &a, cudaStream_t st)
 {
     if (p->merged)
         return launch_pass_n<T>(col_m_pass(p), p->logN, a, 1, st, nullptr, p->tc);
     cudaError_t e;
+    const int colp = p->sched.col_pass == 2 ? PASS_COL_W : PASS_COL;  // both halves in one CTA, or a cluster
     if (p->sched.col_case3 == 1) {
-        e = launch_pass_n<T>(PASS_COL, p->logN, a, (int)p->work_all.size(), st, nullptr, p->tc);
+        e = launch_pass_n<T>(colp, p->logN, a, (int)p->work_all.size(), st, nullptr, p->tc);
     } else {
-        e = launch_pass_n<T>(PASS_COL, p->logN, a, (int)p->work_main.size(), st, nullptr, p->tc);
+        e = launch_pass_n<T>(colp, p->logN, a, (int)p->work_main.size(), st, nullptr, p->tc);
         if (e == cudaSuccess && !p->groups.empty())
             e = launch_pass_n<T>(PASS_COL_G, p->logN, a, (int)p->groups.size(), st, nullptr, p->tc);
     }
@@ -991,6 +993,8 @@ inline bool schedule_ok(const sgf_plan *p, const sgf_schedule &s)
     if (s.col_pass < 0 || s.col_pass > 2 || s.row_inv0 < 0 || s.row_inv0 > 3 || (s.col_case3 != 0 && s.col_case3 != 1))
         return false;
     if (s.row_inv0 == 3 && !p->tma_inv)
+        return false;
+    if (!p->merged && s.col_pass == 2 && (p->prec != SGF_FP32 || p->N < 512))  // k_col_w: FP32, N >= 512
         return false;
     if (p->pot && s.row_inv0 == 2)  // both components per CTA: a potential plan has one
         return false;
@@ -1642,8 +1646,25 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[SGF_A
             if (ms[inv_slot(c)] >= 0.0 && ms[inv_slot(c)] < ms[inv_slot(best.row_inv0)])
                 best.row_inv0 = c;
     }
+    if (!p->merged) {  // general column pass: a cluster per column or both halves in one CTA
+        const sgf_schedule keep = p->sched;
+        for (int c = 0; c <= 2 && s == SGF_OK; c += 2) {
+            sgf_schedule cand = keep;
+            cand.col_pass = c;
+            if (!schedule_ok(p, cand))
+                continue;
+            p->sched = cand;
+            SolveArgs<T> ac;
+            fill_args<T>(p, ds, dx, dy, ac, p->sched);
+            s = timeit([&] { return launch_col<T>(p, ac, st); }, ms[c]);
+        }
+        p->sched = keep;
+        if (s == SGF_OK)
+            best.col_pass = ms[2] >= 0.0 && ms[2] < ms[0] ? 2 : 0;
+    }
     if (!p->merged && !p->groups.empty()) {  // Case-3 outputs grouped or one cluster each
         const sgf_schedule keep = p->sched;
+        p->sched.col_pass = best.col_pass;
         for (int c = 0; c < 2 && s == SGF_OK; ++c) {
             p->sched.col_case3 = c;
             SolveArgs<T> ac;

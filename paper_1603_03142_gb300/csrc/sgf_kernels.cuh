@@ -447,6 +447,189 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
         tc_end(tcx, TCT);
 }
 
+// ------------------------------------------------------------------- col_w
+// k_col with both parity halves of a column in one CTA (thread t: half t / Q,
+// slot t mod Q), each half's transforms on its own named barrier: every input
+// column is staged once for both halves, and 16 warps fit per SM where the
+// 2-CTA cluster kernel fits 8 at N = 4096.  Items (input, field) are
+// double-buffered as in k_col; a chunk work item hands its accumulators to
+// k_col_sum, the others fold the odd half through shared memory, each half
+// storing one component.  FP32 without tensor-core tiles, N >= 512 (FP64's two
+// sequences per thread need more than 128 registers).
+// Shared memory: twiddle area | sbuf[2][SPC] | stage[2] { column[N] (complex),
+// both halves' two spectrum half rows, [half][x, y][N/2 + 4] reals }.  The dual
+// inverse transforms of half b use 2 SPC from sbuf + 2 b SPC (reaching over the
+// stages, free by then), and the fold reuses the start.
+template <typename T, int LOGN, bool BATCH>
+__global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 1) k_col_w(SolveArgs<T> a0, BatchView<T> bv)
+{
+    const int2 wm = BATCH ? bv.map[blockIdx.y] : make_int2(0, (int)blockIdx.y);
+    const SolveArgs<T> &a = BATCH ? bv.args[wm.x] : a0;
+    using C = typename Cx<T>::C;
+    using K = KShape<LOGN>;
+    constexpr int N = K::N, Q = K::Q, P = 2 * N, QS = quarter_stride(N), HQ = quarter_half(N);
+    constexpr int SPC = col_sp<C>(N);
+    constexpr int HB = K::HB_ROW;
+    static_assert(HB > 0, "whole warps per half: N >= 512");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *sbuf = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
+    unsigned char *stage_base = reinterpret_cast<unsigned char *>(sbuf + 2 * SPC);
+    constexpr size_t stage_bytes = (size_t)N * sizeof(C) + 4 * (size_t)HQ * sizeof(T);
+    const int kx = blockIdx.x;
+    const ColWork w = a.col_list[wm.y];
+    const ColOutput o = a.outs[w.out];
+    const int t = threadIdx.x;
+    const int b = t / Q, j = t - b * Q;
+    const int nitems = 3 * w.in_count;
+    const TwLayout tl = tw_layout(F16<LOGN>::twlen, N);
+
+    auto issue = [&](int k) {
+        unsigned char *st = stage_base + (size_t)(k & 1) * stage_bytes;
+        const ColInput ci = a.ins[w.in_begin + k / 3];
+        const FwdSlab sl = a.slabs[ci.slab];
+        const int f = k % 3;
+        cp_block(st, a.fwd + sl.off + ((size_t)f * (N + 1) + kx) * sl.rows, (size_t)sl.rows * sizeof(C));
+        if (spec_quarter(ci.kind)) {
+            const T *sp = reinterpret_cast<const T *>(a.spec) + ci.spec_off;
+            T *dst = reinterpret_cast<T *>(st + (size_t)N * sizeof(C));
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                cp_block(dst + 2 * h * HQ, sp + ((size_t)f * (N + 1) + kx) * QS + h * HQ, (size_t)HQ * sizeof(T));
+                if (ci.kind == SPEC_QUARTER)
+                    cp_block(dst + (2 * h + 1) * HQ, sp + ((size_t)(3 + f) * (N + 1) + kx) * QS + h * HQ,
+                             (size_t)HQ * sizeof(T));
+            }
+        }
+    };
+    cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
+    issue(0);
+    cp_commit();
+    if (nitems > 1)
+        issue(1);
+    cp_commit();
+
+    C acc[2][16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        acc[0][u] = hmk<C>(T(0), T(0));
+        acc[1][u] = hmk<C>(T(0), T(0));
+    }
+    for (int k = 0; k < nitems; ++k) {
+        cp_wait<1>();
+        __syncthreads();
+        const unsigned char *st = stage_base + (size_t)(k & 1) * stage_bytes;
+        const C *col = reinterpret_cast<const C *>(st);
+        const T *spx = reinterpret_cast<const T *>(st + (size_t)N * sizeof(C)) + 2 * b * HQ;  // x row; y at + HQ
+        const ColInput ci = a.ins[w.in_begin + k / 3];
+        const int rows = a.slabs[ci.slab].rows;
+        const int f = k % 3;
+        C v[1][16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int n = j + u * Q;
+            C x = hmk<C>(T(0), T(0));
+            if (n < rows) {
+                x = col[n];
+                if (b)
+                    x = hmul(x, twist(tw, tl, j, u));
+            }
+            v[0][u] = x;
+        }
+        fft_ct<C, false, LOGN, 1, false, HB>(v, sbuf + b * SPC, SPC, j, true, tw, nullptr, b);
+        if (ci.kind == SPEC_QUARTER) {
+            // K0x, K0y imaginary (stored Im), the rest real; bins above N read the
+            // quarter at P - ky with the table's ky parity: + K0x Kxx Kyy, - Kxy K0y Kyx
+            const T mx = (f == 2) ? T(-1) : T(1);
+            const T my = (f == 2) ? T(1) : T(-1);
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int kp = j + u * Q;
+                const bool hi = 2 * kp + b > N;
+                const int q = hi ? N - kp - b : kp;
+                const T rx = spx[q] * (hi ? mx : T(1));
+                const T ry = spx[HQ + q] * (hi ? my : T(1));
+                C tx = hmk<C>(rx * v[0][u].x, rx * v[0][u].y), ty = hmk<C>(ry * v[0][u].x, ry * v[0][u].y);
+                if (f == 0) {
+                    tx = hmk<C>(-tx.y, tx.x);
+                    ty = hmk<C>(-ty.y, ty.x);
+                }
+                acc[0][u] = hadd(acc[0][u], tx);
+                acc[1][u] = hadd(acc[1][u], ty);
+            }
+        } else if (ci.kind == SPEC_QUARTER_PHI) {
+            // the potential alone: P0 real, Px Py imaginary; mirror signs + P0 Px, - Py
+            const T mx = (f == 2) ? T(-1) : T(1);
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int kp = j + u * Q;
+                const bool hi = 2 * kp + b > N;
+                const int q = hi ? N - kp - b : kp;
+                const T rx = spx[q] * (hi ? mx : T(1));
+                C tx = hmk<C>(rx * v[0][u].x, rx * v[0][u].y);
+                if (f != 0)
+                    tx = hmk<C>(-tx.y, tx.x);
+                acc[0][u] = hadd(acc[0][u], tx);
+            }
+        } else if (ci.kind == SPEC_FULL_PHI) {
+            const C *sx = reinterpret_cast<const C *>(a.spec) + ci.spec_off + ((size_t)f * (N + 1) + kx) * P;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int ky = 2 * (j + u * Q) + b;
+                acc[0][u] = hadd(acc[0][u], hmul(__ldg(sx + ky), v[0][u]));
+            }
+        } else {
+            const C *sx = reinterpret_cast<const C *>(a.spec) + ci.spec_off + ((size_t)f * (N + 1) + kx) * P;
+            const C *sy = reinterpret_cast<const C *>(a.spec) + ci.spec_off + ((size_t)(3 + f) * (N + 1) + kx) * P;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int ky = 2 * (j + u * Q) + b;
+                acc[0][u] = hadd(acc[0][u], hmul(__ldg(sx + ky), v[0][u]));
+                acc[1][u] = hadd(acc[1][u], hmul(__ldg(sy + ky), v[0][u]));
+            }
+        }
+        __syncthreads();  // stage (k & 1) and both exchange buffers consumed by every thread
+        if (k + 2 < nitems)
+            issue(k + 2);
+        cp_commit();
+    }
+    cp_wait<0>();
+    if (w.slot >= 0) {  // one chunk of a long input list: hand the accumulators to k_col_sum
+#pragma unroll
+        for (int comp = 0; comp < 2; ++comp) {
+            C *dst = a.partial + ((((size_t)w.slot * 2 + b) * 2 + comp) * (N + 1) + kx) * N;
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+                dst[j + u * Q] = acc[comp][u];
+        }
+        return;
+    }
+    // both inverse transforms of this half; y[n] = even[n] + W_P^{-n} odd[n]
+    fft_ct<C, true, LOGN, 2, false, HB>(acc, sbuf + 2 * b * SPC, SPC, j, true, tw, nullptr, b);
+    __syncthreads();  // every exchange buffer has been read
+    C *fold = sbuf;  // the odd half hands over Fx's twisted values, the even half Fy's own
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        const int n = j + u * Q;
+        if (b == 1)
+            fold[n] = hmulc(acc[0][u], twist(tw, tl, j, u));
+        else
+            fold[N + n] = acc[1][u];
+    }
+    __syncthreads();
+    C *dst = a.bwd + o.off;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        const int n = j + u * Q;
+        if (n >= o.rows)
+            continue;
+        if (b == 0)
+            dst[bwd_index(N, o.rows, 0, kx, n)] = hadd(acc[0][u], fold[n]);
+        else
+            dst[bwd_index(N, o.rows, 1, kx, n)] = hadd(fold[N + n], hmulc(acc[1][u], twist(tw, tl, j, u)));
+    }
+}
+
 // ------------------------------------------------------------------- col_g
 // Column pass of a group of Case-3 phase outputs (Sec. 2.2, Eq. eqnbnmn): the
 // m^2 outputs of one (coarser source, target) pair convolve the same source
@@ -1434,6 +1617,11 @@ struct KSmem {
         const size_t stage = (size_t)N * sizeof(C) + 2 * (size_t)quarter_half(N) * sizeof(T);
         return ctc(KK_COL) + tw() + (size_t)col_sp<C>(N) * sizeof(C) + 2 * stage;
     }
+    static size_t col_w()
+    {
+        const size_t stage = (size_t)N * sizeof(C) + 4 * (size_t)quarter_half(N) * sizeof(T);
+        return tw() + 2 * (size_t)col_sp<C>(N) * sizeof(C) + 2 * stage;
+    }
     static size_t row_inv()
     {
         return rtc(KK_ROW_INV) + tw() + ((2 * (size_t)(N + 1) * sizeof(C) + 15) & ~(size_t)15) +
@@ -1512,7 +1700,7 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
 {
     using K = KShape<LOGN>;
     using S = KSmem<T, LOGN, TC>;
-    static std::atomic<unsigned long long> d[23];
+    static std::atomic<unsigned long long> d[25];
     const BatchView<T> none{nullptr, nullptr};
     const bool batch = bv != nullptr;
     const BatchView<T> v = batch ? *bv : none;
@@ -1602,6 +1790,17 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
     case PASS_COL_MW: {
         SGF_LAUNCH((k_col_mw<T, LOGN, false, TC>), (k_col_mw<T, LOGN, true, TC>), 20, S::col_mw(),
                    dim3(K::N + 1, batch ? count : 1), K::ROW_THREADS)
+        break;
+    }
+    case PASS_COL_W: {
+        if constexpr (!TC && K::HB_ROW > 0 && sizeof(T) == 4) {  // FP64's two sequences need > 128 registers
+            if (S::col_w() > kMaxDynSmem)
+                return cudaErrorInvalidConfiguration;
+            SGF_LAUNCH((k_col_w<T, LOGN, false>), (k_col_w<T, LOGN, true>), 23, S::col_w(), dim3(K::N + 1, count),
+                       K::ROW_THREADS)
+        } else {
+            return cudaErrorInvalidValue;
+        }
         break;
     }
     case PASS_ROW_INV1T: {

@@ -238,3 +238,45 @@ def test_zero_rim_noalloc_matches_solve(lib, n):
     torch.cuda.synchronize()
     assert np.array_equal(fx.double().cpu().numpy(), ref[0][0])
     assert np.array_equal(fy.double().cpu().numpy(), ref[1][0])
+
+
+@pytest.mark.parametrize("case", ["general_1024", "potential_1024", "nest_512", "forest_512"])
+def test_general_col_pass_one_cta_matches_cluster(lib, case):
+    """col_pass 2 on a general plan (k_col_w: both parity halves in one CTA) against
+    col_pass 0 (k_col: a 2-CTA cluster per column), including chunked main outputs
+    (the nest's level 0 has 1 + 4 + 16 inputs) and Case-1 offsets (the forest)."""
+    import torch
+    rng = np.random.Generator(np.random.PCG64(33))
+    kw = {}
+    if case.startswith("general") or case.startswith("potential"):
+        geom = W.Nest(n=1024)
+        sigma = [rng.uniform(0.1, 1.0, (1024, 1024))]
+        kw = {"potential": case.startswith("potential")}
+    elif case == "nest_512":
+        geom, sigma = W.random_nest_problem(rng, 512, 3)
+    else:
+        geom = W.two_patch_forest(512)
+        sigma = [rng.uniform(0.1, 1.0, (512, 512)) for _ in range(geom.levels)]
+    plan = lib.Plan(geom, "fp32", **kw)
+
+    def run():
+        if kw.get("potential"):
+            phi = plan.solve_potential([torch.from_numpy(s).float().cuda() for s in sigma])
+            torch.cuda.synchronize()
+            return [t.double().cpu().numpy() for t in phi]
+        gx, gy = run_gpu(plan, sigma)
+        return gx + gy
+    res = {}
+    for c3 in (0, 1):
+        for col in (0, 2):
+            plan.set_schedule(col, 0, c3)
+            res[(col, c3)] = run()
+    eps = np.finfo(np.float32).eps
+    a = res[(0, 0)]
+    for key, b in res.items():
+        for ga, gb in zip(a, b):
+            assert np.abs(ga - gb).max() <= 64 * eps * np.abs(ga).max(), key
+    for p in (lib.Plan(W.Nest(n=256), "fp32"), lib.Plan(W.Nest(n=512), "fp64"), lib.Plan(W.Nest(n=512), "bf16x")):
+        with pytest.raises(lib.SgfError) as ei:
+            p.set_schedule(2, 0)
+        assert ei.value.status == lib.SGF_EUNSUPPORTED
