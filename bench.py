@@ -451,6 +451,7 @@ def run_batched(args, world, rank, local):
         key = nest.key()
         if key not in base:
             base[key] = sgf.Plan(nest, "fp32")
+            base[key].autotune(reps=2)  # shared plans start from this schedule; a batch group from its first plan's
             plans.append(base[key])
         else:
             plans.append(base[key].share())

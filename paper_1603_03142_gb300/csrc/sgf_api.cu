@@ -1295,7 +1295,7 @@ sgf_status batch_launches(sgf_batch *bt, cudaStream_t st)
         dummy.N = 1 << g.logN;
         if ((e = launch_pass_n<T>(g.merged ? PASS_ROW_FWD_M : PASS_ROW_FWD, g.logN, dummy, g.n_fwd, st, &vf, g.tc)) != cudaSuccess)
             return cuda_fail(e, "batched row_fwd launch");
-        const int colp = !g.merged              ? PASS_COL
+        const int colp = !g.merged              ? (g.sched.col_pass == 2 ? PASS_COL_W : PASS_COL)
                          : g.sched.col_pass == 1 ? PASS_COL_MD
                          : g.sched.col_pass == 2 ? PASS_COL_MW
                                                  : PASS_COL_M;

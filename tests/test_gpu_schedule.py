@@ -280,3 +280,27 @@ def test_general_col_pass_one_cta_matches_cluster(lib, case):
         with pytest.raises(lib.SgfError) as ei:
             p.set_schedule(2, 0)
         assert ei.value.status == lib.SGF_EUNSUPPORTED
+
+
+def test_batch_with_one_cta_column_pass(lib):
+    """A batch group of plans at col_pass 2 runs k_col_w (batch view) for the column pass."""
+    import torch
+    rng = np.random.Generator(np.random.PCG64(34))
+    probs = [W.random_nest_problem(rng, 512, L) for L in (1, 2, 3)]
+    plans = [lib.Plan(nest, "fp32") for nest, _ in probs]
+    for p in plans:
+        p.set_schedule(2, 0)
+    batch = lib.Batch(plans)
+    sig = [[torch.from_numpy(a).float().cuda() for a in s] for _, s in probs]
+    fx = [[torch.empty_like(a) for a in s] for s in sig]
+    fy = [[torch.empty_like(a) for a in s] for s in sig]
+    batch.solve(sig, fx, fy)
+    torch.cuda.synchronize()
+    eps = np.finfo(np.float32).eps
+    for k, (nest, s) in enumerate(probs):
+        plans[k].set_schedule(0, 0)
+        gx, gy = run_gpu(plans[k], s)
+        for l in range(nest.levels):
+            scale = max(np.abs(gx[l]).max(), np.abs(gy[l]).max())
+            assert np.abs(fx[k][l].double().cpu().numpy() - gx[l]).max() <= 64 * eps * scale
+            assert np.abs(fy[k][l].double().cpu().numpy() - gy[l]).max() <= 64 * eps * scale
