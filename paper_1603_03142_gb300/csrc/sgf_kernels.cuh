@@ -417,8 +417,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
             tc_end(tcx, TCT);
         return;  // both CTAs of the cluster take this branch (w is per cluster)
     }
-    // inverse column transforms of Fx^ and Fy^ together; y[n] = even[n] + W_P^{-n} odd[n]
-    fft_ct<C, true, LOGN, 2, TC>(acc, sbuf, SPC, j, active, tw, &tcx);
+    // inverse column transforms of Fx^ and Fy^ together (the potential: its one
+    // component alone); y[n] = even[n] + W_P^{-n} odd[n]
+    const bool two = a.ncomp == 2;
+    if (two)
+        fft_ct<C, true, LOGN, 2, TC>(acc, sbuf, SPC, j, active, tw, &tcx);
+    else
+        fft_ct<C, true, LOGN, 1, TC>(acc, sbuf, SPC, j, active, tw, &tcx);
     C *fold = sbuf;  // 2N complex over sbuf and the stages
     cluster.sync();
     if (b == 1 && active) {
@@ -428,7 +433,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
             const int n = j + u * Q;
             const C w = twist(tw, tl, j, u);
             dst[n] = hmulc(acc[0][u], w);
-            dst[N + n] = hmulc(acc[1][u], w);
+            if (two)
+                dst[N + n] = hmulc(acc[1][u], w);
         }
     }
     cluster.sync();
@@ -439,7 +445,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
             const int n = j + u * Q;
             if (n < o.rows) {
                 dst[bwd_index(N, o.rows, 0, kx, n)] = hadd(acc[0][u], fold[n]);
-                dst[bwd_index(N, o.rows, 1, kx, n)] = hadd(acc[1][u], fold[N + n]);
+                if (two)
+                    dst[bwd_index(N, o.rows, 1, kx, n)] = hadd(acc[1][u], fold[N + n]);
             }
         }
     }
@@ -604,8 +611,13 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 1) k_col_w(SolveArg
         }
         return;
     }
-    // both inverse transforms of this half; y[n] = even[n] + W_P^{-n} odd[n]
-    fft_ct<C, true, LOGN, 2, false, HB>(acc, sbuf + 2 * b * SPC, SPC, j, true, tw, nullptr, b);
+    // both inverse transforms of this half (the potential: its one component
+    // alone); y[n] = even[n] + W_P^{-n} odd[n]
+    const bool two = a.ncomp == 2;
+    if (two)
+        fft_ct<C, true, LOGN, 2, false, HB>(acc, sbuf + 2 * b * SPC, SPC, j, true, tw, nullptr, b);
+    else
+        fft_ct<C, true, LOGN, 1, false, HB>(acc, sbuf + 2 * b * SPC, SPC, j, true, tw, nullptr, b);
     __syncthreads();  // every exchange buffer has been read
     C *fold = sbuf;  // the odd half hands over Fx's twisted values, the even half Fy's own
 #pragma unroll
@@ -613,7 +625,7 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 1) k_col_w(SolveArg
         const int n = j + u * Q;
         if (b == 1)
             fold[n] = hmulc(acc[0][u], twist(tw, tl, j, u));
-        else
+        else if (two)
             fold[N + n] = acc[1][u];
     }
     __syncthreads();
@@ -625,7 +637,7 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 1) k_col_w(SolveArg
             continue;
         if (b == 0)
             dst[bwd_index(N, o.rows, 0, kx, n)] = hadd(acc[0][u], fold[n]);
-        else
+        else if (two)
             dst[bwd_index(N, o.rows, 1, kx, n)] = hadd(fold[N + n], hmulc(acc[1][u], twist(tw, tl, j, u)));
     }
 }
