@@ -334,16 +334,18 @@ def run_gpu(args, world, rank, local):
 
     potential = None
     if not args.no_potential:
-        # the potential (kernel -1/r, three tables per set, one output) on the same
-        # density: the general three-field path, since no zero-rim merge applies
-        plan_phi = sgf.Plan(nest, "fp32", potential=True)
+        # the potential (kernel -1/r, one output) on the same density: its zero-rim
+        # plan (one merged real table over sigma alone), like the forces
+        plan_phi = sgf.Plan(nest, "fp32", potential=True, zero_rim=not args.general)
         plan_phi.autotune(reps=3)
         pms, pprof = timed(plan_phi, args.steps)
         pst = plan_phi.stats()
         pk = {k: v["ms"] / max(1, v["launches"]) for k, v in pprof["kernels"].items() if v["launches"]}
-        # column pass: three forward fields in, three quarter-stored tables, one component out
+        # column pass: the forward fields in (1 zero-rim, 3 general), the quarter-stored tables
+        # (1 merged, 3), one component out
         N1 = n + 1
-        col_bytes = 3 * N1 * n * 8 + 3 * N1 * N1 * 4 + N1 * n * 8
+        nfp = 3 if args.general else 1
+        col_bytes = nfp * N1 * n * 8 + nfp * N1 * N1 * 4 + N1 * n * 8
         potential = {"cells_per_s": world * cells * args.steps / (pms / 1e3), "ms_per_step": pms / args.steps,
                      "schedule": plan_phi.schedule(), "kernel_ms": pk,
                      "algorithmic_bytes_per_solve": pst["algorithmic_bytes"],

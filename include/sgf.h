@@ -154,13 +154,17 @@ sgf_status sgf_plan_create(const sgf_nest_desc *desc, sgf_precision precision, s
  * (v r + u^2 ln(v + r))/2), convolved exactly like the force tables.  Such a
  * plan solves only through sgf_solve_potential; every force entry point
  * (sgf_solve, sgf_solve_host, sgf_solve_noalloc, sgf_solve_batched, batches,
- * the request loop) refuses it with SGF_EINVAL / SGF_EUNSUPPORTED.  Not
- * combinable with SGF_PLAN_ZERO_RIM.  The potential depends on the cell size
- * (Phi scales with h0 at fixed sigma) where the forces do not. */
+ * the request loop) refuses it with SGF_EINVAL / SGF_EUNSUPPORTED.  With
+ * SGF_PLAN_ZERO_RIM (one patch, the same guarantee as for the forces) the three
+ * tables fold into one real table (the central-difference slope stencils of
+ * the zero rim folded in) over sigma alone; such a plan runs the column
+ * schedule col_pass = 2 only (SGF_EUNSUPPORTED where that does not apply:
+ * SGF_BF16X at n = SGF_MAX_N).  The potential depends on the cell size (Phi
+ * scales with h0 at fixed sigma) where the forces do not. */
 
 /* As sgf_plan_create, with option flags (0 = sgf_plan_create).  Errors as
- * sgf_plan_create; SGF_EINVAL for unknown flags, SGF_PLAN_ZERO_RIM with
- * levels > 1, or SGF_PLAN_ZERO_RIM with SGF_PLAN_POTENTIAL. */
+ * sgf_plan_create; SGF_EINVAL for unknown flags or SGF_PLAN_ZERO_RIM with
+ * levels > 1. */
 sgf_status sgf_plan_create_ex(const sgf_nest_desc *desc, sgf_precision precision, uint32_t flags,
                               sgf_plan **out);
 

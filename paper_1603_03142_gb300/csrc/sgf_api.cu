@@ -236,8 +236,6 @@ sgf_status check_flags(int patches, uint32_t flags)
         return fail(SGF_EINVAL, "unknown plan flags 0x%x", flags);
     if ((flags & SGF_PLAN_ZERO_RIM) && patches != 1)
         return fail(SGF_EINVAL, "SGF_PLAN_ZERO_RIM needs a single level and patch (%d patches)", patches);
-    if ((flags & SGF_PLAN_ZERO_RIM) && (flags & SGF_PLAN_POTENTIAL))
-        return fail(SGF_EINVAL, "SGF_PLAN_ZERO_RIM and SGF_PLAN_POTENTIAL do not combine");
     return SGF_OK;
 }
 
@@ -413,15 +411,16 @@ sgf_status build_cover(sgf_plan *p)
 }
 
 // Lists of a zero-rim single-level plan: one slab of sigma alone, one output,
-// one merged spectra set.
+// one merged spectra set (Gx, Gy; the potential: Gphi).
 void build_lists_merged(sgf_plan *p)
 {
     const int N = p->N;
     const size_t T = p->esize, Cb = 2 * p->esize;
     GenSet g{};
-    g.kind = SPEC_MERGED;
+    g.kind = p->pot ? SPEC_MERGED_PHI : SPEC_MERGED;
     g.cas = 4;
     g.m = 1;
+    g.h = p->pot ? p->fo.h0 : 0.0;
     p->sets.push_back(g);
     FwdSlab sl{};
     sl.patch = 0;
@@ -440,7 +439,7 @@ void build_lists_merged(sgf_plan *p)
     p->bwd_elems = 2 * (size_t)(N + 1) * N;
     ColInput ci{};
     ci.slab = 0;
-    ci.kind = SPEC_MERGED;
+    ci.kind = g.kind;
     ci.spec_off = 0;
     p->ins.push_back(ci);
     p->contrib_begin[0] = 0;
@@ -450,9 +449,11 @@ void build_lists_merged(sgf_plan *p)
     p->work_main.push_back(ColWork{0, 0, 1, -1});
     for (int r = 0; r < N / 2; ++r)
         p->items.push_back(FwdItem{0, r});
-    // sigma in, Fx Fy out; 1-field forward and 2-field backward intermediates; 2 quarter spectra
-    p->algorithmic_bytes = 3 * (size_t)N * N * T + 2 * p->fwd_elems * Cb + 2 * p->bwd_elems * Cb +
-                           2 * (size_t)(N + 1) * (N + 1) * T;
+    // sigma in, Fx Fy (Phi) out; 1-field forward and 2-field (1-field) backward
+    // intermediates; 2 (1) quarter spectra
+    const size_t nc = p->pot ? 1 : 2;
+    p->algorithmic_bytes = (1 + nc) * (size_t)N * N * T + 2 * p->fwd_elems * Cb + nc * p->bwd_elems * Cb +
+                           nc * (size_t)(N + 1) * (N + 1) * T;
 }
 
 // Case-3 phase outputs that share one forward transform of their source (k_col_g):
@@ -668,7 +669,7 @@ size_t spectra_total(const sgf_plan *p)
     size_t off = 0;
     for (const auto &g : p->sets) {
         const size_t nt = (size_t)spec_tables(g.kind);
-        const size_t b = g.kind == SPEC_MERGED || spec_quarter(g.kind)
+        const size_t b = g.kind == SPEC_MERGED || g.kind == SPEC_MERGED_PHI || spec_quarter(g.kind)
                              ? nt * (p->N + 1) * quarter_stride(p->N) * p->esize
                              : nt * (p->N + 1) * 2 * p->N * 2 * p->esize;
         off += (b + 255) & ~(size_t)255;
@@ -970,8 +971,11 @@ inline int col_m_pass(const sgf_plan *p)
 template <typename T>
 cudaError_t launch_col(const sgf_plan *p, const SolveArgs<T> &a, cudaStream_t st)
 {
-    if (p->merged)
+    if (p->merged) {
+        if (p->pot && p->sched.col_pass != 2)  // only k_col_mw reads the one-table potential spectra
+            return cudaErrorInvalidValue;
         return launch_pass_n<T>(col_m_pass(p), p->logN, a, 1, st, nullptr, p->tc);
+    }
     cudaError_t e;
     const int colp = p->sched.col_pass == 2 ? PASS_COL_W : PASS_COL;  // both halves in one CTA, or a cluster
     if (p->sched.col_case3 == 1) {
@@ -995,6 +999,8 @@ inline bool schedule_ok(const sgf_plan *p, const sgf_schedule &s)
     if (s.row_inv0 == 3 && !p->tma_inv)
         return false;
     if (!p->merged && s.col_pass == 2 && (p->prec != SGF_FP32 || p->N < 512))  // k_col_w: FP32, N >= 512
+        return false;
+    if (p->merged && p->pot && s.col_pass != 2)  // the zero-rim potential: k_col_mw only
         return false;
     if (p->pot && s.row_inv0 == 2)  // both components per CTA: a potential plan has one
         return false;
@@ -1626,11 +1632,13 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[SGF_A
             if (schedule_ok(p, cand))
                 s = timeit([&] { return launch_pass_n<T>(col_kind[c], p->logN, a, 1, st, nullptr, p->tc); }, ms[c]);
         }
-        if (s == SGF_OK) {
-            best.col_pass = 0;
-            for (int c = 1; c < 3; ++c)
-                if (ms[c] >= 0.0 && ms[c] < ms[best.col_pass])
-                    best.col_pass = c;
+        if (s == SGF_OK) {  // the fastest of the candidates that apply (and were timed)
+            int bc = -1;
+            for (int c = 0; c < 3; ++c)
+                if (ms[c] >= 0.0 && (bc < 0 || ms[c] < ms[bc]))
+                    bc = c;
+            if (bc >= 0)
+                best.col_pass = bc;
         }
     }
     auto inv_slot = [](int c) { return c < 3 ? 3 + c : 8; };  // row_inv0 = 3 appended after col_case3
@@ -1640,11 +1648,13 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[SGF_A
         if (schedule_ok(p, cand))
             s = timeit([&] { return launch_row_inv<T>(p->logN, p->L, p->fo.R, a, st, p->tc, c); }, ms[inv_slot(c)]);
     }
-    if (s == SGF_OK) {
-        best.row_inv0 = 0;
-        for (int c = 1; c < 4; ++c)
-            if (ms[inv_slot(c)] >= 0.0 && ms[inv_slot(c)] < ms[inv_slot(best.row_inv0)])
-                best.row_inv0 = c;
+    if (s == SGF_OK) {  // the fastest of the candidates that apply (and were timed)
+        int bc = -1;
+        for (int c = 0; c < 4; ++c)
+            if (ms[inv_slot(c)] >= 0.0 && (bc < 0 || ms[inv_slot(c)] < ms[inv_slot(bc)]))
+                bc = c;
+        if (bc >= 0)
+            best.row_inv0 = bc;
     }
     if (!p->merged) {  // general column pass: a cluster per column or both halves in one CTA
         const sgf_schedule keep = p->sched;
@@ -1659,7 +1669,7 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[SGF_A
             s = timeit([&] { return launch_col<T>(p, ac, st); }, ms[c]);
         }
         p->sched = keep;
-        if (s == SGF_OK)
+        if (s == SGF_OK && ms[0] >= 0.0)
             best.col_pass = ms[2] >= 0.0 && ms[2] < ms[0] ? 2 : 0;
     }
     if (!p->merged && !p->groups.empty()) {  // Case-3 outputs grouped or one cluster each
@@ -1704,6 +1714,7 @@ void plan_init(sgf_plan *p, const Forest &fo, sgf_precision precision, uint32_t 
     p->L = fo.K;
     p->esize = precision == SGF_FP64 ? 8 : 4;
     p->tma_inv = precision == SGF_FP32 && fo.n >= 512 && fo.R == 1;
+    p->sched = sgf_schedule{p->merged && p->pot ? 2 : 0, 0, 0};  // the zero-rim potential runs col_pass 2
 }
 
 // A validated geometry's plan: lists, recorded schedule, spectra, workspace.
@@ -1717,6 +1728,9 @@ sgf_status plan_create(const Forest &fo, sgf_precision precision, uint32_t flags
         return cuda_fail(e, "cudaGetDevice");
     }
     sgf_status s = build_cover(p);
+    if (s == SGF_OK && !schedule_ok(p, p->sched))
+        s = fail(SGF_EUNSUPPORTED, "no kernel schedule applies (zero-rim potential with SGF_BF16X needs n < %d)",
+                 SGF_MAX_N);
     if (s == SGF_OK) {
         build_lists(p);
         tune_apply(p);
@@ -1846,6 +1860,13 @@ sgf_status sgf_plan_share_ex(const sgf_plan *src, sgf_precision precision, sgf_p
     p->device = src->device;
     if (!schedule_ok(p, p->sched))
         p->sched.row_inv0 = 0;
+    if (!schedule_ok(p, p->sched))
+        p->sched.col_pass = p->merged && p->pot ? 2 : 0;
+    if (!schedule_ok(p, p->sched)) {
+        delete p;
+        return fail(SGF_EUNSUPPORTED, "no kernel schedule applies to the shared plan (zero-rim potential with "
+                                      "SGF_BF16X needs n < %d)", SGF_MAX_N);
+    }
     sgf_status s = build_cover(p);
     if (s == SGF_OK) {
         build_lists(p);

@@ -169,6 +169,20 @@ __device__ __forceinline__ void merged_tables(const AxisMap &mx, const AxisMap &
     out[1] = c0[3] + 0.5 * (xp[4] - xm[4]) + 0.5 * (yp[5] - ym[5]);
 }
 
+// The potential's zero-rim table: P0 + (Px[d + x] - Px[d - x])/2 + (Py[d + y] - Py[d - y])/2
+// (the same stencil algebra as merged_tables).
+__device__ __forceinline__ void merged_tables_phi(const AxisMap &mx, const AxisMap &my, int dx, int dy, double h,
+                                                  double out[1])
+{
+    double c0[3], xp[3], xm[3], yp[3], ym[3];
+    cell_tables_phi(mx, my, dx, dy, 1, 1, h, c0);
+    cell_tables_phi(mx, my, dx + 1, dy, 1, 1, h, xp);
+    cell_tables_phi(mx, my, dx - 1, dy, 1, 1, h, xm);
+    cell_tables_phi(mx, my, dx, dy + 1, 1, 1, h, yp);
+    cell_tables_phi(mx, my, dx, dy - 1, 1, 1, h, ym);
+    out[0] = c0[0] + 0.5 * (xp[1] - xm[1]) + 0.5 * (yp[2] - ym[2]);
+}
+
 __global__ void k_gen_tables(GenSet g, int N, double *__restrict__ tables)
 {
     const int P = 2 * N;
@@ -182,7 +196,9 @@ __global__ void k_gen_tables(GenSet g, int N, double *__restrict__ tables)
     int dx, dy;
     const int ntab = spec_tables(g.kind);
     if (mx.index(px, P, dx) && my.index(py, P, dy)) {
-        if (g.cas == 4)
+        if (g.kind == SPEC_MERGED_PHI)
+            merged_tables_phi(mx, my, dx, dy, g.h, out);
+        else if (g.cas == 4)
             merged_tables(mx, my, dx, dy, out);
         else if (spec_phi(g.kind))
             cell_tables_phi(mx, my, dx, dy, g.cas, g.m, g.h, out);
@@ -243,12 +259,13 @@ __global__ void k_gen_cols(int N, int logN, const double2 *__restrict__ half, co
     __syncthreads();
     block_fft<double2, false>(W, N, logN, 2, tw);
     const double scale = 1.0 / ((double)P * (double)P);
-    if (spec_quarter(kind) || kind == SPEC_MERGED) {
+    if (spec_quarter(kind) || kind == SPEC_MERGED || kind == SPEC_MERGED_PHI) {
         // K0x and K0y (tables 0, 3) are odd in one axis: purely imaginary; merged Gx, Gy
         // too; of the potential tables Px and Py (1, 2), while P0 is real
         const int QS = quarter_stride(N), HQ = quarter_half(N);
         T *dst = reinterpret_cast<T *>(spec) + spec_off + ((size_t)t * (N + 1) + kx) * QS;
-        const bool imag = kind == SPEC_MERGED || (kind == SPEC_QUARTER_PHI ? t != 0 : t == 0 || t == 3);
+        const bool imag = kind == SPEC_MERGED ||
+                          (kind == SPEC_MERGED_PHI ? false : kind == SPEC_QUARTER_PHI ? t != 0 : t == 0 || t == 3);
         for (int idx = tid; idx < QS; idx += nt) {
             const int q = idx < HQ ? 2 * idx : 2 * (idx - HQ) + 1;  // even half, then odd half
             const double2 X = q <= N ? W[(q & 1) * N + (q >> 1)] : make_double2(0.0, 0.0);

@@ -44,6 +44,9 @@
 //     odd in y (imaginary); quarter-stored like SPEC_QUARTER, mirror sign in ky
 //     + for P0 and Px, - for Py.
 //   SPEC_FULL_PHI (Cases 2, 3): complex [table][kx 0..N][ky 0..P).
+//   SPEC_MERGED_PHI (zero-rim single level): 1 table, Gphi = P0 with the
+//     central-difference slope stencils folded in; real and even in both axes,
+//     quarter-stored, mirror sign +.
 #pragma once
 #include <cstddef>
 #include <cstdint>
@@ -66,11 +69,21 @@ struct CoverRect {
     int fine, fx, fy, pad;
 };
 
-enum SpecKind : int { SPEC_QUARTER = 0, SPEC_FULL = 1, SPEC_MERGED = 2, SPEC_QUARTER_PHI = 3, SPEC_FULL_PHI = 4 };
+enum SpecKind : int {
+    SPEC_QUARTER = 0,
+    SPEC_FULL = 1,
+    SPEC_MERGED = 2,
+    SPEC_QUARTER_PHI = 3,
+    SPEC_FULL_PHI = 4,
+    SPEC_MERGED_PHI = 5
+};
 
 inline __host__ __device__ bool spec_quarter(int kind) { return kind == SPEC_QUARTER || kind == SPEC_QUARTER_PHI; }
 inline __host__ __device__ bool spec_phi(int kind) { return kind == SPEC_QUARTER_PHI || kind == SPEC_FULL_PHI; }
-inline __host__ __device__ int spec_tables(int kind) { return kind == SPEC_MERGED ? 2 : spec_phi(kind) ? 3 : 6; }
+inline __host__ __device__ int spec_tables(int kind)
+{
+    return kind == SPEC_MERGED ? 2 : kind == SPEC_MERGED_PHI ? 1 : spec_phi(kind) ? 3 : 6;
+}
 
 // Element (comp, kx, row) of a column output with `rows` rows (complex units).
 inline __host__ __device__ size_t bwd_index(int N, int rows, int comp, int kx, int row)

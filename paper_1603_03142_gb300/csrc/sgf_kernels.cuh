@@ -1511,7 +1511,8 @@ __global__ void __cluster_dims__(2, 1, 1)
 // cluster.  Both inverse transforms in flight (two sequences per thread).
 // Shared memory: twiddle area | column[N] | Gx, Gy half rows of both halves |
 // exchange buffers, half b's two sequences at sbuf + 2 b SPC (then the fold).
-template <typename T, int LOGN, bool BATCH, bool TC>
+// NC = 2: the forces (Gx, Gy); NC = 1: the potential (Gphi alone, one inverse transform).
+template <typename T, int LOGN, bool BATCH, bool TC, int NC = 2>
 __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 1) k_col_mw(SolveArgs<T> a0, BatchView<T> bv)
 {
     const int2 wm = BATCH ? bv.map[blockIdx.y] : make_int2(0, 0);
@@ -1540,10 +1541,12 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 1) k_col_mw(SolveAr
     const T *spec = reinterpret_cast<const T *>(a.spec);
     cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
     cp_block(col, a.fwd + (size_t)kx * N, (size_t)N * sizeof(C));
+    constexpr bool two = NC == 2;  // the forces (Gx, Gy); else the potential (Gphi alone)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         cp_block(gsp + (2 * h) * HQ, spec + (size_t)kx * QS + h * HQ, (size_t)HQ * sizeof(T));
-        cp_block(gsp + (2 * h + 1) * HQ, spec + ((size_t)(N + 1) + kx) * QS + h * HQ, (size_t)HQ * sizeof(T));
+        if (two)
+            cp_block(gsp + (2 * h + 1) * HQ, spec + ((size_t)(N + 1) + kx) * QS + h * HQ, (size_t)HQ * sizeof(T));
     }
     cp_commit();
     cp_wait<0>();
@@ -1562,7 +1565,8 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 1) k_col_mw(SolveAr
         }
         // each half transforms in its own buffers until the fold: half barriers
         fft_ct<C, false, LOGN, 1, TC, TC ? 0 : K::HB_ROW>(v, sbuf + 2 * b * SPC, SPC, j, active, tw, &tcx, b);
-        if (active) {
+        if constexpr (two) {
+          if (active) {
             const T *gx_r = gsp + (2 * b) * HQ, *gy_r = gsp + (2 * b + 1) * HQ;
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
@@ -1574,8 +1578,48 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 1) k_col_mw(SolveAr
                 acc[0][u] = hmk<C>(-gx * v[0][u].y, gx * v[0][u].x);  // i gx v
                 acc[1][u] = hmk<C>(-gy * v[0][u].y, gy * v[0][u].x);
             }
+          }
+        } else if (active) {
+            const T *gp_r = gsp + (2 * b) * HQ;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int kp = j + u * Q;
+                const int q = 2 * kp + b > N ? N - kp - b : kp;
+                const T gp = gp_r[q];  // Gphi real, even in ky
+                acc[0][u] = hmk<C>(gp * v[0][u].x, gp * v[0][u].y);
+            }
         }
     }
+    if constexpr (!two) {  // the potential: one inverse transform, the stores split by n between the halves
+        fft_ct<C, true, LOGN, 1, TC, TC ? 0 : K::HB_ROW>(acc, sbuf + 2 * b * SPC, SPC, j, active, tw, &tcx, b);
+        __syncthreads();  // every exchange buffer has been read
+        C *fold = sbuf;
+        if (active) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int n = j + u * Q;
+                if (b == 1 && u < 8)
+                    fold[n] = hmulc(acc[0][u], twist(tw, tl, j, u));
+                else if (b == 0 && u >= 8)
+                    fold[n] = acc[0][u];
+            }
+        }
+        __syncthreads();
+        if (active) {
+            C *dst = a.bwd;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int n = j + u * Q;
+                if (b == 0 && u < 8)
+                    dst[bwd_index(N, N, 0, kx, n)] = hadd(acc[0][u], fold[n]);
+                else if (b == 1 && u >= 8)
+                    dst[bwd_index(N, N, 0, kx, n)] = hadd(fold[n], hmulc(acc[0][u], twist(tw, tl, j, u)));
+            }
+        }
+        if constexpr (TC)
+            tc_end(tcx, TCT);
+        return;
+    } else {
     fft_ct<C, true, LOGN, 2, TC, TC ? 0 : K::HB_ROW>(acc, sbuf + 2 * b * SPC, SPC, j, active, tw, &tcx, b);
     __syncthreads();  // every exchange buffer has been read
     // fold y = even + W_P^{-n} odd, one component per half: the odd half hands over
@@ -1605,6 +1649,7 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 1) k_col_mw(SolveAr
     }
     if constexpr (TC)
         tc_end(tcx, TCT);
+    }
 }
 
 // ---------------------------------------------------------------- launching
@@ -1712,7 +1757,7 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
 {
     using K = KShape<LOGN>;
     using S = KSmem<T, LOGN, TC>;
-    static std::atomic<unsigned long long> d[25];
+    static std::atomic<unsigned long long> d[26];
     const BatchView<T> none{nullptr, nullptr};
     const bool batch = bv != nullptr;
     const BatchView<T> v = batch ? *bv : none;
@@ -1800,6 +1845,12 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
         break;
     }
     case PASS_COL_MW: {
+        if (!batch && a.ncomp == 1) {  // the zero-rim potential (plans of one patch; never batched)
+            if ((e = ensure_smem(k_col_mw<T, LOGN, false, TC, 1>, S::col_mw(), d[25])) != cudaSuccess)
+                return e;
+            k_col_mw<T, LOGN, false, TC, 1><<<dim3(K::N + 1, 1), K::ROW_THREADS, S::col_mw(), st>>>(a, v);
+            break;
+        }
         SGF_LAUNCH((k_col_mw<T, LOGN, false, TC>), (k_col_mw<T, LOGN, true, TC>), 20, S::col_mw(),
                    dim3(K::N + 1, batch ? count : 1), K::ROW_THREADS)
         break;

@@ -167,12 +167,65 @@ def test_force_entry_points_refuse_potential_plans(lib):
     with pytest.raises(lib.SgfError) as ei:
         lib.Batch([pp])
     assert ei.value.status == lib.SGF_EUNSUPPORTED
+    zr = lib.Plan(nest, "fp32", zero_rim=True, potential=True)  # the zero-rim potential: col_pass 2 only
+    assert zr.schedule()["col_pass"] == 2
     with pytest.raises(lib.SgfError) as ei:
-        lib.Plan(nest, "fp32", zero_rim=True, potential=True)
-    assert ei.value.status == lib.SGF_EINVAL
+        zr.set_schedule(0, 0)
+    assert ei.value.status == lib.SGF_EUNSUPPORTED
     # a shared plan keeps the potential spectra, and gives the same numbers
     q = pp.share()
     a = pp.solve_potential(s)[0]
     b = q.solve_potential(s)[0]
     torch.cuda.synchronize()
     assert torch.equal(a, b)
+
+
+def _zero_rim_sigma(n, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    s = np.zeros((n, n))
+    s[2:-2, 2:-2] = rng.uniform(0.1, 1.0, (n - 4, n - 4))
+    return [s]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x"])
+@pytest.mark.parametrize("n", [64, 512])
+def test_zero_rim_potential_oracle(lib, prec, n):
+    """SGF_PLAN_ZERO_RIM | SGF_PLAN_POTENTIAL (one merged real table over sigma)
+    against the oracle on a density that is zero on the two outer rings."""
+    nest = W.Nest(n=n)
+    sigma = _zero_rim_sigma(n, 40 + n)
+    plan = lib.Plan(nest, prec, potential=True, zero_rim=True)
+    phi = run_phi(plan, sigma)
+    plan.check()
+    if n <= 64:
+        ref = oracle.potential(nest, sigma)[0]
+        assert np.abs(phi[0] - ref).max() <= tol(prec, n) * np.abs(ref).max()
+    else:
+        rng = np.random.Generator(np.random.PCG64(41))
+        ii, jj = rng.integers(0, n, 40), rng.integers(0, n, 40)
+        ref = oracle.potential_at(nest, sigma, np.zeros_like(ii), ii, jj)
+        assert np.abs(phi[0][jj, ii] - ref).max() <= tol(prec, n) * np.abs(ref).max()
+
+
+def test_zero_rim_potential_matches_general_4096(lib):
+    """The merged table and the three-table general plan evaluate the same sum."""
+    nest, sigma = W.config3()
+    a = run_phi(lib.Plan(nest, "fp32", potential=True, zero_rim=True), sigma)[0]
+    b = run_phi(lib.Plan(nest, "fp32", potential=True), sigma)[0]
+    assert np.abs(a - b).max() <= 1e-5 * np.abs(b).max()
+
+
+def test_zero_rim_potential_autotune(lib):
+    """The tuner keeps the zero-rim potential on its one applicable column schedule."""
+    n = 512
+    nest = W.Nest(n=n)
+    sigma = _zero_rim_sigma(n, 7)
+    plan = lib.Plan(nest, "fp32", potential=True, zero_rim=True)
+    r = plan.autotune(reps=1)
+    assert r["chosen"]["col_pass"] == 2
+    assert r["ms"]["col_pass0"] < 0 and r["ms"]["col_pass1"] < 0 and r["ms"]["col_pass2"] > 0
+    phi = run_phi(plan, sigma)[0]
+    rng = np.random.Generator(np.random.PCG64(42))
+    ii, jj = rng.integers(0, n, 30), rng.integers(0, n, 30)
+    ref = oracle.potential_at(nest, sigma, np.zeros_like(ii), ii, jj)
+    assert np.abs(phi[jj, ii] - ref).max() <= tol("fp32", n) * np.abs(ref).max()

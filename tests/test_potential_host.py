@@ -36,11 +36,18 @@ def test_estimate_two_level_sets(prec, esize):
     assert ep["spectra_bytes"] == 2 * q + 8 * f
 
 
-@pytest.mark.parametrize("flags", [sgf.PLAN_POTENTIAL | sgf.PLAN_ZERO_RIM, 0x4])
-def test_flag_rules(flags):
+@pytest.mark.parametrize("nest,flags", [(W.Nest(n=64, levels=1, off=[(0, 0)]), 0x4),
+                                        (W.centred_nest(64, 2), sgf.PLAN_POTENTIAL | sgf.PLAN_ZERO_RIM)])
+def test_flag_rules(nest, flags):
     with pytest.raises(sgf.SgfError) as ei:
-        sgf.estimate(W.Nest(n=64, levels=1, off=[(0, 0)]), "fp32", flags=flags)
+        sgf.estimate(nest, "fp32", flags=flags)
     assert ei.value.status == sgf.SGF_EINVAL
+
+
+def test_zero_rim_potential_one_merged_table():
+    n = 256
+    e = sgf.estimate(W.Nest(n=n, levels=1, off=[(0, 0)]), "fp32", flags=sgf.PLAN_POTENTIAL | sgf.PLAN_ZERO_RIM)
+    assert e["spectra_bytes"] == _al(1 * (n + 1) * (n + 8) * 4)
 
 
 def test_request_loop_refuses_potential():
