@@ -152,9 +152,15 @@ __host__ __device__ constexpr int tc_round(int logn, int tiles, int kind)
 }
 
 // ------------------------------------------------------------------ row_fwd
-// Shared memory: twiddle area | sigma rows[6][N] | sbuf[2 SP_ROW].
+// One CTA per (row pair, field): field f = blockIdx.y of (sigma, x slope, y
+// slope).  The rows it needs (ja and jb; for the y slope the rows either side of
+// each, clamped at the patch edge where the slope is one-sided) are staged in
+// the exchange buffers' space and read before the transform, so a CTA holds the
+// twiddles and the exchange buffers only (two CTAs per SM in FP32).
+// Shared memory: twiddle area | sbuf[2 SP_ROW] (first the staged rows).
 template <typename T, int LOGN, bool BATCH, bool TC>
-__global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd(SolveArgs<T> a0, BatchView<T> bv)
+__global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, sizeof(T) == 4 && !TC ? 2 : 1)
+    k_row_fwd(SolveArgs<T> a0, BatchView<T> bv)
 {
     const int2 wm = BATCH ? bv.map[blockIdx.x] : make_int2(0, (int)blockIdx.x);
     const SolveArgs<T> &a = BATCH ? bv.args[wm.x] : a0;
@@ -171,18 +177,25 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd(SolveArgs
     if constexpr (TC)
         tc_begin(tcx, smem_tc, TCT, TCR, a.status);
     C *tw = reinterpret_cast<C *>(smem_raw);
-    T *srow = reinterpret_cast<T *>(smem_raw + tw_bytes<C>(a.tw_entries));  // rows ja-1, ja, ja+1, jb-1, jb, jb+1
-    C *sbuf = reinterpret_cast<C *>(srow + 6 * N);
+    C *sbuf = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
+    T *srow = reinterpret_cast<T *>(sbuf);  // f < 2: rows ja, jb; f = 2: ja-1, ja+1, jb-1, jb+1
+    const int f = (int)blockIdx.y;
     const FwdItem item = a.fwd_items[wm.y];
     const FwdSlab sl = a.slabs[item.slab];
     const int rows = sl.rows, r0 = 2 * item.row_pair;
     const int ja = sl.m * r0 + sl.py, jb = sl.m * (r0 + 1) + sl.py;
     const T *src = a.src[sl.patch];
     cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
+    if (f < 2) {
+        cp_block(srow, src + (size_t)ja * N, (size_t)N * sizeof(T));
+        cp_block(srow + N, src + (size_t)jb * N, (size_t)N * sizeof(T));
+    } else {
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        const int jr = min(max((q < 3 ? ja : jb) + (q % 3) - 1, 0), N - 1);
-        cp_block(srow + q * N, src + (size_t)jr * N, (size_t)N * sizeof(T));
+        for (int q = 0; q < 4; ++q) {
+            const int jj = q < 2 ? ja : jb;
+            const int jr = (q & 1) ? min(jj + 1, N - 1) : max(jj - 1, 0);
+            cp_block(srow + q * N, src + (size_t)jr * N, (size_t)N * sizeof(T));
+        }
     }
     cp_commit();
     const int t = threadIdx.x;
@@ -191,64 +204,61 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd(SolveArgs
     const TwLayout tl = tw_layout(F16<LOGN>::twlen, N);
     cp_wait<0>();
     __syncthreads();
-    C2 *out = reinterpret_cast<C2 *>(a.fwd + sl.off);  // pairs of rows (r0, r0+1)
-    for (int f = 0; f < 3; ++f) {
-        C v[1][16];
-        if (active) {
+    C v[1][16];
+    if (active) {
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const int c = j + u * Q;
-                T fv[2] = {T(0), T(0)};
-                if (c < rows) {
-                    const int i = sl.m * c + sl.px;
+        for (int u = 0; u < 16; ++u) {
+            const int c = j + u * Q;
+            T fv[2] = {T(0), T(0)};
+            if (c < rows) {
+                const int i = sl.m * c + sl.px;
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int jj = h ? jb : ja;
-                        const T *r = srow + (3 * h + 1) * N;  // row jj; rows jj -+ 1 sit beside it
-                        if (covered(a, sl.patch, jj, i))
-                            continue;
-                        if (f == 0) {
-                            fv[h] = r[i];
-                        } else if (f == 1) {
-                            const int il = i == 0 ? 0 : i - 1, ir = i == N - 1 ? N - 1 : i + 1;
-                            const T d = r[ir] - r[il];
-                            fv[h] = (ir - il == 2) ? T(0.5) * d : d;
-                        } else {
-                            const T *rl = jj == 0 ? r : r - N;
-                            const T *rr = jj == N - 1 ? r : r + N;
-                            const T d = rr[i] - rl[i];
-                            fv[h] = (jj == 0 || jj == N - 1) ? d : T(0.5) * d;
-                        }
+                for (int h = 0; h < 2; ++h) {
+                    const int jj = h ? jb : ja;
+                    if (covered(a, sl.patch, jj, i))
+                        continue;
+                    if (f == 0) {
+                        fv[h] = srow[h * N + i];
+                    } else if (f == 1) {
+                        const T *r = srow + h * N;
+                        const int il = i == 0 ? 0 : i - 1, ir = i == N - 1 ? N - 1 : i + 1;
+                        const T d = r[ir] - r[il];
+                        fv[h] = (ir - il == 2) ? T(0.5) * d : d;
+                    } else {
+                        const T d = srow[(2 * h + 1) * N + i] - srow[2 * h * N + i];
+                        fv[h] = (jj == 0 || jj == N - 1) ? d : T(0.5) * d;
                     }
                 }
-                C z = hmk<C>(fv[0], fv[1]);
-                if (b)
-                    z = hmul(z, twist(tw, tl, j, u));
-                v[0][u] = z;
             }
+            C z = hmk<C>(fv[0], fv[1]);
+            if (b)
+                z = hmul(z, twist(tw, tl, j, u));
+            v[0][u] = z;
         }
-        // block barriers: a half barrier here would need one more block barrier per field
-        fft_ct<C, false, LOGN, 1, TC>(v, sbuf + b * SP, SP, j, active, tw, &tcx);
-        __syncthreads();
-        if (active) {
+    }
+    __syncthreads();  // the staged rows are read: the exchange buffers overwrite them
+    constexpr int HB = TC ? 0 : K::HB_ROW;
+    fft_ct<C, false, LOGN, 1, TC, HB>(v, sbuf + b * SP, SP, j, active, tw, &tcx, b);
+    __syncthreads();
+    if (active) {
 #pragma unroll
-            for (int u = 0; u < 16; ++u)
-                sbuf[b * SP + pad16(j + u * Q)] = v[0][u];
-        }
-        __syncthreads();
-        // X_a = (Z + conj Z~)/2, X_b = (Z - conj Z~)/(2i); Z~ = bin -kx, same parity half
-        for (int kx = t; kx <= N; kx += K::ROW_THREADS) {
-            const int bb = kx & 1, k = kx >> 1;
-            const int km = (N - bb - k) & (N - 1);
-            const C Z = sbuf[bb * SP + pad16(k)];
-            const C Zm = sbuf[bb * SP + pad16(km)];
-            C2 o;
-            o.x = T(0.5) * (Z.x + Zm.x);
-            o.y = T(0.5) * (Z.y - Zm.y);
-            o.z = T(0.5) * (Z.y + Zm.y);
-            o.w = T(-0.5) * (Z.x - Zm.x);
-            out[(((size_t)f * (N + 1) + kx) * rows + r0) >> 1] = o;
-        }
+        for (int u = 0; u < 16; ++u)
+            sbuf[b * SP + pad16(j + u * Q)] = v[0][u];
+    }
+    __syncthreads();
+    // X_a = (Z + conj Z~)/2, X_b = (Z - conj Z~)/(2i); Z~ = bin -kx, same parity half
+    C2 *out = reinterpret_cast<C2 *>(a.fwd + sl.off);  // pairs of rows (r0, r0+1)
+    for (int kx = t; kx <= N; kx += K::ROW_THREADS) {
+        const int bb = kx & 1, k = kx >> 1;
+        const int km = (N - bb - k) & (N - 1);
+        const C Z = sbuf[bb * SP + pad16(k)];
+        const C Zm = sbuf[bb * SP + pad16(km)];
+        C2 o;
+        o.x = T(0.5) * (Z.x + Zm.x);
+        o.y = T(0.5) * (Z.y - Zm.y);
+        o.z = T(0.5) * (Z.y + Zm.y);
+        o.w = T(-0.5) * (Z.x - Zm.x);
+        out[(((size_t)f * (N + 1) + kx) * rows + r0) >> 1] = o;
     }
     if constexpr (TC)
         tc_end(tcx, TCT);
@@ -1667,7 +1677,8 @@ struct KSmem {
     static size_t tw() { return tw_bytes<C>(tw_layout(F16<LOGN>::twlen, N).entries); }
     static size_t row_fwd()
     {
-        return rtc(KK_ROW_FWD) + tw() + 6 * (size_t)N * sizeof(T) + 2 * (size_t)KShape<LOGN>::SP_ROW * sizeof(C);
+        // the staged rows (at most 4 N reals) fit in the exchange buffers' 2 SP_ROW complex
+        return rtc(KK_ROW_FWD) + tw() + 2 * (size_t)KShape<LOGN>::SP_ROW * sizeof(C);
     }
     static size_t col()
     {
@@ -1800,7 +1811,7 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
     }
     switch (pass) {
     case PASS_ROW_FWD: {
-        SGF_LAUNCH((k_row_fwd<T, LOGN, false, TC>), (k_row_fwd<T, LOGN, true, TC>), 0, S::row_fwd(), dim3(count),
+        SGF_LAUNCH((k_row_fwd<T, LOGN, false, TC>), (k_row_fwd<T, LOGN, true, TC>), 0, S::row_fwd(), dim3(count, 3),
                    K::ROW_THREADS)
         break;
     }
