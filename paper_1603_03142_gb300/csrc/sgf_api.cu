@@ -982,8 +982,10 @@ cudaError_t launch_col(const sgf_plan *p, const SolveArgs<T> &a, cudaStream_t st
         e = launch_pass_n<T>(colp, p->logN, a, (int)p->work_all.size(), st, nullptr, p->tc);
     } else {
         e = launch_pass_n<T>(colp, p->logN, a, (int)p->work_main.size(), st, nullptr, p->tc);
+        // the Case-3 groups: one CTA per column as well where the six fields fit (N <= 2048)
+        const int grp = p->sched.col_pass == 2 && p->N <= 2048 ? PASS_COL_GW : PASS_COL_G;
         if (e == cudaSuccess && !p->groups.empty())
-            e = launch_pass_n<T>(PASS_COL_G, p->logN, a, (int)p->groups.size(), st, nullptr, p->tc);
+            e = launch_pass_n<T>(grp, p->logN, a, (int)p->groups.size(), st, nullptr, p->tc);
     }
     if (e != cudaSuccess || p->sums.empty())
         return e;
@@ -1309,7 +1311,8 @@ sgf_status batch_launches(sgf_batch *bt, cudaStream_t st)
             return cuda_fail(e, "batched col launch");
         if (g.n_grp > 0) {
             BatchView<T> vg{args, bt->d_maps + g.map_grp};
-            if ((e = launch_pass_n<T>(PASS_COL_G, g.logN, dummy, g.n_grp, st, &vg, g.tc)) != cudaSuccess)
+            const int grp = !g.merged && g.sched.col_pass == 2 && g.logN <= 11 ? PASS_COL_GW : PASS_COL_G;
+            if ((e = launch_pass_n<T>(grp, g.logN, dummy, g.n_grp, st, &vg, g.tc)) != cudaSuccess)
                 return cuda_fail(e, "batched Case-3 group launch");
         }
         if (g.n_sum > 0) {

@@ -784,6 +784,129 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
         tc_end(tcx, TCT);
 }
 
+// ------------------------------------------------------------------ col_gw
+// k_col_g with both parity halves in one CTA (thread t: half t / Q, slot t mod
+// Q), each half transforming on its own named barrier: half b keeps the three
+// transformed source fields at fld + 3 b N, and per output folds through
+// shared memory with each half storing one component (the potential: one
+// inverse transform, the even half storing).  FP32 without tensor-core tiles,
+// 512 <= N <= 2048 (at 4096 the six fields do not fit).
+// Shared memory: twiddle area | sbuf[2][2 SPC] (half b's two exchange buffers
+// at sbuf + 2 b SPC; the 2N fold at the start) | fld[2][3][N].
+template <typename T, int LOGN, bool BATCH>
+__global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 1) k_col_gw(SolveArgs<T> a0, BatchView<T> bv)
+{
+    const int2 wm = BATCH ? bv.map[blockIdx.y] : make_int2(0, (int)blockIdx.y);
+    const SolveArgs<T> &a = BATCH ? bv.args[wm.x] : a0;
+    using C = typename Cx<T>::C;
+    using K = KShape<LOGN>;
+    constexpr int N = K::N, Q = K::Q, P = 2 * N;
+    constexpr int SPC = col_sp<C>(N);
+    constexpr int HB = K::HB_ROW;
+    static_assert(HB > 0, "whole warps per half: N >= 512");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *sbuf = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
+    const int t = threadIdx.x;
+    const int b = t / Q, j = t - b * Q;
+    C *fld = sbuf + 4 * SPC + 3 * b * N;  // this half's three transformed fields
+    const int kx = blockIdx.x;
+    const TwLayout tl = tw_layout(F16<LOGN>::twlen, N);
+    const ColGroup g = a.groups[wm.y];
+    const FwdSlab sl = a.slabs[a.ins[a.outs[g.out_begin].in_begin].slab];
+    cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
+    cp_commit();
+    cp_wait<0>();
+    __syncthreads();
+    {
+        C v[1][16];
+#pragma unroll 1
+        for (int f = 0; f < 3; ++f) {
+            const C *col = a.fwd + sl.off + ((size_t)f * (N + 1) + kx) * sl.rows;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int n = j + u * Q;
+                C x = hmk<C>(T(0), T(0));
+                if (n < sl.rows) {
+                    x = col[n];
+                    if (b)
+                        x = hmul(x, twist(tw, tl, j, u));
+                }
+                v[0][u] = x;
+            }
+            fft_ct<C, false, LOGN, 1, false, HB>(v, sbuf + 2 * b * SPC, SPC, j, true, tw, nullptr, b);
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+                fld[f * N + u * Q + j] = v[0][u];  // read back by this thread only
+        }
+    }
+    const C *spec = reinterpret_cast<const C *>(a.spec);
+    const bool two = a.ncomp == 2;
+#pragma unroll 1
+    for (int q = 0; q < g.out_count; ++q) {
+        const ColOutput o = a.outs[g.out_begin + q];
+        const ColInput ci = a.ins[o.in_begin];
+        C acc[2][16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            acc[0][u] = hmk<C>(T(0), T(0));
+            acc[1][u] = hmk<C>(T(0), T(0));
+        }
+        if (ci.kind == SPEC_FULL_PHI) {  // the potential alone
+#pragma unroll 1
+            for (int f = 0; f < 3; ++f) {
+                const C *sx = spec + ci.spec_off + ((size_t)f * (N + 1) + kx) * P;
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int ky = 2 * (j + u * Q) + b;
+                    acc[0][u] = hadd(acc[0][u], hmul(__ldg(sx + ky), fld[f * N + u * Q + j]));
+                }
+            }
+        } else {
+#pragma unroll 1
+            for (int f = 0; f < 3; ++f) {
+                const C *sx = spec + ci.spec_off + ((size_t)f * (N + 1) + kx) * P;
+                const C *sy = spec + ci.spec_off + ((size_t)(3 + f) * (N + 1) + kx) * P;
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int ky = 2 * (j + u * Q) + b;
+                    const C x = fld[f * N + u * Q + j];
+                    acc[0][u] = hadd(acc[0][u], hmul(__ldg(sx + ky), x));
+                    acc[1][u] = hadd(acc[1][u], hmul(__ldg(sy + ky), x));
+                }
+            }
+        }
+        // the inverse transforms of this half; y[n] = even[n] + W_P^{-n} odd[n]
+        if (two)
+            fft_ct<C, true, LOGN, 2, false, HB>(acc, sbuf + 2 * b * SPC, SPC, j, true, tw, nullptr, b);
+        else
+            fft_ct<C, true, LOGN, 1, false, HB>(acc, sbuf + 2 * b * SPC, SPC, j, true, tw, nullptr, b);
+        __syncthreads();  // every exchange buffer has been read
+        C *fold = sbuf;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int n = j + u * Q;
+            if (b == 1)
+                fold[n] = hmulc(acc[0][u], twist(tw, tl, j, u));
+            else if (two)
+                fold[N + n] = acc[1][u];
+        }
+        __syncthreads();
+        C *out = a.bwd + o.off;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int n = j + u * Q;
+            if (n >= o.rows)
+                continue;
+            if (b == 0)
+                out[bwd_index(N, o.rows, 0, kx, n)] = hadd(acc[0][u], fold[n]);
+            else if (two)
+                out[bwd_index(N, o.rows, 1, kx, n)] = hadd(fold[N + n], hmulc(acc[1][u], twist(tw, tl, j, u)));
+        }
+        __syncthreads();  // the fold has been read: the next output's exchanges overwrite it
+    }
+}
+
 // ----------------------------------------------------------------- col_sum
 // Second half of the column pass of an output whose input list was split into
 // chunks (k_col work items with a partial slot): the chunks' spectral
@@ -1712,6 +1835,10 @@ struct KSmem {
         return tc(KShape<LOGN>::COL_THREADS, 1, KK_COL_M) + tw() + (size_t)col_sp<C>(N) * sizeof(C) +
                (size_t)N * sizeof(C);
     }
+    static size_t col_gw()
+    {
+        return tw() + 4 * (size_t)col_sp<C>(N) * sizeof(C) + 6 * (size_t)N * sizeof(C);
+    }
     static size_t col_g()
     {
         return tc(KShape<LOGN>::COL_THREADS, 2, KK_COL_G) + tw() + 2 * (size_t)col_sp<C>(N) * sizeof(C) +
@@ -1768,7 +1895,7 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
 {
     using K = KShape<LOGN>;
     using S = KSmem<T, LOGN, TC>;
-    static std::atomic<unsigned long long> d[26];
+    static std::atomic<unsigned long long> d[28];
     const BatchView<T> none{nullptr, nullptr};
     const bool batch = bv != nullptr;
     const BatchView<T> v = batch ? *bv : none;
@@ -1872,6 +1999,17 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
                 return cudaErrorInvalidConfiguration;
             SGF_LAUNCH((k_col_w<T, LOGN, false>), (k_col_w<T, LOGN, true>), 23, S::col_w(), dim3(K::N + 1, count),
                        K::ROW_THREADS)
+        } else {
+            return cudaErrorInvalidValue;
+        }
+        break;
+    }
+    case PASS_COL_GW: {
+        if constexpr (!TC && K::HB_ROW > 0 && sizeof(T) == 4) {
+            if (S::col_gw() > kMaxDynSmem)
+                return cudaErrorInvalidConfiguration;
+            SGF_LAUNCH((k_col_gw<T, LOGN, false>), (k_col_gw<T, LOGN, true>), 26, S::col_gw(),
+                       dim3(K::N + 1, count), K::ROW_THREADS)
         } else {
             return cudaErrorInvalidValue;
         }
