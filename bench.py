@@ -378,7 +378,9 @@ def run_gpu(args, world, rank, local):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
     e2e = {"value": world * cells * e2e_steps / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": n * n * 4, "d2h_bytes_per_step": 2 * n * n * 4}
+           "h2d_bytes_per_step": n * n * 4, "d2h_bytes_per_step": 2 * n * n * 4,
+           "transfer": "sigma copied to the device; Fx, Fy written by the inverse row pass "
+                       "in place to page-locked host memory"}
 
     if rank != 0:
         return

@@ -217,9 +217,14 @@ sgf_status sgf_solve(sgf_plan *plan, const void *const *sigma, void *const *fx, 
  * made without SGF_PLAN_POTENTIAL), SGF_ECUDA (launch). */
 sgf_status sgf_solve_potential(sgf_plan *plan, const void *const *sigma, void *const *phi, void *stream);
 
-/* As sgf_solve, but sigma, fx and fy are HOST pointers (pinned memory gives
- * asynchronous copies).  Copies sigma to the plan's device staging, solves,
- * copies the forces back, and waits for the stream before returning. */
+/* As sgf_solve, but sigma, fx and fy are HOST pointers; waits for the stream
+ * before returning.  sigma is copied to the plan's device staging (allocated
+ * on the first call, 3 * levels arrays, reported in workspace_bytes).  An
+ * output buffer that is page-locked and mapped at the same address on the
+ * device (cudaHostAlloc, or cudaHostRegister, under unified addressing; its
+ * first and last byte are checked) is written by the inverse row pass in place
+ * over the CPU-GPU link; any other output is staged and copied back.  Errors:
+ * as sgf_solve, plus SGF_ENOMEM/SGF_ECUDA from the staging and the copies. */
 sgf_status sgf_solve_host(sgf_plan *plan, const void *const *sigma, void *const *fx,
                           void *const *fy, void *stream);
 

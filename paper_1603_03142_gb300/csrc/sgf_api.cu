@@ -1928,6 +1928,25 @@ sgf_status sgf_solve_potential(sgf_plan *p, const void *const *sigma, void *cons
     return solve_dispatch(p, sigma, phi, nullptr, static_cast<cudaStream_t>(stream));
 }
 
+// A host buffer of `bytes` bytes that kernels may address in place: page-locked
+// and mapped into the device's address space at the same address (memory from
+// cudaHostAlloc, or registered with cudaHostRegister, under unified
+// addressing).  Both ends are checked.  Anything else is staged with copies.
+static bool host_mapped(const void *ptr, size_t bytes)
+{
+    for (const unsigned char *q : {static_cast<const unsigned char *>(ptr),
+                                   static_cast<const unsigned char *>(ptr) + bytes - 1}) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, q) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if (at.type != cudaMemoryTypeHost || at.devicePointer != static_cast<const void *>(q))
+            return false;
+    }
+    return true;
+}
+
 sgf_status sgf_solve_host(sgf_plan *p, const void *const *sigma, void *const *fx, void *const *fy,
                           void *stream)
 {
@@ -1938,6 +1957,15 @@ sgf_status sgf_solve_host(sgf_plan *p, const void *const *sigma, void *const *fx
     const size_t lvl = (size_t)p->N * p->N * p->esize;
     const size_t lvl_al = (lvl + 255) & ~(size_t)255;
     cudaError_t e;
+    // sigma always goes through the staging by a copy: the copy engine reads
+    // host memory faster than the forward row pass does.  Mapped page-locked
+    // output buffers are written by the inverse row pass in place, over the
+    // CPU-GPU link, which saves the device-to-host copy; others are staged.
+    bool map_x[kMaxPatches], map_y[kMaxPatches];
+    for (int l = 0; l < p->L; ++l) {
+        map_x[l] = host_mapped(fx[l], lvl);
+        map_y[l] = host_mapped(fy[l], lvl);
+    }
     if (!p->d_stage) {
         if ((e = cudaMalloc(&p->d_stage, 3 * (size_t)p->L * lvl_al)) != cudaSuccess)
             return cuda_fail(e, "cudaMalloc(host-solve staging)");
@@ -1949,8 +1977,8 @@ sgf_status sgf_solve_host(sgf_plan *p, const void *const *sigma, void *const *fx
     void *dx[kMaxPatches], *dy[kMaxPatches];
     for (int l = 0; l < p->L; ++l) {
         ds[l] = base + (size_t)l * lvl_al;
-        dx[l] = base + (size_t)(p->L + l) * lvl_al;
-        dy[l] = base + (size_t)(2 * p->L + l) * lvl_al;
+        dx[l] = map_x[l] ? fx[l] : base + (size_t)(p->L + l) * lvl_al;
+        dy[l] = map_y[l] ? fy[l] : base + (size_t)(2 * p->L + l) * lvl_al;
         if ((e = cudaMemcpyAsync(const_cast<void *>(ds[l]), sigma[l], lvl, cudaMemcpyHostToDevice, st)) != cudaSuccess)
             return cuda_fail(e, "cudaMemcpyAsync(sigma H2D)");
     }
@@ -1958,8 +1986,8 @@ sgf_status sgf_solve_host(sgf_plan *p, const void *const *sigma, void *const *fx
     if (s != SGF_OK)
         return s;
     for (int l = 0; l < p->L; ++l) {
-        if ((e = cudaMemcpyAsync(fx[l], dx[l], lvl, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(fy[l], dy[l], lvl, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        if ((!map_x[l] && (e = cudaMemcpyAsync(fx[l], dx[l], lvl, cudaMemcpyDeviceToHost, st)) != cudaSuccess) ||
+            (!map_y[l] && (e = cudaMemcpyAsync(fy[l], dy[l], lvl, cudaMemcpyDeviceToHost, st)) != cudaSuccess))
             return cuda_fail(e, "cudaMemcpyAsync(force D2H)");
     }
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess)

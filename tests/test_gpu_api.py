@@ -44,6 +44,56 @@ def test_host_buffers_match_device(lib):
         assert np.array_equal(hy[l].astype(np.float64), dy[l])
 
 
+def _pinned(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+
+
+@pytest.mark.parametrize("mapped", ["all", "sigma", "forces"])
+def test_mapped_host_buffers_are_used_in_place(lib, mapped):
+    """Page-locked output buffers are written by the kernels in place, pageable
+    ones through the staging; sigma is copied either way.  Same bits as the
+    device-buffer solve in every mix."""
+    nest = W.Nest(n=64, levels=3, off=[(0, 0), (10, 20), (16, 0)])
+    rng = np.random.Generator(np.random.PCG64(12))
+    sigma = [rng.uniform(0, 1, (64, 64)).astype(np.float32) for _ in range(3)]
+    plan = lib.Plan(nest, "fp32")
+    dx, dy = run_gpu(plan, sigma)
+    before = plan.stats()["workspace_bytes"]
+    ps = [_pinned(a) for a in sigma] if mapped in ("all", "sigma") else [np.ascontiguousarray(a) for a in sigma]
+    if mapped in ("all", "forces"):
+        hx = [_pinned(np.full((64, 64), np.nan, np.float32)) for _ in range(3)]
+        hy = [_pinned(np.full((64, 64), np.nan, np.float32)) for _ in range(3)]
+    else:
+        hx = [np.full((64, 64), np.nan, np.float32) for _ in range(3)]
+        hy = [np.full((64, 64), np.nan, np.float32) for _ in range(3)]
+
+    def ptr(a):
+        return a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data
+
+    for _ in range(2):
+        plan.solve_host_ptrs([ptr(a) for a in ps], [ptr(a) for a in hx], [ptr(a) for a in hy])
+        for l in range(3):
+            gx = hx[l].numpy() if isinstance(hx[l], torch.Tensor) else hx[l]
+            gy = hy[l].numpy() if isinstance(hy[l], torch.Tensor) else hy[l]
+            assert np.array_equal(gx.astype(np.float64), dx[l])
+            assert np.array_equal(gy.astype(np.float64), dy[l])
+    assert plan.stats()["workspace_bytes"] == before + 3 * 3 * 64 * 64 * 4
+
+
+def test_mapped_host_buffers_zero_rim_4096(lib):
+    """The bench's end-to-end call: 4096^2 zero-rim FP32 with page-locked buffers."""
+    nest, sigma = W.config3(4096, seed=3)
+    sigma = sigma[0].astype(np.float32)
+    plan = lib.Plan(nest, "fp32", zero_rim=True)
+    ts = torch.from_numpy(sigma).cuda()
+    dx, dy = torch.empty_like(ts), torch.empty_like(ts)
+    plan.solve_ptrs([ts.data_ptr()], [dx.data_ptr()], [dy.data_ptr()])
+    torch.cuda.synchronize()
+    ps, hx, hy = _pinned(sigma), _pinned(np.zeros_like(sigma)), _pinned(np.zeros_like(sigma))
+    plan.solve_host_ptrs([ps.data_ptr()], [hx.data_ptr()], [hy.data_ptr()])
+    assert torch.equal(hx, dx.cpu()) and torch.equal(hy, dy.cpu())
+
+
 def test_deterministic_and_shared_plan(lib):
     nest, sigma = W.config2(n=64)
     plan = lib.Plan(nest, "fp32")
