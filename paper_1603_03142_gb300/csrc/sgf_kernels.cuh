@@ -1642,6 +1642,12 @@ __global__ void __cluster_dims__(2, 1, 1)
 // (thread t: half t / (N/16), slot t mod (N/16)): the column is staged once and
 // the odd half is folded through shared memory under the CTA barrier, with no
 // cluster.  Both inverse transforms in flight (two sequences per thread).
+// The CTA walks the columns kx = blockIdx.x, blockIdx.x + gridDim.x, ... (one
+// resident CTA per SM holds the whole shared memory, so consecutive columns of
+// separate CTAs could not overlap): once the forward transform and the
+// spectral product have consumed a column's staging, the next column's input
+// is copied in behind the inverse transforms.  Batches launch one CTA per
+// (column, work item) and walk one column.
 // Shared memory: twiddle area | column[N] | Gx, Gy half rows of both halves |
 // exchange buffers, half b's two sequences at sbuf + 2 b SPC (then the fold).
 // NC = 2: the forces (Gx, Gy); NC = 1: the potential (Gphi alone, one inverse transform).
@@ -1666,123 +1672,128 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 1) k_col_mw(SolveAr
     C *col = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
     T *gsp = reinterpret_cast<T *>(col + N);  // [half][Gx, Gy][HQ]
     C *sbuf = reinterpret_cast<C *>(gsp + 4 * HQ);
-    const int kx = blockIdx.x;
     const int t = threadIdx.x;
     const bool active = t < 2 * Q;
     const int b = active ? t / Q : 0, j = active ? t - b * Q : 0;
     const TwLayout tl = tw_layout(F16<LOGN>::twlen, N);
     const T *spec = reinterpret_cast<const T *>(a.spec);
-    cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
-    cp_block(col, a.fwd + (size_t)kx * N, (size_t)N * sizeof(C));
     constexpr bool two = NC == 2;  // the forces (Gx, Gy); else the potential (Gphi alone)
+    auto stage = [&](int kx) {  // whole block: column kx of the forward slab and its spectra half rows
+        cp_block(col, a.fwd + (size_t)kx * N, (size_t)N * sizeof(C));
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        cp_block(gsp + (2 * h) * HQ, spec + (size_t)kx * QS + h * HQ, (size_t)HQ * sizeof(T));
-        if (two)
-            cp_block(gsp + (2 * h + 1) * HQ, spec + ((size_t)(N + 1) + kx) * QS + h * HQ, (size_t)HQ * sizeof(T));
-    }
-    cp_commit();
-    cp_wait<0>();
-    __syncthreads();
-    C acc[2][16];
-    {
-        C v[1][16];
-        if (active) {
+        for (int h = 0; h < 2; ++h) {
+            cp_block(gsp + (2 * h) * HQ, spec + (size_t)kx * QS + h * HQ, (size_t)HQ * sizeof(T));
+            if (two)
+                cp_block(gsp + (2 * h + 1) * HQ, spec + ((size_t)(N + 1) + kx) * QS + h * HQ, (size_t)HQ * sizeof(T));
+        }
+        cp_commit();
+    };
+    cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
+    stage(blockIdx.x);
+    for (int kx = blockIdx.x; kx <= N; kx += gridDim.x) {
+        cp_wait<0>();
+        __syncthreads();  // column kx staged; the previous column's fold has been read
+        C acc[2][16];
+        {
+            C v[1][16];
+            if (active) {
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                C x = col[j + u * Q];
-                if (b)
-                    x = hmul(x, twist(tw, tl, j, u));
-                v[0][u] = x;
+                for (int u = 0; u < 16; ++u) {
+                    C x = col[j + u * Q];
+                    if (b)
+                        x = hmul(x, twist(tw, tl, j, u));
+                    v[0][u] = x;
+                }
+            }
+            // each half transforms in its own buffers until the fold: half barriers
+            fft_ct<C, false, LOGN, 1, TC, TC ? 0 : K::HB_ROW>(v, sbuf + 2 * b * SPC, SPC, j, active, tw, &tcx, b);
+            if constexpr (two) {
+                if (active) {
+                    const T *gx_r = gsp + (2 * b) * HQ, *gy_r = gsp + (2 * b + 1) * HQ;
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const int kp = j + u * Q;
+                        const bool hi = 2 * kp + b > N;
+                        const int q = hi ? N - kp - b : kp;
+                        const T gx = gx_r[q];                        // Gx even in ky
+                        const T gy = hi ? -gy_r[q] : gy_r[q];        // Gy odd in ky
+                        acc[0][u] = hmk<C>(-gx * v[0][u].y, gx * v[0][u].x);  // i gx v
+                        acc[1][u] = hmk<C>(-gy * v[0][u].y, gy * v[0][u].x);
+                    }
+                }
+            } else if (active) {
+                const T *gp_r = gsp + (2 * b) * HQ;
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int kp = j + u * Q;
+                    const int q = 2 * kp + b > N ? N - kp - b : kp;
+                    const T gp = gp_r[q];  // Gphi real, even in ky
+                    acc[0][u] = hmk<C>(gp * v[0][u].x, gp * v[0][u].y);
+                }
             }
         }
-        // each half transforms in its own buffers until the fold: half barriers
-        fft_ct<C, false, LOGN, 1, TC, TC ? 0 : K::HB_ROW>(v, sbuf + 2 * b * SPC, SPC, j, active, tw, &tcx, b);
-        if constexpr (two) {
-          if (active) {
-            const T *gx_r = gsp + (2 * b) * HQ, *gy_r = gsp + (2 * b + 1) * HQ;
-#pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const int kp = j + u * Q;
-                const bool hi = 2 * kp + b > N;
-                const int q = hi ? N - kp - b : kp;
-                const T gx = gx_r[q];                        // Gx even in ky
-                const T gy = hi ? -gy_r[q] : gy_r[q];        // Gy odd in ky
-                acc[0][u] = hmk<C>(-gx * v[0][u].y, gx * v[0][u].x);  // i gx v
-                acc[1][u] = hmk<C>(-gy * v[0][u].y, gy * v[0][u].x);
-            }
-          }
-        } else if (active) {
-            const T *gp_r = gsp + (2 * b) * HQ;
-#pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const int kp = j + u * Q;
-                const int q = 2 * kp + b > N ? N - kp - b : kp;
-                const T gp = gp_r[q];  // Gphi real, even in ky
-                acc[0][u] = hmk<C>(gp * v[0][u].x, gp * v[0][u].y);
-            }
+        if (kx + (int)gridDim.x <= N) {  // uniform over the block
+            __syncthreads();  // every thread is done with the column and the spectra rows
+            stage(kx + gridDim.x);
         }
-    }
-    if constexpr (!two) {  // the potential: one inverse transform, the stores split by n between the halves
-        fft_ct<C, true, LOGN, 1, TC, TC ? 0 : K::HB_ROW>(acc, sbuf + 2 * b * SPC, SPC, j, active, tw, &tcx, b);
-        __syncthreads();  // every exchange buffer has been read
-        C *fold = sbuf;
-        if (active) {
-#pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const int n = j + u * Q;
-                if (b == 1 && u < 8)
-                    fold[n] = hmulc(acc[0][u], twist(tw, tl, j, u));
-                else if (b == 0 && u >= 8)
-                    fold[n] = acc[0][u];
-            }
-        }
-        __syncthreads();
-        if (active) {
-            C *dst = a.bwd;
-#pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const int n = j + u * Q;
-                if (b == 0 && u < 8)
-                    dst[bwd_index(N, N, 0, kx, n)] = hadd(acc[0][u], fold[n]);
-                else if (b == 1 && u >= 8)
-                    dst[bwd_index(N, N, 0, kx, n)] = hadd(fold[n], hmulc(acc[0][u], twist(tw, tl, j, u)));
-            }
-        }
-        if constexpr (TC)
-            tc_end(tcx, TCT);
-        return;
-    } else {
-    fft_ct<C, true, LOGN, 2, TC, TC ? 0 : K::HB_ROW>(acc, sbuf + 2 * b * SPC, SPC, j, active, tw, &tcx, b);
-    __syncthreads();  // every exchange buffer has been read
-    // fold y = even + W_P^{-n} odd, one component per half: the odd half hands over
-    // Fx's twisted values, the even half Fy's own, and each stores one component
-    C *fold = sbuf;
-    if (active) {
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const int n = j + u * Q;
-            if (b == 1)
-                fold[n] = hmulc(acc[0][u], twist(tw, tl, j, u));
-            else
-                fold[N + n] = acc[1][u];
-        }
-    }
-    __syncthreads();
-    if (active) {
         C *dst = a.bwd;
+        if constexpr (!two) {  // the potential: one inverse transform, the stores split by n between the halves
+            fft_ct<C, true, LOGN, 1, TC, TC ? 0 : K::HB_ROW>(acc, sbuf + 2 * b * SPC, SPC, j, active, tw, &tcx, b);
+            __syncthreads();  // every exchange buffer has been read
+            C *fold = sbuf;
+            if (active) {
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const int n = j + u * Q;
-            if (b == 0)
-                dst[bwd_index(N, N, 0, kx, n)] = hadd(acc[0][u], fold[n]);
-            else
-                dst[bwd_index(N, N, 1, kx, n)] = hadd(fold[N + n], hmulc(acc[1][u], twist(tw, tl, j, u)));
+                for (int u = 0; u < 16; ++u) {
+                    const int n = j + u * Q;
+                    if (b == 1 && u < 8)
+                        fold[n] = hmulc(acc[0][u], twist(tw, tl, j, u));
+                    else if (b == 0 && u >= 8)
+                        fold[n] = acc[0][u];
+                }
+            }
+            __syncthreads();
+            if (active) {
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int n = j + u * Q;
+                    if (b == 0 && u < 8)
+                        dst[bwd_index(N, N, 0, kx, n)] = hadd(acc[0][u], fold[n]);
+                    else if (b == 1 && u >= 8)
+                        dst[bwd_index(N, N, 0, kx, n)] = hadd(fold[n], hmulc(acc[0][u], twist(tw, tl, j, u)));
+                }
+            }
+        } else {
+            fft_ct<C, true, LOGN, 2, TC, TC ? 0 : K::HB_ROW>(acc, sbuf + 2 * b * SPC, SPC, j, active, tw, &tcx, b);
+            __syncthreads();  // every exchange buffer has been read
+            // fold y = even + W_P^{-n} odd, one component per half: the odd half hands over
+            // Fx's twisted values, the even half Fy's own, and each stores one component
+            C *fold = sbuf;
+            if (active) {
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int n = j + u * Q;
+                    if (b == 1)
+                        fold[n] = hmulc(acc[0][u], twist(tw, tl, j, u));
+                    else
+                        fold[N + n] = acc[1][u];
+                }
+            }
+            __syncthreads();
+            if (active) {
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int n = j + u * Q;
+                    if (b == 0)
+                        dst[bwd_index(N, N, 0, kx, n)] = hadd(acc[0][u], fold[n]);
+                    else
+                        dst[bwd_index(N, N, 1, kx, n)] = hadd(fold[N + n], hmulc(acc[1][u], twist(tw, tl, j, u)));
+                }
+            }
         }
     }
+    cp_wait<0>();  // nothing in flight at exit (every staged copy was waited for above)
     if constexpr (TC)
         tc_end(tcx, TCT);
-    }
 }
 
 // ---------------------------------------------------------------- launching
@@ -1890,12 +1901,36 @@ inline cudaError_t ensure_smem(F *kernel, size_t bytes, std::atomic<unsigned lon
     return e;
 }
 
+// CTAs of a kernel that are resident on the current device at once (SMs x
+// CTAs per SM at this block size and shared memory), found once per device
+// for each kernel instance; the grid of a kernel that walks its work items.
+template <typename F>
+inline cudaError_t resident_ctas(F *kernel, int threads, size_t smem, std::atomic<int> (&cache)[64], int *out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    int n = cache[dev & 63].load(std::memory_order_acquire);
+    if (n <= 0) {
+        int sms = 0, per_sm = 0;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+            (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem)) != cudaSuccess)
+            return e;
+        n = sms * (per_sm > 0 ? per_sm : 1);
+        cache[dev & 63].store(n, std::memory_order_release);
+    }
+    *out = n;
+    return cudaSuccess;
+}
+
 template <typename T, int LOGN, bool TC>
 cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t st, const BatchView<T> *bv)
 {
     using K = KShape<LOGN>;
     using S = KSmem<T, LOGN, TC>;
     static std::atomic<unsigned long long> d[28];
+    static std::atomic<int> res_mw[64], res_mw1[64];  // resident CTAs of the walking column pass (NC = 2, 1)
     const BatchView<T> none{nullptr, nullptr};
     const bool batch = bv != nullptr;
     const BatchView<T> v = batch ? *bv : none;
@@ -1932,7 +1967,15 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
             (e = ensure_smem(k_col_g<T, LOGN, false, TC>, S::col_g(), d[14])) != cudaSuccess ||
             (e = ensure_smem(k_col_g<T, LOGN, true, TC>, S::col_g(), d[15])) != cudaSuccess ||
             (e = ensure_smem(k_col_sum<T, LOGN, false, TC>, S::col_sum(), d[16])) != cudaSuccess ||
-            (e = ensure_smem(k_col_sum<T, LOGN, true, TC>, S::col_sum(), d[17])) != cudaSuccess)
+            (e = ensure_smem(k_col_sum<T, LOGN, true, TC>, S::col_sum(), d[17])) != cudaSuccess ||
+            (e = ensure_smem(k_col_mw<T, LOGN, false, TC, 1>, S::col_mw(), d[25])) != cudaSuccess)
+            return e;
+        int grid = 0;
+        if (S::col_mw() <= kMaxDynSmem &&
+            ((e = resident_ctas(k_col_mw<T, LOGN, false, TC>, K::ROW_THREADS, S::col_mw(), res_mw, &grid)) !=
+                 cudaSuccess ||
+             (e = resident_ctas(k_col_mw<T, LOGN, false, TC, 1>, K::ROW_THREADS, S::col_mw(), res_mw1, &grid)) !=
+                 cudaSuccess))
             return e;
         return cudaSuccess;
     }
@@ -1983,14 +2026,26 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
         break;
     }
     case PASS_COL_MW: {
+        // one pass: the CTAs that fit at once walk the N + 1 columns; batches: one CTA per (column, item)
+        int grid = 0;
         if (!batch && a.ncomp == 1) {  // the zero-rim potential (plans of one patch; never batched)
-            if ((e = ensure_smem(k_col_mw<T, LOGN, false, TC, 1>, S::col_mw(), d[25])) != cudaSuccess)
+            if ((e = ensure_smem(k_col_mw<T, LOGN, false, TC, 1>, S::col_mw(), d[25])) != cudaSuccess ||
+                (e = resident_ctas(k_col_mw<T, LOGN, false, TC, 1>, K::ROW_THREADS, S::col_mw(), res_mw1, &grid)) !=
+                    cudaSuccess)
                 return e;
-            k_col_mw<T, LOGN, false, TC, 1><<<dim3(K::N + 1, 1), K::ROW_THREADS, S::col_mw(), st>>>(a, v);
+            k_col_mw<T, LOGN, false, TC, 1><<<dim3(grid < K::N + 1 ? grid : K::N + 1, 1), K::ROW_THREADS,
+                                               S::col_mw(), st>>>(a, v);
             break;
         }
+        if (batch) {
+            grid = K::N + 1;
+        } else if ((e = ensure_smem(k_col_mw<T, LOGN, false, TC>, S::col_mw(), d[20])) != cudaSuccess ||
+                   (e = resident_ctas(k_col_mw<T, LOGN, false, TC>, K::ROW_THREADS, S::col_mw(), res_mw, &grid)) !=
+                       cudaSuccess) {
+            return e;
+        }
         SGF_LAUNCH((k_col_mw<T, LOGN, false, TC>), (k_col_mw<T, LOGN, true, TC>), 20, S::col_mw(),
-                   dim3(K::N + 1, batch ? count : 1), K::ROW_THREADS)
+                   dim3(grid < K::N + 1 ? grid : K::N + 1, batch ? count : 1), K::ROW_THREADS)
         break;
     }
     case PASS_COL_W: {
