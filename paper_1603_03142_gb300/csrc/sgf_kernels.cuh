@@ -1359,6 +1359,11 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 2) k_row_inv1t(cons
 // slopes are folded into the merged spectra).  Also verifies the guarantee:
 // the CTAs of rows 0-1 and N-2..N-1 scan their rows, every CTA its cells in
 // columns 0, 1, N-2, N-1; a nonzero value sets STATUS_RIM_NONZERO.
+// The CTA walks the row pairs blockIdx.x, blockIdx.x + gridDim.x, ...: once a
+// pair's rows are in registers, the next pair's rows are copied in behind the
+// transform.  Only the tensor-core instances walk (launched with the CTAs that
+// fit at once; each CTA builds its DFT tiles and takes its tensor memory once);
+// the others, and batches, take one row pair per CTA, which measured faster.
 // Shared memory: twiddle area | sigma rows[2][N] | sbuf[2 SP_ROW].
 template <typename T, int LOGN, bool BATCH, bool TC>
 __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd_m(SolveArgs<T> a0, BatchView<T> bv)
@@ -1381,66 +1386,75 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd_m(SolveAr
     T *srow = reinterpret_cast<T *>(smem_raw + tw_bytes<C>(a.tw_entries));
     C *sbuf = reinterpret_cast<C *>(srow + 2 * N);
     __shared__ int rim_bad;
-    const int r0 = 2 * blockIdx.x;
-    const T *src = a.src[0] + (size_t)r0 * N;
-    cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
-    cp_block(srow, src, 2 * (size_t)N * sizeof(T));
-    cp_commit();
     const int t = threadIdx.x;
     if (t == 0)
         rim_bad = 0;
+    cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
+    cp_block(srow, a.src[0] + (size_t)(2 * blockIdx.x) * N, 2 * (size_t)N * sizeof(T));
+    cp_commit();
     const bool active = t < 2 * Q;
     const int b = active ? t / Q : 0, j = active ? t - b * Q : 0;
     const TwLayout tl = tw_layout(F16<LOGN>::twlen, N);
-    cp_wait<0>();
-    __syncthreads();
-    {
-        bool bad = false;
-        if (r0 == 0 || r0 == N - 2) {
-            for (int i = t; i < 2 * N; i += K::ROW_THREADS)
-                bad |= srow[i] != T(0);
-        } else if (t < 8) {
-            const int col = (t & 3) < 2 ? (t & 3) : N - 4 + (t & 3);  // 0, 1, N-2, N-1
-            bad = srow[(t >> 2) * N + col] != T(0);
+    constexpr bool WALK = TC && !BATCH;  // the other instances take one row pair per CTA
+    for (int rp = blockIdx.x; rp < N / 2; rp += WALK ? (int)gridDim.x : N / 2) {
+        const int r0 = 2 * rp;
+        cp_wait<0>();
+        __syncthreads();  // rows r0, r0 + 1 staged; the previous pair's bins have been read
+        {
+            bool bad = false;
+            if (r0 == 0 || r0 == N - 2) {
+                for (int i = t; i < 2 * N; i += K::ROW_THREADS)
+                    bad |= srow[i] != T(0);
+            } else if (t < 8) {
+                const int col = (t & 3) < 2 ? (t & 3) : N - 4 + (t & 3);  // 0, 1, N-2, N-1
+                bad = srow[(t >> 2) * N + col] != T(0);
+            }
+            if (bad)
+                rim_bad = 1;
         }
-        if (bad)
-            rim_bad = 1;
-    }
-    C v[1][16];
-    if (active) {
+        C v[1][16];
+        if (active) {
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const int c = j + u * Q;
-            C z = hmk<C>(srow[c], srow[N + c]);
-            if (b)
-                z = hmul(z, twist(tw, tl, j, u));
-            v[0][u] = z;
+            for (int u = 0; u < 16; ++u) {
+                const int c = j + u * Q;
+                C z = hmk<C>(srow[c], srow[N + c]);
+                if (b)
+                    z = hmul(z, twist(tw, tl, j, u));
+                v[0][u] = z;
+            }
+        }
+        if (WALK && rp + (int)gridDim.x < N / 2) {  // uniform over the block
+            __syncthreads();  // every thread has read the rows
+            cp_block(srow, a.src[0] + (size_t)(2 * (rp + gridDim.x)) * N, 2 * (size_t)N * sizeof(T));
+            cp_commit();
+        }
+        constexpr int HB = TC ? 0 : K::HB_ROW;
+        fft_ct<C, false, LOGN, 1, TC, HB>(v, sbuf + b * SP, SP, j, active, tw, &tcx, b);
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+                sbuf[b * SP + pad16(j + u * Q)] = v[0][u];
+        }
+        __syncthreads();
+        C2 *out = reinterpret_cast<C2 *>(a.fwd);
+        for (int kx = t; kx <= N; kx += K::ROW_THREADS) {
+            const int bb = kx & 1, k = kx >> 1;
+            const int km = (N - bb - k) & (N - 1);
+            const C Z = sbuf[bb * SP + pad16(k)];
+            const C Zm = sbuf[bb * SP + pad16(km)];
+            C2 o;
+            o.x = T(0.5) * (Z.x + Zm.x);
+            o.y = T(0.5) * (Z.y - Zm.y);
+            o.z = T(0.5) * (Z.y + Zm.y);
+            o.w = T(-0.5) * (Z.x - Zm.x);
+            out[((size_t)kx * N + r0) >> 1] = o;
         }
     }
-    constexpr int HB = TC ? 0 : K::HB_ROW;
-    fft_ct<C, false, LOGN, 1, TC, HB>(v, sbuf + b * SP, SP, j, active, tw, &tcx, b);
+    cp_wait<0>();
     __syncthreads();
     if (t == 0 && rim_bad)
         atomicOr(a.status, STATUS_RIM_NONZERO);
-    if (active) {
-#pragma unroll
-        for (int u = 0; u < 16; ++u)
-            sbuf[b * SP + pad16(j + u * Q)] = v[0][u];
-    }
-    __syncthreads();
-    C2 *out = reinterpret_cast<C2 *>(a.fwd);
-    for (int kx = t; kx <= N; kx += K::ROW_THREADS) {
-        const int bb = kx & 1, k = kx >> 1;
-        const int km = (N - bb - k) & (N - 1);
-        const C Z = sbuf[bb * SP + pad16(k)];
-        const C Zm = sbuf[bb * SP + pad16(km)];
-        C2 o;
-        o.x = T(0.5) * (Z.x + Zm.x);
-        o.y = T(0.5) * (Z.y - Zm.y);
-        o.z = T(0.5) * (Z.y + Zm.y);
-        o.w = T(-0.5) * (Z.x - Zm.x);
-        out[((size_t)kx * N + r0) >> 1] = o;
-    }
     if constexpr (TC)
         tc_end(tcx, TCT);
 }
@@ -1931,6 +1945,7 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
     using S = KSmem<T, LOGN, TC>;
     static std::atomic<unsigned long long> d[28];
     static std::atomic<int> res_mw[64], res_mw1[64];  // resident CTAs of the walking column pass (NC = 2, 1)
+    static std::atomic<int> res_fm[64];               // and of the walking zero-rim forward row pass
     const BatchView<T> none{nullptr, nullptr};
     const bool batch = bv != nullptr;
     const BatchView<T> v = batch ? *bv : none;
@@ -1977,6 +1992,10 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
              (e = resident_ctas(k_col_mw<T, LOGN, false, TC, 1>, K::ROW_THREADS, S::col_mw(), res_mw1, &grid)) !=
                  cudaSuccess))
             return e;
+        if (S::row_fwd_m() <= kMaxDynSmem &&
+            (e = resident_ctas(k_row_fwd_m<T, LOGN, false, TC>, K::ROW_THREADS, S::row_fwd_m(), res_fm, &grid)) !=
+                cudaSuccess)
+            return e;
         return cudaSuccess;
     }
     switch (pass) {
@@ -2006,8 +2025,15 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
         break;
     }
     case PASS_ROW_FWD_M: {
+        // tensor-core tiles: the CTAs that fit at once walk the N / 2 row pairs (one tensor-memory
+        // allocation per CTA); otherwise, and in batches, one CTA per (pair, item), which measured faster
+        int grid = K::N / 2;
+        if (TC && !batch && ((e = ensure_smem(k_row_fwd_m<T, LOGN, false, TC>, S::row_fwd_m(), d[6])) != cudaSuccess ||
+                       (e = resident_ctas(k_row_fwd_m<T, LOGN, false, TC>, K::ROW_THREADS, S::row_fwd_m(), res_fm,
+                                          &grid)) != cudaSuccess))
+            return e;
         SGF_LAUNCH((k_row_fwd_m<T, LOGN, false, TC>), (k_row_fwd_m<T, LOGN, true, TC>), 6, S::row_fwd_m(),
-                   dim3(K::N / 2, batch ? count : 1), K::ROW_THREADS)
+                   dim3(grid < K::N / 2 ? grid : K::N / 2, batch ? count : 1), K::ROW_THREADS)
         break;
     }
     case PASS_COL_M: {

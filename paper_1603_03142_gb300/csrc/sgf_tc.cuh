@@ -98,6 +98,19 @@ __device__ __forceinline__ void tc_split2(float x0, float x1, uint32_t &hi, uint
     lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
+// cos(pi m / 8) for any integer m >= 0, from the exact values 1, cos(pi/8),
+// sqrt(1/2), sin(pi/8) and 0 (FP32 arithmetic only: every CTA builds its DFT
+// tiles, and double precision runs at a small fraction of the FP32 rate).
+__device__ __forceinline__ float tc_cospi8(int m)
+{
+    const float c1 = 0.92387953251128674f, h = 0.70710678118654752f, s1 = 0.38268343236508978f;
+    m &= 15;
+    const int a = m <= 8 ? m : 16 - m;  // cos(pi (16 - m)/8) = cos(pi m/8)
+    const int q = a <= 4 ? a : 8 - a;   // cos(pi (8 - q)/8) = -cos(pi q/8)
+    const float v = q == 0 ? 1.0f : q == 1 ? c1 : q == 2 ? h : q == 3 ? s1 : 0.0f;
+    return a <= 4 ? v : -v;
+}
+
 // Set up the tensor-core area (every thread calls; contains barriers): `tiles`
 // tiles in all (warp 0 allocates 32 TMEM columns each; tiles is 1, 2, 4 or 8),
 // `rt` A-tile buffers at `area`.
@@ -120,14 +133,13 @@ __device__ __forceinline__ void tc_begin(TcCtx &c, unsigned char *area, int tile
         const int k = n & 15;
         const int m = (u * k) & 15;
         // W16^m = cos(2 pi m/16) -+ i sin(2 pi m/16) (forward: minus)
-        double cs, sn;
-        sincospi((double)m / 8.0, &sn, &cs);
-        const double wr = cs, wi = dir ? sn : -sn;
-        const double vre = n < 16 ? wr : wi;    // coefficient of a_u
-        const double vim = n < 16 ? -wi : wr;   // coefficient of b_u
-        const __nv_bfloat16 hre = __double2bfloat16(vre), him = __double2bfloat16(vim);
-        const __nv_bfloat16 lre = __double2bfloat16(vre - (double)__bfloat162float(hre));
-        const __nv_bfloat16 lim = __double2bfloat16(vim - (double)__bfloat162float(him));
+        const float cs = tc_cospi8(m), sn = tc_cospi8(m + 12);  // sin(pi m/8) = cos(pi (m - 4)/8)
+        const float wr = cs, wi = dir ? sn : -sn;
+        const float vre = n < 16 ? wr : wi;    // coefficient of a_u
+        const float vim = n < 16 ? -wi : wr;   // coefficient of b_u
+        const __nv_bfloat16 hre = __float2bfloat16_rn(vre), him = __float2bfloat16_rn(vim);
+        const __nv_bfloat16 lre = __float2bfloat16_rn(vre - __bfloat162float(hre));
+        const __nv_bfloat16 lim = __float2bfloat16_rn(vim - __bfloat162float(him));
         const uint32_t off = tc_a_off(n, u);
         unsigned char *base = bb + dir * 4096;
         *reinterpret_cast<__nv_bfloat16 *>(base + 0 * 1024 + off) = hre;
