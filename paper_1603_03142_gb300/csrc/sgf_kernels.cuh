@@ -1156,8 +1156,6 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, sizeof(T) == 4 && !
     constexpr int HALF = N / 2 + 1;
     C *sbuf = stg;
     const int tl = BATCH ? wm.y : a.level_base + wm.y;
-    const int comp0 = NC == 1 && (int)blockIdx.x >= N / 2 ? 1 : 0;
-    const int j0 = 2 * ((int)blockIdx.x - comp0 * (N / 2)), j1 = j0 + 1;
     const int t = threadIdx.x;
     const bool active = t < 2 * Q;
     const int b = active ? t / Q : 0, j = active ? t - b * Q : 0;
@@ -1165,70 +1163,81 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, sizeof(T) == 4 && !
     const RowContrib rc = a.contribs[a.contrib_begin[tl]];
     const ColOutput o = a.outs[rc.out_base];
     cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        const C *base = a.bwd + o.off + bwd_index(N, o.rows, comp0 + c, 0, j0);
-        constexpr int PG = 2 * (int)sizeof(C) / 16;  // 16-byte pieces per bin (rows j0, j1 adjacent)
-        for (int q = t; q < (N + 1) * PG; q += K::ROW_THREADS) {
-            const int kx = q / PG, piece = q - kx * PG;
-            C *dst = stg + 2 * ((c * 2 + (kx & 1)) * HALF + (kx >> 1));
-            cp16(dst + piece * (16 / (int)sizeof(C)), base + (size_t)kx * o.rows + piece * (16 / (int)sizeof(C)));
-        }
-    }
-    cp_commit();
-    cp_wait<0>();
-    __syncthreads();
-    C v[NC][16];
-    if (active) {
-#pragma unroll
-        for (int c = 0; c < NC; ++c)
-#pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const int kx = 2 * (j + u * Q) + b;
-                const int k2 = kx <= N ? kx : P - kx;  // same parity as kx
-                const C *pr = stg + 2 * ((c * 2 + b) * HALF + (k2 >> 1));
-                C A, B;
-                if constexpr (sizeof(T) == 4) {  // one 16-byte load (pairs start on 16-byte boundaries)
-                    const float4 ab = *reinterpret_cast<const float4 *>(pr);
-                    A = hmk<C>(ab.x, ab.y);
-                    B = hmk<C>(ab.z, ab.w);
-                } else {
-                    A = pr[0];
-                    B = pr[1];
-                }
-                v[c][u] = kx <= N ? hmk<C>(A.x - B.y, A.y + B.x) : hmk<C>(A.x + B.y, B.x - A.y);
-            }
-    }
-    // the transform's first exchange write follows a barrier, after every read of the stage;
-    // half b's NC sequences at sbuf + (b NC + c) SP
-    constexpr int HB = TC ? 0 : K::HB_ROW;
-    if constexpr (HB > 0)
-        __syncthreads();  // half 0's exchange buffer overlaps half 1's part of the stage
-    fft_ct<C, true, LOGN, NC, TC, HB>(v, sbuf + b * NC * SP, SP, j, active, tw, &tcx, b);
-    __syncthreads();
-    if (active && b == 1) {
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const int n = j + u * Q;
-            const C w = twist(tw, twl, j, u);
-#pragma unroll
-            for (int c = 0; c < NC; ++c)
-                sbuf[c * SP + pad16(n)] = hmulc(v[c][u], w);
-        }
-    }
-    __syncthreads();
-    if (active && b == 0) {
+    // tensor-core instances walk the grid's x items (tiles and tensor memory set up once per CTA)
+    constexpr bool WALK = TC && !BATCH;
+    const int items = WALK ? (NC == 1 ? a.ncomp : 1) * (N / 2) : (int)gridDim.x;
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+        if (WALK && it != (int)blockIdx.x)
+            __syncthreads();  // the previous item's stores have read the exchange buffers
+        const int comp0 = NC == 1 && it >= N / 2 ? 1 : 0;
+        const int j0 = 2 * (it - comp0 * (N / 2)), j1 = j0 + 1;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-            T *out = comp0 + c ? a.fy[tl] : a.fx[tl];
+            const C *base = a.bwd + o.off + bwd_index(N, o.rows, comp0 + c, 0, j0);
+            constexpr int PG = 2 * (int)sizeof(C) / 16;  // 16-byte pieces per bin (rows j0, j1 adjacent)
+            for (int q = t; q < (N + 1) * PG; q += K::ROW_THREADS) {
+                const int kx = q / PG, piece = q - kx * PG;
+                C *dst = stg + 2 * ((c * 2 + (kx & 1)) * HALF + (kx >> 1));
+                cp16(dst + piece * (16 / (int)sizeof(C)), base + (size_t)kx * o.rows + piece * (16 / (int)sizeof(C)));
+            }
+        }
+        cp_commit();
+        cp_wait<0>();
+        __syncthreads();
+        C v[NC][16];
+        if (active) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int kx = 2 * (j + u * Q) + b;
+                    const int k2 = kx <= N ? kx : P - kx;  // same parity as kx
+                    const C *pr = stg + 2 * ((c * 2 + b) * HALF + (k2 >> 1));
+                    C A, B;
+                    if constexpr (sizeof(T) == 4) {  // one 16-byte load (pairs start on 16-byte boundaries)
+                        const float4 ab = *reinterpret_cast<const float4 *>(pr);
+                        A = hmk<C>(ab.x, ab.y);
+                        B = hmk<C>(ab.z, ab.w);
+                    } else {
+                        A = pr[0];
+                        B = pr[1];
+                    }
+                    v[c][u] = kx <= N ? hmk<C>(A.x - B.y, A.y + B.x) : hmk<C>(A.x + B.y, B.x - A.y);
+                }
+        }
+        // the transform's first exchange write follows a barrier, after every read of the stage;
+        // half b's NC sequences at sbuf + (b NC + c) SP
+        constexpr int HB = TC ? 0 : K::HB_ROW;
+        if constexpr (HB > 0)
+            __syncthreads();  // half 0's exchange buffer overlaps half 1's part of the stage
+        fft_ct<C, true, LOGN, NC, TC, HB>(v, sbuf + b * NC * SP, SP, j, active, tw, &tcx, b);
+        __syncthreads();
+        if (active && b == 1) {
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
                 const int n = j + u * Q;
-                const C y = hadd(v[c][u], sbuf[c * SP + pad16(n)]);
-                out[(size_t)j0 * N + n] = covered(a, tl, j0, n) ? T(0) : y.x;
-                out[(size_t)j1 * N + n] = covered(a, tl, j1, n) ? T(0) : y.y;
+                const C w = twist(tw, twl, j, u);
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+                    sbuf[c * SP + pad16(n)] = hmulc(v[c][u], w);
             }
         }
+        __syncthreads();
+        if (active && b == 0) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                T *out = comp0 + c ? a.fy[tl] : a.fx[tl];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int n = j + u * Q;
+                    const C y = hadd(v[c][u], sbuf[c * SP + pad16(n)]);
+                    out[(size_t)j0 * N + n] = covered(a, tl, j0, n) ? T(0) : y.x;
+                    out[(size_t)j1 * N + n] = covered(a, tl, j1, n) ? T(0) : y.y;
+                }
+            }
+        }
+        if (!WALK)
+            break;
     }
     if constexpr (TC)
         tc_end(tcx, TCT);
@@ -1938,6 +1947,14 @@ inline cudaError_t resident_ctas(F *kernel, int threads, size_t smem, std::atomi
     return cudaSuccess;
 }
 
+// Grid x of a walking kernel over `items` work items per patch, `count`
+// patches side by side in y: the resident CTAs shared among the patches.
+inline int min_grid(int items, int resident, int count)
+{
+    const int per = resident / (count > 0 ? count : 1);
+    return per < 1 ? 1 : (per < items ? per : items);
+}
+
 template <typename T, int LOGN, bool TC>
 cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t st, const BatchView<T> *bv)
 {
@@ -1946,6 +1963,7 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
     static std::atomic<unsigned long long> d[28];
     static std::atomic<int> res_mw[64], res_mw1[64];  // resident CTAs of the walking column pass (NC = 2, 1)
     static std::atomic<int> res_fm[64];               // and of the walking zero-rim forward row pass
+    static std::atomic<int> res_ri1[64], res_ri2[64]; // and of the walking inverse row passes (tensor cores)
     const BatchView<T> none{nullptr, nullptr};
     const bool batch = bv != nullptr;
     const BatchView<T> v = batch ? *bv : none;
@@ -2015,13 +2033,32 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
         break;
     }
     case PASS_ROW_INV1: {
+        // tensor-core tiles: the CTAs that fit at once (over the count patches) walk the row pairs
+        int gx = batch ? K::N : a.ncomp * (K::N / 2);
+        if (TC && !batch) {
+            int res = 0;
+            if ((e = ensure_smem(k_row_inv1<T, LOGN, false, TC, 1>, S::row_inv1(1), d[10])) != cudaSuccess ||
+                (e = resident_ctas(k_row_inv1<T, LOGN, false, TC, 1>, K::ROW_THREADS, S::row_inv1(1), res_ri1,
+                                   &res)) != cudaSuccess)
+                return e;
+            gx = min_grid(gx, res, count);
+        }
         SGF_LAUNCH((k_row_inv1<T, LOGN, false, TC, 1>), (k_row_inv1<T, LOGN, true, TC, 1>), 10, S::row_inv1(1),
-                   dim3(batch ? K::N : a.ncomp * (K::N / 2), count), K::ROW_THREADS)
+                   dim3(gx, count), K::ROW_THREADS)
         break;
     }
     case PASS_ROW_INV2: {
+        int gx = K::N / 2;
+        if (TC && !batch) {
+            int res = 0;
+            if ((e = ensure_smem(k_row_inv1<T, LOGN, false, TC, 2>, S::row_inv1(2), d[18])) != cudaSuccess ||
+                (e = resident_ctas(k_row_inv1<T, LOGN, false, TC, 2>, K::ROW_THREADS, S::row_inv1(2), res_ri2,
+                                   &res)) != cudaSuccess)
+                return e;
+            gx = min_grid(gx, res, count);
+        }
         SGF_LAUNCH((k_row_inv1<T, LOGN, false, TC, 2>), (k_row_inv1<T, LOGN, true, TC, 2>), 18, S::row_inv1(2),
-                   dim3(K::N / 2, count), K::ROW_THREADS)
+                   dim3(gx, count), K::ROW_THREADS)
         break;
     }
     case PASS_ROW_FWD_M: {
