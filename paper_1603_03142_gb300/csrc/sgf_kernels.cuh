@@ -1474,8 +1474,9 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd_m(SolveAr
 // distributed shared memory.  The column and the spectrum half rows are read
 // straight into registers (coalesced), Fy^ waits in shared memory while Fx^ is
 // transformed, so a thread holds one sequence at a time and three CTAs fit on
-// an SM.  Shared memory: twiddle area | sbuf[SPC] (exchanges, then the fold) |
-// park[N] (Fy^ in slot order).
+// an SM.  The tensor-core instance is launched with the clusters that fit at
+// once, each walking the columns.  Shared memory: twiddle area | sbuf[SPC]
+// (exchanges, then the fold) | park[N] (Fy^ in slot order).
 template <typename T, int LOGN, bool BATCH, bool TC>
 __global__ void __cluster_dims__(2, 1, 1)
     __launch_bounds__(KShape<LOGN>::COL_THREADS, sizeof(T) == 4 && !TC ? 3 : 1) k_col_m(SolveArgs<T> a0, BatchView<T> bv)
@@ -1499,65 +1500,68 @@ __global__ void __cluster_dims__(2, 1, 1)
     C *park = sbuf + SPC;
     cg::cluster_group cluster = cg::this_cluster();
     const int b = (int)cluster.block_rank();
-    const int kx = blockIdx.x >> 1;
     const int t = threadIdx.x;
     const bool active = t < Q;
     const int j = active ? t : 0;
     const TwLayout tl = tw_layout(F16<LOGN>::twlen, N);
-    const T *gxr = reinterpret_cast<const T *>(a.spec) + (size_t)kx * QS + b * HQ;
-    const T *gyr = reinterpret_cast<const T *>(a.spec) + ((size_t)(N + 1) + kx) * QS + b * HQ;
     cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
     cp_commit();
-    C v[1][16];
-    if (active) {
-        const C *col = a.fwd + (size_t)kx * N;
-#pragma unroll
-        for (int u = 0; u < 16; ++u)
-            v[0][u] = col[j + u * Q];
-    }
-    cp_wait<0>();
-    __syncthreads();
-    if (active && b) {
-#pragma unroll
-        for (int u = 0; u < 16; ++u)
-            v[0][u] = hmul(v[0][u], twist(tw, tl, j, u));
-    }
-    fft_ct<C, false, LOGN, 1, TC>(v, sbuf, SPC, j, active, tw, &tcx);
-    if (active) {
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const int kp = j + u * Q;
-            const bool hi = 2 * kp + b > N;
-            const int q = hi ? N - kp - b : kp;
-            const T gx = __ldg(gxr + q);                               // Gx even in ky
-            const T gy = hi ? -__ldg(gyr + q) : __ldg(gyr + q);        // Gy odd in ky
-            park[u * Q + j] = hmk<C>(-gy * v[0][u].y, gy * v[0][u].x);  // i gy v
-            v[0][u] = hmk<C>(-gx * v[0][u].y, gx * v[0][u].x);          // i gx v
-        }
-    }
-    C *const out = a.bwd;
-#pragma unroll 1
-    for (int comp = 0; comp < 2; ++comp) {
-        if (comp == 1 && active) {
+    // tensor-core instances: the resident clusters walk the columns (tiles and tensor memory set up once)
+    constexpr bool WALK = TC && !BATCH;
+    for (int kx = blockIdx.x >> 1; kx <= N; kx += WALK ? (int)(gridDim.x >> 1) : N + 1) {
+        const T *gxr = reinterpret_cast<const T *>(a.spec) + (size_t)kx * QS + b * HQ;
+        const T *gyr = reinterpret_cast<const T *>(a.spec) + ((size_t)(N + 1) + kx) * QS + b * HQ;
+        C v[1][16];
+        if (active) {
+            const C *col = a.fwd + (size_t)kx * N;
 #pragma unroll
             for (int u = 0; u < 16; ++u)
-                v[0][u] = park[u * Q + j];
+                v[0][u] = col[j + u * Q];
         }
-        // y[n] = even[n] + W_P^{-n} odd[n]
-        fft_ct<C, true, LOGN, 1, TC>(v, sbuf, SPC, j, active, tw, &tcx);
-        cluster.sync();  // both CTAs are done with their exchange buffers
-        if (b == 1 && active) {
-            C *dst = cluster.map_shared_rank(sbuf, 0);
+        cp_wait<0>();
+        __syncthreads();
+        if (active && b) {
 #pragma unroll
             for (int u = 0; u < 16; ++u)
-                dst[j + u * Q] = hmulc(v[0][u], twist(tw, tl, j, u));
+                v[0][u] = hmul(v[0][u], twist(tw, tl, j, u));
         }
-        cluster.sync();
-        if (b == 0 && active) {
+        fft_ct<C, false, LOGN, 1, TC>(v, sbuf, SPC, j, active, tw, &tcx);
+        if (active) {
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
-                const int n = j + u * Q;
-                out[bwd_index(N, N, comp, kx, n)] = hadd(v[0][u], sbuf[n]);
+                const int kp = j + u * Q;
+                const bool hi = 2 * kp + b > N;
+                const int q = hi ? N - kp - b : kp;
+                const T gx = __ldg(gxr + q);                               // Gx even in ky
+                const T gy = hi ? -__ldg(gyr + q) : __ldg(gyr + q);        // Gy odd in ky
+                park[u * Q + j] = hmk<C>(-gy * v[0][u].y, gy * v[0][u].x);  // i gy v
+                v[0][u] = hmk<C>(-gx * v[0][u].y, gx * v[0][u].x);          // i gx v
+            }
+        }
+        C *const out = a.bwd;
+#pragma unroll 1
+        for (int comp = 0; comp < 2; ++comp) {
+            if (comp == 1 && active) {
+#pragma unroll
+                for (int u = 0; u < 16; ++u)
+                    v[0][u] = park[u * Q + j];
+            }
+            // y[n] = even[n] + W_P^{-n} odd[n]
+            fft_ct<C, true, LOGN, 1, TC>(v, sbuf, SPC, j, active, tw, &tcx);
+            cluster.sync();  // both CTAs are done with their exchange buffers
+            if (b == 1 && active) {
+                C *dst = cluster.map_shared_rank(sbuf, 0);
+#pragma unroll
+                for (int u = 0; u < 16; ++u)
+                    dst[j + u * Q] = hmulc(v[0][u], twist(tw, tl, j, u));
+            }
+            cluster.sync();
+            if (b == 0 && active) {
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int n = j + u * Q;
+                    out[bwd_index(N, N, comp, kx, n)] = hadd(v[0][u], sbuf[n]);
+                }
             }
         }
     }
@@ -1568,9 +1572,10 @@ __global__ void __cluster_dims__(2, 1, 1)
 // The same column pass with both inverse transforms in flight at once (B = 2
 // sequences per thread share the barriers): fewer barriers, twice the
 // registers, two CTAs per SM.  The column and the spectrum half rows are
-// staged with asynchronous copies.  Shared memory: twiddle area | sbuf[SPC] |
-// column[N] | Gx, Gy half rows; the second sequence and the 2N fold reuse
-// sbuf + column.
+// staged with asynchronous copies.  The tensor-core instance is launched with
+// the clusters that fit at once, each walking the columns.  Shared memory:
+// twiddle area | sbuf[SPC] | column[N] | Gx, Gy half rows; the second
+// sequence and the 2N fold reuse sbuf + column.
 template <typename T, int LOGN, bool BATCH, bool TC>
 __global__ void __cluster_dims__(2, 1, 1)
     __launch_bounds__(KShape<LOGN>::COL_THREADS, sizeof(T) == 4 && !TC ? 2 : 1) k_col_md(SolveArgs<T> a0, BatchView<T> bv)
@@ -1595,66 +1600,71 @@ __global__ void __cluster_dims__(2, 1, 1)
     T *gsp = reinterpret_cast<T *>(col + N);
     cg::cluster_group cluster = cg::this_cluster();
     const int b = (int)cluster.block_rank();
-    const int kx = blockIdx.x >> 1;
     const int t = threadIdx.x;
     const bool active = t < Q;
     const int j = active ? t : 0;
     const TwLayout tl = tw_layout(F16<LOGN>::twlen, N);
     const T *spec = reinterpret_cast<const T *>(a.spec);
     cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
-    cp_block(col, a.fwd + (size_t)kx * N, (size_t)N * sizeof(C));
-    cp_block(gsp, spec + (size_t)kx * QS + b * HQ, (size_t)HQ * sizeof(T));
-    cp_block(gsp + HQ, spec + ((size_t)(N + 1) + kx) * QS + b * HQ, (size_t)HQ * sizeof(T));
-    cp_commit();
-    cp_wait<0>();
-    __syncthreads();
-    C acc[2][16];
-    {
-        C v[1][16];
-        if (active) {
+    // tensor-core instances: the resident clusters walk the columns (tiles and tensor memory set up once)
+    constexpr bool WALK = TC && !BATCH;
+    for (int kx = blockIdx.x >> 1; kx <= N; kx += WALK ? (int)(gridDim.x >> 1) : N + 1) {
+        if (WALK && kx != (int)(blockIdx.x >> 1))
+            __syncthreads();  // the previous column's fold (over sbuf and the column) has been read
+        cp_block(col, a.fwd + (size_t)kx * N, (size_t)N * sizeof(C));
+        cp_block(gsp, spec + (size_t)kx * QS + b * HQ, (size_t)HQ * sizeof(T));
+        cp_block(gsp + HQ, spec + ((size_t)(N + 1) + kx) * QS + b * HQ, (size_t)HQ * sizeof(T));
+        cp_commit();
+        cp_wait<0>();
+        __syncthreads();
+        C acc[2][16];
+        {
+            C v[1][16];
+            if (active) {
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                C x = col[j + u * Q];
-                if (b)
-                    x = hmul(x, twist(tw, tl, j, u));
-                v[0][u] = x;
+                for (int u = 0; u < 16; ++u) {
+                    C x = col[j + u * Q];
+                    if (b)
+                        x = hmul(x, twist(tw, tl, j, u));
+                    v[0][u] = x;
+                }
+            }
+            fft_ct<C, false, LOGN, 1, TC>(v, sbuf, SPC, j, active, tw, &tcx);
+            if (active) {
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int kp = j + u * Q;
+                    const bool hi = 2 * kp + b > N;
+                    const int q = hi ? N - kp - b : kp;
+                    const T gx = gsp[q];                           // Gx even in ky
+                    const T gy = hi ? -gsp[HQ + q] : gsp[HQ + q];  // Gy odd in ky
+                    acc[0][u] = hmk<C>(-gx * v[0][u].y, gx * v[0][u].x);  // i gx v
+                    acc[1][u] = hmk<C>(-gy * v[0][u].y, gy * v[0][u].x);
+                }
             }
         }
-        fft_ct<C, false, LOGN, 1, TC>(v, sbuf, SPC, j, active, tw, &tcx);
-        if (active) {
+        fft_ct<C, true, LOGN, 2, TC>(acc, sbuf, SPC, j, active, tw, &tcx);  // second sequence over the column
+        C *fold = sbuf;
+        cluster.sync();
+        if (b == 1 && active) {
+            C *dst = cluster.map_shared_rank(fold, 0);
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
-                const int kp = j + u * Q;
-                const bool hi = 2 * kp + b > N;
-                const int q = hi ? N - kp - b : kp;
-                const T gx = gsp[q];                           // Gx even in ky
-                const T gy = hi ? -gsp[HQ + q] : gsp[HQ + q];  // Gy odd in ky
-                acc[0][u] = hmk<C>(-gx * v[0][u].y, gx * v[0][u].x);  // i gx v
-                acc[1][u] = hmk<C>(-gy * v[0][u].y, gy * v[0][u].x);
+                const int n = j + u * Q;
+                const C w = twist(tw, tl, j, u);
+                dst[n] = hmulc(acc[0][u], w);
+                dst[N + n] = hmulc(acc[1][u], w);
             }
         }
-    }
-    fft_ct<C, true, LOGN, 2, TC>(acc, sbuf, SPC, j, active, tw, &tcx);  // second sequence over the column
-    C *fold = sbuf;
-    cluster.sync();
-    if (b == 1 && active) {
-        C *dst = cluster.map_shared_rank(fold, 0);
+        cluster.sync();
+        if (b == 0 && active) {
+            C *dst = a.bwd;
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const int n = j + u * Q;
-            const C w = twist(tw, tl, j, u);
-            dst[n] = hmulc(acc[0][u], w);
-            dst[N + n] = hmulc(acc[1][u], w);
-        }
-    }
-    cluster.sync();
-    if (b == 0 && active) {
-        C *dst = a.bwd;
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const int n = j + u * Q;
-            dst[bwd_index(N, N, 0, kx, n)] = hadd(acc[0][u], fold[n]);
-            dst[bwd_index(N, N, 1, kx, n)] = hadd(acc[1][u], fold[N + n]);
+            for (int u = 0; u < 16; ++u) {
+                const int n = j + u * Q;
+                dst[bwd_index(N, N, 0, kx, n)] = hadd(acc[0][u], fold[n]);
+                dst[bwd_index(N, N, 1, kx, n)] = hadd(acc[1][u], fold[N + n]);
+            }
         }
     }
     if constexpr (TC)
@@ -1964,6 +1974,7 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
     static std::atomic<int> res_mw[64], res_mw1[64];  // resident CTAs of the walking column pass (NC = 2, 1)
     static std::atomic<int> res_fm[64];               // and of the walking zero-rim forward row pass
     static std::atomic<int> res_ri1[64], res_ri2[64]; // and of the walking inverse row passes (tensor cores)
+    static std::atomic<int> res_cm[64], res_cmd[64];  // and of the walking cluster column passes (tensor cores)
     const BatchView<T> none{nullptr, nullptr};
     const bool batch = bv != nullptr;
     const BatchView<T> v = batch ? *bv : none;
@@ -2074,8 +2085,18 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
         break;
     }
     case PASS_COL_M: {
+        // tensor-core tiles: the 2-CTA clusters that fit at once walk the N + 1 columns
+        int gx = 2 * (K::N + 1);
+        if (TC && !batch) {
+            int res = 0;
+            if ((e = ensure_smem(k_col_m<T, LOGN, false, TC>, S::col_m(), d[8])) != cudaSuccess ||
+                (e = resident_ctas(k_col_m<T, LOGN, false, TC>, K::COL_THREADS, S::col_m(), res_cm, &res)) !=
+                    cudaSuccess)
+                return e;
+            gx = 2 * min_grid(K::N + 1, res / 2, 1);
+        }
         SGF_LAUNCH((k_col_m<T, LOGN, false, TC>), (k_col_m<T, LOGN, true, TC>), 8, S::col_m(),
-                   dim3(2 * (K::N + 1), batch ? count : 1), K::COL_THREADS)
+                   dim3(gx, batch ? count : 1), K::COL_THREADS)
         break;
     }
     case PASS_COL_SUM: {
@@ -2146,8 +2167,17 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
         break;
     }
     case PASS_COL_MD: {
+        int gx = 2 * (K::N + 1);  // as PASS_COL_M
+        if (TC && !batch) {
+            int res = 0;
+            if ((e = ensure_smem(k_col_md<T, LOGN, false, TC>, S::col_md(), d[12])) != cudaSuccess ||
+                (e = resident_ctas(k_col_md<T, LOGN, false, TC>, K::COL_THREADS, S::col_md(), res_cmd, &res)) !=
+                    cudaSuccess)
+                return e;
+            gx = 2 * min_grid(K::N + 1, res / 2, 1);
+        }
         SGF_LAUNCH((k_col_md<T, LOGN, false, TC>), (k_col_md<T, LOGN, true, TC>), 12, S::col_md(),
-                   dim3(2 * (K::N + 1), batch ? count : 1), K::COL_THREADS)
+                   dim3(gx, batch ? count : 1), K::COL_THREADS)
         break;
     }
     default:
