@@ -1720,6 +1720,22 @@ void plan_init(sgf_plan *p, const Forest &fo, sgf_precision precision, uint32_t 
     p->sched = sgf_schedule{p->merged && p->pot ? 2 : 0, 0, 0};  // the zero-rim potential runs col_pass 2
 }
 
+// Every kernel instance of the plan's transform size and precision path gets
+// its shared-memory limit and its resident-CTA count here, at plan time, so a
+// solve captured into a CUDA graph makes no attribute or occupancy call.
+template <typename T>
+sgf_status prepare_kernels_t(const sgf_plan *p)
+{
+    SolveArgs<T> dummy{};
+    const cudaError_t e = launch_pass_n<T>(PASS_PREPARE, p->logN, dummy, 0, nullptr, nullptr, p->tc);
+    return e == cudaSuccess ? SGF_OK : cuda_fail(e, "kernel attributes");
+}
+
+sgf_status prepare_kernels(const sgf_plan *p)
+{
+    return p->prec == SGF_FP64 ? prepare_kernels_t<double>(p) : prepare_kernels_t<float>(p);
+}
+
 // A validated geometry's plan: lists, recorded schedule, spectra, workspace.
 sgf_status plan_create(const Forest &fo, sgf_precision precision, uint32_t flags, sgf_plan **out)
 {
@@ -1741,6 +1757,8 @@ sgf_status plan_create(const Forest &fo, sgf_precision precision, uint32_t flags
     }
     if (s == SGF_OK)
         s = plan_alloc_owned(p);
+    if (s == SGF_OK)
+        s = prepare_kernels(p);
     if (s != SGF_OK) {
         std::string msg = g_err;
         plan_free_owned(p);
@@ -1877,6 +1895,8 @@ sgf_status sgf_plan_share_ex(const sgf_plan *src, sgf_precision precision, sgf_p
         p->spec->refs++;
         s = plan_alloc_owned(p);
     }
+    if (s == SGF_OK)
+        s = prepare_kernels(p);
     if (s != SGF_OK) {
         std::string msg = g_err;
         plan_free_owned(p);

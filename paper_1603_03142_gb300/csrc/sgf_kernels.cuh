@@ -1989,7 +1989,7 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
             return e;                                                                 \
         K0<<<grid, threads, smem, st>>>(a, v);                                        \
     }
-    if (pass == PASS_PREPARE) {  // set every shared-memory limit (before a graph capture)
+    if (pass == PASS_PREPARE) {  // every shared-memory limit and resident count, before any graph capture
         if ((e = ensure_smem(k_row_fwd<T, LOGN, false, TC>, S::row_fwd(), d[0])) != cudaSuccess ||
             (e = ensure_smem(k_row_fwd<T, LOGN, true, TC>, S::row_fwd(), d[1])) != cudaSuccess ||
             (e = ensure_smem(k_col<T, LOGN, false, TC>, S::col(), d[2])) != cudaSuccess ||
@@ -2025,6 +2025,31 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
             (e = resident_ctas(k_row_fwd_m<T, LOGN, false, TC>, K::ROW_THREADS, S::row_fwd_m(), res_fm, &grid)) !=
                 cudaSuccess)
             return e;
+        if constexpr (TC) {  // the walking tensor-core instances
+            if ((S::row_inv1(1) <= kMaxDynSmem &&
+                 (e = resident_ctas(k_row_inv1<T, LOGN, false, TC, 1>, K::ROW_THREADS, S::row_inv1(1), res_ri1,
+                                    &grid)) != cudaSuccess) ||
+                (S::row_inv1(2) <= kMaxDynSmem &&
+                 (e = resident_ctas(k_row_inv1<T, LOGN, false, TC, 2>, K::ROW_THREADS, S::row_inv1(2), res_ri2,
+                                    &grid)) != cudaSuccess) ||
+                (S::col_m() <= kMaxDynSmem &&
+                 (e = resident_ctas(k_col_m<T, LOGN, false, TC>, K::COL_THREADS, S::col_m(), res_cm, &grid)) !=
+                     cudaSuccess) ||
+                (S::col_md() <= kMaxDynSmem &&
+                 (e = resident_ctas(k_col_md<T, LOGN, false, TC>, K::COL_THREADS, S::col_md(), res_cmd, &grid)) !=
+                     cudaSuccess))
+                return e;
+        }
+        if constexpr (!TC && K::HB_ROW > 0 && sizeof(T) == 4) {  // the FP32-only kernels
+            if ((S::col_w() <= kMaxDynSmem &&
+                 ((e = ensure_smem(k_col_w<T, LOGN, false>, S::col_w(), d[23])) != cudaSuccess ||
+                  (e = ensure_smem(k_col_w<T, LOGN, true>, S::col_w(), d[24])) != cudaSuccess)) ||
+                (S::col_gw() <= kMaxDynSmem &&
+                 ((e = ensure_smem(k_col_gw<T, LOGN, false>, S::col_gw(), d[26])) != cudaSuccess ||
+                  (e = ensure_smem(k_col_gw<T, LOGN, true>, S::col_gw(), d[27])) != cudaSuccess)) ||
+                (e = ensure_smem(k_row_inv1t<T, LOGN>, S::row_inv1t(), d[22])) != cudaSuccess)
+                return e;
+        }
         return cudaSuccess;
     }
     switch (pass) {
