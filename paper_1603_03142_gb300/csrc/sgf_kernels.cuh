@@ -1132,6 +1132,8 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_inv(SolveArgs
 // buffer of the transform aliases the gather stage.
 // Grid: x = component * N/2 + row pair (NC = 1; component 0 only for the
 // potential) or row pair (NC = 2), y = work item (batch) or patch from level_base.
+// The tensor-core instances are launched with fewer CTAs in x (the resident
+// CTAs shared among the patches), each walking those items in turn.
 template <typename T, int LOGN, bool BATCH, bool TC, int NC>
 __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, sizeof(T) == 4 && !TC && NC == 1 ? 2 : 1)
     k_row_inv1(SolveArgs<T> a0, BatchView<T> bv)
