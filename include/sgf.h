@@ -204,7 +204,9 @@ sgf_status sgf_plan_stats_get(const sgf_plan *plan, sgf_plan_stats *stats);
  * sigma[l], fx[l], fy[l]: device pointers to n*n elements for l < levels,
  * element type per precision, 16-byte aligned; outputs must not alias inputs.
  * stream: a cudaStream_t (NULL = legacy default stream).  Asynchronous and
- * stream-ordered; allocates nothing.  Errors: SGF_EINVAL, SGF_ECUDA (launch). */
+ * stream-ordered; allocates nothing and makes no synchronising call, so it may
+ * be captured into a CUDA graph (the plan set every kernel attribute when it
+ * was created).  Errors: SGF_EINVAL, SGF_ECUDA (launch). */
 sgf_status sgf_solve(sgf_plan *plan, const void *const *sigma, void *const *fx, void *const *fy,
                      void *stream);
 
