@@ -265,10 +265,13 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, sizeof(T) == 4 && !
 }
 
 // --------------------------------------------------------------------- col
+// One 2-CTA cluster (the parity halves) per (column, work item); the
+// tensor-core instance takes kColWalk columns per cluster.
 // Shared memory: twiddle area | sbuf[SPC] | stage[2] { column[N] (complex),
 // this parity's half of the two spectrum rows, 2 x (N/2 + 4) reals }.  The
 // dual inverse transform uses sbuf and the stages as two sequence buffers, and
 // the fold of the odd half reuses them afterwards.
+constexpr int kColWalk = 4;
 template <typename T, int LOGN, bool BATCH, bool TC>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_THREADS) k_col(SolveArgs<T> a0, BatchView<T> bv)
 {
@@ -292,7 +295,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
     constexpr size_t stage_bytes = (size_t)N * sizeof(C) + 2 * (size_t)HQ * sizeof(T);
     cg::cluster_group cluster = cg::this_cluster();
     const int b = (int)cluster.block_rank();  // parity half
-    const int kx = blockIdx.x >> 1;
     const ColWork w = a.col_list[wm.y];
     const ColOutput o = a.outs[w.out];
     const int t = threadIdx.x;
@@ -300,163 +302,167 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
     const int j = active ? t : 0;
     const int nitems = 3 * w.in_count;
     const TwLayout tl = tw_layout(F16<LOGN>::twlen, N);
-
-    auto issue = [&](int k) {
-        unsigned char *st = stage_base + (size_t)(k & 1) * stage_bytes;
-        const ColInput ci = a.ins[w.in_begin + k / 3];
-        const FwdSlab sl = a.slabs[ci.slab];
-        const int f = k % 3;
-        cp_block(st, a.fwd + sl.off + ((size_t)f * (N + 1) + kx) * sl.rows, (size_t)sl.rows * sizeof(C));
-        if (spec_quarter(ci.kind)) {
-            const T *sp = reinterpret_cast<const T *>(a.spec) + ci.spec_off;
-            T *dst = reinterpret_cast<T *>(st + (size_t)N * sizeof(C));
-            cp_block(dst, sp + ((size_t)f * (N + 1) + kx) * QS + b * HQ, (size_t)HQ * sizeof(T));
-            if (ci.kind == SPEC_QUARTER)
-                cp_block(dst + HQ, sp + ((size_t)(3 + f) * (N + 1) + kx) * QS + b * HQ, (size_t)HQ * sizeof(T));
-        }
-    };
     cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
-    issue(0);
-    cp_commit();
-    if (nitems > 1)
-        issue(1);
-    cp_commit();
+    // tensor-core instances: a cluster takes kColWalk columns of its work item, gridDim.x / 2
+    // apart (the tiles, the tensor memory and the twiddles set up once for them)
+    constexpr bool WALK = TC && !BATCH;
+    for (int kx = blockIdx.x >> 1; kx <= N; kx += WALK ? (int)(gridDim.x >> 1) : N + 1) {
+        if (WALK && kx != (int)(blockIdx.x >> 1))
+            __syncthreads();  // the previous column's fold (over sbuf and the stages) has been read
+        auto issue = [&](int k) {
+            unsigned char *st = stage_base + (size_t)(k & 1) * stage_bytes;
+            const ColInput ci = a.ins[w.in_begin + k / 3];
+            const FwdSlab sl = a.slabs[ci.slab];
+            const int f = k % 3;
+            cp_block(st, a.fwd + sl.off + ((size_t)f * (N + 1) + kx) * sl.rows, (size_t)sl.rows * sizeof(C));
+            if (spec_quarter(ci.kind)) {
+                const T *sp = reinterpret_cast<const T *>(a.spec) + ci.spec_off;
+                T *dst = reinterpret_cast<T *>(st + (size_t)N * sizeof(C));
+                cp_block(dst, sp + ((size_t)f * (N + 1) + kx) * QS + b * HQ, (size_t)HQ * sizeof(T));
+                if (ci.kind == SPEC_QUARTER)
+                    cp_block(dst + HQ, sp + ((size_t)(3 + f) * (N + 1) + kx) * QS + b * HQ, (size_t)HQ * sizeof(T));
+            }
+        };
+        issue(0);
+        cp_commit();
+        if (nitems > 1)
+            issue(1);
+        cp_commit();
 
-    C acc[2][16];
+        C acc[2][16];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-        acc[0][u] = hmk<C>(T(0), T(0));
-        acc[1][u] = hmk<C>(T(0), T(0));
-    }
-    for (int k = 0; k < nitems; ++k) {
-        cp_wait<1>();
-        __syncthreads();
-        const unsigned char *st = stage_base + (size_t)(k & 1) * stage_bytes;
-        const C *col = reinterpret_cast<const C *>(st);
-        const T *spx = reinterpret_cast<const T *>(st + (size_t)N * sizeof(C));
-        const ColInput ci = a.ins[w.in_begin + k / 3];
-        const int rows = a.slabs[ci.slab].rows;
-        const int f = k % 3;
-        C v[1][16];
-        if (active) {
+        for (int u = 0; u < 16; ++u) {
+            acc[0][u] = hmk<C>(T(0), T(0));
+            acc[1][u] = hmk<C>(T(0), T(0));
+        }
+        for (int k = 0; k < nitems; ++k) {
+            cp_wait<1>();
+            __syncthreads();
+            const unsigned char *st = stage_base + (size_t)(k & 1) * stage_bytes;
+            const C *col = reinterpret_cast<const C *>(st);
+            const T *spx = reinterpret_cast<const T *>(st + (size_t)N * sizeof(C));
+            const ColInput ci = a.ins[w.in_begin + k / 3];
+            const int rows = a.slabs[ci.slab].rows;
+            const int f = k % 3;
+            C v[1][16];
+            if (active) {
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int n = j + u * Q;
+                    C x = hmk<C>(T(0), T(0));
+                    if (n < rows) {
+                        x = col[n];
+                        if (b)
+                            x = hmul(x, twist(tw, tl, j, u));
+                    }
+                    v[0][u] = x;
+                }
+            }
+            fft_ct<C, false, LOGN, 1, TC>(v, sbuf, SPC, j, active, tw, &tcx);
+            if (active) {
+                if (ci.kind == SPEC_QUARTER) {
+                    // K0x, K0y imaginary (stored Im), the rest real; bins above N read the
+                    // quarter at P - ky with the table's ky parity: + K0x Kxx Kyy, - Kxy K0y Kyx.
+                    // Bin ky = 2k' + b sits at k' of this parity's half row; its mirror
+                    // P - ky sits at N - k' - b.
+                    const T mx = (f == 2) ? T(-1) : T(1);
+                    const T my = (f == 2) ? T(1) : T(-1);
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const int kp = j + u * Q;
+                        const bool hi = 2 * kp + b > N;
+                        const int q = hi ? N - kp - b : kp;
+                        const T rx = spx[q] * (hi ? mx : T(1));
+                        const T ry = spx[HQ + q] * (hi ? my : T(1));
+                        C tx = hmk<C>(rx * v[0][u].x, rx * v[0][u].y), ty = hmk<C>(ry * v[0][u].x, ry * v[0][u].y);
+                        if (f == 0) {
+                            tx = hmk<C>(-tx.y, tx.x);
+                            ty = hmk<C>(-ty.y, ty.x);
+                        }
+                        acc[0][u] = hadd(acc[0][u], tx);
+                        acc[1][u] = hadd(acc[1][u], ty);
+                    }
+                } else if (ci.kind == SPEC_QUARTER_PHI) {
+                    // the potential alone: P0 real, Px Py imaginary; mirror signs + P0 Px, - Py
+                    const T mx = (f == 2) ? T(-1) : T(1);
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const int kp = j + u * Q;
+                        const bool hi = 2 * kp + b > N;
+                        const int q = hi ? N - kp - b : kp;
+                        const T rx = spx[q] * (hi ? mx : T(1));
+                        C tx = hmk<C>(rx * v[0][u].x, rx * v[0][u].y);
+                        if (f != 0)
+                            tx = hmk<C>(-tx.y, tx.x);
+                        acc[0][u] = hadd(acc[0][u], tx);
+                    }
+                } else if (ci.kind == SPEC_FULL_PHI) {
+                    const C *sx = reinterpret_cast<const C *>(a.spec) + ci.spec_off + ((size_t)f * (N + 1) + kx) * P;
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const int ky = 2 * (j + u * Q) + b;
+                        acc[0][u] = hadd(acc[0][u], hmul(__ldg(sx + ky), v[0][u]));
+                    }
+                } else {
+                    const C *sx = reinterpret_cast<const C *>(a.spec) + ci.spec_off + ((size_t)f * (N + 1) + kx) * P;
+                    const C *sy = reinterpret_cast<const C *>(a.spec) + ci.spec_off + ((size_t)(3 + f) * (N + 1) + kx) * P;
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const int ky = 2 * (j + u * Q) + b;
+                        acc[0][u] = hadd(acc[0][u], hmul(__ldg(sx + ky), v[0][u]));
+                        acc[1][u] = hadd(acc[1][u], hmul(__ldg(sy + ky), v[0][u]));
+                    }
+                }
+            }
+            __syncthreads();  // stage (k & 1) consumed by every thread
+            if (k + 2 < nitems)
+                issue(k + 2);
+            cp_commit();
+        }
+        cp_wait<0>();
+        if (w.slot >= 0) {  // one chunk of a long input list: hand the accumulators to k_col_sum
+            if (active) {
+#pragma unroll
+                for (int comp = 0; comp < 2; ++comp) {
+                    C *dst = a.partial + ((((size_t)w.slot * 2 + b) * 2 + comp) * (N + 1) + kx) * N;
+#pragma unroll
+                    for (int u = 0; u < 16; ++u)
+                        dst[j + u * Q] = acc[comp][u];
+                }
+            }
+            continue;  // both CTAs of the cluster take this branch (w is per cluster)
+        }
+        // inverse column transforms of Fx^ and Fy^ together (the potential: its one
+        // component alone); y[n] = even[n] + W_P^{-n} odd[n]
+        const bool two = a.ncomp == 2;
+        if (two)
+            fft_ct<C, true, LOGN, 2, TC>(acc, sbuf, SPC, j, active, tw, &tcx);
+        else
+            fft_ct<C, true, LOGN, 1, TC>(acc, sbuf, SPC, j, active, tw, &tcx);
+        C *fold = sbuf;  // 2N complex over sbuf and the stages
+        cluster.sync();
+        if (b == 1 && active) {
+            C *dst = cluster.map_shared_rank(fold, 0);
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
                 const int n = j + u * Q;
-                C x = hmk<C>(T(0), T(0));
-                if (n < rows) {
-                    x = col[n];
-                    if (b)
-                        x = hmul(x, twist(tw, tl, j, u));
-                }
-                v[0][u] = x;
-            }
-        }
-        fft_ct<C, false, LOGN, 1, TC>(v, sbuf, SPC, j, active, tw, &tcx);
-        if (active) {
-            if (ci.kind == SPEC_QUARTER) {
-                // K0x, K0y imaginary (stored Im), the rest real; bins above N read the
-                // quarter at P - ky with the table's ky parity: + K0x Kxx Kyy, - Kxy K0y Kyx.
-                // Bin ky = 2k' + b sits at k' of this parity's half row; its mirror
-                // P - ky sits at N - k' - b.
-                const T mx = (f == 2) ? T(-1) : T(1);
-                const T my = (f == 2) ? T(1) : T(-1);
-#pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int kp = j + u * Q;
-                    const bool hi = 2 * kp + b > N;
-                    const int q = hi ? N - kp - b : kp;
-                    const T rx = spx[q] * (hi ? mx : T(1));
-                    const T ry = spx[HQ + q] * (hi ? my : T(1));
-                    C tx = hmk<C>(rx * v[0][u].x, rx * v[0][u].y), ty = hmk<C>(ry * v[0][u].x, ry * v[0][u].y);
-                    if (f == 0) {
-                        tx = hmk<C>(-tx.y, tx.x);
-                        ty = hmk<C>(-ty.y, ty.x);
-                    }
-                    acc[0][u] = hadd(acc[0][u], tx);
-                    acc[1][u] = hadd(acc[1][u], ty);
-                }
-            } else if (ci.kind == SPEC_QUARTER_PHI) {
-                // the potential alone: P0 real, Px Py imaginary; mirror signs + P0 Px, - Py
-                const T mx = (f == 2) ? T(-1) : T(1);
-#pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int kp = j + u * Q;
-                    const bool hi = 2 * kp + b > N;
-                    const int q = hi ? N - kp - b : kp;
-                    const T rx = spx[q] * (hi ? mx : T(1));
-                    C tx = hmk<C>(rx * v[0][u].x, rx * v[0][u].y);
-                    if (f != 0)
-                        tx = hmk<C>(-tx.y, tx.x);
-                    acc[0][u] = hadd(acc[0][u], tx);
-                }
-            } else if (ci.kind == SPEC_FULL_PHI) {
-                const C *sx = reinterpret_cast<const C *>(a.spec) + ci.spec_off + ((size_t)f * (N + 1) + kx) * P;
-#pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int ky = 2 * (j + u * Q) + b;
-                    acc[0][u] = hadd(acc[0][u], hmul(__ldg(sx + ky), v[0][u]));
-                }
-            } else {
-                const C *sx = reinterpret_cast<const C *>(a.spec) + ci.spec_off + ((size_t)f * (N + 1) + kx) * P;
-                const C *sy = reinterpret_cast<const C *>(a.spec) + ci.spec_off + ((size_t)(3 + f) * (N + 1) + kx) * P;
-#pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int ky = 2 * (j + u * Q) + b;
-                    acc[0][u] = hadd(acc[0][u], hmul(__ldg(sx + ky), v[0][u]));
-                    acc[1][u] = hadd(acc[1][u], hmul(__ldg(sy + ky), v[0][u]));
-                }
-            }
-        }
-        __syncthreads();  // stage (k & 1) consumed by every thread
-        if (k + 2 < nitems)
-            issue(k + 2);
-        cp_commit();
-    }
-    cp_wait<0>();
-    if (w.slot >= 0) {  // one chunk of a long input list: hand the accumulators to k_col_sum
-        if (active) {
-#pragma unroll
-            for (int comp = 0; comp < 2; ++comp) {
-                C *dst = a.partial + ((((size_t)w.slot * 2 + b) * 2 + comp) * (N + 1) + kx) * N;
-#pragma unroll
-                for (int u = 0; u < 16; ++u)
-                    dst[j + u * Q] = acc[comp][u];
-            }
-        }
-        if constexpr (TC)
-            tc_end(tcx, TCT);
-        return;  // both CTAs of the cluster take this branch (w is per cluster)
-    }
-    // inverse column transforms of Fx^ and Fy^ together (the potential: its one
-    // component alone); y[n] = even[n] + W_P^{-n} odd[n]
-    const bool two = a.ncomp == 2;
-    if (two)
-        fft_ct<C, true, LOGN, 2, TC>(acc, sbuf, SPC, j, active, tw, &tcx);
-    else
-        fft_ct<C, true, LOGN, 1, TC>(acc, sbuf, SPC, j, active, tw, &tcx);
-    C *fold = sbuf;  // 2N complex over sbuf and the stages
-    cluster.sync();
-    if (b == 1 && active) {
-        C *dst = cluster.map_shared_rank(fold, 0);
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const int n = j + u * Q;
-            const C w = twist(tw, tl, j, u);
-            dst[n] = hmulc(acc[0][u], w);
-            if (two)
-                dst[N + n] = hmulc(acc[1][u], w);
-        }
-    }
-    cluster.sync();
-    if (b == 0 && active) {
-        C *dst = a.bwd + o.off;
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const int n = j + u * Q;
-            if (n < o.rows) {
-                dst[bwd_index(N, o.rows, 0, kx, n)] = hadd(acc[0][u], fold[n]);
+                const C w = twist(tw, tl, j, u);
+                dst[n] = hmulc(acc[0][u], w);
                 if (two)
-                    dst[bwd_index(N, o.rows, 1, kx, n)] = hadd(acc[1][u], fold[N + n]);
+                    dst[N + n] = hmulc(acc[1][u], w);
+            }
+        }
+        cluster.sync();
+        if (b == 0 && active) {
+            C *dst = a.bwd + o.off;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int n = j + u * Q;
+                if (n < o.rows) {
+                    dst[bwd_index(N, o.rows, 0, kx, n)] = hadd(acc[0][u], fold[n]);
+                    if (two)
+                        dst[bwd_index(N, o.rows, 1, kx, n)] = hadd(acc[1][u], fold[N + n]);
+                }
             }
         }
     }
@@ -2061,7 +2067,10 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
         break;
     }
     case PASS_COL: {
-        SGF_LAUNCH((k_col<T, LOGN, false, TC>), (k_col<T, LOGN, true, TC>), 2, S::col(), dim3(2 * (K::N + 1), count),
+        // tensor-core tiles: each cluster walks kColWalk columns of its work item (strided by the
+        // clusters of the item), which keeps many clusters per item for balance
+        const int gx = TC && !batch ? 2 * ((K::N + 1 + kColWalk - 1) / kColWalk) : 2 * (K::N + 1);
+        SGF_LAUNCH((k_col<T, LOGN, false, TC>), (k_col<T, LOGN, true, TC>), 2, S::col(), dim3(gx, count),
                    K::COL_THREADS)
         break;
     }
