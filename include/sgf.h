@@ -237,6 +237,10 @@ sgf_status sgf_solve_host(sgf_plan *plan, const void *const *sigma, void *const 
 sgf_status sgf_solve_batched(sgf_plan *const *plans, int32_t count, const void *const *const *sigma,
                              void *const *const *fx, void *const *const *fy, void *stream);
 
+/* Free a plan: its workspace, its host-solve staging and (with its last
+ * sharer) the kernel spectra (cudaFree waits for work still using them).
+ * NULL is accepted (SGF_OK).  A plan still in a batch must not be destroyed
+ * before the batch. */
 sgf_status sgf_plan_destroy(sgf_plan *plan);
 
 /* Fused batches of independent nests (no paper counterpart: throughput for many
@@ -251,10 +255,21 @@ sgf_status sgf_plan_destroy(sgf_plan *plan);
  * waits only for the previous solve's copy; arguments as sgf_solve_batched. */
 typedef struct sgf_batch sgf_batch;
 #define SGF_BATCH_NO_GRAPH 0x1u
+/* plans[0..count): distinct force plans (no SGF_PLAN_POTENTIAL), one
+ * precision, one device; the batch keeps pointers to them.  flags: 0 or
+ * SGF_BATCH_NO_GRAPH.  On success *out owns device and pinned host memory
+ * until sgf_batch_destroy.  Errors: SGF_EINVAL (NULL, repeated or mixed plans,
+ * count < 1), SGF_EUNSUPPORTED (potential plans), SGF_ENOMEM, SGF_ECUDA. */
 sgf_status sgf_batch_create(sgf_plan *const *plans, int32_t count, uint32_t flags, sgf_batch **out);
+/* One fused solve of every nest of the batch: sigma[k], fx[k], fy[k] as in
+ * sgf_solve_batched, in the order the plans were given.  Asynchronous on
+ * `stream`.  Errors: SGF_EINVAL, SGF_ECUDA. */
 sgf_status sgf_batch_solve(sgf_batch *batch, const void *const *const *sigma, void *const *const *fx,
                            void *const *const *fy, void *stream);
+/* *groups: the launch groups (nests of one n and path); *launches_per_solve:
+ * the kernel launches of one sgf_batch_solve.  Either pointer may be NULL. */
 sgf_status sgf_batch_info(const sgf_batch *batch, int32_t *groups, int32_t *launches_per_solve);
+/* Free the batch (not its plans).  NULL is accepted. */
 sgf_status sgf_batch_destroy(sgf_batch *batch);
 
 /* Per-kernel device times of this plan's solves, for measurement (no paper
@@ -338,6 +353,7 @@ typedef struct {
     int32_t col_case3;
 } sgf_schedule;
 
+/* The plan's current schedule.  Errors: SGF_EINVAL for a NULL argument. */
 sgf_status sgf_plan_schedule_get(const sgf_plan *plan, sgf_schedule *schedule);
 /* Errors: SGF_EINVAL for a NULL argument or a choice out of range;
  * SGF_EUNSUPPORTED for col_pass = 2 or row_inv0 = 1 on a SGF_BF16X plan of
