@@ -107,6 +107,9 @@ def _load():
         lib.oracle_forest_potential_targets.argtypes = [fp, dpp, dpp, dpp, ctypes.c_long, ip, ip, ip, dp,
                                                         ctypes.c_int]
         lib.oracle_forest_potential_targets.restype = ctypes.c_int
+        lib.oracle_force_row.argtypes = [ctypes.POINTER(_Nest), dp, dp, dp, ctypes.c_int, ctypes.c_long, ip,
+                                         dp, dp, ctypes.c_int]
+        lib.oracle_force_row.restype = ctypes.c_int
         lib.oracle_max_threads.argtypes = []
         lib.oracle_max_threads.restype = ctypes.c_int
         for name in ("oracle_genconv_case2", "oracle_genconv_case3"):
@@ -226,6 +229,40 @@ def force(desc, sigma, nthreads: int = 0):
     fx, fy = force_at(desc, sigma, lv, iv, jv, nthreads=nthreads)
     return [fx[l * n * n:(l + 1) * n * n].reshape(n, n) for l in range(L)], \
            [fy[l * n * n:(l + 1) * n * n].reshape(n, n) for l in range(L)]
+
+
+def force_row(desc, sigma, jt: int, ii=None, nthreads: int = 0, prepared=None):
+    """(Fx, Fy) at the targets (ii[k], jt) of row jt (every column if ii is None)
+    of a single-level grid: the direct sum of oracle_force_targets, with the cell
+    integrals of each source row evaluated once per cell offset from the target
+    and shared by the row's targets (oracle.c, oracle_force_row)."""
+    if _is_forest(desc) or int(desc.levels) != 1:
+        raise ValueError("force_row takes a single-level grid")
+    n = int(desc.n)
+    sig, dsx, dsy = prepared if prepared is not None else prepare(desc, sigma)
+    iv = np.arange(n, dtype=np.int32) if ii is None else np.ascontiguousarray(ii, dtype=np.int32)
+    fx = np.zeros(iv.size)
+    fy = np.zeros(iv.size)
+    rc = _load().oracle_force_row(ctypes.byref(_nest(desc)), _dp(sig[0]), _dp(dsx[0]), _dp(dsy[0]), int(jt),
+                                  iv.size, iv.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(fx), _dp(fy),
+                                  int(nthreads))
+    if rc:
+        raise ValueError(f"oracle_force_row rc={rc}")
+    return fx, fy
+
+
+def force_col(desc, sigma, it: int, jj=None, nthreads: int = 0):
+    """(Fx, Fy) at the targets (it, jj[k]) of column it (every row if jj is None)
+    of a single-level grid, by the x <-> y symmetry of the method: the grid with
+    sigma transposed has the slope fields of sigma swapped and transposed (the
+    slope rule treats x and y alike), its kernels are those of the original with
+    the roles of u and v exchanged, so its row it holds (Fy, Fx) of column it."""
+    if _is_forest(desc) or int(desc.levels) != 1:
+        raise ValueError("force_col takes a single-level grid")
+    sig, dsx, dsy = prepare(desc, sigma)
+    tr = ([np.ascontiguousarray(sig[0].T)], [np.ascontiguousarray(dsy[0].T)], [np.ascontiguousarray(dsx[0].T)])
+    gy, gx = force_row(desc, None, it, jj, nthreads=nthreads, prepared=tr)
+    return gx, gy
 
 
 def genconv_case2(b, c, m: int, nout: int) -> np.ndarray:

@@ -343,6 +343,107 @@ int oracle_force_targets(const oracle_nest *g, const double *const *sig, const d
     return fail ? -3 : 0;
 }
 
+/* Forces at the targets (ti[k], jt), k < nt, of one row jt of a single-level
+ * grid (levels == 1), from prepared fields: the same direct sum over every
+ * source cell as oracle_force_targets, evaluated for many targets of one row.
+ * On one level every coordinate difference is a whole number of half cells:
+ * a source corner lies (e - 1/2) h from a target centre along x, e = corner
+ * column - target column, and the cell centre a h, a = cell column - target
+ * column; along y likewise with the rows.  So for a source row j the cell
+ * integrals depend on the target only through a, and they are evaluated once
+ * per a in [-(n-1), n-1] (corner antiderivatives on the 2n corner offsets of
+ * the row's two edges, then the double difference, in the order of sum_patch)
+ * and read by every target of the row.  Each target sums the cells row by row,
+ * column by column, as sum_patch does; differences are written (e - 1/2) h,
+ * a h and (j - jt +- 1/2) h, which are the lattice positions themselves (exact
+ * when h is a power of two, as for grids on [-1, 1] with n a power of two).
+ * Returns 0, -1 for a descriptor with more than one level, -2 for a target
+ * outside the grid, -3 when memory runs out. */
+int oracle_force_row(const oracle_nest *g, const double *sig, const double *dsx, const double *dsy, int jt,
+                     long nt, const int *ti, double *fx, double *fy, int nthreads)
+{
+    if (oracle_validate(g) || g->levels != 1)
+        return -1;
+    const int n = g->n;
+    const double h = g->h0;
+    if (jt < 0 || jt >= n)
+        return -2;
+    for (long k = 0; k < nt; ++k)
+        if (ti[k] < 0 || ti[k] >= n)
+            return -2;
+#ifdef _OPENMP
+    if (nthreads > 0)
+        omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    const int E = 2 * n;  /* corner offsets e = -(n-1) .. n at index e + n - 1 */
+    double *lo = (double *)malloc(sizeof(double) * 5 * (size_t)E);
+    double *hi = (double *)malloc(sizeof(double) * 5 * (size_t)E);
+    double *I = (double *)malloc(sizeof(double) * 5 * (size_t)(E - 1));  /* a + n - 1 */
+    double *ax = (double *)calloc((size_t)(nt > 0 ? nt : 1), sizeof(double));
+    double *ay = (double *)calloc((size_t)(nt > 0 ? nt : 1), sizeof(double));
+    if (!lo || !hi || !I || !ax || !ay) {
+        free(lo);
+        free(hi);
+        free(I);
+        free(ax);
+        free(ay);
+        return -3;
+    }
+#pragma omp parallel
+    {
+#pragma omp for schedule(static)
+        for (int x = 0; x < E; ++x)  /* lower edge of source row 0 */
+            corner_values((x - n + 1 - 0.5) * h, (0 - jt - 0.5) * h, lo + 5 * (size_t)x);
+        for (int j = 0; j < n; ++j) {
+#pragma omp for schedule(static)
+            for (int x = 0; x < E; ++x)  /* upper edge of source row j */
+                corner_values((x - n + 1 - 0.5) * h, (j - jt + 0.5) * h, hi + 5 * (size_t)x);
+#pragma omp for schedule(static)
+            for (int x = 0; x < E - 1; ++x) {  /* cell offset a = x - (n - 1) */
+                const double *kbd = hi + 5 * (size_t)(x + 1), *kad = hi + 5 * (size_t)x;
+                const double *kbc = lo + 5 * (size_t)(x + 1), *kac = lo + 5 * (size_t)x;
+                for (int q = 0; q < 5; ++q)
+                    I[5 * (size_t)x + q] = kbd[q] - kad[q] - kbc[q] + kac[q];
+            }
+            const double vc = (j - jt) * h;
+#pragma omp for schedule(static)
+            for (long k = 0; k < nt; ++k) {
+                double sx = ax[k], sy = ay[k];
+                for (int i = 0; i < n; ++i) {
+                    const size_t c = (size_t)j * n + i;
+                    if (sig[c] == 0.0 && dsx[c] == 0.0 && dsy[c] == 0.0)
+                        continue;
+                    const int a = i - ti[k];
+                    const double *Ia = I + 5 * (size_t)(a + n - 1);
+                    const double uc = a * h;
+                    sx += sig[c] * Ia[0] + dsx[c] * (Ia[2] - uc * Ia[0]) + dsy[c] * (Ia[4] - vc * Ia[0]);
+                    sy += sig[c] * Ia[1] + dsx[c] * (Ia[4] - uc * Ia[1]) + dsy[c] * (Ia[3] - vc * Ia[1]);
+                }
+                ax[k] = sx;
+                ay[k] = sy;
+            }
+#pragma omp single
+            {
+                double *t = lo;
+                lo = hi;
+                hi = t;
+            }
+        }
+    }
+    for (long k = 0; k < nt; ++k) {
+        fx[k] = ax[k];
+        fy[k] = ay[k];
+    }
+    free(lo);
+    free(hi);
+    free(I);
+    free(ax);
+    free(ay);
+    return 0;
+}
+
 /* Potential at one target point from the prepared fields of one patch (the
  * same edge-lattice walk as sum_patch). */
 static void sum_patch_potential(int n, double X, double Y, double h, const double *sig, const double *dsx,
