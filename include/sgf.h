@@ -305,8 +305,13 @@ const char *sgf_last_error(void);
  * intermediates live in one fixed array of SGF_NOALLOC_SCRATCH_BYTES in the
  * library's device memory, which every GPU that loads the library holds until
  * the process exits.  The paper has no counterpart to this entry point.
- *   - The first call on a device looks up that array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - A plan whose intermediates fit the array looks up the array's device
+ *     address (cudaGetSymbolAddress) when it is created, in its device's
+ *     context, and keeps it; this call only reads that address.  Under lazy
+ *     module loading the lookup is also when the driver reserves the array,
+ *     so that reservation falls in plan creation, not here.  The address
+ *     lives as long as the plan: a plan does not survive a reset of its
+ *     device (cudaDeviceReset).
  *   - Every call on a device uses the same array: calls whose work overlaps on
  *     the GPU (other streams, other host threads) race and corrupt each other's
  *     results; order them on one stream or synchronise between them.  The

@@ -186,6 +186,9 @@ struct sgf_plan {
     void *d_restricted = nullptr;  // restricted * N * N reals
     // host-buffer solve staging (allocated on first sgf_solve_host)
     void *d_stage = nullptr;
+    // device address of sgf_solve_noalloc's scratch array, looked up at plan
+    // creation when the plan's intermediates fit it (else NULL)
+    void *noalloc_scratch = nullptr;
     size_t workspace_bytes = 0;
     size_t algorithmic_bytes = 0;
     // optional per-kernel timing: 5 events per solve (before restriction, after
@@ -1154,32 +1157,13 @@ sgf_status solve_dispatch(sgf_plan *p, const void *const *sigma, void *const *fx
 // ---- allocation-free solve (sgf_solve_noalloc) -----------------------------
 // Scratch of sgf_solve_noalloc: one file-scope device array, shared by every
 // call on a device and held by every device that loads this library.  Host
-// code must not use the symbol as an address; the per-device address comes
-// from cudaGetSymbolAddress (noalloc_scratch_on_current_device).
+// code must not use the symbol as an address: every plan that fits the array
+// looks its device address up when it is created (noalloc_scratch_lookup), in
+// the plan's own context, so that sgf_solve_noalloc only reads that pointer.
+// The lookup is what makes the driver load this translation unit's module, and
+// with it reserve the array, under lazy module loading; doing it at plan
+// creation keeps that reservation out of the call that promises not to allocate.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SGF_NOALLOC_SCRATCH_BYTES];
-
-std::mutex g_noalloc_mu;
-void *g_noalloc_ptr[64] = {};
-
-// Device address of the scratch array on the current device (looked up once per device).
-sgf_status noalloc_scratch_on_current_device(void **out)
-{
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess)
-        return cuda_fail(e, "cudaGetDevice");
-    if (dev < 0 || dev >= 64)
-        return fail(SGF_EUNSUPPORTED, "device %d: sgf_solve_noalloc supports devices 0..63", dev);
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *ptr = nullptr;
-        if ((e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch)) != cudaSuccess)
-            return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
-        g_noalloc_ptr[dev] = ptr;
-    }
-    *out = g_noalloc_ptr[dev];
-    return SGF_OK;
-}
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -1189,6 +1173,18 @@ size_t noalloc_bytes(const sgf_plan *p)
     const size_t Cb = 2 * p->esize;
     return align256((size_t)p->restricted * p->N * p->N * p->esize) + align256(p->fwd_elems * Cb) +
            align256(p->bwd_elems * Cb) + align256(p->partial_elems * Cb);
+}
+
+// The scratch array's device address in the current context (the plan's
+// device), stored in the plan; called at plan creation for plans that fit.
+sgf_status noalloc_scratch_lookup(sgf_plan *p)
+{
+    void *ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
+    p->noalloc_scratch = ptr;
+    return SGF_OK;
 }
 
 // The solve of solve_impl with its intermediates in `scratch` and without the
@@ -1759,6 +1755,8 @@ sgf_status plan_create(const Forest &fo, sgf_precision precision, uint32_t flags
         s = plan_alloc_owned(p);
     if (s == SGF_OK)
         s = prepare_kernels(p);
+    if (s == SGF_OK && noalloc_bytes(p) <= (size_t)SGF_NOALLOC_SCRATCH_BYTES)
+        s = noalloc_scratch_lookup(p);
     if (s != SGF_OK) {
         std::string msg = g_err;
         plan_free_owned(p);
@@ -1897,6 +1895,8 @@ sgf_status sgf_plan_share_ex(const sgf_plan *src, sgf_precision precision, sgf_p
     }
     if (s == SGF_OK)
         s = prepare_kernels(p);
+    if (s == SGF_OK && noalloc_bytes(p) <= (size_t)SGF_NOALLOC_SCRATCH_BYTES)
+        s = noalloc_scratch_lookup(p);
     if (s != SGF_OK) {
         std::string msg = g_err;
         plan_free_owned(p);
@@ -2165,12 +2165,11 @@ sgf_status sgf_solve_noalloc(sgf_plan *p, const void *const *sigma, void *const 
         return fail(SGF_EUNSUPPORTED,
                     "sgf_solve_noalloc: this plan needs %zu bytes of scratch, above SGF_NOALLOC_SCRATCH_BYTES = %zu",
                     need, (size_t)SGF_NOALLOC_SCRATCH_BYTES);
+    if (!p->noalloc_scratch)
+        return fail(SGF_ECUDA, "sgf_solve_noalloc: the plan holds no scratch address");
     DeviceGuard g(p->device);
-    void *scratch = nullptr;
-    if ((s = noalloc_scratch_on_current_device(&scratch)) != SGF_OK)
-        return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    unsigned char *sc = static_cast<unsigned char *>(scratch);
+    unsigned char *sc = static_cast<unsigned char *>(p->noalloc_scratch);
     return p->prec == SGF_FP64 ? solve_noalloc_impl<double>(p, sigma, fx, fy, st, sc)
                                : solve_noalloc_impl<float>(p, sigma, fx, fy, st, sc);
 }

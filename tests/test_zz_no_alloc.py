@@ -65,3 +65,66 @@ def test_noalloc_refuses_plans_beyond_the_limit(lib):
         plan.solve_noalloc_ptrs([s.data_ptr()], [fx.data_ptr()], [fy.data_ptr()])
     assert e.value.status == lib.SGF_EUNSUPPORTED
     assert "SGF_NOALLOC_SCRATCH_BYTES" in str(e.value)
+
+
+def test_noalloc_bf16x_nest(lib):
+    """The split-BF16 tensor-core kernels (and the level-0 inverse row schedule
+    that replaces the plan's tensor-map gather) through the fixed scratch."""
+    n, L = 256, 2
+    rng = np.random.Generator(np.random.PCG64(23))
+    nest, _ = W.random_nest_problem(rng, n, L)
+    plan = lib.Plan(nest, "bf16x")
+    for call in range(2):
+        sigma = [rng.uniform(0.1, 1.5, (n, n)) for _ in range(L)]
+        ref = run_gpu(plan, sigma)
+        got = _noalloc(plan, sigma)
+        plan.check()
+        errs = rel_linf_levels(nest, got[0], got[1], ref[0], ref[1])
+        assert max(errs) <= tol("fp32", n), (call, errs)
+
+
+def test_noalloc_example3_forest(lib):
+    """Several level-0 patches: the Case-3 group and chunk-sum launches that
+    read the scratch's partial-accumulator region."""
+    f = W.example3_forest(32)
+    sigma = W.two_disk_density(f)
+    plan = lib.Plan(f, "fp32")
+    ref = run_gpu(plan, sigma)
+    for _ in range(2):
+        got = _noalloc(plan, sigma)
+        for p in range(f.patches):
+            assert np.array_equal(got[0][p], ref[0][p]) and np.array_equal(got[1][p], ref[1][p]), p
+
+
+_FRESH = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_1603_03142_gb300 import sgf, workloads as W
+torch.cuda.set_device(0)
+nest = W.Nest(n=256, levels=2, off=[(0, 0), (64, 64)])
+plan = sgf.Plan(nest, "fp32")  # the scratch address is looked up here
+sig = [torch.rand((256, 256), device="cuda") for _ in range(2)]
+fx = [torch.empty_like(s) for s in sig]
+fy = [torch.empty_like(s) for s in sig]
+torch.cuda.synchronize()
+free0 = torch.cuda.mem_get_info()[0]
+plan.solve_noalloc_ptrs([s.data_ptr() for s in sig], [t.data_ptr() for t in fx], [t.data_ptr() for t in fy])
+torch.cuda.synchronize()
+free1 = torch.cuda.mem_get_info()[0]
+print("FREE", free0, free1)
+"""
+
+
+def test_noalloc_first_call_reserves_no_device_memory(lib):
+    """In a fresh process, the first no-allocation solve on the device leaves the
+    device's free memory unchanged: the library's array was reserved when the
+    plan was made, so the call itself takes nothing."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _FRESH, root], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    line = [x for x in r.stdout.splitlines() if x.startswith("FREE")][-1]
+    free0, free1 = map(int, line.split()[1:])
+    assert free0 == free1, (free0, free1)
