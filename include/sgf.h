@@ -124,16 +124,40 @@ typedef struct {
     size_t algorithmic_bytes;   /* HBM bytes one solve must move: inputs, outputs, spectra and
                                    the two transposed intermediates, each read or written once */
     double plan_ms;             /* wall time spent building the spectra */
+    int32_t spectra_sets_streamed; /* sets regenerated at every solve (spectra budget), else 0 */
+    int32_t spectra_waves;      /* window refills per solve (spectra budget), else 0 */
+    size_t spectra_window_bytes; /* the streamed sets' window (spectra budget), else 0 */
 } sgf_plan_stats;
 
 /* Build a plan on the current CUDA device: validates the descriptor, builds
  * every kernel table in FP64 (closed-form cell integrals, Sec. 2.1, Eq.
- * eqnCalK and the slope kernels), transforms them (FP64 FFT) into resident
- * kernel spectra, and allocates the solve workspace.  Blocks until done.
+ * eqnCalK and the slope kernels), transforms them (FP64 FFT) into kernel
+ * spectra, and allocates the solve workspace.  Blocks until done.
+ * spectra_budget: device bytes the plan's kernel spectra may hold, 0 for no
+ * limit.  Each pair of levels with m = 2^|level difference| needs m^2 sets of
+ * spectra (Sec. 2.2, Eqs. eqnbmnn and eqnbnmn), so deep nests hold far more
+ * spectra than grid data.  When they exceed the budget, the sets of the
+ * shallowest pairs stay resident (Case 1 first) and the others are
+ * regenerated in FP64 at every solve, a window of them at a time, inside the
+ * solve's stream: the forces are the same (to rounding: the inputs of an
+ * output are summed in another order), the solve takes the generation time in
+ * addition.  Such a plan takes force solves only (not SGF_PLAN_ZERO_RIM,
+ * which is never that large), cannot join a batch, and refuses
+ * sgf_solve_noalloc; its footprint (sgf_plan_footprint) holds the resident
+ * sets and the window within the budget, plus the generator's FP64 workspace
+ * (sgf_plan_estimate's build_bytes) in its workspace.
  * On success *out owns device memory until sgf_plan_destroy.
  * Errors: SGF_EINVAL (descriptor), SGF_EUNSUPPORTED (n or precision),
- * SGF_ENOMEM, SGF_ECUDA. */
-sgf_status sgf_plan_create(const sgf_nest_desc *desc, sgf_precision precision, sgf_plan **out);
+ * SGF_ENOMEM (also a budget below one set of spectra), SGF_ECUDA. */
+sgf_status sgf_plan_create(const sgf_nest_desc *desc, sgf_precision precision, size_t spectra_budget,
+                           sgf_plan **out);
+
+/* Device bytes a plan holds: *workspace_bytes its own workspace (work lists,
+ * intermediates, and for a plan over its spectra budget the generator's FP64
+ * workspace), *spectra_bytes its kernel spectra (resident sets plus, over
+ * budget, the window of the regenerated ones; shared between plans made by
+ * sgf_plan_share).  The paper has no counterpart.  Errors: SGF_EINVAL. */
+sgf_status sgf_plan_footprint(const sgf_plan *plan, size_t *workspace_bytes, size_t *spectra_bytes);
 
 /* Plan options (bit flags) for sgf_plan_create_ex. */
 #define SGF_PLAN_ZERO_RIM 0x1u
@@ -162,9 +186,9 @@ sgf_status sgf_plan_create(const sgf_nest_desc *desc, sgf_precision precision, s
  * SGF_BF16X at n = SGF_MAX_N).  The potential depends on the cell size (Phi
  * scales with h0 at fixed sigma) where the forces do not. */
 
-/* As sgf_plan_create, with option flags (0 = sgf_plan_create).  Errors as
- * sgf_plan_create; SGF_EINVAL for unknown flags or SGF_PLAN_ZERO_RIM with
- * levels > 1. */
+/* As sgf_plan_create with no spectra budget, with option flags (0 =
+ * sgf_plan_create(desc, precision, 0, out)).  Errors as sgf_plan_create;
+ * SGF_EINVAL for unknown flags or SGF_PLAN_ZERO_RIM with levels > 1. */
 sgf_status sgf_plan_create_ex(const sgf_nest_desc *desc, sgf_precision precision, uint32_t flags,
                               sgf_plan **out);
 
@@ -334,7 +358,10 @@ sgf_status sgf_solve_noalloc(sgf_plan *plan, const void *const *sigma, void *con
  *     n = 4096), 1 = both in flight (two sequences per thread sharing the
  *     barriers; two CTAs per SM, the parity halves of a column in a 2-CTA
  *     cluster), 2 = as 1 with both parity halves in one CTA (no cluster; the
- *     column staged once).
+ *     column staged once), 3 = one thread per slot carrying both parity halves
+ *     of its column, the fold of the halves in registers and the stage
+ *     twiddles of the slot held in registers for the whole launch (force plans
+ *     in SGF_FP32 with n >= 1024; batches run 2 in its place).
  *   row_inv0: 0 = level 0's inverse row pass with one CTA per (row pair,
  *     component), the finer levels through the nest kernel; 2 = the same with
  *     one CTA per row pair holding both components (two sequences per thread
@@ -363,8 +390,9 @@ sgf_status sgf_plan_schedule_get(const sgf_plan *plan, sgf_schedule *schedule);
 /* Errors: SGF_EINVAL for a NULL argument or a choice out of range;
  * SGF_EUNSUPPORTED for col_pass = 2 or row_inv0 = 1 on a SGF_BF16X plan of
  * n = SGF_MAX_N (those kernels have no shared memory left for the tensor-core
- * tiles there), row_inv0 = 2 on a potential plan, row_inv0 = 3 where it does
- * not apply (the autotuner skips all of these). */
+ * tiles there), col_pass = 3 outside zero-rim SGF_FP32 force plans of
+ * n >= 1024, row_inv0 = 2 on a potential plan, row_inv0 = 3 where it does not
+ * apply (the autotuner skips all of these). */
 sgf_status sgf_plan_schedule_set(sgf_plan *plan, const sgf_schedule *schedule);
 
 /* The autotuner: runs one solve on zero density (temporary device buffers),
@@ -376,10 +404,11 @@ sgf_status sgf_plan_schedule_set(sgf_plan *plan, const sgf_schedule *schedule);
  * <row_inv0> <col_case3>" per key, read once, rewritten after each tuning).  chosen (may be
  * NULL) receives the schedule; ms (may be NULL, else SGF_AUTOTUNE_TIMES
  * doubles) the mean milliseconds per launch of col_pass 0, 1, 2, row_inv0 0, 1,
- * 2, col_case3 0, 1, row_inv0 3 (-1 where a candidate does not apply).  Blocks
+ * 2, col_case3 0, 1, row_inv0 3, col_pass 3 (-1 where a candidate does not
+ * apply).  Blocks
  * until done.
  * Errors: SGF_EINVAL, SGF_ENOMEM, SGF_ECUDA. */
-#define SGF_AUTOTUNE_TIMES 9
+#define SGF_AUTOTUNE_TIMES 10
 sgf_status sgf_plan_autotune(sgf_plan *plan, int32_t reps, void *stream, sgf_schedule *chosen, double *ms);
 
 /* Device memory a plan for this nest would hold, computed on the host without
@@ -427,6 +456,12 @@ typedef struct sgf_server sgf_server;
  * sgf_plan_autotune on its own stream when it is created, and later slots of
  * the key take the tuned schedule. */
 #define SGF_SERVER_NO_AUTOTUNE 0x2u
+/* SGF_SERVER_STREAM: a nest whose spectra and generator memory exceed
+ * max_shape_bytes is not rejected but served by plans with a spectra budget
+ * (sgf_plan_create) of max_shape_bytes less the generator memory: those
+ * requests regenerate most of their spectra at every solve and take
+ * correspondingly longer. */
+#define SGF_SERVER_STREAM 0x4u
 
 typedef struct {
     size_t hbm_budget;     /* device bytes the server may hold; 0 = 90% of the free memory at creation */

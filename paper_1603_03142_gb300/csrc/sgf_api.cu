@@ -186,6 +186,22 @@ struct sgf_plan {
     void *d_restricted = nullptr;  // restricted * N * N reals
     // host-buffer solve staging (allocated on first sgf_solve_host)
     void *d_stage = nullptr;
+    // spectra budget (sgf_plan_create): when the kernel spectra exceed it, the
+    // sets that fit stay resident and the others are regenerated at every solve,
+    // wave by wave, through a window (streamed plans)
+    size_t spectra_budget = 0;       // 0: every set resident
+    bool streamed = false;
+    std::vector<int> in_set;         // spectra set of every column input
+    std::vector<int> set_wave;       // per set: -1 resident, else its wave
+    std::vector<std::vector<int>> wave_sets;
+    int waves = 0;
+    size_t resident_bytes = 0, window_bytes = 0;
+    std::vector<ColWork> work_stream;  // the resident pass, then one pass per wave
+    std::vector<int> stream_begin;     // waves + 2 offsets into work_stream
+    const ColWork *d_work_stream = nullptr;
+    void *d_window = nullptr;          // the current wave's sets
+    void *d_gen = nullptr;             // generator workspace: twiddles | FP64 tables | half spectra
+    size_t gen_bytes = 0;
     // device address of sgf_solve_noalloc's scratch array, looked up at plan
     // creation when the plan's intermediates fit it (else NULL)
     void *noalloc_scratch = nullptr;
@@ -643,8 +659,11 @@ void build_lists(sgf_plan *p)
         off += (set_bytes[k] + 255) & ~(size_t)255;
         p->sets[k].spec_off = spec_quarter(p->sets[k].kind) ? set_off[k] / T : set_off[k] / Cb;
     }
-    for (auto &ci : p->ins)
+    p->in_set.clear();
+    for (auto &ci : p->ins) {
+        p->in_set.push_back((int)ci.spec_off);
         ci.spec_off = p->sets[ci.spec_off].spec_off;
+    }
     // algorithmic bytes of one solve
     const size_t ncomp = p->pot ? 1 : 2;
     size_t ab = (1 + ncomp) * (size_t)L * N * N * T;              // sigma in, Fx and Fy (or Phi) out
@@ -680,6 +699,152 @@ size_t spectra_total(const sgf_plan *p)
     return off;
 }
 
+// Stored bytes of one spectra set (256-byte aligned), as spectra_total counts them.
+size_t set_bytes_of(const sgf_plan *p, const GenSet &g)
+{
+    const size_t nt = (size_t)spec_tables(g.kind);
+    const size_t b = g.kind == SPEC_MERGED || g.kind == SPEC_MERGED_PHI || spec_quarter(g.kind)
+                         ? nt * (p->N + 1) * quarter_stride(p->N) * p->esize
+                         : nt * (p->N + 1) * 2 * p->N * 2 * p->esize;
+    return (b + 255) & ~(size_t)255;
+}
+
+// A plan whose kernel spectra exceed its budget.  Residency: the sets of the
+// fewest phases first (Case 1, then the shallowest level pairs), while a window
+// for the largest set still fits beside them; the rest are streamed: packed in
+// set order into waves of at most the window's bytes and regenerated in FP64 at
+// every solve, wave after wave, into the window.  Every solve needs every set
+// once, in the same order, so a fixed resident part and a streaming window move
+// the fewest bytes (a least-recently-used cache would evict each set just before
+// its next use).  Each output's inputs are regrouped resident first, then by
+// wave; the column pass runs once over the resident inputs and once per wave,
+// every output with inputs in more than one pass (or more than kChunkInputs in
+// one) accumulating its chunks in partial slots that k_col_sum adds up.
+// The Case-3 groups of k_col_g are not used (each Case-3 output is its own work item).
+sgf_status plan_stream_layout(sgf_plan *p)
+{
+    const size_t total = spectra_total(p);
+    p->streamed = false;
+    if (p->spectra_budget == 0 || total <= p->spectra_budget)
+        return SGF_OK;
+    if (p->merged || p->pot)
+        return fail(SGF_EUNSUPPORTED,
+                    "a spectra budget below the plan's %zu bytes of spectra needs a force plan without "
+                    "SGF_PLAN_ZERO_RIM", total);
+    const int S = (int)p->sets.size();
+    std::vector<size_t> sb(S);
+    size_t maxset = 0;
+    for (int k = 0; k < S; ++k) {
+        sb[k] = set_bytes_of(p, p->sets[k]);
+        maxset = std::max(maxset, sb[k]);
+    }
+    if (p->spectra_budget < maxset)
+        return fail(SGF_ENOMEM, "spectra budget of %zu bytes is below one kernel-spectrum set (%zu bytes)",
+                    p->spectra_budget, maxset);
+    std::vector<int> order(S);
+    for (int k = 0; k < S; ++k)
+        order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return p->sets[x].m < p->sets[y].m; });
+    std::vector<char> res(S, 0);
+    size_t R = 0;
+    for (int k : order)
+        if (R + sb[k] + maxset <= p->spectra_budget) {
+            res[k] = 1;
+            R += sb[k];
+        }
+    const size_t W = p->spectra_budget - R;
+    p->set_wave.assign(S, -1);
+    p->wave_sets.clear();
+    size_t off_r = 0, off_w = 0, wmax = 0;
+    for (int k = 0; k < S; ++k) {
+        const size_t unit = spec_quarter(p->sets[k].kind) ? p->esize : 2 * p->esize;
+        if (res[k]) {
+            p->sets[k].spec_off = off_r / unit;
+            off_r += sb[k];
+            continue;
+        }
+        if (p->wave_sets.empty() || off_w + sb[k] > W) {
+            p->wave_sets.emplace_back();
+            off_w = 0;
+        }
+        p->set_wave[k] = (int)p->wave_sets.size() - 1;
+        p->wave_sets.back().push_back(k);
+        p->sets[k].spec_off = off_w / unit;
+        off_w += sb[k];
+        wmax = std::max(wmax, off_w);
+    }
+    p->waves = (int)p->wave_sets.size();
+    p->resident_bytes = R;
+    p->window_bytes = wmax;
+    p->streamed = true;
+    // inputs: new offsets, each output's inputs regrouped by pass (resident, then wave order)
+    auto pass_of = [&](int i) { return p->set_wave[p->in_set[i]] + 1; };
+    for (auto &o : p->outs) {
+        std::vector<int> idx(o.in_count);
+        for (int k = 0; k < o.in_count; ++k)
+            idx[k] = o.in_begin + k;
+        std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return pass_of(x) < pass_of(y); });
+        std::vector<ColInput> ins(o.in_count);
+        std::vector<int> sets(o.in_count);
+        for (int k = 0; k < o.in_count; ++k) {
+            ins[k] = p->ins[idx[k]];
+            sets[k] = p->in_set[idx[k]];
+        }
+        for (int k = 0; k < o.in_count; ++k) {
+            p->ins[o.in_begin + k] = ins[k];
+            p->in_set[o.in_begin + k] = sets[k];
+        }
+    }
+    for (size_t i = 0; i < p->ins.size(); ++i)
+        p->ins[i].spec_off = p->sets[p->in_set[i]].spec_off;
+    // work items: per output, runs of inputs of one pass, at most kChunkInputs each
+    std::vector<std::vector<ColWork>> pass(p->waves + 1);
+    p->sums.clear();
+    int slots = 0;
+    for (int oi = 0; oi < (int)p->outs.size(); ++oi) {
+        const ColOutput &o = p->outs[oi];
+        std::vector<ColWork> chunks;
+        std::vector<int> cpass;
+        for (int i = o.in_begin; i < o.in_begin + o.in_count;) {
+            int j = i;
+            while (j < o.in_begin + o.in_count && pass_of(j) == pass_of(i) && j - i < kChunkInputs)
+                ++j;
+            chunks.push_back(ColWork{oi, i, j - i, -1});
+            cpass.push_back(pass_of(i));
+            i = j;
+        }
+        if (chunks.size() == 1) {
+            pass[cpass[0]].push_back(chunks[0]);
+            continue;
+        }
+        const int first = slots;
+        for (size_t c = 0; c < chunks.size(); ++c) {
+            chunks[c].slot = slots++;
+            pass[cpass[c]].push_back(chunks[c]);
+        }
+        p->sums.push_back(ColSum{oi, first, slots - first, 0});
+    }
+    p->partial_elems = (size_t)slots * 4 * p->N * (p->N + 1);
+    p->work_stream.clear();
+    p->stream_begin.assign(1, 0);
+    for (auto &v : pass) {
+        p->work_stream.insert(p->work_stream.end(), v.begin(), v.end());
+        p->stream_begin.push_back((int)p->work_stream.size());
+    }
+    p->groups.clear();
+    return SGF_OK;
+}
+
+// Generator workspace of a streamed plan: FP64 twiddles of the 2N-point
+// transform, six 2N x 2N FP64 tables, six half spectra.
+size_t gen_bytes_of(int N)
+{
+    const size_t P = 2 * (size_t)N;
+    const size_t tw = (P * sizeof(double2) + 255) & ~(size_t)255;
+    const size_t tab = (6 * P * P * sizeof(double) + 255) & ~(size_t)255;
+    return tw + tab + 6 * (size_t)(N + 1) * P * sizeof(double2);
+}
+
 void plan_free_owned(sgf_plan *p)
 {
     int cur = 0;
@@ -692,6 +857,9 @@ void plan_free_owned(sgf_plan *p)
     cudaFree(p->d_stage);
     cudaFree(p->d_partial);
     p->d_partial = nullptr;
+    cudaFree(p->d_window);
+    cudaFree(p->d_gen);
+    p->d_window = p->d_gen = nullptr;
     cudaFree(p->d_status);
     if (p->done)
         cudaEventDestroy(p->done);
@@ -724,8 +892,9 @@ size_t workspace_of(const sgf_plan *p)
     align_push(blob, p->work_main);
     align_push(blob, p->groups);
     align_push(blob, p->sums);
+    align_push(blob, p->work_stream);
     return blob.size() + p->partial_elems * 2 * p->esize + (p->fwd_elems + p->bwd_elems) * 2 * p->esize +
-           (size_t)p->restricted * p->N * p->N * p->esize;
+           (size_t)p->restricted * p->N * p->N * p->esize + (p->streamed ? gen_bytes_of(p->N) : 0);
 }
 
 // Tensor map of the level-0 patch's main column output (the first output, N
@@ -761,6 +930,8 @@ sgf_status encode_tmap_inv(sgf_plan *p)
     return SGF_OK;
 }
 
+void twiddles(int P, std::vector<double> &re, std::vector<double> &im);
+
 // Allocate the plan's own device memory and upload its lists.
 sgf_status plan_alloc_owned(sgf_plan *p)
 {
@@ -774,6 +945,7 @@ sgf_status plan_alloc_owned(sgf_plan *p)
     const size_t o_cmain = align_push(blob, p->work_main);
     const size_t o_grp = align_push(blob, p->groups);
     const size_t o_sum = align_push(blob, p->sums);
+    const size_t o_str = align_push(blob, p->work_stream);
     cudaError_t e;
     if ((e = cudaMalloc(&p->d_lists, blob.size())) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc(work lists)");
@@ -789,6 +961,23 @@ sgf_status plan_alloc_owned(sgf_plan *p)
     p->d_work_main = reinterpret_cast<const ColWork *>(base + o_cmain);
     p->d_groups = reinterpret_cast<const ColGroup *>(base + o_grp);
     p->d_sums = reinterpret_cast<const ColSum *>(base + o_sum);
+    p->d_work_stream = reinterpret_cast<const ColWork *>(base + o_str);
+    if (p->streamed) {  // the window of the streamed sets and the generator's workspace, for every solve
+        if ((e = cudaMalloc(&p->d_window, p->window_bytes)) != cudaSuccess)
+            return cuda_fail(e, "cudaMalloc(spectra window)");
+        p->gen_bytes = gen_bytes_of(p->N);
+        if ((e = cudaMalloc(&p->d_gen, p->gen_bytes)) != cudaSuccess)
+            return cuda_fail(e, "cudaMalloc(table generator workspace)");
+        std::vector<double> re, im;
+        twiddles(2 * p->N, re, im);
+        std::vector<double2> tw64(2 * p->N);
+        for (int k = 0; k < 2 * p->N; ++k)
+            tw64[k] = make_double2(re[k], im[k]);
+        if ((e = upload_landed(p->d_gen, tw64.data(), tw64.size() * sizeof(double2))) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpy(generator twiddles)");
+        if ((e = gen_kernels_init()) != cudaSuccess)
+            return cuda_fail(e, "table kernels init");
+    }
     const size_t Cb = 2 * p->esize;
     if (p->partial_elems && (e = cudaMalloc(&p->d_partial, p->partial_elems * Cb)) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc(chunk accumulators)");
@@ -889,7 +1078,7 @@ sgf_status build_spectra(sgf_plan *p)
         return cuda_fail(e, "cudaMalloc(twiddles)");
     if ((e = upload_landed(sp->tw, twT.data(), tl.entries * sizeof(C))) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpy(twiddles)");
-    sp->bytes = spectra_total(p);
+    sp->bytes = p->streamed ? p->resident_bytes : spectra_total(p);  // a streamed plan: its resident sets
     if ((e = cudaMalloc(&sp->dev, sp->bytes)) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc(kernel spectra)");
     double2 *d_tw64 = nullptr;
@@ -909,6 +1098,8 @@ sgf_status build_spectra(sgf_plan *p)
     if (st == SGF_OK && (e = cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking)) != cudaSuccess)
         st = cuda_fail(e, "cudaStreamCreate(table generation)");
     for (size_t k = 0; st == SGF_OK && k < p->sets.size(); ++k) {
+        if (p->streamed && p->set_wave[k] >= 0)
+            continue;  // regenerated at every solve
         if ((e = launch_gen_set<T>(p->sets[k], N, p->logN, d_tw64, sp->dev, d_tables, d_half, gs)) != cudaSuccess)
             st = cuda_fail(e, "kernel table generation launch");
     }
@@ -963,7 +1154,10 @@ cudaError_t launch_row_inv(int logN, int L, int R, SolveArgs<T> a, cudaStream_t 
 // Zero-rim column pass of the plan's schedule.
 inline int col_m_pass(const sgf_plan *p)
 {
-    return p->sched.col_pass == 1 ? PASS_COL_MD : p->sched.col_pass == 2 ? PASS_COL_MW : PASS_COL_M;
+    return p->sched.col_pass == 1   ? PASS_COL_MD
+           : p->sched.col_pass == 2 ? PASS_COL_MW
+           : p->sched.col_pass == 3 ? PASS_COL_MX
+                                    : PASS_COL_M;
 }
 
 // Column pass of a solve: zero-rim plans through k_col_m / k_col_md / k_col_mw;
@@ -974,6 +1168,35 @@ inline int col_m_pass(const sgf_plan *p)
 template <typename T>
 cudaError_t launch_col(const sgf_plan *p, const SolveArgs<T> &a, cudaStream_t st)
 {
+    if (p->streamed) {  // the resident pass, then per wave: regenerate its sets into the window, its pass
+        SolveArgs<T> b = a;
+        const int colp = p->sched.col_pass == 2 ? PASS_COL_W : PASS_COL;
+        const size_t P = 2 * (size_t)p->N;
+        unsigned char *gen = static_cast<unsigned char *>(p->d_gen);
+        const double2 *tw64 = reinterpret_cast<const double2 *>(gen);
+        double *tables = reinterpret_cast<double *>(gen + ((P * sizeof(double2) + 255) & ~(size_t)255));
+        double2 *half = reinterpret_cast<double2 *>(reinterpret_cast<unsigned char *>(tables) +
+                                                    ((6 * P * P * sizeof(double) + 255) & ~(size_t)255));
+        cudaError_t e = cudaSuccess;
+        for (int ph = 0; ph <= p->waves; ++ph) {
+            if (ph > 0) {
+                for (int k : p->wave_sets[ph - 1])
+                    if ((e = launch_gen_set<T>(p->sets[k], p->N, p->logN, tw64, p->d_window, tables, half, st)) !=
+                        cudaSuccess)
+                        return e;
+            }
+            b.spec = ph > 0 ? p->d_window : p->spec->dev;
+            const int beg = p->stream_begin[ph], cnt = p->stream_begin[ph + 1] - beg;
+            if (cnt == 0)
+                continue;
+            b.col_list = p->d_work_stream + beg;
+            if ((e = launch_pass_n<T>(colp, p->logN, b, cnt, st, nullptr, p->tc)) != cudaSuccess)
+                return e;
+        }
+        if (!p->sums.empty())
+            e = launch_pass_n<T>(PASS_COL_SUM, p->logN, a, (int)p->sums.size(), st, nullptr, p->tc);
+        return e;
+    }
     if (p->merged) {
         if (p->pot && p->sched.col_pass != 2)  // only k_col_mw reads the one-table potential spectra
             return cudaErrorInvalidValue;
@@ -999,7 +1222,10 @@ cudaError_t launch_col(const sgf_plan *p, const SolveArgs<T> &a, cudaStream_t st
 // for level 0) has no shared memory left for tensor-core tiles at n = 4096.
 inline bool schedule_ok(const sgf_plan *p, const sgf_schedule &s)
 {
-    if (s.col_pass < 0 || s.col_pass > 2 || s.row_inv0 < 0 || s.row_inv0 > 3 || (s.col_case3 != 0 && s.col_case3 != 1))
+    if (s.col_pass < 0 || s.col_pass > 3 || s.row_inv0 < 0 || s.row_inv0 > 3 || (s.col_case3 != 0 && s.col_case3 != 1))
+        return false;
+    // k_col_mx: zero-rim forces, FP32 without tensor-core tiles, N >= 1024
+    if (s.col_pass == 3 && !(p->merged && !p->pot && p->prec == SGF_FP32 && p->N >= 1024))
         return false;
     if (s.row_inv0 == 3 && !p->tma_inv)
         return false;
@@ -1301,7 +1527,7 @@ sgf_status batch_launches(sgf_batch *bt, cudaStream_t st)
             return cuda_fail(e, "batched row_fwd launch");
         const int colp = !g.merged              ? (g.sched.col_pass == 2 ? PASS_COL_W : PASS_COL)
                          : g.sched.col_pass == 1 ? PASS_COL_MD
-                         : g.sched.col_pass == 2 ? PASS_COL_MW
+                         : g.sched.col_pass >= 2 ? PASS_COL_MW  // k_col_mx has no batch form
                                                  : PASS_COL_M;
         if ((e = launch_pass_n<T>(colp, g.logN, dummy, g.n_col, st, &vc, g.tc)) != cudaSuccess)
             return cuda_fail(e, "batched col launch");
@@ -1538,7 +1764,7 @@ void tune_load_locked()
     char key[160];
     int a = 0, b = 0, c = 0;
     while (fscanf(f, "%159s %d %d %d", key, &a, &b, &c) == 4)
-        if (a >= 0 && a <= 2 && b >= 0 && b <= 3 && (c == 0 || c == 1))
+        if (a >= 0 && a <= 3 && b >= 0 && b <= 3 && (c == 0 || c == 1))
             g_tune[key] = sgf_schedule{a, b, c};
     fclose(f);
 }
@@ -1624,17 +1850,19 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[SGF_A
         ms[k] = -1.0;
     sgf_schedule best = p->sched;
     if (p->merged) {
-        static const int col_kind[3] = {PASS_COL_M, PASS_COL_MD, PASS_COL_MW};
-        for (int c = 0; c < 3 && s == SGF_OK; ++c) {
+        static const int col_kind[4] = {PASS_COL_M, PASS_COL_MD, PASS_COL_MW, PASS_COL_MX};
+        auto col_slot = [](int c) { return c < 3 ? c : 9; };  // col_pass = 3 appended after row_inv0 = 3
+        for (int c = 0; c < 4 && s == SGF_OK; ++c) {
             sgf_schedule cand = best;
             cand.col_pass = c;
             if (schedule_ok(p, cand))
-                s = timeit([&] { return launch_pass_n<T>(col_kind[c], p->logN, a, 1, st, nullptr, p->tc); }, ms[c]);
+                s = timeit([&] { return launch_pass_n<T>(col_kind[c], p->logN, a, 1, st, nullptr, p->tc); },
+                           ms[col_slot(c)]);
         }
         if (s == SGF_OK) {  // the fastest of the candidates that apply (and were timed)
             int bc = -1;
-            for (int c = 0; c < 3; ++c)
-                if (ms[c] >= 0.0 && (bc < 0 || ms[c] < ms[bc]))
+            for (int c = 0; c < 4; ++c)
+                if (ms[col_slot(c)] >= 0.0 && (bc < 0 || ms[col_slot(c)] < ms[col_slot(bc)]))
                     bc = c;
             if (bc >= 0)
                 best.col_pass = bc;
@@ -1655,7 +1883,7 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[SGF_A
         if (bc >= 0)
             best.row_inv0 = bc;
     }
-    if (!p->merged) {  // general column pass: a cluster per column or both halves in one CTA
+    if (!p->merged && !p->streamed) {  // general column pass: a cluster per column or both halves in one CTA
         const sgf_schedule keep = p->sched;
         for (int c = 0; c <= 2 && s == SGF_OK; c += 2) {
             sgf_schedule cand = keep;
@@ -1671,7 +1899,7 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[SGF_A
         if (s == SGF_OK && ms[0] >= 0.0)
             best.col_pass = ms[2] >= 0.0 && ms[2] < ms[0] ? 2 : 0;
     }
-    if (!p->merged && !p->groups.empty()) {  // Case-3 outputs grouped or one cluster each
+    if (!p->merged && !p->streamed && !p->groups.empty()) {  // Case-3 outputs grouped or one cluster each
         const sgf_schedule keep = p->sched;
         p->sched.col_pass = best.col_pass;
         for (int c = 0; c < 2 && s == SGF_OK; ++c) {
@@ -1733,10 +1961,12 @@ sgf_status prepare_kernels(const sgf_plan *p)
 }
 
 // A validated geometry's plan: lists, recorded schedule, spectra, workspace.
-sgf_status plan_create(const Forest &fo, sgf_precision precision, uint32_t flags, sgf_plan **out)
+sgf_status plan_create(const Forest &fo, sgf_precision precision, uint32_t flags, size_t spectra_budget,
+                       sgf_plan **out)
 {
     sgf_plan *p = new sgf_plan();
     plan_init(p, fo, precision, flags);
+    p->spectra_budget = spectra_budget;
     cudaError_t e = cudaGetDevice(&p->device);
     if (e != cudaSuccess) {
         delete p;
@@ -1748,6 +1978,9 @@ sgf_status plan_create(const Forest &fo, sgf_precision precision, uint32_t flags
                  SGF_MAX_N);
     if (s == SGF_OK) {
         build_lists(p);
+        s = plan_stream_layout(p);
+    }
+    if (s == SGF_OK) {
         tune_apply(p);
         s = precision == SGF_FP64 ? build_spectra<double>(p) : build_spectra<float>(p);
     }
@@ -1755,7 +1988,7 @@ sgf_status plan_create(const Forest &fo, sgf_precision precision, uint32_t flags
         s = plan_alloc_owned(p);
     if (s == SGF_OK)
         s = prepare_kernels(p);
-    if (s == SGF_OK && noalloc_bytes(p) <= (size_t)SGF_NOALLOC_SCRATCH_BYTES)
+    if (s == SGF_OK && !p->streamed && noalloc_bytes(p) <= (size_t)SGF_NOALLOC_SCRATCH_BYTES)
         s = noalloc_scratch_lookup(p);
     if (s != SGF_OK) {
         std::string msg = g_err;
@@ -1792,9 +2025,16 @@ const char *sgf_last_error(void) { return g_err.c_str(); }
 
 const char *sgf_version(void) { return "sgf 0.1.0 sm_103a"; }
 
-sgf_status sgf_plan_create(const sgf_nest_desc *desc, sgf_precision precision, sgf_plan **out)
+sgf_status sgf_plan_create(const sgf_nest_desc *desc, sgf_precision precision, size_t spectra_budget,
+                           sgf_plan **out)
 {
-    return sgf_plan_create_ex(desc, precision, 0u, out);
+    if (!desc || !out)
+        return fail(SGF_EINVAL, "NULL argument");
+    *out = nullptr;
+    sgf_status s = validate(desc, precision);
+    if (s != SGF_OK)
+        return s;
+    return plan_create(forest_of_nest(desc), precision, 0u, spectra_budget, out);
 }
 
 sgf_status sgf_plan_create_ex(const sgf_nest_desc *desc, sgf_precision precision, uint32_t flags,
@@ -1808,7 +2048,7 @@ sgf_status sgf_plan_create_ex(const sgf_nest_desc *desc, sgf_precision precision
         return s;
     if ((s = check_flags(desc->levels, flags)) != SGF_OK)
         return s;
-    return plan_create(forest_of_nest(desc), precision, flags, out);
+    return plan_create(forest_of_nest(desc), precision, flags, 0, out);
 }
 
 sgf_status sgf_plan_create_forest(const sgf_forest_desc *desc, sgf_precision precision, uint32_t flags,
@@ -1823,7 +2063,7 @@ sgf_status sgf_plan_create_forest(const sgf_forest_desc *desc, sgf_precision pre
         return s;
     if ((s = check_flags(fo.K, flags)) != SGF_OK)
         return s;
-    return plan_create(fo, precision, flags, out);
+    return plan_create(fo, precision, flags, 0, out);
 }
 
 sgf_status sgf_plan_estimate(const sgf_nest_desc *desc, sgf_precision precision, uint32_t flags,
@@ -1886,16 +2126,20 @@ sgf_status sgf_plan_share_ex(const sgf_plan *src, sgf_precision precision, sgf_p
         return fail(SGF_EUNSUPPORTED, "no kernel schedule applies to the shared plan (zero-rim potential with "
                                       "SGF_BF16X needs n < %d)", SGF_MAX_N);
     }
+    p->spectra_budget = src->spectra_budget;  // the same resident sets as src's spectra
     sgf_status s = build_cover(p);
     if (s == SGF_OK) {
         build_lists(p);
+        s = plan_stream_layout(p);
+    }
+    if (s == SGF_OK) {
         p->spec = src->spec;
         p->spec->refs++;
         s = plan_alloc_owned(p);
     }
     if (s == SGF_OK)
         s = prepare_kernels(p);
-    if (s == SGF_OK && noalloc_bytes(p) <= (size_t)SGF_NOALLOC_SCRATCH_BYTES)
+    if (s == SGF_OK && !p->streamed && noalloc_bytes(p) <= (size_t)SGF_NOALLOC_SCRATCH_BYTES)
         s = noalloc_scratch_lookup(p);
     if (s != SGF_OK) {
         std::string msg = g_err;
@@ -1923,10 +2167,33 @@ sgf_status sgf_plan_stats_get(const sgf_plan *p, sgf_plan_stats *st)
     st->launches_per_solve = p->restricted + 3 + (p->L > p->fo.R && p->sched.row_inv0 != 1 ? 1 : 0) +
                              (!p->groups.empty() && p->sched.col_case3 == 0 ? 1 : 0) +  // + k_col_g
                              (p->sums.empty() ? 0 : 1);                                  // + k_col_sum
+    if (p->streamed) {  // column passes: one per non-empty pass; three generator kernels per streamed set
+        int passes = 0, streamed_sets = 0;
+        for (int ph = 0; ph <= p->waves; ++ph)
+            passes += p->stream_begin[ph + 1] > p->stream_begin[ph] ? 1 : 0;
+        for (const auto &w : p->wave_sets)
+            streamed_sets += (int)w.size();
+        st->launches_per_solve += passes - 1 + 3 * streamed_sets;
+    }
     st->workspace_bytes = p->workspace_bytes;
     st->spectra_bytes = p->spec ? p->spec->bytes : 0;
     st->algorithmic_bytes = p->algorithmic_bytes;
     st->plan_ms = p->spec ? p->spec->plan_ms : 0.0;
+    int streamed_sets = 0;
+    for (const auto &w : p->wave_sets)
+        streamed_sets += (int)w.size();
+    st->spectra_sets_streamed = p->streamed ? streamed_sets : 0;
+    st->spectra_waves = p->streamed ? p->waves : 0;
+    st->spectra_window_bytes = p->streamed ? p->window_bytes : 0;
+    return SGF_OK;
+}
+
+sgf_status sgf_plan_footprint(const sgf_plan *p, size_t *workspace_bytes, size_t *spectra_bytes)
+{
+    if (!p || !workspace_bytes || !spectra_bytes)
+        return fail(SGF_EINVAL, "NULL argument");
+    *workspace_bytes = p->workspace_bytes;
+    *spectra_bytes = (p->spec ? p->spec->bytes : 0) + (p->streamed ? p->window_bytes : 0);
     return SGF_OK;
 }
 
@@ -2105,15 +2372,15 @@ sgf_status sgf_plan_schedule_set(sgf_plan *p, const sgf_schedule *in)
 {
     if (!p || !in)
         return fail(SGF_EINVAL, "NULL argument");
-    if (in->col_pass < 0 || in->col_pass > 2 || in->row_inv0 < 0 || in->row_inv0 > 3 ||
+    if (in->col_pass < 0 || in->col_pass > 3 || in->row_inv0 < 0 || in->row_inv0 > 3 ||
         (in->col_case3 != 0 && in->col_case3 != 1))
         return fail(SGF_EINVAL, "schedule out of range (col_pass %d, row_inv0 %d, col_case3 %d)", in->col_pass,
                     in->row_inv0, in->col_case3);
     if (!schedule_ok(p, *in))
         return fail(SGF_EUNSUPPORTED,
                     "schedule (col_pass %d, row_inv0 %d) not available for this plan: col_pass = 2 and row_inv0 = 1 "
-                    "need n < %d with SGF_BF16X, row_inv0 = 2 a force plan, row_inv0 = 3 SGF_FP32 with n >= 512 and "
-                    "one level-0 patch",
+                    "need n < %d with SGF_BF16X, col_pass = 3 a zero-rim SGF_FP32 force plan with n >= 1024, "
+                    "row_inv0 = 2 a force plan, row_inv0 = 3 SGF_FP32 with n >= 512 and one level-0 patch",
                     in->col_pass, in->row_inv0, SGF_MAX_N);
     p->sched = *in;
     return SGF_OK;
@@ -2160,6 +2427,9 @@ sgf_status sgf_solve_noalloc(sgf_plan *p, const void *const *sigma, void *const 
     sgf_status s = check_ptrs(p, sigma, fx, fy);
     if (s != SGF_OK)
         return s;
+    if (p->streamed)
+        return fail(SGF_EUNSUPPORTED, "sgf_solve_noalloc: the plan regenerates spectra at every solve "
+                                      "(spectra budget); its window belongs to the plan");
     const size_t need = noalloc_bytes(p);
     if (need > (size_t)SGF_NOALLOC_SCRATCH_BYTES)
         return fail(SGF_EUNSUPPORTED,
@@ -2188,6 +2458,9 @@ sgf_status sgf_batch_create(sgf_plan *const *plans, int32_t count, uint32_t flag
             return fail(SGF_EINVAL, "plan %d is NULL", k);
         if (plans[k]->pot)
             return fail(SGF_EUNSUPPORTED, "plan %d: batches solve forces, not SGF_PLAN_POTENTIAL plans", k);
+        if (plans[k]->streamed)
+            return fail(SGF_EUNSUPPORTED, "plan %d regenerates spectra at every solve (spectra budget); "
+                                          "batches take plans with resident spectra", k);
         if (plans[k]->prec != plans[0]->prec || plans[k]->device != plans[0]->device)
             return fail(SGF_EINVAL, "plans of one batch must share precision and device");
         for (int q = 0; q < k; ++q)

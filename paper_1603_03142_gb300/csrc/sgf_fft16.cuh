@@ -510,4 +510,105 @@ __device__ __forceinline__ void fft_ct(C (*v)[16], C *sbuf, int SP, int j, bool 
 }
 #endif
 
+// ---------------------------------------------------------------------------
+// Register-twiddle engine.  A thread that keeps one slot j for the whole life
+// of a kernel (a CTA walking many columns) holds the twiddles of its slot in
+// registers instead of reading the shared tables at every stage: stage st >= 1
+// needs W_{R Ns}^{r k} for r = 1..R-1 with k = (j + QB N/16) mod Ns for each of
+// its 16/R butterflies QB, at most 15 values.  They are the same numbers the
+// table engine forms (stage_tw: the factored product for Ns >= 256 included),
+// so both engines compute bit-identical transforms.
+template <typename C, int LOGN, int ST>
+__device__ __forceinline__ void load_stage_twiddles(C (&w)[15], const C *tw, int j)
+{
+    using P = F16<LOGN>;
+    constexpr int R = P::radix(ST), NS = P::ns(ST), S = 16 / R;
+    const C *tws = tw + P::twoff(ST);
+#pragma unroll
+    for (int qb = 0; qb < S; ++qb) {
+        const int k = (j + qb * P::Q) & (NS - 1);
+#pragma unroll
+        for (int r = 1; r < R; ++r)
+            w[qb * (R - 1) + r - 1] = stage_tw<C, R, NS>(tws, r, k);
+    }
+}
+
+// Twiddles of every stage after the first: w[st - 1] for st = 1 .. NST - 1.
+template <typename C, int LOGN, int ST = 1>
+__device__ __forceinline__ void load_twiddles_rt(C (*w)[15], const C *tw, int j)
+{
+    if constexpr (ST < F16<LOGN>::NST) {
+        load_stage_twiddles<C, LOGN, ST>(w[ST - 1], tw, j);
+        load_twiddles_rt<C, LOGN, ST + 1>(w, tw, j);
+    }
+}
+
+template <typename C, bool INV, int R, int QB>
+SGF_HD void stage_small_rt(C *v, const C *w)
+{
+    if constexpr (QB < 16 / R) {
+        constexpr int S = 16 / R;
+#pragma unroll
+        for (int r = 1; r < R; ++r)
+            v[QB + r * S] = INV ? hmulc(v[QB + r * S], w[QB * (R - 1) + r - 1]) : hmul(v[QB + r * S], w[QB * (R - 1) + r - 1]);
+        hdft_small<C, INV, R, QB>(v);
+        stage_small_rt<C, INV, R, QB + 1>(v, w);
+    }
+}
+
+#ifdef __CUDACC__
+// Barrier of a group of `count` threads (a multiple of 32) on named barrier `id`.
+__device__ __forceinline__ void group_sync(unsigned id, unsigned count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// fft_stages with the stage twiddles in registers (w, see load_twiddles_rt)
+// and the exchanges of a group of threads on its own named barrier.  B
+// sequences per thread, sequence b at sbuf + b * SP; same entry and exit
+// conditions as fft_stages (sbuf first written after a barrier, last stage read
+// without a closing one).
+template <typename C, bool INV, int LOGN, int B, int ST>
+__device__ __forceinline__ void fft_stages_rt(C (*v)[16], C *sbuf, int SP, int j, const C (*w)[15], unsigned bar,
+                                              unsigned count)
+{
+    using P = F16<LOGN>;
+    if constexpr (ST < P::NST) {
+        constexpr int Q = P::Q, NS = P::ns(ST), R = P::radix(ST);
+        if constexpr (ST > 0) {
+            group_sync(bar, count);  // previous stage's stores are visible
+#pragma unroll
+            for (int bb = 0; bb < B; ++bb)
+#pragma unroll
+                for (int u = 0; u < 16; ++u)
+                    v[bb][u] = sbuf[bb * SP + pad16(j + u * Q)];
+        }
+#pragma unroll
+        for (int bb = 0; bb < B; ++bb) {
+            if constexpr (R == 16) {
+                if constexpr (ST > 0) {
+#pragma unroll
+                    for (int r = 1; r < 16; ++r)
+                        v[bb][r] = INV ? hmulc(v[bb][r], w[ST - 1][r - 1]) : hmul(v[bb][r], w[ST - 1][r - 1]);
+                }
+                hdft16<C, INV>(v[bb]);
+            } else {
+                stage_small_rt<C, INV, R, 0>(v[bb], w[ST - 1]);
+            }
+        }
+        if constexpr (ST + 1 < P::NST) {
+            group_sync(bar, count);  // every thread has read this stage's inputs
+            const int k = j & (NS - 1);
+            const int base = (j - k) * 16 + k;
+#pragma unroll
+            for (int bb = 0; bb < B; ++bb)
+#pragma unroll
+                for (int r = 0; r < 16; ++r)
+                    sbuf[bb * SP + pad16(base + r * NS)] = v[bb][r];
+        }
+        fft_stages_rt<C, INV, LOGN, B, ST + 1>(v, sbuf, SP, j, w, bar, count);
+    }
+}
+#endif
+
 }  // namespace sgf

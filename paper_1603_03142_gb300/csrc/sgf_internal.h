@@ -253,7 +253,8 @@ enum : int {
     PASS_COL_MW = 11,
     PASS_ROW_INV1T = 12,  // PASS_ROW_INV1 with the gather by the tensor memory accelerator (one patch, FP32)
     PASS_COL_W = 13,      // PASS_COL with both parity halves in one CTA (no tensor-core tiles, N >= 512)
-    PASS_COL_GW = 14      // PASS_COL_G likewise (FP32, 512 <= N <= 2048)
+    PASS_COL_GW = 14,     // PASS_COL_G likewise (FP32, 512 <= N <= 2048)
+    PASS_COL_MX = 15      // zero-rim forces: both parity halves per thread, register twiddles (FP32, N >= 1024)
 };
 // Batch mode of the transform passes: a block's nest and its local work index
 // come from a per-launch map (one int2 per block row), and that nest's

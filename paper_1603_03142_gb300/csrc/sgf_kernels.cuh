@@ -1837,6 +1837,134 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 1) k_col_mw(SolveAr
         tc_end(tcx, TCT);
 }
 
+// ------------------------------------------------------------------- col_mx
+// Zero-rim column pass (forces) with one thread per slot j carrying BOTH
+// parity halves of its column: the two forward transforms (x and x W_P^n) run
+// as two sequences of one thread, the spectral products of a bin's even and
+// odd halves stay in that thread, and the fold y[n] = even[n] + W_P^{-n}
+// odd[n] of the inverse transforms is done in registers, so no fold goes
+// through shared memory.  The thread keeps its slot for the whole launch (the
+// CTA walks the columns), so the twiddles of its slot live in registers
+// (load_twiddles_rt) and only the exchanges between stages use shared memory.
+// Fy^ waits in registers (or, PARK, in shared memory in slot order) while Fx^
+// is transformed back.  The N + 1 columns are shared among G = 256 / (N/16)
+// groups of N/16 threads per CTA (one group at N = 4096), each group walking
+// its own columns on its own named barrier, with the next column's input and
+// spectrum half rows copied in behind the inverse transforms.  FP32, no
+// tensor-core tiles, N >= 1024.
+// Shared memory per group: column[N] | Gx, Gy half rows of both halves |
+// exchange buffers [2][SPC] | (PARK) Fy^ [2][N].
+// Fy^ parked in shared memory (true) or kept in registers (false).
+constexpr bool kMxPark = true;
+
+template <int LOGN, bool PARK>
+struct KMx {
+    static constexpr int N = 1 << LOGN, Q = N >> 4;
+    static constexpr int G = Q >= 256 ? 1 : 256 / Q;
+    static constexpr int THREADS = G * Q;
+    static constexpr int SPC = col_sp<float2>(N);
+    static constexpr size_t GROUP_BYTES = (size_t)N * 8 + 4 * (size_t)quarter_half(N) * 4 + 2 * (size_t)SPC * 8 +
+                                          (PARK ? 2 * (size_t)N * 8 : 0);
+    static constexpr size_t SMEM = G * GROUP_BYTES;
+};
+
+template <int LOGN, bool PARK>
+__global__ void __launch_bounds__(KMx<LOGN, PARK>::THREADS, 1) k_col_mx(SolveArgs<float> a)
+{
+    using C = float2;
+    using M = KMx<LOGN, PARK>;
+    using P = F16<LOGN>;
+    constexpr int N = M::N, Q = M::Q, G = M::G, HQ = quarter_half(N), QS = quarter_stride(N), SPC = M::SPC;
+    static_assert(Q >= 64, "named group barriers need whole warps");
+    extern __shared__ __align__(16) unsigned char smem_mx[];
+    const int t = threadIdx.x;
+    const int g = t / Q, j = t - g * Q;
+    unsigned char *gbase = smem_mx + (size_t)g * M::GROUP_BYTES;
+    C *col = reinterpret_cast<C *>(gbase);
+    float *gsp = reinterpret_cast<float *>(col + N);  // [half][Gx, Gy][HQ]
+    C *xb = reinterpret_cast<C *>(gbase + (size_t)N * 8 + 4 * (size_t)HQ * 4);
+    C *park = xb + 2 * SPC;
+    const unsigned bar = 1 + g;
+    C trw[P::NST - 1][15];
+    load_twiddles_rt<C, LOGN>(trw, a.tw, j);
+    const TwLayout tl = tw_layout(P::twlen, N);
+    const C wj = a.tw[tl.base + j];  // W_P^j
+    auto twist_u = [&](int u) { return hmul(wj, hmk<C>((float)kW32c[u], (float)-kW32s[u])); };
+    const float *spec = reinterpret_cast<const float *>(a.spec);
+    auto stage = [&](int kx) {  // this group's threads: column kx and its four spectrum half rows
+        const char *src = reinterpret_cast<const char *>(a.fwd + (size_t)kx * N);
+        for (int o = j * 16; o < N * 8; o += Q * 16)
+            cp16(reinterpret_cast<char *>(col) + o, src + o);
+        for (int h = 0; h < 4; ++h) {  // [half][table]: Gx rows at kx, Gy rows at N + 1 + kx
+            const float *row = spec + ((size_t)(h & 1) * (N + 1) + kx) * QS + (h >> 1) * HQ;
+            for (int o = j * 16; o < HQ * 4; o += Q * 16)
+                cp16(reinterpret_cast<char *>(gsp + h * HQ) + o, reinterpret_cast<const char *>(row) + o);
+        }
+        cp_commit();
+    };
+    const int step = (int)gridDim.x * G;
+    int kx = (int)blockIdx.x * G + g;
+    if (kx <= N)
+        stage(kx);
+    for (; kx <= N; kx += step) {  // uniform over the group
+        cp_wait<0>();
+        group_sync(bar, Q);  // column kx staged; the previous column's exchanges are done
+        C v[2][16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const C x = col[j + u * Q];
+            v[0][u] = x;
+            v[1][u] = hmul(x, twist_u(u));
+        }
+        fft_stages_rt<C, false, LOGN, 2, 0>(v, xb, SPC, j, trw, bar, Q);
+        C fy[PARK ? 1 : 2][16];
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const float *gx_r = gsp + (2 * b) * HQ, *gy_r = gsp + (2 * b + 1) * HQ;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int kp = j + u * Q;
+                const bool hi = 2 * kp + b > N;
+                const int q = hi ? N - kp - b : kp;
+                const float gx = gx_r[q];                  // Gx even in ky
+                const float gy = hi ? -gy_r[q] : gy_r[q];  // Gy odd in ky
+                const C y = hmk<C>(-gy * v[b][u].y, gy * v[b][u].x);  // i gy v
+                if constexpr (PARK)
+                    park[b * N + kp] = y;
+                else
+                    fy[b][u] = y;
+                v[b][u] = hmk<C>(-gx * v[b][u].y, gx * v[b][u].x);  // i gx v
+            }
+        }
+        if (kx + step <= N) {  // uniform over the group
+            group_sync(bar, Q);  // every thread of the group is done with the column and the half rows
+            stage(kx + step);
+        }
+        C *dst = a.bwd;
+        fft_stages_rt<C, true, LOGN, 2, 0>(v, xb, SPC, j, trw, bar, Q);
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+            dst[bwd_index(N, N, 0, kx, j + u * Q)] = hadd(v[0][u], hmulc(v[1][u], twist_u(u)));
+        if constexpr (PARK) {  // this thread's own values: no barrier
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int u = 0; u < 16; ++u)
+                    v[b][u] = park[b * N + j + u * Q];
+            fft_stages_rt<C, true, LOGN, 2, 0>(v, xb, SPC, j, trw, bar, Q);
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+                dst[bwd_index(N, N, 1, kx, j + u * Q)] = hadd(v[0][u], hmulc(v[1][u], twist_u(u)));
+        } else {
+            fft_stages_rt<C, true, LOGN, 2, 0>(fy, xb, SPC, j, trw, bar, Q);
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+                dst[bwd_index(N, N, 1, kx, j + u * Q)] = hadd(fy[0][u], hmulc(fy[1][u], twist_u(u)));
+        }
+    }
+    cp_wait<0>();  // nothing in flight at exit
+}
+
 // ---------------------------------------------------------------- launching
 // Dynamic shared memory per kernel; TC adds the tensor-core area in front.
 template <typename T, int LOGN, bool TC = false>
@@ -1978,7 +2106,8 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
 {
     using K = KShape<LOGN>;
     using S = KSmem<T, LOGN, TC>;
-    static std::atomic<unsigned long long> d[28];
+    static std::atomic<unsigned long long> d[29];
+    static std::atomic<int> res_mx[64];               // resident CTAs of the register-twiddle column pass
     static std::atomic<int> res_mw[64], res_mw1[64];  // resident CTAs of the walking column pass (NC = 2, 1)
     static std::atomic<int> res_fm[64];               // and of the walking zero-rim forward row pass
     static std::atomic<int> res_ri1[64], res_ri2[64]; // and of the walking inverse row passes (tensor cores)
@@ -2056,6 +2185,12 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
                  ((e = ensure_smem(k_col_gw<T, LOGN, false>, S::col_gw(), d[26])) != cudaSuccess ||
                   (e = ensure_smem(k_col_gw<T, LOGN, true>, S::col_gw(), d[27])) != cudaSuccess)) ||
                 (e = ensure_smem(k_row_inv1t<T, LOGN>, S::row_inv1t(), d[22])) != cudaSuccess)
+                return e;
+        }
+        if constexpr (!TC && sizeof(T) == 4 && LOGN >= 10) {
+            using MX = KMx<LOGN, kMxPark>;
+            if ((e = ensure_smem(k_col_mx<LOGN, kMxPark>, MX::SMEM, d[28])) != cudaSuccess ||
+                (e = resident_ctas(k_col_mx<LOGN, kMxPark>, MX::THREADS, MX::SMEM, res_mx, &grid)) != cudaSuccess)
                 return e;
         }
         return cudaSuccess;
@@ -2197,6 +2332,22 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
             if ((e = ensure_smem(k_row_inv1t<T, LOGN>, S::row_inv1t(), d[22])) != cudaSuccess)
                 return e;
             k_row_inv1t<T, LOGN><<<dim3(a.ncomp * (K::N / 2), count), K::ROW_THREADS, S::row_inv1t(), st>>>(a);
+        } else {
+            return cudaErrorInvalidValue;
+        }
+        break;
+    }
+    case PASS_COL_MX: {
+        if constexpr (!TC && sizeof(T) == 4 && LOGN >= 10) {
+            if (batch)
+                return cudaErrorInvalidValue;
+            using MX = KMx<LOGN, kMxPark>;
+            int grid = 0;
+            if ((e = ensure_smem(k_col_mx<LOGN, kMxPark>, MX::SMEM, d[28])) != cudaSuccess ||
+                (e = resident_ctas(k_col_mx<LOGN, kMxPark>, MX::THREADS, MX::SMEM, res_mx, &grid)) != cudaSuccess)
+                return e;
+            const int groups = (K::N + 1 + MX::G - 1) / MX::G;  // CTAs that give every group a column
+            k_col_mx<LOGN, kMxPark><<<grid < groups ? grid : groups, MX::THREADS, MX::SMEM, st>>>(a);
         } else {
             return cudaErrorInvalidValue;
         }

@@ -35,6 +35,7 @@ struct Pending {
     std::string key;   // slot key: spectra key + precision
     std::string skey;  // spectra key
     size_t ws = 0, spectra = 0, build = 0, io = 0;  // bytes (sgf_plan_estimate; io = 3 L n^2 elements)
+    size_t stream_budget = 0;  // SGF_SERVER_STREAM: the spectra budget of this shape's plans, else 0
     double t_submit = 0;
 };
 
@@ -204,7 +205,8 @@ sgf_status slot_create(sgf_server *sv, const Pending &p, Slot **out)
             rc = tmpl ? sgf_plan_share_ex(tmpl, p.r.precision, &s->plan)
                       : fail(SGF_EINVAL, "resident shape without a slot");
         } else if (rc == SGF_OK) {
-            rc = sgf_plan_create_ex(&p.r.desc, p.r.precision, p.r.plan_flags, &s->plan);
+            rc = p.stream_budget ? sgf_plan_create(&p.r.desc, p.r.precision, p.stream_budget, &s->plan)
+                                 : sgf_plan_create_ex(&p.r.desc, p.r.precision, p.r.plan_flags, &s->plan);
         }
         // the kernel schedule of this slot key: tuned once per server (on the slot's own
         // stream, while the other slots keep running), then reused
@@ -304,7 +306,7 @@ sgf_status sgf_server_create(const sgf_server_config *config, sgf_server **out)
     *out = nullptr;
     if (config->max_inflight < 1)
         return fail(SGF_EINVAL, "max_inflight = %d must be >= 1", config->max_inflight);
-    if (config->flags & ~(SGF_SERVER_SIMULATE | SGF_SERVER_NO_AUTOTUNE))
+    if (config->flags & ~(SGF_SERVER_SIMULATE | SGF_SERVER_NO_AUTOTUNE | SGF_SERVER_STREAM))
         return fail(SGF_EINVAL, "unknown server flags 0x%x", config->flags);
     const bool sim = (config->flags & SGF_SERVER_SIMULATE) != 0;
     if (sim && !(config->simulate_gbs > 0.0))
@@ -352,6 +354,19 @@ sgf_status sgf_server_submit(sgf_server *sv, const sgf_request *r)
     p.io = 3 * (size_t)L * align256(lvl);
     p.skey = spectra_key(*r);
     p.key = p.skey + "/p" + std::to_string((int)r->precision);
+    if (sv->cfg.max_shape_bytes && p.spectra + p.build > sv->cfg.max_shape_bytes &&
+        (sv->cfg.flags & SGF_SERVER_STREAM) && r->plan_flags == 0 && p.build < sv->cfg.max_shape_bytes) {
+        // served by plans over a spectra budget: resident sets and a window within the budget,
+        // the generator's workspace kept by every slot's plan
+        const size_t esz = r->precision == SGF_FP64 ? 8 : 4;
+        const size_t one_set = 6 * (size_t)(r->desc.n + 1) * 2 * r->desc.n * 2 * esz;
+        const size_t budget = sv->cfg.max_shape_bytes - p.build;
+        if (budget >= one_set) {
+            p.stream_budget = budget;
+            p.ws += p.build + budget;  // generator workspace and (at most) the window, per slot
+            p.spectra = budget;        // the resident sets, at most the budget
+        }
+    }
     const size_t worst = p.ws + p.io + p.spectra + p.build;
     if (sv->cfg.max_shape_bytes && p.spectra + p.build > sv->cfg.max_shape_bytes) {
         sv->st.rejected++;

@@ -33,12 +33,13 @@ EXPORTS = ["sgf_plan_create", "sgf_plan_create_ex", "sgf_plan_check", "sgf_plan_
            "sgf_batch_solve", "sgf_batch_info", "sgf_batch_destroy", "sgf_plan_estimate", "sgf_server_create",
            "sgf_server_clock", "sgf_server_submit", "sgf_server_progress", "sgf_server_stats_get",
            "sgf_server_destroy", "sgf_plan_schedule_get", "sgf_plan_schedule_set", "sgf_plan_autotune",
-           "sgf_plan_share_ex", "sgf_solve_potential", "sgf_plan_create_forest", "sgf_plan_estimate_forest"]
+           "sgf_plan_share_ex", "sgf_solve_potential", "sgf_plan_create_forest", "sgf_plan_estimate_forest",
+           "sgf_plan_footprint"]
 BATCH_NO_GRAPH = 0x1
 PLAN_ZERO_RIM = 0x1
 PLAN_POTENTIAL = 0x2
 NOALLOC_SCRATCH_BYTES = 32 << 20
-AUTOTUNE_TIMES = 9
+AUTOTUNE_TIMES = 10
 KERNELS = ["restrict", "row_fwd", "col", "row_inv"]
 
 
@@ -60,7 +61,9 @@ class PlanStats(ctypes.Structure):
                 ("forward_slabs", ctypes.c_int32), ("outputs", ctypes.c_int32),
                 ("spectra_sets", ctypes.c_int32), ("launches_per_solve", ctypes.c_int32),
                 ("workspace_bytes", ctypes.c_size_t), ("spectra_bytes", ctypes.c_size_t),
-                ("algorithmic_bytes", ctypes.c_size_t), ("plan_ms", ctypes.c_double)]
+                ("algorithmic_bytes", ctypes.c_size_t), ("plan_ms", ctypes.c_double),
+                ("spectra_sets_streamed", ctypes.c_int32), ("spectra_waves", ctypes.c_int32),
+                ("spectra_window_bytes", ctypes.c_size_t)]
 
 
 class KernelTimes(ctypes.Structure):
@@ -98,9 +101,12 @@ class Schedule(ctypes.Structure):
 
 SERVER_SIMULATE = 0x1
 SERVER_NO_AUTOTUNE = 0x2
+SERVER_STREAM = 0x4
 _vpp = ctypes.POINTER(ctypes.c_void_p)
 _szp = ctypes.POINTER(ctypes.c_size_t)
-_lib.sgf_plan_create.argtypes = [ctypes.POINTER(NestDesc), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+_lib.sgf_plan_create.argtypes = [ctypes.POINTER(NestDesc), ctypes.c_int, ctypes.c_size_t,
+                                 ctypes.POINTER(ctypes.c_void_p)]
+_lib.sgf_plan_footprint.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
 _lib.sgf_plan_create_ex.argtypes = [ctypes.POINTER(NestDesc), ctypes.c_int, ctypes.c_uint32,
                                     ctypes.POINTER(ctypes.c_void_p)]
 _lib.sgf_plan_check.argtypes = [ctypes.c_void_p]
@@ -148,7 +154,7 @@ for _f in ("sgf_plan_create", "sgf_plan_create_ex", "sgf_plan_check", "sgf_plan_
            "sgf_plan_estimate", "sgf_server_create", "sgf_server_submit", "sgf_server_progress",
            "sgf_server_stats_get", "sgf_server_destroy", "sgf_plan_schedule_get", "sgf_plan_schedule_set",
            "sgf_plan_autotune", "sgf_plan_share_ex", "sgf_solve_potential", "sgf_plan_create_forest",
-           "sgf_plan_estimate_forest"):
+           "sgf_plan_estimate_forest", "sgf_plan_footprint"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -218,7 +224,8 @@ def _stream_handle(stream) -> int:
 class Plan:
     """A solve plan: nest geometry + precision, resident kernel spectra, workspace."""
 
-    def __init__(self, nest, precision="fp32", zero_rim: bool = False, potential: bool = False, _handle=None):
+    def __init__(self, nest, precision="fp32", zero_rim: bool = False, potential: bool = False, _handle=None,
+                 spectra_budget: int = 0):
         self.nest = nest
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.n, self.levels = int(nest.n), int(nest.levels)
@@ -229,7 +236,12 @@ class Plan:
             return
         h = ctypes.c_void_p()
         flags = (PLAN_ZERO_RIM if zero_rim else 0) | (PLAN_POTENTIAL if potential else 0)
-        if is_forest(nest):  # per-patch arrays stand where a nest has per-level ones
+        if spectra_budget:  # sgf_plan_create: nests, force plans (spectra over the budget regenerated per solve)
+            if is_forest(nest) or flags:
+                raise ValueError("a spectra budget takes a nest force plan without options")
+            _check(_lib.sgf_plan_create(ctypes.byref(make_desc(nest)), self.precision, int(spectra_budget),
+                                        ctypes.byref(h)), "sgf_plan_create")
+        elif is_forest(nest):  # per-patch arrays stand where a nest has per-level ones
             _check(_lib.sgf_plan_create_forest(ctypes.byref(make_forest_desc(nest)), self.precision, flags,
                                                ctypes.byref(h)), "sgf_plan_create_forest")
         else:
@@ -269,6 +281,12 @@ class Plan:
         _check(_lib.sgf_plan_stats_get(self._h, ctypes.byref(st)), "sgf_plan_stats_get")
         return {name: getattr(st, name) for name, _ in PlanStats._fields_}
 
+    def footprint(self) -> dict:
+        """sgf_plan_footprint: device bytes of the plan's workspace and of its spectra."""
+        ws, sp = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(_lib.sgf_plan_footprint(self._h, ctypes.byref(ws), ctypes.byref(sp)), "sgf_plan_footprint")
+        return {"workspace_bytes": ws.value, "spectra_bytes": sp.value}
+
     def solve_noalloc_ptrs(self, sigma_ptrs, fx_ptrs, fy_ptrs, stream=None):
         """sgf_solve_noalloc: the solve with the library's fixed scratch array (no allocation)."""
         _check(_lib.sgf_solve_noalloc(self._h, _ptrs(sigma_ptrs), _ptrs(fx_ptrs), _ptrs(fy_ptrs),
@@ -292,7 +310,7 @@ class Plan:
         return {"chosen": {"col_pass": sc.col_pass, "row_inv0": sc.row_inv0, "col_case3": sc.col_case3},
                 "ms": {"col_pass0": ms[0], "col_pass1": ms[1], "col_pass2": ms[2], "row_inv0_0": ms[3],
                        "row_inv0_1": ms[4], "row_inv0_2": ms[5], "col_case3_0": ms[6], "col_case3_1": ms[7],
-                       "row_inv0_3": ms[8]}}
+                       "row_inv0_3": ms[8], "col_pass3": ms[9]}}
 
     def profile(self, enable: bool = True):
         _check(_lib.sgf_plan_profile(self._h, 1 if enable else 0), "sgf_plan_profile")
@@ -467,12 +485,13 @@ class Server:
     """
 
     def __init__(self, hbm_budget: int = 0, max_inflight: int = 4, simulate_gbs: Optional[float] = None,
-                 max_shape_bytes: int = 0, autotune: bool = True):
+                 max_shape_bytes: int = 0, autotune: bool = True, stream_large: bool = False):
         cfg = ServerConfig()
         cfg.hbm_budget = int(hbm_budget)
         cfg.max_shape_bytes = int(max_shape_bytes)
         cfg.max_inflight = int(max_inflight)
-        cfg.flags = (SERVER_SIMULATE if simulate_gbs is not None else 0) | (0 if autotune else SERVER_NO_AUTOTUNE)
+        cfg.flags = ((SERVER_SIMULATE if simulate_gbs is not None else 0) | (0 if autotune else SERVER_NO_AUTOTUNE) |
+                     (SERVER_STREAM if stream_large else 0))
         cfg.simulate_gbs = float(simulate_gbs or 0.0)
         h = ctypes.c_void_p()
         _check(_lib.sgf_server_create(ctypes.byref(cfg), ctypes.byref(h)), "sgf_server_create")

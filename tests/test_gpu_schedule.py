@@ -47,7 +47,12 @@ def test_schedules_agree_zero_rim(lib, prec, n):
         with pytest.raises(lib.SgfError) as ei:
             plan.set_schedule(0, 3)
         assert ei.value.status == lib.SGF_EUNSUPPORTED
-    for col in (0, 1, 2):
+    mx = prec == "fp32" and n >= 1024  # col_pass = 3: k_col_mx (both halves per thread, register twiddles)
+    if not mx:
+        with pytest.raises(lib.SgfError) as ei:
+            plan.set_schedule(3, 0)
+        assert ei.value.status == lib.SGF_EUNSUPPORTED
+    for col in (0, 1, 2, 3) if mx else (0, 1, 2):
         for inv in (0, 1, 2, 3) if tma else (0, 1, 2):
             plan.set_schedule(col, inv)
             assert plan.schedule() == {"col_pass": col, "row_inv0": inv, "col_case3": 0}
@@ -137,7 +142,8 @@ print(json.dumps({"r": r, "q": q.schedule()}))
     ms = d["r"]["ms"]
     assert all(ms[k] > 0 for k in ("col_pass0", "col_pass1", "col_pass2", "row_inv0_0", "row_inv0_1", "row_inv0_2"))
     ch = d["r"]["chosen"]
-    cp = [ms["col_pass0"], ms["col_pass1"], ms["col_pass2"]]
+    assert ms["col_pass3"] > 0  # FP32 zero-rim force plan, n = 1024
+    cp = [ms["col_pass0"], ms["col_pass1"], ms["col_pass2"], ms["col_pass3"]]
     assert ch["col_pass"] == cp.index(min(cp))
     assert ms["row_inv0_3"] > 0  # FP32, n = 1024, one level-0 patch
     inv = [ms["row_inv0_0"], ms["row_inv0_1"], ms["row_inv0_2"], ms["row_inv0_3"]]
