@@ -59,3 +59,62 @@ def test_batch_rejects_duplicates(lib):
     p = lib.Plan(W.Nest(n=16), "fp32")
     with pytest.raises(lib.SgfError):
         lib.Batch([p, p])
+
+
+def _c4_subset():
+    """The first nest of every (N, levels) of the seeded 256-nest batched workload
+    (N in {128, 256, 512, 1024}, 1-4 levels): 16 nests."""
+    rng = np.random.Generator(np.random.PCG64(0))  # the draws of W.config4(seed=0), in order
+    seen, out = set(), []
+    for _ in range(256):
+        n = int(rng.choice((128, 256, 512, 1024)))
+        L = int(rng.integers(1, 5))
+        nest, sigma = W.random_nest_problem(rng, n, L)
+        if (n, L) not in seen:
+            seen.add((n, L))
+            out.append((nest, sigma))
+        if len(out) == 16:
+            break
+    return out
+
+
+def _sampled_oracle(nest, sigma, per_level, seed):
+    import oracle
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lv, ii, jj = [], [], []
+    for l in range(nest.levels):
+        free = np.argwhere(~nest.covered_mask(l))
+        pick = free[rng.choice(len(free), size=min(per_level, len(free)), replace=False)]
+        lv.append(np.full(len(pick), l)), jj.append(pick[:, 0]), ii.append(pick[:, 1])
+    lv, ii, jj = np.concatenate(lv), np.concatenate(ii), np.concatenate(jj)
+    ox, oy = oracle.force_at(nest, sigma, lv, ii, jj)
+    return lv, ii, jj, ox, oy
+
+
+@pytest.mark.parametrize("col_pass", [0, 2])
+def test_c4_sized_batch_against_oracle(lib, col_pass):
+    """One fused batch of C4-sized nests (N up to 1024, up to 4 levels), each
+    level compared with the direct-sum oracle on sampled uncovered cells; with
+    col_pass 2 the groups of N >= 512 run the one-CTA column kernels."""
+    from tests._gpu import tol
+    probs = _c4_subset()
+    assert len(probs) == 16
+    plans = [lib.Plan(nest, "fp32") for nest, _ in probs]
+    for p, (nest, _) in zip(plans, probs):
+        if col_pass == 2 and nest.n >= 512:
+            p.set_schedule(2, 0)
+    batch = lib.Batch(plans)
+    sig = [[torch.from_numpy(a).float().cuda() for a in s] for _, s in probs]
+    fx = [[torch.empty_like(a) for a in s] for s in sig]
+    fy = [[torch.empty_like(a) for a in s] for s in sig]
+    batch.solve(sig, fx, fy)
+    torch.cuda.synchronize()
+    for k, (nest, s) in enumerate(probs):
+        lv, ii, jj, ox, oy = _sampled_oracle(nest, s, 64 if nest.n <= 256 else 16, 100 + k)
+        for l in range(nest.levels):
+            m = lv == l
+            gx = fx[k][l].double().cpu().numpy()[jj[m], ii[m]]
+            gy = fy[k][l].double().cpu().numpy()[jj[m], ii[m]]
+            scale = max(np.abs(ox[m]).max(), np.abs(oy[m]).max())
+            err = max(np.abs(gx - ox[m]).max(), np.abs(gy - oy[m]).max())
+            assert err <= tol("fp32", nest.n) * scale, (nest.n, nest.levels, l, err / scale)
