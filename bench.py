@@ -230,6 +230,42 @@ def time_forest(args, world, dev, stream):
     return out
 
 
+def nest_pair_bytes(nests, w: int = 4):
+    """Algorithmic HBM bytes of one solve of each nest (one patch per level, force
+    plans, w bytes per real), split by pair of levels: the same accounting as the
+    library's plan statistics (every intermediate written and read once, every
+    kernel spectrum read once per use, padding not counted).  Case 1 carries the
+    level's own forward slab and main output; a Case-2 pair (finer source, m =
+    2^d) its m^2 phase slabs of n/m rows and m^2 phase spectra; a Case-3 pair
+    (coarser source) its m^2 phase outputs of n/m rows and m^2 phase spectra:
+    bytes grow with m for the intermediates and m^2 for the spectra."""
+    C = 2 * w
+    out = {}
+
+    def add(key, b):
+        out[key] = out.get(key, 0) + b
+    for nest in nests:
+        n, L = int(nest.n), int(nest.levels)
+        n1 = n + 1
+        add("sigma_in_forces_out", 3 * L * n * n * w)
+        if L > 1:  # restriction of every covered level: its input, its copy, the children of its covered cells
+            add("restriction", (L - 1) * (2 * n * n * w + 4 * (n // 2) ** 2 * w))
+        for t in range(L):
+            add("case1", 6 * n1 * n1 * w + 2 * 3 * n1 * n * C + 2 * 2 * n1 * n * C)
+            for s in range(L):
+                if s == t:
+                    continue
+                d = abs(s - t)
+                m = 1 << d
+                spec = m * m * 6 * n1 * 2 * n * C
+                if s > t:  # Case 2: finer source, m^2 phase slabs of n/m rows
+                    add(f"case2_d{d}", spec + 2 * 3 * n1 * n * C * m)
+                else:      # Case 3: coarser source, m^2 phase outputs of n/m rows
+                    add(f"case3_d{d}", spec + 2 * 2 * n1 * n * C * m)
+    tot = sum(out.values())
+    return {"bytes": out, "total": tot, "share": {k: v / tot for k, v in out.items()}}
+
+
 def run_gpu(args, world, rank, local):
     import numpy as np
     import torch
@@ -359,6 +395,17 @@ def run_gpu(args, world, rank, local):
     if not args.no_forest:
         forest = time_forest(args, world, dev, stream)
 
+    # the batched (256 nests) and serving (Poisson mix) workloads, shortened, on the same GPU
+    batched = serving_runs = None
+    if world == 1 and not args.no_nest_workloads:
+        import copy
+        ba = copy.copy(args)
+        ba.steps, ba.warmup = 3, 2
+        batched = run_batched(ba, world, rank, local)
+        sa = copy.copy(args)
+        sa.warmup = 1
+        serving_runs = run_serving(sa, world, rank, local, streams=[(args.rate, 15.0), (0.0, 10.0)])
+
     # e2e: host buffers through the C ABI, copies inside the timed region
     pin_s = torch.from_numpy(sigma[0].astype(np.float32)).pin_memory()
     pin_x = torch.empty((n, n), dtype=torch.float32).pin_memory()
@@ -417,6 +464,12 @@ def run_gpu(args, world, rank, local):
                    "bf16x_path": bf16x,
                    "potential_path": potential,
                    "forest_path": forest,
+                   "batched_path": None if batched is None else {
+                       "workload": batched["config"]["workload"], "cells_per_s": batched["value"],
+                       "ms_per_batch": batched["ms_per_step"], **{k: batched["config"][k] for k in (
+                           "nests", "cells_per_batch", "shapes", "kernel_groups", "launches_per_batch", "plan_s",
+                           "spectra_gib", "algorithmic_bytes_per_batch", "roofline", "bytes_by_pair")}},
+                   "serving_path": serving_runs,
                    "l2": f"{sets} rotating input/output sets ({sets * 3 * n * n * 4 / 2**20:.0f} MiB) > 129 MiB L2",
                    "plan_ms": st["plan_ms"], "spectra_mib": st["spectra_bytes"] / 2**20,
                    "algorithmic_bytes_per_solve": st["algorithmic_bytes"],
@@ -485,9 +538,16 @@ def run_batched(args, world, rank, local):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     cells = sum(probs[k][0].levels * probs[k][0].n ** 2 for k in range(len(probs)))
+    spectra_gib = sum(p.stats()["spectra_bytes"] for p in base.values()) / 2**30
+    algo = sum(plans[i].stats()["algorithmic_bytes"] for i in range(len(plans)))
+    pairs = nest_pair_bytes([probs[k][0] for k in mine])
+    batch.close()
+    for p in plans:
+        p.close()
     if rank != 0:
-        return
+        return None
     shapes = sorted({(p.n, p.levels) for p in base.values()})
+    peak = peaks()[0]
     line = {"metric": METRIC, "value": cells * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -495,19 +555,29 @@ def run_batched(args, world, rank, local):
                        "cells_per_batch": cells, "parallelism": f"replicas{world}", "shapes": len(shapes),
                        "kernel_groups": info["groups"], "launches_per_batch": info["launches_per_solve"],
                        "graph": True, "plan_s": plan_s,
-                       "spectra_gib": sum(p.stats()["spectra_bytes"] for p in base.values()) / 2**30},
+                       "spectra_gib": spectra_gib,
+                       "algorithmic_bytes_per_batch": algo,
+                       "roofline": {"bound": "hbm", "achieved": algo / (ms / args.steps / 1e3) / 1e9, "peak": peak,
+                                    "unit": "GB/s", "frac": algo / (ms / args.steps / 1e3) / 1e9 / peak,
+                                    "scope": "whole batch solve (all passes), rank 0's nests"},
+                       "bytes_by_pair": pairs},
             "gpu_launches": args.steps * info["launches_per_solve"], "clocks": clk.summary()}
-    print(json.dumps(line), flush=True)
+    return line
 
 
-def run_serving(args, world, rank, local):
+def run_serving(args, world, rank, local, streams=None):
     """Serving workload: an open-loop Poisson stream of force requests with host
     buffers, served by the request loop (sgf_server_*): continuous admission by
     HBM footprint onto concurrent streams, spectra resident per shape.  Every
     shape is warmed once (spectra built) before the timed stream.  value = cells
     of the completed requests / span from the first arrival to the last
     completion; latency percentiles over the timed stream.  Each rank serves its
-    own stream (replicas: seed + rank)."""
+    own stream (replicas: seed + rank).
+
+    streams: None (one stream at args.rate for args.seconds; returns its line)
+    or a list of (rate, seconds) run one after the other on the same warmed
+    server (returns one summary per stream); a rate of 0 means 85 % of the
+    accepted load the previous stream's device sustained."""
     import numpy as np
     import torch
     from paper_1603_03142_gb300 import serving, sgf
@@ -516,8 +586,9 @@ def run_serving(args, world, rank, local):
     sizes = tuple(int(x) for x in args.sizes.split(","))
     lv = tuple(int(x) for x in args.levels.split(","))
     precs = tuple(args.precisions.split(","))
-    arr = serving.poisson_arrivals(args.rate, args.seconds, args.seed + rank, sizes, (lv[0], lv[-1]), precs)
-    shapes = sorted({(a.n, a.levels, a.precision) for a in arr})
+    plan_streams = streams if streams is not None else [(args.rate, args.seconds)]
+    # every shape the mix can draw is warmed, whatever the first stream happens to contain
+    shapes = sorted({(n, L, p) for n in sizes for L in range(lv[0], lv[-1] + 1) for p in precs})
     t0 = time.perf_counter()
     pools = serving.make_pools(shapes, seed=args.seed)
     pool_s = time.perf_counter() - t0
@@ -527,54 +598,73 @@ def run_serving(args, world, rank, local):
     t0 = time.perf_counter()
     warm = [serving.Arrival(0.0, n, L, p, 0) for (n, L, p) in shapes]
     wrec, _ = serving.run_stream(srv, warm, pools, id_base=10 ** 8)
+    first = serving.poisson_arrivals(plan_streams[0][0], plan_streams[0][1], args.seed + rank, sizes,
+                                     (lv[0], lv[-1]), precs)
     for k in range(max(0, args.warmup - 1)):
-        serving.run_stream(srv, arr[: max(1, len(arr) // 20)], pools, id_base=10 ** 8 + (k + 1) * 10 ** 6)
+        serving.run_stream(srv, first[: max(1, len(first) // 20)], pools, id_base=10 ** 8 + (k + 1) * 10 ** 6)
     warm_s = time.perf_counter() - t0
-    accepted = {(r.n, r.levels) for r in wrec if r.status == sgf.SGF_OK}
-    torch.cuda.synchronize()
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    with ClockSampler(local) as clk:
-        recs, _ = serving.run_stream(srv, arr, pools)
-    summ = serving.summarize(recs, args.seconds)
+    accepted = sorted({(r.n, r.levels) for r in wrec if r.status == sgf.SGF_OK})
+    rejected_shapes = sorted({(r.n, r.levels) for r in wrec if r.status != sgf.SGF_OK})
+    results = []
+    prev = None
+    for si, (rate, seconds) in enumerate(plan_streams):
+        if rate <= 0:  # 85 % of the accepted load the device sustained in the previous stream
+            acc_frac = max(1e-3, 1.0 - prev["load"]["rejected"] / max(1, prev["requests"]))
+            rate = 0.85 * prev["load"]["achieved_rps"] / acc_frac
+        arr = serving.poisson_arrivals(rate, seconds, args.seed + rank + 1000 * si, sizes, (lv[0], lv[-1]), precs)
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        with ClockSampler(local) as clk:
+            recs, _ = serving.run_stream(srv, arr, pools, id_base=10 ** 9 * (si + 1))
+        summ = serving.summarize(recs, seconds)
+        launches, h2d, d2h = 0, 0, 0
+        for r in recs:
+            if r.status == sgf.SGF_OK:
+                launches += (r.levels - 1) + 3 + (1 if r.levels > 1 else 0)
+                h2d += r.levels * r.n * r.n * 4
+                d2h += 2 * r.levels * r.n * r.n * 4
+        done = max(1, summ.get("completed", 0))
+        value = summ.get("cells_per_s", 0.0)
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([value], device=torch.device("cuda", local), dtype=torch.float64)
+            dist.all_reduce(t)
+            value = float(t.item())
+        res = {"offered_rps": rate, "seconds": seconds, "requests": len(recs), "cells_per_s": value,
+               "latency_ms": {k: summ.get(k) for k in ("p50_ms", "p90_ms", "p99_ms", "max_ms", "mean_ms")},
+               "load": {"offered_rps": summ.get("offered_rps"), "achieved_rps": summ.get("achieved_rps"),
+                        "offered_cells_per_s": summ.get("offered_cells_per_s"), "completed": summ.get("completed"),
+                        "rejected": summ.get("rejected"), "failed": summ.get("failed")},
+               "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d / done,
+                       "d2h_bytes_per_step": d2h / done},
+               "gpu_launches": launches, "clocks": clk.summary(), "mean_ms": summ.get("mean_ms")}
+        results.append(res)
+        prev = res
     st = srv.stats()
-    launches, h2d, d2h = 0, 0, 0
-    for r in recs:
-        if r.status == sgf.SGF_OK:
-            launches += (r.levels - 1) + 3 + (1 if r.levels > 1 else 0)
-            h2d += r.levels * r.n * r.n * 4
-            d2h += 2 * r.levels * r.n * r.n * 4
     srv.close()
-    value = summ.get("cells_per_s", 0.0)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([value, summ.get("span_s", 0.0)], device=torch.device("cuda", local), dtype=torch.float64)
-        vals = [torch.zeros_like(t) for _ in range(world)]
-        dist.all_gather(vals, t)
-        value = float(sum(v[0].item() for v in vals))
     if rank != 0:
-        return
-    done = max(1, summ.get("completed", 0))
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": summ.get("completed", 0),
-            "warmup": args.warmup, "ms_per_step": summ.get("mean_ms"), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        return None
+    common = {"shapes": len(shapes), "shapes_served": accepted, "shapes_rejected": rejected_shapes,
+              "hbm_budget_gib": args.budget_gb, "max_shape_gib": args.max_shape_gb,
+              "max_inflight": args.inflight, "parallelism": f"replicas{world}", "pool_s": pool_s,
+              "warm_s": warm_s, "inputs": "pinned host buffers, copies inside the latency",
+              "server": {k: st[k] for k in ("inflight_peak", "slots", "shapes_resident", "shapes_built",
+                                            "slots_evicted", "bytes_peak")}}
+    if streams is not None:
+        return {"streams": results, **common}
+    r = results[0]
+    line = {"metric": METRIC, "value": r["cells_per_s"], "unit": UNIT, "n_gpus": world,
+            "steps": r["load"]["completed"] or 0, "warmup": args.warmup, "ms_per_step": r["mean_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
             "config": {"workload": f"serving-poisson-{args.rate:g}rps-{args.seconds:g}s-N{sizes[0]}-{sizes[-1]}"
                                    f"-L{lv[0]}-{lv[-1]}-{'+'.join(precs)}",
-                       "requests": len(recs), "shapes": len(shapes), "shapes_served": sorted(accepted),
-                       "hbm_budget_gib": args.budget_gb, "max_shape_gib": args.max_shape_gb,
-                       "max_inflight": args.inflight,
-                       "parallelism": f"replicas{world}", "pool_s": pool_s, "warm_s": warm_s,
-                       "inputs": "pinned host buffers, copies inside the latency"},
-            "latency_ms": {k: summ.get(k) for k in ("p50_ms", "p90_ms", "p99_ms", "max_ms", "mean_ms")},
-            "load": {"offered_rps": summ.get("offered_rps"), "achieved_rps": summ.get("achieved_rps"),
-                     "offered_cells_per_s": summ.get("offered_cells_per_s"), "completed": summ.get("completed"),
-                     "rejected": summ.get("rejected"), "failed": summ.get("failed")},
-            "server": {k: st[k] for k in ("inflight_peak", "slots", "shapes_resident", "shapes_built",
-                                          "slots_evicted", "bytes_peak")},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d / done, "d2h_bytes_per_step": d2h / done},
-            "gpu_launches": launches, "clocks": clk.summary()}
-    print(json.dumps(line), flush=True)
+                       "requests": r["requests"], **common},
+            "latency_ms": r["latency_ms"], "load": r["load"], "e2e": r["e2e"],
+            "gpu_launches": r["gpu_launches"], "clocks": r["clocks"]}
+    return line
 
 
 def main():
@@ -590,6 +680,8 @@ def main():
     ap.add_argument("--no-bf16x", action="store_true", help="skip the split-BF16 tensor-core path")
     ap.add_argument("--no-potential", action="store_true", help="skip the potential (SGF_PLAN_POTENTIAL) timing")
     ap.add_argument("--no-forest", action="store_true", help="skip the two-disk forest (Example 3) timing")
+    ap.add_argument("--no-nest-workloads", action="store_true",
+                    help="uniform: skip the shortened batched and serving runs reported in config")
     ap.add_argument("--forest-n", type=int, default=512, help="cells per side of every patch of the forest")
     ap.add_argument("--schedule", default="auto",
                     help="uniform: 'auto' (autotuner) or 'col_pass,row_inv0' to fix the kernel schedule")
@@ -616,10 +708,10 @@ def main():
         run_reference(args, world, rank)
         return
     world, rank, local = dist_setup()
-    if args.workload == "batched":
-        run_batched(args, world, rank, local)
-    elif args.workload == "serving":
-        run_serving(args, world, rank, local)
+    if args.workload in ("batched", "serving"):
+        line = (run_batched if args.workload == "batched" else run_serving)(args, world, rank, local)
+        if line is not None:
+            print(json.dumps(line), flush=True)
     else:
         run_gpu(args, world, rank, local)
     if world > 1:
