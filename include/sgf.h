@@ -313,6 +313,21 @@ sgf_status sgf_plan_profile(sgf_plan *plan, int32_t enable);
 /* Waits for the recorded solves, returns their summed times and clears them. */
 sgf_status sgf_plan_profile_read(sgf_plan *plan, sgf_kernel_times *out);
 
+/* Testing the bounded-wait error path (no paper counterpart).  The next
+ * sgf_solve of this plan withholds the producers of the device waits named by
+ * `which` -- SGF_INJECT_TMA_GATHER: the bulk copies of the inverse row pass's
+ * gather (schedule row_inv0 = 3); SGF_INJECT_TC_COMMIT: the tensor-core MMAs
+ * and their commit (SGF_BF16X) -- and bounds every device wait of that solve
+ * by wait_cycles SM cycles (> 0) instead of about one second.  Those waits
+ * then run out with nothing in flight: the solve's output is not the method's
+ * and sgf_plan_check reports SGF_ETIMEOUT; the plan and the CUDA context stay
+ * usable, and the next solve is a normal one.  The setting applies to one
+ * sgf_solve and is cleared by it (other entry points ignore it).
+ * Errors: SGF_EINVAL (NULL plan, unknown bits, wait_cycles <= 0). */
+#define SGF_INJECT_TMA_GATHER 0x1u
+#define SGF_INJECT_TC_COMMIT 0x2u
+sgf_status sgf_plan_inject_timeout(sgf_plan *plan, uint32_t which, int64_t wait_cycles);
+
 /* Description of the last failure on the calling thread; valid until the
  * next sgf_* call on this thread.  Never NULL. */
 const char *sgf_last_error(void);
@@ -371,8 +386,11 @@ sgf_status sgf_solve_noalloc(sgf_plan *plan, const void *const *sigma, void *con
  *     gather of a row pair's bins done by the tensor memory accelerator (a
  *     tensor map over the plan's own column output, made at plan creation;
  *     SGF_FP32 plans of n >= 512 with one level-0 patch; sgf_solve_noalloc,
- *     whose intermediates are not the plan's, runs 0 instead).  Potential
- *     plans take no 2.
+ *     whose intermediates are not the plan's, runs 0 instead); 4 = as 3 with
+ *     one thread per slot carrying both parity halves, the slot's stage
+ *     twiddles in registers and the CTAs walking the row pairs, each
+ *     gathering its next row pair behind the current transforms (n >= 1024;
+ *     sgf_solve_noalloc runs 0 instead).  Potential plans take no 2.
  *   col_case3 (nests): 0 = the m^2 Case-3 phase outputs of a (coarser source,
  *     target) pair in one cluster per column, the source's forward column
  *     transforms done once for all of them; 1 = one cluster per phase output,
@@ -391,8 +409,8 @@ sgf_status sgf_plan_schedule_get(const sgf_plan *plan, sgf_schedule *schedule);
  * SGF_EUNSUPPORTED for col_pass = 2 or row_inv0 = 1 on a SGF_BF16X plan of
  * n = SGF_MAX_N (those kernels have no shared memory left for the tensor-core
  * tiles there), col_pass = 3 outside zero-rim SGF_FP32 force plans of
- * n >= 1024, row_inv0 = 2 on a potential plan, row_inv0 = 3 where it does not
- * apply (the autotuner skips all of these). */
+ * n >= 1024, row_inv0 = 2 on a potential plan, row_inv0 = 3 or 4 where it
+ * does not apply (the autotuner skips all of these). */
 sgf_status sgf_plan_schedule_set(sgf_plan *plan, const sgf_schedule *schedule);
 
 /* The autotuner: runs one solve on zero density (temporary device buffers),
@@ -404,11 +422,11 @@ sgf_status sgf_plan_schedule_set(sgf_plan *plan, const sgf_schedule *schedule);
  * <row_inv0> <col_case3>" per key, read once, rewritten after each tuning).  chosen (may be
  * NULL) receives the schedule; ms (may be NULL, else SGF_AUTOTUNE_TIMES
  * doubles) the mean milliseconds per launch of col_pass 0, 1, 2, row_inv0 0, 1,
- * 2, col_case3 0, 1, row_inv0 3, col_pass 3 (-1 where a candidate does not
- * apply).  Blocks
+ * 2, col_case3 0, 1, row_inv0 3, col_pass 3, row_inv0 4 (-1 where a candidate
+ * does not apply).  Blocks
  * until done.
  * Errors: SGF_EINVAL, SGF_ENOMEM, SGF_ECUDA. */
-#define SGF_AUTOTUNE_TIMES 10
+#define SGF_AUTOTUNE_TIMES 11
 sgf_status sgf_plan_autotune(sgf_plan *plan, int32_t reps, void *stream, sgf_schedule *chosen, double *ms);
 
 /* Device memory a plan for this nest would hold, computed on the host without

@@ -205,6 +205,9 @@ struct sgf_plan {
     // device address of sgf_solve_noalloc's scratch array, looked up at plan
     // creation when the plan's intermediates fit it (else NULL)
     void *noalloc_scratch = nullptr;
+    // sgf_plan_inject_timeout: injection bits and wait bound of the next sgf_solve
+    uint32_t inject = 0;
+    long long inject_wait = 0;
     size_t workspace_bytes = 0;
     size_t algorithmic_bytes = 0;
     // optional per-kernel timing: 5 events per solve (before restriction, after
@@ -1143,7 +1146,10 @@ cudaError_t launch_row_inv(int logN, int L, int R, SolveArgs<T> a, cudaStream_t 
     a.level_base = 0;
     if (row_inv0 == 1)
         return launch_pass_n<T>(PASS_ROW_INV, logN, a, L, st, nullptr, tc);
-    const int first = row_inv0 == 2 ? PASS_ROW_INV2 : row_inv0 == 3 ? PASS_ROW_INV1T : PASS_ROW_INV1;
+    const int first = row_inv0 == 2   ? PASS_ROW_INV2
+                      : row_inv0 == 3 ? PASS_ROW_INV1T
+                      : row_inv0 == 4 ? PASS_ROW_INV1X
+                                      : PASS_ROW_INV1;
     cudaError_t e = launch_pass_n<T>(first, logN, a, R, st, nullptr, tc);
     if (e != cudaSuccess || L == R)
         return e;
@@ -1222,7 +1228,10 @@ cudaError_t launch_col(const sgf_plan *p, const SolveArgs<T> &a, cudaStream_t st
 // for level 0) has no shared memory left for tensor-core tiles at n = 4096.
 inline bool schedule_ok(const sgf_plan *p, const sgf_schedule &s)
 {
-    if (s.col_pass < 0 || s.col_pass > 3 || s.row_inv0 < 0 || s.row_inv0 > 3 || (s.col_case3 != 0 && s.col_case3 != 1))
+    if (s.col_pass < 0 || s.col_pass > 3 || s.row_inv0 < 0 || s.row_inv0 > 4 || (s.col_case3 != 0 && s.col_case3 != 1))
+        return false;
+    // k_row_inv1x: the tensor-map gather (row_inv0 = 3's conditions) with n >= 1024
+    if (s.row_inv0 == 4 && !(p->tma_inv && p->N >= 1024))
         return false;
     // k_col_mx: zero-rim forces, FP32 without tensor-core tiles, N >= 1024
     if (s.col_pass == 3 && !(p->merged && !p->pot && p->prec == SGF_FP32 && p->N >= 1024))
@@ -1300,6 +1309,9 @@ sgf_status solve_impl(sgf_plan *p, const void *const *sigma, void *const *fx, vo
     a.tw = static_cast<const typename SolveArgs<T>::C *>(p->spec->tw);
     a.tw_entries = p->spec->tw_entries;
     a.status = p->d_status;
+    a.inject = (int)p->inject;  // a test's one-shot injection (sgf_plan_inject_timeout)
+    a.wait_cycles = p->inject ? p->inject_wait : 0;
+    p->inject = 0;
     a.slabs = p->d_slabs;
     a.fwd_items = p->d_items;
     a.outs = p->d_outs;
@@ -1457,7 +1469,7 @@ sgf_status solve_noalloc_impl(sgf_plan *p, const void *const *sigma, void *const
     if (e != cudaSuccess)
         return cuda_fail(e, "col launch");
     // the plan's tensor map points at its own intermediates, not at the scratch array
-    const int inv0 = p->sched.row_inv0 == 3 ? 0 : p->sched.row_inv0;
+    const int inv0 = p->sched.row_inv0 >= 3 ? 0 : p->sched.row_inv0;
     if ((e = launch_row_inv<T>(p->logN, L, p->fo.R, a, st, p->tc, inv0)) != cudaSuccess)
         return cuda_fail(e, "row_inv launch");
     if ((e = cudaEventRecord(p->done, st)) != cudaSuccess)
@@ -1764,7 +1776,7 @@ void tune_load_locked()
     char key[160];
     int a = 0, b = 0, c = 0;
     while (fscanf(f, "%159s %d %d %d", key, &a, &b, &c) == 4)
-        if (a >= 0 && a <= 3 && b >= 0 && b <= 3 && (c == 0 || c == 1))
+        if (a >= 0 && a <= 3 && b >= 0 && b <= 4 && (c == 0 || c == 1))
             g_tune[key] = sgf_schedule{a, b, c};
     fclose(f);
 }
@@ -1868,8 +1880,8 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[SGF_A
                 best.col_pass = bc;
         }
     }
-    auto inv_slot = [](int c) { return c < 3 ? 3 + c : 8; };  // row_inv0 = 3 appended after col_case3
-    for (int c = 0; c < 4 && s == SGF_OK; ++c) {
+    auto inv_slot = [](int c) { return c < 3 ? 3 + c : c == 3 ? 8 : 10; };  // 3, 4 appended after col_case3
+    for (int c = 0; c < 5 && s == SGF_OK; ++c) {
         sgf_schedule cand = best;
         cand.row_inv0 = c;
         if (schedule_ok(p, cand))
@@ -1877,7 +1889,7 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[SGF_A
     }
     if (s == SGF_OK) {  // the fastest of the candidates that apply (and were timed)
         int bc = -1;
-        for (int c = 0; c < 4; ++c)
+        for (int c = 0; c < 5; ++c)
             if (ms[inv_slot(c)] >= 0.0 && (bc < 0 || ms[inv_slot(c)] < ms[inv_slot(bc)]))
                 bc = c;
         if (bc >= 0)
@@ -2188,6 +2200,19 @@ sgf_status sgf_plan_stats_get(const sgf_plan *p, sgf_plan_stats *st)
     return SGF_OK;
 }
 
+static_assert(SGF_INJECT_TMA_GATHER == (unsigned)INJECT_TMA_GATHER && SGF_INJECT_TC_COMMIT == (unsigned)INJECT_TC_COMMIT,
+              "injection bits");
+
+sgf_status sgf_plan_inject_timeout(sgf_plan *p, uint32_t which, int64_t wait_cycles)
+{
+    if (!p || (which & ~(SGF_INJECT_TMA_GATHER | SGF_INJECT_TC_COMMIT)) || wait_cycles <= 0)
+        return fail(SGF_EINVAL, "sgf_plan_inject_timeout: NULL plan, unknown bits 0x%x or wait_cycles %lld <= 0",
+                    which, (long long)wait_cycles);
+    p->inject = which;
+    p->inject_wait = wait_cycles;
+    return SGF_OK;
+}
+
 sgf_status sgf_plan_footprint(const sgf_plan *p, size_t *workspace_bytes, size_t *spectra_bytes)
 {
     if (!p || !workspace_bytes || !spectra_bytes)
@@ -2372,7 +2397,7 @@ sgf_status sgf_plan_schedule_set(sgf_plan *p, const sgf_schedule *in)
 {
     if (!p || !in)
         return fail(SGF_EINVAL, "NULL argument");
-    if (in->col_pass < 0 || in->col_pass > 3 || in->row_inv0 < 0 || in->row_inv0 > 3 ||
+    if (in->col_pass < 0 || in->col_pass > 3 || in->row_inv0 < 0 || in->row_inv0 > 4 ||
         (in->col_case3 != 0 && in->col_case3 != 1))
         return fail(SGF_EINVAL, "schedule out of range (col_pass %d, row_inv0 %d, col_case3 %d)", in->col_pass,
                     in->row_inv0, in->col_case3);
@@ -2380,7 +2405,8 @@ sgf_status sgf_plan_schedule_set(sgf_plan *p, const sgf_schedule *in)
         return fail(SGF_EUNSUPPORTED,
                     "schedule (col_pass %d, row_inv0 %d) not available for this plan: col_pass = 2 and row_inv0 = 1 "
                     "need n < %d with SGF_BF16X, col_pass = 3 a zero-rim SGF_FP32 force plan with n >= 1024, "
-                    "row_inv0 = 2 a force plan, row_inv0 = 3 SGF_FP32 with n >= 512 and one level-0 patch",
+                    "row_inv0 = 2 a force plan, row_inv0 = 3 SGF_FP32 with n >= 512 and one level-0 patch, "
+                    "row_inv0 = 4 the same with n >= 1024",
                     in->col_pass, in->row_inv0, SGF_MAX_N);
     p->sched = *in;
     return SGF_OK;

@@ -95,6 +95,9 @@ inline __host__ __device__ size_t bwd_index(int N, int rows, int comp, int kx, i
 // wait for tensor-core completion (SGF_BF16X) gave up.
 // STATUS_TMA_TIMEOUT: a bounded wait for a tensor-memory-accelerator copy gave up.
 enum : int { STATUS_RIM_NONZERO = 1, STATUS_TC_TIMEOUT = 2, STATUS_TMA_TIMEOUT = 4 };
+// Test injection bits of SolveArgs::inject (the values of SGF_INJECT_* in sgf.h):
+// the producers of those device waits are withheld for one solve.
+enum : int { INJECT_TMA_GATHER = 1, INJECT_TC_COMMIT = 2 };
 
 // A quarter-stored spectrum row holds ky = 0..N split by parity: even ky
 // (0, 2, .., N) at [0, N/2 + 1), odd ky (1, 3, .., N-1) at [N/2 + 4, N + 4);
@@ -175,6 +178,8 @@ struct SolveArgs {
     const C *tw;                // twiddle area (tw_layout), copied to shared memory by every CTA
     int tw_entries;             // its length in complex entries (even)
     int *status;                // device status word of the plan (STATUS_* bits)
+    long long wait_cycles;      // bound of every device wait in SM cycles; 0: about one second
+    int inject;                 // test injection (SGF_INJECT_*): producers of those waits withheld
     const FwdSlab *slabs;
     const FwdItem *fwd_items;
     const ColOutput *outs;
@@ -254,7 +259,8 @@ enum : int {
     PASS_ROW_INV1T = 12,  // PASS_ROW_INV1 with the gather by the tensor memory accelerator (one patch, FP32)
     PASS_COL_W = 13,      // PASS_COL with both parity halves in one CTA (no tensor-core tiles, N >= 512)
     PASS_COL_GW = 14,     // PASS_COL_G likewise (FP32, 512 <= N <= 2048)
-    PASS_COL_MX = 15      // zero-rim forces: both parity halves per thread, register twiddles (FP32, N >= 1024)
+    PASS_COL_MX = 15,     // zero-rim forces: both parity halves per thread, register twiddles (FP32, N >= 1024)
+    PASS_ROW_INV1X = 16   // PASS_ROW_INV1T likewise (walking, both halves per thread; FP32, N >= 1024)
 };
 // Batch mode of the transform passes: a block's nest and its local work index
 // come from a per-launch map (one int2 per block row), and that nest's

@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, sizeof(T) == 4 && !
     unsigned char *smem_raw = smem_tc + (TC ? tc_smem_bytes(TCR) : 0);
     TcCtx tcx;
     if constexpr (TC)
-        tc_begin(tcx, smem_tc, TCT, TCR, a.status);
+        tc_begin(tcx, smem_tc, TCT, TCR, a.status, a.wait_cycles, a.inject);
     C *tw = reinterpret_cast<C *>(smem_raw);
     C *sbuf = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
     T *srow = reinterpret_cast<T *>(sbuf);  // f < 2: rows ja, jb; f = 2: ja-1, ja+1, jb-1, jb+1
@@ -288,7 +288,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
     unsigned char *smem_raw = smem_tc + (TC ? tc_smem_bytes(TCR) : 0);
     TcCtx tcx;
     if constexpr (TC)
-        tc_begin(tcx, smem_tc, TCT, TCR, a.status);
+        tc_begin(tcx, smem_tc, TCT, TCR, a.status, a.wait_cycles, a.inject);
     C *tw = reinterpret_cast<C *>(smem_raw);
     C *sbuf = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
     unsigned char *stage_base = reinterpret_cast<unsigned char *>(sbuf + SPC);
@@ -684,7 +684,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
     unsigned char *smem_raw = smem_tc + (TC ? tc_smem_bytes(TCR) : 0);
     TcCtx tcx;
     if constexpr (TC)
-        tc_begin(tcx, smem_tc, TCT, TCR, a.status);
+        tc_begin(tcx, smem_tc, TCT, TCR, a.status, a.wait_cycles, a.inject);
     C *tw = reinterpret_cast<C *>(smem_raw);
     C *sbuf = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
     C *fld = sbuf + 2 * SPC;  // after the two exchange buffers of the dual inverse
@@ -935,7 +935,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
     unsigned char *smem_raw = smem_tc + (TC ? tc_smem_bytes(TCR) : 0);
     TcCtx tcx;
     if constexpr (TC)
-        tc_begin(tcx, smem_tc, TCT, TCR, a.status);
+        tc_begin(tcx, smem_tc, TCT, TCR, a.status, a.wait_cycles, a.inject);
     C *tw = reinterpret_cast<C *>(smem_raw);
     C *sbuf = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
     cg::cluster_group cluster = cg::this_cluster();
@@ -1019,7 +1019,7 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_inv(SolveArgs
     unsigned char *smem_raw = smem_tc + (TC ? tc_smem_bytes(TCR) : 0);
     TcCtx tcx;
     if constexpr (TC)
-        tc_begin(tcx, smem_tc, TCT, TCR, a.status);
+        tc_begin(tcx, smem_tc, TCT, TCR, a.status, a.wait_cycles, a.inject);
     C *tw = reinterpret_cast<C *>(smem_raw);
     C *stg = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));  // [kx][2]
     C *sbuf = stg + 2 * (N + 1) + ((2 * (N + 1) * sizeof(C)) % 16 ? 1 : 0);
@@ -1156,7 +1156,7 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, sizeof(T) == 4 && !
     unsigned char *smem_raw = smem_tc + (TC ? tc_smem_bytes(TCR) : 0);
     TcCtx tcx;
     if constexpr (TC)
-        tc_begin(tcx, smem_tc, TCT, TCR, a.status);
+        tc_begin(tcx, smem_tc, TCT, TCR, a.status, a.wait_cycles, a.inject);
     C *tw = reinterpret_cast<C *>(smem_raw);
     // stage: component c, bin kx's two rows (a pair of C) at [c][kx & 1][kx >> 1], so
     // the threads of a parity half read consecutive pairs; then the exchange buffers
@@ -1304,7 +1304,7 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 2) k_row_inv1t(cons
     cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
     cp_commit();
     __syncthreads();  // the mbarrier is initialised
-    if (t == 0) {
+    if (t == 0 && !(a.inject & INJECT_TMA_GATHER)) {  // (a test may withhold the copies)
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mb), "r"(STAGE_BYTES) : "memory");
         const unsigned long long map = reinterpret_cast<unsigned long long>(&a.tmap_inv[0]);
         for (int k = 0; k < NBOX; ++k) {
@@ -1318,24 +1318,16 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 2) k_row_inv1t(cons
         }
     }
     cp_wait<0>();
-    {
-        const long long t0 = clock64();
-        uint32_t ok = 0;
-        while (true) {
-            asm volatile(
-                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-                : "=r"(ok)
-                : "r"(mb), "r"(0u)
-                : "memory");
-            if (ok)
-                break;
-            if (clock64() - t0 > kTmaWaitCycles) {
-                atomicOr(a.status, STATUS_TMA_TIMEOUT);
-                break;
-            }
-        }
+    // bounded wait for the gather; if any thread gave up, the CTA records it, waits once
+    // more (bounded) for copies that may still land in its shared memory, and returns
+    const long long bound = a.wait_cycles > 0 ? a.wait_cycles : kTmaWaitCycles;
+    const bool landed = tc_try_wait(mb, 0u, bound);
+    if (__syncthreads_or(!landed)) {
+        if (t == 0)
+            atomicOr(a.status, STATUS_TMA_TIMEOUT);
+        tc_try_wait(mb, 0u, bound);
+        return;
     }
-    __syncthreads();  // the twiddles are in place
     C v[1][16];
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
@@ -1371,6 +1363,128 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 2) k_row_inv1t(cons
     }
 }
 
+// ---------------------------------------------------------------- row_inv1x
+// The level-0 inverse row pass of k_row_inv1t with the structure of k_col_mx:
+// one thread per slot j carries both parity halves of a row pair's inverse
+// transform (the fold y = even + W_P^{-n} odd is done in registers) with the
+// slot's stage twiddles in registers, and the CTA walks its (row pair,
+// component) items: as soon as an item's bins are in registers, the tensor
+// memory accelerator gathers the next item's bins into the same stage behind
+// the transforms (the exchange buffers do not alias the stage).  G = 256 /
+// (N/16) groups of N/16 threads per CTA, each walking its own items on its own
+// named barrier and mbarrier.  Waits are bounded: a group that gives up records
+// STATUS_TMA_TIMEOUT, waits once more (bounded) for copies still landing in its
+// stage, and stops.  FP32, N >= 1024, one level-0 patch, no batch view.
+// Shared memory per group: 128-byte aligned stage | exchange buffers
+// [2][SP_ROW] | mbarrier, flag.
+template <int LOGN>
+struct KRx {
+    static constexpr int N = 1 << LOGN, Q = N >> 4;
+    static constexpr int G = Q >= 256 ? 1 : 256 / Q;
+    static constexpr int THREADS = G * Q;
+    static constexpr int NBOX = (N + 1 + kTmaBox - 1) / kTmaBox;
+    static constexpr uint32_t STAGE_BYTES = (uint32_t)NBOX * kTmaBox * 16;
+    static constexpr size_t XB = 2 * (size_t)KShape<LOGN>::SP_ROW * 8;
+    static constexpr size_t GROUP_BYTES = ((STAGE_BYTES + XB + 16 + 127) / 128) * 128;
+    static constexpr size_t SMEM = G * GROUP_BYTES + 128;  // + alignment slack
+};
+
+template <int LOGN>
+__global__ void __launch_bounds__(KRx<LOGN>::THREADS, 1) k_row_inv1x(const __grid_constant__ SolveArgs<float> a)
+{
+    using C = float2;
+    using R = KRx<LOGN>;
+    using P = F16<LOGN>;
+    constexpr int N = R::N, Q = R::Q, G = R::G, SP = KShape<LOGN>::SP_ROW, PP = 2 * N;
+    static_assert(Q >= 64, "named group barriers need whole warps");
+    extern __shared__ __align__(16) unsigned char smem_dyn[];
+    const uint32_t base_s = (uint32_t)__cvta_generic_to_shared(smem_dyn);
+    unsigned char *smem_al = smem_dyn + (((base_s + 127u) & ~127u) - base_s);
+    const int t = threadIdx.x;
+    const int g = t / Q, j = t - g * Q;
+    unsigned char *gb = smem_al + (size_t)g * R::GROUP_BYTES;
+    unsigned char *stage = gb;
+    C *xb = reinterpret_cast<C *>(gb + R::STAGE_BYTES);
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(gb + R::STAGE_BYTES + R::XB);
+    volatile int *gave_up = reinterpret_cast<volatile int *>(gb + R::STAGE_BYTES + R::XB + 8);
+    const unsigned bar = 1 + g;
+    const int tl = a.level_base;
+    const int items = a.ncomp * (N / 2);
+    C trw[P::NST - 1][15];
+    load_twiddles_rt<C, LOGN>(trw, a.tw, j);
+    const TwLayout twl = tw_layout(P::twlen, N);
+    const C wj = a.tw[twl.base + j];  // W_P^j
+    auto twist_u = [&](int u) { return hmul(wj, hmk<C>((float)kW32c[u], (float)-kW32s[u])); };
+    const long long bound = a.wait_cycles > 0 ? a.wait_cycles : kTmaWaitCycles;
+    const bool withhold = (a.inject & INJECT_TMA_GATHER) != 0;
+    auto gather = [&](int it) {  // one thread of the group: the bins of item it
+        if (withhold)
+            return;  // (a test withholds the copies)
+        // the stage was last read through the generic proxy: order that before the copies
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        const int comp = it >= N / 2 ? 1 : 0;
+        const int j0 = 2 * (it - comp * (N / 2));
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mb), "r"(R::STAGE_BYTES)
+                     : "memory");
+        const unsigned long long map = reinterpret_cast<unsigned long long>(&a.tmap_inv[0]);
+        for (int k = 0; k < R::NBOX; ++k) {
+            const uint32_t dst = (uint32_t)__cvta_generic_to_shared(stage + (size_t)k * kTmaBox * 16);
+            const int x = 2 * j0, y = comp * (N + 1) + k * kTmaBox;  // x: 4 floats a row pair, 16-byte aligned
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                "[%4];\n" ::"r"(dst),
+                "l"(map), "r"(x), "r"(y), "r"(mb)
+                : "memory");
+        }
+    };
+    const int step = (int)gridDim.x * G;
+    int it = (int)blockIdx.x * G + g;
+    if (j == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(mb), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        *gave_up = 0;
+    }
+    group_sync(bar, Q);  // the mbarrier is initialised
+    if (j == 0 && it < items)
+        gather(it);
+    for (uint32_t phase = 0; it < items; it += step, ++phase) {  // uniform over the group
+        if (!tc_try_wait(mb, phase & 1u, bound))
+            *gave_up = 1;
+        group_sync(bar, Q);
+        if (*gave_up) {  // every thread of the group sees it after the barrier
+            if (j == 0)
+                atomicOr(a.status, STATUS_TMA_TIMEOUT);
+            tc_try_wait(mb, phase & 1u, bound);  // copies that may still land in the stage
+            break;
+        }
+        const int comp = it >= N / 2 ? 1 : 0;
+        const int j0 = 2 * (it - comp * (N / 2)), j1 = j0 + 1;
+        C v[2][16];
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int kx = 2 * (j + u * Q) + b;
+                const int k2 = kx <= N ? kx : PP - kx;
+                const float4 ab = *reinterpret_cast<const float4 *>(stage + (size_t)k2 * 16);
+                const C A = hmk<C>(ab.x, ab.y), B = hmk<C>(ab.z, ab.w);
+                v[b][u] = kx <= N ? hmk<C>(A.x - B.y, A.y + B.x) : hmk<C>(A.x + B.y, B.x - A.y);
+            }
+        group_sync(bar, Q);  // every thread has read the stage
+        if (j == 0 && it + step < items)
+            gather(it + step);
+        fft_stages_rt<C, true, LOGN, 2, 0>(v, xb, SP, j, trw, bar, Q);
+        float *out = comp ? a.fy[tl] : a.fx[tl];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int n = j + u * Q;
+            const C y = hadd(v[0][u], hmulc(v[1][u], twist_u(u)));
+            out[(size_t)j0 * N + n] = covered(a, tl, j0, n) ? 0.0f : y.x;
+            out[(size_t)j1 * N + n] = covered(a, tl, j1, n) ? 0.0f : y.y;
+        }
+    }
+}
+
 // ------------------------------------------------------------ zero-rim path
 // Forward row pass of a SGF_PLAN_ZERO_RIM plan: the rows of sigma alone (the
 // slopes are folded into the merged spectra).  Also verifies the guarantee:
@@ -1398,7 +1512,7 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd_m(SolveAr
     unsigned char *smem_raw = smem_tc + (TC ? tc_smem_bytes(TCR) : 0);
     TcCtx tcx;
     if constexpr (TC)
-        tc_begin(tcx, smem_tc, TCT, TCR, a.status);
+        tc_begin(tcx, smem_tc, TCT, TCR, a.status, a.wait_cycles, a.inject);
     C *tw = reinterpret_cast<C *>(smem_raw);
     T *srow = reinterpret_cast<T *>(smem_raw + tw_bytes<C>(a.tw_entries));
     C *sbuf = reinterpret_cast<C *>(srow + 2 * N);
@@ -1502,7 +1616,7 @@ __global__ void __cluster_dims__(2, 1, 1)
     unsigned char *smem_raw = smem_tc + (TC ? tc_smem_bytes(TCR) : 0);
     TcCtx tcx;
     if constexpr (TC)
-        tc_begin(tcx, smem_tc, TCT, TCR, a.status);
+        tc_begin(tcx, smem_tc, TCT, TCR, a.status, a.wait_cycles, a.inject);
     C *tw = reinterpret_cast<C *>(smem_raw);
     C *sbuf = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
     C *park = sbuf + SPC;
@@ -1601,7 +1715,7 @@ __global__ void __cluster_dims__(2, 1, 1)
     unsigned char *smem_raw = smem_tc + (TC ? tc_smem_bytes(TCR) : 0);
     TcCtx tcx;
     if constexpr (TC)
-        tc_begin(tcx, smem_tc, TCT, TCR, a.status);
+        tc_begin(tcx, smem_tc, TCT, TCR, a.status, a.wait_cycles, a.inject);
     C *tw = reinterpret_cast<C *>(smem_raw);
     C *sbuf = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
     C *col = sbuf + SPC;
@@ -1708,7 +1822,7 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 1) k_col_mw(SolveAr
     unsigned char *smem_raw = smem_tc + (TC ? tc_smem_bytes(TCR) : 0);
     TcCtx tcx;
     if constexpr (TC)
-        tc_begin(tcx, smem_tc, TCT, TCR, a.status);
+        tc_begin(tcx, smem_tc, TCT, TCR, a.status, a.wait_cycles, a.inject);
     C *tw = reinterpret_cast<C *>(smem_raw);
     C *col = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
     T *gsp = reinterpret_cast<T *>(col + N);  // [half][Gx, Gy][HQ]
@@ -2106,8 +2220,9 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
 {
     using K = KShape<LOGN>;
     using S = KSmem<T, LOGN, TC>;
-    static std::atomic<unsigned long long> d[29];
+    static std::atomic<unsigned long long> d[30];
     static std::atomic<int> res_mx[64];               // resident CTAs of the register-twiddle column pass
+    static std::atomic<int> res_rx[64];               // and of the register-twiddle inverse row pass
     static std::atomic<int> res_mw[64], res_mw1[64];  // resident CTAs of the walking column pass (NC = 2, 1)
     static std::atomic<int> res_fm[64];               // and of the walking zero-rim forward row pass
     static std::atomic<int> res_ri1[64], res_ri2[64]; // and of the walking inverse row passes (tensor cores)
@@ -2191,6 +2306,10 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
             using MX = KMx<LOGN, kMxPark>;
             if ((e = ensure_smem(k_col_mx<LOGN, kMxPark>, MX::SMEM, d[28])) != cudaSuccess ||
                 (e = resident_ctas(k_col_mx<LOGN, kMxPark>, MX::THREADS, MX::SMEM, res_mx, &grid)) != cudaSuccess)
+                return e;
+            using RX = KRx<LOGN>;
+            if ((e = ensure_smem(k_row_inv1x<LOGN>, RX::SMEM, d[29])) != cudaSuccess ||
+                (e = resident_ctas(k_row_inv1x<LOGN>, RX::THREADS, RX::SMEM, res_rx, &grid)) != cudaSuccess)
                 return e;
         }
         return cudaSuccess;
@@ -2332,6 +2451,22 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
             if ((e = ensure_smem(k_row_inv1t<T, LOGN>, S::row_inv1t(), d[22])) != cudaSuccess)
                 return e;
             k_row_inv1t<T, LOGN><<<dim3(a.ncomp * (K::N / 2), count), K::ROW_THREADS, S::row_inv1t(), st>>>(a);
+        } else {
+            return cudaErrorInvalidValue;
+        }
+        break;
+    }
+    case PASS_ROW_INV1X: {
+        if constexpr (!TC && sizeof(T) == 4 && LOGN >= 10) {
+            if (batch)
+                return cudaErrorInvalidValue;
+            using RX = KRx<LOGN>;
+            int grid = 0;
+            if ((e = ensure_smem(k_row_inv1x<LOGN>, RX::SMEM, d[29])) != cudaSuccess ||
+                (e = resident_ctas(k_row_inv1x<LOGN>, RX::THREADS, RX::SMEM, res_rx, &grid)) != cudaSuccess)
+                return e;
+            const int groups = (a.ncomp * (K::N / 2) + RX::G - 1) / RX::G;  // CTAs that give every group an item
+            k_row_inv1x<LOGN><<<dim3(grid < groups ? grid : groups, count), RX::THREADS, RX::SMEM, st>>>(a);
         } else {
             return cudaErrorInvalidValue;
         }

@@ -24,8 +24,12 @@
 //
 // Completion of the MMAs is signalled through an mbarrier by tcgen05.commit;
 // every wait on it is bounded, and a timeout sets STATUS_TC_TIMEOUT in the
-// plan's status word and lets the kernel run to its end (the outputs are then
-// not the method's; the host reports SGF_ETIMEOUT).
+// plan's status word, waits once more (bounded) for the completion of MMAs that
+// may still be writing the tensor memory, and lets the kernel run to its end
+// (the outputs are then not the method's; the host reports SGF_ETIMEOUT); the
+// tensor memory is freed at the end as always.  A test can withhold the MMAs
+// and their commit (SGF_INJECT_TC_COMMIT) with a short bound, so that every
+// wait runs out with nothing in flight.
 #pragma once
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -63,6 +67,8 @@ struct TcCtx {
     int T;            // threads rounded up to a multiple of 128
     int rt;           // tiles per round
     int *status;      // plan status word (STATUS_TC_TIMEOUT)
+    long long wait;   // bound of a wait, SM cycles
+    int withhold;     // test injection: issue no MMA and no commit
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -114,7 +120,8 @@ __device__ __forceinline__ float tc_cospi8(int m)
 // Set up the tensor-core area (every thread calls; contains barriers): `tiles`
 // tiles in all (warp 0 allocates 32 TMEM columns each; tiles is 1, 2, 4 or 8),
 // `rt` A-tile buffers at `area`.
-__device__ __forceinline__ void tc_begin(TcCtx &c, unsigned char *area, int tiles, int rt, int *status)
+__device__ __forceinline__ void tc_begin(TcCtx &c, unsigned char *area, int tiles, int rt, int *status,
+                                         long long wait_cycles, int inject)
 {
     const int t = threadIdx.x;
     c.a = smem_u32(area);
@@ -124,6 +131,8 @@ __device__ __forceinline__ void tc_begin(TcCtx &c, unsigned char *area, int tile
     c.T = ((int)blockDim.x + TC_ROWS - 1) / TC_ROWS * TC_ROWS;
     c.rt = rt;
     c.status = status;
+    c.wait = wait_cycles > 0 ? wait_cycles : TC_WAIT_CYCLES;
+    c.withhold = (inject & INJECT_TC_COMMIT) != 0;
     const int cols = 32 * tiles;
     // B: for dir (0 fwd, 1 inv), part p (0 hi_re, 1 hi_im, 2 lo_re, 3 lo_im): K = 16 (u) x N = 32
     // (column n < 16: Re y_n, n >= 16: Im y_{n-16}); stored K-major as 32 rows (n) x 16 (u).
@@ -176,24 +185,33 @@ __device__ __forceinline__ void tc_end(TcCtx &c, int tiles)
     }
 }
 
-// Bounded wait for the next completion of the mbarrier.
-__device__ __forceinline__ void tc_wait(TcCtx &c)
+// Waits at most `bound` cycles for the mbarrier phase of this parity; true if it completed.
+__device__ __forceinline__ bool tc_try_wait(uint32_t mbar, uint32_t parity, long long bound)
 {
-    const uint32_t parity = c.phase & 1u;
     const long long t0 = clock64();
     uint32_t ok = 0;
     while (true) {
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(ok)
-            : "r"(c.mbar), "r"(parity)
+            : "r"(mbar), "r"(parity)
             : "memory");
         if (ok)
-            break;
-        if (clock64() - t0 > TC_WAIT_CYCLES) {
-            atomicOr(c.status, STATUS_TC_TIMEOUT);
-            break;
-        }
+            return true;
+        if (clock64() - t0 > bound)
+            return false;
+    }
+}
+
+// Bounded wait for the next completion of the mbarrier; on expiry the status
+// bit is set and the commit is waited for once more (bounded), so that MMAs
+// still in flight do not write the tensor memory after the kernel moves on.
+__device__ __forceinline__ void tc_wait(TcCtx &c)
+{
+    const uint32_t parity = c.phase & 1u;
+    if (!tc_try_wait(c.mbar, parity, c.wait)) {
+        atomicOr(c.status, STATUS_TC_TIMEOUT);
+        tc_try_wait(c.mbar, parity, c.wait);
     }
     c.phase++;
 }
@@ -241,7 +259,7 @@ __device__ __forceinline__ void tc_dft16(float2 (*v)[16], TcCtx &c, bool active)
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         tc_fence_before();
         __syncthreads();
-        if (t == 0) {
+        if (t == 0 && !c.withhold) {
             tc_fence_after();
             const uint32_t bdir = c.b + (INV ? 4096u : 0u);
             for (int k = r0; k < r1; ++k) {

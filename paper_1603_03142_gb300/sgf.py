@@ -34,12 +34,12 @@ EXPORTS = ["sgf_plan_create", "sgf_plan_create_ex", "sgf_plan_check", "sgf_plan_
            "sgf_server_clock", "sgf_server_submit", "sgf_server_progress", "sgf_server_stats_get",
            "sgf_server_destroy", "sgf_plan_schedule_get", "sgf_plan_schedule_set", "sgf_plan_autotune",
            "sgf_plan_share_ex", "sgf_solve_potential", "sgf_plan_create_forest", "sgf_plan_estimate_forest",
-           "sgf_plan_footprint"]
+           "sgf_plan_footprint", "sgf_plan_inject_timeout"]
 BATCH_NO_GRAPH = 0x1
 PLAN_ZERO_RIM = 0x1
 PLAN_POTENTIAL = 0x2
 NOALLOC_SCRATCH_BYTES = 32 << 20
-AUTOTUNE_TIMES = 10
+AUTOTUNE_TIMES = 11
 KERNELS = ["restrict", "row_fwd", "col", "row_inv"]
 
 
@@ -102,11 +102,14 @@ class Schedule(ctypes.Structure):
 SERVER_SIMULATE = 0x1
 SERVER_NO_AUTOTUNE = 0x2
 SERVER_STREAM = 0x4
+INJECT_TMA_GATHER = 0x1
+INJECT_TC_COMMIT = 0x2
 _vpp = ctypes.POINTER(ctypes.c_void_p)
 _szp = ctypes.POINTER(ctypes.c_size_t)
 _lib.sgf_plan_create.argtypes = [ctypes.POINTER(NestDesc), ctypes.c_int, ctypes.c_size_t,
                                  ctypes.POINTER(ctypes.c_void_p)]
 _lib.sgf_plan_footprint.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
+_lib.sgf_plan_inject_timeout.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int64]
 _lib.sgf_plan_create_ex.argtypes = [ctypes.POINTER(NestDesc), ctypes.c_int, ctypes.c_uint32,
                                     ctypes.POINTER(ctypes.c_void_p)]
 _lib.sgf_plan_check.argtypes = [ctypes.c_void_p]
@@ -154,7 +157,7 @@ for _f in ("sgf_plan_create", "sgf_plan_create_ex", "sgf_plan_check", "sgf_plan_
            "sgf_plan_estimate", "sgf_server_create", "sgf_server_submit", "sgf_server_progress",
            "sgf_server_stats_get", "sgf_server_destroy", "sgf_plan_schedule_get", "sgf_plan_schedule_set",
            "sgf_plan_autotune", "sgf_plan_share_ex", "sgf_solve_potential", "sgf_plan_create_forest",
-           "sgf_plan_estimate_forest", "sgf_plan_footprint"):
+           "sgf_plan_estimate_forest", "sgf_plan_footprint", "sgf_plan_inject_timeout"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -281,6 +284,11 @@ class Plan:
         _check(_lib.sgf_plan_stats_get(self._h, ctypes.byref(st)), "sgf_plan_stats_get")
         return {name: getattr(st, name) for name, _ in PlanStats._fields_}
 
+    def inject_timeout(self, which: int, wait_cycles: int):
+        """sgf_plan_inject_timeout (testing): the next solve withholds the producers of
+        the waits in `which` and bounds every device wait by wait_cycles."""
+        _check(_lib.sgf_plan_inject_timeout(self._h, int(which), int(wait_cycles)), "sgf_plan_inject_timeout")
+
     def footprint(self) -> dict:
         """sgf_plan_footprint: device bytes of the plan's workspace and of its spectra."""
         ws, sp = ctypes.c_size_t(), ctypes.c_size_t()
@@ -310,7 +318,7 @@ class Plan:
         return {"chosen": {"col_pass": sc.col_pass, "row_inv0": sc.row_inv0, "col_case3": sc.col_case3},
                 "ms": {"col_pass0": ms[0], "col_pass1": ms[1], "col_pass2": ms[2], "row_inv0_0": ms[3],
                        "row_inv0_1": ms[4], "row_inv0_2": ms[5], "col_case3_0": ms[6], "col_case3_1": ms[7],
-                       "row_inv0_3": ms[8], "col_pass3": ms[9]}}
+                       "row_inv0_3": ms[8], "col_pass3": ms[9], "row_inv0_4": ms[10]}}
 
     def profile(self, enable: bool = True):
         _check(_lib.sgf_plan_profile(self._h, 1 if enable else 0), "sgf_plan_profile")

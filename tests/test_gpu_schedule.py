@@ -52,8 +52,9 @@ def test_schedules_agree_zero_rim(lib, prec, n):
         with pytest.raises(lib.SgfError) as ei:
             plan.set_schedule(3, 0)
         assert ei.value.status == lib.SGF_EUNSUPPORTED
+    invs = (0, 1, 2, 3, 4) if tma and n >= 1024 else (0, 1, 2, 3) if tma else (0, 1, 2)
     for col in (0, 1, 2, 3) if mx else (0, 1, 2):
-        for inv in (0, 1, 2, 3) if tma else (0, 1, 2):
+        for inv in invs:
             plan.set_schedule(col, inv)
             assert plan.schedule() == {"col_pass": col, "row_inv0": inv, "col_case3": 0}
             outs.append(run_gpu(plan, sigma))
@@ -146,7 +147,8 @@ print(json.dumps({"r": r, "q": q.schedule()}))
     cp = [ms["col_pass0"], ms["col_pass1"], ms["col_pass2"], ms["col_pass3"]]
     assert ch["col_pass"] == cp.index(min(cp))
     assert ms["row_inv0_3"] > 0  # FP32, n = 1024, one level-0 patch
-    inv = [ms["row_inv0_0"], ms["row_inv0_1"], ms["row_inv0_2"], ms["row_inv0_3"]]
+    assert ms["row_inv0_4"] > 0
+    inv = [ms["row_inv0_0"], ms["row_inv0_1"], ms["row_inv0_2"], ms["row_inv0_3"], ms["row_inv0_4"]]
     assert ch["row_inv0"] == inv.index(min(inv))
     assert d["q"] == ch
     lines = table.read_text().split("\n")
@@ -164,8 +166,9 @@ print(json.dumps(sgf.Plan(W.Nest(n=1024), "fp32", zero_rim=True).schedule()))
 
 @pytest.mark.parametrize("case", ["zero_rim_4096", "general_1024", "nest_512", "potential_1024"])
 def test_tma_gather_matches_lane_gather(lib, case):
-    """row_inv0 = 3 (k_row_inv1t) against row_inv0 = 0 (k_row_inv1): the same
-    arithmetic on the same bins, only the gather differs."""
+    """row_inv0 = 3 (k_row_inv1t) and 4 (k_row_inv1x) against row_inv0 = 0
+    (k_row_inv1): the same arithmetic on the same bins, only the gather and the
+    thread layout differ."""
     rng = np.random.Generator(np.random.PCG64(31))
     kw = {}
     if case == "zero_rim_4096":
@@ -196,6 +199,12 @@ def test_tma_gather_matches_lane_gather(lib, case):
     eps = np.finfo(np.float32).eps
     for ga, gb in zip(a[0] + a[1], b[0] + b[1]):
         assert np.abs(ga - gb).max() <= 64 * eps * np.abs(ga).max()
+    if nest.n >= 1024:  # row_inv0 = 4: k_row_inv1x, walking CTAs, both parity halves per thread
+        plan.set_schedule(0, 4)
+        c = run()
+        plan.check()
+        for ga, gc in zip(a[0] + a[1], c[0] + c[1]):
+            assert np.abs(ga - gc).max() <= 64 * eps * np.abs(ga).max()
 
 
 def test_tma_schedule_falls_back_where_it_cannot_apply(lib):
@@ -223,9 +232,10 @@ def test_tma_schedule_falls_back_where_it_cannot_apply(lib):
     # not available: FP64, BF16X, two level-0 patches
     for p in (lib.Plan(nest, "fp64"), lib.Plan(nest, "bf16x"),
               lib.Plan(W.Forest(n=512, level=[0, 0], org=[(0, 0), (512, 0)]), "fp32")):
-        with pytest.raises(lib.SgfError) as ei:
-            p.set_schedule(0, 3)
-        assert ei.value.status == lib.SGF_EUNSUPPORTED
+        for inv in (3, 4):
+            with pytest.raises(lib.SgfError) as ei:
+                p.set_schedule(0, inv)
+            assert ei.value.status == lib.SGF_EUNSUPPORTED
 
 
 @pytest.mark.parametrize("n", [512, 1024])

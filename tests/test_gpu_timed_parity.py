@@ -91,13 +91,15 @@ def sample(n):
 def schedules(n, prec, zero_rim):
     """Every (col_pass, row_inv0) the plan accepts (sgf.h: schedule rules)."""
     cols = ((0, 1, 2, 3) if prec == "fp32" and n >= 1024 else (0, 1, 2)) if zero_rim else (0, 2)
-    invs = (0, 1, 2, 3)
+    invs = (0, 1, 2, 3, 4)
     out = []
     for c in cols:
         for i in invs:
             if c == 2 and not zero_rim and (prec != "fp32" or n < 512):
                 continue
             if i == 3 and (prec != "fp32" or n < 512):
+                continue
+            if i == 4 and (prec != "fp32" or n < 1024):
                 continue
             if prec == "bf16x" and n == 4096 and (c == 2 or i == 1):
                 continue
@@ -144,15 +146,16 @@ def test_4096_autotuned_plan_against_oracle(lib, prec, zero_rim):
     assert s.rel_err(gx[0], gy[0]) <= tol(prec, 4096)
 
 
-@pytest.mark.parametrize("col_pass", [2, 3])
-def test_4096_timed_schedule_explicitly(lib, col_pass):
+@pytest.mark.parametrize("col_pass,row_inv0", [(2, 3), (3, 3), (3, 4)])
+def test_4096_timed_schedule_explicitly(lib, col_pass, row_inv0):
     """Zero-rim FP32 with the level-0 inverse rows gathered by the tensor memory
-    accelerator (k_row_inv1t) behind either walking column pass (k_col_mw,
-    k_col_mx), the candidates the benchmark's autotuner chooses from, solved
-    twice (the second solve runs on the first one's leftover intermediates)."""
+    accelerator (k_row_inv1t, k_row_inv1x) behind either walking column pass
+    (k_col_mw, k_col_mx), the candidates the benchmark's autotuner chooses
+    from, solved twice (the second solve runs on the first one's leftover
+    intermediates)."""
     s = sample(4096)
     plan = lib.Plan(s.nest, "fp32", zero_rim=True)
-    plan.set_schedule(col_pass, 3)
+    plan.set_schedule(col_pass, row_inv0)
     for _ in range(2):
         gx, gy = run_gpu(plan, s.sigma)
         plan.check()
