@@ -49,7 +49,7 @@ extern "C" {
 #endif
 
 #define SGF_MAX_LEVELS 8
-#define SGF_MIN_N 16
+#define SGF_MIN_N 8
 #define SGF_MAX_N 4096        /* SGF_FP32 / SGF_BF16X */
 #define SGF_MAX_N_FP64 2048   /* SGF_FP64 */
 
@@ -74,8 +74,14 @@ typedef enum {
 } sgf_precision;
 
 /* Nest descriptor (Sec. 2.1: nested domains Omega^l, one patch per level,
- * refinement ratio 2).  n: cells per side on every level, a power of two in
- * [SGF_MIN_N, SGF_MAX_N]; levels in [1, SGF_MAX_LEVELS] with 2^(levels-1) <= n/2;
+ * refinement ratio 2).  n: cells per side on every level, even, in
+ * [SGF_MIN_N, SGF_MAX_N] (SGF_MAX_N_FP64 for SGF_FP64).  The transforms run at
+ * the transform size, the smallest power of two >= max(n, 16); when n is below
+ * it every patch runs embedded in an array of that size, zero beyond its n
+ * cells, with its slopes one-sided on its own edges, and the solve pads and
+ * crops the caller's n x n arrays (the convolution is zero-padded to twice the
+ * transform size, so the result is the same discrete sum).  levels in
+ * [1, SGF_MAX_LEVELS] with 2^(levels-1) <= n/2;
  * off[l] (l >= 1): (x, y) offset of level l's corner in level-(l-1) cells,
  * 0 <= off <= n/2 so the child lies inside its parent; off[0] is ignored. */
 typedef struct {
@@ -87,8 +93,9 @@ typedef struct {
 
 /* Forest descriptor (Sec. 2.1: domains Omega^l_k, K^l patches on level l, all
  * patches of a level sharing its cell size h0/2^l; Examples 3-4 of Sec. 3).
- * Every patch has n x n cells (n as for nests: one transform size serves the
- * whole plan); patch p is of level level[p] and its lower-left corner lies at
+ * Every patch has n x n cells (n as for nests, embedded likewise when it is not
+ * a power of two: one transform size serves the whole plan); patch p is of
+ * level level[p] and its lower-left corner lies at
  * (x0, y0) + org[p] cells of that level.  Rules (checked; SGF_EINVAL otherwise):
  *   - 1 <= patches <= SGF_MAX_PATCHES, listed coarsest first: level[0] = 0,
  *     levels never decrease and never skip one, 2^level <= n/2;
@@ -254,7 +261,12 @@ sgf_status sgf_solve_potential(sgf_plan *plan, const void *const *sigma, void *c
 sgf_status sgf_solve_host(sgf_plan *plan, const void *const *sigma, void *const *fx,
                           void *const *fy, void *stream);
 
-/* Solve `count` independent nests on one stream, one nest after the other
+/* (Plans whose n is below their transform size -- n not a power of two, or 8 --
+ * solve through sgf_solve, sgf_solve_potential and sgf_solve_host; batches and
+ * sgf_solve_noalloc refuse them with SGF_EUNSUPPORTED: their staging belongs
+ * to the plan.)
+ *
+ * Solve `count` independent nests on one stream, one nest after the other
  * (sgf_solve for each).  sigma[k], fx[k], fy[k] are the per-level device
  * pointer arrays of nest k; plans must be distinct and share one precision.
  * For fused launches over many nests use sgf_batch_*. */
@@ -395,12 +407,19 @@ sgf_status sgf_solve_noalloc(sgf_plan *plan, const void *const *sigma, void *con
  *     target) pair in one cluster per column, the source's forward column
  *     transforms done once for all of them; 1 = one cluster per phase output,
  *     each transforming the source again.
+ *   col_radix, inv_radix: the radix plan of the n-point transforms of the
+ *     col_pass = 3 and row_inv0 = 4 kernels (0 for every other choice): 0 =
+ *     radix-16 stages closed by one radix-2/4/8 stage where 16 does not divide
+ *     n (1024 = 16.16.4, 2048 = 16.16.8, 4096 = 16.16.16); 1 = the small stage
+ *     first (4.16.16, 8.16.16) or, at n = 4096, four radix-8 stages (8.8.8.8).
  * A new plan starts from {0, 0, 0}, or from the schedule the autotuner recorded for
  * its key (device, n, precision, zero-rim, levels > 1); sgf_plan_share copies it. */
 typedef struct {
     int32_t col_pass;
     int32_t row_inv0;
     int32_t col_case3;
+    int32_t col_radix;   /* radix plan of the col_pass = 3 kernel (0 otherwise) */
+    int32_t inv_radix;   /* radix plan of the row_inv0 = 4 kernel (0 otherwise) */
 } sgf_schedule;
 
 /* The plan's current schedule.  Errors: SGF_EINVAL for a NULL argument. */
@@ -410,7 +429,8 @@ sgf_status sgf_plan_schedule_get(const sgf_plan *plan, sgf_schedule *schedule);
  * n = SGF_MAX_N (those kernels have no shared memory left for the tensor-core
  * tiles there), col_pass = 3 outside zero-rim SGF_FP32 force plans of
  * n >= 1024, row_inv0 = 2 on a potential plan, row_inv0 = 3 or 4 where it
- * does not apply (the autotuner skips all of these). */
+ * does not apply, a radix plan 1 without its register-twiddle kernel (the
+ * autotuner skips all of these). */
 sgf_status sgf_plan_schedule_set(sgf_plan *plan, const sgf_schedule *schedule);
 
 /* The autotuner: runs one solve on zero density (temporary device buffers),
@@ -419,14 +439,15 @@ sgf_status sgf_plan_schedule_set(sgf_plan *plan, const sgf_schedule *schedule);
  * `stream` -- keeps the fastest in the plan and records it for later plans of
  * the same key: in the process, and in the text file named by the environment
  * variable SGF_AUTOTUNE_CACHE if it is set (one line "<key> <col_pass>
- * <row_inv0> <col_case3>" per key, read once, rewritten after each tuning).  chosen (may be
- * NULL) receives the schedule; ms (may be NULL, else SGF_AUTOTUNE_TIMES
- * doubles) the mean milliseconds per launch of col_pass 0, 1, 2, row_inv0 0, 1,
- * 2, col_case3 0, 1, row_inv0 3, col_pass 3, row_inv0 4 (-1 where a candidate
- * does not apply).  Blocks
+ * <row_inv0> <col_case3> <col_radix> <inv_radix>" per key, read once, rewritten
+ * after each tuning).  chosen (may be NULL) receives the schedule; ms (may be
+ * NULL, else SGF_AUTOTUNE_TIMES doubles) the mean milliseconds per launch of
+ * col_pass 0, 1, 2, row_inv0 0, 1, 2, col_case3 0, 1, row_inv0 3, col_pass 3,
+ * row_inv0 4, col_pass 3 with radix plan 1, row_inv0 4 with radix plan 1 (-1
+ * where a candidate does not apply).  Blocks
  * until done.
  * Errors: SGF_EINVAL, SGF_ENOMEM, SGF_ECUDA. */
-#define SGF_AUTOTUNE_TIMES 11
+#define SGF_AUTOTUNE_TIMES 13
 sgf_status sgf_plan_autotune(sgf_plan *plan, int32_t reps, void *stream, sgf_schedule *chosen, double *ms);
 
 /* Device memory a plan for this nest would hold, computed on the host without

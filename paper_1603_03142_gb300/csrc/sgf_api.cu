@@ -102,6 +102,7 @@ struct Spectra {
     void *dev = nullptr;   // all sets, one allocation
     size_t bytes = 0;
     void *tw = nullptr;    // twiddle area (TwLayout) in the solve precision
+    void *twn = nullptr;   // W_N^i, i < N, in the solve precision (register-twiddle kernels)
     int tw_entries = 0;
     double plan_ms = 0.0;
 };
@@ -114,6 +115,7 @@ void spectra_release(Spectra *s)
         cudaSetDevice(s->device);
         cudaFree(s->dev);
         cudaFree(s->tw);
+        cudaFree(s->twn);
         cudaSetDevice(cur);
         delete s;
     }
@@ -151,7 +153,15 @@ struct sgf_plan {
     alignas(64) unsigned char tmap_inv[128] = {};  // its tensor map over the level-0 main column output
     int *d_status = nullptr;   // device status word (STATUS_* bits)
     cudaEvent_t done = nullptr;  // recorded after every solve (sgf_plan_check)
-    int N = 0, logN = 0, L = 0, device = 0;  // L: patches (the levels of a nest)
+    int N = 0, logN = 0, L = 0, device = 0;  // L: patches (the levels of a nest); N: transform size
+    // cells a side of every patch (the descriptor's n).  When it is below the
+    // transform size N (n not a power of two, or 8), each patch runs embedded in
+    // an N x N array: zero density beyond its n cells, its slopes one-sided on
+    // its own edges, and the solve pads the caller's n x n arrays into d_io and
+    // crops the forces back (the convolution stays zero-padded to 2N >= 2n, so
+    // nothing wraps around)
+    int n_log = 0;
+    void *d_io = nullptr;
     size_t esize = 4;  // bytes per real
     Spectra *spec = nullptr;
     // host lists
@@ -261,6 +271,17 @@ sgf_status check_flags(int patches, uint32_t flags)
     return SGF_OK;
 }
 
+// Transform size of a plan whose patches have n cells a side: the smallest
+// power of two >= max(n, SGF_MIN_TRANSFORM_N).  A patch of fewer cells runs
+// embedded in it, zero beyond its n cells (see sgf_plan::n_log).
+int transform_n(int n)
+{
+    int N = 16;
+    while (N < n)
+        N <<= 1;
+    return N;
+}
+
 sgf_status validate(const sgf_nest_desc *d, sgf_precision prec)
 {
     if (!d)
@@ -268,8 +289,8 @@ sgf_status validate(const sgf_nest_desc *d, sgf_precision prec)
     if (prec != SGF_FP64 && prec != SGF_FP32 && prec != SGF_BF16X)
         return fail(SGF_EINVAL, "unknown precision %d", (int)prec);
     const int n = d->n;
-    if (n < SGF_MIN_N || (n & (n - 1)) != 0)
-        return fail(SGF_EINVAL, "n = %d must be a power of two >= %d", n, SGF_MIN_N);
+    if (n < SGF_MIN_N || (n & 1) != 0)
+        return fail(SGF_EINVAL, "n = %d must be even and >= %d", n, SGF_MIN_N);
     if (d->levels < 1 || d->levels > SGF_MAX_LEVELS)
         return fail(SGF_EINVAL, "levels = %d outside [1, %d]", d->levels, SGF_MAX_LEVELS);
     if ((1 << (d->levels - 1)) > n / 2)
@@ -285,8 +306,8 @@ sgf_status validate(const sgf_nest_desc *d, sgf_precision prec)
         return fail(SGF_EUNSUPPORTED, "n = %d above SGF_MAX_N = %d", n, SGF_MAX_N);
     if (prec == SGF_FP64 && n > SGF_MAX_N_FP64)
         return fail(SGF_EUNSUPPORTED, "n = %d above SGF_MAX_N_FP64 = %d", n, SGF_MAX_N_FP64);
-    if (prec == SGF_BF16X && n == SGF_MAX_N && d->levels > 1)
-        return fail(SGF_EUNSUPPORTED, "SGF_BF16X nests (levels > 1) need n < %d", SGF_MAX_N);
+    if (prec == SGF_BF16X && transform_n(n) == SGF_MAX_N && d->levels > 1)
+        return fail(SGF_EUNSUPPORTED, "SGF_BF16X nests (levels > 1) need n <= %d", SGF_MAX_N / 2);
     return SGF_OK;
 }
 
@@ -335,8 +356,8 @@ sgf_status validate_forest(const sgf_forest_desc *d, sgf_precision prec, Forest 
     if (prec != SGF_FP64 && prec != SGF_FP32 && prec != SGF_BF16X)
         return fail(SGF_EINVAL, "unknown precision %d", (int)prec);
     const int n = d->n, K = d->patches;
-    if (n < SGF_MIN_N || (n & (n - 1)) != 0)
-        return fail(SGF_EINVAL, "n = %d must be a power of two >= %d", n, SGF_MIN_N);
+    if (n < SGF_MIN_N || (n & 1) != 0)
+        return fail(SGF_EINVAL, "n = %d must be even and >= %d", n, SGF_MIN_N);
     if (K < 1 || K > SGF_MAX_PATCHES)
         return fail(SGF_EINVAL, "patches = %d outside [1, %d]", K, SGF_MAX_PATCHES);
     if (!(d->h0 > 0.0) || !std::isfinite(d->h0) || !std::isfinite(d->x0) || !std::isfinite(d->y0))
@@ -377,8 +398,8 @@ sgf_status validate_forest(const sgf_forest_desc *d, sgf_precision prec, Forest 
         return fail(SGF_EUNSUPPORTED, "n = %d above SGF_MAX_N = %d", n, SGF_MAX_N);
     if (prec == SGF_FP64 && n > SGF_MAX_N_FP64)
         return fail(SGF_EUNSUPPORTED, "n = %d above SGF_MAX_N_FP64 = %d", n, SGF_MAX_N_FP64);
-    if (prec == SGF_BF16X && n == SGF_MAX_N && K > 1)
-        return fail(SGF_EUNSUPPORTED, "SGF_BF16X plans of more than one patch need n < %d", SGF_MAX_N);
+    if (prec == SGF_BF16X && transform_n(n) == SGF_MAX_N && K > 1)
+        return fail(SGF_EUNSUPPORTED, "SGF_BF16X plans of more than one patch need n <= %d", SGF_MAX_N / 2);
     if (out) {
         Forest f;
         f.n = n;
@@ -862,7 +883,8 @@ void plan_free_owned(sgf_plan *p)
     p->d_partial = nullptr;
     cudaFree(p->d_window);
     cudaFree(p->d_gen);
-    p->d_window = p->d_gen = nullptr;
+    cudaFree(p->d_io);
+    p->d_window = p->d_gen = p->d_io = nullptr;
     cudaFree(p->d_status);
     if (p->done)
         cudaEventDestroy(p->done);
@@ -882,6 +904,13 @@ size_t align_push(std::vector<unsigned char> &blob, const std::vector<X> &v)
     return off;
 }
 
+// Embedding staging of a plan whose n is below its transform size: the padded
+// densities and the forces (or the potential) of every patch, N x N each.
+size_t io_stage_bytes(const sgf_plan *p)
+{
+    return p->n_log == p->N ? 0 : (size_t)(p->pot ? 2 : 3) * p->L * p->N * p->N * p->esize;
+}
+
 // Device bytes plan_alloc_owned allocates for p (lists, intermediates, restricted densities).
 size_t workspace_of(const sgf_plan *p)
 {
@@ -897,7 +926,8 @@ size_t workspace_of(const sgf_plan *p)
     align_push(blob, p->sums);
     align_push(blob, p->work_stream);
     return blob.size() + p->partial_elems * 2 * p->esize + (p->fwd_elems + p->bwd_elems) * 2 * p->esize +
-           (size_t)p->restricted * p->N * p->N * p->esize + (p->streamed ? gen_bytes_of(p->N) : 0);
+           (size_t)p->restricted * p->N * p->N * p->esize + (p->streamed ? gen_bytes_of(p->N) : 0) +
+           io_stage_bytes(p);
 }
 
 // Tensor map of the level-0 patch's main column output (the first output, N
@@ -992,6 +1022,9 @@ sgf_status plan_alloc_owned(sgf_plan *p)
         if ((e = cudaMalloc(&p->d_restricted, (size_t)p->restricted * p->N * p->N * p->esize)) != cudaSuccess)
             return cuda_fail(e, "cudaMalloc(restricted densities)");
     }
+    if (p->n_log != p->N &&
+        (e = cudaMalloc(&p->d_io, io_stage_bytes(p))) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(embedding staging)");
     if ((e = cudaMalloc(&p->d_status, 16)) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc(status word)");
     if ((e = memset_landed(p->d_status, 0, 16)) != cudaSuccess)
@@ -1081,6 +1114,17 @@ sgf_status build_spectra(sgf_plan *p)
         return cuda_fail(e, "cudaMalloc(twiddles)");
     if ((e = upload_landed(sp->tw, twT.data(), tl.entries * sizeof(C))) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpy(twiddles)");
+    {  // the full table W_N^i = W_P^{2i} of the register-twiddle kernels
+        std::vector<C> twn(N);
+        for (int i = 0; i < N; ++i) {
+            twn[i].x = (T)re[2 * i];
+            twn[i].y = (T)im[2 * i];
+        }
+        if ((e = cudaMalloc(&sp->twn, N * sizeof(C))) != cudaSuccess)
+            return cuda_fail(e, "cudaMalloc(twiddle table)");
+        if ((e = upload_landed(sp->twn, twn.data(), N * sizeof(C))) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpy(twiddle table)");
+    }
     sp->bytes = p->streamed ? p->resident_bytes : spectra_total(p);  // a streamed plan: its resident sets
     if ((e = cudaMalloc(&sp->dev, sp->bytes)) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc(kernel spectra)");
@@ -1141,14 +1185,15 @@ sgf_status mark(sgf_plan *p, cudaStream_t st)
 // patch through k_row_inv; row_inv0 = 3: as 0 with the level-0 gather by the
 // tensor memory accelerator (k_row_inv1t; a.tmap_inv set).
 template <typename T>
-cudaError_t launch_row_inv(int logN, int L, int R, SolveArgs<T> a, cudaStream_t st, bool tc, int row_inv0)
+cudaError_t launch_row_inv(int logN, int L, int R, SolveArgs<T> a, cudaStream_t st, bool tc, int row_inv0,
+                           int inv_radix = 0)
 {
     a.level_base = 0;
     if (row_inv0 == 1)
         return launch_pass_n<T>(PASS_ROW_INV, logN, a, L, st, nullptr, tc);
     const int first = row_inv0 == 2   ? PASS_ROW_INV2
                       : row_inv0 == 3 ? PASS_ROW_INV1T
-                      : row_inv0 == 4 ? PASS_ROW_INV1X
+                      : row_inv0 == 4 ? (inv_radix ? PASS_ROW_INV1X_R1 : PASS_ROW_INV1X)
                                       : PASS_ROW_INV1;
     cudaError_t e = launch_pass_n<T>(first, logN, a, R, st, nullptr, tc);
     if (e != cudaSuccess || L == R)
@@ -1162,7 +1207,7 @@ inline int col_m_pass(const sgf_plan *p)
 {
     return p->sched.col_pass == 1   ? PASS_COL_MD
            : p->sched.col_pass == 2 ? PASS_COL_MW
-           : p->sched.col_pass == 3 ? PASS_COL_MX
+           : p->sched.col_pass == 3 ? (p->sched.col_radix ? PASS_COL_MX_R1 : PASS_COL_MX)
                                     : PASS_COL_M;
 }
 
@@ -1233,6 +1278,10 @@ inline bool schedule_ok(const sgf_plan *p, const sgf_schedule &s)
     // k_row_inv1x: the tensor-map gather (row_inv0 = 3's conditions) with n >= 1024
     if (s.row_inv0 == 4 && !(p->tma_inv && p->N >= 1024))
         return false;
+    // radix plans: the register-twiddle kernels only (col_pass 3, row_inv0 4)
+    if ((s.col_radix != 0 && (s.col_radix != 1 || s.col_pass != 3)) ||
+        (s.inv_radix != 0 && (s.inv_radix != 1 || s.row_inv0 != 4)))
+        return false;
     // k_col_mx: zero-rim forces, FP32 without tensor-core tiles, N >= 1024
     if (s.col_pass == 3 && !(p->merged && !p->pot && p->prec == SGF_FP32 && p->N >= 1024))
         return false;
@@ -1253,6 +1302,7 @@ void fill_geometry(const sgf_plan *p, SolveArgs<T> &a)
 {
     a.N = p->N;
     a.logN = p->logN;
+    a.n_log = p->n_log;
     a.L = p->L;
     a.ncomp = p->pot ? 1 : 2;
     for (int s = 0; s <= p->L; ++s) {
@@ -1287,7 +1337,7 @@ cudaError_t fill_sources(const sgf_plan *p, const void *const *sigma, T *restric
 }
 
 template <typename T>
-sgf_status solve_impl(sgf_plan *p, const void *const *sigma, void *const *fx, void *const *fy,
+sgf_status solve_core(sgf_plan *p, const void *const *sigma, void *const *fx, void *const *fy,
                       cudaStream_t st)
 {
     const int L = p->L;
@@ -1307,6 +1357,7 @@ sgf_status solve_impl(sgf_plan *p, const void *const *sigma, void *const *fx, vo
     a.bwd = static_cast<typename SolveArgs<T>::C *>(p->d_bwd);
     a.spec = p->spec->dev;
     a.tw = static_cast<const typename SolveArgs<T>::C *>(p->spec->tw);
+    a.twn = static_cast<const typename SolveArgs<T>::C *>(p->spec->twn);
     a.tw_entries = p->spec->tw_entries;
     a.status = p->d_status;
     a.inject = (int)p->inject;  // a test's one-shot injection (sgf_plan_inject_timeout)
@@ -1336,10 +1387,52 @@ sgf_status solve_impl(sgf_plan *p, const void *const *sigma, void *const *fx, vo
         return cuda_fail(e, "col launch");
     if ((ms = mark(p, st)) != SGF_OK)
         return ms;
-    if ((e = launch_row_inv<T>(p->logN, L, p->fo.R, a, st, p->tc, p->sched.row_inv0)) != cudaSuccess)
+    if ((e = launch_row_inv<T>(p->logN, L, p->fo.R, a, st, p->tc, p->sched.row_inv0, p->sched.inv_radix)) !=
+        cudaSuccess)
         return cuda_fail(e, "row_inv launch");
-    if ((ms = mark(p, st)) != SGF_OK)
-        return ms;
+    return mark(p, st);
+}
+
+// A solve: the caller's arrays directly, or (n below the transform size)
+// padded into the plan's staging, solved there, and the forces cropped back.
+template <typename T>
+sgf_status solve_impl(sgf_plan *p, const void *const *sigma, void *const *fx, void *const *fy,
+                      cudaStream_t st)
+{
+    sgf_status s;
+    cudaError_t e;
+    if (p->n_log == p->N) {
+        s = solve_core<T>(p, sigma, fx, fy, st);
+    } else {
+        const size_t NN = (size_t)p->N * p->N;
+        T *io = static_cast<T *>(p->d_io);
+        IoPtrs<T> pad{}, cx{}, cy{};
+        const void *ss[kMaxPatches];
+        void *sx[kMaxPatches], *sy[kMaxPatches];
+        for (int l = 0; l < p->L; ++l) {
+            ss[l] = io + l * NN;
+            sx[l] = io + (p->L + l) * NN;
+            sy[l] = fy ? io + (2 * p->L + l) * NN : nullptr;
+            pad.src[l] = static_cast<const T *>(sigma[l]);
+            pad.dst[l] = io + l * NN;
+            cx.src[l] = io + (p->L + l) * NN;
+            cx.dst[l] = static_cast<T *>(fx[l]);
+            if (fy) {
+                cy.src[l] = io + (2 * p->L + l) * NN;
+                cy.dst[l] = static_cast<T *>(fy[l]);
+            }
+        }
+        if ((e = launch_pad<T>(pad, p->L, p->n_log, p->N, st)) != cudaSuccess)
+            return cuda_fail(e, "embedding pad launch");
+        s = solve_core<T>(p, ss, sx, fy ? sy : nullptr, st);
+        if (s != SGF_OK)
+            return s;
+        if ((e = launch_crop<T>(cx, p->L, p->n_log, p->N, st)) != cudaSuccess ||
+            (fy && (e = launch_crop<T>(cy, p->L, p->n_log, p->N, st)) != cudaSuccess))
+            return cuda_fail(e, "embedding crop launch");
+    }
+    if (s != SGF_OK)
+        return s;
     if ((e = cudaEventRecord(p->done, st)) != cudaSuccess)
         return cuda_fail(e, "cudaEventRecord(solve completion)");
     return SGF_OK;
@@ -1450,6 +1543,7 @@ sgf_status solve_noalloc_impl(sgf_plan *p, const void *const *sigma, void *const
     a.bwd = reinterpret_cast<typename SolveArgs<T>::C *>(bwd);
     a.spec = p->spec->dev;
     a.tw = static_cast<const typename SolveArgs<T>::C *>(p->spec->tw);
+    a.twn = static_cast<const typename SolveArgs<T>::C *>(p->spec->twn);
     a.tw_entries = p->spec->tw_entries;
     a.status = p->d_status;
     a.slabs = p->d_slabs;
@@ -1496,6 +1590,7 @@ void fill_args(const sgf_plan *p, const void *const *sigma, void *const *fx, voi
     a.bwd = static_cast<typename SolveArgs<T>::C *>(p->d_bwd);
     a.spec = p->spec->dev;
     a.tw = static_cast<const typename SolveArgs<T>::C *>(p->spec->tw);
+    a.twn = static_cast<const typename SolveArgs<T>::C *>(p->spec->twn);
     a.tw_entries = p->spec->tw_entries;
     a.status = p->d_status;
     a.slabs = p->d_slabs;
@@ -1531,39 +1626,44 @@ sgf_status batch_launches(sgf_batch *bt, cudaStream_t st)
             cudaSuccess)
             return cuda_fail(e, "batched restriction launch");
     SolveArgs<T> dummy{};
-    for (const auto &g : bt->groups) {
+    // The groups run one after the other on the solve's stream.  Forking them onto
+    // streams of their own (parallel branches of the graph) measured slower: 256
+    // nests 274 -> 326 ms per batch, the groups' kernels contending for the SMs.
+    for (size_t gi = 0; gi < bt->groups.size(); ++gi) {
+        const auto &g = bt->groups[gi];
+        cudaStream_t gs = st;
         BatchView<T> vf{args, bt->d_maps + g.map_fwd}, vc{args, bt->d_maps + g.map_col};
         BatchView<T> vi1{args, bt->d_maps + g.map_inv1}, vi{args, bt->d_maps + g.map_inv};
         dummy.N = 1 << g.logN;
-        if ((e = launch_pass_n<T>(g.merged ? PASS_ROW_FWD_M : PASS_ROW_FWD, g.logN, dummy, g.n_fwd, st, &vf, g.tc)) != cudaSuccess)
+        if ((e = launch_pass_n<T>(g.merged ? PASS_ROW_FWD_M : PASS_ROW_FWD, g.logN, dummy, g.n_fwd, gs, &vf, g.tc)) != cudaSuccess)
             return cuda_fail(e, "batched row_fwd launch");
         const int colp = !g.merged              ? (g.sched.col_pass == 2 ? PASS_COL_W : PASS_COL)
                          : g.sched.col_pass == 1 ? PASS_COL_MD
                          : g.sched.col_pass >= 2 ? PASS_COL_MW  // k_col_mx has no batch form
                                                  : PASS_COL_M;
-        if ((e = launch_pass_n<T>(colp, g.logN, dummy, g.n_col, st, &vc, g.tc)) != cudaSuccess)
+        if ((e = launch_pass_n<T>(colp, g.logN, dummy, g.n_col, gs, &vc, g.tc)) != cudaSuccess)
             return cuda_fail(e, "batched col launch");
         if (g.n_grp > 0) {
             BatchView<T> vg{args, bt->d_maps + g.map_grp};
             const int grp = !g.merged && g.sched.col_pass == 2 && g.logN <= 11 ? PASS_COL_GW : PASS_COL_G;
-            if ((e = launch_pass_n<T>(grp, g.logN, dummy, g.n_grp, st, &vg, g.tc)) != cudaSuccess)
+            if ((e = launch_pass_n<T>(grp, g.logN, dummy, g.n_grp, gs, &vg, g.tc)) != cudaSuccess)
                 return cuda_fail(e, "batched Case-3 group launch");
         }
         if (g.n_sum > 0) {
             BatchView<T> vs{args, bt->d_maps + g.map_sum};
-            if ((e = launch_pass_n<T>(PASS_COL_SUM, g.logN, dummy, g.n_sum, st, &vs, g.tc)) != cudaSuccess)
+            if ((e = launch_pass_n<T>(PASS_COL_SUM, g.logN, dummy, g.n_sum, gs, &vs, g.tc)) != cudaSuccess)
                 return cuda_fail(e, "batched chunk-sum launch");
         }
         if (g.sched.row_inv0 == 1) {  // every level through k_row_inv (level-0 entries precede the others)
-            if ((e = launch_pass_n<T>(PASS_ROW_INV, g.logN, dummy, g.n_inv1 + g.n_inv, st, &vi1, g.tc)) != cudaSuccess)
+            if ((e = launch_pass_n<T>(PASS_ROW_INV, g.logN, dummy, g.n_inv1 + g.n_inv, gs, &vi1, g.tc)) != cudaSuccess)
                 return cuda_fail(e, "batched row_inv launch");
-            continue;
+        } else {
+            if ((e = launch_pass_n<T>(g.sched.row_inv0 == 2 ? PASS_ROW_INV2 : PASS_ROW_INV1, g.logN, dummy, g.n_inv1,
+                                      gs, &vi1, g.tc)) != cudaSuccess)
+                return cuda_fail(e, "batched row_inv1 launch");
+            if (g.n_inv > 0 && (e = launch_pass_n<T>(PASS_ROW_INV, g.logN, dummy, g.n_inv, gs, &vi, g.tc)) != cudaSuccess)
+                return cuda_fail(e, "batched row_inv launch");
         }
-        if ((e = launch_pass_n<T>(g.sched.row_inv0 == 2 ? PASS_ROW_INV2 : PASS_ROW_INV1, g.logN, dummy, g.n_inv1, st,
-                                  &vi1, g.tc)) != cudaSuccess)
-            return cuda_fail(e, "batched row_inv1 launch");
-        if (g.n_inv > 0 && (e = launch_pass_n<T>(PASS_ROW_INV, g.logN, dummy, g.n_inv, st, &vi, g.tc)) != cudaSuccess)
-            return cuda_fail(e, "batched row_inv launch");
     }
     return SGF_OK;
 }
@@ -1579,6 +1679,7 @@ void batch_free(sgf_batch *bt)
         cudaStreamDestroy(bt->capture_stream);
     if (bt->uploaded)
         cudaEventDestroy(bt->uploaded);
+
     cudaFree(bt->d_args);
     cudaFree(bt->d_maps);
     cudaFreeHost(bt->h_args);
@@ -1761,7 +1862,8 @@ std::string tune_key(const sgf_plan *p)
     return buf;
 }
 
-// Load the table file named by SGF_AUTOTUNE_CACHE once (lines "<key> <col_pass> <row_inv0>").
+// Load the table file named by SGF_AUTOTUNE_CACHE once (lines "<key> <col_pass> <row_inv0>
+// <col_case3> <col_radix> <inv_radix>").
 void tune_load_locked()
 {
     if (g_tune_loaded)
@@ -1774,10 +1876,10 @@ void tune_load_locked()
     if (!f)
         return;
     char key[160];
-    int a = 0, b = 0, c = 0;
-    while (fscanf(f, "%159s %d %d %d", key, &a, &b, &c) == 4)
-        if (a >= 0 && a <= 3 && b >= 0 && b <= 4 && (c == 0 || c == 1))
-            g_tune[key] = sgf_schedule{a, b, c};
+    int a = 0, b = 0, c = 0, d = 0, r = 0;
+    while (fscanf(f, "%159s %d %d %d %d %d", key, &a, &b, &c, &d, &r) == 6)
+        if (a >= 0 && a <= 3 && b >= 0 && b <= 4 && (c == 0 || c == 1) && (d == 0 || d == 1) && (r == 0 || r == 1))
+            g_tune[key] = sgf_schedule{a, b, c, d, r};
     fclose(f);
 }
 
@@ -1794,7 +1896,8 @@ void tune_store(const std::string &key, const sgf_schedule &s)
     if (!f)
         return;
     for (const auto &kv : g_tune)
-        fprintf(f, "%s %d %d %d\n", kv.first.c_str(), kv.second.col_pass, kv.second.row_inv0, kv.second.col_case3);
+        fprintf(f, "%s %d %d %d %d %d\n", kv.first.c_str(), kv.second.col_pass, kv.second.row_inv0,
+                kv.second.col_case3, kv.second.col_radix, kv.second.inv_radix);
     fclose(f);
     rename(tmp.c_str(), path);
 }
@@ -1862,38 +1965,56 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[SGF_A
         ms[k] = -1.0;
     sgf_schedule best = p->sched;
     if (p->merged) {
-        static const int col_kind[4] = {PASS_COL_M, PASS_COL_MD, PASS_COL_MW, PASS_COL_MX};
-        auto col_slot = [](int c) { return c < 3 ? c : 9; };  // col_pass = 3 appended after row_inv0 = 3
-        for (int c = 0; c < 4 && s == SGF_OK; ++c) {
+        // candidates 0..3, and 4 = col_pass 3 with radix plan 1
+        static const int col_kind[5] = {PASS_COL_M, PASS_COL_MD, PASS_COL_MW, PASS_COL_MX, PASS_COL_MX_R1};
+        auto col_slot = [](int c) { return c < 3 ? c : c == 3 ? 9 : 11; };  // appended after row_inv0 = 3, 4
+        auto col_cand = [&](int c) {
             sgf_schedule cand = best;
-            cand.col_pass = c;
-            if (schedule_ok(p, cand))
+            cand.col_pass = c < 4 ? c : 3;
+            cand.col_radix = c == 4 ? 1 : 0;
+            return cand;
+        };
+        for (int c = 0; c < 5 && s == SGF_OK; ++c)
+            if (schedule_ok(p, col_cand(c)))
                 s = timeit([&] { return launch_pass_n<T>(col_kind[c], p->logN, a, 1, st, nullptr, p->tc); },
                            ms[col_slot(c)]);
-        }
         if (s == SGF_OK) {  // the fastest of the candidates that apply (and were timed)
             int bc = -1;
-            for (int c = 0; c < 4; ++c)
+            for (int c = 0; c < 5; ++c)
                 if (ms[col_slot(c)] >= 0.0 && (bc < 0 || ms[col_slot(c)] < ms[col_slot(bc)]))
                     bc = c;
-            if (bc >= 0)
-                best.col_pass = bc;
+            if (bc >= 0) {
+                const sgf_schedule ch = col_cand(bc);
+                best.col_pass = ch.col_pass;
+                best.col_radix = ch.col_radix;
+            }
         }
     }
-    auto inv_slot = [](int c) { return c < 3 ? 3 + c : c == 3 ? 8 : 10; };  // 3, 4 appended after col_case3
-    for (int c = 0; c < 5 && s == SGF_OK; ++c) {
+    // candidates 0..4, and 5 = row_inv0 4 with radix plan 1 (3, 4, 5 appended after col_case3)
+    auto inv_slot = [](int c) { return c < 3 ? 3 + c : c == 3 ? 8 : c == 4 ? 10 : 12; };
+    auto inv_cand = [&](int c) {
         sgf_schedule cand = best;
-        cand.row_inv0 = c;
+        cand.row_inv0 = c < 5 ? c : 4;
+        cand.inv_radix = c == 5 ? 1 : 0;
+        return cand;
+    };
+    for (int c = 0; c < 6 && s == SGF_OK; ++c) {
+        const sgf_schedule cand = inv_cand(c);
         if (schedule_ok(p, cand))
-            s = timeit([&] { return launch_row_inv<T>(p->logN, p->L, p->fo.R, a, st, p->tc, c); }, ms[inv_slot(c)]);
+            s = timeit([&] { return launch_row_inv<T>(p->logN, p->L, p->fo.R, a, st, p->tc, cand.row_inv0,
+                                                      cand.inv_radix); },
+                       ms[inv_slot(c)]);
     }
     if (s == SGF_OK) {  // the fastest of the candidates that apply (and were timed)
         int bc = -1;
-        for (int c = 0; c < 5; ++c)
+        for (int c = 0; c < 6; ++c)
             if (ms[inv_slot(c)] >= 0.0 && (bc < 0 || ms[inv_slot(c)] < ms[inv_slot(bc)]))
                 bc = c;
-        if (bc >= 0)
-            best.row_inv0 = bc;
+        if (bc >= 0) {
+            const sgf_schedule ch = inv_cand(bc);
+            best.row_inv0 = ch.row_inv0;
+            best.inv_radix = ch.inv_radix;
+        }
     }
     if (!p->merged && !p->streamed) {  // general column pass: a cluster per column or both halves in one CTA
         const sgf_schedule keep = p->sched;
@@ -1948,11 +2069,12 @@ void plan_init(sgf_plan *p, const Forest &fo, sgf_precision precision, uint32_t 
     p->merged = (flags & SGF_PLAN_ZERO_RIM) != 0;
     p->pot = (flags & SGF_PLAN_POTENTIAL) != 0;
     p->tc = precision == SGF_BF16X;
-    p->N = fo.n;
-    p->logN = ilog2(fo.n);
+    p->N = transform_n(fo.n);
+    p->logN = ilog2(p->N);
+    p->n_log = fo.n;
     p->L = fo.K;
     p->esize = precision == SGF_FP64 ? 8 : 4;
-    p->tma_inv = precision == SGF_FP32 && fo.n >= 512 && fo.R == 1;
+    p->tma_inv = precision == SGF_FP32 && p->N >= 512 && fo.R == 1;
     p->sched = sgf_schedule{p->merged && p->pot ? 2 : 0, 0, 0};  // the zero-rim potential runs col_pass 2
 }
 
@@ -2169,7 +2291,7 @@ sgf_status sgf_plan_stats_get(const sgf_plan *p, sgf_plan_stats *st)
 {
     if (!p || !st)
         return fail(SGF_EINVAL, "NULL argument");
-    st->n = p->N;
+    st->n = p->n_log;
     st->levels = p->L;
     st->precision = (int)p->prec;
     st->forward_slabs = (int)p->slabs.size();
@@ -2266,7 +2388,7 @@ sgf_status sgf_solve_host(sgf_plan *p, const void *const *sigma, void *const *fx
     if (s != SGF_OK)
         return s;
     DeviceGuard g(p->device);
-    const size_t lvl = (size_t)p->N * p->N * p->esize;
+    const size_t lvl = (size_t)p->n_log * p->n_log * p->esize;  // the caller's n x n arrays
     const size_t lvl_al = (lvl + 255) & ~(size_t)255;
     cudaError_t e;
     // sigma always goes through the staging by a copy: the copy engine reads
@@ -2398,7 +2520,8 @@ sgf_status sgf_plan_schedule_set(sgf_plan *p, const sgf_schedule *in)
     if (!p || !in)
         return fail(SGF_EINVAL, "NULL argument");
     if (in->col_pass < 0 || in->col_pass > 3 || in->row_inv0 < 0 || in->row_inv0 > 4 ||
-        (in->col_case3 != 0 && in->col_case3 != 1))
+        (in->col_case3 != 0 && in->col_case3 != 1) || in->col_radix < 0 || in->col_radix > 1 || in->inv_radix < 0 ||
+        in->inv_radix > 1)
         return fail(SGF_EINVAL, "schedule out of range (col_pass %d, row_inv0 %d, col_case3 %d)", in->col_pass,
                     in->row_inv0, in->col_case3);
     if (!schedule_ok(p, *in))
@@ -2406,7 +2529,7 @@ sgf_status sgf_plan_schedule_set(sgf_plan *p, const sgf_schedule *in)
                     "schedule (col_pass %d, row_inv0 %d) not available for this plan: col_pass = 2 and row_inv0 = 1 "
                     "need n < %d with SGF_BF16X, col_pass = 3 a zero-rim SGF_FP32 force plan with n >= 1024, "
                     "row_inv0 = 2 a force plan, row_inv0 = 3 SGF_FP32 with n >= 512 and one level-0 patch, "
-                    "row_inv0 = 4 the same with n >= 1024",
+                    "row_inv0 = 4 the same with n >= 1024, a radix plan 1 the register-twiddle kernel of its pass",
                     in->col_pass, in->row_inv0, SGF_MAX_N);
     p->sched = *in;
     return SGF_OK;
@@ -2456,6 +2579,9 @@ sgf_status sgf_solve_noalloc(sgf_plan *p, const void *const *sigma, void *const 
     if (p->streamed)
         return fail(SGF_EUNSUPPORTED, "sgf_solve_noalloc: the plan regenerates spectra at every solve "
                                       "(spectra budget); its window belongs to the plan");
+    if (p->n_log != p->N)
+        return fail(SGF_EUNSUPPORTED, "sgf_solve_noalloc: n = %d is solved embedded in %d x %d arrays of the plan",
+                    p->n_log, p->N, p->N);
     const size_t need = noalloc_bytes(p);
     if (need > (size_t)SGF_NOALLOC_SCRATCH_BYTES)
         return fail(SGF_EUNSUPPORTED,
@@ -2487,6 +2613,9 @@ sgf_status sgf_batch_create(sgf_plan *const *plans, int32_t count, uint32_t flag
         if (plans[k]->streamed)
             return fail(SGF_EUNSUPPORTED, "plan %d regenerates spectra at every solve (spectra budget); "
                                           "batches take plans with resident spectra", k);
+        if (plans[k]->n_log != plans[k]->N)
+            return fail(SGF_EUNSUPPORTED, "plan %d: n = %d is not a power of two >= 16; batches take those", k,
+                        plans[k]->n_log);
         if (plans[k]->prec != plans[0]->prec || plans[k]->device != plans[0]->device)
             return fail(SGF_EINVAL, "plans of one batch must share precision and device");
         for (int q = 0; q < k; ++q)

@@ -512,34 +512,63 @@ __device__ __forceinline__ void fft_ct(C (*v)[16], C *sbuf, int SP, int j, bool 
 
 // ---------------------------------------------------------------------------
 // Register-twiddle engine.  A thread that keeps one slot j for the whole life
-// of a kernel (a CTA walking many columns) holds the twiddles of its slot in
-// registers instead of reading the shared tables at every stage: stage st >= 1
-// needs W_{R Ns}^{r k} for r = 1..R-1 with k = (j + QB N/16) mod Ns for each of
-// its 16/R butterflies QB, at most 15 values.  They are the same numbers the
-// table engine forms (stage_tw: the factored product for Ns >= 256 included),
-// so both engines compute bit-identical transforms.
-template <typename C, int LOGN, int ST>
-__device__ __forceinline__ void load_stage_twiddles(C (&w)[15], const C *tw, int j)
+// of a kernel (a CTA walking many columns or row pairs) holds the twiddles of
+// its slot in registers instead of reading shared tables at every stage:
+// stage st >= 1 of radix R needs W_{R Ns}^{r k} for r = 1..R-1 with
+// k = (j + QB N/16) mod Ns for each of its 16/R butterflies QB, at most 15
+// values.  They are read once, at the start of the kernel, from the full table
+// W_N^i (i < N, built on the host in extended precision): W_{R Ns}^{r k} =
+// W_N^{r k N / (R Ns)}.
+//
+// Radix plans (the autotuner chooses): PLAN 0 runs radix-16 stages and closes
+// with one radix-2/4/8 stage when 16 does not divide the length (the table
+// engine's order); PLAN 1 puts that small stage first (n = 1024: 4.16.16,
+// 2048: 8.16.16) or, for n = 4096, runs four radix-8 stages (8.8.8.8).  Every
+// stage reads the slot pattern j + u N/16; a radix-R stage with R < 16 holds
+// 16/R butterflies per slot and writes butterfly QB's outputs, like a radix-16
+// stage writes its one butterfly's, at (jq - k) R + k + r Ns, jq = j + QB N/16.
+template <int LOGN, int PLAN>
+struct FR {
+    static constexpr int N = 1 << LOGN;
+    static constexpr int Q = N >> 4;
+    static constexpr int S16 = LOGN >> 2;
+    static constexpr int RL = 1 << (LOGN & 3);
+    static constexpr bool EIGHTS = PLAN == 1 && (LOGN & 3) == 0 && LOGN % 3 == 0;  // 4096 = 8^4 (512 = 8^3)
+    static constexpr int NST = EIGHTS ? LOGN / 3 : S16 + (RL > 1 ? 1 : 0);
+    static constexpr int radix(int st)
+    {
+        return EIGHTS ? 8 : PLAN == 0 ? (st < S16 ? 16 : RL) : (RL > 1 && st == 0 ? RL : 16);
+    }
+    static constexpr int ns(int st)
+    {
+        int n = 1;
+        for (int s = 0; s < st; ++s)
+            n *= radix(s);
+        return n;
+    }
+};
+
+template <typename C, int LOGN, int PLAN, int ST>
+__device__ __forceinline__ void load_stage_twiddles(C (&w)[15], const C *twn, int j)
 {
-    using P = F16<LOGN>;
-    constexpr int R = P::radix(ST), NS = P::ns(ST), S = 16 / R;
-    const C *tws = tw + P::twoff(ST);
+    using P = FR<LOGN, PLAN>;
+    constexpr int R = P::radix(ST), NS = P::ns(ST), S = 16 / R, N = P::N, STEP = N / (R * NS);
 #pragma unroll
     for (int qb = 0; qb < S; ++qb) {
         const int k = (j + qb * P::Q) & (NS - 1);
 #pragma unroll
         for (int r = 1; r < R; ++r)
-            w[qb * (R - 1) + r - 1] = stage_tw<C, R, NS>(tws, r, k);
+            w[qb * (R - 1) + r - 1] = twn[(r * k * STEP) & (N - 1)];
     }
 }
 
 // Twiddles of every stage after the first: w[st - 1] for st = 1 .. NST - 1.
-template <typename C, int LOGN, int ST = 1>
-__device__ __forceinline__ void load_twiddles_rt(C (*w)[15], const C *tw, int j)
+template <typename C, int LOGN, int PLAN, int ST = 1>
+__device__ __forceinline__ void load_twiddles_rt(C (*w)[15], const C *twn, int j)
 {
-    if constexpr (ST < F16<LOGN>::NST) {
-        load_stage_twiddles<C, LOGN, ST>(w[ST - 1], tw, j);
-        load_twiddles_rt<C, LOGN, ST + 1>(w, tw, j);
+    if constexpr (ST < FR<LOGN, PLAN>::NST) {
+        load_stage_twiddles<C, LOGN, PLAN, ST>(w[ST - 1], twn, j);
+        load_twiddles_rt<C, LOGN, PLAN, ST + 1>(w, twn, j);
     }
 }
 
@@ -563,18 +592,18 @@ __device__ __forceinline__ void group_sync(unsigned id, unsigned count)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-// fft_stages with the stage twiddles in registers (w, see load_twiddles_rt)
-// and the exchanges of a group of threads on its own named barrier.  B
-// sequences per thread, sequence b at sbuf + b * SP; same entry and exit
+// fft_stages with the stage twiddles in registers (w, see load_twiddles_rt), a
+// radix plan, and the exchanges of a group of threads on its own named barrier.
+// B sequences per thread, sequence b at sbuf + b * SP; same entry and exit
 // conditions as fft_stages (sbuf first written after a barrier, last stage read
 // without a closing one).
-template <typename C, bool INV, int LOGN, int B, int ST>
+template <typename C, bool INV, int LOGN, int PLAN, int B, int ST>
 __device__ __forceinline__ void fft_stages_rt(C (*v)[16], C *sbuf, int SP, int j, const C (*w)[15], unsigned bar,
                                               unsigned count)
 {
-    using P = F16<LOGN>;
+    using P = FR<LOGN, PLAN>;
     if constexpr (ST < P::NST) {
-        constexpr int Q = P::Q, NS = P::ns(ST), R = P::radix(ST);
+        constexpr int Q = P::Q, NS = P::ns(ST), R = P::radix(ST), S = 16 / R;
         if constexpr (ST > 0) {
             group_sync(bar, count);  // previous stage's stores are visible
 #pragma unroll
@@ -592,21 +621,28 @@ __device__ __forceinline__ void fft_stages_rt(C (*v)[16], C *sbuf, int SP, int j
                         v[bb][r] = INV ? hmulc(v[bb][r], w[ST - 1][r - 1]) : hmul(v[bb][r], w[ST - 1][r - 1]);
                 }
                 hdft16<C, INV>(v[bb]);
-            } else {
+            } else if constexpr (ST > 0) {
                 stage_small_rt<C, INV, R, 0>(v[bb], w[ST - 1]);
+            } else {  // a first stage: no twiddles (Ns = 1)
+                static_assert(NS == 1, "the first stage has Ns = 1");
+                stage_small_ct<C, INV, P::N, R, 1, 0>(v[bb], j, static_cast<const C *>(nullptr));
             }
         }
         if constexpr (ST + 1 < P::NST) {
             group_sync(bar, count);  // every thread has read this stage's inputs
-            const int k = j & (NS - 1);
-            const int base = (j - k) * 16 + k;
 #pragma unroll
-            for (int bb = 0; bb < B; ++bb)
+            for (int qb = 0; qb < S; ++qb) {
+                const int jq = j + qb * Q;
+                const int k = jq & (NS - 1);
+                const int base = (jq - k) * R + k;
 #pragma unroll
-                for (int r = 0; r < 16; ++r)
-                    sbuf[bb * SP + pad16(base + r * NS)] = v[bb][r];
+                for (int bb = 0; bb < B; ++bb)
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        sbuf[bb * SP + pad16(base + r * NS)] = v[bb][qb + r * S];
+            }
         }
-        fft_stages_rt<C, INV, LOGN, B, ST + 1>(v, sbuf, SP, j, w, bar, count);
+        fft_stages_rt<C, INV, LOGN, PLAN, B, ST + 1>(v, sbuf, SP, j, w, bar, count);
     }
 }
 #endif

@@ -164,7 +164,8 @@ struct FwdItem {
 template <typename T>
 struct SolveArgs {
     using C = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
-    int N, logN, L;             // L: patches (the levels of a nest)
+    int N, logN, L;             // L: patches (the levels of a nest); N: transform size
+    int n_log;                  // cells a side of every patch (<= N; beyond it the embedded arrays are 0)
     int ncomp;                  // output components: 2 (Fx, Fy) or 1 (the potential, in fx)
     int cover_begin[kMaxPatches + 1];  // covered rectangles of patch p: cover[cover_begin[p] .. cover_begin[p+1])
     CoverRect cover[kMaxCover];
@@ -176,6 +177,7 @@ struct SolveArgs {
     C *bwd;                     // column outputs
     const void *spec;           // kernel spectra (T reals / C complex)
     const C *tw;                // twiddle area (tw_layout), copied to shared memory by every CTA
+    const C *twn;               // W_N^i, i < N: the register-twiddle kernels' source
     int tw_entries;             // its length in complex entries (even)
     int *status;                // device status word of the plan (STATUS_* bits)
     long long wait_cycles;      // bound of every device wait in SM cycles; 0: about one second
@@ -260,7 +262,9 @@ enum : int {
     PASS_COL_W = 13,      // PASS_COL with both parity halves in one CTA (no tensor-core tiles, N >= 512)
     PASS_COL_GW = 14,     // PASS_COL_G likewise (FP32, 512 <= N <= 2048)
     PASS_COL_MX = 15,     // zero-rim forces: both parity halves per thread, register twiddles (FP32, N >= 1024)
-    PASS_ROW_INV1X = 16   // PASS_ROW_INV1T likewise (walking, both halves per thread; FP32, N >= 1024)
+    PASS_ROW_INV1X = 16,  // PASS_ROW_INV1T likewise (walking, both halves per thread; FP32, N >= 1024)
+    PASS_COL_MX_R1 = 17,  // PASS_COL_MX with radix plan 1 (see FR)
+    PASS_ROW_INV1X_R1 = 18  // PASS_ROW_INV1X with radix plan 1
 };
 // Batch mode of the transform passes: a block's nest and its local work index
 // come from a per-launch map (one int2 per block row), and that nest's
@@ -278,6 +282,19 @@ cudaError_t launch_pass_n(int pass, int logN, const SolveArgs<T> &a, int count, 
 
 // Build the spectra of one set into spec (element type T: float or double).
 // work_tables: spec_tables(kind)*P*P doubles; work_half: spec_tables(kind)*(N+1)*P double2.
+// Pointers of the embedding copies (k_pad, k_crop): per patch, source and destination.
+template <typename T>
+struct IoPtrs {
+    const T *src[kMaxPatches];
+    T *dst[kMaxPatches];
+};
+// n x n arrays -> N x N arrays, zero beyond the n cells (every patch of L).
+template <typename T>
+cudaError_t launch_pad(const IoPtrs<T> &io, int L, int n, int N, cudaStream_t st);
+// N x N arrays -> their first n x n cells (every patch of L).
+template <typename T>
+cudaError_t launch_crop(const IoPtrs<T> &io, int L, int n, int N, cudaStream_t st);
+
 template <typename T>
 cudaError_t launch_gen_set(const GenSet &g, int N, int logN, const double2 *tw64, void *spec,
                            double *work_tables, double2 *work_half, cudaStream_t st);

@@ -186,6 +186,7 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, sizeof(T) == 4 && !
     const int ja = sl.m * r0 + sl.py, jb = sl.m * (r0 + 1) + sl.py;
     const T *src = a.src[sl.patch];
     cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
+    const int nl = a.n_log;  // the patch's own cells a side (<= N; zero beyond, slopes one-sided on its edges)
     if (f < 2) {
         cp_block(srow, src + (size_t)ja * N, (size_t)N * sizeof(T));
         cp_block(srow + N, src + (size_t)jb * N, (size_t)N * sizeof(T));
@@ -193,8 +194,8 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, sizeof(T) == 4 && !
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int jj = q < 2 ? ja : jb;
-            const int jr = (q & 1) ? min(jj + 1, N - 1) : max(jj - 1, 0);
-            cp_block(srow + q * N, src + (size_t)jr * N, (size_t)N * sizeof(T));
+            const int jr = (q & 1) ? min(jj + 1, nl - 1) : max(jj - 1, 0);
+            cp_block(srow + q * N, src + (size_t)min(jr, N - 1) * N, (size_t)N * sizeof(T));
         }
     }
     cp_commit();
@@ -215,18 +216,18 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, sizeof(T) == 4 && !
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int jj = h ? jb : ja;
-                    if (covered(a, sl.patch, jj, i))
+                    if (i >= nl || jj >= nl || covered(a, sl.patch, jj, i))
                         continue;
                     if (f == 0) {
                         fv[h] = srow[h * N + i];
                     } else if (f == 1) {
                         const T *r = srow + h * N;
-                        const int il = i == 0 ? 0 : i - 1, ir = i == N - 1 ? N - 1 : i + 1;
+                        const int il = i == 0 ? 0 : i - 1, ir = i == nl - 1 ? nl - 1 : i + 1;
                         const T d = r[ir] - r[il];
                         fv[h] = (ir - il == 2) ? T(0.5) * d : d;
                     } else {
                         const T d = srow[(2 * h + 1) * N + i] - srow[2 * h * N + i];
-                        fv[h] = (jj == 0 || jj == N - 1) ? d : T(0.5) * d;
+                        fv[h] = (jj == 0 || jj == nl - 1) ? d : T(0.5) * d;
                     }
                 }
             }
@@ -1389,12 +1390,12 @@ struct KRx {
     static constexpr size_t SMEM = G * GROUP_BYTES + 128;  // + alignment slack
 };
 
-template <int LOGN>
+template <int LOGN, int PLAN>
 __global__ void __launch_bounds__(KRx<LOGN>::THREADS, 1) k_row_inv1x(const __grid_constant__ SolveArgs<float> a)
 {
     using C = float2;
     using R = KRx<LOGN>;
-    using P = F16<LOGN>;
+    using P = FR<LOGN, PLAN>;
     constexpr int N = R::N, Q = R::Q, G = R::G, SP = KShape<LOGN>::SP_ROW, PP = 2 * N;
     static_assert(Q >= 64, "named group barriers need whole warps");
     extern __shared__ __align__(16) unsigned char smem_dyn[];
@@ -1411,8 +1412,8 @@ __global__ void __launch_bounds__(KRx<LOGN>::THREADS, 1) k_row_inv1x(const __gri
     const int tl = a.level_base;
     const int items = a.ncomp * (N / 2);
     C trw[P::NST - 1][15];
-    load_twiddles_rt<C, LOGN>(trw, a.tw, j);
-    const TwLayout twl = tw_layout(P::twlen, N);
+    load_twiddles_rt<C, LOGN, PLAN>(trw, a.twn, j);
+    const TwLayout twl = tw_layout(F16<LOGN>::twlen, N);
     const C wj = a.tw[twl.base + j];  // W_P^j
     auto twist_u = [&](int u) { return hmul(wj, hmk<C>((float)kW32c[u], (float)-kW32s[u])); };
     const long long bound = a.wait_cycles > 0 ? a.wait_cycles : kTmaWaitCycles;
@@ -1473,7 +1474,7 @@ __global__ void __launch_bounds__(KRx<LOGN>::THREADS, 1) k_row_inv1x(const __gri
         group_sync(bar, Q);  // every thread has read the stage
         if (j == 0 && it + step < items)
             gather(it + step);
-        fft_stages_rt<C, true, LOGN, 2, 0>(v, xb, SP, j, trw, bar, Q);
+        fft_stages_rt<C, true, LOGN, PLAN, 2, 0>(v, xb, SP, j, trw, bar, Q);
         float *out = comp ? a.fy[tl] : a.fx[tl];
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
@@ -1533,11 +1534,12 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd_m(SolveAr
         __syncthreads();  // rows r0, r0 + 1 staged; the previous pair's bins have been read
         {
             bool bad = false;
-            if (r0 == 0 || r0 == N - 2) {
+            const int nl = a.n_log;  // the patch's own cells (zero beyond them in an embedded array)
+            if (r0 == 0 || r0 == nl - 2) {
                 for (int i = t; i < 2 * N; i += K::ROW_THREADS)
                     bad |= srow[i] != T(0);
-            } else if (t < 8) {
-                const int col = (t & 3) < 2 ? (t & 3) : N - 4 + (t & 3);  // 0, 1, N-2, N-1
+            } else if (t < 8 && r0 < nl) {
+                const int col = (t & 3) < 2 ? (t & 3) : nl - 4 + (t & 3);  // 0, 1, n-2, n-1
                 bad = srow[(t >> 2) * N + col] != T(0);
             }
             if (bad)
@@ -1982,12 +1984,12 @@ struct KMx {
     static constexpr size_t SMEM = G * GROUP_BYTES;
 };
 
-template <int LOGN, bool PARK>
+template <int LOGN, bool PARK, int PLAN>
 __global__ void __launch_bounds__(KMx<LOGN, PARK>::THREADS, 1) k_col_mx(SolveArgs<float> a)
 {
     using C = float2;
     using M = KMx<LOGN, PARK>;
-    using P = F16<LOGN>;
+    using P = FR<LOGN, PLAN>;
     constexpr int N = M::N, Q = M::Q, G = M::G, HQ = quarter_half(N), QS = quarter_stride(N), SPC = M::SPC;
     static_assert(Q >= 64, "named group barriers need whole warps");
     extern __shared__ __align__(16) unsigned char smem_mx[];
@@ -2000,8 +2002,8 @@ __global__ void __launch_bounds__(KMx<LOGN, PARK>::THREADS, 1) k_col_mx(SolveArg
     C *park = xb + 2 * SPC;
     const unsigned bar = 1 + g;
     C trw[P::NST - 1][15];
-    load_twiddles_rt<C, LOGN>(trw, a.tw, j);
-    const TwLayout tl = tw_layout(P::twlen, N);
+    load_twiddles_rt<C, LOGN, PLAN>(trw, a.twn, j);
+    const TwLayout tl = tw_layout(F16<LOGN>::twlen, N);
     const C wj = a.tw[tl.base + j];  // W_P^j
     auto twist_u = [&](int u) { return hmul(wj, hmk<C>((float)kW32c[u], (float)-kW32s[u])); };
     const float *spec = reinterpret_cast<const float *>(a.spec);
@@ -2030,7 +2032,7 @@ __global__ void __launch_bounds__(KMx<LOGN, PARK>::THREADS, 1) k_col_mx(SolveArg
             v[0][u] = x;
             v[1][u] = hmul(x, twist_u(u));
         }
-        fft_stages_rt<C, false, LOGN, 2, 0>(v, xb, SPC, j, trw, bar, Q);
+        fft_stages_rt<C, false, LOGN, PLAN, 2, 0>(v, xb, SPC, j, trw, bar, Q);
         C fy[PARK ? 1 : 2][16];
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
@@ -2055,7 +2057,7 @@ __global__ void __launch_bounds__(KMx<LOGN, PARK>::THREADS, 1) k_col_mx(SolveArg
             stage(kx + step);
         }
         C *dst = a.bwd;
-        fft_stages_rt<C, true, LOGN, 2, 0>(v, xb, SPC, j, trw, bar, Q);
+        fft_stages_rt<C, true, LOGN, PLAN, 2, 0>(v, xb, SPC, j, trw, bar, Q);
 #pragma unroll
         for (int u = 0; u < 16; ++u)
             dst[bwd_index(N, N, 0, kx, j + u * Q)] = hadd(v[0][u], hmulc(v[1][u], twist_u(u)));
@@ -2065,12 +2067,12 @@ __global__ void __launch_bounds__(KMx<LOGN, PARK>::THREADS, 1) k_col_mx(SolveArg
 #pragma unroll
                 for (int u = 0; u < 16; ++u)
                     v[b][u] = park[b * N + j + u * Q];
-            fft_stages_rt<C, true, LOGN, 2, 0>(v, xb, SPC, j, trw, bar, Q);
+            fft_stages_rt<C, true, LOGN, PLAN, 2, 0>(v, xb, SPC, j, trw, bar, Q);
 #pragma unroll
             for (int u = 0; u < 16; ++u)
                 dst[bwd_index(N, N, 1, kx, j + u * Q)] = hadd(v[0][u], hmulc(v[1][u], twist_u(u)));
         } else {
-            fft_stages_rt<C, true, LOGN, 2, 0>(fy, xb, SPC, j, trw, bar, Q);
+            fft_stages_rt<C, true, LOGN, PLAN, 2, 0>(fy, xb, SPC, j, trw, bar, Q);
 #pragma unroll
             for (int u = 0; u < 16; ++u)
                 dst[bwd_index(N, N, 1, kx, j + u * Q)] = hadd(fy[0][u], hmulc(fy[1][u], twist_u(u)));
@@ -2220,9 +2222,9 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
 {
     using K = KShape<LOGN>;
     using S = KSmem<T, LOGN, TC>;
-    static std::atomic<unsigned long long> d[30];
-    static std::atomic<int> res_mx[64];               // resident CTAs of the register-twiddle column pass
-    static std::atomic<int> res_rx[64];               // and of the register-twiddle inverse row pass
+    static std::atomic<unsigned long long> d[32];
+    static std::atomic<int> res_mx[64], res_mx1[64];  // resident CTAs of the register-twiddle column pass (plans 0, 1)
+    static std::atomic<int> res_rx[64], res_rx1[64];  // and of the register-twiddle inverse row pass
     static std::atomic<int> res_mw[64], res_mw1[64];  // resident CTAs of the walking column pass (NC = 2, 1)
     static std::atomic<int> res_fm[64];               // and of the walking zero-rim forward row pass
     static std::atomic<int> res_ri1[64], res_ri2[64]; // and of the walking inverse row passes (tensor cores)
@@ -2304,12 +2306,15 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
         }
         if constexpr (!TC && sizeof(T) == 4 && LOGN >= 10) {
             using MX = KMx<LOGN, kMxPark>;
-            if ((e = ensure_smem(k_col_mx<LOGN, kMxPark>, MX::SMEM, d[28])) != cudaSuccess ||
-                (e = resident_ctas(k_col_mx<LOGN, kMxPark>, MX::THREADS, MX::SMEM, res_mx, &grid)) != cudaSuccess)
-                return e;
             using RX = KRx<LOGN>;
-            if ((e = ensure_smem(k_row_inv1x<LOGN>, RX::SMEM, d[29])) != cudaSuccess ||
-                (e = resident_ctas(k_row_inv1x<LOGN>, RX::THREADS, RX::SMEM, res_rx, &grid)) != cudaSuccess)
+            if ((e = ensure_smem(k_col_mx<LOGN, kMxPark, 0>, MX::SMEM, d[28])) != cudaSuccess ||
+                (e = resident_ctas(k_col_mx<LOGN, kMxPark, 0>, MX::THREADS, MX::SMEM, res_mx, &grid)) != cudaSuccess ||
+                (e = ensure_smem(k_col_mx<LOGN, kMxPark, 1>, MX::SMEM, d[30])) != cudaSuccess ||
+                (e = resident_ctas(k_col_mx<LOGN, kMxPark, 1>, MX::THREADS, MX::SMEM, res_mx1, &grid)) != cudaSuccess ||
+                (e = ensure_smem(k_row_inv1x<LOGN, 0>, RX::SMEM, d[29])) != cudaSuccess ||
+                (e = resident_ctas(k_row_inv1x<LOGN, 0>, RX::THREADS, RX::SMEM, res_rx, &grid)) != cudaSuccess ||
+                (e = ensure_smem(k_row_inv1x<LOGN, 1>, RX::SMEM, d[31])) != cudaSuccess ||
+                (e = resident_ctas(k_row_inv1x<LOGN, 1>, RX::THREADS, RX::SMEM, res_rx1, &grid)) != cudaSuccess)
                 return e;
         }
         return cudaSuccess;
@@ -2456,33 +2461,39 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
         }
         break;
     }
-    case PASS_ROW_INV1X: {
+    case PASS_ROW_INV1X:
+    case PASS_ROW_INV1X_R1: {
         if constexpr (!TC && sizeof(T) == 4 && LOGN >= 10) {
             if (batch)
                 return cudaErrorInvalidValue;
             using RX = KRx<LOGN>;
+            const bool r1 = pass == PASS_ROW_INV1X_R1;
+            auto *kern = r1 ? k_row_inv1x<LOGN, 1> : k_row_inv1x<LOGN, 0>;
             int grid = 0;
-            if ((e = ensure_smem(k_row_inv1x<LOGN>, RX::SMEM, d[29])) != cudaSuccess ||
-                (e = resident_ctas(k_row_inv1x<LOGN>, RX::THREADS, RX::SMEM, res_rx, &grid)) != cudaSuccess)
+            if ((e = ensure_smem(kern, RX::SMEM, d[r1 ? 31 : 29])) != cudaSuccess ||
+                (e = resident_ctas(kern, RX::THREADS, RX::SMEM, r1 ? res_rx1 : res_rx, &grid)) != cudaSuccess)
                 return e;
             const int groups = (a.ncomp * (K::N / 2) + RX::G - 1) / RX::G;  // CTAs that give every group an item
-            k_row_inv1x<LOGN><<<dim3(grid < groups ? grid : groups, count), RX::THREADS, RX::SMEM, st>>>(a);
+            kern<<<dim3(grid < groups ? grid : groups, count), RX::THREADS, RX::SMEM, st>>>(a);
         } else {
             return cudaErrorInvalidValue;
         }
         break;
     }
-    case PASS_COL_MX: {
+    case PASS_COL_MX:
+    case PASS_COL_MX_R1: {
         if constexpr (!TC && sizeof(T) == 4 && LOGN >= 10) {
             if (batch)
                 return cudaErrorInvalidValue;
             using MX = KMx<LOGN, kMxPark>;
+            const bool r1 = pass == PASS_COL_MX_R1;
+            auto *kern = r1 ? k_col_mx<LOGN, kMxPark, 1> : k_col_mx<LOGN, kMxPark, 0>;
             int grid = 0;
-            if ((e = ensure_smem(k_col_mx<LOGN, kMxPark>, MX::SMEM, d[28])) != cudaSuccess ||
-                (e = resident_ctas(k_col_mx<LOGN, kMxPark>, MX::THREADS, MX::SMEM, res_mx, &grid)) != cudaSuccess)
+            if ((e = ensure_smem(kern, MX::SMEM, d[r1 ? 30 : 28])) != cudaSuccess ||
+                (e = resident_ctas(kern, MX::THREADS, MX::SMEM, r1 ? res_mx1 : res_mx, &grid)) != cudaSuccess)
                 return e;
             const int groups = (K::N + 1 + MX::G - 1) / MX::G;  // CTAs that give every group a column
-            k_col_mx<LOGN, kMxPark><<<grid < groups ? grid : groups, MX::THREADS, MX::SMEM, st>>>(a);
+            kern<<<grid < groups ? grid : groups, MX::THREADS, MX::SMEM, st>>>(a);
         } else {
             return cudaErrorInvalidValue;
         }

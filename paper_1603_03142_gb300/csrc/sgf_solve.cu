@@ -64,6 +64,53 @@ cudaError_t launch_restrict_batch(const SolveArgs<T> *args, const int2 *jobs, in
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- embedding
+// A plan whose patches have n cells a side below its transform size N solves
+// them embedded in N x N arrays: the densities are copied in with zeros beyond
+// n, the forces copied back.
+template <typename T>
+__global__ void k_pad(IoPtrs<T> io, int n, int N)
+{
+    const int l = blockIdx.y;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * N)
+        return;
+    const int j = idx / N, i = idx - j * N;
+    io.dst[l][idx] = i < n && j < n ? io.src[l][(size_t)j * n + i] : T(0);
+}
+
+template <typename T>
+__global__ void k_crop(IoPtrs<T> io, int n, int N)
+{
+    const int l = blockIdx.y;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * n)
+        return;
+    const int j = idx / n, i = idx - j * n;
+    io.dst[l][idx] = io.src[l][(size_t)j * N + i];
+}
+
+template <typename T>
+cudaError_t launch_pad(const IoPtrs<T> &io, int L, int n, int N, cudaStream_t st)
+{
+    const int bs = 256;
+    k_pad<T><<<dim3((N * N + bs - 1) / bs, L), bs, 0, st>>>(io, n, N);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_crop(const IoPtrs<T> &io, int L, int n, int N, cudaStream_t st)
+{
+    const int bs = 256;
+    k_crop<T><<<dim3((n * n + bs - 1) / bs, L), bs, 0, st>>>(io, n, N);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_pad<float>(const IoPtrs<float> &, int, int, int, cudaStream_t);
+template cudaError_t launch_pad<double>(const IoPtrs<double> &, int, int, int, cudaStream_t);
+template cudaError_t launch_crop<float>(const IoPtrs<float> &, int, int, int, cudaStream_t);
+template cudaError_t launch_crop<double>(const IoPtrs<double> &, int, int, int, cudaStream_t);
+
 template cudaError_t launch_restrict_batch<float>(const SolveArgs<float> *, const int2 *, int, int, cudaStream_t);
 template cudaError_t launch_restrict_batch<double>(const SolveArgs<double> *, const int2 *, int, int, cudaStream_t);
 

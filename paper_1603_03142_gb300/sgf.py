@@ -39,7 +39,7 @@ BATCH_NO_GRAPH = 0x1
 PLAN_ZERO_RIM = 0x1
 PLAN_POTENTIAL = 0x2
 NOALLOC_SCRATCH_BYTES = 32 << 20
-AUTOTUNE_TIMES = 11
+AUTOTUNE_TIMES = 13
 KERNELS = ["restrict", "row_fwd", "col", "row_inv"]
 
 
@@ -96,7 +96,8 @@ class ServerStats(ctypes.Structure):
 
 
 class Schedule(ctypes.Structure):
-    _fields_ = [("col_pass", ctypes.c_int32), ("row_inv0", ctypes.c_int32), ("col_case3", ctypes.c_int32)]
+    _fields_ = [("col_pass", ctypes.c_int32), ("row_inv0", ctypes.c_int32), ("col_case3", ctypes.c_int32),
+                ("col_radix", ctypes.c_int32), ("inv_radix", ctypes.c_int32)]
 
 
 SERVER_SIMULATE = 0x1
@@ -303,10 +304,12 @@ class Plan:
     def schedule(self) -> dict:
         sc = Schedule()
         _check(_lib.sgf_plan_schedule_get(self._h, ctypes.byref(sc)), "sgf_plan_schedule_get")
-        return {"col_pass": sc.col_pass, "row_inv0": sc.row_inv0, "col_case3": sc.col_case3}
+        return {"col_pass": sc.col_pass, "row_inv0": sc.row_inv0, "col_case3": sc.col_case3,
+                "col_radix": sc.col_radix, "inv_radix": sc.inv_radix}
 
-    def set_schedule(self, col_pass: int = 0, row_inv0: int = 0, col_case3: int = 0):
-        sc = Schedule(int(col_pass), int(row_inv0), int(col_case3))
+    def set_schedule(self, col_pass: int = 0, row_inv0: int = 0, col_case3: int = 0, col_radix: int = 0,
+                     inv_radix: int = 0):
+        sc = Schedule(int(col_pass), int(row_inv0), int(col_case3), int(col_radix), int(inv_radix))
         _check(_lib.sgf_plan_schedule_set(self._h, ctypes.byref(sc)), "sgf_plan_schedule_set")
 
     def autotune(self, reps: int = 5, stream=None) -> dict:
@@ -315,10 +318,12 @@ class Plan:
         ms = (ctypes.c_double * AUTOTUNE_TIMES)()
         _check(_lib.sgf_plan_autotune(self._h, int(reps), ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(sc),
                                       ms), "sgf_plan_autotune")
-        return {"chosen": {"col_pass": sc.col_pass, "row_inv0": sc.row_inv0, "col_case3": sc.col_case3},
+        return {"chosen": {"col_pass": sc.col_pass, "row_inv0": sc.row_inv0, "col_case3": sc.col_case3,
+                           "col_radix": sc.col_radix, "inv_radix": sc.inv_radix},
                 "ms": {"col_pass0": ms[0], "col_pass1": ms[1], "col_pass2": ms[2], "row_inv0_0": ms[3],
                        "row_inv0_1": ms[4], "row_inv0_2": ms[5], "col_case3_0": ms[6], "col_case3_1": ms[7],
-                       "row_inv0_3": ms[8], "col_pass3": ms[9], "row_inv0_4": ms[10]}}
+                       "row_inv0_3": ms[8], "col_pass3": ms[9], "row_inv0_4": ms[10],
+                       "col_pass3_radix1": ms[11], "row_inv0_4_radix1": ms[12]}}
 
     def profile(self, enable: bool = True):
         _check(_lib.sgf_plan_profile(self._h, 1 if enable else 0), "sgf_plan_profile")

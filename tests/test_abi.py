@@ -38,7 +38,7 @@ def test_version(lib):
 
 
 @pytest.mark.parametrize("bad", [
-    dict(n=12), dict(n=8), dict(n=0), dict(levels=0), dict(levels=9), dict(n=16, levels=5),
+    dict(n=13), dict(n=6), dict(n=0), dict(levels=0), dict(levels=9), dict(n=16, levels=5),
     dict(off=[(0, 0), (9, 0)]), dict(off=[(0, 0), (-1, 0)]), dict(h0=-1.0),
 ])
 def test_invalid_descriptors_rejected_on_host(lib, bad):

@@ -52,13 +52,19 @@ def test_schedules_agree_zero_rim(lib, prec, n):
         with pytest.raises(lib.SgfError) as ei:
             plan.set_schedule(3, 0)
         assert ei.value.status == lib.SGF_EUNSUPPORTED
-    invs = (0, 1, 2, 3, 4) if tma and n >= 1024 else (0, 1, 2, 3) if tma else (0, 1, 2)
-    for col in (0, 1, 2, 3) if mx else (0, 1, 2):
-        for inv in invs:
-            plan.set_schedule(col, inv)
-            assert plan.schedule() == {"col_pass": col, "row_inv0": inv, "col_case3": 0}
+    # (choice, radix plan): col_pass 3 and row_inv0 4 in both radix plans (register-twiddle kernels)
+    invs = [(0, 0), (1, 0), (2, 0)] + ([(3, 0)] if tma else []) + ([(4, 0), (4, 1)] if tma and n >= 1024 else [])
+    cols = [(0, 0), (1, 0), (2, 0)] + ([(3, 0), (3, 1)] if mx else [])
+    for col, cr in cols:
+        for inv, ir in invs:
+            plan.set_schedule(col, inv, 0, cr, ir)
+            assert plan.schedule() == {"col_pass": col, "row_inv0": inv, "col_case3": 0, "col_radix": cr,
+                                       "inv_radix": ir}
             outs.append(run_gpu(plan, sigma))
             plan.check()
+    with pytest.raises(lib.SgfError) as ei:  # a radix plan without its register-twiddle kernel
+        plan.set_schedule(2, 0, 0, 1, 0)
+    assert ei.value.status == lib.SGF_EUNSUPPORTED
     eps = np.finfo(np.float64 if prec == "fp64" else np.float32).eps
     scale = max(np.abs(outs[0][0][0]).max(), np.abs(outs[0][1][0]).max())
     for gx, gy in outs[1:]:
@@ -143,13 +149,16 @@ print(json.dumps({"r": r, "q": q.schedule()}))
     ms = d["r"]["ms"]
     assert all(ms[k] > 0 for k in ("col_pass0", "col_pass1", "col_pass2", "row_inv0_0", "row_inv0_1", "row_inv0_2"))
     ch = d["r"]["chosen"]
-    assert ms["col_pass3"] > 0  # FP32 zero-rim force plan, n = 1024
-    cp = [ms["col_pass0"], ms["col_pass1"], ms["col_pass2"], ms["col_pass3"]]
-    assert ch["col_pass"] == cp.index(min(cp))
+    assert ms["col_pass3"] > 0 and ms["col_pass3_radix1"] > 0  # FP32 zero-rim force plan, n = 1024
+    cp = [ms["col_pass0"], ms["col_pass1"], ms["col_pass2"], ms["col_pass3"], ms["col_pass3_radix1"]]
+    best = cp.index(min(cp))
+    assert (ch["col_pass"], ch["col_radix"]) == ((best, 0) if best < 4 else (3, 1))
     assert ms["row_inv0_3"] > 0  # FP32, n = 1024, one level-0 patch
-    assert ms["row_inv0_4"] > 0
-    inv = [ms["row_inv0_0"], ms["row_inv0_1"], ms["row_inv0_2"], ms["row_inv0_3"], ms["row_inv0_4"]]
-    assert ch["row_inv0"] == inv.index(min(inv))
+    assert ms["row_inv0_4"] > 0 and ms["row_inv0_4_radix1"] > 0
+    inv = [ms["row_inv0_0"], ms["row_inv0_1"], ms["row_inv0_2"], ms["row_inv0_3"], ms["row_inv0_4"],
+           ms["row_inv0_4_radix1"]]
+    best = inv.index(min(inv))
+    assert (ch["row_inv0"], ch["inv_radix"]) == ((best, 0) if best < 5 else (4, 1))
     assert d["q"] == ch
     lines = table.read_text().split("\n")
     assert any("/n1024/p1/zr1/" in ln for ln in lines)

@@ -89,7 +89,8 @@ def sample(n):
 
 
 def schedules(n, prec, zero_rim):
-    """Every (col_pass, row_inv0) the plan accepts (sgf.h: schedule rules)."""
+    """Every (col_pass, row_inv0) the plan accepts (sgf.h: schedule rules); the
+    register-twiddle kernels (col_pass 3, row_inv0 4) also in radix plan 1."""
     cols = ((0, 1, 2, 3) if prec == "fp32" and n >= 1024 else (0, 1, 2)) if zero_rim else (0, 2)
     invs = (0, 1, 2, 3, 4)
     out = []
@@ -103,7 +104,11 @@ def schedules(n, prec, zero_rim):
                 continue
             if prec == "bf16x" and n == 4096 and (c == 2 or i == 1):
                 continue
-            out.append((c, i))
+            out.append((c, i, 0, 0))
+            if c == 3:
+                out.append((c, i, 1, 0))
+            if i == 4:
+                out.append((c, i, 0, 1))
     return out
 
 
@@ -112,11 +117,11 @@ def _check_all(lib, n, prec, zero_rim):
     plan = lib.Plan(s.nest, prec, zero_rim=zero_rim)
     bound = tol(prec, n)
     worst = {}
-    for c, i in schedules(n, prec, zero_rim):
-        plan.set_schedule(c, i)
+    for c, i, cr, ir in schedules(n, prec, zero_rim):
+        plan.set_schedule(c, i, 0, cr, ir)
         gx, gy = run_gpu(plan, s.sigma)
         plan.check()
-        worst[(c, i)] = s.rel_err(gx[0], gy[0])
+        worst[(c, i, cr, ir)] = s.rel_err(gx[0], gy[0])
     bad = {k: v for k, v in worst.items() if not v <= bound}
     assert not bad, (bad, bound)
     return worst

@@ -107,8 +107,8 @@ def test_bad_requests():
     srv = sgf.Server(hbm_budget=1 << 30, max_inflight=1, simulate_gbs=100.0)
     with pytest.raises(ValueError):
         srv.submit(0, W.centred_nest(64, 2), "fp32", _arrays(64, 1), _arrays(64, 2), _arrays(64, 2))
-    with pytest.raises(sgf.SgfError):  # n not a power of two
-        srv.submit(0, W.Nest(n=48, levels=1, off=[(0, 0)]), "fp32", _arrays(48, 1), _arrays(48, 1), _arrays(48, 1))
+    with pytest.raises(sgf.SgfError):  # n odd
+        srv.submit(0, W.Nest(n=47, levels=1, off=[(0, 0)]), "fp32", _arrays(47, 1), _arrays(47, 1), _arrays(47, 1))
     with pytest.raises(sgf.SgfError):
         sgf.Server(hbm_budget=1 << 30, max_inflight=0, simulate_gbs=1.0)
     with pytest.raises(sgf.SgfError):
