@@ -287,8 +287,9 @@ def run_gpu(args, world, rank, local):
         if plan_general is not None:
             plan_general.autotune(reps=3)
     else:
-        col, inv = (int(x) for x in args.schedule.split(","))
-        plan.set_schedule(col, inv)
+        parts = [int(x) for x in args.schedule.split(",")]
+        col, inv = parts[0], parts[1]
+        plan.set_schedule(col, inv, 0, 0, 0, parts[2] if len(parts) > 2 else 0)
         if plan_general is not None:
             plan_general.set_schedule(0, inv)
         tune = {"chosen": plan.schedule(), "ms": None}
@@ -693,7 +694,7 @@ def main():
                     help="uniform: skip the shortened batched and serving runs reported in config")
     ap.add_argument("--forest-n", type=int, default=512, help="cells per side of every patch of the forest")
     ap.add_argument("--schedule", default="auto",
-                    help="uniform: 'auto' (autotuner) or 'col_pass,row_inv0' to fix the kernel schedule")
+                    help="uniform: 'auto' (autotuner) or 'col_pass,row_inv0[,row_fwd]' to fix the kernel schedule")
     ap.add_argument("--workload", default="uniform", choices=["uniform", "batched", "serving"])
     ap.add_argument("--nests", type=int, default=256)
     ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate (requests/s)")

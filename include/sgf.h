@@ -412,6 +412,10 @@ sgf_status sgf_solve_noalloc(sgf_plan *plan, const void *const *sigma, void *con
  *     radix-16 stages closed by one radix-2/4/8 stage where 16 does not divide
  *     n (1024 = 16.16.4, 2048 = 16.16.8, 4096 = 16.16.16); 1 = the small stage
  *     first (4.16.16, 8.16.16) or, at n = 4096, four radix-8 stages (8.8.8.8).
+ *   row_fwd (SGF_PLAN_ZERO_RIM plans): 0 = the forward row pass with one row
+ *     pair per CTA; 1 = two row pairs per CTA, so that neighbouring threads
+ *     store the two pairs' values of one bin together, a whole 32-byte sector
+ *     (SGF_FP32, n >= 1024).
  * A new plan starts from {0, 0, 0}, or from the schedule the autotuner recorded for
  * its key (device, n, precision, zero-rim, levels > 1); sgf_plan_share copies it. */
 typedef struct {
@@ -420,6 +424,7 @@ typedef struct {
     int32_t col_case3;
     int32_t col_radix;   /* radix plan of the col_pass = 3 kernel (0 otherwise) */
     int32_t inv_radix;   /* radix plan of the row_inv0 = 4 kernel (0 otherwise) */
+    int32_t row_fwd;     /* zero-rim forward rows: 0 = one row pair per CTA, 1 = two */
 } sgf_schedule;
 
 /* The plan's current schedule.  Errors: SGF_EINVAL for a NULL argument. */
@@ -429,8 +434,9 @@ sgf_status sgf_plan_schedule_get(const sgf_plan *plan, sgf_schedule *schedule);
  * n = SGF_MAX_N (those kernels have no shared memory left for the tensor-core
  * tiles there), col_pass = 3 outside zero-rim SGF_FP32 force plans of
  * n >= 1024, row_inv0 = 2 on a potential plan, row_inv0 = 3 or 4 where it
- * does not apply, a radix plan 1 without its register-twiddle kernel (the
- * autotuner skips all of these). */
+ * does not apply, a radix plan 1 without its register-twiddle kernel,
+ * row_fwd = 1 outside zero-rim SGF_FP32 plans of n >= 1024 (the autotuner
+ * skips all of these). */
 sgf_status sgf_plan_schedule_set(sgf_plan *plan, const sgf_schedule *schedule);
 
 /* The autotuner: runs one solve on zero density (temporary device buffers),
@@ -439,15 +445,16 @@ sgf_status sgf_plan_schedule_set(sgf_plan *plan, const sgf_schedule *schedule);
  * `stream` -- keeps the fastest in the plan and records it for later plans of
  * the same key: in the process, and in the text file named by the environment
  * variable SGF_AUTOTUNE_CACHE if it is set (one line "<key> <col_pass>
- * <row_inv0> <col_case3> <col_radix> <inv_radix>" per key, read once, rewritten
- * after each tuning).  chosen (may be NULL) receives the schedule; ms (may be
- * NULL, else SGF_AUTOTUNE_TIMES doubles) the mean milliseconds per launch of
- * col_pass 0, 1, 2, row_inv0 0, 1, 2, col_case3 0, 1, row_inv0 3, col_pass 3,
- * row_inv0 4, col_pass 3 with radix plan 1, row_inv0 4 with radix plan 1 (-1
- * where a candidate does not apply).  Blocks
+ * <row_inv0> <col_case3> <col_radix> <inv_radix> <row_fwd>" per key, read
+ * once, rewritten after each tuning).  chosen (may be NULL) receives the
+ * schedule; ms (may be NULL, else SGF_AUTOTUNE_TIMES doubles) the mean
+ * milliseconds per launch of col_pass 0, 1, 2, row_inv0 0, 1, 2, col_case3 0,
+ * 1, row_inv0 3, col_pass 3, row_inv0 4, col_pass 3 with radix plan 1,
+ * row_inv0 4 with radix plan 1, row_fwd 0, 1 (-1 where a candidate does not
+ * apply).  Blocks
  * until done.
  * Errors: SGF_EINVAL, SGF_ENOMEM, SGF_ECUDA. */
-#define SGF_AUTOTUNE_TIMES 13
+#define SGF_AUTOTUNE_TIMES 15
 sgf_status sgf_plan_autotune(sgf_plan *plan, int32_t reps, void *stream, sgf_schedule *chosen, double *ms);
 
 /* Device memory a plan for this nest would hold, computed on the host without

@@ -1278,6 +1278,9 @@ inline bool schedule_ok(const sgf_plan *p, const sgf_schedule &s)
     // k_row_inv1x: the tensor-map gather (row_inv0 = 3's conditions) with n >= 1024
     if (s.row_inv0 == 4 && !(p->tma_inv && p->N >= 1024))
         return false;
+    // two row pairs per CTA in the zero-rim forward rows: FP32 without tensor-core tiles, N >= 1024
+    if (s.row_fwd != 0 && (s.row_fwd != 1 || !(p->merged && p->prec == SGF_FP32 && p->N >= 1024)))
+        return false;
     // radix plans: the register-twiddle kernels only (col_pass 3, row_inv0 4)
     if ((s.col_radix != 0 && (s.col_radix != 1 || s.col_pass != 3)) ||
         (s.inv_radix != 0 && (s.inv_radix != 1 || s.row_inv0 != 4)))
@@ -1376,7 +1379,8 @@ sgf_status solve_core(sgf_plan *p, const void *const *sigma, void *const *fx, vo
     cudaError_t e;
     if ((ms = mark(p, st)) != SGF_OK)
         return ms;
-    e = p->merged ? launch_pass_n<T>(PASS_ROW_FWD_M, p->logN, a, 0, st, nullptr, p->tc)
+    e = p->merged ? launch_pass_n<T>(p->sched.row_fwd == 1 ? PASS_ROW_FWD_M2 : PASS_ROW_FWD_M, p->logN, a, 0, st,
+                                     nullptr, p->tc)
                   : launch_pass_n<T>(PASS_ROW_FWD, p->logN, a, (int)p->items.size(), st, nullptr, p->tc);
     if (e != cudaSuccess)
         return cuda_fail(e, "row_fwd launch");
@@ -1555,7 +1559,8 @@ sgf_status solve_noalloc_impl(sgf_plan *p, const void *const *sigma, void *const
     a.groups = p->d_groups;
     a.sums = p->d_sums;
     a.partial = reinterpret_cast<typename SolveArgs<T>::C *>(partial);
-    cudaError_t e = p->merged ? launch_pass_n<T>(PASS_ROW_FWD_M, p->logN, a, 0, st, nullptr, p->tc)
+    cudaError_t e = p->merged ? launch_pass_n<T>(p->sched.row_fwd == 1 ? PASS_ROW_FWD_M2 : PASS_ROW_FWD_M, p->logN, a,
+                                                 0, st, nullptr, p->tc)
                               : launch_pass_n<T>(PASS_ROW_FWD, p->logN, a, (int)p->items.size(), st, nullptr, p->tc);
     if (e != cudaSuccess)
         return cuda_fail(e, "row_fwd launch");
@@ -1863,7 +1868,7 @@ std::string tune_key(const sgf_plan *p)
 }
 
 // Load the table file named by SGF_AUTOTUNE_CACHE once (lines "<key> <col_pass> <row_inv0>
-// <col_case3> <col_radix> <inv_radix>").
+// <col_case3> <col_radix> <inv_radix> <row_fwd>").
 void tune_load_locked()
 {
     if (g_tune_loaded)
@@ -1876,10 +1881,11 @@ void tune_load_locked()
     if (!f)
         return;
     char key[160];
-    int a = 0, b = 0, c = 0, d = 0, r = 0;
-    while (fscanf(f, "%159s %d %d %d %d %d", key, &a, &b, &c, &d, &r) == 6)
-        if (a >= 0 && a <= 3 && b >= 0 && b <= 4 && (c == 0 || c == 1) && (d == 0 || d == 1) && (r == 0 || r == 1))
-            g_tune[key] = sgf_schedule{a, b, c, d, r};
+    int a = 0, b = 0, c = 0, d = 0, r = 0, w = 0;
+    while (fscanf(f, "%159s %d %d %d %d %d %d", key, &a, &b, &c, &d, &r, &w) == 7)
+        if (a >= 0 && a <= 3 && b >= 0 && b <= 4 && (c == 0 || c == 1) && (d == 0 || d == 1) && (r == 0 || r == 1) &&
+            (w == 0 || w == 1))
+            g_tune[key] = sgf_schedule{a, b, c, d, r, w};
     fclose(f);
 }
 
@@ -1896,8 +1902,8 @@ void tune_store(const std::string &key, const sgf_schedule &s)
     if (!f)
         return;
     for (const auto &kv : g_tune)
-        fprintf(f, "%s %d %d %d %d %d\n", kv.first.c_str(), kv.second.col_pass, kv.second.row_inv0,
-                kv.second.col_case3, kv.second.col_radix, kv.second.inv_radix);
+        fprintf(f, "%s %d %d %d %d %d %d\n", kv.first.c_str(), kv.second.col_pass, kv.second.row_inv0,
+                kv.second.col_case3, kv.second.col_radix, kv.second.inv_radix, kv.second.row_fwd);
     fclose(f);
     rename(tmp.c_str(), path);
 }
@@ -1964,6 +1970,20 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[SGF_A
     for (int k = 0; k < SGF_AUTOTUNE_TIMES; ++k)
         ms[k] = -1.0;
     sgf_schedule best = p->sched;
+    if (p->merged) {  // forward rows: one or two row pairs per CTA (slots 13, 14)
+        for (int c = 0; c < 2 && s == SGF_OK; ++c) {
+            sgf_schedule cand = best;
+            cand.row_fwd = c;
+            if (schedule_ok(p, cand))
+                s = timeit([&] { return launch_pass_n<T>(c ? PASS_ROW_FWD_M2 : PASS_ROW_FWD_M, p->logN, a, 0, st,
+                                                         nullptr, p->tc); },
+                           ms[13 + c]);
+        }
+        if (s == SGF_OK && ms[14] >= 0.0 && ms[14] < ms[13])
+            best.row_fwd = 1;
+        else
+            best.row_fwd = 0;
+    }
     if (p->merged) {
         // candidates 0..3, and 4 = col_pass 3 with radix plan 1
         static const int col_kind[5] = {PASS_COL_M, PASS_COL_MD, PASS_COL_MW, PASS_COL_MX, PASS_COL_MX_R1};
@@ -2521,7 +2541,7 @@ sgf_status sgf_plan_schedule_set(sgf_plan *p, const sgf_schedule *in)
         return fail(SGF_EINVAL, "NULL argument");
     if (in->col_pass < 0 || in->col_pass > 3 || in->row_inv0 < 0 || in->row_inv0 > 4 ||
         (in->col_case3 != 0 && in->col_case3 != 1) || in->col_radix < 0 || in->col_radix > 1 || in->inv_radix < 0 ||
-        in->inv_radix > 1)
+        in->inv_radix > 1 || in->row_fwd < 0 || in->row_fwd > 1)
         return fail(SGF_EINVAL, "schedule out of range (col_pass %d, row_inv0 %d, col_case3 %d)", in->col_pass,
                     in->row_inv0, in->col_case3);
     if (!schedule_ok(p, *in))
@@ -2529,7 +2549,8 @@ sgf_status sgf_plan_schedule_set(sgf_plan *p, const sgf_schedule *in)
                     "schedule (col_pass %d, row_inv0 %d) not available for this plan: col_pass = 2 and row_inv0 = 1 "
                     "need n < %d with SGF_BF16X, col_pass = 3 a zero-rim SGF_FP32 force plan with n >= 1024, "
                     "row_inv0 = 2 a force plan, row_inv0 = 3 SGF_FP32 with n >= 512 and one level-0 patch, "
-                    "row_inv0 = 4 the same with n >= 1024, a radix plan 1 the register-twiddle kernel of its pass",
+                    "row_inv0 = 4 the same with n >= 1024, a radix plan 1 the register-twiddle kernel of its pass, "
+                    "row_fwd = 1 a zero-rim SGF_FP32 plan with n >= 1024",
                     in->col_pass, in->row_inv0, SGF_MAX_N);
     p->sched = *in;
     return SGF_OK;

@@ -438,15 +438,21 @@ SGF_HD void stage_ct(C *v, int j, const C *tw)
 // buffers, the named barrier 1 + half over the HB threads of that half (HB a
 // multiple of 32, each half whole warps), so the halves need not wait for each
 // other between stages.
+// (half 2 and 3: the two halves of a second row pair in k_row_fwd_m2, named
+// barriers 3 and 4; immediate ids keep the block's barrier count at 5)
 template <int HB>
 __device__ __forceinline__ void xsync(int half)
 {
     if constexpr (HB == 0)
         __syncthreads();
-    else if (half)  // warp-uniform; immediate ids keep the block's barrier count at 3
-        asm volatile("bar.sync 2, %0;" ::"n"(HB) : "memory");
-    else
+    else if (half == 0)  // warp-uniform
         asm volatile("bar.sync 1, %0;" ::"n"(HB) : "memory");
+    else if (half == 1)
+        asm volatile("bar.sync 2, %0;" ::"n"(HB) : "memory");
+    else if (half == 2)
+        asm volatile("bar.sync 3, %0;" ::"n"(HB) : "memory");
+    else
+        asm volatile("bar.sync 4, %0;" ::"n"(HB) : "memory");
 }
 
 // 16-point DFTs of the radix-16 stages run as split-BF16 tensor-core tiles

@@ -1592,6 +1592,84 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS) k_row_fwd_m(SolveAr
         tc_end(tcx, TCT);
 }
 
+// k_row_fwd_m (FP32, no tensor-core tiles, no batch view) with two row pairs
+// per CTA: group g = t / (N/8) of 2 N/16 threads transforms row pair
+// 2 blockIdx.x + g exactly as k_row_fwd_m transforms its one (parity halves on
+// named barriers 1 + 2 g + half), and in the store phase two neighbouring
+// lanes write the two row pairs of one bin, rows 4 blockIdx.x .. + 3: 32
+// contiguous bytes, one whole sector, where a CTA of one row pair writes 16.
+// Shared memory: twiddle area | sigma rows [4][N] | sbuf [2 pairs][2 halves][SP_ROW].
+template <int LOGN>
+__global__ void __launch_bounds__((1 << LOGN) / 4) k_row_fwd_m2(SolveArgs<float> a)
+{
+    using C = float2;
+    using C2 = float4;
+    using K = KShape<LOGN>;
+    constexpr int N = K::N, Q = K::Q, SP = K::SP_ROW, T2 = 2 * Q;
+    static_assert(Q >= 32, "whole warps per parity half");
+    extern __shared__ __align__(16) unsigned char smem_f2[];
+    C *tw = reinterpret_cast<C *>(smem_f2);
+    float *srow = reinterpret_cast<float *>(smem_f2 + tw_bytes<C>(a.tw_entries));
+    C *sbuf = reinterpret_cast<C *>(srow + 4 * N);
+    __shared__ int rim_bad;
+    const int t = threadIdx.x;
+    const int g = t / T2, tg = t - g * T2, b = tg / Q, j = tg - b * Q;
+    if (t == 0)
+        rim_bad = 0;
+    cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
+    cp_block(srow, a.src[0] + (size_t)(4 * blockIdx.x) * N, 4 * (size_t)N * sizeof(float));  // both pairs' rows
+    cp_commit();
+    cp_wait<0>();
+    __syncthreads();
+    const int r0 = 4 * (int)blockIdx.x + 2 * g;
+    const float *rows = srow + 2 * g * N;
+    {
+        bool bad = false;
+        const int nl = a.n_log;  // the patch's own cells (zero beyond them in an embedded array)
+        if (r0 == 0 || r0 == nl - 2) {
+            for (int i = tg; i < 2 * N; i += T2)
+                bad |= rows[i] != 0.0f;
+        } else if (tg < 8 && r0 < nl) {
+            const int col = (tg & 3) < 2 ? (tg & 3) : nl - 4 + (tg & 3);  // 0, 1, n-2, n-1
+            bad = rows[(tg >> 2) * N + col] != 0.0f;
+        }
+        if (bad)
+            rim_bad = 1;
+    }
+    const TwLayout tl = tw_layout(F16<LOGN>::twlen, N);
+    C v[1][16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        const int c = j + u * Q;
+        C z = hmk<C>(rows[c], rows[N + c]);
+        if (b)
+            z = hmul(z, twist(tw, tl, j, u));
+        v[0][u] = z;
+    }
+    fft_ct<C, false, LOGN, 1, false, Q>(v, sbuf + (2 * g + b) * SP, SP, j, true, tw, nullptr, 2 * g + b);
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+        sbuf[(2 * g + b) * SP + pad16(j + u * Q)] = v[0][u];
+    __syncthreads();
+    C2 *out = reinterpret_cast<C2 *>(a.fwd);
+    for (int e = t; e < 2 * (N + 1); e += 4 * Q) {  // e = 2 kx + pair: neighbouring lanes, one sector
+        const int pr = e & 1, kx = e >> 1;
+        const int bb = kx & 1, k = kx >> 1;
+        const int km = (N - bb - k) & (N - 1);
+        const C Z = sbuf[(2 * pr + bb) * SP + pad16(k)];
+        const C Zm = sbuf[(2 * pr + bb) * SP + pad16(km)];
+        C2 o;
+        o.x = 0.5f * (Z.x + Zm.x);
+        o.y = 0.5f * (Z.y - Zm.y);
+        o.z = 0.5f * (Z.y + Zm.y);
+        o.w = -0.5f * (Z.x - Zm.x);
+        out[((size_t)kx * N + 4 * blockIdx.x + 2 * pr) >> 1] = o;
+    }
+    if (t == 0 && rim_bad)
+        atomicOr(a.status, STATUS_RIM_NONZERO);
+}
+
 // Column pass of a SGF_PLAN_ZERO_RIM plan: one forward transform, the two
 // merged spectra (Fx^ = Gx^ sigma^, Fy^ = Gy^ sigma^, both imaginary), and the
 // two inverse transforms one after the other; parity halves folded through
@@ -2222,7 +2300,7 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
 {
     using K = KShape<LOGN>;
     using S = KSmem<T, LOGN, TC>;
-    static std::atomic<unsigned long long> d[32];
+    static std::atomic<unsigned long long> d[33];
     static std::atomic<int> res_mx[64], res_mx1[64];  // resident CTAs of the register-twiddle column pass (plans 0, 1)
     static std::atomic<int> res_rx[64], res_rx1[64];  // and of the register-twiddle inverse row pass
     static std::atomic<int> res_mw[64], res_mw1[64];  // resident CTAs of the walking column pass (NC = 2, 1)
@@ -2314,7 +2392,9 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
                 (e = ensure_smem(k_row_inv1x<LOGN, 0>, RX::SMEM, d[29])) != cudaSuccess ||
                 (e = resident_ctas(k_row_inv1x<LOGN, 0>, RX::THREADS, RX::SMEM, res_rx, &grid)) != cudaSuccess ||
                 (e = ensure_smem(k_row_inv1x<LOGN, 1>, RX::SMEM, d[31])) != cudaSuccess ||
-                (e = resident_ctas(k_row_inv1x<LOGN, 1>, RX::THREADS, RX::SMEM, res_rx1, &grid)) != cudaSuccess)
+                (e = resident_ctas(k_row_inv1x<LOGN, 1>, RX::THREADS, RX::SMEM, res_rx1, &grid)) != cudaSuccess ||
+                (e = ensure_smem(k_row_fwd_m2<LOGN>, S::tw() + 4 * (size_t)K::N * sizeof(float) +
+                                                         4 * (size_t)K::SP_ROW * sizeof(float2), d[32])) != cudaSuccess)
                 return e;
         }
         return cudaSuccess;
@@ -2475,6 +2555,19 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
                 return e;
             const int groups = (a.ncomp * (K::N / 2) + RX::G - 1) / RX::G;  // CTAs that give every group an item
             kern<<<dim3(grid < groups ? grid : groups, count), RX::THREADS, RX::SMEM, st>>>(a);
+        } else {
+            return cudaErrorInvalidValue;
+        }
+        break;
+    }
+    case PASS_ROW_FWD_M2: {
+        if constexpr (!TC && sizeof(T) == 4 && LOGN >= 10) {
+            if (batch)
+                return cudaErrorInvalidValue;
+            const size_t smem = S::tw() + 4 * (size_t)K::N * sizeof(float) + 4 * (size_t)K::SP_ROW * sizeof(float2);
+            if ((e = ensure_smem(k_row_fwd_m2<LOGN>, smem, d[32])) != cudaSuccess)
+                return e;
+            k_row_fwd_m2<LOGN><<<K::N / 4, K::N / 4, smem, st>>>(a);
         } else {
             return cudaErrorInvalidValue;
         }

@@ -39,7 +39,7 @@ BATCH_NO_GRAPH = 0x1
 PLAN_ZERO_RIM = 0x1
 PLAN_POTENTIAL = 0x2
 NOALLOC_SCRATCH_BYTES = 32 << 20
-AUTOTUNE_TIMES = 13
+AUTOTUNE_TIMES = 15
 KERNELS = ["restrict", "row_fwd", "col", "row_inv"]
 
 
@@ -97,7 +97,7 @@ class ServerStats(ctypes.Structure):
 
 class Schedule(ctypes.Structure):
     _fields_ = [("col_pass", ctypes.c_int32), ("row_inv0", ctypes.c_int32), ("col_case3", ctypes.c_int32),
-                ("col_radix", ctypes.c_int32), ("inv_radix", ctypes.c_int32)]
+                ("col_radix", ctypes.c_int32), ("inv_radix", ctypes.c_int32), ("row_fwd", ctypes.c_int32)]
 
 
 SERVER_SIMULATE = 0x1
@@ -305,11 +305,11 @@ class Plan:
         sc = Schedule()
         _check(_lib.sgf_plan_schedule_get(self._h, ctypes.byref(sc)), "sgf_plan_schedule_get")
         return {"col_pass": sc.col_pass, "row_inv0": sc.row_inv0, "col_case3": sc.col_case3,
-                "col_radix": sc.col_radix, "inv_radix": sc.inv_radix}
+                "col_radix": sc.col_radix, "inv_radix": sc.inv_radix, "row_fwd": sc.row_fwd}
 
     def set_schedule(self, col_pass: int = 0, row_inv0: int = 0, col_case3: int = 0, col_radix: int = 0,
-                     inv_radix: int = 0):
-        sc = Schedule(int(col_pass), int(row_inv0), int(col_case3), int(col_radix), int(inv_radix))
+                     inv_radix: int = 0, row_fwd: int = 0):
+        sc = Schedule(int(col_pass), int(row_inv0), int(col_case3), int(col_radix), int(inv_radix), int(row_fwd))
         _check(_lib.sgf_plan_schedule_set(self._h, ctypes.byref(sc)), "sgf_plan_schedule_set")
 
     def autotune(self, reps: int = 5, stream=None) -> dict:
@@ -319,11 +319,12 @@ class Plan:
         _check(_lib.sgf_plan_autotune(self._h, int(reps), ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(sc),
                                       ms), "sgf_plan_autotune")
         return {"chosen": {"col_pass": sc.col_pass, "row_inv0": sc.row_inv0, "col_case3": sc.col_case3,
-                           "col_radix": sc.col_radix, "inv_radix": sc.inv_radix},
+                           "col_radix": sc.col_radix, "inv_radix": sc.inv_radix, "row_fwd": sc.row_fwd},
                 "ms": {"col_pass0": ms[0], "col_pass1": ms[1], "col_pass2": ms[2], "row_inv0_0": ms[3],
                        "row_inv0_1": ms[4], "row_inv0_2": ms[5], "col_case3_0": ms[6], "col_case3_1": ms[7],
                        "row_inv0_3": ms[8], "col_pass3": ms[9], "row_inv0_4": ms[10],
-                       "col_pass3_radix1": ms[11], "row_inv0_4_radix1": ms[12]}}
+                       "col_pass3_radix1": ms[11], "row_inv0_4_radix1": ms[12], "row_fwd0": ms[13],
+                       "row_fwd1": ms[14]}}
 
     def profile(self, enable: bool = True):
         _check(_lib.sgf_plan_profile(self._h, 1 if enable else 0), "sgf_plan_profile")

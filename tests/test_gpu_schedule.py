@@ -55,13 +55,15 @@ def test_schedules_agree_zero_rim(lib, prec, n):
     # (choice, radix plan): col_pass 3 and row_inv0 4 in both radix plans (register-twiddle kernels)
     invs = [(0, 0), (1, 0), (2, 0)] + ([(3, 0)] if tma else []) + ([(4, 0), (4, 1)] if tma and n >= 1024 else [])
     cols = [(0, 0), (1, 0), (2, 0)] + ([(3, 0), (3, 1)] if mx else [])
+    fwds = (0, 1) if mx else (0,)  # row_fwd = 1: two row pairs per CTA in the forward rows
     for col, cr in cols:
         for inv, ir in invs:
-            plan.set_schedule(col, inv, 0, cr, ir)
-            assert plan.schedule() == {"col_pass": col, "row_inv0": inv, "col_case3": 0, "col_radix": cr,
-                                       "inv_radix": ir}
-            outs.append(run_gpu(plan, sigma))
-            plan.check()
+            for fw in fwds:
+                plan.set_schedule(col, inv, 0, cr, ir, fw)
+                assert plan.schedule() == {"col_pass": col, "row_inv0": inv, "col_case3": 0, "col_radix": cr,
+                                           "inv_radix": ir, "row_fwd": fw}
+                outs.append(run_gpu(plan, sigma))
+                plan.check()
     with pytest.raises(lib.SgfError) as ei:  # a radix plan without its register-twiddle kernel
         plan.set_schedule(2, 0, 0, 1, 0)
     assert ei.value.status == lib.SGF_EUNSUPPORTED
@@ -159,6 +161,8 @@ print(json.dumps({"r": r, "q": q.schedule()}))
            ms["row_inv0_4_radix1"]]
     best = inv.index(min(inv))
     assert (ch["row_inv0"], ch["inv_radix"]) == ((best, 0) if best < 5 else (4, 1))
+    assert ms["row_fwd0"] > 0 and ms["row_fwd1"] > 0
+    assert ch["row_fwd"] == (1 if ms["row_fwd1"] < ms["row_fwd0"] else 0)
     assert d["q"] == ch
     lines = table.read_text().split("\n")
     assert any("/n1024/p1/zr1/" in ln for ln in lines)
