@@ -279,7 +279,7 @@ def run_gpu(args, world, rank, local):
     # zero-rim plan (verified on the device every solve) is valid; the general
     # three-field path is timed beside it and reported in config
     plan = sgf.Plan(nest, "fp32", zero_rim=not args.general)
-    plan_general = sgf.Plan(nest, "fp32") if not args.general else None
+    plan_general = sgf.Plan(nest, "fp32") if not (args.general or args.solve_only) else None
     # the autotuner picks each pass's kernel schedule (same arithmetic; results agree to rounding),
     # unless --schedule fixes it
     if args.schedule == "auto":
@@ -342,6 +342,15 @@ def run_gpu(args, world, rank, local):
     ms_step = ms / args.steps
     cells = float(n * n)
     value = world * cells * args.steps / (ms / 1e3)
+    if args.solve_only:  # the one plan and its timed solves (small device footprint, for ncu captures)
+        if rank == 0:
+            print(json.dumps({"mode": "solve-only", "n": n, "ms_per_step": ms_step, "cells_per_s": value,
+                              "schedule": plan.schedule(),
+                              "kernel_ms": {k: v["ms"] / max(1, v["launches"]) for k, v in prof["kernels"].items()
+                                            if v["launches"]},
+                              "device_bytes": torch.cuda.max_memory_allocated(dev) + st["workspace_bytes"] +
+                              st["spectra_bytes"]}), flush=True)
+        return
     general = None
     if plan_general is not None:
         gms, gprof = timed(plan_general, args.steps)
@@ -412,28 +421,77 @@ def run_gpu(args, world, rank, local):
         if serving_runs is not None and serving_all is not None:
             serving_runs["all_shapes_stream"] = serving_all
 
-    # e2e: host buffers through the C ABI, copies inside the timed region
-    pin_s = torch.from_numpy(sigma[0].astype(np.float32)).pin_memory()
-    pin_x = torch.empty((n, n), dtype=torch.float32).pin_memory()
-    pin_y = torch.empty((n, n), dtype=torch.float32).pin_memory()
-    for _ in range(2):
-        plan.solve_host_ptrs([pin_s.data_ptr()], [pin_x.data_ptr()], [pin_y.data_ptr()], stream)
-    e2e_steps = max(3, args.steps // 2)
+    # e2e: host buffers through the C ABI, copies inside the timed region.  The
+    # pipelined call (sgf_solve_host_many) over a ring of page-locked sets:
+    # every step copies its density in and its forces out, overlapping the
+    # neighbouring steps' transforms.  The one-call-per-step figure
+    # (sgf_solve_host, forces written in place over the link) rides along.
+    ring = 3
+    pin_s = [torch.from_numpy(W.config3(n, seed=7 + k)[1][0].astype(np.float32)).pin_memory() if k else
+             torch.from_numpy(sigma[0].astype(np.float32)).pin_memory() for k in range(ring)]
+    pin_x = [torch.empty((n, n), dtype=torch.float32).pin_memory() for _ in range(ring)]
+    pin_y = [torch.empty((n, n), dtype=torch.float32).pin_memory() for _ in range(ring)]
+    e2e_steps = max(6, args.steps)
+    sel = [k % ring for k in range(e2e_steps)]
+    sp = [pin_s[k].data_ptr() for k in sel]
+    xp = [pin_x[k].data_ptr() for k in sel]
+    yp = [pin_y[k].data_ptr() for k in sel]
+    plan.solve_host_many_ptrs(ring, sp[:ring], xp[:ring], yp[:ring], stream)  # staging allocated, warm
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        plan.solve_host_ptrs([pin_s.data_ptr()], [pin_x.data_ptr()], [pin_y.data_ptr()], stream)
+    plan.solve_host_many_ptrs(e2e_steps, sp, xp, yp, stream)
     e2e_s = time.perf_counter() - t0
+    for _ in range(2):
+        plan.solve_host_ptrs([pin_s[0].data_ptr()], [pin_x[0].data_ptr()], [pin_y[0].data_ptr()], stream)
+    t1 = time.perf_counter()
+    for k in sel:
+        plan.solve_host_ptrs([pin_s[k].data_ptr()], [pin_x[k].data_ptr()], [pin_y[k].data_ptr()], stream)
+    serial_s = time.perf_counter() - t1
+    # the CPU-GPU link alone: one device-to-host copy of a step's forces and one
+    # host-to-device copy of its density, each timed by itself and both at once
+    link_s = torch.cuda.Stream(dev)
+    dfx = torch.empty((2, n, n), dtype=torch.float32, device=dev)
+    hfx = torch.empty((2, n, n), dtype=torch.float32).pin_memory()
+    dsg = torch.empty((n, n), dtype=torch.float32, device=dev)
+
+    def link_time(d2h, h2d, reps=5):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        for r in range(reps + 1):
+            if r == 1:
+                ev[0].record(stream)
+            if h2d:
+                link_s.wait_stream(stream)  # both copies start together
+                with torch.cuda.stream(link_s):
+                    dsg.copy_(pin_s[0], non_blocking=True)
+            if d2h:
+                with torch.cuda.stream(stream):
+                    hfx.copy_(dfx, non_blocking=True)
+            if h2d:
+                stream.wait_stream(link_s)
+        ev[1].record(stream)
+        ev[1].synchronize()
+        return ev[0].elapsed_time(ev[1]) / 1e3 / reps
+
+    t_d2h, t_h2d, t_both = link_time(True, False), link_time(False, True), link_time(True, True)
     if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        t = torch.tensor([e2e_s, serial_s], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s, serial_s = (float(v) for v in t.tolist())
     e2e = {"value": world * cells * e2e_steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": n * n * 4, "d2h_bytes_per_step": 2 * n * n * 4,
-           "transfer": "sigma copied to the device; Fx, Fy written by the inverse row pass "
-                       "in place to page-locked host memory"}
+           "steps": e2e_steps,
+           "transfer": "sgf_solve_host_many over a ring of 3 page-locked sets: each step's sigma copied in "
+                       "and Fx, Fy copied out on two copy streams, overlapping the neighbouring steps' solves",
+           "link": {"d2h_gbs": 2 * n * n * 4 / t_d2h / 1e9, "h2d_gbs": n * n * 4 / t_h2d / 1e9,
+                    "both_ms": t_both * 1e3,
+                    "bound": world * cells / t_both, "frac": (cells * e2e_steps / e2e_s) / (cells / t_both),
+                    "what": "a step's copies alone (CUDA events): 128 MiB out and 64 MiB in at once; bound = "
+                            "cells per step over that time"},
+           "one_call_per_step": {"value": world * cells * e2e_steps / serial_s,
+                                 "call": "sgf_solve_host (sigma copied in, Fx, Fy written in place to "
+                                         "page-locked host memory by the inverse row pass; waits per step)"}}
 
     if rank != 0:
         return
@@ -690,6 +748,8 @@ def main():
     ap.add_argument("--no-bf16x", action="store_true", help="skip the split-BF16 tensor-core path")
     ap.add_argument("--no-potential", action="store_true", help="skip the potential (SGF_PLAN_POTENTIAL) timing")
     ap.add_argument("--no-forest", action="store_true", help="skip the two-disk forest (Example 3) timing")
+    ap.add_argument("--solve-only", action="store_true",
+                    help="only the timed solves of the one plan (no other path, no e2e); prints a short line")
     ap.add_argument("--no-nest-workloads", action="store_true",
                     help="uniform: skip the shortened batched and serving runs reported in config")
     ap.add_argument("--forest-n", type=int, default=512, help="cells per side of every patch of the forest")

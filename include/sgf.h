@@ -261,6 +261,23 @@ sgf_status sgf_solve_potential(sgf_plan *plan, const void *const *sigma, void *c
 sgf_status sgf_solve_host(sgf_plan *plan, const void *const *sigma, void *const *fx,
                           void *const *fy, void *stream);
 
+/* Solves `count` independent problems of this plan whose densities and forces
+ * are in HOST memory, each as sgf_solve_host, with the copies of neighbouring
+ * problems overlapping: while problem k is transformed on `stream`, the
+ * density of problem k+1 is copied in on one copy stream and the forces of
+ * problem k-1 are copied out on another, through two alternating sets of
+ * device staging (allocated on the first call, 6 * levels arrays, reported in
+ * workspace_bytes).  Problem k's level l is sigma[k * levels + l], fx[k *
+ * levels + l], fy[k * levels + l] (n*n elements each); the copies overlap only
+ * for page-locked host buffers (cudaHostAlloc / cudaHostRegister), others are
+ * copied synchronously by the runtime.  Outputs must not alias inputs, nor
+ * another problem's outputs.  Blocks until every force is in host memory.
+ * count = 0 is a no-op.  Errors: as sgf_solve_host; SGF_EINVAL for count < 0
+ * or a potential plan.  A failure may leave earlier problems' forces
+ * written and later ones not. */
+sgf_status sgf_solve_host_many(sgf_plan *plan, int32_t count, const void *const *sigma, void *const *fx,
+                               void *const *fy, void *stream);
+
 /* (Plans whose n is below their transform size -- n not a power of two, or 8 --
  * solve through sgf_solve, sgf_solve_potential and sgf_solve_host; batches and
  * sgf_solve_noalloc refuse them with SGF_EUNSUPPORTED: their staging belongs
@@ -402,13 +419,16 @@ sgf_status sgf_solve_noalloc(sgf_plan *plan, const void *const *sigma, void *con
  *     one thread per slot carrying both parity halves, the slot's stage
  *     twiddles in registers and the CTAs walking the row pairs, each
  *     gathering its next row pair behind the current transforms (n >= 1024;
- *     sgf_solve_noalloc runs 0 instead).  Potential plans take no 2.
+ *     sgf_solve_noalloc runs 0 instead); 5 = as 4 with two row pairs per
+ *     item, gathered together as 32-byte pieces (two neighbouring pairs'
+ *     bins) and transformed one after the other (same conditions as 4).
+ *     Potential plans take no 2.
  *   col_case3 (nests): 0 = the m^2 Case-3 phase outputs of a (coarser source,
  *     target) pair in one cluster per column, the source's forward column
  *     transforms done once for all of them; 1 = one cluster per phase output,
  *     each transforming the source again.
  *   col_radix, inv_radix: the radix plan of the n-point transforms of the
- *     col_pass = 3 and row_inv0 = 4 kernels (0 for every other choice): 0 =
+ *     col_pass = 3 and row_inv0 = 4, 5 kernels (0 for every other choice): 0 =
  *     radix-16 stages closed by one radix-2/4/8 stage where 16 does not divide
  *     n (1024 = 16.16.4, 2048 = 16.16.8, 4096 = 16.16.16); 1 = the small stage
  *     first (4.16.16, 8.16.16) or, at n = 4096, four radix-8 stages (8.8.8.8).
@@ -423,7 +443,7 @@ typedef struct {
     int32_t row_inv0;
     int32_t col_case3;
     int32_t col_radix;   /* radix plan of the col_pass = 3 kernel (0 otherwise) */
-    int32_t inv_radix;   /* radix plan of the row_inv0 = 4 kernel (0 otherwise) */
+    int32_t inv_radix;   /* radix plan of the row_inv0 = 4, 5 kernels (0 otherwise) */
     int32_t row_fwd;     /* zero-rim forward rows: 0 = one row pair per CTA, 1 = two */
 } sgf_schedule;
 
@@ -433,7 +453,7 @@ sgf_status sgf_plan_schedule_get(const sgf_plan *plan, sgf_schedule *schedule);
  * SGF_EUNSUPPORTED for col_pass = 2 or row_inv0 = 1 on a SGF_BF16X plan of
  * n = SGF_MAX_N (those kernels have no shared memory left for the tensor-core
  * tiles there), col_pass = 3 outside zero-rim SGF_FP32 force plans of
- * n >= 1024, row_inv0 = 2 on a potential plan, row_inv0 = 3 or 4 where it
+ * n >= 1024, row_inv0 = 2 on a potential plan, row_inv0 = 3, 4 or 5 where it
  * does not apply, a radix plan 1 without its register-twiddle kernel,
  * row_fwd = 1 outside zero-rim SGF_FP32 plans of n >= 1024 (the autotuner
  * skips all of these). */
@@ -450,11 +470,10 @@ sgf_status sgf_plan_schedule_set(sgf_plan *plan, const sgf_schedule *schedule);
  * schedule; ms (may be NULL, else SGF_AUTOTUNE_TIMES doubles) the mean
  * milliseconds per launch of col_pass 0, 1, 2, row_inv0 0, 1, 2, col_case3 0,
  * 1, row_inv0 3, col_pass 3, row_inv0 4, col_pass 3 with radix plan 1,
- * row_inv0 4 with radix plan 1, row_fwd 0, 1 (-1 where a candidate does not
- * apply).  Blocks
- * until done.
+ * row_inv0 4 with radix plan 1, row_fwd 0, 1, row_inv0 5, row_inv0 5 with
+ * radix plan 1 (-1 where a candidate does not apply).  Blocks until done.
  * Errors: SGF_EINVAL, SGF_ENOMEM, SGF_ECUDA. */
-#define SGF_AUTOTUNE_TIMES 15
+#define SGF_AUTOTUNE_TIMES 17
 sgf_status sgf_plan_autotune(sgf_plan *plan, int32_t reps, void *stream, sgf_schedule *chosen, double *ms);
 
 /* Device memory a plan for this nest would hold, computed on the host without

@@ -151,6 +151,7 @@ struct sgf_plan {
     sgf_schedule sched{};      // tile schedule of the transform passes (autotuner)
     bool tma_inv = false;      // row_inv0 = 3 available: FP32, N >= 512, one level-0 patch
     alignas(64) unsigned char tmap_inv[128] = {};  // its tensor map over the level-0 main column output
+    alignas(64) unsigned char tmap_inv2[128] = {}; // the same with two row pairs a box (k_row_inv2x)
     int *d_status = nullptr;   // device status word (STATUS_* bits)
     cudaEvent_t done = nullptr;  // recorded after every solve (sgf_plan_check)
     int N = 0, logN = 0, L = 0, device = 0;  // L: patches (the levels of a nest); N: transform size
@@ -196,6 +197,11 @@ struct sgf_plan {
     void *d_restricted = nullptr;  // restricted * N * N reals
     // host-buffer solve staging (allocated on first sgf_solve_host)
     void *d_stage = nullptr;
+    // sgf_solve_host_many: two alternating staging sets, its copy-in and
+    // copy-out streams and per set the events in-copied / solved / out-copied
+    void *d_pipe = nullptr;
+    cudaStream_t pipe_in = nullptr, pipe_out = nullptr;
+    cudaEvent_t pipe_ev[6] = {};
     // spectra budget (sgf_plan_create): when the kernel spectra exceed it, the
     // sets that fit stay resident and the others are regenerated at every solve,
     // wave by wave, through a window (streamed plans)
@@ -879,6 +885,18 @@ void plan_free_owned(sgf_plan *p)
     cudaFree(p->d_bwd);
     cudaFree(p->d_restricted);
     cudaFree(p->d_stage);
+    cudaFree(p->d_pipe);
+    p->d_pipe = nullptr;
+    for (cudaEvent_t &ev : p->pipe_ev) {
+        if (ev)
+            cudaEventDestroy(ev);
+        ev = nullptr;
+    }
+    for (cudaStream_t *q : {&p->pipe_in, &p->pipe_out}) {
+        if (*q)
+            cudaStreamDestroy(*q);
+        *q = nullptr;
+    }
     cudaFree(p->d_partial);
     p->d_partial = nullptr;
     cudaFree(p->d_window);
@@ -930,10 +948,10 @@ size_t workspace_of(const sgf_plan *p)
            io_stage_bytes(p);
 }
 
-// Tensor map of the level-0 patch's main column output (the first output, N
-// rows), as k_row_inv1t reads it: floats [comp * (N+1) + kx][2N] (row stride N
-// complex), boxes of 4 floats (one row pair) x kTmaBox bins, zero fill beyond
-// the end.
+// Tensor maps of the level-0 patch's main column output (the first output, N
+// rows), as k_row_inv1t / k_row_inv1x and k_row_inv2x read it: floats
+// [comp * (N+1) + kx][2N] (row stride N complex), boxes of 4 floats (one row
+// pair) and of 8 floats (two row pairs) x kTmaBox bins, zero fill beyond the end.
 sgf_status encode_tmap_inv(sgf_plan *p)
 {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -953,13 +971,16 @@ sgf_status encode_tmap_inv(sgf_plan *p)
     void *base = static_cast<unsigned char *>(p->d_bwd) + o.off * 2 * p->esize;
     const cuuint64_t dims[2] = {2 * (cuuint64_t)N, 2 * (cuuint64_t)(N + 1)};
     const cuuint64_t strides[1] = {(cuuint64_t)N * 2 * sizeof(float)};
-    const cuuint32_t box[2] = {4, (cuuint32_t)kTmaBox};
     const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = encode(reinterpret_cast<CUtensorMap *>(p->tmap_inv), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base,
-                              dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS)
-        return fail(SGF_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    for (int w = 0; w < 2; ++w) {
+        const cuuint32_t box[2] = {w ? 8u : 4u, (cuuint32_t)kTmaBox};
+        const CUresult r =
+            encode(reinterpret_cast<CUtensorMap *>(w ? p->tmap_inv2 : p->tmap_inv), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                   base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+            return fail(SGF_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    }
     return SGF_OK;
 }
 
@@ -1183,17 +1204,24 @@ sgf_status mark(sgf_plan *p, cudaStream_t st)
 // through k_row_inv1 with one / both components per CTA, the finer patches
 // (main output plus Case-3 phases) through k_row_inv; row_inv0 = 1: every
 // patch through k_row_inv; row_inv0 = 3: as 0 with the level-0 gather by the
-// tensor memory accelerator (k_row_inv1t; a.tmap_inv set).
+// tensor memory accelerator (k_row_inv1t; a.tmap_inv set); 4: k_row_inv1x;
+// 5: k_row_inv2x, whose map of two row pairs a box (tmap2) replaces a.tmap_inv.
 template <typename T>
 cudaError_t launch_row_inv(int logN, int L, int R, SolveArgs<T> a, cudaStream_t st, bool tc, int row_inv0,
-                           int inv_radix = 0)
+                           int inv_radix = 0, const unsigned char *tmap2 = nullptr)
 {
     a.level_base = 0;
     if (row_inv0 == 1)
         return launch_pass_n<T>(PASS_ROW_INV, logN, a, L, st, nullptr, tc);
+    if (row_inv0 == 5) {
+        if (!tmap2)
+            return cudaErrorInvalidValue;
+        std::memcpy(a.tmap_inv, tmap2, sizeof a.tmap_inv);
+    }
     const int first = row_inv0 == 2   ? PASS_ROW_INV2
                       : row_inv0 == 3 ? PASS_ROW_INV1T
                       : row_inv0 == 4 ? (inv_radix ? PASS_ROW_INV1X_R1 : PASS_ROW_INV1X)
+                      : row_inv0 == 5 ? (inv_radix ? PASS_ROW_INV2X_R1 : PASS_ROW_INV2X)
                                       : PASS_ROW_INV1;
     cudaError_t e = launch_pass_n<T>(first, logN, a, R, st, nullptr, tc);
     if (e != cudaSuccess || L == R)
@@ -1273,17 +1301,17 @@ cudaError_t launch_col(const sgf_plan *p, const SolveArgs<T> &a, cudaStream_t st
 // for level 0) has no shared memory left for tensor-core tiles at n = 4096.
 inline bool schedule_ok(const sgf_plan *p, const sgf_schedule &s)
 {
-    if (s.col_pass < 0 || s.col_pass > 3 || s.row_inv0 < 0 || s.row_inv0 > 4 || (s.col_case3 != 0 && s.col_case3 != 1))
+    if (s.col_pass < 0 || s.col_pass > 3 || s.row_inv0 < 0 || s.row_inv0 > 5 || (s.col_case3 != 0 && s.col_case3 != 1))
         return false;
-    // k_row_inv1x: the tensor-map gather (row_inv0 = 3's conditions) with n >= 1024
-    if (s.row_inv0 == 4 && !(p->tma_inv && p->N >= 1024))
+    // k_row_inv1x, k_row_inv2x: the tensor-map gather (row_inv0 = 3's conditions) with n >= 1024
+    if ((s.row_inv0 == 4 || s.row_inv0 == 5) && !(p->tma_inv && p->N >= 1024))
         return false;
     // two row pairs per CTA in the zero-rim forward rows: FP32 without tensor-core tiles, N >= 1024
     if (s.row_fwd != 0 && (s.row_fwd != 1 || !(p->merged && p->prec == SGF_FP32 && p->N >= 1024)))
         return false;
-    // radix plans: the register-twiddle kernels only (col_pass 3, row_inv0 4)
+    // radix plans: the register-twiddle kernels only (col_pass 3, row_inv0 4 and 5)
     if ((s.col_radix != 0 && (s.col_radix != 1 || s.col_pass != 3)) ||
-        (s.inv_radix != 0 && (s.inv_radix != 1 || s.row_inv0 != 4)))
+        (s.inv_radix != 0 && (s.inv_radix != 1 || s.row_inv0 < 4)))
         return false;
     // k_col_mx: zero-rim forces, FP32 without tensor-core tiles, N >= 1024
     if (s.col_pass == 3 && !(p->merged && !p->pot && p->prec == SGF_FP32 && p->N >= 1024))
@@ -1391,7 +1419,8 @@ sgf_status solve_core(sgf_plan *p, const void *const *sigma, void *const *fx, vo
         return cuda_fail(e, "col launch");
     if ((ms = mark(p, st)) != SGF_OK)
         return ms;
-    if ((e = launch_row_inv<T>(p->logN, L, p->fo.R, a, st, p->tc, p->sched.row_inv0, p->sched.inv_radix)) !=
+    if ((e = launch_row_inv<T>(p->logN, L, p->fo.R, a, st, p->tc, p->sched.row_inv0, p->sched.inv_radix,
+                               p->tmap_inv2)) !=
         cudaSuccess)
         return cuda_fail(e, "row_inv launch");
     return mark(p, st);
@@ -1883,7 +1912,7 @@ void tune_load_locked()
     char key[160];
     int a = 0, b = 0, c = 0, d = 0, r = 0, w = 0;
     while (fscanf(f, "%159s %d %d %d %d %d %d", key, &a, &b, &c, &d, &r, &w) == 7)
-        if (a >= 0 && a <= 3 && b >= 0 && b <= 4 && (c == 0 || c == 1) && (d == 0 || d == 1) && (r == 0 || r == 1) &&
+        if (a >= 0 && a <= 3 && b >= 0 && b <= 5 && (c == 0 || c == 1) && (d == 0 || d == 1) && (r == 0 || r == 1) &&
             (w == 0 || w == 1))
             g_tune[key] = sgf_schedule{a, b, c, d, r, w};
     fclose(f);
@@ -2010,24 +2039,26 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[SGF_A
             }
         }
     }
-    // candidates 0..4, and 5 = row_inv0 4 with radix plan 1 (3, 4, 5 appended after col_case3)
-    auto inv_slot = [](int c) { return c < 3 ? 3 + c : c == 3 ? 8 : c == 4 ? 10 : 12; };
+    // candidates 0..4, 5 = row_inv0 4 with radix plan 1, 6 = row_inv0 5 and 7 = row_inv0 5 with
+    // radix plan 1 (3..7 appended after col_case3)
+    static const int inv_slots[8] = {3, 4, 5, 8, 10, 12, 15, 16};
+    auto inv_slot = [](int c) { return inv_slots[c]; };
     auto inv_cand = [&](int c) {
         sgf_schedule cand = best;
-        cand.row_inv0 = c < 5 ? c : 4;
-        cand.inv_radix = c == 5 ? 1 : 0;
+        cand.row_inv0 = c < 5 ? c : c == 5 ? 4 : 5;
+        cand.inv_radix = c == 5 || c == 7 ? 1 : 0;
         return cand;
     };
-    for (int c = 0; c < 6 && s == SGF_OK; ++c) {
+    for (int c = 0; c < 8 && s == SGF_OK; ++c) {
         const sgf_schedule cand = inv_cand(c);
         if (schedule_ok(p, cand))
             s = timeit([&] { return launch_row_inv<T>(p->logN, p->L, p->fo.R, a, st, p->tc, cand.row_inv0,
-                                                      cand.inv_radix); },
+                                                      cand.inv_radix, p->tmap_inv2); },
                        ms[inv_slot(c)]);
     }
     if (s == SGF_OK) {  // the fastest of the candidates that apply (and were timed)
         int bc = -1;
-        for (int c = 0; c < 6; ++c)
+        for (int c = 0; c < 8; ++c)
             if (ms[inv_slot(c)] >= 0.0 && (bc < 0 || ms[inv_slot(c)] < ms[inv_slot(bc)]))
                 bc = c;
         if (bc >= 0) {
@@ -2449,6 +2480,88 @@ sgf_status sgf_solve_host(sgf_plan *p, const void *const *sigma, void *const *fx
     return SGF_OK;
 }
 
+sgf_status sgf_solve_host_many(sgf_plan *p, int32_t count, const void *const *sigma, void *const *fx,
+                               void *const *fy, void *stream)
+{
+    if (!p)
+        return fail(SGF_EINVAL, "plan is NULL");
+    if (count < 0 || (count > 0 && (!sigma || !fx || !fy)))
+        return fail(SGF_EINVAL, "bad arguments (count %d)", (int)count);
+    for (int k = 0; k < count; ++k) {
+        sgf_status s = check_ptrs(p, sigma + (size_t)k * p->L, fx + (size_t)k * p->L, fy + (size_t)k * p->L);
+        if (s != SGF_OK)
+            return s;
+    }
+    if (count == 0)
+        return SGF_OK;
+    DeviceGuard g(p->device);
+    const int L = p->L;
+    const size_t lvl = (size_t)p->n_log * p->n_log * p->esize;  // the caller's n x n arrays
+    const size_t lvl_al = (lvl + 255) & ~(size_t)255;
+    cudaError_t e;
+    if (!p->d_pipe) {
+        if ((e = cudaMalloc(&p->d_pipe, 6 * (size_t)L * lvl_al)) != cudaSuccess)
+            return cuda_fail(e, "cudaMalloc(host-solve pipeline staging)");
+        p->workspace_bytes += 6 * (size_t)L * lvl_al;
+    }
+    for (cudaStream_t *q : {&p->pipe_in, &p->pipe_out})
+        if (!*q && (e = cudaStreamCreateWithFlags(q, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamCreate(host-solve pipeline)");
+    for (cudaEvent_t &ev : p->pipe_ev)
+        if (!ev && (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(e, "cudaEventCreate(host-solve pipeline)");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t *in_ev = p->pipe_ev, *solved_ev = p->pipe_ev + 2, *out_ev = p->pipe_ev + 4;
+    // earlier work on the caller's stream (its buffers' producers) comes first
+    if ((e = cudaEventRecord(solved_ev[0], st)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(p->pipe_in, solved_ev[0], 0)) != cudaSuccess)
+        return cuda_fail(e, "host-solve pipeline ordering");
+    for (int k = 0; k < count; ++k) {
+        const int slot = k & 1;
+        auto base = static_cast<unsigned char *>(p->d_pipe) + (size_t)slot * 3 * L * lvl_al;
+        const void *ds[kMaxPatches];
+        void *dx[kMaxPatches], *dy[kMaxPatches];
+        for (int l = 0; l < L; ++l) {
+            ds[l] = base + (size_t)l * lvl_al;
+            dx[l] = base + (size_t)(L + l) * lvl_al;
+            dy[l] = base + (size_t)(2 * L + l) * lvl_al;
+        }
+        // copy in: the set's density is free once problem k-2 was solved
+        if (k >= 2 && (e = cudaStreamWaitEvent(p->pipe_in, solved_ev[slot], 0)) != cudaSuccess)
+            return cuda_fail(e, "host-solve pipeline ordering");
+        for (int l = 0; l < L; ++l)
+            if ((e = cudaMemcpyAsync(const_cast<void *>(ds[l]), sigma[(size_t)k * L + l], lvl, cudaMemcpyHostToDevice,
+                                     p->pipe_in)) != cudaSuccess)
+                return cuda_fail(e, "cudaMemcpyAsync(sigma H2D)");
+        if ((e = cudaEventRecord(in_ev[slot], p->pipe_in)) != cudaSuccess)
+            return cuda_fail(e, "cudaEventRecord(host-solve pipeline)");
+        // solve: the density is in, and the set's forces of problem k-2 are out
+        if ((e = cudaStreamWaitEvent(st, in_ev[slot], 0)) != cudaSuccess ||
+            (k >= 2 && (e = cudaStreamWaitEvent(st, out_ev[slot], 0)) != cudaSuccess))
+            return cuda_fail(e, "host-solve pipeline ordering");
+        sgf_status s = solve_dispatch(p, ds, dx, dy, st);
+        if (s != SGF_OK)
+            return s;
+        if ((e = cudaEventRecord(solved_ev[slot], st)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(p->pipe_out, solved_ev[slot], 0)) != cudaSuccess)
+            return cuda_fail(e, "host-solve pipeline ordering");
+        // copy out
+        for (int l = 0; l < L; ++l)
+            if ((e = cudaMemcpyAsync(fx[(size_t)k * L + l], dx[l], lvl, cudaMemcpyDeviceToHost, p->pipe_out)) !=
+                    cudaSuccess ||
+                (e = cudaMemcpyAsync(fy[(size_t)k * L + l], dy[l], lvl, cudaMemcpyDeviceToHost, p->pipe_out)) !=
+                    cudaSuccess)
+                return cuda_fail(e, "cudaMemcpyAsync(force D2H)");
+        if ((e = cudaEventRecord(out_ev[slot], p->pipe_out)) != cudaSuccess)
+            return cuda_fail(e, "cudaEventRecord(host-solve pipeline)");
+    }
+    // the caller's stream ends after the last copy out
+    if ((e = cudaStreamWaitEvent(st, out_ev[(count - 1) & 1], 0)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(e, "solve (host buffers, pipelined)");
+    return SGF_OK;
+}
+
 sgf_status sgf_solve_batched(sgf_plan *const *plans, int32_t count, const void *const *const *sigma,
                              void *const *const *fx, void *const *const *fy, void *stream)
 {
@@ -2539,7 +2652,7 @@ sgf_status sgf_plan_schedule_set(sgf_plan *p, const sgf_schedule *in)
 {
     if (!p || !in)
         return fail(SGF_EINVAL, "NULL argument");
-    if (in->col_pass < 0 || in->col_pass > 3 || in->row_inv0 < 0 || in->row_inv0 > 4 ||
+    if (in->col_pass < 0 || in->col_pass > 3 || in->row_inv0 < 0 || in->row_inv0 > 5 ||
         (in->col_case3 != 0 && in->col_case3 != 1) || in->col_radix < 0 || in->col_radix > 1 || in->inv_radix < 0 ||
         in->inv_radix > 1 || in->row_fwd < 0 || in->row_fwd > 1)
         return fail(SGF_EINVAL, "schedule out of range (col_pass %d, row_inv0 %d, col_case3 %d)", in->col_pass,

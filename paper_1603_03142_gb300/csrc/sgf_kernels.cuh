@@ -1486,6 +1486,142 @@ __global__ void __launch_bounds__(KRx<LOGN>::THREADS, 1) k_row_inv1x(const __gri
     }
 }
 
+// ---------------------------------------------------------------- row_inv2x
+// k_row_inv1x with two row pairs per item: the tensor memory accelerator gathers
+// both pairs' bins of one component at once, so each copied piece is the 32
+// bytes of two neighbouring pairs (a.tmap_inv encoded with boxes of 8 floats),
+// half the requests a pair-by-pair gather makes.  The two pairs are
+// transformed one after the other from the stage; the next item's gather is
+// issued once the second pair is in registers.  A thread reads its two parity
+// halves' bins in the order (s, 1 - s), s = bit 1 of its slot, so that the eight
+// threads of a quarter warp touch eight distinct 16-byte bank groups in pairs
+// (two-way, as the one-pair stage) instead of four-way.  G groups as many as fit
+// in shared memory (at most 256 threads).  FP32, N >= 1024, one level-0 patch.
+// Dynamic shared memory a CTA may opt in to (227 KB).
+constexpr size_t kMaxDynSmem = 232448;
+
+template <int LOGN>
+struct KR2x {
+    static constexpr int N = 1 << LOGN, Q = N >> 4;
+    static constexpr int NBOX = (N + 1 + kTmaBox - 1) / kTmaBox;
+    static constexpr uint32_t STAGE_BYTES = (uint32_t)NBOX * kTmaBox * 32;
+    static constexpr size_t XB = 2 * (size_t)KShape<LOGN>::SP_ROW * 8;
+    static constexpr size_t GROUP_BYTES = ((STAGE_BYTES + XB + 16 + 127) / 128) * 128;
+    static constexpr int GMAX = Q >= 256 ? 1 : 256 / Q;
+    static constexpr int GFIT = (int)((kMaxDynSmem - 128) / GROUP_BYTES);
+    static constexpr int G = GFIT < GMAX ? GFIT : GMAX;
+    static constexpr int THREADS = G * Q;
+    static constexpr size_t SMEM = G * GROUP_BYTES + 128;  // + alignment slack
+    static_assert(G >= 1, "one group's stage must fit in shared memory");
+};
+
+template <int LOGN, int PLAN>
+__global__ void __launch_bounds__(KR2x<LOGN>::THREADS, 1) k_row_inv2x(const __grid_constant__ SolveArgs<float> a)
+{
+    using C = float2;
+    using R = KR2x<LOGN>;
+    using P = FR<LOGN, PLAN>;
+    constexpr int N = R::N, Q = R::Q, SP = KShape<LOGN>::SP_ROW, PP = 2 * N;
+    static_assert(Q >= 64, "named group barriers need whole warps");
+    extern __shared__ __align__(16) unsigned char smem_dyn[];
+    const uint32_t base_s = (uint32_t)__cvta_generic_to_shared(smem_dyn);
+    unsigned char *smem_al = smem_dyn + (((base_s + 127u) & ~127u) - base_s);
+    const int t = threadIdx.x;
+    const int g = t / Q, j = t - g * Q;
+    unsigned char *gb = smem_al + (size_t)g * R::GROUP_BYTES;
+    unsigned char *stage = gb;
+    C *xb = reinterpret_cast<C *>(gb + R::STAGE_BYTES);
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(gb + R::STAGE_BYTES + R::XB);
+    volatile int *gave_up = reinterpret_cast<volatile int *>(gb + R::STAGE_BYTES + R::XB + 8);
+    const unsigned bar = 1 + g;
+    const int tl = a.level_base;
+    const int items = a.ncomp * (N / 4);
+    C trw[P::NST - 1][15];
+    load_twiddles_rt<C, LOGN, PLAN>(trw, a.twn, j);
+    const TwLayout twl = tw_layout(F16<LOGN>::twlen, N);
+    const C wj = a.tw[twl.base + j];  // W_P^j
+    auto twist_u = [&](int u) { return hmul(wj, hmk<C>((float)kW32c[u], (float)-kW32s[u])); };
+    const long long bound = a.wait_cycles > 0 ? a.wait_cycles : kTmaWaitCycles;
+    const bool withhold = (a.inject & INJECT_TMA_GATHER) != 0;
+    const int s = (j >> 1) & 1;  // which parity half this thread reads first
+    auto gather = [&](int it) {  // one thread of the group: the bins of item it
+        if (withhold)
+            return;  // (a test withholds the copies)
+        // the stage was last read through the generic proxy: order that before the copies
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        const int comp = it >= N / 4 ? 1 : 0;
+        const int q = it - comp * (N / 4);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mb), "r"(R::STAGE_BYTES)
+                     : "memory");
+        const unsigned long long map = reinterpret_cast<unsigned long long>(&a.tmap_inv[0]);
+        for (int k = 0; k < R::NBOX; ++k) {
+            const uint32_t dst = (uint32_t)__cvta_generic_to_shared(stage + (size_t)k * kTmaBox * 32);
+            const int x = 8 * q, y = comp * (N + 1) + k * kTmaBox;  // x: 8 floats two row pairs, 32-byte aligned
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                "[%4];\n" ::"r"(dst),
+                "l"(map), "r"(x), "r"(y), "r"(mb)
+                : "memory");
+        }
+    };
+    // bin kx of pair h (0, 1) of the staged item as the packed complex row value
+    auto bin = [&](int kx, int h) {
+        const int k2 = kx <= N ? kx : PP - kx;
+        const float4 ab = *reinterpret_cast<const float4 *>(stage + (size_t)k2 * 32 + h * 16);
+        const C A = hmk<C>(ab.x, ab.y), B = hmk<C>(ab.z, ab.w);
+        return kx <= N ? hmk<C>(A.x - B.y, A.y + B.x) : hmk<C>(A.x + B.y, B.x - A.y);
+    };
+    const int step = (int)gridDim.x * R::G;
+    int it = (int)blockIdx.x * R::G + g;
+    if (j == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(mb), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        *gave_up = 0;
+    }
+    group_sync(bar, Q);  // the mbarrier is initialised
+    if (j == 0 && it < items)
+        gather(it);
+    for (uint32_t phase = 0; it < items; it += step, ++phase) {  // uniform over the group
+        if (!tc_try_wait(mb, phase & 1u, bound))
+            *gave_up = 1;
+        group_sync(bar, Q);
+        if (*gave_up) {  // every thread of the group sees it after the barrier
+            if (j == 0)
+                atomicOr(a.status, STATUS_TMA_TIMEOUT);
+            tc_try_wait(mb, phase & 1u, bound);  // copies that may still land in the stage
+            break;
+        }
+        const int comp = it >= N / 4 ? 1 : 0;
+        const int q = it - comp * (N / 4);
+        float *out = comp ? a.fy[tl] : a.fx[tl];
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            C v[2][16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int k0 = 2 * (j + u * Q);
+                const C first = bin(k0 + s, h), second = bin(k0 + 1 - s, h);
+                v[0][u] = s ? second : first;
+                v[1][u] = s ? first : second;
+            }
+            if (h == 1) {
+                group_sync(bar, Q);  // every thread has read the stage (and pair 0's exchanges)
+                if (j == 0 && it + step < items)
+                    gather(it + step);
+            }
+            fft_stages_rt<C, true, LOGN, PLAN, 2, 0>(v, xb, SP, j, trw, bar, Q);
+            const int j0 = 4 * q + 2 * h, j1 = j0 + 1;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int n = j + u * Q;
+                const C y = hadd(v[0][u], hmulc(v[1][u], twist_u(u)));
+                out[(size_t)j0 * N + n] = covered(a, tl, j0, n) ? 0.0f : y.x;
+                out[(size_t)j1 * N + n] = covered(a, tl, j1, n) ? 0.0f : y.y;
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------ zero-rim path
 // Forward row pass of a SGF_PLAN_ZERO_RIM plan: the rows of sigma alone (the
 // slopes are folded into the merged spectra).  Also verifies the guarantee:
@@ -2245,7 +2381,6 @@ struct KSmem {
 // that needs more than an SM offers (k_row_inv with tensor-core tiles at
 // n = 4096, a configuration the host refuses) is left alone here; launching it
 // would fail with a launch error.
-constexpr size_t kMaxDynSmem = 232448;
 template <typename F>
 inline cudaError_t ensure_smem(F *kernel, size_t bytes, std::atomic<unsigned long long> &done)
 {
@@ -2300,9 +2435,10 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
 {
     using K = KShape<LOGN>;
     using S = KSmem<T, LOGN, TC>;
-    static std::atomic<unsigned long long> d[33];
+    static std::atomic<unsigned long long> d[35];
     static std::atomic<int> res_mx[64], res_mx1[64];  // resident CTAs of the register-twiddle column pass (plans 0, 1)
     static std::atomic<int> res_rx[64], res_rx1[64];  // and of the register-twiddle inverse row pass
+    static std::atomic<int> res_r2[64], res_r21[64];  // and of its two-pair form
     static std::atomic<int> res_mw[64], res_mw1[64];  // resident CTAs of the walking column pass (NC = 2, 1)
     static std::atomic<int> res_fm[64];               // and of the walking zero-rim forward row pass
     static std::atomic<int> res_ri1[64], res_ri2[64]; // and of the walking inverse row passes (tensor cores)
@@ -2393,6 +2529,12 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
                 (e = resident_ctas(k_row_inv1x<LOGN, 0>, RX::THREADS, RX::SMEM, res_rx, &grid)) != cudaSuccess ||
                 (e = ensure_smem(k_row_inv1x<LOGN, 1>, RX::SMEM, d[31])) != cudaSuccess ||
                 (e = resident_ctas(k_row_inv1x<LOGN, 1>, RX::THREADS, RX::SMEM, res_rx1, &grid)) != cudaSuccess ||
+                (e = ensure_smem(k_row_inv2x<LOGN, 0>, KR2x<LOGN>::SMEM, d[33])) != cudaSuccess ||
+                (e = resident_ctas(k_row_inv2x<LOGN, 0>, KR2x<LOGN>::THREADS, KR2x<LOGN>::SMEM, res_r2, &grid)) !=
+                    cudaSuccess ||
+                (e = ensure_smem(k_row_inv2x<LOGN, 1>, KR2x<LOGN>::SMEM, d[34])) != cudaSuccess ||
+                (e = resident_ctas(k_row_inv2x<LOGN, 1>, KR2x<LOGN>::THREADS, KR2x<LOGN>::SMEM, res_r21, &grid)) !=
+                    cudaSuccess ||
                 (e = ensure_smem(k_row_fwd_m2<LOGN>, S::tw() + 4 * (size_t)K::N * sizeof(float) +
                                                          4 * (size_t)K::SP_ROW * sizeof(float2), d[32])) != cudaSuccess)
                 return e;
@@ -2555,6 +2697,25 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
                 return e;
             const int groups = (a.ncomp * (K::N / 2) + RX::G - 1) / RX::G;  // CTAs that give every group an item
             kern<<<dim3(grid < groups ? grid : groups, count), RX::THREADS, RX::SMEM, st>>>(a);
+        } else {
+            return cudaErrorInvalidValue;
+        }
+        break;
+    }
+    case PASS_ROW_INV2X:
+    case PASS_ROW_INV2X_R1: {
+        if constexpr (!TC && sizeof(T) == 4 && LOGN >= 10) {
+            if (batch)
+                return cudaErrorInvalidValue;
+            using R2 = KR2x<LOGN>;
+            const bool r1 = pass == PASS_ROW_INV2X_R1;
+            auto *kern = r1 ? k_row_inv2x<LOGN, 1> : k_row_inv2x<LOGN, 0>;
+            int grid = 0;
+            if ((e = ensure_smem(kern, R2::SMEM, d[r1 ? 34 : 33])) != cudaSuccess ||
+                (e = resident_ctas(kern, R2::THREADS, R2::SMEM, r1 ? res_r21 : res_r2, &grid)) != cudaSuccess)
+                return e;
+            const int groups = (a.ncomp * (K::N / 4) + R2::G - 1) / R2::G;  // CTAs that give every group an item
+            kern<<<dim3(grid < groups ? grid : groups, count), R2::THREADS, R2::SMEM, st>>>(a);
         } else {
             return cudaErrorInvalidValue;
         }

@@ -34,12 +34,12 @@ EXPORTS = ["sgf_plan_create", "sgf_plan_create_ex", "sgf_plan_check", "sgf_plan_
            "sgf_server_clock", "sgf_server_submit", "sgf_server_progress", "sgf_server_stats_get",
            "sgf_server_destroy", "sgf_plan_schedule_get", "sgf_plan_schedule_set", "sgf_plan_autotune",
            "sgf_plan_share_ex", "sgf_solve_potential", "sgf_plan_create_forest", "sgf_plan_estimate_forest",
-           "sgf_plan_footprint", "sgf_plan_inject_timeout"]
+           "sgf_plan_footprint", "sgf_plan_inject_timeout", "sgf_solve_host_many"]
 BATCH_NO_GRAPH = 0x1
 PLAN_ZERO_RIM = 0x1
 PLAN_POTENTIAL = 0x2
 NOALLOC_SCRATCH_BYTES = 32 << 20
-AUTOTUNE_TIMES = 15
+AUTOTUNE_TIMES = 17
 KERNELS = ["restrict", "row_fwd", "col", "row_inv"]
 
 
@@ -119,6 +119,7 @@ _lib.sgf_plan_share_ex.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER
 _lib.sgf_plan_stats_get.argtypes = [ctypes.c_void_p, ctypes.POINTER(PlanStats)]
 _lib.sgf_solve.argtypes = [ctypes.c_void_p, _vpp, _vpp, _vpp, ctypes.c_void_p]
 _lib.sgf_solve_host.argtypes = [ctypes.c_void_p, _vpp, _vpp, _vpp, ctypes.c_void_p]
+_lib.sgf_solve_host_many.argtypes = [ctypes.c_void_p, ctypes.c_int32, _vpp, _vpp, _vpp, ctypes.c_void_p]
 _lib.sgf_solve_noalloc.argtypes = [ctypes.c_void_p, _vpp, _vpp, _vpp, ctypes.c_void_p]
 _lib.sgf_solve_potential.argtypes = [ctypes.c_void_p, _vpp, _vpp, ctypes.c_void_p]
 _lib.sgf_batch_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.c_uint32,
@@ -158,7 +159,7 @@ for _f in ("sgf_plan_create", "sgf_plan_create_ex", "sgf_plan_check", "sgf_plan_
            "sgf_plan_estimate", "sgf_server_create", "sgf_server_submit", "sgf_server_progress",
            "sgf_server_stats_get", "sgf_server_destroy", "sgf_plan_schedule_get", "sgf_plan_schedule_set",
            "sgf_plan_autotune", "sgf_plan_share_ex", "sgf_solve_potential", "sgf_plan_create_forest",
-           "sgf_plan_estimate_forest", "sgf_plan_footprint", "sgf_plan_inject_timeout"):
+           "sgf_plan_estimate_forest", "sgf_plan_footprint", "sgf_plan_inject_timeout", "sgf_solve_host_many"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -324,7 +325,7 @@ class Plan:
                        "row_inv0_1": ms[4], "row_inv0_2": ms[5], "col_case3_0": ms[6], "col_case3_1": ms[7],
                        "row_inv0_3": ms[8], "col_pass3": ms[9], "row_inv0_4": ms[10],
                        "col_pass3_radix1": ms[11], "row_inv0_4_radix1": ms[12], "row_fwd0": ms[13],
-                       "row_fwd1": ms[14]}}
+                       "row_fwd1": ms[14], "row_inv0_5": ms[15], "row_inv0_5_radix1": ms[16]}}
 
     def profile(self, enable: bool = True):
         _check(_lib.sgf_plan_profile(self._h, 1 if enable else 0), "sgf_plan_profile")
@@ -391,6 +392,12 @@ class Plan:
     def solve_host_ptrs(self, sigma_ptrs, fx_ptrs, fy_ptrs, stream=None):
         _check(_lib.sgf_solve_host(self._h, _ptrs(sigma_ptrs), _ptrs(fx_ptrs), _ptrs(fy_ptrs),
                                    ctypes.c_void_p(_stream_handle(stream))), "sgf_solve_host")
+
+    def solve_host_many_ptrs(self, count, sigma_ptrs, fx_ptrs, fy_ptrs, stream=None):
+        """sgf_solve_host_many: `count` problems in host memory, problem k's level l at
+        index k * levels + l of each pointer list; copies overlap the transforms."""
+        _check(_lib.sgf_solve_host_many(self._h, int(count), _ptrs(sigma_ptrs), _ptrs(fx_ptrs), _ptrs(fy_ptrs),
+                                        ctypes.c_void_p(_stream_handle(stream))), "sgf_solve_host_many")
 
     def close(self):
         if getattr(self, "_h", None):

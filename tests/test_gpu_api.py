@@ -94,6 +94,64 @@ def test_mapped_host_buffers_zero_rim_4096(lib):
     assert torch.equal(hx, dx.cpu()) and torch.equal(hy, dy.cpu())
 
 
+@pytest.mark.parametrize("pinned", [True, False], ids=["pinned", "pageable"])
+def test_host_many_matches_device_solves(lib, pinned):
+    """sgf_solve_host_many over five 3-level problems (both staging sets used
+    twice or more, a distinct density per problem): every problem's forces are
+    the device-buffer solve's, bit for bit, and nothing else is written."""
+    nest = W.Nest(n=64, levels=3, off=[(0, 0), (10, 20), (16, 0)])
+    rng = np.random.Generator(np.random.PCG64(21))
+    probs = [[rng.uniform(0, 1, (64, 64)).astype(np.float32) for _ in range(3)] for _ in range(5)]
+    plan = lib.Plan(nest, "fp32")
+    ref = [run_gpu(plan, s) for s in probs]
+    before = plan.stats()["workspace_bytes"]
+    wrap = _pinned if pinned else np.ascontiguousarray
+    ps = [[wrap(a) for a in s] for s in probs]
+    hx = [[wrap(np.full((64, 64), np.nan, np.float32)) for _ in range(3)] for _ in probs]
+    hy = [[wrap(np.full((64, 64), np.nan, np.float32)) for _ in range(3)] for _ in probs]
+
+    def ptr(a):
+        return a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data
+
+    def arr(a):
+        return a.numpy() if isinstance(a, torch.Tensor) else a
+
+    flat = lambda xs: [ptr(a) for s in xs for a in s]  # noqa: E731
+    for _ in range(2):
+        plan.solve_host_many_ptrs(len(probs), flat(ps), flat(hx), flat(hy))
+        for k in range(len(probs)):
+            for l in range(3):
+                assert np.array_equal(arr(hx[k][l]).astype(np.float64), ref[k][0][l]), (k, l)
+                assert np.array_equal(arr(hy[k][l]).astype(np.float64), ref[k][1][l]), (k, l)
+    assert plan.stats()["workspace_bytes"] == before + 6 * 3 * 64 * 64 * 4
+    plan.solve_host_many_ptrs(0, [], [], [])  # a no-op
+    with pytest.raises(lib.SgfError) as e:
+        plan.solve_host_many_ptrs(-1, [], [], [])
+    assert e.value.status == lib.SGF_EINVAL
+    with pytest.raises(lib.SgfError) as e:  # problem 1's level 2 density missing
+        plan.solve_host_many_ptrs(2, flat(ps)[:5] + [0], flat(hx)[:6], flat(hy)[:6])
+    assert e.value.status == lib.SGF_EINVAL
+
+
+def test_host_many_zero_rim_4096(lib):
+    """The bench's end-to-end call: three 4096^2 zero-rim FP32 problems, page-locked."""
+    plan = lib.Plan(W.Nest(n=4096), "fp32", zero_rim=True)
+    sig = [W.config3(4096, seed=3 + k)[1][0].astype(np.float32) for k in range(3)]
+    ref = []
+    for s in sig:
+        ts = torch.from_numpy(s).cuda()
+        dx, dy = torch.empty_like(ts), torch.empty_like(ts)
+        plan.solve_ptrs([ts.data_ptr()], [dx.data_ptr()], [dy.data_ptr()])
+        ref.append((dx.cpu(), dy.cpu()))
+    ps = [_pinned(s) for s in sig]
+    hx = [_pinned(np.zeros_like(s)) for s in sig]
+    hy = [_pinned(np.zeros_like(s)) for s in sig]
+    plan.solve_host_many_ptrs(3, [a.data_ptr() for a in ps], [a.data_ptr() for a in hx], [a.data_ptr() for a in hy])
+    plan.check()
+    for k in range(3):
+        assert torch.equal(hx[k], ref[k][0]) and torch.equal(hy[k], ref[k][1])
+
+
 def test_deterministic_and_shared_plan(lib):
     nest, sigma = W.config2(n=64)
     plan = lib.Plan(nest, "fp32")

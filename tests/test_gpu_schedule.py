@@ -52,8 +52,9 @@ def test_schedules_agree_zero_rim(lib, prec, n):
         with pytest.raises(lib.SgfError) as ei:
             plan.set_schedule(3, 0)
         assert ei.value.status == lib.SGF_EUNSUPPORTED
-    # (choice, radix plan): col_pass 3 and row_inv0 4 in both radix plans (register-twiddle kernels)
-    invs = [(0, 0), (1, 0), (2, 0)] + ([(3, 0)] if tma else []) + ([(4, 0), (4, 1)] if tma and n >= 1024 else [])
+    # (choice, radix plan): col_pass 3 and row_inv0 4, 5 in both radix plans (register-twiddle kernels)
+    invs = [(0, 0), (1, 0), (2, 0)] + ([(3, 0)] if tma else []) + (
+        [(4, 0), (4, 1), (5, 0), (5, 1)] if tma and n >= 1024 else [])
     cols = [(0, 0), (1, 0), (2, 0)] + ([(3, 0), (3, 1)] if mx else [])
     fwds = (0, 1) if mx else (0,)  # row_fwd = 1: two row pairs per CTA in the forward rows
     for col, cr in cols:
@@ -157,10 +158,11 @@ print(json.dumps({"r": r, "q": q.schedule()}))
     assert (ch["col_pass"], ch["col_radix"]) == ((best, 0) if best < 4 else (3, 1))
     assert ms["row_inv0_3"] > 0  # FP32, n = 1024, one level-0 patch
     assert ms["row_inv0_4"] > 0 and ms["row_inv0_4_radix1"] > 0
+    assert ms["row_inv0_5"] > 0 and ms["row_inv0_5_radix1"] > 0
     inv = [ms["row_inv0_0"], ms["row_inv0_1"], ms["row_inv0_2"], ms["row_inv0_3"], ms["row_inv0_4"],
-           ms["row_inv0_4_radix1"]]
+           ms["row_inv0_4_radix1"], ms["row_inv0_5"], ms["row_inv0_5_radix1"]]
     best = inv.index(min(inv))
-    assert (ch["row_inv0"], ch["inv_radix"]) == ((best, 0) if best < 5 else (4, 1))
+    assert (ch["row_inv0"], ch["inv_radix"]) == [(0, 0), (1, 0), (2, 0), (3, 0), (4, 0), (4, 1), (5, 0), (5, 1)][best]
     assert ms["row_fwd0"] > 0 and ms["row_fwd1"] > 0
     assert ch["row_fwd"] == (1 if ms["row_fwd1"] < ms["row_fwd0"] else 0)
     assert d["q"] == ch
@@ -179,9 +181,9 @@ print(json.dumps(sgf.Plan(W.Nest(n=1024), "fp32", zero_rim=True).schedule()))
 
 @pytest.mark.parametrize("case", ["zero_rim_4096", "general_1024", "nest_512", "potential_1024"])
 def test_tma_gather_matches_lane_gather(lib, case):
-    """row_inv0 = 3 (k_row_inv1t) and 4 (k_row_inv1x) against row_inv0 = 0
-    (k_row_inv1): the same arithmetic on the same bins, only the gather and the
-    thread layout differ."""
+    """row_inv0 = 3 (k_row_inv1t), 4 (k_row_inv1x) and 5 (k_row_inv2x) against
+    row_inv0 = 0 (k_row_inv1): the same arithmetic on the same bins, only the
+    gather and the thread layout differ."""
     rng = np.random.Generator(np.random.PCG64(31))
     kw = {}
     if case == "zero_rim_4096":
@@ -212,12 +214,13 @@ def test_tma_gather_matches_lane_gather(lib, case):
     eps = np.finfo(np.float32).eps
     for ga, gb in zip(a[0] + a[1], b[0] + b[1]):
         assert np.abs(ga - gb).max() <= 64 * eps * np.abs(ga).max()
-    if nest.n >= 1024:  # row_inv0 = 4: k_row_inv1x, walking CTAs, both parity halves per thread
-        plan.set_schedule(0, 4)
-        c = run()
-        plan.check()
-        for ga, gc in zip(a[0] + a[1], c[0] + c[1]):
-            assert np.abs(ga - gc).max() <= 64 * eps * np.abs(ga).max()
+    if nest.n >= 1024:  # row_inv0 = 4, 5: k_row_inv1x / k_row_inv2x, walking CTAs, both parity halves per thread
+        for inv in (4, 5):
+            plan.set_schedule(0, inv)
+            c = run()
+            plan.check()
+            for ga, gc in zip(a[0] + a[1], c[0] + c[1]):
+                assert np.abs(ga - gc).max() <= 64 * eps * np.abs(ga).max()
 
 
 def test_tma_schedule_falls_back_where_it_cannot_apply(lib):
@@ -245,7 +248,7 @@ def test_tma_schedule_falls_back_where_it_cannot_apply(lib):
     # not available: FP64, BF16X, two level-0 patches
     for p in (lib.Plan(nest, "fp64"), lib.Plan(nest, "bf16x"),
               lib.Plan(W.Forest(n=512, level=[0, 0], org=[(0, 0), (512, 0)]), "fp32")):
-        for inv in (3, 4):
+        for inv in (3, 4, 5):
             with pytest.raises(lib.SgfError) as ei:
                 p.set_schedule(0, inv)
             assert ei.value.status == lib.SGF_EUNSUPPORTED

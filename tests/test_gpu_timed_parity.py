@@ -90,9 +90,9 @@ def sample(n):
 
 def schedules(n, prec, zero_rim):
     """Every (col_pass, row_inv0) the plan accepts (sgf.h: schedule rules); the
-    register-twiddle kernels (col_pass 3, row_inv0 4) also in radix plan 1."""
+    register-twiddle kernels (col_pass 3, row_inv0 4 and 5) also in radix plan 1."""
     cols = ((0, 1, 2, 3) if prec == "fp32" and n >= 1024 else (0, 1, 2)) if zero_rim else (0, 2)
-    invs = (0, 1, 2, 3, 4)
+    invs = (0, 1, 2, 3, 4, 5)
     out = []
     for c in cols:
         for i in invs:
@@ -100,14 +100,14 @@ def schedules(n, prec, zero_rim):
                 continue
             if i == 3 and (prec != "fp32" or n < 512):
                 continue
-            if i == 4 and (prec != "fp32" or n < 1024):
+            if i in (4, 5) and (prec != "fp32" or n < 1024):
                 continue
             if prec == "bf16x" and n == 4096 and (c == 2 or i == 1):
                 continue
             out.append((c, i, 0, 0, 0))
             if c == 3:
                 out.append((c, i, 1, 0, 0))
-            if i == 4:
+            if i in (4, 5):
                 out.append((c, i, 0, 1, 0))
             if zero_rim and prec == "fp32" and n >= 1024 and c in (2, 3):
                 out.append((c, i, 0, 0, 1))  # two row pairs per CTA in the forward rows
@@ -153,10 +153,10 @@ def test_4096_autotuned_plan_against_oracle(lib, prec, zero_rim):
     assert s.rel_err(gx[0], gy[0]) <= tol(prec, 4096)
 
 
-@pytest.mark.parametrize("col_pass,row_inv0", [(2, 3), (3, 3), (3, 4)])
+@pytest.mark.parametrize("col_pass,row_inv0", [(2, 3), (3, 3), (3, 4), (3, 5)])
 def test_4096_timed_schedule_explicitly(lib, col_pass, row_inv0):
     """Zero-rim FP32 with the level-0 inverse rows gathered by the tensor memory
-    accelerator (k_row_inv1t, k_row_inv1x) behind either walking column pass
+    accelerator (k_row_inv1t, k_row_inv1x, k_row_inv2x) behind either walking column pass
     (k_col_mw, k_col_mx), the candidates the benchmark's autotuner chooses
     from, solved twice (the second solve runs on the first one's leftover
     intermediates)."""

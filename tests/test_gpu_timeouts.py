@@ -41,10 +41,11 @@ def test_tensor_core_commit_withheld(lib):
     assert max(rel_linf_levels(nest, gx, gy, ox, oy)) <= tol("bf16x", 64)
 
 
-@pytest.mark.parametrize("n,row_inv0", [(512, 3), (1024, 4)])
+@pytest.mark.parametrize("n,row_inv0", [(512, 3), (1024, 4), (1024, 5), (2048, 5)])
 def test_tma_gather_withheld(lib, n, row_inv0):
-    """k_row_inv1t (one row pair per CTA) and k_row_inv1x (walking CTAs that
-    gather their next row pair behind the transforms)."""
+    """k_row_inv1t (one row pair per CTA), k_row_inv1x (walking CTAs that
+    gather their next row pair behind the transforms) and k_row_inv2x (two row
+    pairs per gather; three groups per CTA at 1024, two at 2048)."""
     nest = W.Nest(n=n)
     s = np.zeros((n, n))
     s[2:-2, 2:-2] = np.random.Generator(np.random.PCG64(4)).uniform(0.1, 1.0, (n - 4, n - 4))
