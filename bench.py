@@ -105,9 +105,10 @@ def csrc_digest() -> str:
     return h.hexdigest()
 
 
-def recorded_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
-    when the CUDA sources changed since those counters were taken."""
+def recorded_ncu(kernel: str, table: str = "dram_bytes_per_launch"):
+    """A per-launch ncu figure of `kernel` from the committed summary (DRAM
+    bytes, or the FP32-pipe record), or None when the CUDA sources changed
+    since those counters were taken."""
     f = ROOT / "profiles" / "traffic.json"
     if not f.exists():
         return None
@@ -117,7 +118,11 @@ def recorded_traffic(kernel: str):
         return None
     if d.get("csrc_sha256") != csrc_digest():
         return None
-    return d.get("dram_bytes_per_launch", {}).get(kernel)
+    return d.get(table, {}).get(kernel)
+
+
+def recorded_traffic(kernel: str):
+    return recorded_ncu(kernel)
 
 
 def dist_setup():
@@ -510,6 +515,7 @@ def run_gpu(args, world, rank, local):
     achieved = algo[dom] / (avg_ms / 1e3) / 1e9
     total_ms = sum(v["ms"] for v in kern.values())
     traffic = recorded_traffic(dom)
+    pipe = recorded_ncu(dom, "fp32_pipe_per_launch")
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample_rate(n, seconds=args.ref_seconds)
@@ -542,7 +548,12 @@ def run_gpu(args, world, rank, local):
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
                      "algorithmic_bytes_per_launch": algo[dom],
                      "kernel_ms": {k: v["ms"] / max(1, v["launches"]) for k, v in kern.items() if v["launches"]},
-                     "kernel_share": {k: v["ms"] / total_ms for k, v in kern.items() if v["launches"]}},
+                     "kernel_share": {k: v["ms"] / total_ms for k, v in kern.items() if v["launches"]},
+                     # the FP32 roof beside the HBM one: the same kernel's FMA-pipe and issue activity
+                     # from the committed ncu capture (null once its sources change)
+                     "fp32_pipe": None if pipe is None else {
+                         "fma_pipe_active": pipe["fma_pipe_active_pct"] / 100.0,
+                         "issue_active": pipe["issue_active_pct"] / 100.0, "source": "ncu, profiles/traffic.json"}},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": args.steps * st["launches_per_solve"],

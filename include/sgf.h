@@ -432,10 +432,12 @@ sgf_status sgf_solve_noalloc(sgf_plan *plan, const void *const *sigma, void *con
  *     radix-16 stages closed by one radix-2/4/8 stage where 16 does not divide
  *     n (1024 = 16.16.4, 2048 = 16.16.8, 4096 = 16.16.16); 1 = the small stage
  *     first (4.16.16, 8.16.16) or, at n = 4096, four radix-8 stages (8.8.8.8).
- *   row_fwd (SGF_PLAN_ZERO_RIM plans): 0 = the forward row pass with one row
- *     pair per CTA; 1 = two row pairs per CTA, so that neighbouring threads
- *     store the two pairs' values of one bin together, a whole 32-byte sector
- *     (SGF_FP32, n >= 1024).
+ *   row_fwd: 0 = the forward row pass with one row pair per CTA (and, on
+ *     plans without SGF_PLAN_ZERO_RIM, one field per CTA); 1 = two row pairs
+ *     per CTA, so that neighbouring threads store the two pairs' values of one
+ *     bin together, a whole 32-byte sector, and on plans without
+ *     SGF_PLAN_ZERO_RIM all three fields (sigma and its two slopes) in that
+ *     CTA, one after the other, the source rows read once (SGF_FP32, n >= 1024).
  * A new plan starts from {0, 0, 0}, or from the schedule the autotuner recorded for
  * its key (device, n, precision, zero-rim, levels > 1); sgf_plan_share copies it. */
 typedef struct {
@@ -444,7 +446,7 @@ typedef struct {
     int32_t col_case3;
     int32_t col_radix;   /* radix plan of the col_pass = 3 kernel (0 otherwise) */
     int32_t inv_radix;   /* radix plan of the row_inv0 = 4, 5 kernels (0 otherwise) */
-    int32_t row_fwd;     /* zero-rim forward rows: 0 = one row pair per CTA, 1 = two */
+    int32_t row_fwd;     /* forward rows: 0 = one row pair per CTA, 1 = two */
 } sgf_schedule;
 
 /* The plan's current schedule.  Errors: SGF_EINVAL for a NULL argument. */
@@ -455,7 +457,7 @@ sgf_status sgf_plan_schedule_get(const sgf_plan *plan, sgf_schedule *schedule);
  * tiles there), col_pass = 3 outside zero-rim SGF_FP32 force plans of
  * n >= 1024, row_inv0 = 2 on a potential plan, row_inv0 = 3, 4 or 5 where it
  * does not apply, a radix plan 1 without its register-twiddle kernel,
- * row_fwd = 1 outside zero-rim SGF_FP32 plans of n >= 1024 (the autotuner
+ * row_fwd = 1 outside SGF_FP32 plans of n >= 1024 (the autotuner
  * skips all of these). */
 sgf_status sgf_plan_schedule_set(sgf_plan *plan, const sgf_schedule *schedule);
 

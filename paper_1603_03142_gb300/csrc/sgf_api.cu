@@ -1306,8 +1306,9 @@ inline bool schedule_ok(const sgf_plan *p, const sgf_schedule &s)
     // k_row_inv1x, k_row_inv2x: the tensor-map gather (row_inv0 = 3's conditions) with n >= 1024
     if ((s.row_inv0 == 4 || s.row_inv0 == 5) && !(p->tma_inv && p->N >= 1024))
         return false;
-    // two row pairs per CTA in the zero-rim forward rows: FP32 without tensor-core tiles, N >= 1024
-    if (s.row_fwd != 0 && (s.row_fwd != 1 || !(p->merged && p->prec == SGF_FP32 && p->N >= 1024)))
+    // two row pairs per CTA in the forward rows (k_row_fwd_m2 / k_row_fwd2): FP32 without tensor-core
+    // tiles, N >= 1024
+    if (s.row_fwd != 0 && (s.row_fwd != 1 || !(p->prec == SGF_FP32 && !p->tc && p->N >= 1024)))
         return false;
     // radix plans: the register-twiddle kernels only (col_pass 3, row_inv0 4 and 5)
     if ((s.col_radix != 0 && (s.col_radix != 1 || s.col_pass != 3)) ||
@@ -1409,7 +1410,8 @@ sgf_status solve_core(sgf_plan *p, const void *const *sigma, void *const *fx, vo
         return ms;
     e = p->merged ? launch_pass_n<T>(p->sched.row_fwd == 1 ? PASS_ROW_FWD_M2 : PASS_ROW_FWD_M, p->logN, a, 0, st,
                                      nullptr, p->tc)
-                  : launch_pass_n<T>(PASS_ROW_FWD, p->logN, a, (int)p->items.size(), st, nullptr, p->tc);
+                  : launch_pass_n<T>(p->sched.row_fwd == 1 ? PASS_ROW_FWD2 : PASS_ROW_FWD, p->logN, a,
+                                     (int)p->items.size(), st, nullptr, p->tc);
     if (e != cudaSuccess)
         return cuda_fail(e, "row_fwd launch");
     if ((ms = mark(p, st)) != SGF_OK)
@@ -1590,7 +1592,8 @@ sgf_status solve_noalloc_impl(sgf_plan *p, const void *const *sigma, void *const
     a.partial = reinterpret_cast<typename SolveArgs<T>::C *>(partial);
     cudaError_t e = p->merged ? launch_pass_n<T>(p->sched.row_fwd == 1 ? PASS_ROW_FWD_M2 : PASS_ROW_FWD_M, p->logN, a,
                                                  0, st, nullptr, p->tc)
-                              : launch_pass_n<T>(PASS_ROW_FWD, p->logN, a, (int)p->items.size(), st, nullptr, p->tc);
+                              : launch_pass_n<T>(p->sched.row_fwd == 1 ? PASS_ROW_FWD2 : PASS_ROW_FWD, p->logN, a,
+                                                 (int)p->items.size(), st, nullptr, p->tc);
     if (e != cudaSuccess)
         return cuda_fail(e, "row_fwd launch");
     e = launch_col<T>(p, a, st);
@@ -1999,13 +2002,15 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[SGF_A
     for (int k = 0; k < SGF_AUTOTUNE_TIMES; ++k)
         ms[k] = -1.0;
     sgf_schedule best = p->sched;
-    if (p->merged) {  // forward rows: one or two row pairs per CTA (slots 13, 14)
+    {  // forward rows: one or two row pairs per CTA (slots 13, 14)
+        const int items = (int)p->items.size();
+        const int k0 = p->merged ? PASS_ROW_FWD_M : PASS_ROW_FWD, k1 = p->merged ? PASS_ROW_FWD_M2 : PASS_ROW_FWD2;
+        const int cnt = p->merged ? 0 : items;
         for (int c = 0; c < 2 && s == SGF_OK; ++c) {
             sgf_schedule cand = best;
             cand.row_fwd = c;
             if (schedule_ok(p, cand))
-                s = timeit([&] { return launch_pass_n<T>(c ? PASS_ROW_FWD_M2 : PASS_ROW_FWD_M, p->logN, a, 0, st,
-                                                         nullptr, p->tc); },
+                s = timeit([&] { return launch_pass_n<T>(c ? k1 : k0, p->logN, a, cnt, st, nullptr, p->tc); },
                            ms[13 + c]);
         }
         if (s == SGF_OK && ms[14] >= 0.0 && ms[14] < ms[13])

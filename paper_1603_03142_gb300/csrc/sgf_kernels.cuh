@@ -32,6 +32,7 @@
 //                schedule of the same arithmetic, chosen by the autotuner).
 #pragma once
 #include <atomic>
+#include <type_traits>
 #include <cooperative_groups.h>
 
 #include "sgf_fft16.cuh"
@@ -263,6 +264,118 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, sizeof(T) == 4 && !
     }
     if constexpr (TC)
         tc_end(tcx, TCT);
+}
+
+// ----------------------------------------------------------------- row_fwd2
+// k_row_fwd (FP32, no tensor-core tiles, no batch view) with two work items
+// (row pairs) per CTA and the three fields (sigma, x slope, y slope) of both in
+// the one CTA, one field after the other: the source rows are read once per
+// CTA from global memory (the slopes' neighbours from the L1 cache) instead of
+// once per field CTA, and in the store phase two neighbouring lanes write the
+// two items' values of one bin, 32 contiguous bytes where the items are
+// neighbouring row pairs of one slab (every item of a slab with an even number
+// of row pairs).  Group g = t / (N/8) of 2 N/16 threads takes item
+// 2 blockIdx.x + g (parity halves on named barriers 1 + 2 g + half); a group
+// without an item (an odd item count) only keeps the block barriers.  The
+// field values are those of k_row_fwd, expression for expression.
+// Shared memory: twiddle area | sbuf [2 items][2 halves][SP_ROW].
+template <int LOGN>
+__global__ void __launch_bounds__((1 << LOGN) / 4) k_row_fwd2(const __grid_constant__ SolveArgs<float> a, int items)
+{
+    using C = float2;
+    using C2 = float4;
+    using K = KShape<LOGN>;
+    constexpr int N = K::N, Q = K::Q, SP = K::SP_ROW, T2 = 2 * Q;
+    static_assert(Q >= 32, "whole warps per parity half");
+    extern __shared__ __align__(16) unsigned char smem_f3[];
+    C *tw = reinterpret_cast<C *>(smem_f3);
+    C *sbuf = reinterpret_cast<C *>(smem_f3 + tw_bytes<C>(a.tw_entries));
+    cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
+    cp_commit();
+    const int t = threadIdx.x;
+    const int g = t / T2, tg = t - g * T2, b = tg / Q, j = tg - b * Q;
+    const int item_g = 2 * (int)blockIdx.x + g;
+    const bool active = item_g < items;
+    const FwdItem item = a.fwd_items[active ? item_g : 0];
+    const FwdSlab sl = a.slabs[item.slab];
+    const int rows = sl.rows, r0 = 2 * item.row_pair;
+    const int ja = sl.m * r0 + sl.py, jb = sl.m * (r0 + 1) + sl.py;
+    const float *src = a.src[sl.patch];
+    const int nl = a.n_log;
+    // the other group's slab (its store addresses)
+    const int item_o = 2 * (int)blockIdx.x + (g ^ 1);
+    const TwLayout tl = tw_layout(F16<LOGN>::twlen, N);
+    cp_wait<0>();
+    __syncthreads();
+    auto field = [&](auto fcv) {  // one field after the other, each compiled on its own
+        constexpr int f = decltype(fcv)::value;
+        C v[1][16];
+        if (active) {  // the field's 16 inputs of this thread's slot
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int c = j + u * Q;
+                float fv[2] = {0.0f, 0.0f};
+                if (c < rows) {
+                    const int i = sl.m * c + sl.px;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int jj = h ? jb : ja;
+                        if (i >= nl || jj >= nl || covered(a, sl.patch, jj, i))
+                            continue;
+                        const float *r = src + (size_t)jj * N;
+                        if constexpr (f == 0) {
+                            fv[h] = __ldg(r + i);
+                        } else if constexpr (f == 1) {
+                            const int il = i == 0 ? 0 : i - 1, ir = i == nl - 1 ? nl - 1 : i + 1;
+                            const float d = __ldg(r + ir) - __ldg(r + il);
+                            fv[h] = (ir - il == 2) ? 0.5f * d : d;
+                        } else {
+                            const int jd = max(jj - 1, 0), ju = min(jj + 1, nl - 1);
+                            const float d = __ldg(src + (size_t)min(ju, N - 1) * N + i) -
+                                            __ldg(src + (size_t)min(jd, N - 1) * N + i);
+                            fv[h] = (jj == 0 || jj == nl - 1) ? d : 0.5f * d;
+                        }
+                    }
+                }
+                C z = hmk<C>(fv[0], fv[1]);
+                if (b)
+                    z = hmul(z, twist(tw, tl, j, u));
+                v[0][u] = z;
+            }
+        }
+        fft_ct<C, false, LOGN, 1, false, Q>(v, sbuf + (2 * g + b) * SP, SP, j, active, tw, nullptr, 2 * g + b);
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+                sbuf[(2 * g + b) * SP + pad16(j + u * Q)] = v[0][u];
+        }
+        __syncthreads();
+        // X_a = (Z + conj Z~)/2, X_b = (Z - conj Z~)/(2i); Z~ = bin -kx, same parity half
+        for (int e = t; e < 2 * (N + 1); e += 4 * Q) {  // e = 2 kx + item: neighbouring lanes, one sector
+            const int pr = e & 1, kx = e >> 1;
+            const int it = 2 * (int)blockIdx.x + pr;
+            if (it >= items)
+                continue;
+            const FwdItem ip = pr == g ? item : a.fwd_items[item_o];
+            const FwdSlab sp = pr == g ? sl : a.slabs[ip.slab];
+            const int bb = kx & 1, k = kx >> 1;
+            const int km = (N - bb - k) & (N - 1);
+            const C Z = sbuf[(2 * pr + bb) * SP + pad16(k)];
+            const C Zm = sbuf[(2 * pr + bb) * SP + pad16(km)];
+            C2 o;
+            o.x = 0.5f * (Z.x + Zm.x);
+            o.y = 0.5f * (Z.y - Zm.y);
+            o.z = 0.5f * (Z.y + Zm.y);
+            o.w = -0.5f * (Z.x - Zm.x);
+            C2 *out = reinterpret_cast<C2 *>(a.fwd + sp.off);  // pairs of rows (r0, r0+1)
+            out[(((size_t)f * (N + 1) + kx) * sp.rows + 2 * ip.row_pair) >> 1] = o;
+        }
+        __syncthreads();  // sbuf is free for the next field's exchanges
+    };
+    field(std::integral_constant<int, 0>{});
+    field(std::integral_constant<int, 1>{});
+    field(std::integral_constant<int, 2>{});
 }
 
 // --------------------------------------------------------------------- col
@@ -2435,7 +2548,7 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
 {
     using K = KShape<LOGN>;
     using S = KSmem<T, LOGN, TC>;
-    static std::atomic<unsigned long long> d[35];
+    static std::atomic<unsigned long long> d[36];
     static std::atomic<int> res_mx[64], res_mx1[64];  // resident CTAs of the register-twiddle column pass (plans 0, 1)
     static std::atomic<int> res_rx[64], res_rx1[64];  // and of the register-twiddle inverse row pass
     static std::atomic<int> res_r2[64], res_r21[64];  // and of its two-pair form
@@ -2533,6 +2646,8 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
                 (e = resident_ctas(k_row_inv2x<LOGN, 0>, KR2x<LOGN>::THREADS, KR2x<LOGN>::SMEM, res_r2, &grid)) !=
                     cudaSuccess ||
                 (e = ensure_smem(k_row_inv2x<LOGN, 1>, KR2x<LOGN>::SMEM, d[34])) != cudaSuccess ||
+                (e = ensure_smem(k_row_fwd2<LOGN>, S::tw() + 4 * (size_t)K::SP_ROW * sizeof(float2), d[35])) !=
+                    cudaSuccess ||
                 (e = resident_ctas(k_row_inv2x<LOGN, 1>, KR2x<LOGN>::THREADS, KR2x<LOGN>::SMEM, res_r21, &grid)) !=
                     cudaSuccess ||
                 (e = ensure_smem(k_row_fwd_m2<LOGN>, S::tw() + 4 * (size_t)K::N * sizeof(float) +
@@ -2716,6 +2831,20 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
                 return e;
             const int groups = (a.ncomp * (K::N / 4) + R2::G - 1) / R2::G;  // CTAs that give every group an item
             kern<<<dim3(grid < groups ? grid : groups, count), R2::THREADS, R2::SMEM, st>>>(a);
+        } else {
+            return cudaErrorInvalidValue;
+        }
+        break;
+    }
+    case PASS_ROW_FWD2: {
+        if constexpr (!TC && sizeof(T) == 4 && LOGN >= 10) {
+            if (batch)
+                return cudaErrorInvalidValue;
+            const size_t smem = S::tw() + 4 * (size_t)K::SP_ROW * sizeof(float2);
+            if ((e = ensure_smem(k_row_fwd2<LOGN>, smem, d[35])) != cudaSuccess)
+                return e;
+            if (count > 0)
+                k_row_fwd2<LOGN><<<(count + 1) / 2, K::N / 4, smem, st>>>(a, count);
         } else {
             return cudaErrorInvalidValue;
         }

@@ -109,7 +109,7 @@ def schedules(n, prec, zero_rim):
                 out.append((c, i, 1, 0, 0))
             if i in (4, 5):
                 out.append((c, i, 0, 1, 0))
-            if zero_rim and prec == "fp32" and n >= 1024 and c in (2, 3):
+            if prec == "fp32" and n >= 1024 and (c in (2, 3) or not zero_rim):
                 out.append((c, i, 0, 0, 1))  # two row pairs per CTA in the forward rows
     return out
 
