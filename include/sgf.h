@@ -437,7 +437,11 @@ sgf_status sgf_solve_noalloc(sgf_plan *plan, const void *const *sigma, void *con
  *     per CTA, so that neighbouring threads store the two pairs' values of one
  *     bin together, a whole 32-byte sector, and on plans without
  *     SGF_PLAN_ZERO_RIM all three fields (sigma and its two slopes) in that
- *     CTA, one after the other, the source rows read once (SGF_FP32, n >= 1024).
+ *     CTA, one after the other, the source rows read once (SGF_FP32, n >= 1024);
+ *     2 (SGF_PLAN_ZERO_RIM plans, SGF_FP32, n >= 1024) = as 1 with one thread
+ *     per slot carrying both parity halves and the slot's stage twiddles in
+ *     registers, the CTAs walking items of two row pairs, each staging its
+ *     next item's rows behind the current transforms.
  * A new plan starts from {0, 0, 0}, or from the schedule the autotuner recorded for
  * its key (device, n, precision, zero-rim, levels > 1); sgf_plan_share copies it. */
 typedef struct {
@@ -446,7 +450,7 @@ typedef struct {
     int32_t col_case3;
     int32_t col_radix;   /* radix plan of the col_pass = 3 kernel (0 otherwise) */
     int32_t inv_radix;   /* radix plan of the row_inv0 = 4, 5 kernels (0 otherwise) */
-    int32_t row_fwd;     /* forward rows: 0 = one row pair per CTA, 1 = two */
+    int32_t row_fwd;     /* forward rows: 0 = one row pair per CTA, 1 = two, 2 = two, walking */
 } sgf_schedule;
 
 /* The plan's current schedule.  Errors: SGF_EINVAL for a NULL argument. */
@@ -457,7 +461,8 @@ sgf_status sgf_plan_schedule_get(const sgf_plan *plan, sgf_schedule *schedule);
  * tiles there), col_pass = 3 outside zero-rim SGF_FP32 force plans of
  * n >= 1024, row_inv0 = 2 on a potential plan, row_inv0 = 3, 4 or 5 where it
  * does not apply, a radix plan 1 without its register-twiddle kernel,
- * row_fwd = 1 outside SGF_FP32 plans of n >= 1024 (the autotuner
+ * row_fwd = 1 outside SGF_FP32 plans of n >= 1024, row_fwd = 2 outside
+ * SGF_PLAN_ZERO_RIM SGF_FP32 plans of n >= 1024 (the autotuner
  * skips all of these). */
 sgf_status sgf_plan_schedule_set(sgf_plan *plan, const sgf_schedule *schedule);
 
@@ -473,9 +478,10 @@ sgf_status sgf_plan_schedule_set(sgf_plan *plan, const sgf_schedule *schedule);
  * milliseconds per launch of col_pass 0, 1, 2, row_inv0 0, 1, 2, col_case3 0,
  * 1, row_inv0 3, col_pass 3, row_inv0 4, col_pass 3 with radix plan 1,
  * row_inv0 4 with radix plan 1, row_fwd 0, 1, row_inv0 5, row_inv0 5 with
- * radix plan 1 (-1 where a candidate does not apply).  Blocks until done.
+ * radix plan 1, row_fwd 2 (-1 where a candidate does not apply).  Blocks
+ * until done.
  * Errors: SGF_EINVAL, SGF_ENOMEM, SGF_ECUDA. */
-#define SGF_AUTOTUNE_TIMES 17
+#define SGF_AUTOTUNE_TIMES 18
 sgf_status sgf_plan_autotune(sgf_plan *plan, int32_t reps, void *stream, sgf_schedule *chosen, double *ms);
 
 /* Device memory a plan for this nest would hold, computed on the host without

@@ -1230,6 +1230,12 @@ cudaError_t launch_row_inv(int logN, int L, int R, SolveArgs<T> a, cudaStream_t 
     return launch_pass_n<T>(PASS_ROW_INV, logN, a, L - R, st, nullptr, tc);
 }
 
+// Zero-rim forward row pass of the plan's schedule.
+inline int zero_rim_fwd_pass(const sgf_plan *p)
+{
+    return p->sched.row_fwd == 2 ? PASS_ROW_FWD_X : p->sched.row_fwd == 1 ? PASS_ROW_FWD_M2 : PASS_ROW_FWD_M;
+}
+
 // Zero-rim column pass of the plan's schedule.
 inline int col_m_pass(const sgf_plan *p)
 {
@@ -1306,9 +1312,10 @@ inline bool schedule_ok(const sgf_plan *p, const sgf_schedule &s)
     // k_row_inv1x, k_row_inv2x: the tensor-map gather (row_inv0 = 3's conditions) with n >= 1024
     if ((s.row_inv0 == 4 || s.row_inv0 == 5) && !(p->tma_inv && p->N >= 1024))
         return false;
-    // two row pairs per CTA in the forward rows (k_row_fwd_m2 / k_row_fwd2): FP32 without tensor-core
-    // tiles, N >= 1024
-    if (s.row_fwd != 0 && (s.row_fwd != 1 || !(p->prec == SGF_FP32 && !p->tc && p->N >= 1024)))
+    // two row pairs per CTA in the forward rows (k_row_fwd_m2 / k_row_fwd2; 2: k_row_fwd_x, zero-rim
+    // plans): FP32 without tensor-core tiles, N >= 1024
+    if (s.row_fwd != 0 && ((s.row_fwd != 1 && s.row_fwd != 2) || !(p->prec == SGF_FP32 && !p->tc && p->N >= 1024) ||
+                           (s.row_fwd == 2 && !p->merged)))
         return false;
     // radix plans: the register-twiddle kernels only (col_pass 3, row_inv0 4 and 5)
     if ((s.col_radix != 0 && (s.col_radix != 1 || s.col_pass != 3)) ||
@@ -1408,7 +1415,7 @@ sgf_status solve_core(sgf_plan *p, const void *const *sigma, void *const *fx, vo
     cudaError_t e;
     if ((ms = mark(p, st)) != SGF_OK)
         return ms;
-    e = p->merged ? launch_pass_n<T>(p->sched.row_fwd == 1 ? PASS_ROW_FWD_M2 : PASS_ROW_FWD_M, p->logN, a, 0, st,
+    e = p->merged ? launch_pass_n<T>(zero_rim_fwd_pass(p), p->logN, a, 0, st,
                                      nullptr, p->tc)
                   : launch_pass_n<T>(p->sched.row_fwd == 1 ? PASS_ROW_FWD2 : PASS_ROW_FWD, p->logN, a,
                                      (int)p->items.size(), st, nullptr, p->tc);
@@ -1590,7 +1597,7 @@ sgf_status solve_noalloc_impl(sgf_plan *p, const void *const *sigma, void *const
     a.groups = p->d_groups;
     a.sums = p->d_sums;
     a.partial = reinterpret_cast<typename SolveArgs<T>::C *>(partial);
-    cudaError_t e = p->merged ? launch_pass_n<T>(p->sched.row_fwd == 1 ? PASS_ROW_FWD_M2 : PASS_ROW_FWD_M, p->logN, a,
+    cudaError_t e = p->merged ? launch_pass_n<T>(zero_rim_fwd_pass(p), p->logN, a,
                                                  0, st, nullptr, p->tc)
                               : launch_pass_n<T>(p->sched.row_fwd == 1 ? PASS_ROW_FWD2 : PASS_ROW_FWD, p->logN, a,
                                                  (int)p->items.size(), st, nullptr, p->tc);
@@ -1916,7 +1923,7 @@ void tune_load_locked()
     int a = 0, b = 0, c = 0, d = 0, r = 0, w = 0;
     while (fscanf(f, "%159s %d %d %d %d %d %d", key, &a, &b, &c, &d, &r, &w) == 7)
         if (a >= 0 && a <= 3 && b >= 0 && b <= 5 && (c == 0 || c == 1) && (d == 0 || d == 1) && (r == 0 || r == 1) &&
-            (w == 0 || w == 1))
+            w >= 0 && w <= 2)
             g_tune[key] = sgf_schedule{a, b, c, d, r, w};
     fclose(f);
 }
@@ -2002,21 +2009,24 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[SGF_A
     for (int k = 0; k < SGF_AUTOTUNE_TIMES; ++k)
         ms[k] = -1.0;
     sgf_schedule best = p->sched;
-    {  // forward rows: one or two row pairs per CTA (slots 13, 14)
+    {  // forward rows: row_fwd 0, 1 (slots 13, 14) and, zero-rim plans, 2 (slot 17)
         const int items = (int)p->items.size();
-        const int k0 = p->merged ? PASS_ROW_FWD_M : PASS_ROW_FWD, k1 = p->merged ? PASS_ROW_FWD_M2 : PASS_ROW_FWD2;
+        const int kind[3] = {p->merged ? PASS_ROW_FWD_M : PASS_ROW_FWD, p->merged ? PASS_ROW_FWD_M2 : PASS_ROW_FWD2,
+                             PASS_ROW_FWD_X};
+        const int slot[3] = {13, 14, 17};
         const int cnt = p->merged ? 0 : items;
-        for (int c = 0; c < 2 && s == SGF_OK; ++c) {
+        for (int c = 0; c < 3 && s == SGF_OK; ++c) {
             sgf_schedule cand = best;
             cand.row_fwd = c;
             if (schedule_ok(p, cand))
-                s = timeit([&] { return launch_pass_n<T>(c ? k1 : k0, p->logN, a, cnt, st, nullptr, p->tc); },
-                           ms[13 + c]);
+                s = timeit([&] { return launch_pass_n<T>(kind[c], p->logN, a, cnt, st, nullptr, p->tc); },
+                           ms[slot[c]]);
         }
-        if (s == SGF_OK && ms[14] >= 0.0 && ms[14] < ms[13])
-            best.row_fwd = 1;
-        else
-            best.row_fwd = 0;
+        int bc = 0;
+        for (int c = 1; c < 3; ++c)
+            if (s == SGF_OK && ms[slot[c]] >= 0.0 && ms[slot[c]] < ms[slot[bc]])
+                bc = c;
+        best.row_fwd = bc;
     }
     if (p->merged) {
         // candidates 0..3, and 4 = col_pass 3 with radix plan 1
@@ -2659,7 +2669,7 @@ sgf_status sgf_plan_schedule_set(sgf_plan *p, const sgf_schedule *in)
         return fail(SGF_EINVAL, "NULL argument");
     if (in->col_pass < 0 || in->col_pass > 3 || in->row_inv0 < 0 || in->row_inv0 > 5 ||
         (in->col_case3 != 0 && in->col_case3 != 1) || in->col_radix < 0 || in->col_radix > 1 || in->inv_radix < 0 ||
-        in->inv_radix > 1 || in->row_fwd < 0 || in->row_fwd > 1)
+        in->inv_radix > 1 || in->row_fwd < 0 || in->row_fwd > 2)
         return fail(SGF_EINVAL, "schedule out of range (col_pass %d, row_inv0 %d, col_case3 %d)", in->col_pass,
                     in->row_inv0, in->col_case3);
     if (!schedule_ok(p, *in))

@@ -1919,6 +1919,135 @@ __global__ void __launch_bounds__((1 << LOGN) / 4) k_row_fwd_m2(SolveArgs<float>
         atomicOr(a.status, STATUS_RIM_NONZERO);
 }
 
+// k_row_fwd_m2 with the structure of k_row_inv2x: one thread per slot j
+// carries both parity halves of a row pair's transform (x and x W_P^n as two
+// sequences) with the slot's stage twiddles in registers, and the CTA walks
+// its items of two row pairs (rows 4q .. 4q + 3): the item's four sigma rows
+// are staged by cp.async, the pairs are transformed one after the other, the
+// first pair's bins wait in their own buffer while the second is transformed,
+// and the next item's rows are copied in as soon as the second pair is in
+// registers.  Neighbouring lanes then store the two pairs' values of one bin,
+// one 32-byte sector.  G = 256 / (N/16) groups of N/16 threads per CTA, each
+// walking its own items on its own named barrier.  Also verifies the zero rim
+// as k_row_fwd_m does.  FP32, N >= 1024, one patch, no batch view.
+// Shared memory per group: sigma rows [4][N] | exchange buffers [2][SP_ROW] |
+// first pair's bins [2][SP_ROW].
+template <int LOGN>
+struct KFx {
+    static constexpr int N = 1 << LOGN, Q = N >> 4;
+    static constexpr int G = Q >= 256 ? 1 : 256 / Q;
+    static constexpr int THREADS = G * Q;
+    static constexpr size_t XB = 2 * (size_t)KShape<LOGN>::SP_ROW * 8;
+    static constexpr size_t GROUP_BYTES = 4 * (size_t)N * 4 + 2 * XB;
+    static constexpr size_t SMEM = G * GROUP_BYTES;
+};
+
+template <int LOGN, int PLAN>
+__global__ void __launch_bounds__(KFx<LOGN>::THREADS, 1) k_row_fwd_x(const __grid_constant__ SolveArgs<float> a)
+{
+    using C = float2;
+    using C2 = float4;
+    using R = KFx<LOGN>;
+    using P = FR<LOGN, PLAN>;
+    constexpr int N = R::N, Q = R::Q, SP = KShape<LOGN>::SP_ROW;
+    static_assert(Q >= 64, "named group barriers need whole warps");
+    extern __shared__ __align__(16) unsigned char smem_fx[];
+    const int t = threadIdx.x;
+    const int g = t / Q, j = t - g * Q;
+    unsigned char *gb = smem_fx + (size_t)g * R::GROUP_BYTES;
+    float *rows = reinterpret_cast<float *>(gb);
+    C *xb = reinterpret_cast<C *>(gb + 4 * (size_t)N * 4);
+    C *za = xb + 2 * SP;
+    __shared__ int rim_bad;
+    if (t == 0)
+        rim_bad = 0;
+    __syncthreads();
+    const unsigned bar = 1 + g;
+    const int nl = a.n_log;
+    const int items = N / 4;
+    C trw[P::NST - 1][15];
+    load_twiddles_rt<C, LOGN, PLAN>(trw, a.twn, j);
+    const TwLayout tl = tw_layout(F16<LOGN>::twlen, N);
+    const C wj = a.tw[tl.base + j];  // W_P^j
+    auto twist_u = [&](int u) { return hmul(wj, hmk<C>((float)kW32c[u], (float)-kW32s[u])); };
+    const float *src = a.src[0];
+    auto stage = [&](int it) {  // this group's threads: rows 4 it .. 4 it + 3 (contiguous)
+        const char *s = reinterpret_cast<const char *>(src + (size_t)(4 * it) * N);
+        for (int o = j * 16; o < 4 * N * 4; o += Q * 16)
+            cp16(reinterpret_cast<char *>(rows) + o, s + o);
+        cp_commit();
+    };
+    const int step = (int)gridDim.x * R::G;
+    int it = (int)blockIdx.x * R::G + g;
+    if (it < items)
+        stage(it);
+    bool bad = false;
+    for (; it < items; it += step) {  // uniform over the group
+        cp_wait<0>();
+        group_sync(bar, Q);  // the item's rows are staged; the previous item's bins are stored
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {  // the zero rim: rows 0, 1 and nl-2, nl-1 whole, columns 0, 1, nl-2, nl-1
+            const int r0 = 4 * it + 2 * h;
+            const float *rp = rows + 2 * h * N;
+            if (r0 == 0 || r0 == nl - 2) {
+                for (int i = j; i < 2 * N; i += Q)
+                    bad |= rp[i] != 0.0f;
+            } else if (j < 8 && r0 < nl) {
+                const int col = (j & 3) < 2 ? (j & 3) : nl - 4 + (j & 3);
+                bad |= rp[(j >> 2) * N + col] != 0.0f;
+            }
+        }
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            C v[2][16];
+            const float *rp = rows + 2 * h * N;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int c = j + u * Q;
+                const C z = hmk<C>(rp[c], rp[N + c]);
+                v[0][u] = z;
+                v[1][u] = hmul(z, twist_u(u));
+            }
+            if (h == 1) {
+                group_sync(bar, Q);  // every thread has read the rows
+                if (it + step < items)
+                    stage(it + step);
+            }
+            fft_stages_rt<C, false, LOGN, PLAN, 2, 0>(v, xb, SP, j, trw, bar, Q);
+            group_sync(bar, Q);  // the last stage's reads of the exchange buffers are done
+            C *zb = h ? xb : za;
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int u = 0; u < 16; ++u)
+                    zb[b * SP + pad16(j + u * Q)] = v[b][u];
+        }
+        group_sync(bar, Q);  // both pairs' bins are in shared memory
+        // X_a = (Z + conj Z~)/2, X_b = (Z - conj Z~)/(2i); Z~ = bin -kx, same parity half
+        C2 *out = reinterpret_cast<C2 *>(a.fwd);
+        for (int e = j; e < 2 * (N + 1); e += Q) {  // e = 2 kx + pair: neighbouring lanes, one sector
+            const int pr = e & 1, kx = e >> 1;
+            const C *zb = pr ? xb : za;
+            const int bb = kx & 1, k = kx >> 1;
+            const int km = (N - bb - k) & (N - 1);
+            const C Z = zb[bb * SP + pad16(k)];
+            const C Zm = zb[bb * SP + pad16(km)];
+            C2 o;
+            o.x = 0.5f * (Z.x + Zm.x);
+            o.y = 0.5f * (Z.y - Zm.y);
+            o.z = 0.5f * (Z.y + Zm.y);
+            o.w = -0.5f * (Z.x - Zm.x);
+            out[((size_t)kx * N + 4 * it + 2 * pr) >> 1] = o;
+        }
+    }
+    cp_wait<0>();  // nothing in flight at exit
+    if (bad)
+        rim_bad = 1;
+    __syncthreads();
+    if (t == 0 && rim_bad)
+        atomicOr(a.status, STATUS_RIM_NONZERO);
+}
+
 // Column pass of a SGF_PLAN_ZERO_RIM plan: one forward transform, the two
 // merged spectra (Fx^ = Gx^ sigma^, Fy^ = Gy^ sigma^, both imaginary), and the
 // two inverse transforms one after the other; parity halves folded through
@@ -2548,10 +2677,11 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
 {
     using K = KShape<LOGN>;
     using S = KSmem<T, LOGN, TC>;
-    static std::atomic<unsigned long long> d[36];
+    static std::atomic<unsigned long long> d[38];
     static std::atomic<int> res_mx[64], res_mx1[64];  // resident CTAs of the register-twiddle column pass (plans 0, 1)
     static std::atomic<int> res_rx[64], res_rx1[64];  // and of the register-twiddle inverse row pass
     static std::atomic<int> res_r2[64], res_r21[64];  // and of its two-pair form
+    static std::atomic<int> res_fx[64];               // and of the register-twiddle forward row pass
     static std::atomic<int> res_mw[64], res_mw1[64];  // resident CTAs of the walking column pass (NC = 2, 1)
     static std::atomic<int> res_fm[64];               // and of the walking zero-rim forward row pass
     static std::atomic<int> res_ri1[64], res_ri2[64]; // and of the walking inverse row passes (tensor cores)
@@ -2647,6 +2777,9 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
                     cudaSuccess ||
                 (e = ensure_smem(k_row_inv2x<LOGN, 1>, KR2x<LOGN>::SMEM, d[34])) != cudaSuccess ||
                 (e = ensure_smem(k_row_fwd2<LOGN>, S::tw() + 4 * (size_t)K::SP_ROW * sizeof(float2), d[35])) !=
+                    cudaSuccess ||
+                (e = ensure_smem(k_row_fwd_x<LOGN, 0>, KFx<LOGN>::SMEM, d[36])) != cudaSuccess ||
+                (e = resident_ctas(k_row_fwd_x<LOGN, 0>, KFx<LOGN>::THREADS, KFx<LOGN>::SMEM, res_fx, &grid)) !=
                     cudaSuccess ||
                 (e = resident_ctas(k_row_inv2x<LOGN, 1>, KR2x<LOGN>::THREADS, KR2x<LOGN>::SMEM, res_r21, &grid)) !=
                     cudaSuccess ||
@@ -2831,6 +2964,22 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
                 return e;
             const int groups = (a.ncomp * (K::N / 4) + R2::G - 1) / R2::G;  // CTAs that give every group an item
             kern<<<dim3(grid < groups ? grid : groups, count), R2::THREADS, R2::SMEM, st>>>(a);
+        } else {
+            return cudaErrorInvalidValue;
+        }
+        break;
+    }
+    case PASS_ROW_FWD_X: {
+        if constexpr (!TC && sizeof(T) == 4 && LOGN >= 10) {
+            if (batch)
+                return cudaErrorInvalidValue;
+            using FX = KFx<LOGN>;
+            int grid = 0;
+            if ((e = ensure_smem(k_row_fwd_x<LOGN, 0>, FX::SMEM, d[36])) != cudaSuccess ||
+                (e = resident_ctas(k_row_fwd_x<LOGN, 0>, FX::THREADS, FX::SMEM, res_fx, &grid)) != cudaSuccess)
+                return e;
+            const int groups = (K::N / 4 + FX::G - 1) / FX::G;  // CTAs that give every group an item
+            k_row_fwd_x<LOGN, 0><<<grid < groups ? grid : groups, FX::THREADS, FX::SMEM, st>>>(a);
         } else {
             return cudaErrorInvalidValue;
         }

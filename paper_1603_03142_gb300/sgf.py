@@ -39,7 +39,7 @@ BATCH_NO_GRAPH = 0x1
 PLAN_ZERO_RIM = 0x1
 PLAN_POTENTIAL = 0x2
 NOALLOC_SCRATCH_BYTES = 32 << 20
-AUTOTUNE_TIMES = 17
+AUTOTUNE_TIMES = 18
 KERNELS = ["restrict", "row_fwd", "col", "row_inv"]
 
 
@@ -325,7 +325,8 @@ class Plan:
                        "row_inv0_1": ms[4], "row_inv0_2": ms[5], "col_case3_0": ms[6], "col_case3_1": ms[7],
                        "row_inv0_3": ms[8], "col_pass3": ms[9], "row_inv0_4": ms[10],
                        "col_pass3_radix1": ms[11], "row_inv0_4_radix1": ms[12], "row_fwd0": ms[13],
-                       "row_fwd1": ms[14], "row_inv0_5": ms[15], "row_inv0_5_radix1": ms[16]}}
+                       "row_fwd1": ms[14], "row_inv0_5": ms[15], "row_inv0_5_radix1": ms[16],
+                       "row_fwd2": ms[17]}}
 
     def profile(self, enable: bool = True):
         _check(_lib.sgf_plan_profile(self._h, 1 if enable else 0), "sgf_plan_profile")

@@ -56,7 +56,7 @@ def test_schedules_agree_zero_rim(lib, prec, n):
     invs = [(0, 0), (1, 0), (2, 0)] + ([(3, 0)] if tma else []) + (
         [(4, 0), (4, 1), (5, 0), (5, 1)] if tma and n >= 1024 else [])
     cols = [(0, 0), (1, 0), (2, 0)] + ([(3, 0), (3, 1)] if mx else [])
-    fwds = (0, 1) if mx else (0,)  # row_fwd = 1: two row pairs per CTA in the forward rows
+    fwds = (0, 1, 2) if mx else (0,)  # row_fwd = 1, 2: two row pairs per CTA in the forward rows (2 walking)
     for col, cr in cols:
         for inv, ir in invs:
             for fw in fwds:
@@ -126,6 +126,9 @@ def test_general_forward_two_pairs(lib, levels):
         with pytest.raises(lib.SgfError) as ei:
             p.set_schedule(0, 0, 0, 0, 0, 1)
         assert ei.value.status == lib.SGF_EUNSUPPORTED
+    with pytest.raises(lib.SgfError) as ei:  # row_fwd = 2 (k_row_fwd_x): zero-rim plans only
+        plan.set_schedule(2, 0, 0, 0, 0, 2)
+    assert ei.value.status == lib.SGF_EUNSUPPORTED
 
 
 def test_bf16x_4096_refuses_nest_inverse_schedule(lib):
@@ -193,8 +196,9 @@ print(json.dumps({"r": r, "q": q.schedule()}))
            ms["row_inv0_4_radix1"], ms["row_inv0_5"], ms["row_inv0_5_radix1"]]
     best = inv.index(min(inv))
     assert (ch["row_inv0"], ch["inv_radix"]) == [(0, 0), (1, 0), (2, 0), (3, 0), (4, 0), (4, 1), (5, 0), (5, 1)][best]
-    assert ms["row_fwd0"] > 0 and ms["row_fwd1"] > 0
-    assert ch["row_fwd"] == (1 if ms["row_fwd1"] < ms["row_fwd0"] else 0)
+    assert ms["row_fwd0"] > 0 and ms["row_fwd1"] > 0 and ms["row_fwd2"] > 0
+    fw = [ms["row_fwd0"], ms["row_fwd1"], ms["row_fwd2"]]
+    assert ch["row_fwd"] == fw.index(min(fw))
     assert d["q"] == ch
     lines = table.read_text().split("\n")
     assert any("/n1024/p1/zr1/" in ln for ln in lines)

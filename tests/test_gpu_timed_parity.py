@@ -111,6 +111,8 @@ def schedules(n, prec, zero_rim):
                 out.append((c, i, 0, 1, 0))
             if prec == "fp32" and n >= 1024 and (c in (2, 3) or not zero_rim):
                 out.append((c, i, 0, 0, 1))  # two row pairs per CTA in the forward rows
+            if zero_rim and prec == "fp32" and n >= 1024 and c in (2, 3) and i in (3, 5):
+                out.append((c, i, 0, 0, 2))  # the walking register-twiddle forward rows
     return out
 
 
@@ -153,8 +155,8 @@ def test_4096_autotuned_plan_against_oracle(lib, prec, zero_rim):
     assert s.rel_err(gx[0], gy[0]) <= tol(prec, 4096)
 
 
-@pytest.mark.parametrize("col_pass,row_inv0", [(2, 3), (3, 3), (3, 4), (3, 5)])
-def test_4096_timed_schedule_explicitly(lib, col_pass, row_inv0):
+@pytest.mark.parametrize("col_pass,row_inv0,row_fwd", [(2, 3, 0), (3, 3, 1), (3, 4, 1), (3, 5, 1), (3, 5, 2)])
+def test_4096_timed_schedule_explicitly(lib, col_pass, row_inv0, row_fwd):
     """Zero-rim FP32 with the level-0 inverse rows gathered by the tensor memory
     accelerator (k_row_inv1t, k_row_inv1x, k_row_inv2x) behind either walking column pass
     (k_col_mw, k_col_mx), the candidates the benchmark's autotuner chooses
@@ -162,7 +164,7 @@ def test_4096_timed_schedule_explicitly(lib, col_pass, row_inv0):
     intermediates)."""
     s = sample(4096)
     plan = lib.Plan(s.nest, "fp32", zero_rim=True)
-    plan.set_schedule(col_pass, row_inv0)
+    plan.set_schedule(col_pass, row_inv0, 0, 0, 0, row_fwd)
     for _ in range(2):
         gx, gy = run_gpu(plan, s.sigma)
         plan.check()

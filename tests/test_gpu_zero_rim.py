@@ -63,21 +63,24 @@ def test_zero_rim_4096_sampled(lib):
     assert abs(np.sum(s * gx[0])) <= 1e-5 * np.sum(np.abs(s * gx[0]))
 
 
+@pytest.mark.parametrize("n,row_fwd", [(64, 0), (1024, 1), (1024, 2)])
 @pytest.mark.parametrize("where", ["row0", "row_last", "col1", "col_last"])
-def test_rim_violation_reported(lib, where):
-    n = 64
+def test_rim_violation_reported(lib, where, n, row_fwd):
+    """Every forward row kernel of the zero-rim plan checks the rim: k_row_fwd_m
+    (row_fwd 0), k_row_fwd_m2 (1) and the walking k_row_fwd_x (2)."""
     nest = W.Nest(n=n)
     s = rim_free(n, 5)
     plan = lib.Plan(nest, "fp32", zero_rim=True)
+    plan.set_schedule(0, 0, 0, 0, 0, row_fwd)
     run_gpu(plan, [s])
     plan.check()  # clean input: no report
     bad = s.copy()
     if where == "row0":
-        bad[0, 30] = 1.0
+        bad[0, n // 2 - 2] = 1.0
     elif where == "row_last":
         bad[n - 2, 7] = 1.0
     elif where == "col1":
-        bad[33, 1] = 1.0
+        bad[n // 2 + 1, 1] = 1.0
     else:
         bad[12, n - 1] = 1.0
     run_gpu(plan, [bad])
