@@ -1931,14 +1931,16 @@ __global__ void __launch_bounds__((1 << LOGN) / 4) k_row_fwd_m2(SolveArgs<float>
 // walking its own items on its own named barrier.  Also verifies the zero rim
 // as k_row_fwd_m does.  FP32, N >= 1024, one patch, no batch view.
 // Shared memory per group: sigma rows [4][N] | exchange buffers [2][SP_ROW] |
-// first pair's bins [2][SP_ROW].
+// 32 bytes | first pair's bins [2][SP_ROW].  (The 32 bytes put the two pairs'
+// bins of one index in different banks: the unpack of a quarter warp reads
+// four bins of each half of each pair.)
 template <int LOGN>
 struct KFx {
     static constexpr int N = 1 << LOGN, Q = N >> 4;
     static constexpr int G = Q >= 256 ? 1 : 256 / Q;
     static constexpr int THREADS = G * Q;
     static constexpr size_t XB = 2 * (size_t)KShape<LOGN>::SP_ROW * 8;
-    static constexpr size_t GROUP_BYTES = 4 * (size_t)N * 4 + 2 * XB;
+    static constexpr size_t GROUP_BYTES = 4 * (size_t)N * 4 + 2 * XB + 32;
     static constexpr size_t SMEM = G * GROUP_BYTES;
 };
 
@@ -1957,7 +1959,7 @@ __global__ void __launch_bounds__(KFx<LOGN>::THREADS, 1) k_row_fwd_x(const __gri
     unsigned char *gb = smem_fx + (size_t)g * R::GROUP_BYTES;
     float *rows = reinterpret_cast<float *>(gb);
     C *xb = reinterpret_cast<C *>(gb + 4 * (size_t)N * 4);
-    C *za = xb + 2 * SP;
+    C *za = xb + 2 * SP + 4;
     __shared__ int rim_bad;
     if (t == 0)
         rim_bad = 0;
