@@ -189,8 +189,8 @@ sgf_status sgf_plan_footprint(const sgf_plan *plan, size_t *workspace_bytes, siz
  * SGF_PLAN_ZERO_RIM (one patch, the same guarantee as for the forces) the three
  * tables fold into one real table (the central-difference slope stencils of
  * the zero rim folded in) over sigma alone; such a plan runs the column
- * schedule col_pass = 2 only (SGF_EUNSUPPORTED where that does not apply:
- * SGF_BF16X at n = SGF_MAX_N).  The potential depends on the cell size (Phi
+ * schedules col_pass = 2 and, in SGF_FP32 with n >= 1024, 3 only
+ * (SGF_EUNSUPPORTED where they do not apply: SGF_BF16X at n = SGF_MAX_N).  The potential depends on the cell size (Phi
  * scales with h0 at fixed sigma) where the forces do not. */
 
 /* As sgf_plan_create with no spectra budget, with option flags (0 =
@@ -404,8 +404,8 @@ sgf_status sgf_solve_noalloc(sgf_plan *plan, const void *const *sigma, void *con
  *     cluster), 2 = as 1 with both parity halves in one CTA (no cluster; the
  *     column staged once), 3 = one thread per slot carrying both parity halves
  *     of its column, the fold of the halves in registers and the stage
- *     twiddles of the slot held in registers for the whole launch (force plans
- *     in SGF_FP32 with n >= 1024; batches run 2 in its place).
+ *     twiddles of the slot held in registers for the whole launch (SGF_FP32
+ *     with n >= 1024; batches run 2 in its place).
  *   row_inv0: 0 = level 0's inverse row pass with one CTA per (row pair,
  *     component), the finer levels through the nest kernel; 2 = the same with
  *     one CTA per row pair holding both components (two sequences per thread
@@ -458,8 +458,8 @@ sgf_status sgf_plan_schedule_get(const sgf_plan *plan, sgf_schedule *schedule);
 /* Errors: SGF_EINVAL for a NULL argument or a choice out of range;
  * SGF_EUNSUPPORTED for col_pass = 2 or row_inv0 = 1 on a SGF_BF16X plan of
  * n = SGF_MAX_N (those kernels have no shared memory left for the tensor-core
- * tiles there), col_pass = 3 outside zero-rim SGF_FP32 force plans of
- * n >= 1024, row_inv0 = 2 on a potential plan, row_inv0 = 3, 4 or 5 where it
+ * tiles there), col_pass = 3 outside zero-rim SGF_FP32 plans of n >= 1024,
+ * col_pass other than 2 and 3 on a zero-rim potential plan, row_inv0 = 2 on a potential plan, row_inv0 = 3, 4 or 5 where it
  * does not apply, a radix plan 1 without its register-twiddle kernel,
  * row_fwd = 1 outside SGF_FP32 plans of n >= 1024, row_fwd = 2 outside
  * SGF_PLAN_ZERO_RIM SGF_FP32 plans of n >= 1024 (the autotuner

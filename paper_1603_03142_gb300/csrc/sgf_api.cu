@@ -1283,8 +1283,8 @@ cudaError_t launch_col(const sgf_plan *p, const SolveArgs<T> &a, cudaStream_t st
         return e;
     }
     if (p->merged) {
-        if (p->pot && p->sched.col_pass != 2)  // only k_col_mw reads the one-table potential spectra
-            return cudaErrorInvalidValue;
+        if (p->pot && p->sched.col_pass != 2 && p->sched.col_pass != 3)  // only k_col_mw and k_col_mx read
+            return cudaErrorInvalidValue;                                   // the one-table potential spectra
         return launch_pass_n<T>(col_m_pass(p), p->logN, a, 1, st, nullptr, p->tc);
     }
     cudaError_t e;
@@ -1321,14 +1321,14 @@ inline bool schedule_ok(const sgf_plan *p, const sgf_schedule &s)
     if ((s.col_radix != 0 && (s.col_radix != 1 || s.col_pass != 3)) ||
         (s.inv_radix != 0 && (s.inv_radix != 1 || s.row_inv0 < 4)))
         return false;
-    // k_col_mx: zero-rim forces, FP32 without tensor-core tiles, N >= 1024
-    if (s.col_pass == 3 && !(p->merged && !p->pot && p->prec == SGF_FP32 && p->N >= 1024))
+    // k_col_mx: zero-rim forces or potential, FP32 without tensor-core tiles, N >= 1024
+    if (s.col_pass == 3 && !(p->merged && p->prec == SGF_FP32 && p->N >= 1024))
         return false;
     if (s.row_inv0 == 3 && !p->tma_inv)
         return false;
     if (!p->merged && s.col_pass == 2 && (p->prec != SGF_FP32 || p->N < 512))  // k_col_w: FP32, N >= 512
         return false;
-    if (p->merged && p->pot && s.col_pass != 2)  // the zero-rim potential: k_col_mw only
+    if (p->merged && p->pot && s.col_pass != 2 && s.col_pass != 3)  // the zero-rim potential: k_col_mw, k_col_mx
         return false;
     if (p->pot && s.row_inv0 == 2)  // both components per CTA: a potential plan has one
         return false;

@@ -2425,7 +2425,9 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 1) k_col_mw(SolveAr
 // groups of N/16 threads per CTA (one group at N = 4096), each group walking
 // its own columns on its own named barrier, with the next column's input and
 // spectrum half rows copied in behind the inverse transforms.  FP32, no
-// tensor-core tiles, N >= 1024.
+// tensor-core tiles, N >= 1024.  NC = 1: the potential of a zero-rim potential
+// plan (Gphi, real and even in ky, alone; one inverse transform per column,
+// nothing parked).
 // Shared memory per group: column[N] | Gx, Gy half rows of both halves |
 // exchange buffers [2][SPC] | (PARK) Fy^ [2][N].
 // Fy^ parked in shared memory (true) or kept in registers (false).
@@ -2442,9 +2444,10 @@ struct KMx {
     static constexpr size_t SMEM = G * GROUP_BYTES;
 };
 
-template <int LOGN, bool PARK, int PLAN>
+template <int LOGN, bool PARK, int PLAN, int NC = 2>
 __global__ void __launch_bounds__(KMx<LOGN, PARK>::THREADS, 1) k_col_mx(SolveArgs<float> a)
 {
+    constexpr bool two = NC == 2;  // the forces (Gx, Gy); else the potential (Gphi alone)
     using C = float2;
     using M = KMx<LOGN, PARK>;
     using P = FR<LOGN, PLAN>;
@@ -2469,7 +2472,7 @@ __global__ void __launch_bounds__(KMx<LOGN, PARK>::THREADS, 1) k_col_mx(SolveArg
         const char *src = reinterpret_cast<const char *>(a.fwd + (size_t)kx * N);
         for (int o = j * 16; o < N * 8; o += Q * 16)
             cp16(reinterpret_cast<char *>(col) + o, src + o);
-        for (int h = 0; h < 4; ++h) {  // [half][table]: Gx rows at kx, Gy rows at N + 1 + kx
+        for (int h = 0; h < 4; h += two ? 1 : 2) {  // [half][table]: Gx rows at kx, Gy rows at N + 1 + kx
             const float *row = spec + ((size_t)(h & 1) * (N + 1) + kx) * QS + (h >> 1) * HQ;
             for (int o = j * 16; o < HQ * 4; o += Q * 16)
                 cp16(reinterpret_cast<char *>(gsp + h * HQ) + o, reinterpret_cast<const char *>(row) + o);
@@ -2491,23 +2494,37 @@ __global__ void __launch_bounds__(KMx<LOGN, PARK>::THREADS, 1) k_col_mx(SolveArg
             v[1][u] = hmul(x, twist_u(u));
         }
         fft_stages_rt<C, false, LOGN, PLAN, 2, 0>(v, xb, SPC, j, trw, bar, Q);
-        C fy[PARK ? 1 : 2][16];
+        C fy[PARK || !two ? 1 : 2][16];
+        if constexpr (two) {
 #pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const float *gx_r = gsp + (2 * b) * HQ, *gy_r = gsp + (2 * b + 1) * HQ;
+            for (int b = 0; b < 2; ++b) {
+                const float *gx_r = gsp + (2 * b) * HQ, *gy_r = gsp + (2 * b + 1) * HQ;
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const int kp = j + u * Q;
-                const bool hi = 2 * kp + b > N;
-                const int q = hi ? N - kp - b : kp;
-                const float gx = gx_r[q];                  // Gx even in ky
-                const float gy = hi ? -gy_r[q] : gy_r[q];  // Gy odd in ky
-                const C y = hmk<C>(-gy * v[b][u].y, gy * v[b][u].x);  // i gy v
-                if constexpr (PARK)
-                    park[b * N + kp] = y;
-                else
-                    fy[b][u] = y;
-                v[b][u] = hmk<C>(-gx * v[b][u].y, gx * v[b][u].x);  // i gx v
+                for (int u = 0; u < 16; ++u) {
+                    const int kp = j + u * Q;
+                    const bool hi = 2 * kp + b > N;
+                    const int q = hi ? N - kp - b : kp;
+                    const float gx = gx_r[q];                  // Gx even in ky
+                    const float gy = hi ? -gy_r[q] : gy_r[q];  // Gy odd in ky
+                    const C y = hmk<C>(-gy * v[b][u].y, gy * v[b][u].x);  // i gy v
+                    if constexpr (PARK)
+                        park[b * N + kp] = y;
+                    else
+                        fy[b][u] = y;
+                    v[b][u] = hmk<C>(-gx * v[b][u].y, gx * v[b][u].x);  // i gx v
+                }
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const float *gp_r = gsp + (2 * b) * HQ;
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int kp = j + u * Q;
+                    const int q = 2 * kp + b > N ? N - kp - b : kp;
+                    const float gp = gp_r[q];  // Gphi real, even in ky
+                    v[b][u] = hmk<C>(gp * v[b][u].x, gp * v[b][u].y);
+                }
             }
         }
         if (kx + step <= N) {  // uniform over the group
@@ -2519,7 +2536,7 @@ __global__ void __launch_bounds__(KMx<LOGN, PARK>::THREADS, 1) k_col_mx(SolveArg
 #pragma unroll
         for (int u = 0; u < 16; ++u)
             dst[bwd_index(N, N, 0, kx, j + u * Q)] = hadd(v[0][u], hmulc(v[1][u], twist_u(u)));
-        if constexpr (PARK) {  // this thread's own values: no barrier
+        if constexpr (two && PARK) {  // Fy^: this thread's own values, no barrier
 #pragma unroll
             for (int b = 0; b < 2; ++b)
 #pragma unroll
@@ -2529,7 +2546,7 @@ __global__ void __launch_bounds__(KMx<LOGN, PARK>::THREADS, 1) k_col_mx(SolveArg
 #pragma unroll
             for (int u = 0; u < 16; ++u)
                 dst[bwd_index(N, N, 1, kx, j + u * Q)] = hadd(v[0][u], hmulc(v[1][u], twist_u(u)));
-        } else {
+        } else if constexpr (two) {
             fft_stages_rt<C, true, LOGN, PLAN, 2, 0>(fy, xb, SPC, j, trw, bar, Q);
 #pragma unroll
             for (int u = 0; u < 16; ++u)
@@ -2679,11 +2696,12 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
 {
     using K = KShape<LOGN>;
     using S = KSmem<T, LOGN, TC>;
-    static std::atomic<unsigned long long> d[38];
+    static std::atomic<unsigned long long> d[40];
     static std::atomic<int> res_mx[64], res_mx1[64];  // resident CTAs of the register-twiddle column pass (plans 0, 1)
     static std::atomic<int> res_rx[64], res_rx1[64];  // and of the register-twiddle inverse row pass
     static std::atomic<int> res_r2[64], res_r21[64];  // and of its two-pair form
     static std::atomic<int> res_fx[64];               // and of the register-twiddle forward row pass
+    static std::atomic<int> res_mxp[64], res_mxp1[64]; // and of the register-twiddle column pass, potential
     static std::atomic<int> res_mw[64], res_mw1[64];  // resident CTAs of the walking column pass (NC = 2, 1)
     static std::atomic<int> res_fm[64];               // and of the walking zero-rim forward row pass
     static std::atomic<int> res_ri1[64], res_ri2[64]; // and of the walking inverse row passes (tensor cores)
@@ -2781,6 +2799,12 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
                 (e = ensure_smem(k_row_fwd2<LOGN>, S::tw() + 4 * (size_t)K::SP_ROW * sizeof(float2), d[35])) !=
                     cudaSuccess ||
                 (e = ensure_smem(k_row_fwd_x<LOGN, 0>, KFx<LOGN>::SMEM, d[36])) != cudaSuccess ||
+                (e = ensure_smem(k_col_mx<LOGN, kMxPark, 0, 1>, MX::SMEM, d[37])) != cudaSuccess ||
+                (e = resident_ctas(k_col_mx<LOGN, kMxPark, 0, 1>, MX::THREADS, MX::SMEM, res_mxp, &grid)) !=
+                    cudaSuccess ||
+                (e = ensure_smem(k_col_mx<LOGN, kMxPark, 1, 1>, MX::SMEM, d[38])) != cudaSuccess ||
+                (e = resident_ctas(k_col_mx<LOGN, kMxPark, 1, 1>, MX::THREADS, MX::SMEM, res_mxp1, &grid)) !=
+                    cudaSuccess ||
                 (e = resident_ctas(k_row_fwd_x<LOGN, 0>, KFx<LOGN>::THREADS, KFx<LOGN>::SMEM, res_fx, &grid)) !=
                     cudaSuccess ||
                 (e = resident_ctas(k_row_inv2x<LOGN, 1>, KR2x<LOGN>::THREADS, KR2x<LOGN>::SMEM, res_r21, &grid)) !=
@@ -3021,10 +3045,13 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
                 return cudaErrorInvalidValue;
             using MX = KMx<LOGN, kMxPark>;
             const bool r1 = pass == PASS_COL_MX_R1;
-            auto *kern = r1 ? k_col_mx<LOGN, kMxPark, 1> : k_col_mx<LOGN, kMxPark, 0>;
+            const bool pot = a.ncomp == 1;  // the zero-rim potential
+            auto *kern = pot ? (r1 ? k_col_mx<LOGN, kMxPark, 1, 1> : k_col_mx<LOGN, kMxPark, 0, 1>)
+                             : (r1 ? k_col_mx<LOGN, kMxPark, 1> : k_col_mx<LOGN, kMxPark, 0>);
             int grid = 0;
-            if ((e = ensure_smem(kern, MX::SMEM, d[r1 ? 30 : 28])) != cudaSuccess ||
-                (e = resident_ctas(kern, MX::THREADS, MX::SMEM, r1 ? res_mx1 : res_mx, &grid)) != cudaSuccess)
+            if ((e = ensure_smem(kern, MX::SMEM, d[pot ? (r1 ? 38 : 37) : (r1 ? 30 : 28)])) != cudaSuccess ||
+                (e = resident_ctas(kern, MX::THREADS, MX::SMEM, pot ? (r1 ? res_mxp1 : res_mxp) : (r1 ? res_mx1 : res_mx),
+                                   &grid)) != cudaSuccess)
                 return e;
             const int groups = (K::N + 1 + MX::G - 1) / MX::G;  // CTAs that give every group a column
             kern<<<grid < groups ? grid : groups, MX::THREADS, MX::SMEM, st>>>(a);

@@ -167,11 +167,12 @@ def test_force_entry_points_refuse_potential_plans(lib):
     with pytest.raises(lib.SgfError) as ei:
         lib.Batch([pp])
     assert ei.value.status == lib.SGF_EUNSUPPORTED
-    zr = lib.Plan(nest, "fp32", zero_rim=True, potential=True)  # the zero-rim potential: col_pass 2 only
+    zr = lib.Plan(nest, "fp32", zero_rim=True, potential=True)  # the zero-rim potential: col_pass 2 (3 from n = 1024)
     assert zr.schedule()["col_pass"] == 2
-    with pytest.raises(lib.SgfError) as ei:
-        zr.set_schedule(0, 0)
-    assert ei.value.status == lib.SGF_EUNSUPPORTED
+    for col in (0, 3):
+        with pytest.raises(lib.SgfError) as ei:
+            zr.set_schedule(col, 0)
+        assert ei.value.status == lib.SGF_EUNSUPPORTED
     # a shared plan keeps the potential spectra, and gives the same numbers
     q = pp.share()
     a = pp.solve_potential(s)[0]
@@ -205,6 +206,31 @@ def test_zero_rim_potential_oracle(lib, prec, n):
         ii, jj = rng.integers(0, n, 40), rng.integers(0, n, 40)
         ref = oracle.potential_at(nest, sigma, np.zeros_like(ii), ii, jj)
         assert np.abs(phi[0][jj, ii] - ref).max() <= tol(prec, n) * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n", [1024, 2048])
+def test_zero_rim_potential_register_twiddle_column(lib, n):
+    """col_pass 3 on a zero-rim potential plan (k_col_mx with one component, in
+    both radix plans, behind both walking forward row kernels) against col_pass 2
+    (k_col_mw): same expressions, so the potentials agree to rounding; and
+    against the oracle on sampled cells."""
+    nest = W.Nest(n=n)
+    sigma = _zero_rim_sigma(n, 50 + n)
+    plan = lib.Plan(nest, "fp32", potential=True, zero_rim=True)
+    plan.set_schedule(2, 0)
+    ref_gpu = run_phi(plan, sigma)[0]
+    eps = np.finfo(np.float32).eps
+    scale = np.abs(ref_gpu).max()
+    for radix in (0, 1):
+        for fw in (0, 2):
+            plan.set_schedule(3, 5, 0, radix, 0, fw)
+            phi = run_phi(plan, sigma)[0]
+            plan.check()
+            assert np.abs(phi - ref_gpu).max() <= 64 * eps * scale, (radix, fw)
+    rng = np.random.Generator(np.random.PCG64(51))
+    ii, jj = rng.integers(0, n, 24), rng.integers(0, n, 24)
+    ref = oracle.potential_at(nest, sigma, np.zeros_like(ii), ii, jj)
+    assert np.abs(phi[jj, ii] - ref).max() <= tol("fp32", n) * np.abs(ref).max()
 
 
 def test_zero_rim_potential_matches_general_4096(lib):
