@@ -1774,11 +1774,32 @@ sgf_status batch_build(sgf_batch *bt)
             g.n_fwd = (int)members[gi].size();
         }
         g.map_col = maps.size();
-        for (int k : members[gi]) {
-            const sgf_plan *p = bt->plans[k];
-            const int n = g.sched.col_case3 == 0 ? (int)p->work_main.size() : (int)p->work_all.size();
-            for (int o = 0; o < n; ++o)
-                maps.push_back(make_int2(k, o));
+        {
+            // work item o of every plan sharing one set of spectra, then o + 1: the
+            // column kernel (k_col_w) runs neighbouring map rows of one column
+            // together, so those CTAs read the same spectrum rows while they are in L2
+            auto items = [&](const sgf_plan *p) {
+                return g.sched.col_case3 == 0 ? (int)p->work_main.size() : (int)p->work_all.size();
+            };
+            std::vector<std::vector<int>> by_spec;
+            std::map<const void *, int> spec_idx;
+            for (int k : members[gi]) {
+                const void *key = bt->plans[k]->spec->dev;
+                if (!spec_idx.count(key)) {
+                    spec_idx[key] = (int)by_spec.size();
+                    by_spec.emplace_back();
+                }
+                by_spec[spec_idx[key]].push_back(k);
+            }
+            for (const auto &ks : by_spec) {
+                int nmax = 0;
+                for (int k : ks)
+                    nmax = std::max(nmax, items(bt->plans[k]));
+                for (int o = 0; o < nmax; ++o)
+                    for (int k : ks)
+                        if (o < items(bt->plans[k]))
+                            maps.push_back(make_int2(k, o));
+            }
         }
         g.n_col = (int)(maps.size() - g.map_col);
         g.map_grp = maps.size();

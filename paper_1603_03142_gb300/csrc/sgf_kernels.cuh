@@ -593,6 +593,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
 // k_col_sum, the others fold the odd half through shared memory, each half
 // storing one component.  FP32 without tensor-core tiles, N >= 512 (FP64's two
 // sequences per thread need more than 128 registers).
+// Batches launch the map rows along x and the columns along y, so that the
+// CTAs of one column run the map rows in order: the batch orders its rows so
+// that work items reading the same spectra (plans sharing them) are
+// neighbours, and those CTAs find the spectrum rows in L2.
 // Shared memory: twiddle area | sbuf[2][SPC] | stage[2] { column[N] (complex),
 // both halves' two spectrum half rows, [half][x, y][N/2 + 4] reals }.  The dual
 // inverse transforms of half b use 2 SPC from sbuf + 2 b SPC (reaching over the
@@ -600,7 +604,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
 template <typename T, int LOGN, bool BATCH>
 __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 1) k_col_w(SolveArgs<T> a0, BatchView<T> bv)
 {
-    const int2 wm = BATCH ? bv.map[blockIdx.y] : make_int2(0, (int)blockIdx.y);
+    const int2 wm = BATCH ? bv.map[blockIdx.x] : make_int2(0, (int)blockIdx.y);
     const SolveArgs<T> &a = BATCH ? bv.args[wm.x] : a0;
     using C = typename Cx<T>::C;
     using K = KShape<LOGN>;
@@ -613,7 +617,7 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 1) k_col_w(SolveArg
     C *sbuf = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
     unsigned char *stage_base = reinterpret_cast<unsigned char *>(sbuf + 2 * SPC);
     constexpr size_t stage_bytes = (size_t)N * sizeof(C) + 4 * (size_t)HQ * sizeof(T);
-    const int kx = blockIdx.x;
+    const int kx = BATCH ? (int)blockIdx.y : (int)blockIdx.x;
     const ColWork w = a.col_list[wm.y];
     const ColOutput o = a.outs[w.out];
     const int t = threadIdx.x;
@@ -2927,8 +2931,8 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
         if constexpr (!TC && K::HB_ROW > 0 && sizeof(T) == 4) {  // FP64's two sequences need > 128 registers
             if (S::col_w() > kMaxDynSmem)
                 return cudaErrorInvalidConfiguration;
-            SGF_LAUNCH((k_col_w<T, LOGN, false>), (k_col_w<T, LOGN, true>), 23, S::col_w(), dim3(K::N + 1, count),
-                       K::ROW_THREADS)
+            SGF_LAUNCH((k_col_w<T, LOGN, false>), (k_col_w<T, LOGN, true>), 23, S::col_w(),
+                       batch ? dim3(count, K::N + 1) : dim3(K::N + 1, count), K::ROW_THREADS)
         } else {
             return cudaErrorInvalidValue;
         }
