@@ -562,6 +562,58 @@ def run_gpu(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_nest_solves(args, world, rank, local):
+    """--solve-only --nest-levels L: one general FP32 nest plan (the concentric
+    nest of the batched workload, n x n cells a level) and its timed solves on
+    two rotating sets of device buffers; prints a short line (a small device
+    footprint, for ncu captures of the nest kernels)."""
+    import numpy as np
+    import torch
+    from paper_1603_03142_gb300 import sgf, workloads as W
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rng = np.random.Generator(np.random.PCG64(args.seed + rank))
+    nest, sigma = W.random_nest_problem(rng, args.n, args.nest_levels)
+    plan = sgf.Plan(nest, "fp32")
+    if args.schedule == "auto":
+        plan.autotune(reps=3)
+    else:
+        parts = [int(x) for x in args.schedule.split(",")]
+        plan.set_schedule(parts[0], parts[1], 0, 0, 0, parts[2] if len(parts) > 2 else 0)
+    sig = [[torch.from_numpy(a.astype(np.float32)).to(dev).roll(shifts=k, dims=1).contiguous() for a in sigma]
+           for k in range(2)]
+    fx = [[torch.empty_like(a) for a in s] for s in sig]
+    fy = [[torch.empty_like(a) for a in s] for s in sig]
+    stream = torch.cuda.current_stream(dev)
+
+    def step(k):
+        q = k % 2
+        plan.solve_ptrs([a.data_ptr() for a in sig[q]], [a.data_ptr() for a in fx[q]],
+                        [a.data_ptr() for a in fy[q]], stream)
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    plan.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for k in range(args.steps):
+        step(k)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    plan.profile(False)
+    plan.check()
+    prof = plan.profile_read()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if rank == 0:
+        print(json.dumps({"mode": "solve-only", "n": args.n, "levels": args.nest_levels, "ms_per_step": ms,
+                          "cells_per_s": args.nest_levels * args.n * args.n / (ms / 1e3),
+                          "schedule": plan.schedule(),
+                          "kernel_ms": {k: v["ms"] / max(1, v["launches"]) for k, v in prof["kernels"].items()
+                                        if v["launches"]},
+                          "device_bytes": torch.cuda.max_memory_allocated(dev) + plan.stats()["workspace_bytes"] +
+                          plan.stats()["spectra_bytes"]}), flush=True)
+
+
 def run_batched(args, world, rank, local):
     """Batched workload: independent concentric nests of uneven N and level
     count solved as one fused batch (sgf_batch_*).  value = all cells of all
@@ -761,6 +813,8 @@ def main():
     ap.add_argument("--no-forest", action="store_true", help="skip the two-disk forest (Example 3) timing")
     ap.add_argument("--solve-only", action="store_true",
                     help="only the timed solves of the one plan (no other path, no e2e); prints a short line")
+    ap.add_argument("--nest-levels", type=int, default=0,
+                    help="with --solve-only: a general FP32 nest of this many levels (n x n cells each) instead")
     ap.add_argument("--no-nest-workloads", action="store_true",
                     help="uniform: skip the shortened batched and serving runs reported in config")
     ap.add_argument("--forest-n", type=int, default=512, help="cells per side of every patch of the forest")
@@ -793,6 +847,8 @@ def main():
         line = (run_batched if args.workload == "batched" else run_serving)(args, world, rank, local)
         if line is not None:
             print(json.dumps(line), flush=True)
+    elif args.solve_only and args.nest_levels > 0:
+        run_nest_solves(args, world, rank, local)
     else:
         run_gpu(args, world, rank, local)
     if world > 1:

@@ -585,6 +585,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
 }
 
 // ------------------------------------------------------------------- col_w
+// Bytes of one k_col_w input stage: the column, then either the quarter
+// spectrum half rows or, where they fit beside two CTAs per SM (N <= 1024), the
+// full complex spectrum rows of an input of Cases 2 and 3 (x and y tables,
+// 2N bins each), so that those are copied in ahead like the column instead of
+// being loaded in the product.
+template <typename T, int LOGN>
+struct ColWStage {
+    using C = typename Cx<T>::C;
+    static constexpr int N = 1 << LOGN;
+    static constexpr bool FULL = LOGN <= 11;
+    static constexpr size_t QB = 4 * (size_t)quarter_half(N) * sizeof(T);
+    static constexpr size_t FB = FULL ? 2 * (size_t)(2 * N) * sizeof(C) : 0;
+    static constexpr size_t BYTES = (size_t)N * sizeof(C) + (QB > FB ? QB : FB);
+};
+
 // k_col with both parity halves of a column in one CTA (thread t: half t / Q,
 // slot t mod Q), each half's transforms on its own named barrier: every input
 // column is staged once for both halves, and 16 warps fit per SM where the
@@ -598,7 +613,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
 // that work items reading the same spectra (plans sharing them) are
 // neighbours, and those CTAs find the spectrum rows in L2.
 // Shared memory: twiddle area | sbuf[2][SPC] | stage[2] { column[N] (complex),
-// both halves' two spectrum half rows, [half][x, y][N/2 + 4] reals }.  The dual
+// both halves' two spectrum half rows, [half][x, y][N/2 + 4] reals, or (see
+// ColWStage) the full rows [x, y][2N] complex }.  The dual
 // inverse transforms of half b use 2 SPC from sbuf + 2 b SPC (reaching over the
 // stages, free by then), and the fold reuses the start.
 template <typename T, int LOGN, bool BATCH>
@@ -616,7 +632,8 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 1) k_col_w(SolveArg
     C *tw = reinterpret_cast<C *>(smem_raw);
     C *sbuf = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
     unsigned char *stage_base = reinterpret_cast<unsigned char *>(sbuf + 2 * SPC);
-    constexpr size_t stage_bytes = (size_t)N * sizeof(C) + 4 * (size_t)HQ * sizeof(T);
+    using CS = ColWStage<T, LOGN>;
+    constexpr size_t stage_bytes = CS::BYTES;
     const int kx = BATCH ? (int)blockIdx.y : (int)blockIdx.x;
     const ColWork w = a.col_list[wm.y];
     const ColOutput o = a.outs[w.out];
@@ -641,6 +658,12 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 1) k_col_w(SolveArg
                     cp_block(dst + (2 * h + 1) * HQ, sp + ((size_t)(3 + f) * (N + 1) + kx) * QS + h * HQ,
                              (size_t)HQ * sizeof(T));
             }
+        } else if constexpr (CS::FULL) {  // x (and, forces, y) rows of the full spectra
+            const C *sp = reinterpret_cast<const C *>(a.spec) + ci.spec_off;
+            C *dst = reinterpret_cast<C *>(st + (size_t)N * sizeof(C));
+            cp_block(dst, sp + ((size_t)f * (N + 1) + kx) * P, (size_t)P * sizeof(C));
+            if (ci.kind == SPEC_FULL)
+                cp_block(dst + P, sp + ((size_t)(3 + f) * (N + 1) + kx) * P, (size_t)P * sizeof(C));
         }
     };
     cp_block(tw, a.tw, tw_bytes<C>(a.tw_entries));
@@ -711,6 +734,22 @@ __global__ void __launch_bounds__(KShape<LOGN>::ROW_THREADS, 1) k_col_w(SolveArg
                 if (f != 0)
                     tx = hmk<C>(-tx.y, tx.x);
                 acc[0][u] = hadd(acc[0][u], tx);
+            }
+        } else if constexpr (CS::FULL) {  // the staged full rows
+            const C *sx = reinterpret_cast<const C *>(st + (size_t)N * sizeof(C)), *sy = sx + P;
+            if (ci.kind == SPEC_FULL_PHI) {
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int ky = 2 * (j + u * Q) + b;
+                    acc[0][u] = hadd(acc[0][u], hmul(sx[ky], v[0][u]));
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int ky = 2 * (j + u * Q) + b;
+                    acc[0][u] = hadd(acc[0][u], hmul(sx[ky], v[0][u]));
+                    acc[1][u] = hadd(acc[1][u], hmul(sy[ky], v[0][u]));
+                }
             }
         } else if (ci.kind == SPEC_FULL_PHI) {
             const C *sx = reinterpret_cast<const C *>(a.spec) + ci.spec_off + ((size_t)f * (N + 1) + kx) * P;
@@ -2583,11 +2622,7 @@ struct KSmem {
         const size_t stage = (size_t)N * sizeof(C) + 2 * (size_t)quarter_half(N) * sizeof(T);
         return ctc(KK_COL) + tw() + (size_t)col_sp<C>(N) * sizeof(C) + 2 * stage;
     }
-    static size_t col_w()
-    {
-        const size_t stage = (size_t)N * sizeof(C) + 4 * (size_t)quarter_half(N) * sizeof(T);
-        return tw() + 2 * (size_t)col_sp<C>(N) * sizeof(C) + 2 * stage;
-    }
+    static size_t col_w() { return tw() + 2 * (size_t)col_sp<C>(N) * sizeof(C) + 2 * ColWStage<T, LOGN>::BYTES; }
     static size_t row_inv()
     {
         return rtc(KK_ROW_INV) + tw() + ((2 * (size_t)(N + 1) * sizeof(C) + 15) & ~(size_t)15) +
