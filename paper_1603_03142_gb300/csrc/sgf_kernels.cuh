@@ -379,10 +379,27 @@ __global__ void __launch_bounds__((1 << LOGN) / 4) k_row_fwd2(const __grid_const
 }
 
 // --------------------------------------------------------------------- col
+// Bytes of one k_col input stage: the column, then this parity's half of the
+// quarter spectrum rows or, for FP32 data with N <= 1024, this parity's bins of
+// the full complex spectrum rows of an input of Cases 2 and 3 (x and y tables,
+// N bins each, gathered from every other bin), copied in ahead like the column
+// instead of being loaded in the product.  Not in the tensor-core instances:
+// there the larger stage costs more in resident clusters than it saves.
+template <typename T, int LOGN, bool TC>
+struct ColStage {
+    using C = typename Cx<T>::C;
+    static constexpr int N = 1 << LOGN;
+    static constexpr bool FULL = sizeof(T) == 4 && LOGN <= 10 && !TC;
+    static constexpr size_t QB = 2 * (size_t)quarter_half(N) * sizeof(T);
+    static constexpr size_t FB = FULL ? 2 * (size_t)N * sizeof(C) : 0;
+    static constexpr size_t BYTES = (size_t)N * sizeof(C) + (QB > FB ? QB : FB);
+};
+
 // One 2-CTA cluster (the parity halves) per (column, work item); the
 // tensor-core instance takes kColWalk columns per cluster.
 // Shared memory: twiddle area | sbuf[SPC] | stage[2] { column[N] (complex),
-// this parity's half of the two spectrum rows, 2 x (N/2 + 4) reals }.  The
+// this parity's half of the two spectrum rows, 2 x (N/2 + 4) reals, or (see
+// ColStage) this parity's bins of the full rows [x, y][N] complex }.  The
 // dual inverse transform uses sbuf and the stages as two sequence buffers, and
 // the fold of the odd half reuses them afterwards.
 constexpr int kColWalk = 4;
@@ -406,7 +423,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
     C *tw = reinterpret_cast<C *>(smem_raw);
     C *sbuf = reinterpret_cast<C *>(smem_raw + tw_bytes<C>(a.tw_entries));
     unsigned char *stage_base = reinterpret_cast<unsigned char *>(sbuf + SPC);
-    constexpr size_t stage_bytes = (size_t)N * sizeof(C) + 2 * (size_t)HQ * sizeof(T);
+    using CS = ColStage<T, LOGN, TC>;
+    constexpr size_t stage_bytes = CS::BYTES;
     cg::cluster_group cluster = cg::this_cluster();
     const int b = (int)cluster.block_rank();  // parity half
     const ColWork w = a.col_list[wm.y];
@@ -435,6 +453,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
                 cp_block(dst, sp + ((size_t)f * (N + 1) + kx) * QS + b * HQ, (size_t)HQ * sizeof(T));
                 if (ci.kind == SPEC_QUARTER)
                     cp_block(dst + HQ, sp + ((size_t)(3 + f) * (N + 1) + kx) * QS + b * HQ, (size_t)HQ * sizeof(T));
+            } else if constexpr (CS::FULL) {  // this parity's bins ky = 2 k' + b of the x (and y) rows
+                const C *sp = reinterpret_cast<const C *>(a.spec) + ci.spec_off;
+                const C *rx = sp + ((size_t)f * (N + 1) + kx) * P, *ry = sp + ((size_t)(3 + f) * (N + 1) + kx) * P;
+                C *dst = reinterpret_cast<C *>(st + (size_t)N * sizeof(C));
+                const bool two = ci.kind == SPEC_FULL;
+                for (int q = threadIdx.x; q < N; q += blockDim.x) {
+                    cp8(dst + q, rx + 2 * q + b);
+                    if (two)
+                        cp8(dst + N + q, ry + 2 * q + b);
+                }
             }
         };
         issue(0);
@@ -509,6 +537,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
                         if (f != 0)
                             tx = hmk<C>(-tx.y, tx.x);
                         acc[0][u] = hadd(acc[0][u], tx);
+                    }
+                } else if constexpr (CS::FULL) {  // the staged bins of this parity
+                    const C *sx = reinterpret_cast<const C *>(st + (size_t)N * sizeof(C)), *sy = sx + N;
+                    if (ci.kind == SPEC_FULL_PHI) {
+#pragma unroll
+                        for (int u = 0; u < 16; ++u)
+                            acc[0][u] = hadd(acc[0][u], hmul(sx[j + u * Q], v[0][u]));
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) {
+                            acc[0][u] = hadd(acc[0][u], hmul(sx[j + u * Q], v[0][u]));
+                            acc[1][u] = hadd(acc[1][u], hmul(sy[j + u * Q], v[0][u]));
+                        }
                     }
                 } else if (ci.kind == SPEC_FULL_PHI) {
                     const C *sx = reinterpret_cast<const C *>(a.spec) + ci.spec_off + ((size_t)f * (N + 1) + kx) * P;
@@ -2619,8 +2660,7 @@ struct KSmem {
     }
     static size_t col()
     {
-        const size_t stage = (size_t)N * sizeof(C) + 2 * (size_t)quarter_half(N) * sizeof(T);
-        return ctc(KK_COL) + tw() + (size_t)col_sp<C>(N) * sizeof(C) + 2 * stage;
+        return ctc(KK_COL) + tw() + (size_t)col_sp<C>(N) * sizeof(C) + 2 * ColStage<T, LOGN, TC>::BYTES;
     }
     static size_t col_w() { return tw() + 2 * (size_t)col_sp<C>(N) * sizeof(C) + 2 * ColWStage<T, LOGN>::BYTES; }
     static size_t row_inv()
