@@ -438,9 +438,11 @@ sgf_status sgf_solve_noalloc(sgf_plan *plan, const void *const *sigma, void *con
  *     bin together, a whole 32-byte sector, and on plans without
  *     SGF_PLAN_ZERO_RIM all three fields (sigma and its two slopes) in that
  *     CTA, one after the other, the source rows read once (SGF_FP32, n >= 1024);
- *     2 (SGF_PLAN_ZERO_RIM plans, SGF_FP32, n >= 1024) = as 1 with one thread
- *     per slot carrying both parity halves and the slot's stage twiddles in
- *     registers, the CTAs walking items of two row pairs, each staging its
+ *     2 (SGF_FP32, n >= 1024; SGF_PLAN_ZERO_RIM plans, and other plans of
+ *     one patch) = one thread per slot carrying both parity halves and the
+ *     slot's stage twiddles in registers, the CTAs walking the row pairs
+ *     (zero-rim: items of two, stored as whole sectors as in 1; otherwise one,
+ *     its three fields from one staging of its sigma rows), each staging its
  *     next item's rows behind the current transforms.
  * A new plan starts from {0, 0, 0}, or from the schedule the autotuner recorded for
  * its key (device, n, precision, zero-rim, levels > 1); sgf_plan_share copies it. */
@@ -462,7 +464,7 @@ sgf_status sgf_plan_schedule_get(const sgf_plan *plan, sgf_schedule *schedule);
  * col_pass other than 2 and 3 on a zero-rim potential plan, row_inv0 = 2 on a potential plan, row_inv0 = 3, 4 or 5 where it
  * does not apply, a radix plan 1 without its register-twiddle kernel,
  * row_fwd = 1 outside SGF_FP32 plans of n >= 1024, row_fwd = 2 outside
- * SGF_PLAN_ZERO_RIM SGF_FP32 plans of n >= 1024 (the autotuner
+ * SGF_FP32 plans of n >= 1024 that are zero-rim or of one patch (the autotuner
  * skips all of these). */
 sgf_status sgf_plan_schedule_set(sgf_plan *plan, const sgf_schedule *schedule);
 

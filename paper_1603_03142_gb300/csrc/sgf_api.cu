@@ -1236,6 +1236,12 @@ inline int zero_rim_fwd_pass(const sgf_plan *p)
     return p->sched.row_fwd == 2 ? PASS_ROW_FWD_X : p->sched.row_fwd == 1 ? PASS_ROW_FWD_M2 : PASS_ROW_FWD_M;
 }
 
+// Three-field forward row pass of the plan's schedule.
+inline int general_fwd_pass(const sgf_plan *p)
+{
+    return p->sched.row_fwd == 2 ? PASS_ROW_FWD3X : p->sched.row_fwd == 1 ? PASS_ROW_FWD2 : PASS_ROW_FWD;
+}
+
 // Zero-rim column pass of the plan's schedule.
 inline int col_m_pass(const sgf_plan *p)
 {
@@ -1312,10 +1318,11 @@ inline bool schedule_ok(const sgf_plan *p, const sgf_schedule &s)
     // k_row_inv1x, k_row_inv2x: the tensor-map gather (row_inv0 = 3's conditions) with n >= 1024
     if ((s.row_inv0 == 4 || s.row_inv0 == 5) && !(p->tma_inv && p->N >= 1024))
         return false;
-    // two row pairs per CTA in the forward rows (k_row_fwd_m2 / k_row_fwd2; 2: k_row_fwd_x, zero-rim
-    // plans): FP32 without tensor-core tiles, N >= 1024
+    // forward rows, FP32 without tensor-core tiles, N >= 1024: two row pairs per CTA (k_row_fwd_m2 /
+    // k_row_fwd2), or 2: the register-twiddle engine (k_row_fwd_x on zero-rim plans; k_row_fwd3x on
+    // other plans of one patch, whose one forward slab is the patch's own rows)
     if (s.row_fwd != 0 && ((s.row_fwd != 1 && s.row_fwd != 2) || !(p->prec == SGF_FP32 && !p->tc && p->N >= 1024) ||
-                           (s.row_fwd == 2 && !p->merged)))
+                           (s.row_fwd == 2 && !p->merged && !(p->L == 1 && p->slabs.size() == 1))))
         return false;
     // radix plans: the register-twiddle kernels only (col_pass 3, row_inv0 4 and 5)
     if ((s.col_radix != 0 && (s.col_radix != 1 || s.col_pass != 3)) ||
@@ -1417,8 +1424,7 @@ sgf_status solve_core(sgf_plan *p, const void *const *sigma, void *const *fx, vo
         return ms;
     e = p->merged ? launch_pass_n<T>(zero_rim_fwd_pass(p), p->logN, a, 0, st,
                                      nullptr, p->tc)
-                  : launch_pass_n<T>(p->sched.row_fwd == 1 ? PASS_ROW_FWD2 : PASS_ROW_FWD, p->logN, a,
-                                     (int)p->items.size(), st, nullptr, p->tc);
+                  : launch_pass_n<T>(general_fwd_pass(p), p->logN, a, (int)p->items.size(), st, nullptr, p->tc);
     if (e != cudaSuccess)
         return cuda_fail(e, "row_fwd launch");
     if ((ms = mark(p, st)) != SGF_OK)
@@ -1599,8 +1605,8 @@ sgf_status solve_noalloc_impl(sgf_plan *p, const void *const *sigma, void *const
     a.partial = reinterpret_cast<typename SolveArgs<T>::C *>(partial);
     cudaError_t e = p->merged ? launch_pass_n<T>(zero_rim_fwd_pass(p), p->logN, a,
                                                  0, st, nullptr, p->tc)
-                              : launch_pass_n<T>(p->sched.row_fwd == 1 ? PASS_ROW_FWD2 : PASS_ROW_FWD, p->logN, a,
-                                                 (int)p->items.size(), st, nullptr, p->tc);
+                              : launch_pass_n<T>(general_fwd_pass(p), p->logN, a, (int)p->items.size(), st, nullptr,
+                                                 p->tc);
     if (e != cudaSuccess)
         return cuda_fail(e, "row_fwd launch");
     e = launch_col<T>(p, a, st);
@@ -2030,10 +2036,10 @@ sgf_status autotune_impl(sgf_plan *p, int reps, cudaStream_t st, double ms[SGF_A
     for (int k = 0; k < SGF_AUTOTUNE_TIMES; ++k)
         ms[k] = -1.0;
     sgf_schedule best = p->sched;
-    {  // forward rows: row_fwd 0, 1 (slots 13, 14) and, zero-rim plans, 2 (slot 17)
+    {  // forward rows: row_fwd 0, 1 (slots 13, 14) and 2 (slot 17)
         const int items = (int)p->items.size();
         const int kind[3] = {p->merged ? PASS_ROW_FWD_M : PASS_ROW_FWD, p->merged ? PASS_ROW_FWD_M2 : PASS_ROW_FWD2,
-                             PASS_ROW_FWD_X};
+                             p->merged ? PASS_ROW_FWD_X : PASS_ROW_FWD3X};
         const int slot[3] = {13, 14, 17};
         const int cnt = p->merged ? 0 : items;
         for (int c = 0; c < 3 && s == SGF_OK; ++c) {

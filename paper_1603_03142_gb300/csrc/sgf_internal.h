@@ -269,7 +269,8 @@ enum : int {
     PASS_ROW_INV2X = 20,    // PASS_ROW_INV1X with two row pairs per item (32-byte gather boxes; a.tmap_inv of boxes 8 x kTmaBox)
     PASS_ROW_INV2X_R1 = 21, // PASS_ROW_INV2X with radix plan 1
     PASS_ROW_FWD2 = 22,     // PASS_ROW_FWD with two work items and all three fields per CTA (FP32, N >= 1024, no batch view)
-    PASS_ROW_FWD_X = 23     // PASS_ROW_FWD_M2 walking, both halves per thread, register twiddles (FP32, N >= 1024, no batch view)
+    PASS_ROW_FWD_X = 23,    // PASS_ROW_FWD_M2 walking, both halves per thread, register twiddles (FP32, N >= 1024, no batch view)
+    PASS_ROW_FWD3X = 24     // PASS_ROW_FWD likewise for a plan of one patch (the three fields per row pair in one CTA)
 };
 // Batch mode of the transform passes: a block's nest and its local work index
 // come from a per-launch map (one int2 per block row), and that nest's

@@ -2134,6 +2134,134 @@ __global__ void __launch_bounds__(KFx<LOGN>::THREADS, 1) k_row_fwd_x(const __gri
         atomicOr(a.status, STATUS_RIM_NONZERO);
 }
 
+// The three-field forward row pass (k_row_fwd) of a plan of one patch without
+// the zero rim, on the register-twiddle engine: one thread per slot j carries
+// both parity halves of a row pair's transform with the slot's stage twiddles
+// in registers, and the CTA walks the row pairs.  A row pair's fields (sigma,
+// its x slope, its y slope, exactly as k_row_fwd forms them) all come from the
+// four sigma rows r0 - 1 .. r0 + 2 (clamped to the array), staged once by
+// cp.async into one of two buffers: the next pair's rows are copied in while
+// this pair's three fields are transformed one after the other.  The bins of a
+// field are unpacked through the exchange buffers and stored in 16-byte pieces
+// (one row pair).  G = 256 / (N/16) groups of N/16 threads per CTA, each
+// walking its own pairs on its own named barrier.  FP32, N >= 1024, no batch
+// view.  Shared memory per group: sigma rows [2][4][N] | exchange buffers
+// [2][SP_ROW].
+template <int LOGN>
+struct KF3x {
+    static constexpr int N = 1 << LOGN, Q = N >> 4;
+    static constexpr int G = Q >= 256 ? 1 : 256 / Q;
+    static constexpr int THREADS = G * Q;
+    static constexpr size_t ROWS = 4 * (size_t)N * 4;
+    static constexpr size_t GROUP_BYTES = 2 * ROWS + 2 * (size_t)KShape<LOGN>::SP_ROW * 8;
+    static constexpr size_t SMEM = G * GROUP_BYTES;
+};
+
+template <int LOGN, int PLAN>
+__global__ void __launch_bounds__(KF3x<LOGN>::THREADS, 1) k_row_fwd3x(const __grid_constant__ SolveArgs<float> a)
+{
+    using C = float2;
+    using C2 = float4;
+    using R = KF3x<LOGN>;
+    using P = FR<LOGN, PLAN>;
+    constexpr int N = R::N, Q = R::Q, SP = KShape<LOGN>::SP_ROW;
+    static_assert(Q >= 64, "named group barriers need whole warps");
+    extern __shared__ __align__(16) unsigned char smem_f3x[];
+    const int t = threadIdx.x;
+    const int g = t / Q, j = t - g * Q;
+    unsigned char *gb = smem_f3x + (size_t)g * R::GROUP_BYTES;
+    C *xb = reinterpret_cast<C *>(gb + 2 * R::ROWS);
+    const unsigned bar = 1 + g;
+    const int nl = a.n_log;
+    const FwdSlab sl = a.slabs[0];
+    const int items = N / 2;
+    C trw[P::NST - 1][15];
+    load_twiddles_rt<C, LOGN, PLAN>(trw, a.twn, j);
+    const TwLayout tl = tw_layout(F16<LOGN>::twlen, N);
+    const C wj = a.tw[tl.base + j];  // W_P^j
+    auto twist_u = [&](int u) { return hmul(wj, hmk<C>((float)kW32c[u], (float)-kW32s[u])); };
+    const float *src = a.src[0];
+    auto first_row = [&](int it) { return min(max(2 * it - 1, 0), N - 4); };
+    auto stage = [&](int it, int buf) {  // this group's threads: rows first_row .. + 3 (contiguous)
+        const char *s = reinterpret_cast<const char *>(src + (size_t)first_row(it) * N);
+        char *d = reinterpret_cast<char *>(gb + (size_t)buf * R::ROWS);
+        for (int o = j * 16; o < 4 * N * 4; o += Q * 16)
+            cp16(d + o, s + o);
+        cp_commit();
+    };
+    const int step = (int)gridDim.x * R::G;
+    int it = (int)blockIdx.x * R::G + g;
+    if (it < items)
+        stage(it, 0);
+    C2 *out = reinterpret_cast<C2 *>(a.fwd + sl.off);
+    for (int buf = 0; it < items; it += step, buf ^= 1) {  // uniform over the group
+        cp_wait<0>();
+        group_sync(bar, Q);  // this pair's rows are staged; the other buffer is free
+        if (it + step < items)
+            stage(it + step, buf ^ 1);
+        const int r0 = 2 * it, s0 = first_row(it);
+        const float *rows = reinterpret_cast<const float *>(gb + (size_t)buf * R::ROWS);
+        auto row = [&](int jj) { return rows + (size_t)(jj - s0) * N; };
+        auto field = [&](auto fcv) {  // one field after the other, each compiled on its own
+            constexpr int f = decltype(fcv)::value;
+            C v[2][16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int i = j + u * Q;
+                float fv[2] = {0.0f, 0.0f};
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int jj = r0 + h;
+                    if (i >= nl || jj >= nl)
+                        continue;
+                    if constexpr (f == 0) {
+                        fv[h] = row(jj)[i];
+                    } else if constexpr (f == 1) {
+                        const float *r = row(jj);
+                        const int il = i == 0 ? 0 : i - 1, ir = i == nl - 1 ? nl - 1 : i + 1;
+                        const float d = r[ir] - r[il];
+                        fv[h] = (ir - il == 2) ? 0.5f * d : d;
+                    } else {
+                        const int jd = max(jj - 1, 0), ju = min(jj + 1, nl - 1);
+                        const float d = row(min(ju, N - 1))[i] - row(min(jd, N - 1))[i];
+                        fv[h] = (jj == 0 || jj == nl - 1) ? d : 0.5f * d;
+                    }
+                }
+                const C z = hmk<C>(fv[0], fv[1]);
+                v[0][u] = z;
+                v[1][u] = hmul(z, twist_u(u));
+            }
+            fft_stages_rt<C, false, LOGN, PLAN, 2, 0>(v, xb, SP, j, trw, bar, Q);
+            group_sync(bar, Q);  // the last stage's reads of the exchange buffers are done
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int u = 0; u < 16; ++u)
+                    xb[b * SP + pad16(j + u * Q)] = v[b][u];
+            group_sync(bar, Q);
+            // X_a = (Z + conj Z~)/2, X_b = (Z - conj Z~)/(2i); Z~ = bin -kx, same parity half
+            for (int kx = j; kx <= N; kx += Q) {
+                const int bb = kx & 1, k = kx >> 1;
+                const int km = (N - bb - k) & (N - 1);
+                const C Z = xb[bb * SP + pad16(k)];
+                const C Zm = xb[bb * SP + pad16(km)];
+                C2 o;
+                o.x = 0.5f * (Z.x + Zm.x);
+                o.y = 0.5f * (Z.y - Zm.y);
+                o.z = 0.5f * (Z.y + Zm.y);
+                o.w = -0.5f * (Z.x - Zm.x);
+                out[(((size_t)f * (N + 1) + kx) * sl.rows + r0) >> 1] = o;
+            }
+            // the next field's transform writes the exchange buffers only after
+            // its first stage's barrier, when every thread has read them here
+        };
+        field(std::integral_constant<int, 0>{});
+        field(std::integral_constant<int, 1>{});
+        field(std::integral_constant<int, 2>{});
+    }
+    cp_wait<0>();  // nothing in flight at exit
+}
+
 // Column pass of a SGF_PLAN_ZERO_RIM plan: one forward transform, the two
 // merged spectra (Fx^ = Gx^ sigma^, Fy^ = Gy^ sigma^, both imaginary), and the
 // two inverse transforms one after the other; parity halves folded through
@@ -2780,6 +2908,7 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
     static std::atomic<int> res_rx[64], res_rx1[64];  // and of the register-twiddle inverse row pass
     static std::atomic<int> res_r2[64], res_r21[64];  // and of its two-pair form
     static std::atomic<int> res_fx[64];               // and of the register-twiddle forward row pass
+    static std::atomic<int> res_f3x[64];              // and of its three-field form
     static std::atomic<int> res_mxp[64], res_mxp1[64]; // and of the register-twiddle column pass, potential
     static std::atomic<int> res_mw[64], res_mw1[64];  // resident CTAs of the walking column pass (NC = 2, 1)
     static std::atomic<int> res_fm[64];               // and of the walking zero-rim forward row pass
@@ -2878,6 +3007,9 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
                 (e = ensure_smem(k_row_fwd2<LOGN>, S::tw() + 4 * (size_t)K::SP_ROW * sizeof(float2), d[35])) !=
                     cudaSuccess ||
                 (e = ensure_smem(k_row_fwd_x<LOGN, 0>, KFx<LOGN>::SMEM, d[36])) != cudaSuccess ||
+                (e = ensure_smem(k_row_fwd3x<LOGN, 0>, KF3x<LOGN>::SMEM, d[39])) != cudaSuccess ||
+                (e = resident_ctas(k_row_fwd3x<LOGN, 0>, KF3x<LOGN>::THREADS, KF3x<LOGN>::SMEM, res_f3x, &grid)) !=
+                    cudaSuccess ||
                 (e = ensure_smem(k_col_mx<LOGN, kMxPark, 0, 1>, MX::SMEM, d[37])) != cudaSuccess ||
                 (e = resident_ctas(k_col_mx<LOGN, kMxPark, 0, 1>, MX::THREADS, MX::SMEM, res_mxp, &grid)) !=
                     cudaSuccess ||
@@ -3069,6 +3201,22 @@ cudaError_t launch_pass(int pass, const SolveArgs<T> &a, int count, cudaStream_t
                 return e;
             const int groups = (a.ncomp * (K::N / 4) + R2::G - 1) / R2::G;  // CTAs that give every group an item
             kern<<<dim3(grid < groups ? grid : groups, count), R2::THREADS, R2::SMEM, st>>>(a);
+        } else {
+            return cudaErrorInvalidValue;
+        }
+        break;
+    }
+    case PASS_ROW_FWD3X: {
+        if constexpr (!TC && sizeof(T) == 4 && LOGN >= 10) {
+            if (batch)
+                return cudaErrorInvalidValue;
+            using F3 = KF3x<LOGN>;
+            int grid = 0;
+            if ((e = ensure_smem(k_row_fwd3x<LOGN, 0>, F3::SMEM, d[39])) != cudaSuccess ||
+                (e = resident_ctas(k_row_fwd3x<LOGN, 0>, F3::THREADS, F3::SMEM, res_f3x, &grid)) != cudaSuccess)
+                return e;
+            const int groups = (K::N / 2 + F3::G - 1) / F3::G;  // CTAs that give every group a row pair
+            k_row_fwd3x<LOGN, 0><<<grid < groups ? grid : groups, F3::THREADS, F3::SMEM, st>>>(a);
         } else {
             return cudaErrorInvalidValue;
         }

@@ -101,10 +101,12 @@ def test_nest_schedules_agree(lib, prec):
 @pytest.mark.parametrize("levels", [1, 3])
 def test_general_forward_two_pairs(lib, levels):
     """row_fwd = 1 on plans without the zero rim (k_row_fwd2: two row pairs and
-    the three fields per CTA) against row_fwd = 0 (k_row_fwd: one CTA per row
-    pair and field), on a uniform 1024^2 grid and on a 3-level 1024^2 nest whose
-    Case-2 phase slabs (m = 2, 4) give items of several slabs; same expressions,
-    so the forces agree to rounding.  Refused for BF16X, FP64 and n < 1024."""
+    the three fields per CTA) and, on the uniform grid, 2 (k_row_fwd3x: the
+    register-twiddle engine, walking row pairs) against row_fwd = 0 (k_row_fwd:
+    one CTA per row pair and field), on a uniform 1024^2 grid and on a 3-level
+    1024^2 nest whose Case-2 phase slabs (m = 2, 4) give items of several slabs;
+    same expressions, so the forces agree to rounding.  Refused for BF16X, FP64,
+    n < 1024 and (row_fwd 2) several patches."""
     rng = np.random.Generator(np.random.PCG64(40 + levels))
     if levels == 1:
         nest = W.Nest(n=1024)
@@ -113,22 +115,25 @@ def test_general_forward_two_pairs(lib, levels):
         nest, sigma = W.random_nest_problem(rng, 1024, levels)
     plan = lib.Plan(nest, "fp32")
     res = []
-    for fw in (0, 1):
+    fws = (0, 1, 2) if levels == 1 else (0, 1)  # 2: k_row_fwd3x, plans of one patch
+    for fw in fws:
         plan.set_schedule(2, 0, 0, 0, 0, fw)
         res.append(run_gpu(plan, sigma))
         plan.check()
     eps = np.finfo(np.float32).eps
-    for l in range(nest.levels):
-        scale = max(np.abs(res[0][0][l]).max(), np.abs(res[0][1][l]).max())
-        d = max(np.abs(res[0][0][l] - res[1][0][l]).max(), np.abs(res[0][1][l] - res[1][1][l]).max())
-        assert d <= 64 * eps * scale, (l, d / scale)
+    for other in res[1:]:
+        for l in range(nest.levels):
+            scale = max(np.abs(res[0][0][l]).max(), np.abs(res[0][1][l]).max())
+            d = max(np.abs(res[0][0][l] - other[0][l]).max(), np.abs(res[0][1][l] - other[1][l]).max())
+            assert d <= 64 * eps * scale, (l, d / scale)
     for p in (lib.Plan(nest, "bf16x"), lib.Plan(W.Nest(n=1024), "fp64"), lib.Plan(W.Nest(n=512), "fp32")):
         with pytest.raises(lib.SgfError) as ei:
             p.set_schedule(0, 0, 0, 0, 0, 1)
         assert ei.value.status == lib.SGF_EUNSUPPORTED
-    with pytest.raises(lib.SgfError) as ei:  # row_fwd = 2 (k_row_fwd_x): zero-rim plans only
-        plan.set_schedule(2, 0, 0, 0, 0, 2)
-    assert ei.value.status == lib.SGF_EUNSUPPORTED
+    if levels > 1:  # row_fwd = 2: zero-rim plans and plans of one patch only
+        with pytest.raises(lib.SgfError) as ei:
+            plan.set_schedule(2, 0, 0, 0, 0, 2)
+        assert ei.value.status == lib.SGF_EUNSUPPORTED
 
 
 def test_bf16x_4096_refuses_nest_inverse_schedule(lib):

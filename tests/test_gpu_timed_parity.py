@@ -111,7 +111,7 @@ def schedules(n, prec, zero_rim):
                 out.append((c, i, 0, 1, 0))
             if prec == "fp32" and n >= 1024 and (c in (2, 3) or not zero_rim):
                 out.append((c, i, 0, 0, 1))  # two row pairs per CTA in the forward rows
-            if zero_rim and prec == "fp32" and n >= 1024 and c in (2, 3) and i in (3, 5):
+            if prec == "fp32" and n >= 1024 and i in (3, 5) and (c in (2, 3) or not zero_rim):
                 out.append((c, i, 0, 0, 2))  # the walking register-twiddle forward rows
     return out
 
