@@ -410,22 +410,6 @@ def run_gpu(args, world, rank, local):
     if not args.no_forest:
         forest = time_forest(args, world, dev, stream)
 
-    # the batched (256 nests) and serving (Poisson mix) workloads, shortened, on the same GPU
-    batched = serving_runs = None
-    if world == 1 and not args.no_nest_workloads:
-        import copy
-        ba = copy.copy(args)
-        ba.steps, ba.warmup = 3, 2
-        batched = run_batched(ba, world, rank, local)
-        sa = copy.copy(args)
-        sa.warmup = 1
-        serving_runs = run_serving(sa, world, rank, local, streams=[(args.rate, 15.0), (0.0, 10.0)])
-        # every shape of the mix served, none rejected: the shapes over the cap regenerate most of
-        # their spectra at every solve (seconds each), so this stream runs at a low rate
-        serving_all = run_serving(sa, world, rank, local, streams=[(4.0, 4.0)], stream_large=True)
-        if serving_runs is not None and serving_all is not None:
-            serving_runs["all_shapes_stream"] = serving_all
-
     # e2e: host buffers through the C ABI, copies inside the timed region.  The
     # pipelined call (sgf_solve_host_many) over a ring of page-locked sets:
     # every step copies its density in and its forces out, overlapping the
@@ -497,6 +481,26 @@ def run_gpu(args, world, rank, local):
            "one_call_per_step": {"value": world * cells * e2e_steps / serial_s,
                                  "call": "sgf_solve_host (sigma copied in, Fx, Fy written in place to "
                                          "page-locked host memory by the inverse row pass; waits per step)"}}
+
+    # the batched (256 nests) and serving (Poisson mix) workloads, shortened, on the same GPU
+    # (after the end-to-end run: their servers hold most of the device and much page-locked memory)
+    batched = serving_runs = None
+    if world == 1 and not args.no_nest_workloads:
+        import copy
+        ba = copy.copy(args)
+        ba.steps, ba.warmup = 3, 2
+        batched = run_batched(ba, world, rank, local)
+        sa = copy.copy(args)
+        sa.warmup = 1
+        serving_runs = run_serving(sa, world, rank, local, streams=[(args.rate, 15.0), (0.0, 10.0)])
+        # every shape of the mix served, none rejected: the shapes over the cap regenerate most of
+        # their spectra at every solve (seconds each), so this stream runs at a low rate
+        serving_all = run_serving(sa, world, rank, local, streams=[(4.0, 4.0)], stream_large=True)
+        if serving_runs is not None and serving_all is not None:
+            serving_runs["all_shapes_stream"] = serving_all
+        import gc
+        gc.collect()  # the servers' plans, spectra and page-locked request buffers
+        torch.cuda.empty_cache()
 
     if rank != 0:
         return

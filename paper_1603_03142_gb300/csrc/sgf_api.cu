@@ -2344,21 +2344,28 @@ sgf_status sgf_plan_share_ex(const sgf_plan *src, sgf_precision precision, sgf_p
     plan_init(p, src->fo, precision, src->flags);
     p->sched = src->sched;
     p->device = src->device;
-    if (!schedule_ok(p, p->sched))
-        p->sched.row_inv0 = 0;
-    if (!schedule_ok(p, p->sched))
-        p->sched.col_pass = p->merged && p->pot ? 2 : 0;
-    if (!schedule_ok(p, p->sched)) {
-        delete p;
-        return fail(SGF_EUNSUPPORTED, "no kernel schedule applies to the shared plan (zero-rim potential with "
-                                      "SGF_BF16X needs n < %d)", SGF_MAX_N);
-    }
     p->spectra_budget = src->spectra_budget;  // the same resident sets as src's spectra
     sgf_status s = build_cover(p);
     if (s == SGF_OK) {
         build_lists(p);
-        s = plan_stream_layout(p);
+        // src's schedule where it applies to this plan (its precision, its lists);
+        // else the choices that always do, one pass at a time
+        if (!schedule_ok(p, p->sched))
+            p->sched.row_fwd = 0;
+        if (!schedule_ok(p, p->sched)) {
+            p->sched.row_inv0 = 0;
+            p->sched.inv_radix = 0;
+        }
+        if (!schedule_ok(p, p->sched)) {
+            p->sched.col_pass = p->merged && p->pot ? 2 : 0;
+            p->sched.col_radix = 0;
+        }
+        if (!schedule_ok(p, p->sched))
+            s = fail(SGF_EUNSUPPORTED, "no kernel schedule applies to the shared plan (zero-rim potential with "
+                                       "SGF_BF16X needs n < %d)", SGF_MAX_N);
     }
+    if (s == SGF_OK)
+        s = plan_stream_layout(p);
     if (s == SGF_OK) {
         p->spec = src->spec;
         p->spec->refs++;

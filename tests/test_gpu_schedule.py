@@ -134,6 +134,13 @@ def test_general_forward_two_pairs(lib, levels):
         with pytest.raises(lib.SgfError) as ei:
             plan.set_schedule(2, 0, 0, 0, 0, 2)
         assert ei.value.status == lib.SGF_EUNSUPPORTED
+    else:  # a shared plan takes the schedule (checked against its own lists), or falls back per pass
+        plan.set_schedule(2, 0, 0, 0, 0, 2)
+        q = plan.share()
+        assert q.schedule()["row_fwd"] == 2
+        gq = run_gpu(q, sigma)
+        assert np.array_equal(gq[0][0], res[2][0][0]) and np.array_equal(gq[1][0], res[2][1][0])
+        assert plan.share("bf16x").schedule()["row_fwd"] == 0
 
 
 def test_bf16x_4096_refuses_nest_inverse_schedule(lib):
