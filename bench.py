@@ -283,7 +283,8 @@ def run_gpu(args, world, rank, local):
     # the benchmark density is tapered to zero well inside the domain, so the
     # zero-rim plan (verified on the device every solve) is valid; the general
     # three-field path is timed beside it and reported in config
-    plan = sgf.Plan(nest, "fp32", zero_rim=not args.general)
+    # (--solve-only --solve-precision bf16x: the split-BF16 plan alone, for ncu captures of its kernels)
+    plan = sgf.Plan(nest, args.solve_precision if args.solve_only else "fp32", zero_rim=not args.general)
     plan_general = sgf.Plan(nest, "fp32") if not (args.general or args.solve_only) else None
     # the autotuner picks each pass's kernel schedule (same arithmetic; results agree to rounding),
     # unless --schedule fixes it
@@ -817,6 +818,8 @@ def main():
     ap.add_argument("--no-forest", action="store_true", help="skip the two-disk forest (Example 3) timing")
     ap.add_argument("--solve-only", action="store_true",
                     help="only the timed solves of the one plan (no other path, no e2e); prints a short line")
+    ap.add_argument("--solve-precision", default="fp32", choices=["fp32", "bf16x"],
+                    help="with --solve-only: the precision of the one plan")
     ap.add_argument("--nest-levels", type=int, default=0,
                     help="with --solve-only: a general FP32 nest of this many levels (n x n cells each) instead")
     ap.add_argument("--no-nest-workloads", action="store_true",
