@@ -73,3 +73,40 @@ def test_committed_traffic_record_names_the_timed_kernels(bench):
     assert set(d["dram_bytes_per_launch"]) == {"row_fwd", "col", "row_inv"}
     assert d["sources"] == list(bench.KERNEL_SOURCES)
     assert "--clock-control none" in d["command"]
+
+
+def test_fp32_pipe_record_goes_stale_with_the_sources(bench, tmp_path, monkeypatch):
+    (tmp_path / "profiles").mkdir()
+    rec = {"fma_pipe_active_pct": 48.0, "issue_active_pct": 49.0, "duration_us": 220.0}
+    (tmp_path / "profiles" / "traffic.json").write_text(
+        json.dumps({"csrc_sha256": "abc", "fp32_pipe_per_launch": {"col": rec}}))
+    monkeypatch.setattr(bench, "ROOT", tmp_path)
+    monkeypatch.setattr(bench, "csrc_digest", lambda: "abc")
+    assert bench.recorded_ncu("col", "fp32_pipe_per_launch") == rec
+    assert bench.recorded_ncu("row_inv", "fp32_pipe_per_launch") is None
+    monkeypatch.setattr(bench, "csrc_digest", lambda: "changed")
+    assert bench.recorded_ncu("col", "fp32_pipe_per_launch") is None
+
+
+def test_committed_records_match_the_sources(bench):
+    """The committed DRAM and FP32-pipe record was taken on the kernel sources in
+    the tree (else the bench would report it as null)."""
+    d = json.loads((ROOT / "profiles" / "traffic.json").read_text())
+    assert d["csrc_sha256"] == bench.csrc_digest()
+    assert set(d["fp32_pipe_per_launch"]) == {"row_fwd", "col", "row_inv"}
+
+
+def test_profile_commands_use_flags_bench_accepts():
+    """Every bench.py flag a committed profile summary's command uses is one the
+    bench's argument parser knows (the summaries must stay runnable)."""
+    import re
+    helptext = _run(["--help"]).stdout
+    flags = set()
+    for f in (ROOT / "profiles").glob("*.md"):
+        for line in f.read_text().splitlines():
+            if "bench.py" in line:
+                flags.update(re.findall(r"(--[a-z][a-z0-9-]*)", line.split("bench.py", 1)[1]))
+    flags -= {"--clock-control", "--set", "--section", "--metrics", "--csv", "--log-file", "--kernel-name-base"}
+    assert flags, "no bench.py command found under profiles/"
+    missing = sorted(fl for fl in flags if fl not in helptext)
+    assert not missing, missing
