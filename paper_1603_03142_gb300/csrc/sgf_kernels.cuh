@@ -627,10 +627,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(KShape<LOGN>::COL_TH
 
 // ------------------------------------------------------------------- col_w
 // Bytes of one k_col_w input stage: the column, then either the quarter
-// spectrum half rows or, where they fit beside two CTAs per SM (N <= 1024), the
-// full complex spectrum rows of an input of Cases 2 and 3 (x and y tables,
-// 2N bins each), so that those are copied in ahead like the column instead of
-// being loaded in the product.
+// spectrum half rows or, for N <= 2048, the full complex spectrum rows of an
+// input of Cases 2 and 3 (x and y tables, 2N bins each), so that those are
+// copied in ahead like the column instead of being loaded in the product (two
+// CTAs per SM still fit at N = 1024, one at 2048, where it measured faster all
+// the same; at 4096 two stages would not fit).
 template <typename T, int LOGN>
 struct ColWStage {
     using C = typename Cx<T>::C;
